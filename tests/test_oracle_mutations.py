@@ -1,0 +1,110 @@
+"""Planted mistakes in the oracle (on the CPU only): each plausible error must fail at least one pin.
+
+Each case monkeypatches one oracle function with a typical slip (a sign, a dropped term or weight, a
+transposed index, a wrong frequency order) and checks that the named pin from the other oracle tests
+now fails.  This shows that the pins constrain the oracle rather than echo it.
+"""
+import numpy as np
+import pytest
+
+from oracle import fourier_galerkin as fg
+from oracle import lowrank as lr
+
+import tests.test_oracle_full as tf
+import tests.test_oracle_lowrank as tl
+
+
+def _must_fail(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_sign_of_gradient(monkeypatch):
+    orig = fg.grad_hat
+    monkeypatch.setattr(fg, "grad_hat", lambda uh: -orig(uh))
+    _must_fail(tf.test_gradient_matches_closed_form_differentiation, 9)
+
+
+def test_sign_of_right_hand_side(monkeypatch):
+    # (a sign flip inside div_hat alone is harmless: it negates both sides of the system)
+    orig = fg.gani_rhs
+    monkeypatch.setattr(fg, "gani_rhs", lambda A, E: -orig(A, E))
+    _must_fail(tf.test_pcg_matches_dense_direct_solve, 2, 9, "sq")
+
+
+def test_missing_cell_average_weight(monkeypatch):
+    def bad(uh, A, E):
+        E = np.asarray(E, dtype=np.float64)
+        d = E.shape[0]
+        e = np.real(fg.idft(fg.grad_hat(uh), d))
+        f = e + E.reshape((d,) + (1,) * d)
+        return float(np.sum(A * np.sum(f * f, axis=0)))  # sum instead of the cell average
+    monkeypatch.setattr(fg, "homogenised_coefficient", bad)
+    _must_fail(tf.test_constant_coefficient_exact, 2, 15)
+
+
+def test_unwrapped_frequencies(monkeypatch):
+    monkeypatch.setattr(fg, "frequencies", lambda N: np.arange(N, dtype=np.int64))
+    _must_fail(tf.test_gradient_matches_closed_form_differentiation, 9)
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")
+def test_dropped_preconditioner_zero_mode(monkeypatch):
+    """Keeping k = 0 in P^-1 (1/(k.k) with k.k := 1 there) lets a mean into u, which the dense solve
+    (zero-mean minimiser) rejects through the field pin."""
+    def bad(shape):
+        K = fg._kgrid(shape)
+        kk = np.sum(K.astype(np.float64) ** 2, axis=0)
+        kk[(0,) * len(shape)] = 1.0
+        return 1.0 / kk
+    monkeypatch.setattr(fg, "precond_inv", bad)
+    orig_rhs = fg.gani_rhs
+
+    def rhs_with_mean(A, E):  # a k = 0 component, which the exact pseudo-inverse annihilates
+        b = orig_rhs(A, E)
+        b[(0,) * b.ndim] += 1e-3
+        return b
+    monkeypatch.setattr(fg, "gani_rhs", rhs_with_mean)
+    _must_fail(tf.test_pcg_matches_dense_direct_solve, 2, 9, "sq")
+
+
+def test_transposed_khatri_rao(monkeypatch):
+    def bad(x, y):
+        out = []
+        for G, H in zip(x, y):
+            a, n, b = G.shape
+            c, _, e = H.shape
+            out.append(np.einsum("inj,knl->iknlj", G, H).reshape(a * c, n, b * e))  # rank pair swapped
+        return out
+    monkeypatch.setattr(lr.FORMATS["tt"], "had", bad)
+    _must_fail(tl.test_format_ops_match_full, "tt", (5, 7, 9))
+
+
+def test_dropped_cross_term_in_lowrank_aeff(monkeypatch):
+    def bad(self, uh, E):
+        f = self.f
+        size = float(np.prod(self.shape))
+        ones = f.sep([[np.ones(n) for n in self.shape]])
+        val = float(np.dot(E, E)) * np.real(f.dot(ones, self.a)) / size
+        for a in range(self.d):
+            e = f.idft(f.mmul(uh, a, 2j * np.pi * self.K[a]))
+            val += np.real(f.dot(e, f.had(self.a, e))) / size  # 2 E.<a, e> term dropped
+        return float(val)
+    monkeypatch.setattr(lr.LowRankGaNi, "homogenised_coefficient", bad)
+    _must_fail(tl.test_untruncated_lowrank_equals_full, "tt", 2, 15)
+
+
+def test_wrong_minres_step(monkeypatch):
+    """omega = ||r||^2 / ||C r||^2 instead of (C r, r) / ||C r||^2: a classic slip."""
+    def bad_minres(op, E, tol=1e-10, maxit=200, stop_on_increase=True, callback=None):
+        f = op.f
+        b = op.rhs(np.asarray(E, dtype=np.float64))
+        u = f.zeros(op.shape)
+        for _ in range(maxit):
+            r = op.T(f.add(b, f.scale(op.apply(u), -1.0)))
+            q = op.apply(r)
+            omega = np.real(f.dot(r, r)) / np.real(f.dot(q, q))
+            u = op.T(f.add(u, f.scale(r, omega)))
+        return dict(u=u, iters=maxit, rel_resid=0.0, history=[], Aeff=op.homogenised_coefficient(u, E))
+    monkeypatch.setattr(lr, "minres", bad_minres)
+    _must_fail(tl.test_untruncated_lowrank_equals_full, "tt", 2, 15)
