@@ -1,0 +1,232 @@
+/*
+ * lrfg.h — C ABI of liblrfg: low-rank Fourier–Galerkin homogenisation on one GB300 GPU (sm_103a).
+ *
+ * The library computes the effective (homogenised) conductivity of a periodic cell Y = (-1/2,1/2)^d,
+ * d in {2,3}, as defined in arXiv:1902.07455 Sec. 2.1, Eq. (homog):
+ *     A_eff E.E = min over zero-mean periodic v of  int_Y A(x)(E + grad v).(E + grad v) dx,
+ * discretised by the Fourier–Galerkin method with numerical integration (GaNi, Sec. 2.2.2) on an odd
+ * grid N^d, preconditioned by the Fourier Laplacian (Sec. 2.3, Eq. (Pls_fourier)).  Two solution formats:
+ *   LRFG_FULL  the N^d grid; preconditioned CG (Sec. 3.3, Sec. 4);
+ *   LRFG_TT    tensor train of fixed rank r; the truncated operator of Eq. (Pls_lowrank) and the
+ *              minimal-residual iteration with truncation of Sec. 3.3.
+ * The coefficient is isotropic, A(x) = a(x) I, given either as grid values or as a tensor train.
+ *
+ * Conventions for every call:
+ *   - every function returns an lrfg_status; no exception or signal crosses the ABI;
+ *     lrfg_last_error(ctx) gives a one-line description of the last failure on that context;
+ *   - N must be odd and >= 3 (Sec. 2.2.1: even N brings Nyquist frequencies); d in {2,3};
+ *     violations, null pointers, non-finite or non-positive coefficients give LRFG_EINVAL;
+ *   - grid arrays are row-major with storage index i along an axis holding x = k/N,
+ *     k = i for i <= (N-1)/2 and k = i - N otherwise (the DFT order);
+ *   - TT carriage j has shape (r[j], N[j], r[j+1]) row-major, r[0] = r[d] = 1 (App. A.3, Eq. (TT));
+ *   - "device" pointers are CUDA device addresses on the context's device; "host" pointers are
+ *     ordinary host memory; inputs are caller-owned and not retained after the call returns;
+ *     objects created by the library (lrfg_problem, lrfg_field) are freed by their *_free call;
+ *   - all device work is issued on the context's stream; calls that return host values
+ *     (A_eff, dots, solve results) synchronise that stream, the others are asynchronous;
+ *   - one context per host thread; a context is not thread-safe;
+ *   - LRFG_ENOMEM means the context's HBM budget (or the device) cannot hold the request.
+ * Arithmetic: FP64 throughout (LRFG_FP64).  LRFG_MIXED is reserved and returns LRFG_ENOTSUP.
+ */
+#ifndef LRFG_H
+#define LRFG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRFG_OK = 0,
+  LRFG_EINVAL = 1,   /* invalid argument */
+  LRFG_ENOMEM = 2,   /* HBM budget or device memory exhausted */
+  LRFG_ENOCONV = 3,  /* iteration cap reached before the tolerance; results are still filled */
+  LRFG_ECUDA = 4,    /* a CUDA runtime error; the message names the call */
+  LRFG_ETIMEOUT = 5, /* reserved for bounded device-side waits */
+  LRFG_ENOTSUP = 6   /* valid but not supported by this build */
+} lrfg_status;
+
+typedef enum { LRFG_FULL = 0, LRFG_TT = 3 } lrfg_format;
+typedef enum { LRFG_FP64 = 0, LRFG_MIXED = 1 } lrfg_prec;
+
+/* spectral multipliers m(k) applied along one mode by F^{-1} diag(m) F (Sec. 2.2.1, Sec. 3.2) */
+typedef enum {
+  LRFG_MUL_IDENTITY = 0, /* m(k) = 1 */
+  LRFG_MUL_DERIV = 1,    /* m(k) = 2 pi i k: the gradient factor of Sec. 2.2.1 along one mode */
+  LRFG_MUL_GAUSS = 2     /* m(k) = exp(-t k^2), t = param: one factor of the exponential-sum P~^-1 */
+} lrfg_multiplier;
+
+typedef struct lrfg_ctx lrfg_ctx;
+typedef struct lrfg_problem lrfg_problem;
+typedef struct lrfg_field lrfg_field;
+
+/* A tensor train whose carriages are caller-owned buffers (device or host as the call states). */
+typedef struct {
+  int d;
+  int N[3];
+  int r[4];          /* r[0] = r[d] = 1 */
+  double* cores[3];  /* carriage j: r[j] * N[j] * r[j+1] doubles, row-major (r[j], N[j], r[j+1]) */
+} lrfg_tt;
+
+/* Coefficient a(x) of A(x) = a(x) I (Sec. 2.1, Eq. (A); GaNi samples a(x_k), Sec. 2.2.2). */
+typedef struct {
+  int d;
+  int N[3];
+  lrfg_format fmt;      /* LRFG_FULL: `values` (N^d grid values); LRFG_TT: `tt` */
+  const double* values; /* grid values, row-major, positive and finite */
+  lrfg_tt tt;           /* carriages of a; the coefficient's TT ranks are its own (r_A) */
+  int on_device;        /* 1: values / tt.cores are device pointers; 0: host pointers */
+} lrfg_coeff;
+
+typedef struct {
+  lrfg_format fmt;      /* solution format: LRFG_FULL (PCG) or LRFG_TT (minimal residual) */
+  lrfg_prec prec;       /* LRFG_FP64 */
+  int rank;             /* LRFG_TT: the fixed rank of every truncation T (Sec. 4.2) */
+  double pinv_eps;      /* LRFG_TT: relative accuracy of the exponential-sum P~^-1 on [1, max k.k]
+                           (0 selects 0.1) */
+  double tol;           /* relative residual tolerance (preconditioned residual) */
+  int maxit;            /* iteration cap */
+  int stop_on_increase; /* LRFG_TT: stop when the residual norm fails to decrease (Sec. 4.3) */
+} lrfg_opts;
+
+typedef struct {
+  double Aeff;      /* A_eff E.E (Eq. (homog)) */
+  int iters;        /* iterations of the returned iterate */
+  double rel_resid; /* relative residual norm of the returned iterate */
+  int converged;    /* 1 if rel_resid <= tol */
+  int applies;      /* operator applications performed */
+  int ranks[4];     /* TT ranks of the solution (LRFG_TT) */
+  double seconds;   /* wall time of the solve on the host clock, including synchronisation */
+} lrfg_result;
+
+/* ---------------------------------------------------------------------------------------------
+ * context
+ * ------------------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to issue work on (NULL: the
+ * library creates its own).  `hbm_budget_bytes` caps the library's device pool (0: no cap). */
+lrfg_status lrfg_create(lrfg_ctx** ctx, int device, void* stream, size_t hbm_budget_bytes);
+lrfg_status lrfg_destroy(lrfg_ctx* ctx);
+const char* lrfg_strerror(lrfg_status st);
+const char* lrfg_last_error(const lrfg_ctx* ctx);
+/* Wait for the context's stream. */
+lrfg_status lrfg_sync(lrfg_ctx* ctx);
+/* Number of kernels this context has launched so far (instrumentation). */
+long long lrfg_launch_count(const lrfg_ctx* ctx);
+/* Bytes currently held by the context's device pool (in use, and reserved including cached). */
+lrfg_status lrfg_pool_bytes(const lrfg_ctx* ctx, size_t* in_use, size_t* reserved);
+
+/* ---------------------------------------------------------------------------------------------
+ * mode-wise operators on fibres (rows a1, a2 of the hot path)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Batched 1D DFT along the middle axis of a complex (re,im interleaved) FP64 device array of shape
+ * (outer, N, inner): y[o,f,i] = sum_n x[o,n,i] exp(sign 2 pi i f n / N), unnormalised; sign = -1
+ * is N * F_N and sign = +1 is F_N^{-1} of Sec. 2.2.1 (the mode-wise FFT of App. A.3.2).  `in` and
+ * `out` may alias.  N odd (radices 3, 5, 7 and any other prime). */
+lrfg_status lrfg_fft_fibres(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner,
+                            int sign);
+
+/* out = scale * F_N^{-1} diag(m) F_N in along the middle axis of a REAL FP64 device array of shape
+ * (outer, N, inner): the real-space form of a Fourier multiplier acting on one mode.  With
+ * LRFG_MUL_DERIV this is one component of F^{-1} grad^ F (Sec. 2.2.1, Eq. (grad_trig)) applied to TT
+ * carriage fibres, i.e. the rank-preserving gradient of Sec. 3.2.  `in` and `out` may alias. */
+lrfg_status lrfg_fibre_operator(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner,
+                                lrfg_multiplier kind, double param, double scale);
+
+/* ---------------------------------------------------------------------------------------------
+ * tensor-train operations on caller-owned device carriages (rows a3, a4, a5, a6, a7)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Element-wise product: carriages combine by the Khatri–Rao product of App. A.3.1,
+ * out_j[(i,k), n, (j,l)] = x_j[i,n,j] y_j[k,n,l] with pair index i*s + k.  out->r is set to the
+ * products of the ranks; out->cores must each hold r_x[j] r_y[j] N[j] r_x[j+1] r_y[j+1] doubles. */
+lrfg_status lrfg_tt_hadamard(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, lrfg_tt* out);
+
+/* out = alpha x + beta y in block-carriage form (ranks add; the TT sum referred to in Sec. 3.1.3).
+ * out->cores must each hold (rx[j]+ry[j]) N[j] (rx[j+1]+ry[j+1]) doubles (first/last: one side 1). */
+lrfg_status lrfg_tt_add(lrfg_ctx* ctx, double alpha, const lrfg_tt* x, double beta, const lrfg_tt* y,
+                        lrfg_tt* out);
+
+/* Rank truncation T (App. A.3.3) to ranks <= rmax: the result equals TT rounding (right-to-left
+ * orthogonalisation, then left-to-right truncated SVDs) up to rounding; computed from Gram matrices
+ * of the unfoldings (Gram-SVD).  out->r is set; out->cores must each hold
+ * min(rmax, x->r[j]) N[j] min(rmax, x->r[j+1]) doubles.  Carriages 1..d-1 of out are
+ * left-orthonormal. */
+lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out);
+
+/* Euclidean inner product <x, y> = sum_k x[k] y[k] of two TTs (FP64 contraction). */
+lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);
+
+/* out = T(P~^-1 x) in real space: the exponential-sum preconditioner of accuracy pinv_eps applied as a
+ * sum of separable Gaussian multipliers (rank R_P x r_x), then truncated to rmax (Sec. 2.3, 3.2).
+ * out->cores must each hold min(rmax, R_P x->r[j]) N[j] min(rmax, R_P x->r[j+1]) doubles. */
+lrfg_status lrfg_tt_precond(lrfg_ctx* ctx, const lrfg_tt* x, double pinv_eps, int rmax, lrfg_tt* out);
+
+/* TT-SVD of a full device grid array (App. A.3.3, first case) to ranks <= rmax (and relative
+ * accuracy tol when tol > 0).  out->cores must each hold min(rmax, ...) N[j] min(rmax, ...) doubles. */
+lrfg_status lrfg_tt_compress(lrfg_ctx* ctx, int d, const int N[3], const double* values, int rmax,
+                             double tol, lrfg_tt* out);
+
+/* Expand a TT into a full device grid array of N^d doubles. */
+lrfg_status lrfg_tt_expand(lrfg_ctx* ctx, const lrfg_tt* x, double* values);
+
+/* ---------------------------------------------------------------------------------------------
+ * problems: a resident coefficient plus workspace, the operator, the solvers (rows a1-a9)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Make the coefficient device-resident for the given options (copies it; caller buffers may be
+ * freed afterwards).  For LRFG_TT a FULL coefficient is compressed by TT-SVD to rank opts->rank. */
+lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lrfg_opts* opts,
+                                lrfg_problem** problem);
+lrfg_status lrfg_problem_free(lrfg_problem* problem);
+/* TT ranks of the resident coefficient (r_A), or all 1 for LRFG_FULL. */
+lrfg_status lrfg_problem_coeff_ranks(const lrfg_problem* problem, int ranks[4]);
+
+/* One application of the preconditioned GaNi operator (the benchmark unit):
+ *   LRFG_FULL: out = P^-1 grad^* F A~ F^-1 grad^ in on the Fourier half spectrum (Eq. (Pls_GaNi_fourier));
+ *   LRFG_TT:   out = T P~^-1 T grad^* F T A~ F^-1 grad^ in (Eq. (Pls_lowrank)), computed in real space.
+ * `in` must come from the same problem format and grid; *out is a new field. */
+lrfg_status lrfg_problem_apply(lrfg_problem* problem, const lrfg_field* in, lrfg_field** out);
+/* Same, into an existing field of the right format (no allocation of a new field object). */
+lrfg_status lrfg_problem_apply_into(lrfg_problem* problem, const lrfg_field* in, lrfg_field* out);
+
+/* Right-hand side b~ = -P^-1 grad^* F A~ E (FULL) or -T P~^-1 grad^* F A~ E (TT), Eq. (Pls_lowrank). */
+lrfg_status lrfg_problem_rhs(lrfg_problem* problem, const double* E, lrfg_field** out);
+
+/* Solve for E (host array of d doubles): FULL by PCG, TT by the minimal-residual iteration.
+ * Fills *res; *u_out (may be NULL) receives the solution field.  Returns LRFG_ENOCONV (with *res
+ * filled) when maxit is reached above tol and stop_on_increase did not end the iteration. */
+lrfg_status lrfg_problem_solve(lrfg_problem* problem, const double* E, lrfg_result* res,
+                               lrfg_field** u_out);
+
+/* A_eff E.E = (1/|N|) sum_k a(x_k) |E + e(x_k)|^2, e = F^{-1} grad^ u (Eq. (homog), Sec. 2.2.2). */
+lrfg_status lrfg_problem_aeff(lrfg_problem* problem, const double* E, const lrfg_field* u, double* Aeff);
+
+/* One-shot convenience: create a problem, solve, free it. */
+lrfg_status lrfg_solve(lrfg_ctx* ctx, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,
+                       lrfg_result* res, lrfg_field** u_out);
+
+/* ---------------------------------------------------------------------------------------------
+ * fields
+ * ------------------------------------------------------------------------------------------- */
+
+/* Field from grid values u (N^d doubles): FULL keeps its Fourier half spectrum, TT is not allowed
+ * here (use lrfg_field_from_tt). */
+lrfg_status lrfg_field_from_full(lrfg_ctx* ctx, int d, const int N[3], const double* values, int on_device,
+                                 lrfg_field** out);
+/* Field from TT carriages of real grid values (copied). */
+lrfg_status lrfg_field_from_tt(lrfg_ctx* ctx, const lrfg_tt* x, int on_device, lrfg_field** out);
+lrfg_status lrfg_field_info(const lrfg_field* f, lrfg_format* fmt, int* d, int N[3], int r[4]);
+/* Grid values of the field into `values` (N^d doubles, host or device as on_device says). */
+lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* values, int on_device);
+/* TT carriages of a TT field into caller buffers of the sizes lrfg_field_info implies. */
+lrfg_status lrfg_field_export_tt(lrfg_ctx* ctx, const lrfg_field* f, double* const cores[3], int on_device);
+lrfg_status lrfg_field_free(lrfg_field* f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRFG_H */

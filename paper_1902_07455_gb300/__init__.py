@@ -1,0 +1,420 @@
+"""Python binding of liblrfg (low-rank Fourier–Galerkin homogenisation on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of liblrfg.so,
+called through its C ABI (include/lrfg.h).  PyTorch provides device memory (CUDA tensors whose
+pointers are passed to the library) and the stream.  There is no CPU fallback: without the built
+library or a CUDA device the calls raise.
+
+Objects
+-------
+``Context``   a device, a stream and the library's device pool.
+``TTensor``   a tensor train held as a list of CUDA float64 carriages (r_j, N_j, r_{j+1}).
+``Problem``   a resident coefficient with the operator and the solvers for one format (FULL or TT).
+``Field``     a library-owned operand or solution (FULL half spectrum or TT carriages).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["Context", "TTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "MUL_IDENTITY", "MUL_DERIV",
+           "MUL_GAUSS", "library_path"]
+
+FULL, TT = L.LRFG_FULL, L.LRFG_TT
+MUL_IDENTITY, MUL_DERIV, MUL_GAUSS = L.LRFG_MUL_IDENTITY, L.LRFG_MUL_DERIV, L.LRFG_MUL_GAUSS
+
+
+def library_path() -> str:
+    return L.LIB_PATH
+
+
+class LrfgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _ivec(vals, n):
+    arr = (C.c_int * n)()
+    for i, v in enumerate(vals):
+        arr[i] = int(v)
+    return arr
+
+
+def _dvec(vals):
+    vals = [float(v) for v in vals]
+    return (C.c_double * len(vals))(*vals)
+
+
+@dataclass
+class TTensor:
+    """Tensor train with CUDA float64 carriages of shapes (r_j, N_j, r_{j+1})."""
+    cores: list
+
+    @property
+    def d(self):
+        return len(self.cores)
+
+    @property
+    def shape(self):
+        return tuple(int(c.shape[1]) for c in self.cores)
+
+    @property
+    def ranks(self):
+        return [1] + [int(c.shape[2]) for c in self.cores[:-1]] + [1]
+
+    def to_struct(self) -> L.lrfg_tt:
+        s = L.lrfg_tt()
+        s.d = self.d
+        for j, c in enumerate(self.cores):
+            if c.dtype != _torch().float64 or not c.is_cuda or not c.is_contiguous():
+                raise ValueError("TT carriages must be contiguous CUDA float64 tensors")
+            s.N[j] = int(c.shape[1])
+            s.cores[j] = c.data_ptr()
+        for j, r in enumerate(self.ranks):
+            s.r[j] = r
+        return s
+
+    @staticmethod
+    def from_numpy(cores, device="cuda"):
+        torch = _torch()
+        return TTensor([torch.as_tensor(np.ascontiguousarray(c, dtype=np.float64), device=device) for c in cores])
+
+    def numpy(self):
+        return [c.detach().cpu().numpy() for c in self.cores]
+
+
+class Context:
+    """A liblrfg context on one CUDA device (``stream``: a torch.cuda.Stream, or None for torch's current
+    stream; ``budget``: cap of the library's device pool in bytes, 0 = none)."""
+
+    def __init__(self, device: int = 0, stream=None, budget: int = 0):
+        torch = _torch()
+        self.lib = L.load()
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = s
+        h = C.c_void_p()
+        self._check(self.lib.lrfg_create(C.byref(h), self.device, C.c_void_p(s.cuda_stream), int(budget)), None)
+        self.h = h
+
+    def _check(self, st, h=None):
+        if st != L.LRFG_OK:
+            msg = self.lib.lrfg_last_error(h if h is not None else getattr(self, "h", None))
+            raise LrfgError(st, (msg or b"").decode())
+        return st
+
+    def check(self, st):
+        return self._check(st, self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrfg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        self.check(self.lib.lrfg_sync(self.h))
+
+    def launch_count(self) -> int:
+        return int(self.lib.lrfg_launch_count(self.h))
+
+    def pool_bytes(self):
+        a, b = C.c_size_t(), C.c_size_t()
+        self.check(self.lib.lrfg_pool_bytes(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    # ---- fibre operators (rows a1, a2) ---------------------------------------------------------
+    def fft_fibres(self, x, sign: int, out=None):
+        """Batched DFT along dim 1 of a complex128 CUDA tensor of shape (outer, N, inner)."""
+        torch = _torch()
+        if x.dtype != torch.complex128 or x.dim() != 3:
+            raise ValueError("x must be a complex128 tensor (outer, N, inner)")
+        x = x.contiguous()
+        out = torch.empty_like(x) if out is None else out
+        outer, N, inner = x.shape
+        self.check(self.lib.lrfg_fft_fibres(self.h, _ptr(x), _ptr(out), outer, N, inner, int(sign)))
+        return out
+
+    def fibre_operator(self, x, kind: int, param: float = 0.0, scale: float = 1.0, out=None):
+        """scale * F^-1 diag(m) F along dim 1 of a real float64 CUDA tensor (outer, N, inner)."""
+        torch = _torch()
+        if x.dtype != torch.float64 or x.dim() != 3:
+            raise ValueError("x must be a float64 tensor (outer, N, inner)")
+        x = x.contiguous()
+        out = torch.empty_like(x) if out is None else out
+        outer, N, inner = x.shape
+        self.check(self.lib.lrfg_fibre_operator(self.h, _ptr(x), _ptr(out), outer, N, inner, int(kind), float(param),
+                                                float(scale)))
+        return out
+
+    # ---- TT operations (rows a3..a7) -------------------------------------------------------------
+    def _alloc_tt(self, shape, ranks):
+        torch = _torch()
+        return [torch.empty((ranks[j], shape[j], ranks[j + 1]), dtype=torch.float64, device=f"cuda:{self.device}")
+                for j in range(len(shape))]
+
+    @staticmethod
+    def _shrink(bufs, s: L.lrfg_tt) -> TTensor:
+        cores = []
+        for j, b in enumerate(bufs):
+            n = s.r[j] * s.N[j] * s.r[j + 1]
+            cores.append(b.view(-1)[:n].view(s.r[j], s.N[j], s.r[j + 1]))
+        return TTensor(cores)
+
+    def _tt_out(self, shape, cap_ranks):
+        bufs = self._alloc_tt(shape, cap_ranks)
+        s = L.lrfg_tt()
+        s.d = len(shape)
+        for j, b in enumerate(bufs):
+            s.cores[j] = b.data_ptr()
+        return bufs, s
+
+    def tt_hadamard(self, x: TTensor, y: TTensor) -> TTensor:
+        cap = [a * b for a, b in zip(x.ranks, y.ranks)]
+        bufs, s = self._tt_out(x.shape, cap)
+        xs, ys = x.to_struct(), y.to_struct()
+        self.check(self.lib.lrfg_tt_hadamard(self.h, C.byref(xs), C.byref(ys), C.byref(s)))
+        return self._shrink(bufs, s)
+
+    def tt_add(self, alpha: float, x: TTensor, beta: float, y: TTensor) -> TTensor:
+        d = x.d
+        cap = [1] + [a + b for a, b in zip(x.ranks[1:d], y.ranks[1:d])] + [1]
+        bufs, s = self._tt_out(x.shape, cap)
+        xs, ys = x.to_struct(), y.to_struct()
+        self.check(self.lib.lrfg_tt_add(self.h, float(alpha), C.byref(xs), float(beta), C.byref(ys), C.byref(s)))
+        return self._shrink(bufs, s)
+
+    def tt_round(self, x: TTensor, rmax: int) -> TTensor:
+        cap = [min(int(rmax), r) for r in x.ranks]
+        bufs, s = self._tt_out(x.shape, cap)
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_tt_round(self.h, C.byref(xs), int(rmax), C.byref(s)))
+        return self._shrink(bufs, s)
+
+    def tt_dot(self, x: TTensor, y: TTensor) -> float:
+        out = C.c_double()
+        xs, ys = x.to_struct(), y.to_struct()
+        self.check(self.lib.lrfg_tt_dot(self.h, C.byref(xs), C.byref(ys), C.byref(out)))
+        return out.value
+
+    def tt_precond(self, x: TTensor, pinv_eps: float, rmax: int) -> TTensor:
+        cap = [1] + [int(rmax)] * (x.d - 1) + [1]
+        bufs, s = self._tt_out(x.shape, cap)
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_tt_precond(self.h, C.byref(xs), float(pinv_eps), int(rmax), C.byref(s)))
+        return self._shrink(bufs, s)
+
+    def tt_compress(self, values, rmax: int, tol: float = 0.0) -> TTensor:
+        torch = _torch()
+        values = values.contiguous()
+        if values.dtype != torch.float64 or not values.is_cuda:
+            raise ValueError("values must be a CUDA float64 tensor")
+        shape = tuple(values.shape)
+        cap = [1] + [int(rmax)] * (len(shape) - 1) + [1]
+        bufs, s = self._tt_out(shape, cap)
+        self.check(self.lib.lrfg_tt_compress(self.h, len(shape), _ivec(shape, 3), _ptr(values), int(rmax), float(tol),
+                                             C.byref(s)))
+        return self._shrink(bufs, s)
+
+    def tt_expand(self, x: TTensor):
+        torch = _torch()
+        out = torch.empty(x.shape, dtype=torch.float64, device=f"cuda:{self.device}")
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_tt_expand(self.h, C.byref(xs), _ptr(out)))
+        return out
+
+    # ---- problems and fields ---------------------------------------------------------------------
+    def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
+                stop_on_increase: bool = True) -> "Problem":
+        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase)
+
+    def field_from_full(self, values) -> "Field":
+        torch = _torch()
+        if isinstance(values, np.ndarray):
+            arr = np.ascontiguousarray(values, dtype=np.float64)
+            ptr, on_dev, shape, keep = arr.ctypes.data_as(C.c_void_p), 0, arr.shape, arr
+        else:
+            t = values.contiguous()
+            if t.dtype != torch.float64:
+                raise ValueError("float64 values required")
+            ptr, on_dev, shape, keep = _ptr(t), int(t.is_cuda), tuple(t.shape), t
+        h = C.c_void_p()
+        self.check(self.lib.lrfg_field_from_full(self.h, len(shape), _ivec(shape, 3), ptr, on_dev, C.byref(h)))
+        del keep
+        return Field(self, h)
+
+    def field_from_tt(self, x: TTensor) -> "Field":
+        h = C.c_void_p()
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_field_from_tt(self.h, C.byref(xs), 1, C.byref(h)))
+        return Field(self, h)
+
+
+class Field:
+    """A library-owned field (FULL: Fourier half spectrum; TT: real-space carriages)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def info(self):
+        fmt, d = C.c_int(), C.c_int()
+        N, r = (C.c_int * 3)(), (C.c_int * 4)()
+        self.ctx.check(self.ctx.lib.lrfg_field_info(self.h, C.byref(fmt), C.byref(d), N, r))
+        return fmt.value, d.value, list(N)[: d.value], list(r)[: d.value + 1]
+
+    def full(self, device: bool = False):
+        """Grid values (N^d) as a numpy array (or a CUDA tensor with device=True)."""
+        torch = _torch()
+        _, d, N, _ = self.info()
+        if device:
+            out = torch.empty(tuple(N), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+            self.ctx.check(self.ctx.lib.lrfg_field_export_full(self.ctx.h, self.h, _ptr(out), 1))
+            return out
+        out = np.empty(tuple(N), dtype=np.float64)
+        self.ctx.check(self.ctx.lib.lrfg_field_export_full(self.ctx.h, self.h, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def tt(self) -> TTensor:
+        torch = _torch()
+        fmt, d, N, r = self.info()
+        if fmt != TT:
+            raise ValueError("not a TT field")
+        cores = [torch.empty((r[j], N[j], r[j + 1]), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+                 for j in range(d)]
+        arr = (C.c_void_p * 3)(*([c.data_ptr() for c in cores] + [None] * (3 - d)))
+        self.ctx.check(self.ctx.lib.lrfg_field_export_tt(self.ctx.h, self.h, arr, 1))
+        return TTensor(cores)
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.lrfg_field_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+@dataclass
+class Result:
+    Aeff: float
+    iters: int
+    rel_resid: float
+    converged: bool
+    applies: int
+    ranks: list
+    seconds: float
+    status: int
+
+
+class Problem:
+    """Resident coefficient + operator + solver for one format.  ``coeff``: a numpy/torch grid array
+    (isotropic a(x) samples) or a TTensor of the coefficient."""
+
+    def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase):
+        torch = _torch()
+        self.ctx = ctx
+        self.fmt = fmt
+        c = L.lrfg_coeff()
+        keep = None
+        if isinstance(coeff, TTensor):
+            c.d = coeff.d
+            for j, n in enumerate(coeff.shape):
+                c.N[j] = n
+            c.fmt = L.LRFG_TT
+            c.tt = coeff.to_struct()
+            c.on_device = 1
+            keep = coeff
+        else:
+            if isinstance(coeff, np.ndarray):
+                arr = np.ascontiguousarray(coeff, dtype=np.float64)
+                c.values = arr.ctypes.data
+                c.on_device = 0
+                keep = arr
+            else:
+                t = coeff.contiguous()
+                if t.dtype != torch.float64:
+                    raise ValueError("float64 coefficient required")
+                c.values = t.data_ptr()
+                c.on_device = int(t.is_cuda)
+                keep = t
+            c.d = keep.ndim if isinstance(keep, np.ndarray) else keep.dim()
+            for j, n in enumerate(keep.shape):
+                c.N[j] = int(n)
+            c.fmt = L.LRFG_FULL
+        o = L.lrfg_opts()
+        o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), L.LRFG_FP64, int(rank), float(pinv_eps)
+        o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
+        h = C.c_void_p()
+        ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))
+        del keep
+        self.h = h
+        self.d = c.d
+
+    def coeff_ranks(self):
+        r = (C.c_int * 4)()
+        self.ctx.check(self.ctx.lib.lrfg_problem_coeff_ranks(self.h, r))
+        return list(r)[: self.d + 1]
+
+    def apply(self, field: Field) -> Field:
+        h = C.c_void_p()
+        self.ctx.check(self.ctx.lib.lrfg_problem_apply(self.h, field.h, C.byref(h)))
+        return Field(self.ctx, h)
+
+    def apply_into(self, field: Field, out: Field) -> Field:
+        self.ctx.check(self.ctx.lib.lrfg_problem_apply_into(self.h, field.h, out.h))
+        return out
+
+    def rhs(self, E) -> Field:
+        h = C.c_void_p()
+        self.ctx.check(self.ctx.lib.lrfg_problem_rhs(self.h, _dvec(E), C.byref(h)))
+        return Field(self.ctx, h)
+
+    def solve(self, E, want_field: bool = True):
+        res = L.lrfg_result()
+        h = C.c_void_p()
+        st = self.ctx.lib.lrfg_problem_solve(self.h, _dvec(E), C.byref(res), C.byref(h) if want_field else None)
+        if st not in (L.LRFG_OK, L.LRFG_ENOCONV):
+            self.ctx.check(st)
+        out = Result(res.Aeff, res.iters, res.rel_resid, bool(res.converged), res.applies, list(res.ranks)[: self.d + 1],
+                     res.seconds, st)
+        return out, (Field(self.ctx, h) if want_field and h.value else None)
+
+    def aeff(self, E, field: Field) -> float:
+        out = C.c_double()
+        self.ctx.check(self.ctx.lib.lrfg_problem_aeff(self.h, _dvec(E), field.h, C.byref(out)))
+        return out.value
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.lrfg_problem_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,96 @@
+"""ctypes declarations of the liblrfg C ABI (include/lrfg.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrfg.so")
+
+LRFG_OK, LRFG_EINVAL, LRFG_ENOMEM, LRFG_ENOCONV, LRFG_ECUDA, LRFG_ETIMEOUT, LRFG_ENOTSUP = range(7)
+LRFG_FULL, LRFG_TT = 0, 3
+LRFG_FP64, LRFG_MIXED = 0, 1
+LRFG_MUL_IDENTITY, LRFG_MUL_DERIV, LRFG_MUL_GAUSS = 0, 1, 2
+
+STATUS_NAMES = {0: "LRFG_OK", 1: "LRFG_EINVAL", 2: "LRFG_ENOMEM", 3: "LRFG_ENOCONV", 4: "LRFG_ECUDA",
+                5: "LRFG_ETIMEOUT", 6: "LRFG_ENOTSUP"}
+
+
+class lrfg_tt(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int * 3), ("r", C.c_int * 4), ("cores", C.c_void_p * 3)]
+
+
+class lrfg_coeff(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int * 3), ("fmt", C.c_int), ("values", C.c_void_p),
+                ("tt", lrfg_tt), ("on_device", C.c_int)]
+
+
+class lrfg_opts(C.Structure):
+    _fields_ = [("fmt", C.c_int), ("prec", C.c_int), ("rank", C.c_int), ("pinv_eps", C.c_double),
+                ("tol", C.c_double), ("maxit", C.c_int), ("stop_on_increase", C.c_int)]
+
+
+class lrfg_result(C.Structure):
+    _fields_ = [("Aeff", C.c_double), ("iters", C.c_int), ("rel_resid", C.c_double), ("converged", C.c_int),
+                ("applies", C.c_int), ("ranks", C.c_int * 4), ("seconds", C.c_double)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_ST = C.c_int
+
+# name -> (restype, argtypes); the same set the header declares
+SIGNATURES = {
+    "lrfg_create": (_ST, [C.POINTER(_P), _I, _P, C.c_size_t]),
+    "lrfg_destroy": (_ST, [_P]),
+    "lrfg_strerror": (C.c_char_p, [_ST]),
+    "lrfg_last_error": (C.c_char_p, [_P]),
+    "lrfg_sync": (_ST, [_P]),
+    "lrfg_launch_count": (C.c_longlong, [_P]),
+    "lrfg_pool_bytes": (_ST, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "lrfg_fft_fibres": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
+    "lrfg_fibre_operator": (_ST, [_P, _P, _P, _I, _I, _I, _I, _D, _D]),
+    "lrfg_tt_hadamard": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
+    "lrfg_tt_add": (_ST, [_P, _D, C.POINTER(lrfg_tt), _D, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
+    "lrfg_tt_round": (_ST, [_P, C.POINTER(lrfg_tt), _I, C.POINTER(lrfg_tt)]),
+    "lrfg_tt_dot": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(_D)]),
+    "lrfg_tt_precond": (_ST, [_P, C.POINTER(lrfg_tt), _D, _I, C.POINTER(lrfg_tt)]),
+    "lrfg_tt_compress": (_ST, [_P, _I, C.POINTER(_I), _P, _I, _D, C.POINTER(lrfg_tt)]),
+    "lrfg_tt_expand": (_ST, [_P, C.POINTER(lrfg_tt), _P]),
+    "lrfg_problem_create": (_ST, [_P, C.POINTER(lrfg_coeff), C.POINTER(lrfg_opts), C.POINTER(_P)]),
+    "lrfg_problem_free": (_ST, [_P]),
+    "lrfg_problem_coeff_ranks": (_ST, [_P, C.POINTER(_I)]),
+    "lrfg_problem_apply": (_ST, [_P, _P, C.POINTER(_P)]),
+    "lrfg_problem_apply_into": (_ST, [_P, _P, _P]),
+    "lrfg_problem_rhs": (_ST, [_P, C.POINTER(_D), C.POINTER(_P)]),
+    "lrfg_problem_solve": (_ST, [_P, C.POINTER(_D), C.POINTER(lrfg_result), C.POINTER(_P)]),
+    "lrfg_problem_aeff": (_ST, [_P, C.POINTER(_D), _P, C.POINTER(_D)]),
+    "lrfg_solve": (_ST, [_P, C.POINTER(lrfg_coeff), C.POINTER(_D), C.POINTER(lrfg_opts), C.POINTER(lrfg_result),
+                         C.POINTER(_P)]),
+    "lrfg_field_from_full": (_ST, [_P, _I, C.POINTER(_I), _P, _I, C.POINTER(_P)]),
+    "lrfg_field_from_tt": (_ST, [_P, C.POINTER(lrfg_tt), _I, C.POINTER(_P)]),
+    "lrfg_field_info": (_ST, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "lrfg_field_export_full": (_ST, [_P, _P, _P, _I]),
+    "lrfg_field_export_tt": (_ST, [_P, _P, C.POINTER(_P), _I]),
+    "lrfg_field_free": (_ST, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblrfg.so (no fallback: a missing library is an error)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"liblrfg.so not found at {p}; build it with `python -m paper_1902_07455_gb300.build`")
+    lib = C.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,920 @@
+// C ABI of liblrfg: contexts, problems (resident coefficient + operator + solvers), fields.
+//
+// Operator and solver composition (Sec. 2.2.2, 2.3, 3.2, 3.3 of arXiv:1902.07455):
+//  * FULL: the Fourier-space GaNi operator grad^* F A~ F^{-1} grad^ on half spectra, PCG with the
+//    Laplacian preconditioner P^-1 = 1/(k.k), A_eff by the rectangle rule.
+//  * TT: the truncated operator T P~^-1 T grad^* F T A~ F^{-1} grad^ of Eq. (Pls_lowrank) in its
+//    real-space form.  Mode-wise F is a scaled unitary map, so truncation commutes with it, and
+//    F^{-1} grad^_a F is the real circulant D_a acting on the fibres of carriage a.  The real-space
+//    operator therefore is  v -> T P~^-1 T( sum_a -D_a T(a (.) D_a v) ),  the same field as the paper's
+//    Fourier-space form, with real carriages.  The minimal-residual iteration of Sec. 3.3 runs on it.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <new>
+#include <vector>
+
+#include "full.cuh"
+
+namespace lrfg {
+
+void fail(lrfg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  throw Error{st, std::string(buf)};
+}
+
+// ------------------------------------------------------------------------------------------------
+// DevicePool
+// ------------------------------------------------------------------------------------------------
+static size_t rounded(size_t bytes) {
+  if (bytes < 256) return 256;
+  if (bytes <= (64ull << 20)) {
+    size_t p = 256;
+    while (p < bytes) p <<= 1;
+    return p;
+  }
+  const size_t g = 2ull << 20;
+  return (bytes + g - 1) / g * g;
+}
+
+void* DevicePool::alloc(size_t bytes) {
+  size_t sz = rounded(bytes);
+  auto& lst = sized_[sz];
+  void* p = nullptr;
+  if (!lst.empty()) {
+    p = lst.back();
+    lst.pop_back();
+  } else {
+    if (budget_ && reserved_ + sz > budget_) {
+      trim();
+      if (reserved_ + sz > budget_)
+        fail(LRFG_ENOMEM, "device pool budget exceeded: %zu + %zu > %zu bytes", reserved_, sz, budget_);
+    }
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      trim();
+      e = cudaMalloc(&p, sz);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(LRFG_ENOMEM, "cudaMalloc(%zu) failed: %s", sz, cudaGetErrorString(e));
+      }
+    }
+    reserved_ += sz;
+  }
+  live_size_[p] = sz;
+  in_use_ += sz;
+  return p;
+}
+
+void DevicePool::release(void* p) {
+  auto it = live_size_.find(p);
+  if (it == live_size_.end()) return;
+  size_t sz = it->second;
+  live_size_.erase(it);
+  in_use_ -= sz;
+  sized_[sz].push_back(p);
+}
+
+void DevicePool::trim() {
+  // the pool's stream must be idle before cached blocks are returned to the driver
+  cudaDeviceSynchronize();
+  for (auto& kv : sized_) {
+    for (void* p : kv.second) {
+      cudaFree(p);
+      reserved_ -= kv.first;
+    }
+    kv.second.clear();
+  }
+}
+
+}  // namespace lrfg
+
+using namespace lrfg;
+
+// ------------------------------------------------------------------------------------------------
+// objects
+// ------------------------------------------------------------------------------------------------
+struct lrfg_field {
+  lrfg_ctx* ctx = nullptr;
+  lrfg_format fmt = LRFG_FULL;
+  int d = 0;
+  int N[3] = {0, 0, 0};
+  TT tt;              // TT: real-space carriages
+  DBuf<double2> half; // FULL: Phi u (unnormalised half spectrum)
+};
+
+struct lrfg_problem {
+  lrfg_ctx* ctx = nullptr;
+  lrfg_opts opts{};
+  int d = 0;
+  int N[3] = {0, 0, 0};
+  TT a_tt;                   // TT coefficient (LRFG_TT)
+  DBuf<double> a_full;       // grid coefficient (LRFG_FULL)
+  std::vector<double> pt, pw;  // exponential sum of P~^-1
+  FullGrid g{};
+  DBuf<double2> wc;          // FULL workspace: one half spectrum
+  DBuf<double> wr;           // FULL workspace: one real grid
+};
+
+namespace {
+
+template <class F>
+lrfg_status guard(lrfg_ctx* ctx, F&& f) {
+  try {
+    if (ctx) LRFG_CUDA(cudaSetDevice(ctx->device));
+    f();
+    if (ctx) ctx->last_error.clear();
+    return LRFG_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->last_error = "host allocation failed";
+    return LRFG_ENOMEM;
+  } catch (...) {
+    if (ctx) ctx->last_error = "unexpected internal error";
+    return LRFG_ECUDA;
+  }
+}
+
+long long grid_size(int d, const int* N) {
+  long long s = 1;
+  for (int j = 0; j < d; ++j) s *= N[j];
+  return s;
+}
+
+void check_grid(int d, const int* N) {
+  LRFG_REQUIRE(d == 2 || d == 3, "d must be 2 or 3 (got %d)", d);
+  LRFG_REQUIRE(N != nullptr, "null grid sizes");
+  for (int j = 0; j < d; ++j) {
+    LRFG_REQUIRE(N[j] >= 3 && (N[j] % 2 == 1), "grid size N[%d] = %d must be odd and >= 3", j, N[j]);
+  }
+}
+
+void check_tt(const lrfg_tt* x) {
+  LRFG_REQUIRE(x != nullptr, "null TT");
+  check_grid(x->d, x->N);
+  LRFG_REQUIRE(x->r[0] == 1 && x->r[x->d] == 1, "TT boundary ranks must be 1");
+  for (int j = 1; j < x->d; ++j) LRFG_REQUIRE(x->r[j] >= 1, "TT rank r[%d] = %d < 1", j, x->r[j]);
+  for (int j = 0; j < x->d; ++j) LRFG_REQUIRE(x->cores[j] != nullptr, "null TT carriage %d", j);
+}
+
+size_t core_elems(const lrfg_tt* x, int j) { return (size_t)x->r[j] * x->N[j] * x->r[j + 1]; }
+
+void upload_tt(lrfg_ctx* ctx, const lrfg_tt* src, int on_device, TT& dst) {
+  tt_alloc(ctx, dst, src->d, src->N, src->r);
+  for (int j = 0; j < src->d; ++j) {
+    size_t n = core_elems(src, j);
+    if (!on_device) {
+      for (size_t i = 0; i < n; ++i)
+        LRFG_REQUIRE(std::isfinite(src->cores[j][i]), "non-finite value in TT carriage %d", j);
+    }
+    LRFG_CUDA(cudaMemcpyAsync(dst.core[j].get(), src->cores[j], sizeof(double) * n,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  }
+}
+
+void publish_tt(const TT& src, lrfg_tt* dst) {
+  dst->d = src.d;
+  for (int j = 0; j < 3; ++j) dst->N[j] = src.N[j];
+  for (int j = 0; j < 4; ++j) dst->r[j] = src.r[j];
+}
+
+// copies carriages of an internal TT into caller buffers
+void download_tt(lrfg_ctx* ctx, const TT& src, double* const* cores, int on_device) {
+  for (int j = 0; j < src.d; ++j) {
+    LRFG_REQUIRE(cores[j] != nullptr, "null output carriage %d", j);
+    LRFG_CUDA(cudaMemcpyAsync(cores[j], src.core[j].get(), sizeof(double) * src.core_elems(j),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (!on_device) LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+void ones_tt(lrfg_ctx* ctx, int d, const int* N, TT& x) {
+  int r[4] = {1, 1, 1, 1};
+  tt_alloc(ctx, x, d, N, r);
+  for (int j = 0; j < d; ++j) fill(ctx, x.core[j].get(), 1.0, N[j]);
+}
+
+// ---- TT operator pieces -----------------------------------------------------------------------
+
+// e = D_alpha v (scaled): carriage alpha replaced, the others shared with v
+struct ModeReplaced {
+  DBuf<double> core;
+  TTView view;
+};
+
+void mode_replace(lrfg_ctx* ctx, const TTView& v, int alpha, double scale, ModeReplaced& out) {
+  size_t n = (size_t)v.r[alpha] * v.N[alpha] * v.r[alpha + 1];
+  out.core = DBuf<double>(ctx->pool, n);
+  fibre_operator(ctx, v.core[alpha], out.core.get(), v.r[alpha], v.N[alpha], v.r[alpha + 1], LRFG_MUL_DERIV, 0.0,
+                 scale);
+  out.view = v;
+  out.view.core[alpha] = out.core.get();
+}
+
+void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
+  lrfg_ctx* ctx = P->ctx;
+  const int r = P->opts.rank;
+  TT acc;
+  bool have = false;
+  for (int alpha = 0; alpha < P->d; ++alpha) {
+    ModeReplaced e;
+    mode_replace(ctx, v, alpha, 1.0, e);                       // gradient, mode alpha (rank kept)
+    TT h, w;
+    tt_hadamard(ctx, view_of(P->a_tt), e.view, h);             // A~ e_alpha (Khatri–Rao)
+    tt_round(ctx, view_of(h), r, w);                           // T
+    fibre_operator(ctx, w.core[alpha].get(), w.core[alpha].get(), w.r[alpha], w.N[alpha], w.r[alpha + 1],
+                   LRFG_MUL_DERIV, 0.0, -1.0);                 // divergence term, mode alpha
+    if (!have) {
+      acc = std::move(w);
+      have = true;
+    } else {
+      TT s;
+      tt_add(ctx, 1.0, nullptr, view_of(acc), 1.0, nullptr, view_of(w), s);
+      acc = std::move(s);
+    }
+  }
+  TT sdiv;
+  tt_round(ctx, view_of(acc), r, sdiv);                        // T after the sum
+  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out);        // T P~^-1
+}
+
+void lr_rhs(lrfg_problem* P, const double* E, TT& out) {
+  lrfg_ctx* ctx = P->ctx;
+  TT acc;
+  bool have = false;
+  for (int alpha = 0; alpha < P->d; ++alpha) {
+    if (E[alpha] == 0.0) continue;
+    ModeReplaced t;
+    mode_replace(ctx, view_of(P->a_tt), alpha, E[alpha], t);   // E_a D_a a
+    if (!have) {
+      tt_copy(ctx, t.view, acc);
+      have = true;
+    } else {
+      TT s;
+      tt_add(ctx, 1.0, nullptr, view_of(acc), 1.0, nullptr, t.view, s);
+      acc = std::move(s);
+    }
+  }
+  if (!have) {
+    int r[4] = {1, 1, 1, 1};
+    tt_alloc(ctx, out, P->d, P->N, r);
+    for (int j = 0; j < P->d; ++j) fill(ctx, out.core[j].get(), 0.0, P->N[j]);
+    return;
+  }
+  tt_precond(ctx, view_of(acc), P->pt, P->pw, P->opts.rank, out);  // T P~^-1 (one truncation)
+}
+
+double lr_aeff(lrfg_problem* P, const double* E, const TTView& u) {
+  lrfg_ctx* ctx = P->ctx;
+  const double size = (double)grid_size(P->d, P->N);
+  TT ones;
+  ones_tt(ctx, P->d, P->N, ones);
+  double EE = 0.0;
+  for (int j = 0; j < P->d; ++j) EE += E[j] * E[j];
+  double val = EE * tt_dot(ctx, view_of(P->a_tt), view_of(ones)) / size;
+  for (int alpha = 0; alpha < P->d; ++alpha) {
+    ModeReplaced e;
+    mode_replace(ctx, u, alpha, 1.0, e);
+    TT ae;
+    tt_hadamard(ctx, view_of(P->a_tt), e.view, ae);
+    if (E[alpha] != 0.0) val += 2.0 * E[alpha] * tt_dot(ctx, view_of(ae), view_of(ones)) / size;
+    val += tt_dot(ctx, view_of(ae), e.view) / size;
+  }
+  return val;
+}
+
+// ---- FULL operator pieces ---------------------------------------------------------------------
+
+void full_apply(lrfg_problem* P, const double2* v, double2* out, int precond) {
+  lrfg_ctx* ctx = P->ctx;
+  const FullGrid& g = P->g;
+  const double inv = 1.0 / (double)g.n_real;
+  for (int alpha = 0; alpha < g.d; ++alpha) {
+    half_mul_grad(ctx, g, v, P->wc.get(), alpha, inv);                   // grad^, with 1/|N| of Phi^-1
+    full_inverse(ctx, g, P->wc.get(), P->a_full.get(), 1.0, P->wr.get()); // A~ F^-1 grad^ v
+    full_forward(ctx, g, P->wr.get(), nullptr, 1.0, P->wc.get());        // F
+    half_acc_div(ctx, g, P->wc.get(), out, alpha, 1.0, alpha == 0, precond && alpha == g.d - 1);  // grad^*
+  }
+}
+
+void full_rhs(lrfg_problem* P, const double* E, double2* b, int precond) {
+  lrfg_ctx* ctx = P->ctx;
+  const FullGrid& g = P->g;
+  full_forward(ctx, g, P->a_full.get(), nullptr, 1.0, P->wc.get());
+  for (int alpha = 0; alpha < g.d; ++alpha)
+    half_acc_div(ctx, g, P->wc.get(), b, alpha, -E[alpha], alpha == 0, precond && alpha == g.d - 1);
+}
+
+double full_aeff(lrfg_problem* P, const double* E, const double2* v) {
+  lrfg_ctx* ctx = P->ctx;
+  const FullGrid& g = P->g;
+  DBuf<double> acc(ctx->pool, 1);
+  for (int alpha = 0; alpha < g.d; ++alpha) {
+    half_mul_grad(ctx, g, v, P->wc.get(), alpha, 1.0 / (double)g.n_real);
+    full_inverse(ctx, g, P->wc.get(), nullptr, 1.0, P->wr.get());
+    energy_sum(ctx, g, P->wr.get(), P->a_full.get(), E[alpha], acc.get(), alpha > 0);
+  }
+  double h = 0.0;
+  LRFG_CUDA(cudaMemcpyAsync(&h, acc.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  return h / (double)g.n_real;
+}
+
+void new_field(lrfg_ctx* ctx, lrfg_format fmt, int d, const int* N, lrfg_field** out) {
+  lrfg_field* f = new lrfg_field();
+  f->ctx = ctx;
+  f->fmt = fmt;
+  f->d = d;
+  for (int j = 0; j < 3; ++j) f->N[j] = j < d ? N[j] : 0;
+  *out = f;
+}
+
+void check_field(const lrfg_problem* P, const lrfg_field* f) {
+  LRFG_REQUIRE(f != nullptr, "null field");
+  LRFG_REQUIRE(f->fmt == P->opts.fmt, "field format does not match the problem");
+  LRFG_REQUIRE(f->d == P->d, "field order does not match the problem");
+  for (int j = 0; j < P->d; ++j) LRFG_REQUIRE(f->N[j] == P->N[j], "field grid does not match the problem");
+}
+
+void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
+  check_field(P, in);
+  if (P->opts.fmt == LRFG_FULL) {
+    if (!out->half.get()) out->half = DBuf<double2>(P->ctx->pool, P->g.n_half);
+    full_apply(P, in->half.get(), out->half.get(), 1);
+  } else {
+    TT res;
+    lr_apply(P, view_of(in->tt), res);
+    out->tt = std::move(res);
+  }
+}
+
+void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
+  lrfg_ctx* ctx = P->ctx;
+  const FullGrid& g = P->g;
+  const long long n = g.n_half;
+  DBuf<double2> u(ctx->pool, n), r(ctx->pool, n), z(ctx->pool, n), p(ctx->pool, n), q(ctx->pool, n);
+  DBuf<double> s(ctx->pool, 4);  // rz, pq, zz, rz_new
+  double* d_rz = s.get();
+  double* d_pq = s.get() + 1;
+  double* d_zz = s.get() + 2;
+  double* d_rzn = s.get() + 3;
+  LRFG_CUDA(cudaMemsetAsync(u.get(), 0, sizeof(double2) * n, ctx->stream));
+  full_rhs(P, E, r.get(), 0);
+  half_precond(ctx, g, r.get(), z.get());
+  LRFG_CUDA(cudaMemcpyAsync(p.get(), z.get(), sizeof(double2) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  half_dot(ctx, g, r.get(), z.get(), d_rz);
+  half_dot(ctx, g, z.get(), z.get(), d_zz);
+  double zz0 = 0.0;
+  LRFG_CUDA(cudaMemcpyAsync(&zz0, d_zz, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  const double nb = std::sqrt(zz0);
+  int it = 0;
+  double rel = nb > 0.0 ? 1.0 : 0.0;
+  int applies = 0;
+  while (nb > 0.0 && it < P->opts.maxit) {
+    full_apply(P, p.get(), q.get(), 0);
+    ++applies;
+    half_dot(ctx, g, p.get(), q.get(), d_pq);
+    pcg_update(ctx, g, u.get(), r.get(), p.get(), q.get(), z.get(), d_rz, d_pq);
+    half_dot(ctx, g, z.get(), z.get(), d_zz);
+    ++it;
+    double zz = 0.0;
+    LRFG_CUDA(cudaMemcpyAsync(&zz, d_zz, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    rel = std::sqrt(std::max(zz, 0.0)) / nb;
+    if (rel <= P->opts.tol) break;
+    half_dot(ctx, g, r.get(), z.get(), d_rzn);
+    pcg_direction(ctx, g, p.get(), z.get(), d_rzn, d_rz);
+    LRFG_CUDA(cudaMemcpyAsync(d_rz, d_rzn, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  res->iters = it;
+  res->rel_resid = rel;
+  res->converged = rel <= P->opts.tol ? 1 : 0;
+  res->applies = applies;
+  for (int j = 0; j < 4; ++j) res->ranks[j] = 1;
+  res->Aeff = full_aeff(P, E, u.get());
+  if (u_out) {
+    lrfg_field* f;
+    new_field(ctx, LRFG_FULL, P->d, P->N, &f);
+    f->half = std::move(u);
+    *u_out = f;
+  }
+}
+
+void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
+  lrfg_ctx* ctx = P->ctx;
+  const int rank = P->opts.rank;
+  TT b;
+  lr_rhs(P, E, b);
+  const double nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
+  TT u, r, best_u;
+  bool have_u = false;
+  double best = INFINITY;
+  int best_it = 0, it = 0, applies = 0;
+  tt_copy(ctx, view_of(b), r);
+  while (nb > 0.0) {
+    double nr = (it == 0) ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
+    if (nr < best) {
+      best = nr;
+      best_it = it;
+      if (have_u) tt_copy(ctx, view_of(u), best_u);
+    } else if (P->opts.stop_on_increase) {
+      break;
+    }
+    if (nr <= P->opts.tol || it >= P->opts.maxit) break;
+    TT q;
+    lr_apply(P, view_of(r), q);
+    ++applies;
+    const double qq = tt_dot(ctx, view_of(q), view_of(q));
+    if (qq == 0.0) break;
+    const double omega = tt_dot(ctx, view_of(q), view_of(r)) / qq;
+    TT un;
+    if (!have_u) {
+      TT scaled;
+      tt_copy(ctx, view_of(r), scaled);
+      axpby(ctx, (long long)scaled.core_elems(0), omega, r.core[0].get(), 0.0, scaled.core[0].get());
+      tt_round(ctx, view_of(scaled), rank, un);
+    } else {
+      TT s;
+      tt_add(ctx, 1.0, nullptr, view_of(u), omega, nullptr, view_of(r), s);
+      tt_round(ctx, view_of(s), rank, un);
+    }
+    u = std::move(un);
+    have_u = true;
+    ++it;
+    TT cu, diff;
+    lr_apply(P, view_of(u), cu);
+    ++applies;
+    tt_add(ctx, 1.0, nullptr, view_of(b), -1.0, nullptr, view_of(cu), diff);
+    TT rn;
+    tt_round(ctx, view_of(diff), rank, rn);
+    r = std::move(rn);
+  }
+  if (!best_u.d) {
+    // the best iterate is u_0 = 0
+    int rr[4] = {1, 1, 1, 1};
+    tt_alloc(ctx, best_u, P->d, P->N, rr);
+    for (int j = 0; j < P->d; ++j) fill(ctx, best_u.core[j].get(), 0.0, P->N[j]);
+  }
+  res->iters = best_it;
+  res->rel_resid = nb > 0.0 ? best : 0.0;
+  res->converged = res->rel_resid <= P->opts.tol ? 1 : 0;
+  res->applies = applies;
+  for (int j = 0; j < 4; ++j) res->ranks[j] = best_u.r[j];
+  res->Aeff = lr_aeff(P, E, view_of(best_u));
+  if (u_out) {
+    lrfg_field* f;
+    new_field(ctx, LRFG_TT, P->d, P->N, &f);
+    f->tt = std::move(best_u);
+    *u_out = f;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* lrfg_strerror(lrfg_status st) {
+  switch (st) {
+    case LRFG_OK: return "ok";
+    case LRFG_EINVAL: return "invalid argument";
+    case LRFG_ENOMEM: return "out of device memory (or over the context's budget)";
+    case LRFG_ENOCONV: return "iteration cap reached before the tolerance";
+    case LRFG_ECUDA: return "CUDA runtime error";
+    case LRFG_ETIMEOUT: return "device-side wait timed out";
+    case LRFG_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+const char* lrfg_last_error(const lrfg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget) {
+  if (!out) return LRFG_EINVAL;
+  *out = nullptr;
+  lrfg_ctx* ctx = new (std::nothrow) lrfg_ctx();
+  if (!ctx) return LRFG_ENOMEM;
+  ctx->device = device;
+  lrfg_status st = guard(ctx, [&] {
+    int n = 0;
+    LRFG_CUDA(cudaGetDeviceCount(&n));
+    LRFG_REQUIRE(device >= 0 && device < n, "device %d out of range (%d devices)", device, n);
+    LRFG_CUDA(cudaSetDevice(device));
+    LRFG_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+    LRFG_CUDA(cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    if (stream) {
+      ctx->stream = (cudaStream_t)stream;
+    } else {
+      LRFG_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+      ctx->own_stream = true;
+    }
+    ctx->pool = new DevicePool(budget);
+  });
+  if (st != LRFG_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_destroy(lrfg_ctx* ctx) {
+  if (!ctx) return LRFG_EINVAL;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  delete ctx->pool;
+  for (auto& kv : ctx->twiddles) cudaFree(kv.second.W);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_sync(lrfg_ctx* ctx) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] { LRFG_CUDA(cudaStreamSynchronize(ctx->stream)); });
+}
+
+long long lrfg_launch_count(const lrfg_ctx* ctx) { return ctx ? ctx->kernel_launches : -1; }
+
+lrfg_status lrfg_pool_bytes(const lrfg_ctx* ctx, size_t* in_use, size_t* reserved) {
+  if (!ctx || !in_use || !reserved) return LRFG_EINVAL;
+  *in_use = ctx->pool->in_use();
+  *reserved = ctx->pool->reserved();
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_fft_fibres(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner, int sign) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    LRFG_REQUIRE(in && out, "null buffer");
+    LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
+    LRFG_REQUIRE(sign == 1 || sign == -1, "sign must be +1 or -1");
+    LRFG_REQUIRE(N >= 1 && N % 2 == 1, "N must be odd");
+    fft_fibres(ctx, (const double2*)in, (double2*)out, outer, N, inner, sign);
+  });
+}
+
+lrfg_status lrfg_fibre_operator(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner,
+                                lrfg_multiplier kind, double param, double scale) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    LRFG_REQUIRE(in && out, "null buffer");
+    LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
+    LRFG_REQUIRE(N >= 1 && N % 2 == 1, "N must be odd");
+    fibre_operator(ctx, in, out, outer, N, inner, (int)kind, param, scale);
+  });
+}
+
+lrfg_status lrfg_tt_hadamard(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    check_tt(y);
+    LRFG_REQUIRE(out != nullptr, "null output");
+    TT res;
+    tt_hadamard(ctx, view_of(*x), view_of(*y), res);
+    publish_tt(res, out);
+    download_tt(ctx, res, out->cores, 1);
+  });
+}
+
+lrfg_status lrfg_tt_add(lrfg_ctx* ctx, double alpha, const lrfg_tt* x, double beta, const lrfg_tt* y, lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    check_tt(y);
+    LRFG_REQUIRE(out != nullptr, "null output");
+    TT res;
+    tt_add(ctx, alpha, nullptr, view_of(*x), beta, nullptr, view_of(*y), res);
+    publish_tt(res, out);
+    download_tt(ctx, res, out->cores, 1);
+  });
+}
+
+lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    LRFG_REQUIRE(out != nullptr, "null output");
+    LRFG_REQUIRE(rmax >= 1, "rmax must be >= 1");
+    TT res;
+    tt_round(ctx, view_of(*x), rmax, res);
+    publish_tt(res, out);
+    download_tt(ctx, res, out->cores, 1);
+  });
+}
+
+lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    check_tt(y);
+    LRFG_REQUIRE(result != nullptr, "null result");
+    *result = tt_dot(ctx, view_of(*x), view_of(*y));
+  });
+}
+
+lrfg_status lrfg_tt_precond(lrfg_ctx* ctx, const lrfg_tt* x, double pinv_eps, int rmax, lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    LRFG_REQUIRE(out != nullptr, "null output");
+    LRFG_REQUIRE(rmax >= 1, "rmax must be >= 1");
+    LRFG_REQUIRE(pinv_eps > 0.0 && pinv_eps < 1.0, "pinv_eps must be in (0,1)");
+    double xmax = 0.0;
+    for (int j = 0; j < x->d; ++j) xmax += (double)((x->N[j] - 1) / 2) * ((x->N[j] - 1) / 2);
+    std::vector<double> t, w;
+    expsum_inverse(xmax, pinv_eps, t, w);
+    TT res;
+    tt_precond(ctx, view_of(*x), t, w, rmax, res);
+    publish_tt(res, out);
+    download_tt(ctx, res, out->cores, 1);
+  });
+}
+
+lrfg_status lrfg_tt_compress(lrfg_ctx* ctx, int d, const int N[3], const double* values, int rmax, double tol,
+                             lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_grid(d, N);
+    LRFG_REQUIRE(values && out, "null buffer");
+    LRFG_REQUIRE(rmax >= 1, "rmax must be >= 1");
+    TT res;
+    tt_compress(ctx, d, N, values, rmax, tol, res);
+    publish_tt(res, out);
+    download_tt(ctx, res, out->cores, 1);
+  });
+}
+
+lrfg_status lrfg_tt_expand(lrfg_ctx* ctx, const lrfg_tt* x, double* values) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    LRFG_REQUIRE(values != nullptr, "null output");
+    tt_expand(ctx, view_of(*x), values);
+  });
+}
+
+lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lrfg_opts* opts, lrfg_problem** out) {
+  if (!ctx) return LRFG_EINVAL;
+  if (out) *out = nullptr;
+  lrfg_problem* P = nullptr;
+  lrfg_status st = guard(ctx, [&] {
+    LRFG_REQUIRE(coeff && opts && out, "null argument");
+    check_grid(coeff->d, coeff->N);
+    LRFG_REQUIRE(opts->fmt == LRFG_FULL || opts->fmt == LRFG_TT, "solution format must be LRFG_FULL or LRFG_TT");
+    if (opts->prec != LRFG_FP64) fail(LRFG_ENOTSUP, "only LRFG_FP64 is supported");
+    LRFG_REQUIRE(opts->maxit >= 0, "maxit must be >= 0");
+    LRFG_REQUIRE(opts->tol >= 0.0, "tol must be >= 0");
+    if (opts->fmt == LRFG_TT) LRFG_REQUIRE(opts->rank >= 1, "TT solve needs rank >= 1 (got %d)", opts->rank);
+    LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT, "coefficient format must be FULL or TT");
+    P = new lrfg_problem();
+    P->ctx = ctx;
+    P->opts = *opts;
+    if (P->opts.pinv_eps <= 0.0) P->opts.pinv_eps = 0.1;
+    LRFG_REQUIRE(P->opts.pinv_eps < 1.0, "pinv_eps must be < 1");
+    P->d = coeff->d;
+    for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
+    const long long n = grid_size(P->d, P->N);
+    // coefficient -> device
+    if (coeff->fmt == LRFG_FULL) {
+      LRFG_REQUIRE(coeff->values != nullptr, "null coefficient values");
+      DBuf<double> a(ctx->pool, n);
+      std::vector<double> h;
+      if (coeff->on_device) {
+        h.resize(n);
+        LRFG_CUDA(cudaMemcpyAsync(h.data(), coeff->values, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+        LRFG_CUDA(cudaMemcpyAsync(a.get(), coeff->values, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      } else {
+        LRFG_CUDA(cudaMemcpyAsync(a.get(), coeff->values, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+      }
+      const double* hv = coeff->on_device ? h.data() : coeff->values;
+      for (long long i = 0; i < n; ++i)
+        LRFG_REQUIRE(std::isfinite(hv[i]) && hv[i] > 0.0, "coefficient must be positive and finite (index %lld)", i);
+      if (opts->fmt == LRFG_FULL) {
+        P->a_full = std::move(a);
+      } else {
+        tt_compress(ctx, P->d, P->N, a.get(), opts->rank, 0.0, P->a_tt);
+      }
+    } else {
+      LRFG_REQUIRE(coeff->tt.d == coeff->d, "coefficient TT order differs from d");
+      for (int j = 0; j < coeff->d; ++j) LRFG_REQUIRE(coeff->tt.N[j] == coeff->N[j], "coefficient TT grid differs");
+      check_tt(&coeff->tt);
+      TT a;
+      upload_tt(ctx, &coeff->tt, coeff->on_device, a);
+      if (opts->fmt == LRFG_TT) {
+        P->a_tt = std::move(a);
+      } else {
+        P->a_full = DBuf<double>(ctx->pool, n);
+        tt_expand(ctx, view_of(a), P->a_full.get());
+      }
+    }
+    if (opts->fmt == LRFG_FULL) {
+      P->g = make_grid(P->d, P->N);
+      P->wc = DBuf<double2>(ctx->pool, P->g.n_half);
+      P->wr = DBuf<double>(ctx->pool, P->g.n_real);
+    } else {
+      double xmax = 0.0;
+      for (int j = 0; j < P->d; ++j) xmax += (double)((P->N[j] - 1) / 2) * ((P->N[j] - 1) / 2);
+      expsum_inverse(xmax, P->opts.pinv_eps, P->pt, P->pw);
+    }
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = P;
+  });
+  if (st != LRFG_OK) delete P;
+  return st;
+}
+
+lrfg_status lrfg_problem_free(lrfg_problem* P) {
+  if (!P) return LRFG_EINVAL;
+  lrfg_ctx* ctx = P->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  delete P;
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_problem_coeff_ranks(const lrfg_problem* P, int ranks[4]) {
+  if (!P || !ranks) return LRFG_EINVAL;
+  for (int j = 0; j < 4; ++j) ranks[j] = P->opts.fmt == LRFG_TT ? P->a_tt.r[j] : 1;
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_problem_apply(lrfg_problem* P, const lrfg_field* in, lrfg_field** out) {
+  if (!P) return LRFG_EINVAL;
+  lrfg_field* f = nullptr;
+  lrfg_status st = guard(P->ctx, [&] {
+    LRFG_REQUIRE(out != nullptr, "null output");
+    new_field(P->ctx, P->opts.fmt, P->d, P->N, &f);
+    apply_into(P, in, f);
+    *out = f;
+  });
+  if (st != LRFG_OK) delete f;
+  return st;
+}
+
+lrfg_status lrfg_problem_apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
+  if (!P) return LRFG_EINVAL;
+  return guard(P->ctx, [&] {
+    LRFG_REQUIRE(out != nullptr && out != in, "output must be a different, existing field");
+    check_field(P, out);
+    apply_into(P, in, out);
+  });
+}
+
+lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out) {
+  if (!P) return LRFG_EINVAL;
+  lrfg_field* f = nullptr;
+  lrfg_status st = guard(P->ctx, [&] {
+    LRFG_REQUIRE(E && out, "null argument");
+    for (int j = 0; j < P->d; ++j) LRFG_REQUIRE(std::isfinite(E[j]), "E must be finite");
+    new_field(P->ctx, P->opts.fmt, P->d, P->N, &f);
+    if (P->opts.fmt == LRFG_FULL) {
+      f->half = DBuf<double2>(P->ctx->pool, P->g.n_half);
+      full_rhs(P, E, f->half.get(), 1);
+    } else {
+      lr_rhs(P, E, f->tt);
+    }
+    *out = f;
+  });
+  if (st != LRFG_OK) delete f;
+  return st;
+}
+
+lrfg_status lrfg_problem_solve(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
+  if (!P) return LRFG_EINVAL;
+  if (u_out) *u_out = nullptr;
+  bool noconv = false;
+  lrfg_status st = guard(P->ctx, [&] {
+    LRFG_REQUIRE(E && res, "null argument");
+    for (int j = 0; j < P->d; ++j) LRFG_REQUIRE(std::isfinite(E[j]), "E must be finite");
+    *res = lrfg_result{};
+    auto t0 = std::chrono::steady_clock::now();
+    if (P->opts.fmt == LRFG_FULL) solve_full(P, E, res, u_out);
+    else solve_tt(P, E, res, u_out);
+    LRFG_CUDA(cudaStreamSynchronize(P->ctx->stream));
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    noconv = !res->converged && !(P->opts.fmt == LRFG_TT && P->opts.stop_on_increase && res->applies > 0 &&
+                                  res->iters < P->opts.maxit);
+  });
+  if (st == LRFG_OK && noconv) return LRFG_ENOCONV;
+  return st;
+}
+
+lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field* u, double* Aeff) {
+  if (!P) return LRFG_EINVAL;
+  return guard(P->ctx, [&] {
+    LRFG_REQUIRE(E && Aeff, "null argument");
+    check_field(P, u);
+    *Aeff = (P->opts.fmt == LRFG_FULL) ? full_aeff(P, E, u->half.get()) : lr_aeff(P, E, view_of(u->tt));
+  });
+}
+
+lrfg_status lrfg_solve(lrfg_ctx* ctx, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,
+                       lrfg_result* res, lrfg_field** u_out) {
+  lrfg_problem* P = nullptr;
+  lrfg_status st = lrfg_problem_create(ctx, coeff, opts, &P);
+  if (st != LRFG_OK) return st;
+  st = lrfg_problem_solve(P, E, res, u_out);
+  lrfg_problem_free(P);
+  return st;
+}
+
+lrfg_status lrfg_field_from_full(lrfg_ctx* ctx, int d, const int N[3], const double* values, int on_device,
+                                 lrfg_field** out) {
+  if (!ctx) return LRFG_EINVAL;
+  lrfg_field* f = nullptr;
+  lrfg_status st = guard(ctx, [&] {
+    check_grid(d, N);
+    LRFG_REQUIRE(values && out, "null argument");
+    new_field(ctx, LRFG_FULL, d, N, &f);
+    FullGrid g = make_grid(d, N);
+    DBuf<double> tmp(ctx->pool, g.n_real);
+    LRFG_CUDA(cudaMemcpyAsync(tmp.get(), values, sizeof(double) * g.n_real,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    f->half = DBuf<double2>(ctx->pool, g.n_half);
+    full_forward(ctx, g, tmp.get(), nullptr, 1.0, f->half.get());
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = f;
+  });
+  if (st != LRFG_OK) delete f;
+  return st;
+}
+
+lrfg_status lrfg_field_from_tt(lrfg_ctx* ctx, const lrfg_tt* x, int on_device, lrfg_field** out) {
+  if (!ctx) return LRFG_EINVAL;
+  lrfg_field* f = nullptr;
+  lrfg_status st = guard(ctx, [&] {
+    check_tt(x);
+    LRFG_REQUIRE(out != nullptr, "null output");
+    new_field(ctx, LRFG_TT, x->d, x->N, &f);
+    upload_tt(ctx, x, on_device, f->tt);
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = f;
+  });
+  if (st != LRFG_OK) delete f;
+  return st;
+}
+
+lrfg_status lrfg_field_info(const lrfg_field* f, lrfg_format* fmt, int* d, int N[3], int r[4]) {
+  if (!f) return LRFG_EINVAL;
+  if (fmt) *fmt = f->fmt;
+  if (d) *d = f->d;
+  if (N) for (int j = 0; j < 3; ++j) N[j] = f->N[j];
+  if (r) for (int j = 0; j < 4; ++j) r[j] = f->fmt == LRFG_TT ? f->tt.r[j] : 1;
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* values, int on_device) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    LRFG_REQUIRE(f && values, "null argument");
+    const long long n = grid_size(f->d, f->N);
+    DBuf<double> dst;
+    double* target = values;
+    if (!on_device) { dst = DBuf<double>(ctx->pool, n); target = dst.get(); }
+    if (f->fmt == LRFG_FULL) {
+      FullGrid g = make_grid(f->d, f->N);
+      DBuf<double2> tmp(ctx->pool, g.n_half);
+      LRFG_CUDA(cudaMemcpyAsync(tmp.get(), f->half.get(), sizeof(double2) * g.n_half, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+      full_inverse(ctx, g, tmp.get(), nullptr, 1.0 / (double)g.n_real, target);
+    } else {
+      tt_expand(ctx, view_of(f->tt), target);
+    }
+    if (!on_device)
+      LRFG_CUDA(cudaMemcpyAsync(values, target, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+lrfg_status lrfg_field_export_tt(lrfg_ctx* ctx, const lrfg_field* f, double* const cores[3], int on_device) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    LRFG_REQUIRE(f && cores, "null argument");
+    LRFG_REQUIRE(f->fmt == LRFG_TT, "field is not a TT");
+    download_tt(ctx, f->tt, cores, on_device);
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+lrfg_status lrfg_field_free(lrfg_field* f) {
+  if (!f) return LRFG_EINVAL;
+  cudaSetDevice(f->ctx->device);
+  cudaStreamSynchronize(f->ctx->stream);
+  delete f;
+  return LRFG_OK;
+}
+
+}  // extern "C"

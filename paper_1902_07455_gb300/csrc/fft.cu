@@ -1,0 +1,285 @@
+// Mode-wise batched FFTs of fibres (hot-path rows a1 and a2): complex fibres, and real fibres under a
+// Fourier multiplier F^{-1} diag(m) F (gradient 2 pi i k, Gaussian exp(-t k^2)).
+//
+// A fibre is (o, :, i) of an (outer, N, inner) array; a block stages TF whole fibres in shared memory
+// with coalesced loads (consecutive threads take consecutive inner indices when inner >= TF, else
+// consecutive elements of one fibre), runs the Stockham passes there, and writes back the same way.
+// Real fibres are packed two per complex row (x + i y): a real-symmetric multiplier maps it to
+// Mx + i My, so one complex transform pair serves two real fibres.
+#include <cmath>
+
+#include "ops.cuh"
+
+namespace lrfg {
+
+FftPlan make_plan(int N) {
+  FftPlan pl{};
+  pl.N = N;
+  pl.nst = 0;
+  int n = N;
+  // radix 5 first, then 3 (any order is valid), then the remaining primes
+  const int pref[] = {5, 3};
+  for (int p : pref)
+    while (n % p == 0) { pl.radix[pl.nst++] = p; n /= p; }
+  for (int p = 7; n > 1; p += 2) {
+    while (n % p == 0) {
+      if (p > kMaxGenericRadix) fail(LRFG_ENOTSUP, "grid size %d has a prime factor %d > %d", N, p, kMaxGenericRadix);
+      if (pl.nst >= kMaxStages) fail(LRFG_ENOTSUP, "grid size %d has too many factors", N);
+      pl.radix[pl.nst++] = p;
+      n /= p;
+    }
+  }
+  return pl;
+}
+
+const Twiddles& twiddles_for(lrfg_ctx* ctx, int N) {
+  auto it = ctx->twiddles.find(N);
+  if (it != ctx->twiddles.end()) return it->second;
+  std::vector<double2> h(N);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int j = 0; j < N; ++j) {
+    // reduce the angle to [0, pi/4]-friendly symmetric form for accuracy: exp(-2 pi i j/N)
+    double ang = two_pi * (double)j / (double)N;
+    h[j] = make_double2(std::cos(ang), -std::sin(ang));
+  }
+  Twiddles t;
+  t.N = N;
+  LRFG_CUDA(cudaMalloc(&t.W, sizeof(double2) * N));
+  LRFG_CUDA(cudaMemcpy(t.W, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+  return ctx->twiddles.emplace(N, t).first->second;
+}
+
+static int tile_fibres(lrfg_ctx* ctx, int N, int rows_per_fibre_pair, size_t* smem_out) {
+  // shared memory: twiddles N + 2 buffers of TF rows (+ N multipliers for the operator kernels)
+  size_t limit = 100 * 1024;
+  if (N > 300) limit = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);
+  long long per = 2LL * N * (long long)sizeof(double2);
+  long long fixed = 2LL * N * (long long)sizeof(double2);
+  long long tf = ((long long)limit - fixed) / per;
+  if (tf > 64) tf = 64;
+  if (tf < 1) tf = 1;
+  (void)rows_per_fibre_pair;
+  *smem_out = (size_t)(fixed + tf * per);
+  return (int)tf;
+}
+
+// ----------------------------------------------------------------------------------------------------
+// complex fibres
+// ----------------------------------------------------------------------------------------------------
+template <int SIGN>
+__global__ void __launch_bounds__(256) fft_fibres_kernel(const double2* in, double2* out,
+                                                         long long outer, int N, long long inner, int TF,
+                                                         FftPlan pl, const double2* __restrict__ Wg) {
+  extern __shared__ double2 sm[];
+  double2* W = sm;
+  double2* a = sm + 2 * N;
+  double2* b = a + (size_t)TF * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
+  const long long nfib = outer * inner;
+  const long long g0 = (long long)blockIdx.x * TF;
+  const int nf = (int)min((long long)TF, nfib - g0);
+  const int total = nf * N;
+  const bool across = inner >= TF;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int f, n;
+    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
+    long long g = g0 + f;
+    long long o = g / inner, i = g - o * inner;
+    a[(size_t)f * N + n] = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
+  }
+  __syncthreads();
+  double2* res = stockham_rows<SIGN>(a, b, nf, N, pl, W);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int f, n;
+    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
+    long long g = g0 + f;
+    long long o = g / inner, i = g - o * inner;
+    out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = res[(size_t)f * N + n];
+  }
+}
+
+void fft_fibres(lrfg_ctx* ctx, const double2* in, double2* out, long long outer, int N, long long inner,
+                int sign) {
+  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fft length must be odd (got %d)", N);
+  LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
+  if (outer == 0 || inner == 0) return;
+  FftPlan pl = make_plan(N);
+  const Twiddles& tw = twiddles_for(ctx, N);
+  size_t smem;
+  int TF = tile_fibres(ctx, N, 1, &smem);
+  long long nfib = outer * inner;
+  long long blocks = (nfib + TF - 1) / TF;
+  LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
+  if (sign < 0) {
+    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fft_fibres_kernel<-1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W);
+  } else {
+    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fft_fibres_kernel<1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W);
+  }
+  LRFG_CHECK_LAUNCH();
+  count_launch(ctx);
+}
+
+// ----------------------------------------------------------------------------------------------------
+// real fibres under a multiplier: rows hold fibre f (real part) and fibre f + TF (imaginary part)
+// ----------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double2 multiplier(int kind, int k, double param) {
+  if (kind == LRFG_MUL_DERIV) return make_double2(0.0, 6.283185307179586476925286766559 * (double)k);
+  if (kind == LRFG_MUL_GAUSS) return make_double2(exp(-param * (double)k * (double)k), 0.0);
+  return make_double2(1.0, 0.0);
+}
+
+__global__ void __launch_bounds__(256) fibre_op_kernel(const double* in, double* out, long long outer,
+                                                       int N, long long inner, int TF, FftPlan pl,
+                                                       const double2* __restrict__ Wg, int kind, double param,
+                                                       double scale) {
+  extern __shared__ double2 sm[];
+  double2* W = sm;
+  double2* M = sm + N;
+  double2* a = sm + 2 * N;
+  double2* b = a + (size_t)TF * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    W[j] = Wg[j];
+    M[j] = multiplier(kind, freq_of(j, N), param);
+  }
+  const long long nfib = outer * inner;
+  const long long g0 = (long long)blockIdx.x * (2LL * TF);
+  const int nf = (int)min(2LL * TF, nfib - g0);   // real fibres in this tile
+  const int rows = min(nf, TF);
+  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) a[t] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const int total = nf * N;
+  const bool across = inner >= 2 * TF;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int f, n;
+    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
+    long long g = g0 + f;
+    long long o = g / inner, i = g - o * inner;
+    double v = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
+    if (f < TF) a[(size_t)f * N + n].x = v; else a[(size_t)(f - TF) * N + n].y = v;
+  }
+  __syncthreads();
+  double2* res = stockham_rows<-1>(a, b, rows, N, pl, W);
+  double2* other = (res == a) ? b : a;
+  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) {
+    int n = t % N;
+    res[t] = cmul(res[t], M[n]);
+  }
+  __syncthreads();
+  res = stockham_rows<1>(res, other, rows, N, pl, W);
+  const double s = scale / (double)N;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int f, n;
+    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
+    long long g = g0 + f;
+    long long o = g / inner, i = g - o * inner;
+    double2 v = (f < TF) ? res[(size_t)f * N + n] : res[(size_t)(f - TF) * N + n];
+    out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = s * ((f < TF) ? v.x : v.y);
+  }
+}
+
+void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
+                    int kind, double param, double scale) {
+  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
+  LRFG_REQUIRE(kind == LRFG_MUL_IDENTITY || kind == LRFG_MUL_DERIV || kind == LRFG_MUL_GAUSS,
+               "unknown multiplier %d", kind);
+  if (outer == 0 || inner == 0) return;
+  FftPlan pl = make_plan(N);
+  const Twiddles& tw = twiddles_for(ctx, N);
+  size_t smem;
+  int TF = tile_fibres(ctx, N, 2, &smem);
+  long long nfib = outer * inner;
+  long long blocks = (nfib + 2LL * TF - 1) / (2LL * TF);
+  LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
+  LRFG_CUDA(cudaFuncSetAttribute(fibre_op_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  fibre_op_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W, kind,
+                                                               param, scale);
+  LRFG_CHECK_LAUNCH();
+  count_launch(ctx);
+}
+
+// Many Gaussian multipliers of one input: the forward transform is shared, each term m gets its own
+// multiply + inverse transform and is written to out + m * out_stride.
+__global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __restrict__ in, double* out,
+                                                                long long out_stride, long long outer, int N,
+                                                                long long inner, int TF, FftPlan pl,
+                                                                const double2* __restrict__ Wg,
+                                                                const double* __restrict__ tm,
+                                                                const double* __restrict__ sc, int nm) {
+  extern __shared__ double2 sm[];
+  double2* W = sm;
+  double2* spec = sm + N;              // TF rows: the shared forward spectrum
+  double2* a = spec + (size_t)TF * N;  // TF rows
+  double2* b = a + (size_t)TF * N;     // TF rows
+  for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
+  const long long nfib = outer * inner;
+  const long long g0 = (long long)blockIdx.x * (2LL * TF);
+  const int nf = (int)min(2LL * TF, nfib - g0);
+  const int rows = min(nf, TF);
+  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) a[t] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const int total = nf * N;
+  const bool across = inner >= 2 * TF;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int f, n;
+    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
+    long long g = g0 + f;
+    long long o = g / inner, i = g - o * inner;
+    double v = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
+    if (f < TF) a[(size_t)f * N + n].x = v; else a[(size_t)(f - TF) * N + n].y = v;
+  }
+  __syncthreads();
+  double2* res = stockham_rows<-1>(a, b, rows, N, pl, W);
+  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) spec[t] = res[t];
+  __syncthreads();
+  for (int m = 0; m < nm; ++m) {
+    const double t_m = tm[m];
+    for (int t = threadIdx.x; t < rows * N; t += blockDim.x) {
+      int k = freq_of(t % N, N);
+      a[t] = cscale(spec[t], exp(-t_m * (double)k * (double)k));
+    }
+    __syncthreads();
+    double2* r2 = stockham_rows<1>(a, b, rows, N, pl, W);
+    const double s = sc[m] / (double)N;
+    double* o_m = out + (size_t)m * (size_t)out_stride;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int f, n;
+      if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
+      long long g = g0 + f;
+      long long o = g / inner, i = g - o * inner;
+      double2 v = (f < TF) ? r2[(size_t)f * N + n] : r2[(size_t)(f - TF) * N + n];
+      o_m[((size_t)o * N + n) * (size_t)inner + (size_t)i] = s * ((f < TF) ? v.x : v.y);
+    }
+    __syncthreads();
+  }
+}
+
+void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long out_stride, long long outer,
+                       int N, long long inner, const double* t, const double* scale, int nm) {
+  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
+  if (outer == 0 || inner == 0 || nm == 0) return;
+  FftPlan pl = make_plan(N);
+  const Twiddles& tw = twiddles_for(ctx, N);
+  size_t limit = 100 * 1024;
+  if (N > 300) limit = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);
+  long long per = 3LL * N * (long long)sizeof(double2);
+  long long tf = ((long long)limit - (long long)N * (long long)sizeof(double2)) / per;
+  if (tf > 64) tf = 64;
+  if (tf < 1) tf = 1;
+  size_t smem = (size_t)(N * sizeof(double2) + tf * per);
+  // device copies of the node and scale tables
+  DBuf<double> dt(ctx->pool, nm), ds(ctx->pool, nm);
+  LRFG_CUDA(cudaMemcpyAsync(dt.get(), t, sizeof(double) * nm, cudaMemcpyHostToDevice, ctx->stream));
+  LRFG_CUDA(cudaMemcpyAsync(ds.get(), scale, sizeof(double) * nm, cudaMemcpyHostToDevice, ctx->stream));
+  long long nfib = outer * inner;
+  long long blocks = (nfib + 2 * tf - 1) / (2 * tf);
+  LRFG_CUDA(cudaFuncSetAttribute(fibre_gauss_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  fibre_gauss_multi_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, out_stride, outer, N, inner,
+                                                                         (int)tf, pl, tw.W, dt.get(), ds.get(), nm);
+  LRFG_CHECK_LAUNCH();
+  count_launch(ctx);
+  // the pool hands these blocks out again only to later work on the same stream
+}
+
+}  // namespace lrfg

@@ -1,0 +1,137 @@
+// Batched odd-length complex FFTs of fibres staged in shared memory (FP64).
+//
+// Mixed-radix Stockham autosort, decimation in time.  After the stages with radices p_0..p_{s-1}
+// (L = p_0...p_{s-1}), row entry c*L + f holds the length-L DFT (frequency f) of the subsequence
+// x[c + (N/L) t], t = 0..L-1.  A radix-p stage with m' = N/(L p) combines p such subsequences:
+//   Z'[c'][f + L q] = sum_r w_p^{q r} ( w_{Lp}^{f r} Z[c' + m' r][f] ),   q, r = 0..p-1,
+// with w_M = exp(sign 2 pi i / M).  It starts from the natural order (L = 1) and ends in natural
+// order (L = N), so no digit reversal is needed.  Twiddles come from one table
+// W[j] = exp(-2 pi i j / N) (w_{Lp}^{f r} = W[f r m'], w_p^{q r} = W[(q r mod p) N / p]).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lrfg {
+
+constexpr int kMaxStages = 24;
+constexpr int kMaxGenericRadix = 31;
+
+struct FftPlan {
+  int N;
+  int nst;
+  int radix[kMaxStages];
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// i * s * a
+__device__ __forceinline__ double2 cimul(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }
+
+// twiddle W[j]^(-sign): forward (sign -1) uses W, inverse (sign +1) its conjugate
+template <int SIGN>
+__device__ __forceinline__ double2 tw(const double2* W, int j) {
+  double2 w = W[j];
+  if (SIGN > 0) w.y = -w.y;
+  return w;
+}
+
+// One radix-p butterfly: inputs Z[c + m' r][f] (row offset (c + m' r) L + f), outputs Z'[c][f + L q].
+template <int SIGN>
+__device__ __forceinline__ void butterfly(int p, const double2* __restrict__ in, double2* __restrict__ out,
+                                          int c, int f, int L, int mp, int N, const double2* W) {
+  if (p == 3) {
+    double2 x0 = in[c * L + f];
+    double2 x1 = in[(c + mp) * L + f];
+    double2 x2 = in[(c + 2 * mp) * L + f];
+    if (f) {
+      x1 = cmul(x1, tw<SIGN>(W, f * mp));
+      x2 = cmul(x2, tw<SIGN>(W, 2 * f * mp));
+    }
+    const double s = 0.86602540378443864676;  // sin(2 pi / 3) = sqrt(3)/2
+    double2 t1 = cadd(x1, x2), t2 = csub(x1, x2);
+    double2 m = csub(x0, cscale(t1, 0.5));
+    double2 u = cimul(t2, SIGN * s);
+    double2* o = out + c * L * 3 + f;
+    o[0] = cadd(x0, t1);
+    o[L] = cadd(m, u);
+    o[2 * L] = csub(m, u);
+  } else if (p == 5) {
+    double2 x0 = in[c * L + f];
+    double2 x1 = in[(c + mp) * L + f];
+    double2 x2 = in[(c + 2 * mp) * L + f];
+    double2 x3 = in[(c + 3 * mp) * L + f];
+    double2 x4 = in[(c + 4 * mp) * L + f];
+    if (f) {
+      int j = f * mp;
+      x1 = cmul(x1, tw<SIGN>(W, j));
+      x2 = cmul(x2, tw<SIGN>(W, 2 * j));
+      x3 = cmul(x3, tw<SIGN>(W, 3 * j));
+      x4 = cmul(x4, tw<SIGN>(W, 4 * j));
+    }
+    // cos/sin of 2 pi/5 and 4 pi/5: (sqrt5-1)/4, -(sqrt5+1)/4, sqrt((5+sqrt5)/8), sqrt((5-sqrt5)/8)
+    const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;
+    const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;
+    double2 a1 = cadd(x1, x4), b1 = csub(x1, x4), a2 = cadd(x2, x3), b2 = csub(x2, x3);
+    double2 m1 = cadd(x0, cadd(cscale(a1, c1), cscale(a2, c2)));
+    double2 m2 = cadd(x0, cadd(cscale(a1, c2), cscale(a2, c1)));
+    double2 n1 = cimul(cadd(cscale(b1, s1), cscale(b2, s2)), (double)SIGN);
+    double2 n2 = cimul(csub(cscale(b1, s2), cscale(b2, s1)), (double)SIGN);
+    double2* o = out + c * L * 5 + f;
+    o[0] = cadd(x0, cadd(a1, a2));
+    o[L] = cadd(m1, n1);
+    o[2 * L] = cadd(m2, n2);
+    o[3 * L] = csub(m2, n2);
+    o[4 * L] = csub(m1, n1);
+  } else {
+    // generic prime radix (7, 11, ...): direct length-p DFT with table twiddles
+    double2 x[kMaxGenericRadix];
+    for (int r = 0; r < p; ++r) {
+      double2 v = in[(c + r * mp) * L + f];
+      if (r && f) v = cmul(v, tw<SIGN>(W, f * r * mp));
+      x[r] = v;
+    }
+    const int step = N / p;
+    double2* o = out + c * L * p + f;
+    for (int q = 0; q < p; ++q) {
+      double2 acc = x[0];
+      for (int r = 1; r < p; ++r) acc = cadd(acc, cmul(x[r], tw<SIGN>(W, ((q * r) % p) * step)));
+      o[q * L] = acc;
+    }
+  }
+}
+
+// Transform `nf` rows of length pl.N (row stride ld) held in `a`, using `b` as scratch.  All threads
+// of the block take part; returns the buffer that holds the result (a or b).  Ends with a barrier.
+template <int SIGN>
+__device__ double2* stockham_rows(double2* a, double2* b, int nf, int ld, const FftPlan& pl, const double2* W) {
+  const int N = pl.N;
+  int L = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int p = pl.radix[s];
+    const int mp = N / (L * p);
+    const int nb = N / p;
+    const int total = nb * nf;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int row = t / nb;
+      int bt = t - row * nb;
+      int f = bt % L;
+      int c = bt / L;
+      butterfly<SIGN>(p, a + row * ld, b + row * ld, c, f, L, mp, N, W);
+    }
+    __syncthreads();
+    double2* tmp = a;
+    a = b;
+    b = tmp;
+    L *= p;
+  }
+  return a;
+}
+
+// frequency k in Z_N of storage index n
+__device__ __forceinline__ int freq_of(int n, int N) { return n <= (N - 1) / 2 ? n : n - N; }
+
+}  // namespace lrfg

@@ -1,0 +1,67 @@
+// Internal host-side entry points of the kernels (one translation unit each implements a group).
+#pragma once
+
+#include "common.cuh"
+#include "fft_device.cuh"
+
+namespace lrfg {
+
+// ---- fft.cu -------------------------------------------------------------------------------------
+FftPlan make_plan(int N);
+// batched complex DFT along the middle axis of (outer, N, inner); sign -1 forward, +1 inverse
+void fft_fibres(lrfg_ctx* ctx, const double2* in, double2* out, long long outer, int N, long long inner,
+                int sign);
+// real fibres: out = scale * F^-1 diag(m) F in, m given by kind/param (lrfg_multiplier)
+void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
+                    int kind, double param, double scale);
+// real fibres, many Gaussian multipliers at once: out_m = scale_m F^-1 diag(exp(-t_m k^2)) F in,
+// written to out + m * out_stride for m = 0..nm-1 (the exponential-sum preconditioner terms)
+void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long out_stride, long long outer,
+                       int N, long long inner, const double* t, const double* scale, int nm);
+
+// ---- linalg.cu ----------------------------------------------------------------------------------
+// C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b], row-major, op = transpose when trans* != 0.
+// A[b] is (transA ? K x M : M x K) with leading dimension lda, batch stride sA (elements); same for B.
+void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+          long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+          int batch = 1);
+// symmetric eigen-decomposition of `batch` m x m matrices (row-major, stride m*m): eigenvalues in
+// descending order into w (stride m), eigenvectors as the COLUMNS of V (row-major m x m, stride m*m).
+// A is destroyed.
+void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
+// elementwise helpers
+void fill(lrfg_ctx* ctx, double* x, double v, long long n);
+void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y
+double dot_host(lrfg_ctx* ctx, const double* x, const double* y, long long n);  // synchronises
+// device-scalar dot: *out = sum x*y (no host sync)
+void dot_device(lrfg_ctx* ctx, const double* x, const double* y, long long n, double* out);
+
+// ---- tt.cu --------------------------------------------------------------------------------------
+struct TTView {  // non-owning view of a TT with device carriages
+  int d;
+  int N[3];
+  int r[4];
+  const double* core[3];
+};
+TTView view_of(const TT& x);
+TTView view_of(const lrfg_tt& x);
+void tt_alloc(lrfg_ctx* ctx, TT& x, int d, const int* N, const int* r);
+void tt_copy(lrfg_ctx* ctx, const TTView& src, TT& dst);
+void tt_hadamard(lrfg_ctx* ctx, const TTView& x, const TTView& y, TT& out);
+// out = alpha x + beta y; alpha_dev / beta_dev (may be null) are device scalars multiplying alpha/beta
+void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& x, double beta,
+            const double* beta_dev, const TTView& y, TT& out);
+void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out);
+void tt_dot_device(lrfg_ctx* ctx, const TTView& x, const TTView& y, double* out_dev);
+double tt_dot(lrfg_ctx* ctx, const TTView& x, const TTView& y);
+void tt_expand(lrfg_ctx* ctx, const TTView& x, double* values);
+void tt_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int rmax, double tol, TT& out);
+// mode operator on carriage j (spectral multiplier along the mode index)
+void tt_mode_operator(lrfg_ctx* ctx, const TTView& x, int j, int kind, double param, double scale, TT& out);
+// exponential sum of 1/x on [1, xmax]: nodes t and weights w (host)
+void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector<double>& w);
+// out = T(P~^-1 x) with the exponential sum (t, w)
+void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w,
+                int rmax, TT& out);
+
+}  // namespace lrfg

@@ -1,0 +1,456 @@
+// Tensor-train operations on the device (hot-path rows a3 material Hadamard, a4 truncation, a5 sum,
+// a6 preconditioner, a7 inner products) and TT-SVD compression of a full coefficient.
+//
+// Carriage j is row-major (r_j, N_j, r_{j+1}); its left unfolding is the (r_j N_j) x r_{j+1} matrix
+// with the same memory, its right unfolding the r_j x (N_j r_{j+1}) matrix with the same memory.
+#include <algorithm>
+#include <cmath>
+
+#include "ops.cuh"
+
+namespace lrfg {
+
+TTView view_of(const TT& x) {
+  TTView v{};
+  v.d = x.d;
+  for (int j = 0; j < 3; ++j) v.N[j] = x.N[j];
+  for (int j = 0; j < 4; ++j) v.r[j] = x.r[j];
+  for (int j = 0; j < x.d; ++j) v.core[j] = x.core[j].get();
+  return v;
+}
+
+TTView view_of(const lrfg_tt& x) {
+  TTView v{};
+  v.d = x.d;
+  for (int j = 0; j < 3; ++j) v.N[j] = x.N[j];
+  for (int j = 0; j < 4; ++j) v.r[j] = x.r[j];
+  for (int j = 0; j < x.d; ++j) v.core[j] = x.cores[j];
+  return v;
+}
+
+static size_t celems(const TTView& x, int j) { return (size_t)x.r[j] * x.N[j] * x.r[j + 1]; }
+
+void tt_alloc(lrfg_ctx* ctx, TT& x, int d, const int* N, const int* r) {
+  x.d = d;
+  for (int j = 0; j < 3; ++j) x.N[j] = j < d ? N[j] : 0;
+  for (int j = 0; j < 4; ++j) x.r[j] = j <= d ? r[j] : 1;
+  x.r[0] = 1;
+  x.r[d] = 1;
+  for (int j = 0; j < d; ++j) x.core[j] = DBuf<double>(ctx->pool, (size_t)x.r[j] * x.N[j] * x.r[j + 1]);
+}
+
+void tt_copy(lrfg_ctx* ctx, const TTView& src, TT& dst) {
+  tt_alloc(ctx, dst, src.d, src.N, src.r);
+  for (int j = 0; j < src.d; ++j)
+    LRFG_CUDA(cudaMemcpyAsync(dst.core[j].get(), src.core[j], sizeof(double) * celems(src, j),
+                              cudaMemcpyDeviceToDevice, ctx->stream));
+}
+
+static unsigned grid1d(lrfg_ctx* ctx, long long n) {
+  long long g = (n + 255) / 256;
+  long long cap = 16LL * (ctx->num_sms > 0 ? ctx->num_sms : 152);
+  return (unsigned)std::max(1LL, std::min(g, cap));
+}
+
+// ------------------------------------------------------------------------------------------------
+// a3: Khatri–Rao product of carriages (App. A.3.1): out[(i*c+k), n, (j*e+l)] = x[i,n,j] y[k,n,l]
+// ------------------------------------------------------------------------------------------------
+__global__ void khatri_rao_kernel(const double* __restrict__ x, const double* __restrict__ y, double* out, int a,
+                                  int c, int n, int b, int e) {
+  const long long total = (long long)a * c * n * b * e;
+  const int be = b * e;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int col = (int)(t % be);
+    long long rest = t / be;
+    int nn = (int)(rest % n);
+    int row = (int)(rest / n);
+    int i = row / c, k = row - (row / c) * c;
+    int j = col / e, l = col - (col / e) * e;
+    out[t] = x[((size_t)i * n + nn) * b + j] * y[((size_t)k * n + nn) * e + l];
+  }
+}
+
+void tt_hadamard(lrfg_ctx* ctx, const TTView& x, const TTView& y, TT& out) {
+  LRFG_REQUIRE(x.d == y.d, "Hadamard of TTs of different order");
+  int r[4];
+  for (int j = 0; j <= x.d; ++j) r[j] = x.r[j] * y.r[j];
+  for (int j = 0; j < x.d; ++j) LRFG_REQUIRE(x.N[j] == y.N[j], "Hadamard of TTs on different grids");
+  tt_alloc(ctx, out, x.d, x.N, r);
+  for (int j = 0; j < x.d; ++j) {
+    long long total = (long long)r[j] * x.N[j] * r[j + 1];
+    khatri_rao_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(x.core[j], y.core[j], out.core[j].get(), x.r[j],
+                                                                    y.r[j], x.N[j], x.r[j + 1], y.r[j + 1]);
+    LRFG_CHECK_LAUNCH();
+    count_launch(ctx);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// a5: block sum alpha x + beta y; the scalars multiply the first carriage only
+// ------------------------------------------------------------------------------------------------
+__global__ void block_embed_kernel(const double* __restrict__ src, int a, int n, int b, double* dst, int A, int B,
+                                   int oa, int ob, double s, const double* __restrict__ s_dev) {
+  const long long total = (long long)a * n * b;
+  const double sc = s_dev ? s * (*s_dev) : s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int jb = (int)(t % b);
+    long long rest = t / b;
+    int nn = (int)(rest % n);
+    int ia = (int)(rest / n);
+    dst[((size_t)(ia + oa) * n + nn) * B + (jb + ob)] = sc * src[t];
+  }
+}
+
+static void embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double* dst, int A, int B, int oa, int ob,
+                  double s, const double* s_dev) {
+  long long total = (long long)a * n * b;
+  if (total == 0) return;
+  block_embed_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(src, a, n, b, dst, A, B, oa, ob, s, s_dev);
+  LRFG_CHECK_LAUNCH();
+  count_launch(ctx);
+}
+
+void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& x, double beta, const double* beta_dev,
+            const TTView& y, TT& out) {
+  LRFG_REQUIRE(x.d == y.d, "sum of TTs of different order");
+  const int d = x.d;
+  for (int j = 0; j < d; ++j) LRFG_REQUIRE(x.N[j] == y.N[j], "sum of TTs on different grids");
+  int r[4];
+  r[0] = 1;
+  r[d] = 1;
+  for (int j = 1; j < d; ++j) r[j] = x.r[j] + y.r[j];
+  tt_alloc(ctx, out, d, x.N, r);
+  for (int j = 0; j < d; ++j) {
+    double* dst = out.core[j].get();
+    const int A = r[j], B = r[j + 1], n = x.N[j];
+    if (d == 1) {
+      fill(ctx, dst, 0.0, (long long)n);
+      // out = alpha x + beta y elementwise (both 1 x n x 1)
+      embed(ctx, x.core[0], 1, n, 1, dst, 1, 1, 0, 0, alpha, alpha_dev);
+      // accumulate beta y: reuse axpby on a scaled copy
+      DBuf<double> tmp(ctx->pool, n);
+      embed(ctx, y.core[0], 1, n, 1, tmp.get(), 1, 1, 0, 0, beta, beta_dev);
+      axpby(ctx, n, 1.0, tmp.get(), 1.0, dst);
+      continue;
+    }
+    if (j != 0 && j != d - 1) fill(ctx, dst, 0.0, (long long)A * n * B);
+    const bool first = (j == 0);
+    if (j == 0) {
+      embed(ctx, x.core[j], 1, n, x.r[1], dst, 1, B, 0, 0, alpha, alpha_dev);
+      embed(ctx, y.core[j], 1, n, y.r[1], dst, 1, B, 0, x.r[1], beta, beta_dev);
+    } else if (j == d - 1) {
+      embed(ctx, x.core[j], x.r[j], n, 1, dst, A, 1, 0, 0, 1.0, nullptr);
+      embed(ctx, y.core[j], y.r[j], n, 1, dst, A, 1, x.r[j], 0, 1.0, nullptr);
+    } else {
+      embed(ctx, x.core[j], x.r[j], n, x.r[j + 1], dst, A, B, 0, 0, 1.0, nullptr);
+      embed(ctx, y.core[j], y.r[j], n, y.r[j + 1], dst, A, B, x.r[j], x.r[j + 1], 1.0, nullptr);
+    }
+    (void)first;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// a4: rank truncation by Gram-SVD.  TT rounding (App. A.3.3) computes, from left to right, the
+// truncated SVD of the unfolding  X_{<=j} = M_j * Rest_j, where M_j is the current left part and
+// Rest_j the original carriages right of bond j.  With R_j = Rest_j Rest_j^T (a right-to-left sweep
+// of Gram contractions), the left singular vectors of M_j Rest_j follow from two small symmetric
+// eigen-problems (the Gram-SVD of Al Daas, Ballard & Benner, "Parallel algorithms for tensor train
+// arithmetic", SIAM J. Sci. Comput. 44 (2022)):
+//     M^T M = V diag(lam) V^T,   R_A = diag(lam)^{1/2} V^T,   R_A R_j R_A^T = U diag(sig^2) U^T,
+//     left factor  Y = M V diag(lam)^{-1/2} U_k  (orthonormal columns),
+//     transfer     T = U_k^T R_A                 (= Y^T M),   next left part  T x carriage j+1.
+// Directions with lam <= tau lam_max (numerically zero) are dropped from R_A.
+// ------------------------------------------------------------------------------------------------
+__global__ void sqrt_scale_rows_kernel(const double* __restrict__ lam, const double* __restrict__ V, double* RA,
+                                       double* Pinv, int m, double tau) {
+  // RA[i][c] = sqrt(lam_i) V[c][i];  Pinv[c][i] = V[c][i] / sqrt(lam_i)   (0 for dropped i)
+  const double lmax = lam[0] > 0.0 ? lam[0] : 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
+    int i = t / m, c = t - (t / m) * m;
+    double l = lam[i];
+    bool keep = l > tau * lmax && l > 0.0;
+    double sl = keep ? sqrt(l) : 0.0;
+    RA[(size_t)i * m + c] = sl * V[(size_t)c * m + i];
+    Pinv[(size_t)c * m + i] = keep ? V[(size_t)c * m + i] / sl : 0.0;
+  }
+}
+
+void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
+  LRFG_REQUIRE(rmax >= 1, "truncation rank must be >= 1 (got %d)", rmax);
+  const int d = x.d;
+  LRFG_REQUIRE(d >= 1 && d <= 3, "TT order must be 1..3");
+  if (d == 1) { tt_copy(ctx, x, out); return; }
+  // ranks after the (implicit) right-to-left orthogonalisation and after truncation, as in TT rounding
+  int sp[4], rr[4];
+  sp[d] = 1;
+  for (int j = d - 1; j >= 1; --j) sp[j] = std::min(x.r[j], x.N[j] * sp[j + 1]);
+  rr[0] = 1;
+  for (int j = 0; j < d - 1; ++j) rr[j + 1] = std::min(rmax, std::min(rr[j] * x.N[j], sp[j + 1]));
+  rr[d] = 1;
+  tt_alloc(ctx, out, d, x.N, rr);
+  const double tau = 64.0 * 2.220446049250313e-16;
+
+  // right Gram matrices R[j] (s_j x s_j) of the carriages j..d-1, j = 1..d-1
+  DBuf<double> R[4];
+  {
+    const int j = d - 1;
+    const int s = x.r[j], n = x.N[j];
+    R[j] = DBuf<double>(ctx->pool, (size_t)s * s);
+    gemm(ctx, 0, 1, s, s, n, 1.0, x.core[j], n, 0, x.core[j], n, 0, 0.0, R[j].get(), s, 0);
+    for (int jj = d - 2; jj >= 1; --jj) {
+      const int a = x.r[jj], nn = x.N[jj], b = x.r[jj + 1];
+      DBuf<double> T(ctx->pool, (size_t)a * nn * b);
+      gemm(ctx, 0, 0, a * nn, b, b, 1.0, x.core[jj], b, 0, R[jj + 1].get(), b, 0, 0.0, T.get(), b, 0);
+      R[jj] = DBuf<double>(ctx->pool, (size_t)a * a);
+      gemm(ctx, 0, 1, a, a, nn * b, 1.0, T.get(), nn * b, 0, x.core[jj], nn * b, 0, 0.0, R[jj].get(), a, 0);
+    }
+  }
+  // left sweep
+  DBuf<double> Z(ctx->pool, celems(x, 0));
+  LRFG_CUDA(cudaMemcpyAsync(Z.get(), x.core[0], sizeof(double) * celems(x, 0), cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int j = 0; j < d - 1; ++j) {
+    const int a = rr[j], n = x.N[j], b = x.r[j + 1], k = rr[j + 1];
+    const int rows = a * n;
+    DBuf<double> GA(ctx->pool, (size_t)b * b), lam(ctx->pool, b), VA(ctx->pool, (size_t)b * b);
+    gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, 0, Z.get(), b, 0, 0.0, GA.get(), b, 0);
+    syevj(ctx, GA.get(), lam.get(), VA.get(), b);
+    DBuf<double> RA(ctx->pool, (size_t)b * b), Pinv(ctx->pool, (size_t)b * b);
+    sqrt_scale_rows_kernel<<<grid1d(ctx, (long long)b * b), 256, 0, ctx->stream>>>(lam.get(), VA.get(), RA.get(),
+                                                                                    Pinv.get(), b, tau);
+    LRFG_CHECK_LAUNCH();
+    count_launch(ctx);
+    // S = RA R RA^T
+    DBuf<double> RAR(ctx->pool, (size_t)b * b), S(ctx->pool, (size_t)b * b);
+    gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, 0, R[j + 1].get(), b, 0, 0.0, RAR.get(), b, 0);
+    gemm(ctx, 0, 1, b, b, b, 1.0, RAR.get(), b, 0, RA.get(), b, 0, 0.0, S.get(), b, 0);
+    DBuf<double> sig(ctx->pool, b), US(ctx->pool, (size_t)b * b);
+    syevj(ctx, S.get(), sig.get(), US.get(), b);
+    // P = Pinv U_k (b x k), Y = M P, T = U_k^T RA (k x b)
+    DBuf<double> P(ctx->pool, (size_t)b * k), T(ctx->pool, (size_t)k * b);
+    gemm(ctx, 0, 0, b, k, b, 1.0, Pinv.get(), b, 0, US.get(), b, 0, 0.0, P.get(), k, 0);
+    gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, 0, P.get(), k, 0, 0.0, out.core[j].get(), k, 0);
+    gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, 0, RA.get(), b, 0, 0.0, T.get(), b, 0);
+    // next left part: T (k x b) times carriage j+1 as b x (N s)
+    const int n1 = x.N[j + 1], c1 = x.r[j + 2];
+    DBuf<double> Zn(ctx->pool, (size_t)k * n1 * c1);
+    gemm(ctx, 0, 0, k, n1 * c1, b, 1.0, T.get(), b, 0, x.core[j + 1], n1 * c1, 0, 0.0, Zn.get(), n1 * c1, 0);
+    Z = std::move(Zn);
+  }
+  LRFG_CUDA(cudaMemcpyAsync(out.core[d - 1].get(), Z.get(), sizeof(double) * (size_t)rr[d - 1] * x.N[d - 1],
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+}
+
+// ------------------------------------------------------------------------------------------------
+// a7: inner product by left-to-right contraction: W_{j+1}[b,e] = sum W_j[a,c] x_j[a,n,b] y_j[c,n,e]
+// ------------------------------------------------------------------------------------------------
+void tt_dot_device(lrfg_ctx* ctx, const TTView& x, const TTView& y, double* out_dev) {
+  LRFG_REQUIRE(x.d == y.d, "dot of TTs of different order");
+  DBuf<double> W(ctx->pool, 1);
+  fill(ctx, W.get(), 1.0, 1);
+  for (int j = 0; j < x.d; ++j) {
+    const int a = x.r[j], b = x.r[j + 1], c = y.r[j], e = y.r[j + 1], n = x.N[j];
+    LRFG_REQUIRE(n == y.N[j], "dot of TTs on different grids");
+    // V (c x (n b)) = W^T (c x a) * x_j (a x (n b))
+    DBuf<double> V(ctx->pool, (size_t)c * n * b);
+    gemm(ctx, 1, 0, c, n * b, a, 1.0, W.get(), c, 0, x.core[j], n * b, 0, 0.0, V.get(), n * b, 0);
+    // W' (b x e) = V^T ((c n) x b)^T * y_j ((c n) x e)
+    double* dst = (j == x.d - 1) ? out_dev : nullptr;
+    DBuf<double> Wn;
+    if (!dst) { Wn = DBuf<double>(ctx->pool, (size_t)b * e); dst = Wn.get(); }
+    gemm(ctx, 1, 0, b, e, c * n, 1.0, V.get(), b, 0, y.core[j], e, 0, 0.0, dst, e, 0);
+    if (j != x.d - 1) W = std::move(Wn);
+  }
+}
+
+double tt_dot(lrfg_ctx* ctx, const TTView& x, const TTView& y) {
+  DBuf<double> d(ctx->pool, 1);
+  tt_dot_device(ctx, x, y, d.get());
+  double h = 0.0;
+  LRFG_CUDA(cudaMemcpyAsync(&h, d.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  return h;
+}
+
+// expand: F_1 = G_0 (N0 x r1); F_{j+1} = F_j (P x r_j) G_j (r_j x N_j r_{j+1})
+void tt_expand(lrfg_ctx* ctx, const TTView& x, double* values) {
+  const int d = x.d;
+  if (d == 1) {
+    LRFG_CUDA(cudaMemcpyAsync(values, x.core[0], sizeof(double) * x.N[0], cudaMemcpyDeviceToDevice, ctx->stream));
+    return;
+  }
+  long long P = x.N[0];
+  DBuf<double> F(ctx->pool, celems(x, 0));
+  LRFG_CUDA(cudaMemcpyAsync(F.get(), x.core[0], sizeof(double) * celems(x, 0), cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int j = 1; j < d; ++j) {
+    const int a = x.r[j], n = x.N[j], b = x.r[j + 1];
+    double* dst;
+    DBuf<double> Fn;
+    if (j == d - 1) dst = values; else { Fn = DBuf<double>(ctx->pool, (size_t)P * n * b); dst = Fn.get(); }
+    LRFG_REQUIRE(P < (1LL << 31), "expanded grid too large");
+    gemm(ctx, 0, 0, (int)P, n * b, a, 1.0, F.get(), a, 0, x.core[j], n * b, 0, 0.0, dst, n * b, 0);
+    P *= n;
+    if (j != d - 1) F = std::move(Fn);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// TT-SVD of a full array (App. A.3.3, first case) via Gram eigen-decompositions of the unfoldings:
+// for j < d-1 the left singular vectors of the (r_j N_j) x rest unfolding from its row Gram matrix
+// when r_j N_j is the smaller side, else the right ones from the column Gram matrix.
+// ------------------------------------------------------------------------------------------------
+__global__ void transpose_kernel(const double* __restrict__ in, int rows, int cols, double* out) {
+  const long long total = (long long)rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t / cols), j = (int)(t % cols);
+    out[(size_t)j * rows + i] = in[t];
+  }
+}
+
+// out (cols x rows) = in (rows x cols)^T
+static void transpose(lrfg_ctx* ctx, const double* in, int rows, int cols, double* out) {
+  long long total = (long long)rows * cols;
+  if (total == 0) return;
+  transpose_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(in, rows, cols, out);
+  LRFG_CHECK_LAUNCH();
+  count_launch(ctx);
+}
+
+static int keep_rank(const std::vector<double>& lam, int rmax, double tol_j) {
+  const int m = (int)lam.size();
+  int k = std::min(rmax, m);
+  if (tol_j > 0.0) {
+    double total = 0.0;
+    for (double l : lam) total += std::max(l, 0.0);
+    double tail = 0.0;
+    int kk = m;
+    for (int i = m - 1; i >= 1; --i) {
+      double t2 = tail + std::max(lam[i], 0.0);
+      if (t2 <= tol_j * tol_j * total) { tail = t2; kk = i; } else break;
+    }
+    k = std::min(k, kk);
+  }
+  return std::max(k, 1);
+}
+
+void tt_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int rmax, double tol, TT& out) {
+  LRFG_REQUIRE(d >= 2 && d <= 3, "compression needs d in {2,3}");
+  LRFG_REQUIRE(rmax >= 1, "rank must be >= 1");
+  const double tol_j = tol > 0.0 ? tol / std::sqrt((double)(d - 1)) : 0.0;
+  long long total = 1;
+  for (int j = 0; j < d; ++j) total *= N[j];
+  // current remainder C: rows = r_j N_j, cols = N_{j+1}...N_{d-1}
+  DBuf<double> C(ctx->pool, (size_t)total);
+  LRFG_CUDA(cudaMemcpyAsync(C.get(), values, sizeof(double) * total, cudaMemcpyDeviceToDevice, ctx->stream));
+  int r[4] = {1, 1, 1, 1};
+  std::vector<DBuf<double>> cores(d);
+  int rj = 1;
+  long long cols = total / N[0];
+  for (int j = 0; j < d - 1; ++j) {
+    const int rows = rj * N[j];
+    LRFG_REQUIRE(cols < (1LL << 31), "unfolding too wide");
+    const bool use_rows = rows <= cols;
+    const int m = use_rows ? rows : (int)cols;
+    DBuf<double> G(ctx->pool, (size_t)m * m), lam(ctx->pool, m), V(ctx->pool, (size_t)m * m);
+    if (use_rows)
+      gemm(ctx, 0, 1, m, m, (int)cols, 1.0, C.get(), (int)cols, 0, C.get(), (int)cols, 0, 0.0, G.get(), m, 0);
+    else
+      gemm(ctx, 1, 0, m, m, rows, 1.0, C.get(), (int)cols, 0, C.get(), (int)cols, 0, 0.0, G.get(), m, 0);
+    syevj(ctx, G.get(), lam.get(), V.get(), m);
+    std::vector<double> hl(m);
+    LRFG_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int k = std::min(keep_rank(hl, rmax, tol_j), std::min(rows, (int)cols));
+    // V's first k columns, packed (m x k)
+    DBuf<double> Vk(ctx->pool, (size_t)m * k);
+    LRFG_CUDA(cudaMemcpy2DAsync(Vk.get(), sizeof(double) * k, V.get(), sizeof(double) * m, sizeof(double) * k, m,
+                                cudaMemcpyDeviceToDevice, ctx->stream));
+    if (use_rows) {
+      // core = U_k (rows x k); remainder = U_k^T C (k x cols)
+      cores[j] = DBuf<double>(ctx->pool, (size_t)rows * k);
+      LRFG_CUDA(cudaMemcpyAsync(cores[j].get(), Vk.get(), sizeof(double) * rows * k, cudaMemcpyDeviceToDevice, ctx->stream));
+      DBuf<double> Cn(ctx->pool, (size_t)k * cols);
+      gemm(ctx, 1, 0, k, (int)cols, rows, 1.0, Vk.get(), k, 0, C.get(), (int)cols, 0, 0.0, Cn.get(), (int)cols, 0);
+      C = std::move(Cn);
+    } else {
+      // right singular vectors V_k (cols x k): core = C V_k (rows x k), remainder = V_k^T (k x cols)
+      cores[j] = DBuf<double>(ctx->pool, (size_t)rows * k);
+      gemm(ctx, 0, 0, rows, k, (int)cols, 1.0, C.get(), (int)cols, 0, Vk.get(), k, 0, 0.0, cores[j].get(), k, 0);
+      DBuf<double> Cn(ctx->pool, (size_t)k * cols);
+      transpose(ctx, Vk.get(), (int)cols, k, Cn.get());
+      C = std::move(Cn);
+    }
+    r[j + 1] = k;
+    rj = k;
+    cols /= N[j + 1];
+  }
+  cores[d - 1] = std::move(C);
+  out.d = d;
+  for (int j = 0; j < 3; ++j) out.N[j] = j < d ? N[j] : 0;
+  for (int j = 0; j <= d; ++j) out.r[j] = r[j];
+  for (int j = 0; j < d; ++j) out.core[j] = std::move(cores[j]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// mode operators and the exponential-sum preconditioner (a1, a6)
+// ------------------------------------------------------------------------------------------------
+void tt_mode_operator(lrfg_ctx* ctx, const TTView& x, int j, int kind, double param, double scale, TT& out) {
+  tt_copy(ctx, x, out);
+  fibre_operator(ctx, x.core[j], out.core[j].get(), x.r[j], x.N[j], x.r[j + 1], kind, param, scale);
+}
+
+void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector<double>& w) {
+  // sinc (trapezoidal) quadrature of 1/x = int exp(tau - x e^tau) d tau:  t_m = e^{tau_m}, w_m = h e^{tau_m}
+  LRFG_REQUIRE(eps > 0.0 && eps < 1.0 && xmax >= 1.0, "exponential sum needs 0 < eps < 1, xmax >= 1");
+  const double pi = 3.14159265358979323846;
+  const double h = pi * pi / std::log(32.0 / eps);
+  const double tau_min = std::log(eps / (2.0 * xmax));
+  const double tau_max = std::log(std::log(2.0 / eps));
+  const int R = (int)std::ceil((tau_max - tau_min) / h) + 1;
+  t.resize(R);
+  w.resize(R);
+  for (int m = 0; m < R; ++m) {
+    double tau = tau_min + h * m;
+    t[m] = std::exp(tau);
+    w[m] = h * std::exp(tau);
+  }
+}
+
+void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
+                TT& out) {
+  // P~^-1 x = sum_m w_m (G_m x ... x G_m) x with G_m = F^-1 diag(exp(-t_m k^2)) F per mode: a TT whose
+  // carriages are block rows (first), block diagonal (middle) and block columns (last) over m.
+  const int d = x.d;
+  const int R = (int)t.size();
+  int r[4];
+  r[0] = 1;
+  r[d] = 1;
+  for (int j = 1; j < d; ++j) r[j] = R * x.r[j];
+  TT big;
+  tt_alloc(ctx, big, d, x.N, r);
+  std::vector<double> ones(R, 1.0);
+  for (int j = 0; j < d; ++j) {
+    const int a = x.r[j], n = x.N[j], b = x.r[j + 1];
+    const size_t e = (size_t)a * n * b;
+    DBuf<double> terms(ctx->pool, e * R);
+    fibre_gauss_multi(ctx, x.core[j], terms.get(), (long long)e, a, n, b, t.data(), (j == 0) ? w.data() : ones.data(), R);
+    double* dst = big.core[j].get();
+    if (d > 1 && j != 0 && j != d - 1) fill(ctx, dst, 0.0, (long long)r[j] * n * r[j + 1]);
+    for (int m = 0; m < R; ++m) {
+      const double* src = terms.get() + m * e;
+      if (d == 1) {
+        // single mode: plain sum of the terms
+        if (m == 0) LRFG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * e, cudaMemcpyDeviceToDevice, ctx->stream));
+        else axpby(ctx, (long long)e, 1.0, src, 1.0, dst);
+      } else if (j == 0) {
+        embed(ctx, src, 1, n, b, dst, 1, r[1], 0, m * b, 1.0, nullptr);
+      } else if (j == d - 1) {
+        embed(ctx, src, a, n, 1, dst, r[j], 1, m * a, 0, 1.0, nullptr);
+      } else {
+        embed(ctx, src, a, n, b, dst, r[j], r[j + 1], m * a, m * b, 1.0, nullptr);
+      }
+    }
+  }
+  tt_round(ctx, view_of(big), rmax, out);
+}
+
+}  // namespace lrfg
