@@ -104,8 +104,9 @@ typedef struct {
  * context
  * ------------------------------------------------------------------------------------------- */
 
-/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to issue work on (NULL: the
- * library creates its own).  `hbm_budget_bytes` caps the library's device pool (0: no cap). */
+/* Create a context on CUDA device `device`.  `stream` is the cudaStream_t all work is issued on (NULL:
+ * the legacy default stream).  `hbm_budget_bytes` caps the library's device pool (0: no cap).
+ * lrfg_destroy fails with LRFG_EINVAL while problems or fields of the context are still alive. */
 lrfg_status lrfg_create(lrfg_ctx** ctx, int device, void* stream, size_t hbm_budget_bytes);
 lrfg_status lrfg_destroy(lrfg_ctx* ctx);
 const char* lrfg_strerror(lrfg_status st);

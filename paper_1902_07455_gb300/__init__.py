@@ -15,6 +15,7 @@ Objects
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -98,8 +99,9 @@ class TTensor:
 
 
 class Context:
-    """A liblrfg context on one CUDA device (``stream``: a torch.cuda.Stream, or None for torch's current
-    stream; ``budget``: cap of the library's device pool in bytes, 0 = none)."""
+    """A liblrfg context on one CUDA device.  ``stream``: a torch.cuda.Stream, or None for torch's current
+    stream at creation; the library issues all its work there, so torch ops on the same stream see its
+    results in order.  ``budget``: cap of the library's device pool in bytes, 0 = none."""
 
     def __init__(self, device: int = 0, stream=None, budget: int = 0):
         torch = _torch()
@@ -111,6 +113,7 @@ class Context:
         h = C.c_void_p()
         self._check(self.lib.lrfg_create(C.byref(h), self.device, C.c_void_p(s.cuda_stream), int(budget)), None)
         self.h = h
+        self._children = weakref.WeakSet()
 
     def _check(self, st, h=None):
         if st != L.LRFG_OK:
@@ -122,9 +125,16 @@ class Context:
         return self._check(st, self.h)
 
     def close(self):
+        """Free every problem and field of this context, then the context."""
         if getattr(self, "h", None):
+            for child in list(self._children):
+                child.free()
             self.lib.lrfg_destroy(self.h)
             self.h = None
+
+    def _adopt(self, obj):
+        self._children.add(obj)
+        return obj
 
     def __del__(self):
         try:
@@ -259,7 +269,8 @@ class Context:
                 raise ValueError("float64 values required")
             ptr, on_dev, shape, keep = _ptr(t), int(t.is_cuda), tuple(t.shape), t
         h = C.c_void_p()
-        self.check(self.lib.lrfg_field_from_full(self.h, len(shape), _ivec(shape, 3), ptr, on_dev, C.byref(h)))
+        self.check(self.lib.lrfg_field_from_full(self.h, len(shape), _ivec(list(shape)[:3], 3), ptr, on_dev,
+                                                 C.byref(h)))
         del keep
         return Field(self, h)
 
@@ -276,6 +287,7 @@ class Field:
     def __init__(self, ctx: Context, handle):
         self.ctx = ctx
         self.h = handle
+        ctx._adopt(self)
 
     def info(self):
         fmt, d = C.c_int(), C.c_int()
@@ -307,9 +319,9 @@ class Field:
         return TTensor(cores)
 
     def free(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.lrfg_field_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -362,7 +374,7 @@ class Problem:
                 c.on_device = int(t.is_cuda)
                 keep = t
             c.d = keep.ndim if isinstance(keep, np.ndarray) else keep.dim()
-            for j, n in enumerate(keep.shape):
+            for j, n in enumerate(list(keep.shape)[:3]):  # the library rejects d outside {2, 3}
                 c.N[j] = int(n)
             c.fmt = L.LRFG_FULL
         o = L.lrfg_opts()
@@ -373,6 +385,7 @@ class Problem:
         del keep
         self.h = h
         self.d = c.d
+        ctx._adopt(self)
 
     def coeff_ranks(self):
         r = (C.c_int * 4)()
@@ -409,9 +422,9 @@ class Problem:
         return out.value
 
     def free(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.lrfg_problem_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

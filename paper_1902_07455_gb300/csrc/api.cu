@@ -329,11 +329,18 @@ double full_aeff(lrfg_problem* P, const double* E, const double2* v) {
 
 void new_field(lrfg_ctx* ctx, lrfg_format fmt, int d, const int* N, lrfg_field** out) {
   lrfg_field* f = new lrfg_field();
+  ctx->live_objects++;
   f->ctx = ctx;
   f->fmt = fmt;
   f->d = d;
   for (int j = 0; j < 3; ++j) f->N[j] = j < d ? N[j] : 0;
   *out = f;
+}
+
+// undo new_field() for a field that never reached the caller
+void discard_field(lrfg_field* f) {
+  f->ctx->live_objects--;
+  delete f;
 }
 
 void check_field(const lrfg_problem* P, const lrfg_field* f) {
@@ -512,12 +519,7 @@ lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget)
     LRFG_CUDA(cudaSetDevice(device));
     LRFG_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     LRFG_CUDA(cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-    if (stream) {
-      ctx->stream = (cudaStream_t)stream;
-    } else {
-      LRFG_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
-      ctx->own_stream = true;
-    }
+    ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
     ctx->pool = new DevicePool(budget);
   });
   if (st != LRFG_OK) {
@@ -530,11 +532,14 @@ lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget)
 
 lrfg_status lrfg_destroy(lrfg_ctx* ctx) {
   if (!ctx) return LRFG_EINVAL;
+  if (ctx->live_objects > 0) {
+    ctx->last_error = "free every problem and field of this context before destroying it";
+    return LRFG_EINVAL;
+  }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   delete ctx->pool;
   for (auto& kv : ctx->twiddles) cudaFree(kv.second.W);
-  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return LRFG_OK;
 }
@@ -556,8 +561,8 @@ lrfg_status lrfg_pool_bytes(const lrfg_ctx* ctx, size_t* in_use, size_t* reserve
 lrfg_status lrfg_fft_fibres(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner, int sign) {
   if (!ctx) return LRFG_EINVAL;
   return guard(ctx, [&] {
-    LRFG_REQUIRE(in && out, "null buffer");
     LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
+    LRFG_REQUIRE((in && out) || (long long)outer * inner == 0, "null buffer");
     LRFG_REQUIRE(sign == 1 || sign == -1, "sign must be +1 or -1");
     LRFG_REQUIRE(N >= 1 && N % 2 == 1, "N must be odd");
     fft_fibres(ctx, (const double2*)in, (double2*)out, outer, N, inner, sign);
@@ -568,8 +573,8 @@ lrfg_status lrfg_fibre_operator(lrfg_ctx* ctx, const double* in, double* out, in
                                 lrfg_multiplier kind, double param, double scale) {
   if (!ctx) return LRFG_EINVAL;
   return guard(ctx, [&] {
-    LRFG_REQUIRE(in && out, "null buffer");
     LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
+    LRFG_REQUIRE((in && out) || (long long)outer * inner == 0, "null buffer");
     LRFG_REQUIRE(N >= 1 && N % 2 == 1, "N must be odd");
     fibre_operator(ctx, in, out, outer, N, inner, (int)kind, param, scale);
   });
@@ -679,6 +684,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     if (opts->fmt == LRFG_TT) LRFG_REQUIRE(opts->rank >= 1, "TT solve needs rank >= 1 (got %d)", opts->rank);
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT, "coefficient format must be FULL or TT");
     P = new lrfg_problem();
+    ctx->live_objects++;
     P->ctx = ctx;
     P->opts = *opts;
     if (P->opts.pinv_eps <= 0.0) P->opts.pinv_eps = 0.1;
@@ -732,7 +738,10 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     *out = P;
   });
-  if (st != LRFG_OK) delete P;
+  if (st != LRFG_OK && P) {
+    delete P;
+    ctx->live_objects--;
+  }
   return st;
 }
 
@@ -742,6 +751,7 @@ lrfg_status lrfg_problem_free(lrfg_problem* P) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   delete P;
+  ctx->live_objects--;
   return LRFG_OK;
 }
 
@@ -760,7 +770,7 @@ lrfg_status lrfg_problem_apply(lrfg_problem* P, const lrfg_field* in, lrfg_field
     apply_into(P, in, f);
     *out = f;
   });
-  if (st != LRFG_OK) delete f;
+  if (st != LRFG_OK && f) discard_field(f);
   return st;
 }
 
@@ -788,7 +798,7 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
     }
     *out = f;
   });
-  if (st != LRFG_OK) delete f;
+  if (st != LRFG_OK && f) discard_field(f);
   return st;
 }
 
@@ -848,7 +858,7 @@ lrfg_status lrfg_field_from_full(lrfg_ctx* ctx, int d, const int N[3], const dou
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     *out = f;
   });
-  if (st != LRFG_OK) delete f;
+  if (st != LRFG_OK && f) discard_field(f);
   return st;
 }
 
@@ -863,7 +873,7 @@ lrfg_status lrfg_field_from_tt(lrfg_ctx* ctx, const lrfg_tt* x, int on_device, l
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     *out = f;
   });
-  if (st != LRFG_OK) delete f;
+  if (st != LRFG_OK && f) discard_field(f);
   return st;
 }
 
@@ -911,9 +921,11 @@ lrfg_status lrfg_field_export_tt(lrfg_ctx* ctx, const lrfg_field* f, double* con
 
 lrfg_status lrfg_field_free(lrfg_field* f) {
   if (!f) return LRFG_EINVAL;
-  cudaSetDevice(f->ctx->device);
-  cudaStreamSynchronize(f->ctx->stream);
+  lrfg_ctx* ctx = f->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
   delete f;
+  ctx->live_objects--;
   return LRFG_OK;
 }
 

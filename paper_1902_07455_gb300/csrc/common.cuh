@@ -112,14 +112,14 @@ struct Twiddles {
 // the context owns the device, the stream, the pool and cached tables
 struct lrfg_ctx {
   int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
+  cudaStream_t stream = nullptr;  // caller's stream (NULL: the legacy default stream)
   lrfg::DevicePool* pool = nullptr;
   std::map<int, lrfg::Twiddles> twiddles;
   std::string last_error;
   int num_sms = 0;
   int max_smem_optin = 0;
   long long kernel_launches = 0;  // launches issued through this context (instrumentation)
+  long long live_objects = 0;     // problems and fields not yet freed
 };
 
 namespace lrfg {
