@@ -161,17 +161,44 @@ void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& 
 //     transfer     T = U_k^T R_A                 (= Y^T M),   next left part  T x carriage j+1.
 // Directions with lam <= tau lam_max (numerically zero) are dropped from R_A.
 // ------------------------------------------------------------------------------------------------
-__global__ void sqrt_scale_rows_kernel(const double* __restrict__ lam, const double* __restrict__ V, double* RA,
-                                       double* Pinv, int m, double tau) {
-  // RA[i][c] = sqrt(lam_i) V[c][i];  Pinv[c][i] = V[c][i] / sqrt(lam_i)   (0 for dropped i)
+// Bond balancing: with c_i = (R_ii / GA_ii)^{1/4} the diagonal scaling M -> M C, Rest -> C^{-1} Rest
+// leaves the tensor unchanged and equalises the two Gram diagonals (GA -> C GA C, R -> C^{-1} R C^{-1}).
+// It keeps the eigen-decompositions accurate when the columns of the left part and the rows of the
+// right part have very different scales (e.g. after Khatri–Rao products and exponential sums).
+__global__ void balance_kernel(double* GA, double* R, double* c, int m) {
+  extern __shared__ double cs[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double ga = GA[(size_t)i * m + i], rb = R[(size_t)i * m + i];
+    cs[i] = (ga > 0.0 && rb > 0.0) ? sqrt(sqrt(rb / ga)) : 1.0;
+    c[i] = cs[i];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, j = t - (t / m) * m;
+    double f = cs[i] * cs[j];
+    GA[t] *= f;
+    R[t] /= f;
+  }
+}
+
+// From the eigen-decomposition GA = V diag(lam) V^T (balanced):
+//   RA[i][col]  = sqrt(lam_i) V[col][i]            (for S = RA R RA^T)
+//   RAc[i][col] = sqrt(lam_i) V[col][i] / c_col     (transfer, undoes the balancing)
+//   Pc[row][i]  = c_row V[row][i] / sqrt(lam_i)     (left factor, undoes the balancing)
+// Directions with lam <= tau lam_max are dropped (rows/columns set to 0).
+__global__ void sqrt_scale_rows_kernel(const double* __restrict__ lam, const double* __restrict__ V,
+                                       const double* __restrict__ c, double* RA, double* RAc, double* Pc, int m,
+                                       double tau) {
   const double lmax = lam[0] > 0.0 ? lam[0] : 0.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
-    int i = t / m, c = t - (t / m) * m;
+    int i = t / m, col = t - (t / m) * m;
     double l = lam[i];
     bool keep = l > tau * lmax && l > 0.0;
     double sl = keep ? sqrt(l) : 0.0;
-    RA[(size_t)i * m + c] = sl * V[(size_t)c * m + i];
-    Pinv[(size_t)c * m + i] = keep ? V[(size_t)c * m + i] / sl : 0.0;
+    double v = V[(size_t)col * m + i];
+    RA[(size_t)i * m + col] = sl * v;
+    RAc[(size_t)i * m + col] = sl * v / c[col];
+    Pc[(size_t)col * m + i] = keep ? c[col] * v / sl : 0.0;
   }
 }
 
@@ -188,7 +215,7 @@ void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
   for (int j = 0; j < d - 1; ++j) rr[j + 1] = std::min(rmax, std::min(rr[j] * x.N[j], sp[j + 1]));
   rr[d] = 1;
   tt_alloc(ctx, out, d, x.N, rr);
-  const double tau = 64.0 * 2.220446049250313e-16;
+  const double tau = 1e-30;
 
   // right Gram matrices R[j] (s_j x s_j) of the carriages j..d-1, j = 1..d-1
   DBuf<double> R[4];
@@ -212,24 +239,28 @@ void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
     const int a = rr[j], n = x.N[j], b = x.r[j + 1], k = rr[j + 1];
     const int rows = a * n;
     DBuf<double> GA(ctx->pool, (size_t)b * b), lam(ctx->pool, b), VA(ctx->pool, (size_t)b * b);
+    DBuf<double> cb(ctx->pool, b);
     gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, 0, Z.get(), b, 0, 0.0, GA.get(), b, 0);
-    syevj(ctx, GA.get(), lam.get(), VA.get(), b);
-    DBuf<double> RA(ctx->pool, (size_t)b * b), Pinv(ctx->pool, (size_t)b * b);
-    sqrt_scale_rows_kernel<<<grid1d(ctx, (long long)b * b), 256, 0, ctx->stream>>>(lam.get(), VA.get(), RA.get(),
-                                                                                    Pinv.get(), b, tau);
+    balance_kernel<<<1, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b);
     LRFG_CHECK_LAUNCH();
     count_launch(ctx);
-    // S = RA R RA^T
+    syevj(ctx, GA.get(), lam.get(), VA.get(), b);
+    DBuf<double> RA(ctx->pool, (size_t)b * b), RAc(ctx->pool, (size_t)b * b), Pc(ctx->pool, (size_t)b * b);
+    sqrt_scale_rows_kernel<<<grid1d(ctx, (long long)b * b), 256, 0, ctx->stream>>>(lam.get(), VA.get(), cb.get(), RA.get(),
+                                                                                    RAc.get(), Pc.get(), b, tau);
+    LRFG_CHECK_LAUNCH();
+    count_launch(ctx);
+    // S = RA R RA^T (balanced)
     DBuf<double> RAR(ctx->pool, (size_t)b * b), S(ctx->pool, (size_t)b * b);
     gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, 0, R[j + 1].get(), b, 0, 0.0, RAR.get(), b, 0);
     gemm(ctx, 0, 1, b, b, b, 1.0, RAR.get(), b, 0, RA.get(), b, 0, 0.0, S.get(), b, 0);
     DBuf<double> sig(ctx->pool, b), US(ctx->pool, (size_t)b * b);
     syevj(ctx, S.get(), sig.get(), US.get(), b);
-    // P = Pinv U_k (b x k), Y = M P, T = U_k^T RA (k x b)
+    // P = Pc U_k (b x k), Y = M P, T = U_k^T RAc (k x b)
     DBuf<double> P(ctx->pool, (size_t)b * k), T(ctx->pool, (size_t)k * b);
-    gemm(ctx, 0, 0, b, k, b, 1.0, Pinv.get(), b, 0, US.get(), b, 0, 0.0, P.get(), k, 0);
+    gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, 0, US.get(), b, 0, 0.0, P.get(), k, 0);
     gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, 0, P.get(), k, 0, 0.0, out.core[j].get(), k, 0);
-    gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, 0, RA.get(), b, 0, 0.0, T.get(), b, 0);
+    gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, 0, RAc.get(), b, 0, 0.0, T.get(), b, 0);
     // next left part: T (k x b) times carriage j+1 as b x (N s)
     const int n1 = x.N[j + 1], c1 = x.r[j + 2];
     DBuf<double> Zn(ctx->pool, (size_t)k * n1 * c1);
