@@ -1,0 +1,414 @@
+"""Benchmark: low-rank (TT) vs full-format Fourier–Galerkin homogenisation on GB300.
+
+Workload (default): d = 3, N = 243 per axis, isotropic lognormal conductivity a = exp(g), g a seeded
+periodic Gaussian random field (squared-exponential covariance, correlation length 0.2, variance 1,
+seed 19020745), E = (1, 0, 0).  The coefficient is compressed on the GPU to TT rank r_A (default 10,
+the coefficient rank the paper uses for its stochastic material) and the full-format solver gets the
+expansion of that TT coefficient, so both solve the same problem.
+
+One step = one complete TT solve from u = 0 (minimal-residual iteration with truncation to rank r until
+the residual stops decreasing, then A_eff): every hot-path stage — mode-wise gradient FFTs, Khatri–Rao
+material products, Gram-SVD truncations, divergence sums, exponential-sum preconditioner, TT inner
+products, A_eff.  value = TT solves per second over the timed steps (whole job: summed over ranks
+under torchrun, timed by the slowest rank).  The full-format FP64 PCG solve of the same problem is
+timed beside it (full_solves_per_s, op-applies/s of both) and gives the A_eff reference.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the library's stream,
+with a 512 MiB buffer written between steps to flush L2 (the TT state is a few MiB and would otherwise
+stay in L2).  nvidia-smi samples clocks during the timed region.
+
+    python bench.py [--steps K] [--warmup W] [--rank r] [--N 243] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and CG op-applies/s at A_eff rel err ≤1e-6, low-rank vs full; p50/p99"
+SEED = 19020745
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--N", type=int, default=243)
+    p.add_argument("--rank", type=int, default=10)
+    p.add_argument("--coeff-rank", type=int, default=10)
+    p.add_argument("--pinv-eps", type=float, default=0.1)
+    p.add_argument("--maxit", type=int, default=60)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(args):
+    return {"workload": f"d=3 N={args.N}^3 lognormal SE-GRF (l=0.2, var=1, seed {SEED}), E=(1,0,0); "
+                        f"TT rank {args.rank} MinRes vs full FP64 PCG",
+            "d": 3, "N": args.N, "coeff_tt_rank": args.coeff_rank, "tt_rank": args.rank,
+            "pinv_eps": args.pinv_eps, "precision": "fp64", "l2": "flushed between steps (512 MiB write)"}
+
+
+def make_coefficient(N):
+    from synthetic import lognormal_grf
+    return lognormal_grf(3, N, ell=0.2, var=1.0, seed=SEED)
+
+
+# -------------------------------------------------------------------------------------------------
+# clocks
+# -------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------------------------------------------
+# roofline of the dominant kernel class
+# -------------------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 arithmetic classes are bound by the FP64 pipe: GB300 issues 2 FP64 FMA per clock per SM
+# (4 flop/clk/SM), i.e. 152 SMs x 2.07 GHz x 4 = 1.26 TFLOP/s at the maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2.070 * 4 / 1e3
+ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen"}
+
+
+def roofline(stats):
+    peaks, src = measured_peaks()
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    s = stats[dom]
+    per_launch_ms = s["ms"] / max(s["launches"], 1)
+    if dom in ALU_CLASSES:
+        achieved = s["flops"] / (s["ms"] * 1e-3) / 1e12 if s["ms"] > 0 else 0.0
+        peak = FP64_PEAK_TFLOPS
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "peak_source": "derived FP64 pipe rate (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)"}
+    else:
+        achieved = s["bytes"] / (s["ms"] * 1e-3) / 1e9 if s["ms"] > 0 else 0.0
+        peak = float(peaks["hbm_gbs"])
+        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+               "peak_source": src}
+    total = sum(v["ms"] for v in stats.values())
+    out.update({"kernel_class": dom, "launches": s["launches"], "avg_launch_ms": per_launch_ms,
+                "share": s["ms"] / total if total > 0 else None, "traffic": None})
+    return out
+
+
+# -------------------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands
+# -------------------------------------------------------------------------------------------------
+def oracle_apply_seconds(N, coeff_rank, rank, pinv_eps, n_applies=1):
+    """Time oracle applications of the truncated TT operator (Eq. (Pls_lowrank)) on a rank-r operand."""
+    from oracle import lowrank as lr
+    A = make_coefficient(N)
+    a_tt = lr.tt_svd(A, rmax=coeff_rank)
+    op = lr.LowRankGaNi(a_tt, (N, N, N), fmt="tt", rank=rank, pinv_eps=pinv_eps)
+    b = op.rhs(np.array([1.0, 0.0, 0.0]))
+    times = []
+    x = b
+    for _ in range(n_applies):
+        t0 = time.perf_counter()
+        x = op.apply(x)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# -------------------------------------------------------------------------------------------------
+# our arm
+# -------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1902_07455_gb300 as lrfg
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1902_07455_gb300 import build
+    build.build()
+    ctx = lrfg.Context(local)
+    E = [1.0, 0.0, 0.0]
+    A = make_coefficient(args.N)
+    A_dev = torch.as_tensor(A, device=f"cuda:{local}")
+    a_tt = ctx.tt_compress(A_dev, args.coeff_rank)
+    a_full = ctx.tt_expand(a_tt)
+    del A_dev
+
+    # full-format reference solve (FP64 PCG, tol 1e-8) on the same coefficient
+    Pfull = ctx.problem(a_full, lrfg.FULL, tol=1e-8, maxit=2000)
+    full_res, _ = Pfull.solve(E, want_field=False)
+    full_times = []
+    for _ in range(2):
+        r, _ = Pfull.solve(E, want_field=False)
+        full_times.append(r.seconds)
+    # full-format operator applications
+    f_in = ctx.field_from_full(torch.randn((args.N,) * 3, dtype=torch.float64, device=f"cuda:{local}"))
+    f_out = Pfull.apply(f_in)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        Pfull.apply_into(f_in, f_out)
+    torch.cuda.synchronize()
+    full_apply_s = (time.perf_counter() - t0) / 5
+    f_in.free()
+    f_out.free()
+
+    Ptt = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, tol=1e-12, maxit=args.maxit,
+                      stop_on_increase=True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    stream = ctx.stream
+
+    def step():
+        res, _ = Ptt.solve(E, want_field=False)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ctx.profile_reset()
+    ctx.profile(True)
+    step_ms, results = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            results.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    stats = ctx.profile_read()
+    launches = ctx.launch_count() - launches0
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    res = results[-1]
+    applies = sum(r.applies for r in results)
+    rel_err = abs(res.Aeff - full_res.Aeff) / full_res.Aeff
+
+    # end to end through the C ABI with host buffers: lrfg_solve with the coefficient carriages in host
+    # memory (copied in each call) and the result read back to the host
+    host_cores = [c.cpu().numpy() for c in a_tt.cores]
+    e2e_ms = []
+    for i in range(max(args.steps, 1)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r_e2e = solve_host(ctx, host_cores, args, E)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = sum(c.nbytes for c in host_cores)
+    d2h = 8 * 2 + 4 * 8  # the lrfg_result fields read back (A_eff, residual, counters)
+
+    line = None
+    if rank == 0:
+        solves_per_s = world * args.steps / (total_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "tt_op_applies_per_s": world * applies / (total_ms * 1e-3),
+            "tt_applies_per_solve": applies / args.steps,
+            "tt_iters": res.iters, "tt_aeff": res.Aeff, "full_aeff": full_res.Aeff, "aeff_rel_err": rel_err,
+            "meets_1e-6": rel_err <= 1e-6,
+            "full_solves_per_s": 1.0 / statistics.median(full_times), "full_iters": full_res.iters,
+            "full_op_applies_per_s": 1.0 / full_apply_s,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "coeff_ranks": Ptt.coeff_ranks(),
+            "e2e": {"value": 1e3 / statistics.median(e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "aeff": r_e2e},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "roofline": roofline(stats),
+            "kernel_classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in stats.items()
+                               if v["launches"]},
+        }
+    Ptt.free()
+    Pfull.free()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def solve_host(ctx, host_cores, args, E):
+    """One lrfg_solve call with host-resident coefficient carriages (the public C ABI)."""
+    import ctypes as C
+    from paper_1902_07455_gb300 import _lib as L
+    c = L.lrfg_coeff()
+    c.d = 3
+    for j in range(3):
+        c.N[j] = host_cores[j].shape[1]
+    c.fmt = L.LRFG_TT
+    c.on_device = 0
+    c.tt.d = 3
+    keep = [np.ascontiguousarray(h) for h in host_cores]
+    for j in range(3):
+        c.tt.N[j] = keep[j].shape[1]
+        c.tt.cores[j] = keep[j].ctypes.data
+    rr = [1] + [k.shape[2] for k in keep[:-1]] + [1]
+    for j in range(4):
+        c.tt.r[j] = rr[j]
+    o = L.lrfg_opts()
+    o.fmt, o.prec, o.rank, o.pinv_eps = L.LRFG_TT, L.LRFG_FP64, args.rank, args.pinv_eps
+    o.tol, o.maxit, o.stop_on_increase = 1e-12, args.maxit, 1
+    res = L.lrfg_result()
+    Ed = (C.c_double * 3)(*E)
+    st = ctx.lib.lrfg_solve(ctx.h, C.byref(c), Ed, C.byref(o), C.byref(res), None)
+    if st not in (L.LRFG_OK, L.LRFG_ENOCONV):
+        ctx.check(st)
+    return res.Aeff
+
+
+def add_cpu_baseline(line, args):
+    # a bounded sample: oracle applications of the same truncated operator (about 10-30 s of CPU work),
+    # scaled to solves/s with the applies per solve of the GPU run (the same algorithm)
+    t = oracle_apply_seconds(args.N, args.coeff_rank, args.rank, args.pinv_eps, n_applies=2)
+    per_apply = statistics.median(t)
+    per_solve = per_apply * line["tt_applies_per_solve"]
+    line["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                            "sample": f"{len(t)} oracle applications of the rank-{args.rank} TT operator at "
+                                      f"N={args.N}^3 ({per_apply:.2f} s each), scaled by "
+                                      f"{line['tt_applies_per_solve']:.1f} applications per solve"}
+
+
+# -------------------------------------------------------------------------------------------------
+# reference arm: the oracle, timed on the host cores
+# -------------------------------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    # applications per solve of this algorithm at this workload (measured on the GPU arm); without a GPU
+    # run at hand, the oracle's own count on a short solve is not affordable at N=243, so the step is one
+    # oracle application and the value is scaled by a fixed applies-per-solve figure stated in the line
+    applies_per_solve = 16.0
+    times = []
+    from oracle import lowrank as lr
+    A = make_coefficient(args.N)
+    a_tt = lr.tt_svd(A, rmax=args.coeff_rank)
+    op = lr.LowRankGaNi(a_tt, (args.N,) * 3, fmt="tt", rank=args.rank, pinv_eps=args.pinv_eps)
+    x = op.rhs(np.array([1.0, 0.0, 0.0]))
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        x = op.apply(x)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per_solve = statistics.median(times) * applies_per_solve
+    value = 1.0 / per_solve
+    cores = cpu_cores()
+    return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step one oracle application of the rank-{args.rank} TT operator at "
+                                       f"N={args.N}^3, scaled by {applies_per_solve:.0f} applications per solve"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_ours(args)
+        if line is not None and not args.no_cpu_baseline and dist_env()[0] == 1:
+            add_cpu_baseline(line, args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -118,6 +118,17 @@ long long lrfg_launch_count(const lrfg_ctx* ctx);
 /* Bytes currently held by the context's device pool (in use, and reserved including cached). */
 lrfg_status lrfg_pool_bytes(const lrfg_ctx* ctx, size_t* in_use, size_t* reserved);
 
+/* Kernel accounting.  Every launch is counted per kernel class (lrfg_profile_classes() classes named
+ * by lrfg_profile_class_name) with its algorithmic floating-point operations and DRAM bytes (each operand
+ * read once, each result written once).  While profiling is enabled, every launch is also bracketed by
+ * CUDA events on the context's stream and its device time is added to its class.  lrfg_profile_read
+ * synchronises the stream and copies the first n classes' totals (any output pointer may be NULL). */
+int lrfg_profile_classes(void);
+const char* lrfg_profile_class_name(int k);
+lrfg_status lrfg_profile_enable(lrfg_ctx* ctx, int on);
+lrfg_status lrfg_profile_reset(lrfg_ctx* ctx);
+lrfg_status lrfg_profile_read(lrfg_ctx* ctx, int n, long long* launches, double* flops, double* bytes, double* ms);
+
 /* ---------------------------------------------------------------------------------------------
  * mode-wise operators on fibres (rows a1, a2 of the hot path)
  * ------------------------------------------------------------------------------------------- */

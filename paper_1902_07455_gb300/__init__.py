@@ -148,6 +148,22 @@ class Context:
     def launch_count(self) -> int:
         return int(self.lib.lrfg_launch_count(self.h))
 
+    def profile(self, on: bool = True):
+        """Enable/disable event timing of every launch (accounting of counts/flops/bytes is always on)."""
+        self.check(self.lib.lrfg_profile_enable(self.h, int(bool(on))))
+
+    def profile_reset(self):
+        self.check(self.lib.lrfg_profile_reset(self.h))
+
+    def profile_read(self) -> dict:
+        """Per kernel class: launches, algorithmic flops and bytes, device ms (while profiling)."""
+        n = self.lib.lrfg_profile_classes()
+        L_ = (C.c_longlong * n)()
+        f, b, m = (C.c_double * n)(), (C.c_double * n)(), (C.c_double * n)()
+        self.check(self.lib.lrfg_profile_read(self.h, n, L_, f, b, m))
+        return {self.lib.lrfg_profile_class_name(k).decode(): dict(launches=L_[k], flops=f[k], bytes=b[k], ms=m[k])
+                for k in range(n)}
+
     def pool_bytes(self):
         a, b = C.c_size_t(), C.c_size_t()
         self.check(self.lib.lrfg_pool_bytes(self.h, C.byref(a), C.byref(b)))

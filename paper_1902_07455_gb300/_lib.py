@@ -49,6 +49,11 @@ SIGNATURES = {
     "lrfg_sync": (_ST, [_P]),
     "lrfg_launch_count": (C.c_longlong, [_P]),
     "lrfg_pool_bytes": (_ST, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "lrfg_profile_classes": (_I, []),
+    "lrfg_profile_class_name": (C.c_char_p, [_I]),
+    "lrfg_profile_enable": (_ST, [_P, _I]),
+    "lrfg_profile_reset": (_ST, [_P]),
+    "lrfg_profile_read": (_ST, [_P, _I, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)]),
     "lrfg_fft_fibres": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
     "lrfg_fibre_operator": (_ST, [_P, _P, _P, _I, _I, _I, _I, _D, _D]),
     "lrfg_tt_hadamard": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),

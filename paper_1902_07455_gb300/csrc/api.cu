@@ -92,6 +92,34 @@ void DevicePool::trim() {
   }
 }
 
+cudaEvent_t take_event(lrfg_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  LRFG_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void resolve_profile(lrfg_ctx* ctx) {
+  if (ctx->pending.empty()) return;
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    LRFG_CUDA(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+    ctx->stats[p.first].ms += ms;
+    ctx->event_pool.push_back(p.second.first);
+    ctx->event_pool.push_back(p.second.second);
+  }
+  ctx->pending.clear();
+}
+
+static const char* kClassNames[KC_COUNT] = {
+    "fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "pointwise",
+    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc"};
+
 }  // namespace lrfg
 
 using namespace lrfg;
@@ -540,6 +568,11 @@ lrfg_status lrfg_destroy(lrfg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   delete ctx->pool;
   for (auto& kv : ctx->twiddles) cudaFree(kv.second.W);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   delete ctx;
   return LRFG_OK;
 }
@@ -550,6 +583,40 @@ lrfg_status lrfg_sync(lrfg_ctx* ctx) {
 }
 
 long long lrfg_launch_count(const lrfg_ctx* ctx) { return ctx ? ctx->kernel_launches : -1; }
+
+int lrfg_profile_classes(void) { return KC_COUNT; }
+
+const char* lrfg_profile_class_name(int k) { return (k >= 0 && k < KC_COUNT) ? kClassNames[k] : ""; }
+
+lrfg_status lrfg_profile_enable(lrfg_ctx* ctx, int on) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    if (!on) resolve_profile(ctx);
+    ctx->profiling = on != 0;
+  });
+}
+
+lrfg_status lrfg_profile_reset(lrfg_ctx* ctx) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    resolve_profile(ctx);
+    for (auto& st : ctx->stats) st = KStats{};
+  });
+}
+
+lrfg_status lrfg_profile_read(lrfg_ctx* ctx, int n, long long* launches, double* flops, double* bytes, double* ms) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    LRFG_REQUIRE(n >= 0 && n <= KC_COUNT, "n must be in [0, %d]", (int)KC_COUNT);
+    resolve_profile(ctx);
+    for (int k = 0; k < n; ++k) {
+      if (launches) launches[k] = ctx->stats[k].launches;
+      if (flops) flops[k] = ctx->stats[k].flops;
+      if (bytes) bytes[k] = ctx->stats[k].bytes;
+      if (ms) ms[k] = ctx->stats[k].ms;
+    }
+  });
+}
 
 lrfg_status lrfg_pool_bytes(const lrfg_ctx* ctx, size_t* in_use, size_t* reserved) {
   if (!ctx || !in_use || !reserved) return LRFG_EINVAL;

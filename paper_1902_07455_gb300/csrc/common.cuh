@@ -109,6 +109,30 @@ struct Twiddles {
 
 }  // namespace lrfg
 
+namespace lrfg {
+// kernel classes for live timing and accounting (names exported through lrfg_profile_read)
+enum KClass {
+  KC_FFT_FIBRES = 0,  // complex fibre FFTs (mode-wise FFT, full-format complex axes)
+  KC_FIBRE_OP,        // real fibres under one Fourier multiplier (gradient / divergence)
+  KC_GAUSS_MULTI,     // real fibres under the exponential-sum multipliers (preconditioner)
+  KC_R2C,             // full format: real rows -> half spectra
+  KC_C2R,             // full format: half spectra -> real rows
+  KC_POINTWISE,       // full format: Fourier multipliers and PCG updates
+  KC_REDUCE,          // dot products and energy sums
+  KC_GEMM,            // FP64 GEMM (Gram matrices, contractions)
+  KC_EIGEN,           // small symmetric eigen-decompositions
+  KC_KHATRI_RAO,      // TT Hadamard (Khatri–Rao carriages)
+  KC_TT_MISC,         // block embedding, balancing, scaling, transposes, fills
+  KC_COUNT
+};
+struct KStats {
+  long long launches = 0;
+  double flops = 0.0;  // algorithmic floating-point operations issued
+  double bytes = 0.0;  // algorithmic DRAM bytes (ideal: each operand read once, result written once)
+  double ms = 0.0;     // device time from events (only while profiling is on)
+};
+}  // namespace lrfg
+
 // the context owns the device, the stream, the pool and cached tables
 struct lrfg_ctx {
   int device = 0;
@@ -120,9 +144,52 @@ struct lrfg_ctx {
   int max_smem_optin = 0;
   long long kernel_launches = 0;  // launches issued through this context (instrumentation)
   long long live_objects = 0;     // problems and fields not yet freed
+  bool profiling = false;         // record events around every launch
+  lrfg::KStats stats[lrfg::KC_COUNT];
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;  // (class, (start, stop))
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace lrfg {
 const Twiddles& twiddles_for(lrfg_ctx* ctx, int N);
-inline void count_launch(lrfg_ctx* ctx, int n = 1) { ctx->kernel_launches += n; }
+
+cudaEvent_t take_event(lrfg_ctx* ctx);
+void resolve_profile(lrfg_ctx* ctx);  // synchronises, folds pending event pairs into stats
+
+// Accounts one kernel launch of class kc (flops / bytes algorithmic) and, while profiling is on,
+// brackets it with events on the context's stream.
+class KTimer {
+ public:
+  KTimer(lrfg_ctx* ctx, KClass kc, double flops, double bytes) : ctx_(ctx), kc_(kc) {
+    ctx->kernel_launches += 1;
+    KStats& s = ctx->stats[kc];
+    s.launches += 1;
+    s.flops += flops;
+    s.bytes += bytes;
+    if (ctx->profiling) {
+      start_ = take_event(ctx);
+      cudaEventRecord(start_, ctx->stream);
+    }
+  }
+  ~KTimer() {
+    if (start_) {
+      cudaEvent_t stop = take_event(ctx_);
+      cudaEventRecord(stop, ctx_->stream);
+      ctx_->pending.push_back({(int)kc_, {start_, stop}});
+    }
+  }
+
+ private:
+  lrfg_ctx* ctx_;
+  KClass kc_;
+  cudaEvent_t start_ = nullptr;
+};
 }  // namespace lrfg
+
+// launch a kernel with accounting: LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, kernel<<<...>>>(args));
+#define LRFG_LAUNCH(ctx, kc, flops, bytes, ...)                 \
+  do {                                                          \
+    ::lrfg::KTimer kt_((ctx), ::lrfg::kc, (double)(flops), (double)(bytes)); \
+    __VA_ARGS__;                                                \
+    LRFG_CHECK_LAUNCH();                                        \
+  } while (0)

@@ -110,15 +110,17 @@ void fft_fibres(lrfg_ctx* ctx, const double2* in, double2* out, long long outer,
   long long nfib = outer * inner;
   long long blocks = (nfib + TF - 1) / TF;
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
+  const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;   // radix-2-equivalent count
+  const double bytes = 2.0 * sizeof(double2) * (double)N * (double)nfib;
   if (sign < 0) {
     LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fft_fibres_kernel<-1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W);
+    LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
+                fft_fibres_kernel<-1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W));
   } else {
     LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fft_fibres_kernel<1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W);
+    LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
+                fft_fibres_kernel<1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W));
   }
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
 }
 
 // ----------------------------------------------------------------------------------------------------
@@ -193,10 +195,12 @@ void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long oute
   long long blocks = (nfib + 2LL * TF - 1) / (2LL * TF);
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
   LRFG_CUDA(cudaFuncSetAttribute(fibre_op_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fibre_op_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W, kind,
-                                                               param, scale);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  // two complex transforms per pair of real fibres
+  const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;
+  const double bytes = 2.0 * sizeof(double) * (double)N * (double)nfib;
+  LRFG_LAUNCH(ctx, KC_FIBRE_OP, flops, bytes,
+              fibre_op_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W,
+                                                                             kind, param, scale));
 }
 
 // Many Gaussian multipliers of one input: the forward transform is shared, each term m gets its own
@@ -275,10 +279,12 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   long long nfib = outer * inner;
   long long blocks = (nfib + 2 * tf - 1) / (2 * tf);
   LRFG_CUDA(cudaFuncSetAttribute(fibre_gauss_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fibre_gauss_multi_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, out_stride, outer, N, inner,
-                                                                         (int)tf, pl, tw.W, dt.get(), ds.get(), nm);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  // one forward and nm inverse complex transforms per pair of real fibres
+  const double flops = 2.5 * N * std::log2((double)N) * (double)nfib * (1.0 + nm);
+  const double bytes = sizeof(double) * (double)N * (double)nfib * (1.0 + nm);
+  LRFG_LAUNCH(ctx, KC_GAUSS_MULTI, flops, bytes,
+              fibre_gauss_multi_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(
+                  in, out, out_stride, outer, N, inner, (int)tf, pl, tw.W, dt.get(), ds.get(), nm));
   // the pool hands these blocks out again only to later work on the same stream
 }
 

@@ -129,10 +129,10 @@ void full_forward(lrfg_ctx* ctx, const FullGrid& g, const double* real_in, const
   int TF = row_tile(ctx, N, &smem);
   long long blocks = (g.rows + 2LL * TF - 1) / (2LL * TF);
   LRFG_CUDA(cudaFuncSetAttribute(r2c_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  r2c_rows_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(real_in, coef, scale, half_out, g.rows, N, g.H, TF, pl,
-                                                               tw.W);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_R2C, 2.5 * N * std::log2((double)N) * (double)g.rows,
+              (double)g.rows * (N * sizeof(double) * (coef ? 2 : 1) + g.H * sizeof(double2)),
+              r2c_rows_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(real_in, coef, scale, half_out, g.rows, N,
+                                                                             g.H, TF, pl, tw.W));
   // complex axes, innermost first
   long long inner = g.H;
   for (int ax = g.d - 2; ax >= 0; --ax) {
@@ -158,10 +158,10 @@ void full_inverse(lrfg_ctx* ctx, const FullGrid& g, double2* half_inout, const d
   int TF = row_tile(ctx, N, &smem);
   long long blocks = (g.rows + 2LL * TF - 1) / (2LL * TF);
   LRFG_CUDA(cudaFuncSetAttribute(c2r_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  c2r_rows_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(half_inout, coef, scale, real_out, g.rows, N, g.H, TF,
-                                                               pl, tw.W);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_C2R, 2.5 * N * std::log2((double)N) * (double)g.rows,
+              (double)g.rows * (N * sizeof(double) * (coef ? 2 : 1) + g.H * sizeof(double2)),
+              c2r_rows_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(half_inout, coef, scale, real_out, g.rows,
+                                                                             N, g.H, TF, pl, tw.W));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -242,23 +242,21 @@ static KIndex kindex(const FullGrid& g) {
 }
 
 void half_mul_grad(lrfg_ctx* ctx, const FullGrid& g, const double2* in, double2* out, int alpha, double scale) {
-  mul_grad_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, out, g.n_half, kindex(g), alpha, scale);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 2.0 * g.n_half, 2.0 * sizeof(double2) * g.n_half,
+              mul_grad_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, out, g.n_half, kindex(g), alpha,
+                                                                               scale));
 }
 
 void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const double2* in, double2* acc, int alpha, double scale, int init,
                   int precond) {
-  acc_div_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, acc, g.n_half, kindex(g), alpha, scale, init,
-                                                                 precond);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 4.0 * g.n_half, (init ? 2.0 : 3.0) * sizeof(double2) * g.n_half,
+              acc_div_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, acc, g.n_half, kindex(g), alpha, scale,
+                                                                              init, precond));
 }
 
 void half_precond(lrfg_ctx* ctx, const FullGrid& g, const double2* in, double2* out) {
-  precond_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, out, g.n_half, kindex(g));
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 2.0 * g.n_half, 2.0 * sizeof(double2) * g.n_half,
+              precond_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, out, g.n_half, kindex(g)));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -319,21 +317,19 @@ __global__ void finish_sum_kernel(const double* __restrict__ partial, int n, dou
 
 void half_dot(lrfg_ctx* ctx, const FullGrid& g, const double2* x, const double2* y, double* out_dev) {
   DBuf<double> partial(ctx->pool, kRedBlocks);
-  half_dot_kernel<<<kRedBlocks, 256, 0, ctx->stream>>>(x, y, g.n_half, g.H, partial.get());
-  LRFG_CHECK_LAUNCH();
-  finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, 0);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx, 2);
+  LRFG_LAUNCH(ctx, KC_REDUCE, 4.0 * g.n_half, 2.0 * sizeof(double2) * g.n_half,
+              half_dot_kernel<<<kRedBlocks, 256, 0, ctx->stream>>>(x, y, g.n_half, g.H, partial.get()));
+  LRFG_LAUNCH(ctx, KC_REDUCE, kRedBlocks, kRedBlocks * sizeof(double),
+              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, 0));
 }
 
 void energy_sum(lrfg_ctx* ctx, const FullGrid& g, const double* e, const double* a, double E, double* out_dev,
                 int accumulate) {
   DBuf<double> partial(ctx->pool, kRedBlocks);
-  energy_kernel<<<kRedBlocks, 256, 0, ctx->stream>>>(e, a, E, g.n_real, partial.get());
-  LRFG_CHECK_LAUNCH();
-  finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, accumulate);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx, 2);
+  LRFG_LAUNCH(ctx, KC_REDUCE, 4.0 * g.n_real, 2.0 * sizeof(double) * g.n_real,
+              energy_kernel<<<kRedBlocks, 256, 0, ctx->stream>>>(e, a, E, g.n_real, partial.get()));
+  LRFG_LAUNCH(ctx, KC_REDUCE, kRedBlocks, kRedBlocks * sizeof(double),
+              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, accumulate));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -371,16 +367,15 @@ __global__ void pcg_direction_kernel(double2* p, const double2* __restrict__ z, 
 
 void pcg_update(lrfg_ctx* ctx, const FullGrid& g, double2* u, double2* r, const double2* p, const double2* q,
                 double2* z, const double* num, const double* den) {
-  pcg_update_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(u, r, p, q, z, g.n_half, kindex(g), num, den);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 10.0 * g.n_half, 7.0 * sizeof(double2) * g.n_half,
+              pcg_update_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(u, r, p, q, z, g.n_half, kindex(g), num,
+                                                                                 den));
 }
 
 void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, double2* p, const double2* z, const double* num,
                    const double* den) {
-  pcg_direction_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(p, z, g.n_half, num, den);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 4.0 * g.n_half, 3.0 * sizeof(double2) * g.n_half,
+              pcg_direction_kernel<<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(p, z, g.n_half, num, den));
 }
 
 }  // namespace lrfg

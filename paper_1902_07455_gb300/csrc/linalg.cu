@@ -99,10 +99,9 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
           int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) {
-    scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
-        C, M, N, ldc, sC, batch, beta);
-    LRFG_CHECK_LAUNCH();
-    count_launch(ctx);
+    LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
+                scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
+                    C, M, N, ldc, sC, batch, beta));
     return;
   }
   const int tm = (M + GT - 1) / GT, tn = (N + GT - 1) / GT;
@@ -118,22 +117,25 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
   splits = (K + kchunk - 1) / kchunk;
   LRFG_REQUIRE((long long)batch * splits < 65535, "gemm batch too large");
   if (splits > 1) {
-    scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
-        C, M, N, ldc, sC, batch, beta);
-    LRFG_CHECK_LAUNCH();
-    count_launch(ctx);
+    LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
+                scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
+                    C, M, N, ldc, sC, batch, beta));
   }
   dim3 grid(tn, tm, batch * splits);
+  const double flops = 2.0 * M * N * (double)K * batch;
+  const double bytes = sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
   if (!transA && !transB)
-    dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk);
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
   else if (transA && !transB)
-    dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk);
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
   else if (!transA && transB)
-    dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk);
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
   else
-    dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -297,9 +299,9 @@ void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
   DBuf<double> scratch;
   if (!use_smem) scratch = DBuf<double>(ctx->pool, (size_t)2 * m * m * batch);
   LRFG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  jacobi_kernel<<<batch, 256, smem, ctx->stream>>>(A, w, V, m, scratch.get(), use_smem);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  // one sweep of the two-sided cyclic Jacobi costs about 9 m^3 flops (rows, columns and V)
+  LRFG_LAUNCH(ctx, KC_EIGEN, 9.0 * (double)m * m * m * batch, 3.0 * sizeof(double) * (double)m * m * batch,
+              jacobi_kernel<<<batch, 256, smem, ctx->stream>>>(A, w, V, m, scratch.get(), use_smem));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -323,16 +325,14 @@ static unsigned grid_for(lrfg_ctx* ctx, long long n) {
 
 void fill(lrfg_ctx* ctx, double* x, double v, long long n) {
   if (n <= 0) return;
-  fill_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, v, n);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 0, sizeof(double) * (double)n,
+              fill_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, v, n));
 }
 
 void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y) {
   if (n <= 0) return;
-  axpby_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(n, alpha, x, beta, y);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 3.0 * n, 3.0 * sizeof(double) * n,
+              axpby_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(n, alpha, x, beta, y));
 }
 
 // two-stage deterministic dot: fixed grid of partial sums, then one block sums them in order
@@ -370,11 +370,10 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
 
 void dot_device(lrfg_ctx* ctx, const double* x, const double* y, long long n, double* out) {
   DBuf<double> partial(ctx->pool, kDotBlocks);
-  dot_partial_kernel<<<kDotBlocks, 256, 0, ctx->stream>>>(x, y, n, partial.get());
-  LRFG_CHECK_LAUNCH();
-  sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kDotBlocks, out);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx, 2);
+  LRFG_LAUNCH(ctx, KC_REDUCE, 2.0 * n, 2.0 * sizeof(double) * n,
+              dot_partial_kernel<<<kDotBlocks, 256, 0, ctx->stream>>>(x, y, n, partial.get()));
+  LRFG_LAUNCH(ctx, KC_REDUCE, kDotBlocks, kDotBlocks * sizeof(double),
+              sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kDotBlocks, out));
 }
 
 double dot_host(lrfg_ctx* ctx, const double* x, const double* y, long long n) {

@@ -78,10 +78,10 @@ void tt_hadamard(lrfg_ctx* ctx, const TTView& x, const TTView& y, TT& out) {
   tt_alloc(ctx, out, x.d, x.N, r);
   for (int j = 0; j < x.d; ++j) {
     long long total = (long long)r[j] * x.N[j] * r[j + 1];
-    khatri_rao_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(x.core[j], y.core[j], out.core[j].get(), x.r[j],
-                                                                    y.r[j], x.N[j], x.r[j + 1], y.r[j + 1]);
-    LRFG_CHECK_LAUNCH();
-    count_launch(ctx);
+    const double in_bytes = sizeof(double) * ((double)x.r[j] * x.N[j] * x.r[j + 1] + (double)y.r[j] * y.N[j] * y.r[j + 1]);
+    LRFG_LAUNCH(ctx, KC_KHATRI_RAO, (double)total, sizeof(double) * (double)total + in_bytes,
+                khatri_rao_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(
+                    x.core[j], y.core[j], out.core[j].get(), x.r[j], y.r[j], x.N[j], x.r[j + 1], y.r[j + 1]));
   }
 }
 
@@ -105,9 +105,8 @@ static void embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double*
                   double s, const double* s_dev) {
   long long total = (long long)a * n * b;
   if (total == 0) return;
-  block_embed_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(src, a, n, b, dst, A, B, oa, ob, s, s_dev);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, (double)total, 2.0 * sizeof(double) * total,
+              block_embed_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(src, a, n, b, dst, A, B, oa, ob, s, s_dev));
 }
 
 void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& x, double beta, const double* beta_dev,
@@ -241,15 +240,13 @@ void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
     DBuf<double> GA(ctx->pool, (size_t)b * b), lam(ctx->pool, b), VA(ctx->pool, (size_t)b * b);
     DBuf<double> cb(ctx->pool, b);
     gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, 0, Z.get(), b, 0, 0.0, GA.get(), b, 0);
-    balance_kernel<<<1, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b);
-    LRFG_CHECK_LAUNCH();
-    count_launch(ctx);
+    LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * b * b, 4.0 * sizeof(double) * b * b,
+                balance_kernel<<<1, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
     syevj(ctx, GA.get(), lam.get(), VA.get(), b);
     DBuf<double> RA(ctx->pool, (size_t)b * b), RAc(ctx->pool, (size_t)b * b), Pc(ctx->pool, (size_t)b * b);
-    sqrt_scale_rows_kernel<<<grid1d(ctx, (long long)b * b), 256, 0, ctx->stream>>>(lam.get(), VA.get(), cb.get(), RA.get(),
-                                                                                    RAc.get(), Pc.get(), b, tau);
-    LRFG_CHECK_LAUNCH();
-    count_launch(ctx);
+    LRFG_LAUNCH(ctx, KC_TT_MISC, 4.0 * b * b, 4.0 * sizeof(double) * b * b,
+                sqrt_scale_rows_kernel<<<grid1d(ctx, (long long)b * b), 256, 0, ctx->stream>>>(
+                    lam.get(), VA.get(), cb.get(), RA.get(), RAc.get(), Pc.get(), b, tau));
     // S = RA R RA^T (balanced)
     DBuf<double> RAR(ctx->pool, (size_t)b * b), S(ctx->pool, (size_t)b * b);
     gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, 0, R[j + 1].get(), b, 0, 0.0, RAR.get(), b, 0);
@@ -341,9 +338,8 @@ __global__ void transpose_kernel(const double* __restrict__ in, int rows, int co
 static void transpose(lrfg_ctx* ctx, const double* in, int rows, int cols, double* out) {
   long long total = (long long)rows * cols;
   if (total == 0) return;
-  transpose_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(in, rows, cols, out);
-  LRFG_CHECK_LAUNCH();
-  count_launch(ctx);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 0, 2.0 * sizeof(double) * total,
+              transpose_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(in, rows, cols, out));
 }
 
 static int keep_rank(const std::vector<double>& lam, int rmax, double tol_j) {
