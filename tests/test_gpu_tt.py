@@ -65,7 +65,7 @@ def test_round_matches_oracle(ctx, shape, big, small, rmax):
     for c in got.cores[:-1]:
         M = c.reshape(-1, c.shape[2])
         I = (M.T @ M).cpu().numpy()
-        assert np.abs(I - np.eye(I.shape[0])).max() <= 1e-10
+        assert np.abs(I - np.eye(I.shape[0])).max() <= 1e-8  # Gram-based factor: eps * cond(bond)^2
 
 
 def test_round_without_truncation_and_rank_deficient(ctx):
