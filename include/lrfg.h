@@ -171,6 +171,23 @@ lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* ou
 /* Euclidean inner product <x, y> = sum_k x[k] y[k] of two TTs (FP64 contraction). */
 lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);
 
+/* The same inner product as lrfg_tt_dot, for callers that cannot allocate device memory when they need
+ * it: code running while a stream is captured into a CUDA graph, applications whose own allocator owns
+ * all device memory, loops that must not wait on the driver's allocator.  (The paper has no counterpart:
+ * this is a calling convention of the library, not part of the method.)
+ *   - allocates nothing: the contraction intermediates live in one file-scope 4 MiB device array
+ *     (524288 doubles) that every GPU loading the library holds until the process exits;
+ *   - x, y: device carriages as for lrfg_tt_dot; `result` is a DEVICE pointer to one double, written
+ *     asynchronously on the context's stream (nothing is synchronised or copied to the host);
+ *   - the intermediates must fit: 2 max_j(r_x[j] r_y[j]) + max_j(r_y[j] N[j] r_x[j+1]) <= 524288
+ *     doubles, else LRFG_EINVAL with a message (nothing is launched); e.g. ranks 40 x 40 fit up to
+ *     N = 325;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress with that
+ *     device current); make that first call before any stream capture begins;
+ *   - all calls share the one array and overwrite it: calls whose work overlaps on the GPU (on
+ *     different streams or contexts of the same device, or from several host threads) race. */
+lrfg_status lrfg_tt_dot_noalloc(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);
+
 /* out = T(P~^-1 x) in real space: the exponential-sum preconditioner of accuracy pinv_eps applied as a
  * sum of separable Gaussian multipliers (rank R_P x r_x), then truncated to rmax (Sec. 2.3, 3.2).
  * out->cores must each hold min(rmax, R_P x->r[j]) N[j] min(rmax, R_P x->r[j+1]) doubles. */

@@ -243,6 +243,17 @@ class Context:
         self.check(self.lib.lrfg_tt_dot(self.h, C.byref(xs), C.byref(ys), C.byref(out)))
         return out.value
 
+    def tt_dot_noalloc(self, x: TTensor, y: TTensor, out):
+        """<x, y> into the CUDA float64 tensor ``out`` (one element) without any device allocation by the
+        library: for callers that cannot allocate at that point (stream capture, a foreign allocator).
+        Asynchronous on the context's stream; intermediates live in a fixed 4 MiB device array."""
+        torch = _torch()
+        if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
+            raise ValueError("out must be a CUDA float64 tensor with at least one element")
+        xs, ys = x.to_struct(), y.to_struct()
+        self.check(self.lib.lrfg_tt_dot_noalloc(self.h, C.byref(xs), C.byref(ys), _ptr(out)))
+        return out
+
     def tt_precond(self, x: TTensor, pinv_eps: float, rmax: int) -> TTensor:
         cap = [1] + [int(rmax)] * (x.d - 1) + [1]
         bufs, s = self._tt_out(x.shape, cap)

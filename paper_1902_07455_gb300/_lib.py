@@ -60,6 +60,7 @@ SIGNATURES = {
     "lrfg_tt_add": (_ST, [_P, _D, C.POINTER(lrfg_tt), _D, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
     "lrfg_tt_round": (_ST, [_P, C.POINTER(lrfg_tt), _I, C.POINTER(lrfg_tt)]),
     "lrfg_tt_dot": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(_D)]),
+    "lrfg_tt_dot_noalloc": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), _P]),
     "lrfg_tt_precond": (_ST, [_P, C.POINTER(lrfg_tt), _D, _I, C.POINTER(lrfg_tt)]),
     "lrfg_tt_compress": (_ST, [_P, _I, C.POINTER(_I), _P, _I, _D, C.POINTER(lrfg_tt)]),
     "lrfg_tt_expand": (_ST, [_P, C.POINTER(lrfg_tt), _P]),
