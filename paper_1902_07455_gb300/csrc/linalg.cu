@@ -9,42 +9,44 @@
 namespace lrfg {
 
 // ------------------------------------------------------------------------------------------------
-// GEMM: 64x64 output tile per block, k-step 16, 256 threads with 4x4 outputs each (rows ty+16i,
-// columns tx+16j).  Long-K products split K across blocks (split-K) and accumulate with atomics.
+// GEMM: TILE x TILE output tile per block (64 or 32), k-step 16, 256 threads with (TILE/16)^2 outputs
+// each (rows ty+16i, columns tx+16j).  Small or long-K products split K across blocks (split-K) and
+// accumulate with atomics into C pre-scaled by beta.
 // ------------------------------------------------------------------------------------------------
-constexpr int GT = 64, GK = 16;
+constexpr int GK = 16;
 
-template <bool TA, bool TB>
+template <bool TA, bool TB, int TILE>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                     int lda, long long sA, const double* __restrict__ B, int ldb,
                                                     long long sB, double beta, double* C, int ldc, long long sC,
                                                     int splits, int kchunk) {
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
+  constexpr int MT = TILE / 16;
+  __shared__ double As[GK][TILE + 1];
+  __shared__ double Bs[GK][TILE + 1];
   const int batch = blockIdx.z / splits, split = blockIdx.z - (blockIdx.z / splits) * splits;
   A += (size_t)batch * sA;
   B += (size_t)batch * sB;
   C += (size_t)batch * sC;
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const int m0 = blockIdx.y * TILE, n0 = blockIdx.x * TILE;
   const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  double acc[MT][MT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < MT; ++j) acc[i][j] = 0.0;
   for (int k0 = kbeg; k0 < kend; k0 += GK) {
-    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+    for (int e = threadIdx.x; e < TILE * GK; e += 256) {
       int mm, kk;
-      if (TA) { mm = e % GT; kk = e / GT; } else { kk = e % GK; mm = e / GK; }
+      if (TA) { mm = e % TILE; kk = e / TILE; } else { kk = e % GK; mm = e / GK; }
       int gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
       if (gm < M && gk < kend) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
       As[kk][mm] = v;
     }
-    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+    for (int e = threadIdx.x; e < TILE * GK; e += 256) {
       int nn, kk;
-      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % GT; kk = e / GT; }
+      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % TILE; kk = e / TILE; }
       int gn = n0 + nn, gk = k0 + kk;
       double v = 0.0;
       if (gn < N && gk < kend) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
@@ -53,24 +55,24 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[4];
+      double a[MT], b[MT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < MT; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < MT; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < MT; ++i) {
     int gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < MT; ++j) {
       int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       double* c = C + (size_t)gm * ldc + gn;
@@ -94,6 +96,26 @@ __global__ void scale_matrix_kernel(double* C, int M, int N, int ldc, long long 
   }
 }
 
+template <int TILE>
+static void gemm_launch(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A,
+                        int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc,
+                        long long sC, int batch, int splits, int kchunk, double flops, double bytes) {
+  const int tm = (M + TILE - 1) / TILE, tn = (N + TILE - 1) / TILE;
+  dim3 grid(tn, tm, batch * splits);
+  if (!transA && !transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
+  else if (transA && !transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
+  else if (!transA && transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
+  else
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
+}
+
 void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
           long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
           int batch) {
@@ -104,12 +126,15 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
                     C, M, N, ldc, sC, batch, beta));
     return;
   }
-  const int tm = (M + GT - 1) / GT, tn = (N + GT - 1) / GT;
-  long long tiles = (long long)tm * tn * batch;
-  int target = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
+  // small outputs use 32x32 tiles (more blocks); K is split until about two blocks per SM are busy,
+  // with at least 64 of K per block
+  const int tile = ((long long)M * N <= 256LL * 256LL) ? 32 : 64;
+  const int tm = (M + tile - 1) / tile, tn = (N + tile - 1) / tile;
+  const long long tiles = (long long)tm * tn * batch;
+  const int target = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
   int splits = 1;
   if (tiles < target) {
-    splits = (int)std::min<long long>((target + tiles - 1) / tiles, (K + 255) / 256);
+    splits = (int)std::min<long long>((target + tiles - 1) / tiles, std::max(1, K / 64));
     if (splits < 1) splits = 1;
   }
   int kchunk = (K + splits - 1) / splits;
@@ -121,30 +146,33 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
                 scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
                     C, M, N, ldc, sC, batch, beta));
   }
-  dim3 grid(tn, tm, batch * splits);
   const double flops = 2.0 * M * N * (double)K * batch;
   const double bytes = sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
-  if (!transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
-  else if (transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
-  else if (!transA && transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
+  if (tile == 32)
+    gemm_launch<32>(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, splits,
+                    kchunk, flops, bytes);
   else
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
+    gemm_launch<64>(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, splits,
+                    kchunk, flops, bytes);
 }
 
 // ------------------------------------------------------------------------------------------------
-// Symmetric eigensolver: cyclic two-sided Jacobi with the round-robin (circle) ordering, so that each
-// round applies m'/2 disjoint rotations in parallel (Golub & Van Loan, "Matrix Computations", 4th ed.,
-// Sec. 8.5 — the 2x2 symmetric Schur step and parallel orderings).  One block per matrix; the working
-// matrices live in shared memory when they fit, otherwise in a global scratch slice.
+// Symmetric eigensolver, two stages:
+//  1. cyclic two-sided Jacobi with the round-robin (circle) ordering, so that each round applies m'/2
+//     disjoint rotations in parallel (Golub & Van Loan, "Matrix Computations", 4th ed., Sec. 8.5: the
+//     2x2 symmetric Schur step and parallel orderings).  One block per matrix, working matrices in
+//     shared memory when they fit, else in a global scratch slice.  The working precision T is FP32
+//     for speed (GB300 issues FP32 at ~58x its FP64 rate) or FP64.
+//  2. (FP32 start) refinement to FP64 accuracy by the iteration of Ogita & Aishima, "Iterative
+//     refinement for symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35 (2018):
+//        R = I - X^T X,  S = X^T A X,  lam_i = S_ii / (1 - R_ii),
+//        E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > delta,  R_ij / 2 otherwise,
+//        X <- X + X E,   delta = 2 (||S - diag(lam)|| + ||A|| ||R||),
+//     which converges quadratically; eigenvalues closer than delta are treated as a cluster whose
+//     invariant subspace (not its individual vectors) is refined.  All of it is GEMM work in FP64.
 // ------------------------------------------------------------------------------------------------
 constexpr int kJacobiMaxSweeps = 30;
+constexpr int kJacobiThreads = 512;
 
 __device__ __forceinline__ void rr_pair(int round, int i, int mp, int* p, int* q) {
   // circle method: player mp-1 fixed, the others rotate
@@ -154,59 +182,66 @@ __device__ __forceinline__ void rr_pair(int round, int i, int mp, int* p, int* q
   *q = (round - i + n1) % n1;
 }
 
-__global__ void __launch_bounds__(256) jacobi_kernel(double* Ag, double* w, double* Vout, int m, double* scratch,
-                                                     int use_smem) {
-  extern __shared__ double sm[];
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double* __restrict__ Ag, double* w,
+                                                               double* Vout, int m, T* scratch, int use_smem,
+                                                               T eps) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int mp = m + (m & 1);
   const int npair = mp / 2;
-  double* A;
-  double* V;
-  double* Ain = Ag + (size_t)blockIdx.x * m * m;
-  double* cs = sm;            // 2 * npair (c, s)
-  int* pq = (int*)(cs + 2 * npair);  // 2 * npair
-  double* red = (double*)(pq + 2 * npair + ((2 * npair) & 1));  // 64 doubles for reductions
-  int* rank = (int*)(red + 64);      // m ints
-  if (use_smem) {
-    A = (double*)(rank + m + (m & 1));
+  T* cs = (T*)smraw;                                   // 2 npair (c, s)
+  int* pq = (int*)(cs + 2 * npair);                    // 2 npair
+  T* red = (T*)(pq + 2 * npair);                       // 32 partial sums
+  int* rank = (int*)(red + 32);                        // m (+1) ints
+  T* A;
+  T* V;
+  if (use_smem == 2) {         // A and V in shared memory
+    A = (T*)(rank + m + (m & 1));
     V = A + (size_t)m * m;
+  } else if (use_smem == 1) {  // A in shared memory, V in a global scratch slice
+    A = (T*)(rank + m + (m & 1));
+    V = scratch + (size_t)blockIdx.x * m * m;
   } else {
     A = scratch + (size_t)blockIdx.x * 2 * m * m;
     V = A + (size_t)m * m;
   }
+  const double* Ain = Ag + (size_t)blockIdx.x * m * m;
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-    A[t] = Ain[t];
-    V[t] = ((t / m) == (t % m)) ? 1.0 : 0.0;
+    A[t] = (T)Ain[t];
+    V[t] = ((t / m) == (t % m)) ? T(1) : T(0);
   }
   __syncthreads();
-  // reference scale: Frobenius norm of A
-  double loc = 0.0;
+  T loc = 0;
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) loc += A[t] * A[t];
-  for (int o = 16; o; o >>= 1) loc += __shfl_xor_sync(0xffffffff, loc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    red[32] = s;
-  }
-  __syncthreads();
-  const double fro2 = red[32];
-  const double tiny = 1e-300;
-  if (m > 1 && fro2 > 0.0) {
+  const T fro2 = block_sum(loc, red);
+  const T tol2 = T(16) * eps * eps * fro2;
+  T prev_off = fro2;
+  if (m > 1 && fro2 > T(0)) {
     for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
       for (int round = 0; round < mp - 1; ++round) {
         for (int i = threadIdx.x; i < npair; i += blockDim.x) {
           int p, q;
           rr_pair(round, i, mp, &p, &q);
           if (p > q) { int t = p; p = q; q = t; }
-          double c = 1.0, s = 0.0;
+          T c = 1, s = 0;
           if (q < m) {
-            double apq = A[(size_t)p * m + q];
-            double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
-            if (fabs(apq) > tiny && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-              double tau = (aqq - app) / (2.0 * apq);
-              double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-              c = 1.0 / sqrt(1.0 + t * t);
+            T apq = A[(size_t)p * m + q];
+            T app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+            if (apq != T(0) && fabs(apq) > T(0.01) * eps * sqrt(fabs(app * aqq))) {
+              T tau = (aqq - app) / (T(2) * apq);
+              T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+              c = T(1) / sqrt(T(1) + t * t);
               s = t * c;
             }
           } else {
@@ -215,17 +250,17 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double* Ag, double* w, doub
           cs[2 * i] = c;
           cs[2 * i + 1] = s;
           pq[2 * i] = p;
-          pq[2 * i + 1] = q;
+          pq[2 * i + 1] = (s == T(0)) ? -1 : q;
         }
         __syncthreads();
         // rows: A <- J^T A
         for (int t = threadIdx.x; t < npair * m; t += blockDim.x) {
           int i = t / m, j = t - (t / m) * m;
-          int p = pq[2 * i], q = pq[2 * i + 1];
+          int q = pq[2 * i + 1];
           if (q < 0) continue;
-          double c = cs[2 * i], s = cs[2 * i + 1];
-          if (s == 0.0) continue;
-          double ap = A[(size_t)p * m + j], aq = A[(size_t)q * m + j];
+          int p = pq[2 * i];
+          T c = cs[2 * i], s = cs[2 * i + 1];
+          T ap = A[(size_t)p * m + j], aq = A[(size_t)q * m + j];
           A[(size_t)p * m + j] = c * ap - s * aq;
           A[(size_t)q * m + j] = s * ap + c * aq;
         }
@@ -233,45 +268,36 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double* Ag, double* w, doub
         // columns: A <- A J, V <- V J
         for (int t = threadIdx.x; t < npair * m; t += blockDim.x) {
           int i = t / m, j = t - (t / m) * m;
-          int p = pq[2 * i], q = pq[2 * i + 1];
+          int q = pq[2 * i + 1];
           if (q < 0) continue;
-          double c = cs[2 * i], s = cs[2 * i + 1];
-          if (s == 0.0) continue;
-          double ap = A[(size_t)j * m + p], aq = A[(size_t)j * m + q];
+          int p = pq[2 * i];
+          T c = cs[2 * i], s = cs[2 * i + 1];
+          T ap = A[(size_t)j * m + p], aq = A[(size_t)j * m + q];
           A[(size_t)j * m + p] = c * ap - s * aq;
           A[(size_t)j * m + q] = s * ap + c * aq;
-          double vp = V[(size_t)j * m + p], vq = V[(size_t)j * m + q];
+          T vp = V[(size_t)j * m + p], vq = V[(size_t)j * m + q];
           V[(size_t)j * m + p] = c * vp - s * vq;
           V[(size_t)j * m + q] = s * vp + c * vq;
         }
         __syncthreads();
       }
-      // convergence: off-diagonal mass relative to ||A||_F
-      double off = 0.0;
+      T off = 0;
       for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
         int i = t / m, j = t - (t / m) * m;
         if (i != j) off += A[t] * A[t];
       }
-      for (int o = 16; o; o >>= 1) off += __shfl_xor_sync(0xffffffff, off, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-        red[33] = s;
-      }
-      __syncthreads();
-      const double offs = red[33];
-      __syncthreads();
-      if (offs <= (double)m * (double)m * 1e-30 * fro2) break;
+      off = block_sum(off, red);
+      // converged, or rounding has stopped the decrease (off-diagonal mass at the precision floor)
+      if (off <= tol2 || (off > T(0.25) * prev_off && off <= T(4096) * eps * eps * fro2)) break;
+      prev_off = off;
     }
   }
   // sort descending: rank[j] = position of eigenvalue j (ties by index)
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    double lj = A[(size_t)j * m + j];
+    T lj = A[(size_t)j * m + j];
     int pos = 0;
     for (int i = 0; i < m; ++i) {
-      double li = A[(size_t)i * m + i];
+      T li = A[(size_t)i * m + i];
       if (li > lj || (li == lj && i < j)) ++pos;
     }
     rank[j] = pos;
@@ -279,29 +305,96 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double* Ag, double* w, doub
   __syncthreads();
   double* wb = w + (size_t)blockIdx.x * m;
   double* Vb = Vout + (size_t)blockIdx.x * m * m;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) wb[rank[j]] = A[(size_t)j * m + j];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) wb[rank[j]] = (double)A[(size_t)j * m + j];
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
     int i = t / m, j = t - (t / m) * m;
-    Vb[(size_t)i * m + rank[j]] = V[t];
+    Vb[(size_t)i * m + rank[j]] = (double)V[t];
+  }
+}
+
+template <typename T>
+static void jacobi_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, int m, int batch) {
+  const int mp = m + (m & 1);
+  const int npair = mp / 2;
+  size_t head = sizeof(T) * 2 * npair + sizeof(int) * 2 * npair + sizeof(T) * 32 + sizeof(int) * (m + (m & 1));
+  head = (head + 15) / 16 * 16;
+  const size_t limit = (size_t)std::min(ctx->max_smem_optin, 220 * 1024);
+  const size_t one = head + sizeof(T) * (size_t)m * m, two = one + sizeof(T) * (size_t)m * m;
+  int use_smem = two <= limit ? 2 : (one <= limit ? 1 : 0);
+  size_t smem = use_smem == 2 ? two : (use_smem == 1 ? one : head);
+  DBuf<T> scratch;
+  if (use_smem == 1) scratch = DBuf<T>(ctx->pool, (size_t)m * m * batch);
+  if (use_smem == 0) scratch = DBuf<T>(ctx->pool, (size_t)2 * m * m * batch);
+  LRFG_CUDA(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const T eps = sizeof(T) == 4 ? (T)1.1920929e-07 : (T)2.220446049250313e-16;
+  // one sweep of the two-sided cyclic Jacobi costs about 9 m^3 flops (rows, columns and V)
+  LRFG_LAUNCH(ctx, KC_EIGEN, 9.0 * (double)m * m * m * batch, 3.0 * sizeof(double) * (double)m * m * batch,
+              jacobi_kernel<T><<<batch, kJacobiThreads, smem, ctx->stream>>>(A, w, V, m, scratch.get(), use_smem,
+                                                                              eps));
+}
+
+// Ogita–Aishima correction from G = X^T X and S = X^T A X (one block per matrix): writes lam and E.
+__global__ void __launch_bounds__(512) oa_correction_kernel(const double* __restrict__ Ag, const double* __restrict__ Gg,
+                                                            const double* __restrict__ Sg, double* lamg, double* Eg,
+                                                            int m) {
+  __shared__ double red[32];
+  const size_t off = (size_t)blockIdx.x * m * m;
+  const double* A = Ag + off;
+  const double* G = Gg + off;
+  const double* S = Sg + off;
+  double* E = Eg + off;
+  double* lam = lamg + (size_t)blockIdx.x * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = S[(size_t)i * m + i] / G[(size_t)i * m + i];
+  __syncthreads();
+  double a2 = 0.0, r2 = 0.0, s2 = 0.0;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, j = t - (t / m) * m;
+    double r = (i == j ? 1.0 : 0.0) - G[t];
+    double sd = (i == j) ? S[t] - lam[i] : S[t];
+    a2 += A[t] * A[t];
+    r2 += r * r;
+    s2 += sd * sd;
+  }
+  a2 = block_sum(a2, red);
+  r2 = block_sum(r2, red);
+  s2 = block_sum(s2, red);
+  const double delta = 2.0 * (sqrt(s2) + sqrt(a2) * sqrt(r2));
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    int i = t / m, j = t - (t / m) * m;
+    double r = (i == j ? 1.0 : 0.0) - G[t];
+    double e;
+    if (i == j) {
+      e = 0.5 * r;
+    } else {
+      double gap = lam[j] - lam[i];
+      e = (fabs(gap) > delta) ? (S[t] + lam[j] * r) / gap : 0.5 * r;
+    }
+    E[t] = e;
   }
 }
 
 void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
   if (m <= 0 || batch <= 0) return;
-  const int mp = m + (m & 1);
-  const int npair = mp / 2;
-  size_t head = sizeof(double) * 2 * npair + sizeof(int) * (2 * npair + ((2 * npair) & 1)) + sizeof(double) * 64 +
-                sizeof(int) * (m + (m & 1));
-  head = (head + 15) / 16 * 16;
-  size_t full = head + sizeof(double) * 2 * (size_t)m * m;
-  int use_smem = full <= (size_t)std::min(ctx->max_smem_optin, 200 * 1024) ? 1 : 0;
-  size_t smem = use_smem ? full : head;
-  DBuf<double> scratch;
-  if (!use_smem) scratch = DBuf<double>(ctx->pool, (size_t)2 * m * m * batch);
-  LRFG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // one sweep of the two-sided cyclic Jacobi costs about 9 m^3 flops (rows, columns and V)
-  LRFG_LAUNCH(ctx, KC_EIGEN, 9.0 * (double)m * m * m * batch, 3.0 * sizeof(double) * (double)m * m * batch,
-              jacobi_kernel<<<batch, 256, smem, ctx->stream>>>(A, w, V, m, scratch.get(), use_smem));
+  jacobi_launch<float>(ctx, A, w, V, m, batch);
+  if (m == 1) return;
+  const long long mm = (long long)m * m;
+  DBuf<double> G(ctx->pool, mm * batch), AV(ctx->pool, mm * batch), S(ctx->pool, mm * batch),
+      E(ctx->pool, mm * batch), Vn(ctx->pool, mm * batch);
+  for (int it = 0; it < 3; ++it) {
+    gemm(ctx, 1, 0, m, m, m, 1.0, V, m, mm, V, m, mm, 0.0, G.get(), m, mm, batch);
+    gemm(ctx, 0, 0, m, m, m, 1.0, A, m, mm, V, m, mm, 0.0, AV.get(), m, mm, batch);
+    gemm(ctx, 1, 0, m, m, m, 1.0, V, m, mm, AV.get(), m, mm, 0.0, S.get(), m, mm, batch);
+    LRFG_LAUNCH(ctx, KC_EIGEN, 8.0 * (double)mm * batch, 4.0 * sizeof(double) * mm * batch,
+                oa_correction_kernel<<<batch, 512, 0, ctx->stream>>>(A, G.get(), S.get(), w, E.get(), m));
+    LRFG_CUDA(cudaMemcpyAsync(Vn.get(), V, sizeof(double) * mm * batch, cudaMemcpyDeviceToDevice, ctx->stream));
+    gemm(ctx, 0, 0, m, m, m, 1.0, V, m, mm, E.get(), m, mm, 1.0, Vn.get(), m, mm, batch);
+    LRFG_CUDA(cudaMemcpyAsync(V, Vn.get(), sizeof(double) * mm * batch, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+}
+
+void syevj_fp64(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
+  if (m <= 0 || batch <= 0) return;
+  jacobi_launch<double>(ctx, A, w, V, m, batch);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -27,8 +27,10 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
           int batch = 1);
 // symmetric eigen-decomposition of `batch` m x m matrices (row-major, stride m*m): eigenvalues in
 // descending order into w (stride m), eigenvectors as the COLUMNS of V (row-major m x m, stride m*m).
-// A is destroyed.
+// A is left unchanged.  syevj: FP32 Jacobi + three FP64 Ogita–Aishima refinement steps (FP64 accuracy);
+// syevj_fp64: FP64 Jacobi throughout.
 void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
+void syevj_fp64(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
 // elementwise helpers
 void fill(lrfg_ctx* ctx, double* x, double v, long long n);
 void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y
