@@ -249,25 +249,37 @@ void mode_replace(lrfg_ctx* ctx, const TTView& v, int alpha, double scale, ModeR
 void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
   lrfg_ctx* ctx = P->ctx;
   const int r = P->opts.rank;
-  TT acc;
-  bool have = false;
-  for (int alpha = 0; alpha < P->d; ++alpha) {
-    ModeReplaced e;
-    mode_replace(ctx, v, alpha, 1.0, e);                       // gradient, mode alpha (rank kept)
-    TT h, w;
-    tt_hadamard(ctx, view_of(P->a_tt), e.view, h);             // A~ e_alpha (Khatri–Rao)
-    tt_round(ctx, view_of(h), r, w);                           // T
-    fibre_operator(ctx, w.core[alpha].get(), w.core[alpha].get(), w.r[alpha], w.N[alpha], w.r[alpha + 1],
-                   LRFG_MUL_DERIV, 0.0, -1.0);                 // divergence term, mode alpha
-    if (!have) {
-      acc = std::move(w);
-      have = true;
-    } else {
-      TT s;
-      tt_add(ctx, 1.0, nullptr, view_of(acc), 1.0, nullptr, view_of(w), s);
-      acc = std::move(s);
-    }
+  const int d = P->d;
+  const TTView a = view_of(P->a_tt);
+  // gradient carriages D_a v_a (rank kept; the other carriages are shared with v)
+  DBuf<double> grad[3];
+  for (int alpha = 0; alpha < d; ++alpha) {
+    grad[alpha] = DBuf<double>(ctx->pool, (size_t)v.r[alpha] * v.N[alpha] * v.r[alpha + 1]);
+    fibre_operator(ctx, v.core[alpha], grad[alpha].get(), v.r[alpha], v.N[alpha], v.r[alpha + 1], LRFG_MUL_DERIV,
+                   0.0, 1.0);
   }
+  // material products A~ e_a for all components at once (Khatri–Rao carriages), one batch of d TTs
+  int rk[4];
+  for (int j = 0; j <= d; ++j) rk[j] = a.r[j] * v.r[j];
+  TTBatch kr;
+  ttb_alloc(ctx, kr, d, v.N, rk, d);
+  for (int alpha = 0; alpha < d; ++alpha)
+    for (int j = 0; j < d; ++j)
+      khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1], (j == alpha) ? grad[j].get() : v.core[j], v.r[j],
+                 v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
+  for (auto& g : grad) g.reset();
+  TTBatch w;
+  tt_round_batch(ctx, batch_view(kr), r, w);                     // T, all components in one sweep
+  kr = TTBatch();
+  // divergence terms: -D_a on carriage a of component a, then the block sum over a
+  TTView terms[3];
+  for (int alpha = 0; alpha < d; ++alpha) {
+    terms[alpha] = item_view(w, alpha);
+    double* c = w.core[alpha].get() + (size_t)alpha * w.elems(alpha);
+    fibre_operator(ctx, c, c, w.r[alpha], w.N[alpha], w.r[alpha + 1], LRFG_MUL_DERIV, 0.0, -1.0);
+  }
+  TT acc;
+  tt_add_many(ctx, terms, nullptr, d, acc);
   TT sdiv;
   tt_round(ctx, view_of(acc), r, sdiv);                        // T after the sum
   tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out);        // T P~^-1

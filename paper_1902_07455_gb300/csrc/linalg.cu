@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(512) oa_correction_kernel(const double* __rest
   }
 }
 
-void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
+void syevj_mixed(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
   if (m <= 0 || batch <= 0) return;
   jacobi_launch<float>(ctx, A, w, V, m, batch);
   if (m == 1) return;
@@ -392,7 +392,7 @@ void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
   }
 }
 
-void syevj_fp64(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
+void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch) {
   if (m <= 0 || batch <= 0) return;
   jacobi_launch<double>(ctx, A, w, V, m, batch);
 }

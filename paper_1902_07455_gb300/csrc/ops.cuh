@@ -27,10 +27,11 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
           int batch = 1);
 // symmetric eigen-decomposition of `batch` m x m matrices (row-major, stride m*m): eigenvalues in
 // descending order into w (stride m), eigenvectors as the COLUMNS of V (row-major m x m, stride m*m).
-// A is left unchanged.  syevj: FP32 Jacobi + three FP64 Ogita–Aishima refinement steps (FP64 accuracy);
-// syevj_fp64: FP64 Jacobi throughout.
+// A is left unchanged.  syevj: FP64 Jacobi (absolute accuracy eps64 ||A||).  syevj_mixed: FP32 Jacobi +
+// three FP64 Ogita–Aishima refinement steps; its eigenvectors are accurate only for eigenvalues that
+// FP32 separates (gaps above ~1e-6 ||A||), so it serves the mixed-precision path, not the FP64 one.
 void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
-void syevj_fp64(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
+void syevj_mixed(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
 // elementwise helpers
 void fill(lrfg_ctx* ctx, double* x, double v, long long n);
 void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y
@@ -45,11 +46,35 @@ struct TTView {  // non-owning view of a TT with device carriages
   int r[4];
   const double* core[3];
 };
+// nb tensor trains of identical shape stored item after item in one buffer per carriage
+struct TTBatch {
+  int d = 0, nb = 0;
+  int N[3] = {0, 0, 0};
+  int r[4] = {1, 1, 1, 1};
+  DBuf<double> core[3];
+  size_t elems(int j) const { return (size_t)r[j] * N[j] * r[j + 1]; }
+};
+struct TTBatchView {
+  int d, nb;
+  int N[3];
+  int r[4];
+  const double* core[3];  // item b of carriage j at core[j] + b * elems(j)
+  size_t elems(int j) const { return (size_t)r[j] * N[j] * r[j + 1]; }
+};
+void ttb_alloc(lrfg_ctx* ctx, TTBatch& x, int d, const int* N, const int* r, int nb);
+TTBatchView batch_view(const TTBatch& x);
+TTView item_view(const TTBatch& x, int b);
+// rank truncation of every item of a batch (one batched Gram-SVD sweep)
+void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out);
 TTView view_of(const TT& x);
 TTView view_of(const lrfg_tt& x);
 void tt_alloc(lrfg_ctx* ctx, TT& x, int d, const int* N, const int* r);
 void tt_copy(lrfg_ctx* ctx, const TTView& src, TT& dst);
 void tt_hadamard(lrfg_ctx* ctx, const TTView& x, const TTView& y, TT& out);
+// Khatri–Rao product of one carriage pair into dst: (a c) x n x (b e)
+void khatri_rao(lrfg_ctx* ctx, const double* x, int a, int n, int b, const double* y, int c, int e, double* dst);
+// sum of nb TTs (views) in block form, each item scaled by scales[i] (on the first carriage)
+void tt_add_many(lrfg_ctx* ctx, const TTView* xs, const double* scales, int nb, TT& out);
 // out = alpha x + beta y; alpha_dev / beta_dev (may be null) are device scalars multiplying alpha/beta
 void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& x, double beta,
             const double* beta_dev, const TTView& y, TT& out);

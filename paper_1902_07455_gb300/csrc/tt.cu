@@ -70,6 +70,14 @@ __global__ void khatri_rao_kernel(const double* __restrict__ x, const double* __
   }
 }
 
+void khatri_rao(lrfg_ctx* ctx, const double* x, int a, int n, int b, const double* y, int c, int e, double* dst) {
+  long long total = (long long)a * c * n * b * e;
+  if (total == 0) return;
+  const double in_bytes = sizeof(double) * ((double)a * n * b + (double)c * n * e);
+  LRFG_LAUNCH(ctx, KC_KHATRI_RAO, (double)total, sizeof(double) * (double)total + in_bytes,
+              khatri_rao_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(x, y, dst, a, c, n, b, e));
+}
+
 void tt_hadamard(lrfg_ctx* ctx, const TTView& x, const TTView& y, TT& out) {
   LRFG_REQUIRE(x.d == y.d, "Hadamard of TTs of different order");
   int r[4];
@@ -107,6 +115,38 @@ static void embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double*
   if (total == 0) return;
   LRFG_LAUNCH(ctx, KC_TT_MISC, (double)total, 2.0 * sizeof(double) * total,
               block_embed_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(src, a, n, b, dst, A, B, oa, ob, s, s_dev));
+}
+
+void tt_add_many(lrfg_ctx* ctx, const TTView* xs, const double* scales, int nb, TT& out) {
+  LRFG_REQUIRE(nb >= 1, "empty sum");
+  const int d = xs[0].d;
+  int r[4];
+  r[0] = 1;
+  r[d] = 1;
+  for (int j = 1; j < d; ++j) {
+    r[j] = 0;
+    for (int i = 0; i < nb; ++i) r[j] += xs[i].r[j];
+  }
+  for (int i = 0; i < nb; ++i) {
+    LRFG_REQUIRE(xs[i].d == d, "sum of TTs of different order");
+    for (int j = 0; j < d; ++j) LRFG_REQUIRE(xs[i].N[j] == xs[0].N[j], "sum of TTs on different grids");
+  }
+  tt_alloc(ctx, out, d, xs[0].N, r);
+  for (int j = 0; j < d; ++j) {
+    double* dst = out.core[j].get();
+    const int A = r[j], B = r[j + 1], n = xs[0].N[j];
+    if (d > 1 && j != 0 && j != d - 1) fill(ctx, dst, 0.0, (long long)A * n * B);
+    int oa = 0, ob = 0;
+    for (int i = 0; i < nb; ++i) {
+      const TTView& x = xs[i];
+      if (d == 1) LRFG_REQUIRE(false, "use tt_add for order-1 tensors");
+      if (j == 0) embed(ctx, x.core[j], 1, n, x.r[1], dst, 1, B, 0, ob, scales ? scales[i] : 1.0, nullptr);
+      else if (j == d - 1) embed(ctx, x.core[j], x.r[j], n, 1, dst, A, 1, oa, 0, 1.0, nullptr);
+      else embed(ctx, x.core[j], x.r[j], n, x.r[j + 1], dst, A, B, oa, ob, 1.0, nullptr);
+      oa += x.r[j];
+      ob += x.r[j + 1];
+    }
+  }
 }
 
 void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& x, double beta, const double* beta_dev,
@@ -164,8 +204,11 @@ void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& 
 // leaves the tensor unchanged and equalises the two Gram diagonals (GA -> C GA C, R -> C^{-1} R C^{-1}).
 // It keeps the eigen-decompositions accurate when the columns of the left part and the rows of the
 // right part have very different scales (e.g. after Khatri–Rao products and exponential sums).
-__global__ void balance_kernel(double* GA, double* R, double* c, int m) {
+__global__ void balance_kernel(double* GAg, double* Rg, double* cg, int m) {
   extern __shared__ double cs[];
+  double* GA = GAg + (size_t)blockIdx.x * m * m;
+  double* R = Rg + (size_t)blockIdx.x * m * m;
+  double* c = cg + (size_t)blockIdx.x * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double ga = GA[(size_t)i * m + i], rb = R[(size_t)i * m + i];
     cs[i] = (ga > 0.0 && rb > 0.0) ? sqrt(sqrt(rb / ga)) : 1.0;
@@ -184,10 +227,17 @@ __global__ void balance_kernel(double* GA, double* R, double* c, int m) {
 //   RA[i][col]  = sqrt(lam_i) V[col][i]            (for S = RA R RA^T)
 //   RAc[i][col] = sqrt(lam_i) V[col][i] / c_col     (transfer, undoes the balancing)
 //   Pc[row][i]  = c_row V[row][i] / sqrt(lam_i)     (left factor, undoes the balancing)
-// Directions with lam <= tau lam_max are dropped (rows/columns set to 0).
-__global__ void sqrt_scale_rows_kernel(const double* __restrict__ lam, const double* __restrict__ V,
-                                       const double* __restrict__ c, double* RA, double* RAc, double* Pc, int m,
+// Directions with lam <= tau lam_max are dropped (rows/columns set to 0).  Batch index: blockIdx.y.
+__global__ void sqrt_scale_rows_kernel(const double* __restrict__ lamg, const double* __restrict__ Vg,
+                                       const double* __restrict__ cg, double* RAg, double* RAcg, double* Pcg, int m,
                                        double tau) {
+  const size_t mm = (size_t)m * m, bo = blockIdx.y;
+  const double* lam = lamg + bo * m;
+  const double* V = Vg + bo * mm;
+  const double* c = cg + bo * m;
+  double* RA = RAg + bo * mm;
+  double* RAc = RAcg + bo * mm;
+  double* Pc = Pcg + bo * mm;
   const double lmax = lam[0] > 0.0 ? lam[0] : 0.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
     int i = t / m, col = t - (t / m) * m;
@@ -201,11 +251,10 @@ __global__ void sqrt_scale_rows_kernel(const double* __restrict__ lam, const dou
   }
 }
 
-void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
+void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out) {
   LRFG_REQUIRE(rmax >= 1, "truncation rank must be >= 1 (got %d)", rmax);
-  const int d = x.d;
-  LRFG_REQUIRE(d >= 1 && d <= 3, "TT order must be 1..3");
-  if (d == 1) { tt_copy(ctx, x, out); return; }
+  const int d = x.d, nb = x.nb;
+  LRFG_REQUIRE(d >= 1 && d <= 3 && nb >= 1, "TT order must be 1..3");
   // ranks after the (implicit) right-to-left orthogonalisation and after truncation, as in TT rounding
   int sp[4], rr[4];
   sp[d] = 1;
@@ -213,59 +262,117 @@ void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
   rr[0] = 1;
   for (int j = 0; j < d - 1; ++j) rr[j + 1] = std::min(rmax, std::min(rr[j] * x.N[j], sp[j + 1]));
   rr[d] = 1;
-  tt_alloc(ctx, out, d, x.N, rr);
+  ttb_alloc(ctx, out, d, x.N, rr, nb);
+  if (d == 1) {
+    LRFG_CUDA(cudaMemcpyAsync(out.core[0].get(), x.core[0], sizeof(double) * x.elems(0) * nb,
+                              cudaMemcpyDeviceToDevice, ctx->stream));
+    return;
+  }
   const double tau = 1e-30;
 
-  // right Gram matrices R[j] (s_j x s_j) of the carriages j..d-1, j = 1..d-1
+  // right Gram matrices R[j] (s_j x s_j per batch item) of the carriages j..d-1, j = 1..d-1
   DBuf<double> R[4];
   {
     const int j = d - 1;
     const int s = x.r[j], n = x.N[j];
-    R[j] = DBuf<double>(ctx->pool, (size_t)s * s);
-    gemm(ctx, 0, 1, s, s, n, 1.0, x.core[j], n, 0, x.core[j], n, 0, 0.0, R[j].get(), s, 0);
+    const long long sx = (long long)x.elems(j), ss = (long long)s * s;
+    R[j] = DBuf<double>(ctx->pool, (size_t)ss * nb);
+    gemm(ctx, 0, 1, s, s, n, 1.0, x.core[j], n, sx, x.core[j], n, sx, 0.0, R[j].get(), s, ss, nb);
     for (int jj = d - 2; jj >= 1; --jj) {
       const int a = x.r[jj], nn = x.N[jj], b = x.r[jj + 1];
-      DBuf<double> T(ctx->pool, (size_t)a * nn * b);
-      gemm(ctx, 0, 0, a * nn, b, b, 1.0, x.core[jj], b, 0, R[jj + 1].get(), b, 0, 0.0, T.get(), b, 0);
-      R[jj] = DBuf<double>(ctx->pool, (size_t)a * a);
-      gemm(ctx, 0, 1, a, a, nn * b, 1.0, T.get(), nn * b, 0, x.core[jj], nn * b, 0, 0.0, R[jj].get(), a, 0);
+      const long long sxj = (long long)x.elems(jj), sb = (long long)b * b, sa = (long long)a * a;
+      DBuf<double> T(ctx->pool, (size_t)sxj * nb);
+      gemm(ctx, 0, 0, a * nn, b, b, 1.0, x.core[jj], b, sxj, R[jj + 1].get(), b, sb, 0.0, T.get(), b, sxj, nb);
+      R[jj] = DBuf<double>(ctx->pool, (size_t)sa * nb);
+      gemm(ctx, 0, 1, a, a, nn * b, 1.0, T.get(), nn * b, sxj, x.core[jj], nn * b, sxj, 0.0, R[jj].get(), a, sa, nb);
     }
   }
   // left sweep
-  DBuf<double> Z(ctx->pool, celems(x, 0));
-  LRFG_CUDA(cudaMemcpyAsync(Z.get(), x.core[0], sizeof(double) * celems(x, 0), cudaMemcpyDeviceToDevice, ctx->stream));
+  DBuf<double> Z(ctx->pool, x.elems(0) * nb);
+  LRFG_CUDA(cudaMemcpyAsync(Z.get(), x.core[0], sizeof(double) * x.elems(0) * nb, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
   for (int j = 0; j < d - 1; ++j) {
     const int a = rr[j], n = x.N[j], b = x.r[j + 1], k = rr[j + 1];
     const int rows = a * n;
-    DBuf<double> GA(ctx->pool, (size_t)b * b), lam(ctx->pool, b), VA(ctx->pool, (size_t)b * b);
-    DBuf<double> cb(ctx->pool, b);
-    gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, 0, Z.get(), b, 0, 0.0, GA.get(), b, 0);
-    LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * b * b, 4.0 * sizeof(double) * b * b,
-                balance_kernel<<<1, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
-    syevj(ctx, GA.get(), lam.get(), VA.get(), b);
-    DBuf<double> RA(ctx->pool, (size_t)b * b), RAc(ctx->pool, (size_t)b * b), Pc(ctx->pool, (size_t)b * b);
-    LRFG_LAUNCH(ctx, KC_TT_MISC, 4.0 * b * b, 4.0 * sizeof(double) * b * b,
-                sqrt_scale_rows_kernel<<<grid1d(ctx, (long long)b * b), 256, 0, ctx->stream>>>(
-                    lam.get(), VA.get(), cb.get(), RA.get(), RAc.get(), Pc.get(), b, tau));
+    const long long sz = (long long)rows * b, sbb = (long long)b * b, sout = (long long)out.elems(j);
+    DBuf<double> GA(ctx->pool, (size_t)sbb * nb), lam(ctx->pool, (size_t)b * nb), VA(ctx->pool, (size_t)sbb * nb);
+    DBuf<double> cb(ctx->pool, (size_t)b * nb);
+    gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, sz, Z.get(), b, sz, 0.0, GA.get(), b, sbb, nb);
+    LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
+                balance_kernel<<<nb, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
+    syevj(ctx, GA.get(), lam.get(), VA.get(), b, nb);
+    DBuf<double> RA(ctx->pool, (size_t)sbb * nb), RAc(ctx->pool, (size_t)sbb * nb), Pc(ctx->pool, (size_t)sbb * nb);
+    dim3 g2(std::max(1u, std::min(grid1d(ctx, sbb), 64u)), nb);
+    LRFG_LAUNCH(ctx, KC_TT_MISC, 4.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
+                sqrt_scale_rows_kernel<<<g2, 256, 0, ctx->stream>>>(lam.get(), VA.get(), cb.get(), RA.get(), RAc.get(),
+                                                                      Pc.get(), b, tau));
     // S = RA R RA^T (balanced)
-    DBuf<double> RAR(ctx->pool, (size_t)b * b), S(ctx->pool, (size_t)b * b);
-    gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, 0, R[j + 1].get(), b, 0, 0.0, RAR.get(), b, 0);
-    gemm(ctx, 0, 1, b, b, b, 1.0, RAR.get(), b, 0, RA.get(), b, 0, 0.0, S.get(), b, 0);
-    DBuf<double> sig(ctx->pool, b), US(ctx->pool, (size_t)b * b);
-    syevj(ctx, S.get(), sig.get(), US.get(), b);
+    DBuf<double> RAR(ctx->pool, (size_t)sbb * nb), S(ctx->pool, (size_t)sbb * nb);
+    gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, RAR.get(), b, sbb, nb);
+    gemm(ctx, 0, 1, b, b, b, 1.0, RAR.get(), b, sbb, RA.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
+    DBuf<double> sig(ctx->pool, (size_t)b * nb), US(ctx->pool, (size_t)sbb * nb);
+    syevj(ctx, S.get(), sig.get(), US.get(), b, nb);
     // P = Pc U_k (b x k), Y = M P, T = U_k^T RAc (k x b)
-    DBuf<double> P(ctx->pool, (size_t)b * k), T(ctx->pool, (size_t)k * b);
-    gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, 0, US.get(), b, 0, 0.0, P.get(), k, 0);
-    gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, 0, P.get(), k, 0, 0.0, out.core[j].get(), k, 0);
-    gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, 0, RAc.get(), b, 0, 0.0, T.get(), b, 0);
+    const long long sbk = (long long)b * k;
+    DBuf<double> P(ctx->pool, (size_t)sbk * nb), T(ctx->pool, (size_t)sbk * nb);
+    gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, sbb, US.get(), b, sbb, 0.0, P.get(), k, sbk, nb);
+    gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, sz, P.get(), k, sbk, 0.0, out.core[j].get(), k, sout, nb);
+    gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, sbb, RAc.get(), b, sbb, 0.0, T.get(), b, sbk, nb);
     // next left part: T (k x b) times carriage j+1 as b x (N s)
     const int n1 = x.N[j + 1], c1 = x.r[j + 2];
-    DBuf<double> Zn(ctx->pool, (size_t)k * n1 * c1);
-    gemm(ctx, 0, 0, k, n1 * c1, b, 1.0, T.get(), b, 0, x.core[j + 1], n1 * c1, 0, 0.0, Zn.get(), n1 * c1, 0);
+    const long long szn = (long long)k * n1 * c1;
+    DBuf<double> Zn(ctx->pool, (size_t)szn * nb);
+    gemm(ctx, 0, 0, k, n1 * c1, b, 1.0, T.get(), b, sbk, x.core[j + 1], n1 * c1, (long long)x.elems(j + 1), 0.0,
+         Zn.get(), n1 * c1, szn, nb);
     Z = std::move(Zn);
   }
-  LRFG_CUDA(cudaMemcpyAsync(out.core[d - 1].get(), Z.get(), sizeof(double) * (size_t)rr[d - 1] * x.N[d - 1],
+  LRFG_CUDA(cudaMemcpyAsync(out.core[d - 1].get(), Z.get(), sizeof(double) * out.elems(d - 1) * nb,
                             cudaMemcpyDeviceToDevice, ctx->stream));
+}
+
+void ttb_alloc(lrfg_ctx* ctx, TTBatch& x, int d, const int* N, const int* r, int nb) {
+  x.d = d;
+  x.nb = nb;
+  for (int j = 0; j < 3; ++j) x.N[j] = j < d ? N[j] : 0;
+  for (int j = 0; j < 4; ++j) x.r[j] = j <= d ? r[j] : 1;
+  x.r[0] = 1;
+  x.r[d] = 1;
+  for (int j = 0; j < d; ++j) x.core[j] = DBuf<double>(ctx->pool, x.elems(j) * nb);
+}
+
+TTBatchView batch_view(const TTBatch& x) {
+  TTBatchView v{};
+  v.d = x.d;
+  v.nb = x.nb;
+  for (int j = 0; j < 3; ++j) v.N[j] = x.N[j];
+  for (int j = 0; j < 4; ++j) v.r[j] = x.r[j];
+  for (int j = 0; j < x.d; ++j) v.core[j] = x.core[j].get();
+  return v;
+}
+
+TTView item_view(const TTBatch& x, int b) {
+  TTView v{};
+  v.d = x.d;
+  for (int j = 0; j < 3; ++j) v.N[j] = x.N[j];
+  for (int j = 0; j < 4; ++j) v.r[j] = x.r[j];
+  for (int j = 0; j < x.d; ++j) v.core[j] = x.core[j].get() + (size_t)b * x.elems(j);
+  return v;
+}
+
+void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
+  if (x.d == 1) { tt_copy(ctx, x, out); return; }
+  TTBatchView bv{};
+  bv.d = x.d;
+  bv.nb = 1;
+  for (int j = 0; j < 3; ++j) bv.N[j] = x.N[j];
+  for (int j = 0; j < 4; ++j) bv.r[j] = x.r[j];
+  for (int j = 0; j < x.d; ++j) bv.core[j] = x.core[j];
+  TTBatch ob;
+  tt_round_batch(ctx, bv, rmax, ob);
+  out.d = ob.d;
+  for (int j = 0; j < 3; ++j) out.N[j] = ob.N[j];
+  for (int j = 0; j < 4; ++j) out.r[j] = ob.r[j];
+  for (int j = 0; j < ob.d; ++j) out.core[j] = std::move(ob.core[j]);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -1,0 +1,61 @@
+"""Write stored oracle values for the full-size parity tests (calls only oracle/ and synthetic/).
+
+    python tests/golden/make_golden.py [--N 243] [--ranks 5 10]
+
+Workload: d = 3, N^3 grid, lognormal SE-GRF coefficient (l = 0.2, variance 1, seed 19020745) compressed
+by the oracle's TT-SVD to rank 10; the full-format reference solves the expansion of that TT coefficient
+(the comparison protocol of Sec. 4.1); E = (1, 0, 0).  Output: tests/golden/config2_lognormal_<N>.json with
+the full PCG A_eff (tolerance 1e-8), its iteration count, and the TT minimal-residual A_eff at each rank
+(exponential-sum accuracy 0.1, stop when the residual fails to decrease, at most 60 iterations).
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import fourier_galerkin as fg  # noqa: E402
+from oracle import lowrank as lr  # noqa: E402
+from synthetic import lognormal_grf  # noqa: E402
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--N", type=int, default=243)
+    p.add_argument("--ranks", type=int, nargs="*", default=[5, 10])
+    p.add_argument("--coeff-rank", type=int, default=10)
+    args = p.parse_args()
+    N = args.N
+    E = np.array([1.0, 0.0, 0.0])
+    A = lognormal_grf(3, N, ell=0.2, var=1.0, seed=19020745)
+    a_tt = lr.tt_svd(A, rmax=args.coeff_rank)
+    A_r = lr.tt_full(a_tt)
+    out = {"workload": f"d=3 N={N}^3 lognormal SE-GRF l=0.2 var=1 seed 19020745, coefficient TT rank "
+                       f"{args.coeff_rank} (oracle TT-SVD), E=(1,0,0)",
+           "coeff_ranks": lr.tt_ranks(a_tt), "coeff_mean": float(A_r.mean())}
+    t0 = time.time()
+    full = fg.solve_gani(A_r, E, tol=1e-8, maxit=2000)
+    out["full"] = {"Aeff": full["Aeff"], "iters": full["iters"], "rel_resid": full["rel_resid"],
+                   "seconds": time.time() - t0, "tol": 1e-8}
+    print("full", out["full"], flush=True)
+    out["tt"] = {}
+    for r in args.ranks:
+        t0 = time.time()
+        op = lr.LowRankGaNi(a_tt, (N, N, N), fmt="tt", rank=r, pinv_eps=0.1)
+        res = lr.minres(op, E, maxit=60)
+        out["tt"][str(r)] = {"Aeff": res["Aeff"], "iters": res["iters"], "rel_resid": res["rel_resid"],
+                             "seconds": time.time() - t0}
+        print("tt", r, out["tt"][str(r)], flush=True)
+    path = os.path.join(HERE, f"config2_lognormal_{N}.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path)
+
+
+if __name__ == "__main__":
+    main()
