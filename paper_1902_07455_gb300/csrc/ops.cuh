@@ -32,6 +32,13 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
 // FP32 separates (gaps above ~1e-6 ||A||), so it serves the mixed-precision path, not the FP64 one.
 void syevj(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
 void syevj_mixed(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batch = 1);
+// FP64 k largest eigenpairs by tridiagonalisation, bisection and inverse iteration: w[0..k) descending,
+// eigenvectors in the first k columns of V (n x n row-major per batch item).  A is left unchanged.
+void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch = 1);
+// Gram-SVD left factors from a balanced Gram matrix G (b x b per item) and the balancing c: pivoted
+// Cholesky; writes RA, RAc, Pc (b x b each per item) as the Gram-SVD needs them.
+void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
+                 double* Pc);
 // elementwise helpers
 void fill(lrfg_ctx* ctx, double* x, double v, long long n);
 void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y

@@ -1,0 +1,509 @@
+// FP64 symmetric eigensolver for the k largest eigenpairs (k = n: all of them), one block per matrix:
+//  1. Householder tridiagonalisation  Q^T A Q = T  (Golub & Van Loan, "Matrix Computations", 4th ed.,
+//     Alg. 8.3.1), reflectors kept in the columns below the diagonal;
+//  2. eigenvalues of T by bisection on Sturm counts of the LDL^T recurrence (G&VL Sec. 8.4.1);
+//  3. eigenvectors of T by inverse iteration (G&VL Sec. 8.2.2) with the tridiagonal LU factorisation
+//     of T - lambda I with partial pivoting (G&VL Sec. 4.3), three passes, vectors of eigenvalues closer
+//     than 1e-3 ||T|| re-orthogonalised against each other by modified Gram-Schmidt after each pass;
+//  4. back-transformation by the stored reflectors.
+// About 4/3 n^3 + 2 k n^2 flops against ~9 n^3 per sweep (and several sweeps) for cyclic Jacobi, with the
+// same absolute accuracy (eps ||A||), which is what the Gram-SVD truncation needs.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "ops.cuh"
+
+namespace lrfg {
+
+constexpr int kSyevxThreads = 512;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+  return v;
+}
+
+__device__ double block_reduce_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x: sign changes of the Sturm sequence
+// p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1} (Barth, Martin & Wilkinson, Numer. Math.
+// 9 (1967) 386-393), a zero term taking the sign opposite to its predecessor.  Division-free (FP64
+// division is a long dependent chain on this part); the pair (p_{i-1}, p_i) is rescaled by exact powers of
+// two to stay in range.
+__device__ int sturm_count(const double* d, const double* e2, int n, double x) {
+  const double up = 0x1p+600, down = 0x1p-600;
+  double pm = 1.0, p = d[0] - x;
+  int sprev = 1, c = 0;
+  int s = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
+  c += s != sprev;
+  sprev = s;
+  for (int i = 1; i < n; ++i) {
+    double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
+    pm = p;
+    p = pn;
+    if (fabs(p) > up) { p *= down; pm *= down; }
+    else if (fabs(p) < down && fabs(pm) < down) { p *= up; pm *= up; }
+    s = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
+    c += s != sprev;
+    sprev = s;
+  }
+  return c;
+}
+
+// LU with partial pivoting of the tridiagonal T - lam I (sub = super = e, diag d - lam).  Factors in
+// dl (multipliers), dd (diag of U), du (1st super), du2 (2nd super), piv (1 = rows i, i+1 swapped).
+__device__ void trid_factor(const double* d, const double* e, int n, double lam, double tiny, double* dl, double* dd,
+                            double* du, double* du2, int* piv) {
+  for (int i = 0; i < n; ++i) dd[i] = d[i] - lam;
+  for (int i = 0; i < n - 1; ++i) {
+    dl[i] = e[i];
+    du[i] = e[i];
+    du2[i] = 0.0;
+    piv[i] = 0;
+  }
+  for (int i = 0; i < n - 1; ++i) {
+    if (fabs(dd[i]) >= fabs(dl[i])) {
+      if (dd[i] == 0.0) dd[i] = tiny;
+      double f = dl[i] / dd[i];
+      dl[i] = f;
+      dd[i + 1] -= f * du[i];
+    } else {
+      double f = dd[i] / dl[i];
+      dd[i] = dl[i];
+      dl[i] = f;
+      double t = du[i];
+      du[i] = dd[i + 1];
+      dd[i + 1] = t - f * dd[i + 1];
+      if (i < n - 2) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
+      }
+      piv[i] = 1;
+    }
+  }
+  if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
+}
+
+__device__ void trid_solve(int n, const double* dl, const double* dd, const double* du, const double* du2,
+                           const int* piv, double* b) {
+  for (int i = 0; i < n - 1; ++i) {
+    if (!piv[i]) {
+      b[i + 1] -= dl[i] * b[i];
+    } else {
+      double t = b[i];
+      b[i] = b[i + 1];
+      b[i + 1] = t - dl[i] * b[i];
+    }
+  }
+  // back substitution, rescaling the computed tail when a term would overflow (the direction is what
+  // inverse iteration needs)
+  const double big = 1e150;
+  for (int i = n - 1; i >= 0; --i) {
+    double v = b[i];
+    if (i + 1 < n) v -= du[i] * b[i + 1];
+    if (i + 2 < n) v -= du2[i] * b[i + 2];
+    if (fabs(v) > big * fabs(dd[i])) {
+      for (int l = i + 1; l < n; ++l) b[l] *= 1e-150;
+      v *= 1e-150;
+    }
+    b[i] = v / dd[i];
+  }
+}
+
+// W: n x n work matrix (shared or global), Y: k vectors of length n (vector-major), lu: per-vector LU
+// scratch (4n doubles + n ints as doubles), all per block.
+__global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __restrict__ Ag, int n, int k, double* wg,
+                                                              double* Vg, int ldv, double* scratch, int use_smem) {
+  extern __shared__ __align__(16) double sm[];
+  double* red = sm;            // 32
+  double* d = red + 32;        // n
+  double* e = d + n;           // n
+  double* beta = e + n;        // n
+  double* pv = beta + n;       // n: p / w of the current reflector
+  double* vv = pv + n;         // n: current reflector v
+  double* e2 = vv + n;         // n: e^2 for the Sturm counts
+  double* lam = e2 + n;        // k
+  const size_t nn = (size_t)n * n;
+  const size_t per = nn + (size_t)k * n + (size_t)k * 5 * n;  // global scratch per block
+  double* gbase = scratch + (size_t)blockIdx.x * per;
+  double* W = use_smem ? (lam + k) : gbase;
+  double* Y = gbase + nn;
+  double* lu = Y + (size_t)k * n;
+  const double* A = Ag + (size_t)blockIdx.x * nn;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+
+  for (size_t t = tid; t < nn; t += nthr) W[t] = A[t];
+  __syncthreads();
+
+  // 1. tridiagonalisation
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    double x0 = W[(size_t)(j + 1) * n + j];
+    double loc = 0.0;
+    for (int i = tid; i < m; i += nthr) {
+      double xi = W[(size_t)(j + 1 + i) * n + j];
+      vv[i] = xi;
+      if (i > 0) loc += xi * xi;
+    }
+    const double tail2 = block_reduce_sum(loc, red);
+    if (tail2 == 0.0) {
+      if (tid == 0) {
+        d[j] = W[(size_t)j * n + j];
+        e[j] = x0;
+        beta[j] = 0.0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const double alpha = -copysign(sqrt(x0 * x0 + tail2), x0);
+    const double v0 = x0 - alpha;
+    const double b = 2.0 / (tail2 + v0 * v0);
+    if (tid == 0) {
+      vv[0] = v0;
+      d[j] = W[(size_t)j * n + j];
+      e[j] = alpha;
+      beta[j] = b;
+    }
+    __syncthreads();
+    // keep v in column j below the diagonal for the back-transformation
+    for (int i = tid; i < m; i += nthr) W[(size_t)(j + 1 + i) * n + j] = vv[i];
+    // p = b A22 v   (one warp per row block)
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int i = warp; i < m; i += nw) {
+      const double* row = W + (size_t)(j + 1 + i) * n + (j + 1);
+      double s = 0.0;
+      for (int l = lane; l < m; l += 32) s += row[l] * vv[l];
+      s = warp_sum(s);
+      if (lane == 0) pv[i] = b * s;
+    }
+    __syncthreads();
+    double kl = 0.0;
+    for (int i = tid; i < m; i += nthr) kl += vv[i] * pv[i];
+    const double K = 0.5 * b * block_reduce_sum(kl, red);
+    for (int i = tid; i < m; i += nthr) pv[i] -= K * vv[i];
+    __syncthreads();
+    // A22 -= v w^T + w v^T
+    for (size_t t = tid; t < (size_t)m * m; t += nthr) {
+      int i = (int)(t / m), l = (int)(t - (t / m) * m);
+      W[(size_t)(j + 1 + i) * n + (j + 1 + l)] -= vv[i] * pv[l] + pv[i] * vv[l];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = W[(size_t)(n - 2) * n + (n - 2)];
+      e[n - 2] = W[(size_t)(n - 1) * n + (n - 2)];
+      if (n >= 3) beta[n - 2] = 0.0;
+    }
+    d[n - 1] = W[(size_t)(n - 1) * n + (n - 1)];
+    e[n - 1] = 0.0;
+    beta[n - 1] = 0.0;
+  }
+  __syncthreads();
+
+  // 2. bisection for the k largest eigenvalues (thread t: the t-th largest)
+  double lo = d[0], hi = d[0], emax2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < n - 1) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  for (int i = tid; i < n; i += nthr) e2[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
+  __syncthreads();
+  if (tnorm == 0.0) {
+    // the zero matrix: eigenvalues 0, eigenvectors the unit vectors
+    double* w0 = wg + (size_t)blockIdx.x * n;
+    double* V0 = Vg + (size_t)blockIdx.x * (size_t)n * ldv;
+    for (int t = tid; t < k; t += nthr) w0[t] = 0.0;
+    for (size_t q = tid; q < (size_t)k * n; q += nthr) {
+      int t = (int)(q / n), i = (int)(q - (q / n) * n);
+      V0[(size_t)i * ldv + t] = (i == t) ? 1.0 : 0.0;
+    }
+    return;
+  }
+  for (int t = tid; t < k; t += nthr) {
+    const int idx = n - 1 - t;
+    double a = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, c = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (a + c);
+      if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 4.0 * pivmin) break;
+      if (sturm_count(d, e2, n, mid) > idx) c = mid; else a = mid;
+    }
+    lam[t] = 0.5 * (a + c);
+  }
+  __syncthreads();
+  // separate exactly equal eigenvalues slightly so that their factorisations differ
+  if (tid == 0) {
+    const double sep = 10.0 * DBL_EPSILON * tnorm;
+    for (int t = 1; t < k; ++t)
+      if (lam[t - 1] - lam[t] < sep) lam[t] = lam[t - 1] - sep;
+  }
+  __syncthreads();
+
+  // 3. inverse iteration, three passes with cluster re-orthogonalisation
+  const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+  for (int t = tid; t < k; t += nthr) {
+    double* y = Y + (size_t)t * n;
+    // deterministic start vector with entries in [0.5, 1.5)
+    unsigned h = 2166136261u ^ (unsigned)(t * 2654435761u);
+    for (int i = 0; i < n; ++i) {
+      h = h * 1664525u + 1013904223u;
+      y[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+    }
+    double* f = lu + (size_t)t * 5 * n;
+    trid_factor(d, e, n, lam[t], tiny, f, f + n, f + 2 * n, f + 3 * n, (int*)(f + 4 * n));
+  }
+  __syncthreads();
+  const double ortol = 1e-3 * tnorm;
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int t = tid; t < k; t += nthr) {
+      double* y = Y + (size_t)t * n;
+      const double* f = lu + (size_t)t * 5 * n;
+      trid_solve(n, f, f + n, f + 2 * n, f + 3 * n, (const int*)(f + 4 * n), y);
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) s += y[i] * y[i];
+      if (s > 0.0 && isfinite(s)) {
+        s = 1.0 / sqrt(s);
+        for (int i = 0; i < n; ++i) y[i] *= s;
+      } else {
+        // a breakdown (all-zero or overflowed solve): restart from a unit vector, the
+        // re-orthogonalisation and the next pass recover the direction
+        for (int i = 0; i < n; ++i) y[i] = (i == (t * 7 + pass) % n) ? 1.0 : 0.0;
+      }
+    }
+    __syncthreads();
+    // modified Gram-Schmidt within clusters, by warp 0, in descending order of the eigenvalues
+    if (tid < 32) {
+      for (int t = 1; t < k; ++t) {
+        double* yt = Y + (size_t)t * n;
+        bool touched = false;
+        for (int s = t - 1; s >= 0 && lam[s] - lam[t] <= ortol; --s) {
+          const double* ys = Y + (size_t)s * n;
+          double dp = 0.0;
+          for (int i = tid; i < n; i += 32) dp += ys[i] * yt[i];
+          dp = warp_sum(dp);
+          for (int i = tid; i < n; i += 32) yt[i] -= dp * ys[i];
+          touched = true;
+        }
+        if (touched) {
+          double s2 = 0.0;
+          for (int i = tid; i < n; i += 32) s2 += yt[i] * yt[i];
+          s2 = warp_sum(s2);
+          const double sc = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+          for (int i = tid; i < n; i += 32) yt[i] *= sc;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+
+  // 4. back-transformation x = H_0 H_1 ... H_{n-3} y (one warp per vector; the reflectors are read-only)
+  const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+  for (int t = warp; t < k; t += nw) {
+    double* yv = Y + (size_t)t * n;
+    for (int j = n - 3; j >= 0; --j) {
+      const double b = beta[j];
+      if (b == 0.0) continue;
+      const int m = n - j - 1;
+      double* y = yv + (j + 1);
+      double s = 0.0;
+      for (int i = lane; i < m; i += 32) s += W[(size_t)(j + 1 + i) * n + j] * y[i];
+      s = b * warp_sum(s);
+      for (int i = lane; i < m; i += 32) y[i] -= s * W[(size_t)(j + 1 + i) * n + j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // outputs: eigenvalues descending, eigenvectors as the first k columns of V (leading dimension ldv)
+  double* w = wg + (size_t)blockIdx.x * n;
+  double* V = Vg + (size_t)blockIdx.x * (size_t)n * ldv;
+  for (int t = tid; t < k; t += nthr) w[t] = lam[t];
+  for (size_t q = tid; q < (size_t)k * n; q += nthr) {
+    int t = (int)(q / n), i = (int)(q - (q / n) * n);
+    V[(size_t)i * ldv + t] = Y[(size_t)t * n + i];
+  }
+}
+
+void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch) {
+  if (n <= 0 || batch <= 0 || k <= 0) return;
+  k = std::min(k, n);
+  const size_t head = sizeof(double) * (32 + 6 * (size_t)n + k);
+  const size_t full = head + sizeof(double) * (size_t)n * n;
+  const int use_smem = full <= (size_t)std::min(ctx->max_smem_optin, 200 * 1024) ? 1 : 0;
+  const size_t smem = use_smem ? full : head;
+  const size_t per = (size_t)n * n + (size_t)k * n + (size_t)k * 5 * n;
+  DBuf<double> scratch(ctx->pool, per * batch);
+  LRFG_CUDA(cudaFuncSetAttribute(syevx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const double flops = (4.0 / 3.0 * n * (double)n * n + 4.0 * (double)k * n * n + 60.0 * k * n) * batch;
+  LRFG_LAUNCH(ctx, KC_EIGEN, flops, sizeof(double) * (2.0 * n * n + (double)k * n) * batch,
+              syevx_kernel<<<batch, kSyevxThreads, smem, ctx->stream>>>(A, n, k, w, V, n, scratch.get(), use_smem));
+}
+
+}  // namespace lrfg
+
+namespace lrfg {
+
+// ------------------------------------------------------------------------------------------------
+// Factor of a (balanced) Gram matrix for the Gram-SVD: pivoted Cholesky P^T G P = L L^T (Golub & Van
+// Loan Sec. 4.2, diagonal pivoting for semidefinite matrices), stopped when the largest remaining
+// pivot falls below tau = 1e-20 times the largest initial diagonal (numerical rank rho): those
+// directions have singular values below 1e-10 of the largest, where an FP64 Gram matrix no longer
+// determines them (an emulation of the truncation on exponential-sum outputs loses accuracy, 1e-9 ->
+// 4e-7, when pivots down to 1e-26 are kept).  Outputs, for the
+// orthonormal basis Q = M C P L11^{-T} of the left part M (C the balancing scaling):
+//   RA  (b x b): rows i < rho hold L^T P^T (so G = RA^T RA up to the dropped Schur complement),
+//   RAc (b x b): RA with column j divided by c_j (undoes the balancing in the transfer matrix),
+//   Pc  (b x b): Pc[perm[l]][q] = c[perm[l]] (L11^{-1})[q][l] for l, q < rho (so Q = M Pc).
+// One block per matrix; the working matrices are in shared memory when they fit.
+// ------------------------------------------------------------------------------------------------
+constexpr int kCholThreads = 512;
+
+__global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double* __restrict__ Gg,
+                                                                   const double* __restrict__ cg, int b, double tau,
+                                                                   double* RAg, double* RAcg, double* Pcg,
+                                                                   double* scratch, int use_smem) {
+  extern __shared__ __align__(16) double sm[];
+  double* redv = sm;                   // 32 values
+  int* redi = (int*)(redv + 32);       // 32 indices
+  int* perm = redi + 32;               // b
+  int* flag = perm + b;                // 2: rho, pivot
+  const size_t bb = (size_t)b * b;
+  double* W = use_smem ? (double*)(flag + 2 + ((b + 2) & 1) + 64) : scratch + (size_t)blockIdx.x * 2 * bb;
+  double* Li = W + bb;                 // L11^{-1}
+  const double* G = Gg + (size_t)blockIdx.x * bb;
+  const double* c = cg + (size_t)blockIdx.x * b;
+  double* RA = RAg + (size_t)blockIdx.x * bb;
+  double* RAc = RAcg + (size_t)blockIdx.x * bb;
+  double* Pc = Pcg + (size_t)blockIdx.x * bb;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  for (size_t t = tid; t < bb; t += nthr) W[t] = G[t];
+  for (int i = tid; i < b; i += nthr) perm[i] = i;
+  __syncthreads();
+  double md = 0.0;
+  for (int i = tid; i < b; i += nthr) md = fmax(md, W[(size_t)i * b + i]);
+  for (int o = 16; o; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffff, md, o));
+  if (lane == 0) redv[warp] = md;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < nw; ++i) m = fmax(m, redv[i]);
+    redv[31] = m;
+    flag[0] = b;
+  }
+  __syncthreads();
+  const double maxd0 = redv[31];
+  for (int k = 0; k < b; ++k) {
+    // pivot: largest remaining diagonal
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < b; i += nthr) {
+      double v = W[(size_t)i * b + i];
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffff, best, o);
+      int oi = __shfl_xor_sync(0xffffffff, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    __syncthreads();
+    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = -1.0;
+      int bx = k;
+      for (int i = 0; i < nw; ++i)
+        if (redv[i] > bv || (redv[i] == bv && redi[i] < bx)) { bv = redv[i]; bx = redi[i]; }
+      flag[1] = bx;
+      if (!(bv > tau * maxd0) || !(bv > 0.0)) flag[0] = k;
+    }
+    __syncthreads();
+    if (flag[0] == k) break;
+    const int p = flag[1];
+    if (p != k) {
+      // symmetric interchange of rows/columns k and p
+      for (int j = tid; j < b; j += nthr) {
+        double t = W[(size_t)k * b + j];
+        W[(size_t)k * b + j] = W[(size_t)p * b + j];
+        W[(size_t)p * b + j] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < b; i += nthr) {
+        double t = W[(size_t)i * b + k];
+        W[(size_t)i * b + k] = W[(size_t)i * b + p];
+        W[(size_t)i * b + p] = t;
+      }
+      if (tid == 0) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+      __syncthreads();
+    }
+    const double lkk = sqrt(W[(size_t)k * b + k]);
+    const double inv = 1.0 / lkk;
+    __syncthreads();
+    for (int i = k + 1 + tid; i < b; i += nthr) W[(size_t)i * b + k] *= inv;
+    if (tid == 0) W[(size_t)k * b + k] = lkk;
+    __syncthreads();
+    // Schur complement update of the whole trailing block (kept symmetric so that later interchanges
+    // can swap full rows and columns)
+    const int m = b - k - 1;
+    for (int i = warp; i < m; i += nw) {
+      const double li = W[(size_t)(k + 1 + i) * b + k];
+      for (int j = lane; j < m; j += 32)
+        W[(size_t)(k + 1 + i) * b + (k + 1 + j)] -= li * W[(size_t)(k + 1 + j) * b + k];
+    }
+    __syncthreads();
+  }
+  const int rho = flag[0];
+  // L11^{-1}: one thread per column q, forward substitution
+  for (int q = tid; q < rho; q += nthr) {
+    for (int i = 0; i < q; ++i) Li[(size_t)i * b + q] = 0.0;
+    for (int i = q; i < rho; ++i) {
+      double s = (i == q) ? 1.0 : 0.0;
+      for (int l = q; l < i; ++l) s -= W[(size_t)i * b + l] * Li[(size_t)l * b + q];
+      Li[(size_t)i * b + q] = s / W[(size_t)i * b + i];
+    }
+  }
+  __syncthreads();
+  // outputs
+  for (size_t t = tid; t < bb; t += nthr) {
+    int i = (int)(t / b), l = (int)(t - (t / b) * b);  // RA row i, permuted column l
+    double v = (i < rho && l >= i) ? W[(size_t)l * b + i] : 0.0;
+    int col = perm[l];
+    RA[(size_t)i * b + col] = v;
+    RAc[(size_t)i * b + col] = v / c[col];
+  }
+  for (size_t t = tid; t < bb; t += nthr) {
+    int l = (int)(t / b), q = (int)(t - (t / b) * b);  // Pc row perm[l], column q
+    double v = (l < rho && q < rho && q >= l) ? c[perm[l]] * Li[(size_t)q * b + l] : 0.0;
+    Pc[(size_t)perm[l] * b + q] = v;
+  }
+}
+
+void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
+                 double* Pc) {
+  if (b <= 0 || batch <= 0) return;
+  const size_t head = sizeof(double) * 32 + sizeof(int) * (32 + b + 2 + ((b + 2) & 1)) + sizeof(double) * 64;
+  const size_t full = head + sizeof(double) * 2 * (size_t)b * b;
+  const int use_smem = full <= (size_t)std::min(ctx->max_smem_optin, 220 * 1024) ? 1 : 0;
+  const size_t smem = use_smem ? full : head;
+  DBuf<double> scratch;
+  if (!use_smem) scratch = DBuf<double>(ctx->pool, (size_t)2 * b * b * batch);
+  LRFG_CUDA(cudaFuncSetAttribute(gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const double flops = (2.0 * b * (double)b * b / 3.0 + b * (double)b * b / 3.0) * batch;
+  LRFG_LAUNCH(ctx, KC_EIGEN, flops, sizeof(double) * 4.0 * b * b * batch,
+              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-20, RA, RAc, Pc,
+                                                                               scratch.get(), use_smem));
+}
+
+}  // namespace lrfg

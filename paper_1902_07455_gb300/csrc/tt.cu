@@ -295,23 +295,18 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
     const int a = rr[j], n = x.N[j], b = x.r[j + 1], k = rr[j + 1];
     const int rows = a * n;
     const long long sz = (long long)rows * b, sbb = (long long)b * b, sout = (long long)out.elems(j);
-    DBuf<double> GA(ctx->pool, (size_t)sbb * nb), lam(ctx->pool, (size_t)b * nb), VA(ctx->pool, (size_t)sbb * nb);
-    DBuf<double> cb(ctx->pool, (size_t)b * nb);
+    DBuf<double> GA(ctx->pool, (size_t)sbb * nb), cb(ctx->pool, (size_t)b * nb);
     gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, sz, Z.get(), b, sz, 0.0, GA.get(), b, sbb, nb);
     LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
                 balance_kernel<<<nb, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
-    syevj(ctx, GA.get(), lam.get(), VA.get(), b, nb);
     DBuf<double> RA(ctx->pool, (size_t)sbb * nb), RAc(ctx->pool, (size_t)sbb * nb), Pc(ctx->pool, (size_t)sbb * nb);
-    dim3 g2(std::max(1u, std::min(grid1d(ctx, sbb), 64u)), nb);
-    LRFG_LAUNCH(ctx, KC_TT_MISC, 4.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
-                sqrt_scale_rows_kernel<<<g2, 256, 0, ctx->stream>>>(lam.get(), VA.get(), cb.get(), RA.get(), RAc.get(),
-                                                                      Pc.get(), b, tau));
+    gram_factor(ctx, GA.get(), cb.get(), b, nb, RA.get(), RAc.get(), Pc.get());
     // S = RA R RA^T (balanced)
     DBuf<double> RAR(ctx->pool, (size_t)sbb * nb), S(ctx->pool, (size_t)sbb * nb);
     gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, RAR.get(), b, sbb, nb);
     gemm(ctx, 0, 1, b, b, b, 1.0, RAR.get(), b, sbb, RA.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
     DBuf<double> sig(ctx->pool, (size_t)b * nb), US(ctx->pool, (size_t)sbb * nb);
-    syevj(ctx, S.get(), sig.get(), US.get(), b, nb);
+    syevx(ctx, S.get(), sig.get(), US.get(), b, k, nb);
     // P = Pc U_k (b x k), Y = M P, T = U_k^T RAc (k x b)
     const long long sbk = (long long)b * k;
     DBuf<double> P(ctx->pool, (size_t)sbk * nb), T(ctx->pool, (size_t)sbk * nb);

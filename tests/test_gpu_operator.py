@@ -111,7 +111,11 @@ def test_tt_untruncated_equals_full(ctx):
                     stop_on_increase=False)
     res, u = P.solve(E)
     assert abs(res.Aeff - full["Aeff"]) <= 1e-9 * full["Aeff"]
-    assert rel(u.full(), np.real(fg.idft(full["uh"], d))) <= 1e-7
+    # the field is unique up to a constant: P~^-1 (unlike P^-1) does not vanish at k = 0, so rounding noise
+    # there can leave a tiny mean in the low-rank iterate; compare the zero-mean parts
+    g = u.full()
+    ref = np.real(fg.idft(full["uh"], d))
+    assert rel(g - g.mean(), ref - ref.mean()) <= 1e-7
 
 
 def test_full_coefficient_compressed_for_tt(ctx):
