@@ -190,10 +190,11 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
     const double K = 0.5 * b * block_reduce_sum(kl, red);
     for (int i = tid; i < m; i += nthr) pv[i] -= K * vv[i];
     __syncthreads();
-    // A22 -= v w^T + w v^T
-    for (size_t t = tid; t < (size_t)m * m; t += nthr) {
-      int i = (int)(t / m), l = (int)(t - (t / m) * m);
-      W[(size_t)(j + 1 + i) * n + (j + 1 + l)] -= vv[i] * pv[l] + pv[i] * vv[l];
+    // A22 -= v w^T + w v^T (one warp per row)
+    for (int i = warp; i < m; i += nw) {
+      double* row = W + (size_t)(j + 1 + i) * n + (j + 1);
+      const double vi = vv[i], wi = pv[i];
+      for (int l = lane; l < m; l += 32) row[l] -= vi * pv[l] + wi * vv[l];
     }
     __syncthreads();
   }
