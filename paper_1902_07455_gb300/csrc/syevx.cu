@@ -23,14 +23,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Block sum: warp partials, then warp 0 alone combines them (FP64 issue slots are scarce: 2 lanes/clk/SM)
 __device__ double block_reduce_sum(double v, double* red) {
   v = warp_sum(v);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;
+  if (threadIdx.x < 32) {
+    double s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 // Number of eigenvalues of the symmetric tridiagonal (d, e) below x: sign changes of the Sturm sequence
@@ -38,20 +43,52 @@ __device__ double block_reduce_sum(double v, double* red) {
 // 9 (1967) 386-393), a zero term taking the sign opposite to its predecessor.  Division-free (FP64
 // division is a long dependent chain on this part); the pair (p_{i-1}, p_i) is rescaled by exact powers of
 // two to stay in range.
+__device__ __forceinline__ int sign_of(double p, int sprev) {
+  // sign from the bit pattern (integer pipe): +1, -1, or opposite of the predecessor for a zero
+  const long long bits = __double_as_longlong(p);
+  if ((bits & 0x7fffffffffffffffLL) == 0) return -sprev;
+  return bits < 0 ? -1 : 1;
+}
+
 __device__ int sturm_count(const double* d, const double* e2, int n, double x) {
   const double up = 0x1p+600, down = 0x1p-600;
   double pm = 1.0, p = d[0] - x;
   int sprev = 1, c = 0;
-  int s = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
+  int s = sign_of(p, sprev);
   c += s != sprev;
   sprev = s;
   for (int i = 1; i < n; ++i) {
     double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
     pm = p;
     p = pn;
-    if (fabs(p) > up) { p *= down; pm *= down; }
-    else if (fabs(p) < down && fabs(pm) < down) { p *= up; pm *= up; }
-    s = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
+    // biased exponents of |p| and |pm| (integer pipe) for the range checks against 2^(+-600)
+    const int ep = (int)((__double_as_longlong(p) >> 52) & 0x7ff), epm = (int)((__double_as_longlong(pm) >> 52) & 0x7ff);
+    if (ep > 1023 + 600) { p *= down; pm *= down; }
+    else if (ep < 1023 - 600 && epm < 1023 - 600) { p *= up; pm *= up; }
+    s = sign_of(p, sprev);
+    c += s != sprev;
+    sprev = s;
+  }
+  return c;
+}
+
+// The same count in FP32 (rescaling by 2^(+-60)), used only to localise eigenvalues before the FP64
+// multisection; its brackets are verified with FP64 counts.
+__device__ int sturm_count_f32(const float* d, const float* e2, int n, float x) {
+  const float up = 0x1p+60f, down = 0x1p-60f;
+  float pm = 1.0f, p = d[0] - x;
+  int sprev = 1, c = 0;
+  int s = (__float_as_int(p) & 0x7fffffff) == 0 ? -sprev : (__float_as_int(p) < 0 ? -1 : 1);
+  c += s != sprev;
+  sprev = s;
+  for (int i = 1; i < n; ++i) {
+    float pn = fmaf(d[i] - x, p, -e2[i - 1] * pm);
+    pm = p;
+    p = pn;
+    const int ep = (__float_as_int(p) >> 23) & 0xff, epm = (__float_as_int(pm) >> 23) & 0xff;
+    if (ep > 127 + 60) { p *= down; pm *= down; }
+    else if (ep < 127 - 60 && epm < 127 - 60) { p *= up; pm *= up; }
+    s = (__float_as_int(p) & 0x7fffffff) == 0 ? -sprev : (__float_as_int(p) < 0 ? -1 : 1);
     c += s != sprev;
     sprev = s;
   }
@@ -59,7 +96,8 @@ __device__ int sturm_count(const double* d, const double* e2, int n, double x) {
 }
 
 // LU with partial pivoting of the tridiagonal T - lam I (sub = super = e, diag d - lam).  Factors in
-// dl (multipliers), dd (diag of U), du (1st super), du2 (2nd super), piv (1 = rows i, i+1 swapped).
+// dl (multipliers), dd (reciprocals of the diagonal of U), du (1st super), du2 (2nd super), piv (1 = rows
+// i, i+1 swapped).
 __device__ void trid_factor(const double* d, const double* e, int n, double lam, double tiny, double* dl, double* dd,
                             double* du, double* du2, int* piv) {
   for (int i = 0; i < n; ++i) dd[i] = d[i] - lam;
@@ -90,6 +128,7 @@ __device__ void trid_factor(const double* d, const double* e, int n, double lam,
     }
   }
   if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
+  for (int i = 0; i < n; ++i) dd[i] = 1.0 / dd[i];  // the solves multiply by the reciprocal pivots
 }
 
 __device__ void trid_solve(int n, const double* dl, const double* dd, const double* du, const double* du2,
@@ -110,11 +149,12 @@ __device__ void trid_solve(int n, const double* dl, const double* dd, const doub
     double v = b[i];
     if (i + 1 < n) v -= du[i] * b[i + 1];
     if (i + 2 < n) v -= du2[i] * b[i + 2];
-    if (fabs(v) > big * fabs(dd[i])) {
+    double y = v * dd[i];
+    if (fabs(y) > big) {
       for (int l = i + 1; l < n; ++l) b[l] *= 1e-150;
-      v *= 1e-150;
+      y *= 1e-150;
     }
-    b[i] = v / dd[i];
+    b[i] = y;
   }
 }
 
@@ -123,8 +163,8 @@ __device__ void trid_solve(int n, const double* dl, const double* dd, const doub
 __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __restrict__ Ag, int n, int k, double* wg,
                                                               double* Vg, int ldv, double* scratch, int use_smem) {
   extern __shared__ __align__(16) double sm[];
-  double* red = sm;            // 32
-  double* d = red + 32;        // n
+  double* red = sm;            // 33 (32 partials + the result) + padding
+  double* d = red + 40;        // n
   double* e = d + n;           // n
   double* beta = e + n;        // n
   double* pv = beta + n;       // n: p / w of the current reflector
@@ -134,7 +174,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   const size_t nn = (size_t)n * n;
   const size_t per = nn + (size_t)k * n + (size_t)k * 5 * n;  // global scratch per block
   double* gbase = scratch + (size_t)blockIdx.x * per;
-  double* W = use_smem ? (lam + k) : gbase;
+  double* W = use_smem ? (lam + k + n) : gbase;  // after lam and the FP32 copies (2n floats = n doubles)
   double* Y = gbase + nn;
   double* lu = Y + (size_t)k * n;
   const double* A = Ag + (size_t)blockIdx.x * nn;
@@ -175,15 +215,23 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
     __syncthreads();
     // keep v in column j below the diagonal for the back-transformation
     for (int i = tid; i < m; i += nthr) W[(size_t)(j + 1 + i) * n + j] = vv[i];
-    // p = b A22 v   (one warp per row block)
-    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-    for (int i = warp; i < m; i += nw) {
-      const double* row = W + (size_t)(j + 1 + i) * n + (j + 1);
-      double s = 0.0;
-      for (int l = lane; l < m; l += 32) s += row[l] * vv[l];
-      s = warp_sum(s);
-      if (lane == 0) pv[i] = b * s;
+    // p = b A22 v: thread i takes row i, reading column i of the symmetric trailing block so that
+    // neighbouring threads read neighbouring words (no warp reductions, which cost FP64 issue slots)
+    for (int i = tid; i < m; i += nthr) {
+      const double* col = W + (size_t)(j + 1) * n + (j + 1 + i);
+      // four independent accumulators: an FP64 FMA has a 64-cycle latency on this part
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int l = 0;
+      for (; l + 3 < m; l += 4) {
+        s0 = fma(col[(size_t)l * n], vv[l], s0);
+        s1 = fma(col[(size_t)(l + 1) * n], vv[l + 1], s1);
+        s2 = fma(col[(size_t)(l + 2) * n], vv[l + 2], s2);
+        s3 = fma(col[(size_t)(l + 3) * n], vv[l + 3], s3);
+      }
+      for (; l < m; ++l) s0 = fma(col[(size_t)l * n], vv[l], s0);
+      pv[i] = b * ((s0 + s1) + (s2 + s3));
     }
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
     __syncthreads();
     double kl = 0.0;
     for (int i = tid; i < m; i += nthr) kl += vv[i] * pv[i];
@@ -233,12 +281,39 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
     }
     return;
   }
+  // (a) FP32 localisation: 24 halvings of the Gershgorin interval, one thread per eigenvalue
+  float* df = (float*)(lam + k);       // n floats (overlaps nothing: W starts after these when in smem)
+  float* e2f = df + n;                 // n floats
+  for (int i = tid; i < n; i += nthr) {
+    df[i] = (float)d[i];
+    e2f[i] = (float)e2[i];
+  }
+  __syncthreads();
+  double* bra = pv;  // reuse: bracket lower ends for the k eigenvalues (pv, vv are free now)
+  double* brc = vv;  // bracket upper ends
+  const double glo = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, ghi = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
   for (int t = tid; t < k; t += nthr) {
     const int idx = n - 1 - t;
-    double a = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, c = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
+    float a = (float)glo, c = (float)ghi;
+    for (int it = 0; it < 24; ++it) {
+      float mid = 0.5f * (a + c);
+      if (!(mid > a && mid < c)) break;
+      if (sturm_count_f32(df, e2f, n, mid) > idx) c = mid; else a = mid;
+    }
+    const double w = (double)c - (double)a;
+    bra[t] = fmax(glo, (double)a - 4.0 * w - 1e-6 * tnorm);
+    brc[t] = fmin(ghi, (double)c + 4.0 * w + 1e-6 * tnorm);
+  }
+  __syncthreads();
+  // (b) FP64: verify each bracket with FP64 counts (fall back to the Gershgorin interval), then bisect to
+  // the FP64 resolution, one thread per eigenvalue (about 30 halvings remain after the FP32 phase)
+  for (int t = tid; t < k; t += nthr) {
+    const int idx = n - 1 - t;
+    double a = bra[t], c = brc[t];
+    if (!(sturm_count(d, e2, n, a) <= idx && sturm_count(d, e2, n, c) > idx)) { a = glo; c = ghi; }
     for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (a + c);
-      if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 4.0 * pivmin) break;
+      if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 1e-3 * DBL_EPSILON * tnorm + 4.0 * pivmin) break;
+      const double mid = 0.5 * (a + c);
       if (sturm_count(d, e2, n, mid) > idx) c = mid; else a = mid;
     }
     lam[t] = 0.5 * (a + c);
@@ -341,7 +416,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
 void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch) {
   if (n <= 0 || batch <= 0 || k <= 0) return;
   k = std::min(k, n);
-  const size_t head = sizeof(double) * (32 + 6 * (size_t)n + k);
+  const size_t head = sizeof(double) * (40 + 7 * (size_t)n + k);
   const size_t full = head + sizeof(double) * (size_t)n * n;
   const int use_smem = full <= (size_t)std::min(ctx->max_smem_optin, 200 * 1024) ? 1 : 0;
   const size_t smem = use_smem ? full : head;
