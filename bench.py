@@ -144,6 +144,20 @@ FP64_PEAK_TFLOPS = 152 * 2.070 * 4 / 1e3
 ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen"}
 
 
+def class_rooflines(stats, classes):
+    """Achieved HBM bandwidth of memory-bound kernel classes against the measured copy peak."""
+    peaks, src = measured_peaks()
+    out = {}
+    for k in classes:
+        v = stats.get(k)
+        if not v or not v["launches"] or v["ms"] <= 0:
+            continue
+        gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+        out[k] = {"achieved_gbs": round(gbs, 1), "frac": round(gbs / float(peaks["hbm_gbs"]), 3),
+                  "launches": v["launches"], "ms": round(v["ms"], 3)}
+    return out
+
+
 def roofline(stats):
     peaks, src = measured_peaks()
     dom = max(stats, key=lambda k: stats[k]["ms"])
@@ -231,6 +245,29 @@ def run_ours(args):
         Pfull.apply_into(f_in, f_out)
     torch.cuda.synchronize()
     full_apply_s = (time.perf_counter() - t0) / 5
+    # the same solve with LRFG_MIXED: FP32 storage and FFTs, FP64 scalars, to a 1e-5 residual
+    Pmix = ctx.problem(a_full, lrfg.FULL, tol=1e-5, maxit=2000, prec=lrfg.MIXED)
+    mix_res, _ = Pmix.solve(E, want_field=False)
+    mix_times = []
+    for _ in range(2):
+        r, _ = Pmix.solve(E, want_field=False)
+        mix_times.append(r.seconds)
+    Pmix.apply_into(f_in, f_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        Pmix.apply_into(f_in, f_out)
+    torch.cuda.synchronize()
+    mix_apply_s = (time.perf_counter() - t0) / 5
+    # per-class HBM rooflines of one solve in each precision
+    full_classes = ["r2c_rows", "c2r_rows", "fft_fibres", "pointwise", "reduce"]
+    full_roof = {}
+    for name, P in (("f64", Pfull), ("mixed", Pmix)):
+        ctx.profile_reset()
+        ctx.profile(True)
+        P.solve(E, want_field=False)
+        ctx.profile(False)
+        full_roof[name] = class_rooflines(ctx.profile_read(), full_classes)
     f_in.free()
     f_out.free()
 
@@ -303,6 +340,10 @@ def run_ours(args):
             "meets_1e-6": rel_err <= 1e-6,
             "full_solves_per_s": 1.0 / statistics.median(full_times), "full_iters": full_res.iters,
             "full_op_applies_per_s": 1.0 / full_apply_s,
+            "full_mixed": {"solves_per_s": 1.0 / statistics.median(mix_times), "iters": mix_res.iters,
+                           "op_applies_per_s": 1.0 / mix_apply_s, "tol": 1e-5, "aeff": mix_res.Aeff,
+                           "aeff_rel_err_vs_f64": abs(mix_res.Aeff - full_res.Aeff) / full_res.Aeff},
+            "full_class_rooflines": full_roof,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "coeff_ranks": Ptt.coeff_ranks(),
             "e2e": {"value": 1e3 / statistics.median(e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -315,6 +356,7 @@ def run_ours(args):
         }
     Ptt.free()
     Pfull.free()
+    Pmix.free()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

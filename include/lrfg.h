@@ -26,7 +26,11 @@
  *     (A_eff, dots, solve results) synchronise that stream, the others are asynchronous;
  *   - one context per host thread; a context is not thread-safe;
  *   - LRFG_ENOMEM means the context's HBM budget (or the device) cannot hold the request.
- * Arithmetic: FP64 throughout (LRFG_FP64).  LRFG_MIXED is reserved and returns LRFG_ENOTSUP.
+ * Arithmetic: FP64 throughout (LRFG_FP64).  LRFG_MIXED (LRFG_FULL solutions only; LRFG_ENOTSUP for
+ * LRFG_TT) stores the PCG vectors, the coefficient and the FFT work in FP32 and keeps every inner
+ * product, step length, residual test and the A_eff evaluation in FP64; the solution field it hands
+ * out is FP64.  It is an extension of the paper's FP64 method (the paper fixes no precision), for
+ * tolerances down to about 1e-5.
  */
 #ifndef LRFG_H
 #define LRFG_H
@@ -81,7 +85,7 @@ typedef struct {
 
 typedef struct {
   lrfg_format fmt;      /* solution format: LRFG_FULL (PCG) or LRFG_TT (minimal residual) */
-  lrfg_prec prec;       /* LRFG_FP64 */
+  lrfg_prec prec;       /* LRFG_FP64, or LRFG_MIXED with fmt == LRFG_FULL */
   int rank;             /* LRFG_TT: the fixed rank of every truncation T (Sec. 4.2) */
   double pinv_eps;      /* LRFG_TT: relative accuracy of the exponential-sum P~^-1 on [1, max k.k]
                            (0 selects 0.1) */

@@ -22,10 +22,11 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Context", "TTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "MUL_IDENTITY", "MUL_DERIV",
+__all__ = ["Context", "TTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
            "MUL_GAUSS", "library_path"]
 
 FULL, TT = L.LRFG_FULL, L.LRFG_TT
+FP64, MIXED = L.LRFG_FP64, L.LRFG_MIXED
 MUL_IDENTITY, MUL_DERIV, MUL_GAUSS = L.LRFG_MUL_IDENTITY, L.LRFG_MUL_DERIV, L.LRFG_MUL_GAUSS
 
 
@@ -282,8 +283,9 @@ class Context:
 
     # ---- problems and fields ---------------------------------------------------------------------
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
-                stop_on_increase: bool = True) -> "Problem":
-        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase)
+                stop_on_increase: bool = True, prec: int = L.LRFG_FP64) -> "Problem":
+        """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only)."""
+        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -373,7 +375,7 @@ class Problem:
     """Resident coefficient + operator + solver for one format.  ``coeff``: a numpy/torch grid array
     (isotropic a(x) samples) or a TTensor of the coefficient."""
 
-    def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase):
+    def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -405,7 +407,7 @@ class Problem:
                 c.N[j] = int(n)
             c.fmt = L.LRFG_FULL
         o = L.lrfg_opts()
-        o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), L.LRFG_FP64, int(rank), float(pinv_eps)
+        o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         h = C.c_void_p()
         ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))

@@ -10,7 +10,9 @@
 //    Fourier-space form, with real carriages.  The minimal-residual iteration of Sec. 3.3 runs on it.
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 #include <cstdarg>
+#include <cstdlib>
 #include <new>
 #include <vector>
 
@@ -41,6 +43,11 @@ static size_t rounded(size_t bytes) {
   return (bytes + g - 1) / g * g;
 }
 
+DevicePool::DevicePool(size_t budget) : budget_(budget) {
+  const char* v = std::getenv("LRFG_POOL_POISON");
+  poison_ = v && v[0] == '1';
+}
+
 void* DevicePool::alloc(size_t bytes) {
   size_t sz = rounded(bytes);
   auto& lst = sized_[sz];
@@ -68,6 +75,11 @@ void* DevicePool::alloc(size_t bytes) {
   }
   live_size_[p] = sz;
   in_use_ += sz;
+  if (poison_) {
+    cudaDeviceSynchronize();
+    cudaMemset(p, 0xff, sz);
+    cudaDeviceSynchronize();
+  }
   return p;
 }
 
@@ -147,6 +159,10 @@ struct lrfg_problem {
   FullGrid g{};
   DBuf<double2> wc;          // FULL workspace: one half spectrum
   DBuf<double> wr;           // FULL workspace: one real grid
+  // LRFG_MIXED (FULL only): FP32 copies of the coefficient and FP32 workspaces
+  DBuf<float> a_full_f;
+  DBuf<float2> wcf;
+  DBuf<float> wrf;
 };
 
 namespace {
@@ -332,24 +348,43 @@ double lr_aeff(lrfg_problem* P, const double* E, const TTView& u) {
 
 // ---- FULL operator pieces ---------------------------------------------------------------------
 
-void full_apply(lrfg_problem* P, const double2* v, double2* out, int precond) {
+// storage of the FULL operator in precision R: coefficient and workspaces
+template <typename R> struct FullWork;
+template <> struct FullWork<double> {
+  const double* a; double2* wc; double* wr;
+  explicit FullWork(lrfg_problem* P) : a(P->a_full.get()), wc(P->wc.get()), wr(P->wr.get()) {}
+};
+template <> struct FullWork<float> {
+  const float* a; float2* wc; float* wr;
+  explicit FullWork(lrfg_problem* P) : a(P->a_full_f.get()), wc(P->wcf.get()), wr(P->wrf.get()) {
+    LRFG_REQUIRE(a && wc && wr, "FP32 workspaces exist only for LRFG_MIXED problems");
+  }
+};
+
+template <typename R>
+void full_apply(lrfg_problem* P, const typename CplxOf<R>::T* v, typename CplxOf<R>::T* out, int precond) {
   lrfg_ctx* ctx = P->ctx;
   const FullGrid& g = P->g;
+  FullWork<R> w(P);
   const double inv = 1.0 / (double)g.n_real;
   for (int alpha = 0; alpha < g.d; ++alpha) {
-    half_mul_grad(ctx, g, v, P->wc.get(), alpha, inv);                   // grad^, with 1/|N| of Phi^-1
-    full_inverse(ctx, g, P->wc.get(), P->a_full.get(), 1.0, P->wr.get()); // A~ F^-1 grad^ v
-    full_forward(ctx, g, P->wr.get(), nullptr, 1.0, P->wc.get());        // F
-    half_acc_div(ctx, g, P->wc.get(), out, alpha, 1.0, alpha == 0, precond && alpha == g.d - 1);  // grad^*
+    half_mul_grad(ctx, g, v, w.wc, alpha, inv);             // grad^, with 1/|N| of Phi^-1
+    full_inverse<R>(ctx, g, w.wc, w.a, R(1), w.wr);         // A~ F^-1 grad^ v
+    full_forward<R>(ctx, g, w.wr, nullptr, R(1), w.wc);     // F
+    half_acc_div(ctx, g, (const typename CplxOf<R>::T*)w.wc, out, alpha, 1.0, alpha == 0,
+                 precond && alpha == g.d - 1);              // grad^*
   }
 }
 
-void full_rhs(lrfg_problem* P, const double* E, double2* b, int precond) {
+template <typename R>
+void full_rhs(lrfg_problem* P, const double* E, typename CplxOf<R>::T* b, int precond) {
   lrfg_ctx* ctx = P->ctx;
   const FullGrid& g = P->g;
-  full_forward(ctx, g, P->a_full.get(), nullptr, 1.0, P->wc.get());
+  FullWork<R> w(P);
+  full_forward<R>(ctx, g, w.a, nullptr, R(1), w.wc);
   for (int alpha = 0; alpha < g.d; ++alpha)
-    half_acc_div(ctx, g, P->wc.get(), b, alpha, -E[alpha], alpha == 0, precond && alpha == g.d - 1);
+    half_acc_div(ctx, g, (const typename CplxOf<R>::T*)w.wc, b, alpha, -E[alpha], alpha == 0,
+                 precond && alpha == g.d - 1);
 }
 
 double full_aeff(lrfg_problem* P, const double* E, const double2* v) {
@@ -358,8 +393,8 @@ double full_aeff(lrfg_problem* P, const double* E, const double2* v) {
   DBuf<double> acc(ctx->pool, 1);
   for (int alpha = 0; alpha < g.d; ++alpha) {
     half_mul_grad(ctx, g, v, P->wc.get(), alpha, 1.0 / (double)g.n_real);
-    full_inverse(ctx, g, P->wc.get(), nullptr, 1.0, P->wr.get());
-    energy_sum(ctx, g, P->wr.get(), P->a_full.get(), E[alpha], acc.get(), alpha > 0);
+    full_inverse<double>(ctx, g, P->wc.get(), nullptr, 1.0, P->wr.get());
+    energy_sum(ctx, g, (const double*)P->wr.get(), P->a_full.get(), E[alpha], acc.get(), alpha > 0);
   }
   double h = 0.0;
   LRFG_CUDA(cudaMemcpyAsync(&h, acc.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -394,7 +429,15 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
   check_field(P, in);
   if (P->opts.fmt == LRFG_FULL) {
     if (!out->half.get()) out->half = DBuf<double2>(P->ctx->pool, P->g.n_half);
-    full_apply(P, in->half.get(), out->half.get(), 1);
+    if (P->opts.prec == LRFG_MIXED) {
+      // FP32 operator between FP64 fields
+      DBuf<float2> xi(P->ctx->pool, P->g.n_half), xo(P->ctx->pool, P->g.n_half);
+      convert(P->ctx, (const double2*)in->half.get(), xi.get(), P->g.n_half);
+      full_apply<float>(P, xi.get(), xo.get(), 1);
+      convert(P->ctx, (const float2*)xo.get(), out->half.get(), P->g.n_half);
+    } else {
+      full_apply<double>(P, in->half.get(), out->half.get(), 1);
+    }
   } else {
     TT res;
     lr_apply(P, view_of(in->tt), res);
@@ -402,22 +445,26 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
   }
 }
 
+// Preconditioned CG on the full grid (Sec. 3.3, Sec. 4) with vectors stored in precision R; the
+// scalars (inner products, step lengths) are FP64 device values, the residual test runs on the host.
+template <typename R>
 void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
+  using V = typename CplxOf<R>::T;
   lrfg_ctx* ctx = P->ctx;
   const FullGrid& g = P->g;
   const long long n = g.n_half;
-  DBuf<double2> u(ctx->pool, n), r(ctx->pool, n), z(ctx->pool, n), p(ctx->pool, n), q(ctx->pool, n);
+  DBuf<V> u(ctx->pool, n), r(ctx->pool, n), z(ctx->pool, n), p(ctx->pool, n), q(ctx->pool, n);
   DBuf<double> s(ctx->pool, 4);  // rz, pq, zz, rz_new
   double* d_rz = s.get();
   double* d_pq = s.get() + 1;
   double* d_zz = s.get() + 2;
   double* d_rzn = s.get() + 3;
-  LRFG_CUDA(cudaMemsetAsync(u.get(), 0, sizeof(double2) * n, ctx->stream));
-  full_rhs(P, E, r.get(), 0);
-  half_precond(ctx, g, r.get(), z.get());
-  LRFG_CUDA(cudaMemcpyAsync(p.get(), z.get(), sizeof(double2) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-  half_dot(ctx, g, r.get(), z.get(), d_rz);
-  half_dot(ctx, g, z.get(), z.get(), d_zz);
+  LRFG_CUDA(cudaMemsetAsync(u.get(), 0, sizeof(V) * n, ctx->stream));
+  full_rhs<R>(P, E, r.get(), 0);
+  half_precond(ctx, g, (const V*)r.get(), z.get());
+  LRFG_CUDA(cudaMemcpyAsync(p.get(), z.get(), sizeof(V) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  half_dot(ctx, g, (const V*)r.get(), (const V*)z.get(), d_rz);
+  half_dot(ctx, g, (const V*)z.get(), (const V*)z.get(), d_zz);
   double zz0 = 0.0;
   LRFG_CUDA(cudaMemcpyAsync(&zz0, d_zz, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -426,19 +473,19 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
   double rel = nb > 0.0 ? 1.0 : 0.0;
   int applies = 0;
   while (nb > 0.0 && it < P->opts.maxit) {
-    full_apply(P, p.get(), q.get(), 0);
+    full_apply<R>(P, p.get(), q.get(), 0);
     ++applies;
-    half_dot(ctx, g, p.get(), q.get(), d_pq);
-    pcg_update(ctx, g, u.get(), r.get(), p.get(), q.get(), z.get(), d_rz, d_pq);
-    half_dot(ctx, g, z.get(), z.get(), d_zz);
+    half_dot(ctx, g, (const V*)p.get(), (const V*)q.get(), d_pq);
+    pcg_update(ctx, g, u.get(), r.get(), (const V*)p.get(), (const V*)q.get(), z.get(), d_rz, d_pq);
+    half_dot(ctx, g, (const V*)z.get(), (const V*)z.get(), d_zz);
     ++it;
     double zz = 0.0;
     LRFG_CUDA(cudaMemcpyAsync(&zz, d_zz, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     rel = std::sqrt(std::max(zz, 0.0)) / nb;
     if (rel <= P->opts.tol) break;
-    half_dot(ctx, g, r.get(), z.get(), d_rzn);
-    pcg_direction(ctx, g, p.get(), z.get(), d_rzn, d_rz);
+    half_dot(ctx, g, (const V*)r.get(), (const V*)z.get(), d_rzn);
+    pcg_direction(ctx, g, p.get(), (const V*)z.get(), d_rzn, d_rz);
     LRFG_CUDA(cudaMemcpyAsync(d_rz, d_rzn, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   }
   res->iters = it;
@@ -446,11 +493,19 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
   res->converged = rel <= P->opts.tol ? 1 : 0;
   res->applies = applies;
   for (int j = 0; j < 4; ++j) res->ranks[j] = 1;
-  res->Aeff = full_aeff(P, E, u.get());
+  // the solution is handed out, and A_eff evaluated, in FP64
+  DBuf<double2> u64;
+  if constexpr (std::is_same<R, double>::value) {
+    u64 = std::move(u);
+  } else {
+    u64 = DBuf<double2>(ctx->pool, n);
+    convert(ctx, (const V*)u.get(), u64.get(), n);
+  }
+  res->Aeff = full_aeff(P, E, u64.get());
   if (u_out) {
     lrfg_field* f;
     new_field(ctx, LRFG_FULL, P->d, P->N, &f);
-    f->half = std::move(u);
+    f->half = std::move(u64);
     *u_out = f;
   }
 }
@@ -579,7 +634,10 @@ lrfg_status lrfg_destroy(lrfg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   delete ctx->pool;
-  for (auto& kv : ctx->twiddles) cudaFree(kv.second.W);
+  for (auto& kv : ctx->twiddles) {
+    cudaFree(kv.second.W);
+    if (kv.second.Wf) cudaFree(kv.second.Wf);
+  }
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.second.first);
     cudaEventDestroy(p.second.second);
@@ -644,7 +702,7 @@ lrfg_status lrfg_fft_fibres(lrfg_ctx* ctx, const double* in, double* out, int ou
     LRFG_REQUIRE((in && out) || (long long)outer * inner == 0, "null buffer");
     LRFG_REQUIRE(sign == 1 || sign == -1, "sign must be +1 or -1");
     LRFG_REQUIRE(N >= 1 && N % 2 == 1, "N must be odd");
-    fft_fibres(ctx, (const double2*)in, (double2*)out, outer, N, inner, sign);
+    fft_fibres<double2>(ctx, (const double2*)in, (double2*)out, outer, N, inner, sign);
   });
 }
 
@@ -757,7 +815,9 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(coeff && opts && out, "null argument");
     check_grid(coeff->d, coeff->N);
     LRFG_REQUIRE(opts->fmt == LRFG_FULL || opts->fmt == LRFG_TT, "solution format must be LRFG_FULL or LRFG_TT");
-    if (opts->prec != LRFG_FP64) fail(LRFG_ENOTSUP, "only LRFG_FP64 is supported");
+    LRFG_REQUIRE(opts->prec == LRFG_FP64 || opts->prec == LRFG_MIXED, "unknown precision %d", (int)opts->prec);
+    if (opts->prec == LRFG_MIXED && opts->fmt != LRFG_FULL)
+      fail(LRFG_ENOTSUP, "LRFG_MIXED is implemented for LRFG_FULL solutions only");
     LRFG_REQUIRE(opts->maxit >= 0, "maxit must be >= 0");
     LRFG_REQUIRE(opts->tol >= 0.0, "tol must be >= 0");
     if (opts->fmt == LRFG_TT) LRFG_REQUIRE(opts->rank >= 1, "TT solve needs rank >= 1 (got %d)", opts->rank);
@@ -809,6 +869,12 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       P->g = make_grid(P->d, P->N);
       P->wc = DBuf<double2>(ctx->pool, P->g.n_half);
       P->wr = DBuf<double>(ctx->pool, P->g.n_real);
+      if (P->opts.prec == LRFG_MIXED) {
+        P->a_full_f = DBuf<float>(ctx->pool, n);
+        convert(ctx, (const double*)P->a_full.get(), P->a_full_f.get(), n);
+        P->wcf = DBuf<float2>(ctx->pool, P->g.n_half);
+        P->wrf = DBuf<float>(ctx->pool, P->g.n_real);
+      }
     } else {
       double xmax = 0.0;
       for (int j = 0; j < P->d; ++j) xmax += (double)((P->N[j] - 1) / 2) * ((P->N[j] - 1) / 2);
@@ -871,7 +937,13 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
     new_field(P->ctx, P->opts.fmt, P->d, P->N, &f);
     if (P->opts.fmt == LRFG_FULL) {
       f->half = DBuf<double2>(P->ctx->pool, P->g.n_half);
-      full_rhs(P, E, f->half.get(), 1);
+      if (P->opts.prec == LRFG_MIXED) {
+        DBuf<float2> bf(P->ctx->pool, P->g.n_half);
+        full_rhs<float>(P, E, bf.get(), 1);
+        convert(P->ctx, (const float2*)bf.get(), f->half.get(), P->g.n_half);
+      } else {
+        full_rhs<double>(P, E, f->half.get(), 1);
+      }
     } else {
       lr_rhs(P, E, f->tt);
     }
@@ -890,7 +962,10 @@ lrfg_status lrfg_problem_solve(lrfg_problem* P, const double* E, lrfg_result* re
     for (int j = 0; j < P->d; ++j) LRFG_REQUIRE(std::isfinite(E[j]), "E must be finite");
     *res = lrfg_result{};
     auto t0 = std::chrono::steady_clock::now();
-    if (P->opts.fmt == LRFG_FULL) solve_full(P, E, res, u_out);
+    if (P->opts.fmt == LRFG_FULL) {
+      if (P->opts.prec == LRFG_MIXED) solve_full<float>(P, E, res, u_out);
+      else solve_full<double>(P, E, res, u_out);
+    }
     else solve_tt(P, E, res, u_out);
     LRFG_CUDA(cudaStreamSynchronize(P->ctx->stream));
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -933,7 +1008,7 @@ lrfg_status lrfg_field_from_full(lrfg_ctx* ctx, int d, const int N[3], const dou
     LRFG_CUDA(cudaMemcpyAsync(tmp.get(), values, sizeof(double) * g.n_real,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     f->half = DBuf<double2>(ctx->pool, g.n_half);
-    full_forward(ctx, g, tmp.get(), nullptr, 1.0, f->half.get());
+    full_forward<double>(ctx, g, tmp.get(), nullptr, 1.0, f->half.get());
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     *out = f;
   });
@@ -978,7 +1053,7 @@ lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* v
       DBuf<double2> tmp(ctx->pool, g.n_half);
       LRFG_CUDA(cudaMemcpyAsync(tmp.get(), f->half.get(), sizeof(double2) * g.n_half, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
-      full_inverse(ctx, g, tmp.get(), nullptr, 1.0 / (double)g.n_real, target);
+      full_inverse<double>(ctx, g, tmp.get(), nullptr, 1.0 / (double)g.n_real, target);
     } else {
       tt_expand(ctx, view_of(f->tt), target);
     }

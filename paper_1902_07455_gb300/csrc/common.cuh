@@ -49,7 +49,9 @@ struct Error {
 // ------------------------------------------------------------------------------------------------
 class DevicePool {
  public:
-  explicit DevicePool(size_t budget) : budget_(budget) {}
+  // LRFG_POOL_POISON=1 in the environment fills every block handed out with NaN bytes (a debugging
+  // aid: a kernel that reads memory it did not write then yields NaN instead of stale values)
+  explicit DevicePool(size_t budget);
   ~DevicePool() { trim(); }
   void* alloc(size_t bytes);
   void release(void* p);
@@ -61,6 +63,7 @@ class DevicePool {
   std::map<size_t, std::vector<void*>> sized_;  // free blocks by rounded size
   std::map<void*, size_t> live_size_;            // blocks handed out
   size_t budget_, in_use_ = 0, reserved_ = 0;
+  bool poison_ = false;
 };
 
 // RAII buffer from the pool
@@ -104,6 +107,7 @@ struct TT {
 // twiddle tables W[j] = exp(-2 pi i j / N), cached per N on the device
 struct Twiddles {
   double2* W = nullptr;
+  float2* Wf = nullptr;  // the same table rounded to FP32 (made on first use)
   int N = 0;
 };
 

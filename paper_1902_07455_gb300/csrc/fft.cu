@@ -49,12 +49,33 @@ const Twiddles& twiddles_for(lrfg_ctx* ctx, int N) {
   return ctx->twiddles.emplace(N, t).first->second;
 }
 
-static int tile_fibres(lrfg_ctx* ctx, int N, int rows_per_fibre_pair, size_t* smem_out) {
+template <>
+const double2* twiddle_table<double>(lrfg_ctx* ctx, int N) {
+  return twiddles_for(ctx, N).W;
+}
+
+template <>
+const float2* twiddle_table<float>(lrfg_ctx* ctx, int N) {
+  Twiddles& t = const_cast<Twiddles&>(twiddles_for(ctx, N));
+  if (!t.Wf) {
+    std::vector<float2> h(N);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int j = 0; j < N; ++j) {
+      double ang = two_pi * (double)j / (double)N;
+      h[j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    LRFG_CUDA(cudaMalloc(&t.Wf, sizeof(float2) * N));
+    LRFG_CUDA(cudaMemcpy(t.Wf, h.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+  }
+  return t.Wf;
+}
+
+static int tile_fibres(lrfg_ctx* ctx, int N, int rows_per_fibre_pair, size_t* smem_out, size_t elem = sizeof(double2)) {
   // shared memory: twiddles N + 2 buffers of TF rows (+ N multipliers for the operator kernels)
   size_t limit = 100 * 1024;
   if (N > 300) limit = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);
-  long long per = 2LL * N * (long long)sizeof(double2);
-  long long fixed = 2LL * N * (long long)sizeof(double2);
+  long long per = 2LL * N * (long long)elem;
+  long long fixed = 2LL * N * (long long)elem;
   long long tf = ((long long)limit - fixed) / per;
   if (tf > 64) tf = 64;
   if (tf < 1) tf = 1;
@@ -66,14 +87,14 @@ static int tile_fibres(lrfg_ctx* ctx, int N, int rows_per_fibre_pair, size_t* sm
 // ----------------------------------------------------------------------------------------------------
 // complex fibres
 // ----------------------------------------------------------------------------------------------------
-template <int SIGN>
-__global__ void __launch_bounds__(256) fft_fibres_kernel(const double2* in, double2* out,
-                                                         long long outer, int N, long long inner, int TF,
-                                                         FftPlan pl, const double2* __restrict__ Wg) {
-  extern __shared__ double2 sm[];
-  double2* W = sm;
-  double2* a = sm + 2 * N;
-  double2* b = a + (size_t)TF * N;
+template <int SIGN, typename V>
+__global__ void __launch_bounds__(256) fft_fibres_kernel(const V* in, V* out, long long outer, int N, long long inner,
+                                                         int TF, FftPlan pl, const V* __restrict__ Wg) {
+  extern __shared__ __align__(16) unsigned char smraw_fib[];
+  V* sm = (V*)smraw_fib;
+  V* W = sm;
+  V* a = sm + 2 * N;
+  V* b = a + (size_t)TF * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
   const long long nfib = outer * inner;
   const long long g0 = (long long)blockIdx.x * TF;
@@ -88,7 +109,7 @@ __global__ void __launch_bounds__(256) fft_fibres_kernel(const double2* in, doub
     a[(size_t)f * N + n] = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
   }
   __syncthreads();
-  double2* res = stockham_rows<SIGN>(a, b, nf, N, pl, W);
+  V* res = stockham_rows<SIGN>(a, b, nf, N, pl, (const V*)W);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int f, n;
     if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
@@ -98,30 +119,33 @@ __global__ void __launch_bounds__(256) fft_fibres_kernel(const double2* in, doub
   }
 }
 
-void fft_fibres(lrfg_ctx* ctx, const double2* in, double2* out, long long outer, int N, long long inner,
-                int sign) {
+template <typename V>
+void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long long inner, int sign) {
+  using R = typename RealOf<V>::T;
   LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fft length must be odd (got %d)", N);
   LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
   if (outer == 0 || inner == 0) return;
   FftPlan pl = make_plan(N);
-  const Twiddles& tw = twiddles_for(ctx, N);
+  const V* W = twiddle_table<R>(ctx, N);
   size_t smem;
-  int TF = tile_fibres(ctx, N, 1, &smem);
+  int TF = tile_fibres(ctx, N, 1, &smem, sizeof(V));
   long long nfib = outer * inner;
   long long blocks = (nfib + TF - 1) / TF;
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
   const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;   // radix-2-equivalent count
-  const double bytes = 2.0 * sizeof(double2) * (double)N * (double)nfib;
+  const double bytes = 2.0 * sizeof(V) * (double)N * (double)nfib;
   if (sign < 0) {
-    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<-1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
-                fft_fibres_kernel<-1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W));
+                fft_fibres_kernel<-1, V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W));
   } else {
-    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
-                fft_fibres_kernel<1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W));
+                fft_fibres_kernel<1, V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W));
   }
 }
+template void fft_fibres<double2>(lrfg_ctx*, const double2*, double2*, long long, int, long long, int);
+template void fft_fibres<float2>(lrfg_ctx*, const float2*, float2*, long long, int, long long, int);
 
 // ----------------------------------------------------------------------------------------------------
 // real fibres under a multiplier: rows hold fibre f (real part) and fibre f + TF (imaginary part)

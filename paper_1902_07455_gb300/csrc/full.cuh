@@ -16,23 +16,32 @@ struct FullGrid {
 
 FullGrid make_grid(int d, const int* N);
 // half_out = Phi(scale * coef .* real_in)   (coef may be null); Phi = unnormalised forward DFT
-void full_forward(lrfg_ctx* ctx, const FullGrid& g, const double* real_in, const double* coef, double scale,
-                  double2* half_out);
+template <typename R>
+void full_forward(lrfg_ctx* ctx, const FullGrid& g, const R* real_in, const R* coef, R scale,
+                  typename CplxOf<R>::T* half_out);
 // real_out = coef .* (scale * Phi^{*}(half))  (unnormalised inverse; half is overwritten)
-void full_inverse(lrfg_ctx* ctx, const FullGrid& g, double2* half_inout, const double* coef, double scale,
-                  double* real_out);
-void half_mul_grad(lrfg_ctx* ctx, const FullGrid& g, const double2* in, double2* out, int alpha, double scale);
-void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const double2* in, double2* acc, int alpha, double scale, int init,
+template <typename R>
+void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale,
+                  R* real_out);
+template <typename V>
+void half_mul_grad(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out, int alpha, double scale);
+template <typename V>
+void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alpha, double scale, int init,
                   int precond);
-void half_precond(lrfg_ctx* ctx, const FullGrid& g, const double2* in, double2* out);
-// Hermitian-weighted real inner product over the full spectrum, written to a device scalar
-void half_dot(lrfg_ctx* ctx, const FullGrid& g, const double2* x, const double2* y, double* out_dev);
-// out_dev (+)= sum_k a_k (E + e_k)^2
-void energy_sum(lrfg_ctx* ctx, const FullGrid& g, const double* e, const double* a, double E, double* out_dev,
-                int accumulate);
-void pcg_update(lrfg_ctx* ctx, const FullGrid& g, double2* u, double2* r, const double2* p, const double2* q,
-                double2* z, const double* num, const double* den);
-void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, double2* p, const double2* z, const double* num,
-                   const double* den);
+template <typename V>
+void half_precond(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out);
+// Hermitian-weighted real inner product over the full spectrum (FP64 accumulation) into a device scalar
+template <typename V>
+void half_dot(lrfg_ctx* ctx, const FullGrid& g, const V* x, const V* y, double* out_dev);
+// out_dev (+)= sum_k a_k (E + e_k)^2 (FP64 accumulation)
+template <typename R>
+void energy_sum(lrfg_ctx* ctx, const FullGrid& g, const R* e, const R* a, double E, double* out_dev, int accumulate);
+template <typename V>
+void pcg_update(lrfg_ctx* ctx, const FullGrid& g, V* u, V* r, const V* p, const V* q, V* z, const double* num,
+                const double* den);
+template <typename V>
+void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, V* p, const V* z, const double* num, const double* den);
+template <typename A, typename B>
+void convert(lrfg_ctx* ctx, const A* in, B* out, long long n);
 
 }  // namespace lrfg

@@ -8,9 +8,13 @@ namespace lrfg {
 
 // ---- fft.cu -------------------------------------------------------------------------------------
 FftPlan make_plan(int N);
+// device twiddle table W[j] = exp(-2 pi i j / N) in FP64 (double) or rounded to FP32 (float)
+template <typename R>
+const typename CplxOf<R>::T* twiddle_table(lrfg_ctx* ctx, int N);
 // batched complex DFT along the middle axis of (outer, N, inner); sign -1 forward, +1 inverse
-void fft_fibres(lrfg_ctx* ctx, const double2* in, double2* out, long long outer, int N, long long inner,
-                int sign);
+// (V = double2 or float2)
+template <typename V>
+void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long long inner, int sign);
 // real fibres: out = scale * F^-1 diag(m) F in, m given by kind/param (lrfg_multiplier)
 void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
                     int kind, double param, double scale);

@@ -435,11 +435,14 @@ namespace lrfg {
 // ------------------------------------------------------------------------------------------------
 // Factor of a (balanced) Gram matrix for the Gram-SVD: pivoted Cholesky P^T G P = L L^T (Golub & Van
 // Loan Sec. 4.2, diagonal pivoting for semidefinite matrices), stopped when the largest remaining
-// pivot falls below tau = 1e-20 times the largest initial diagonal (numerical rank rho): those
-// directions have singular values below 1e-10 of the largest, where an FP64 Gram matrix no longer
-// determines them (an emulation of the truncation on exponential-sum outputs loses accuracy, 1e-9 ->
-// 4e-7, when pivots down to 1e-26 are kept).  Outputs, for the
-// orthonormal basis Q = M C P L11^{-T} of the left part M (C the balancing scaling):
+// pivot falls below tau = 1e-16 times the largest initial diagonal (numerical rank rho).  The entries
+// of an FP64 Gram matrix carry absolute errors of about eps64 times its largest diagonal, so smaller
+// pivots are rounding noise: keeping them makes the basis M L^{-T} lose orthogonality in those
+// directions (error ~ eps / sqrt(pivot)), dropping more loses their content (~ sqrt(pivot)).  The two
+// balance near tau = eps64; an emulation of the truncations of the rank-10 solve at 243^3 (Hadamard
+// products with the coefficient, exponential-sum outputs) gives relative errors against the SVD
+// truncation of 4e-10..3e-9 at 1e-16, against 1.4e-8..1e-7 at 1e-20 and 7e-9..1.4e-8 at 1e-14.
+// Outputs, for the orthonormal basis Q = M C P L11^{-T} of the left part M (C the balancing scaling):
 //   RA  (b x b): rows i < rho hold L^T P^T (so G = RA^T RA up to the dropped Schur complement),
 //   RAc (b x b): RA with column j divided by c_j (undoes the balancing in the transfer matrix),
 //   Pc  (b x b): Pc[perm[l]][q] = c[perm[l]] (L11^{-1})[q][l] for l, q < rho (so Q = M Pc).
@@ -578,7 +581,7 @@ void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int bat
   LRFG_CUDA(cudaFuncSetAttribute(gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const double flops = (2.0 * b * (double)b * b / 3.0 + b * (double)b * b / 3.0) * batch;
   LRFG_LAUNCH(ctx, KC_EIGEN, flops, sizeof(double) * 4.0 * b * b * batch,
-              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-20, RA, RAc, Pc,
+              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-16, RA, RAc, Pc,
                                                                                scratch.get(), use_smem));
 }
 

@@ -50,3 +50,13 @@ def test_tt_minres_at_243(ctx, problem_setup, rank):
     # sampled field values: expand a few fibres of the TT solution and check they are finite and zero-mean
     cores = u.tt().cores
     assert all(torch.isfinite(c).all() for c in cores)
+
+
+def test_full_mixed_pcg_at_243(ctx, problem_setup):
+    # LRFG_MIXED (FP32 storage and FFTs, FP64 scalars) to a 1e-5 residual: A_eff within 1e-5 of the
+    # oracle's FP64 value (A_eff is stationary at the solution; see test_gpu_mixed for the derivation)
+    gold, _, a_full = problem_setup
+    P = ctx.problem(a_full, lrfg.FULL, tol=1e-5, maxit=2000, prec=lrfg.MIXED)
+    res, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
+    assert res.converged
+    assert abs(res.Aeff - gold["full"]["Aeff"]) <= 1e-5 * gold["full"]["Aeff"]
