@@ -141,7 +141,7 @@ def measured_peaks():
 # FP64 arithmetic classes are bound by the FP64 pipe: GB300 issues 2 FP64 FMA per clock per SM
 # (4 flop/clk/SM), i.e. 152 SMs x 2.07 GHz x 4 = 1.26 TFLOP/s at the maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2.070 * 4 / 1e3
-ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen"}
+ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen", "gram_factor"}
 
 
 def class_rooflines(stats, classes):

@@ -130,7 +130,7 @@ void resolve_profile(lrfg_ctx* ctx) {
 
 static const char* kClassNames[KC_COUNT] = {
     "fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "pointwise",
-    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc"};
+    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor"};
 
 }  // namespace lrfg
 

@@ -127,6 +127,7 @@ enum KClass {
   KC_EIGEN,           // small symmetric eigen-decompositions
   KC_KHATRI_RAO,      // TT Hadamard (Khatri–Rao carriages)
   KC_TT_MISC,         // block embedding, balancing, scaling, transposes, fills
+  KC_CHOL,            // pivoted Cholesky factors of the Gram matrices (TT rounding)
   KC_COUNT
 };
 struct KStats {

@@ -39,10 +39,19 @@ void syevj_mixed(lrfg_ctx* ctx, double* A, double* w, double* V, int m, int batc
 // FP64 k largest eigenpairs by tridiagonalisation, bisection and inverse iteration: w[0..k) descending,
 // eigenvectors in the first k columns of V (n x n row-major per batch item).  A is left unchanged.
 void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch = 1);
-// Gram-SVD left factors from a balanced Gram matrix G (b x b per item) and the balancing c: pivoted
-// Cholesky; writes RA, RAc, Pc (b x b each per item) as the Gram-SVD needs them.
+// Top-k left singular pairs of B (n x n per item, nonzero block nA[b] x nB[b]) from BBt = B B^T and
+// BtB = B^T B: the smaller of the two nonzero blocks is decomposed (w = sigma^2); left vectors in the
+// first k columns of V, completed to min(k, nA) orthonormal columns.
+// The same on the leading n_eff[b] x n_eff[b] block of A (the rest of A is zero); the eigenvector
+// rows beyond n_eff and the columns beyond min(k, n_eff) are zero.
+void syevx_sized(lrfg_ctx* ctx, const double* A, const int* n_eff, double* w, double* V, int n, int k, int batch);
+void syevx_product(lrfg_ctx* ctx, const double* BBt, const double* BtB, const double* B, const int* nA,
+                   const int* nB, double* w, double* V, int n, int k, int batch);
+// Gram-SVD factors from a balanced Gram matrix G (b x b per item) and the balancing c: pivoted
+// Cholesky; writes RA (G ~ RA^T RA, nonzero rows first), RAc and Pc (b x b each per item; skipped when
+// null, and then c may be null), and the numerical rank into rho (may be null).
 void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
-                 double* Pc);
+                 double* Pc, int* rho = nullptr);
 // elementwise helpers
 void fill(lrfg_ctx* ctx, double* x, double v, long long n);
 void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y

@@ -159,28 +159,52 @@ __device__ void trid_solve(int n, const double* dl, const double* dd, const doub
 }
 
 // W: n x n work matrix (shared or global), Y: k vectors of length n (vector-major), lu: per-vector LU
-// scratch (4n doubles + n ints as doubles), all per block.
-__global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __restrict__ Ag, int n, int k, double* wg,
-                                                              double* Vg, int ldv, double* scratch, int use_smem) {
+// scratch (4n doubles + n ints as doubles), all per block.  nl, kl: the launch sizes (strides of the
+// inputs and outputs).  Optional reduced problem (nAg != null): the symmetric input A = B B^T has its
+// nonzero block in the leading nA x nA corner, and A2 = B^T B (B: nl x nl, nonzero block nA x nB) has
+// it in the leading nB x nB corner.  The smaller of the two is decomposed; when that is A2, the left
+// vectors are mapped back as u = B w / sigma and re-orthonormalised (modified Gram-Schmidt), and
+// completed by unit vectors when B has fewer than k nonzero singular values.
+__global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __restrict__ Ag, int nl, int kl, double* wg,
+                                                              double* Vg, int ldv, double* scratch, int use_smem,
+                                                              const int* __restrict__ nAg, const int* __restrict__ nBg,
+                                                              const double* __restrict__ A2g,
+                                                              const double* __restrict__ Bg) {
   extern __shared__ __align__(16) double sm[];
   double* red = sm;            // 33 (32 partials + the result) + padding
-  double* d = red + 40;        // n
-  double* e = d + n;           // n
-  double* beta = e + n;        // n
-  double* pv = beta + n;       // n: p / w of the current reflector
-  double* vv = pv + n;         // n: current reflector v
-  double* e2 = vv + n;         // n: e^2 for the Sturm counts
-  double* lam = e2 + n;        // k
-  const size_t nn = (size_t)n * n;
-  const size_t per = nn + (size_t)k * n + (size_t)k * 5 * n;  // global scratch per block
+  double* d = red + 40;        // nl
+  double* e = d + nl;          // nl
+  double* beta = e + nl;       // nl
+  double* pv = beta + nl;      // nl: p / w of the current reflector
+  double* vv = pv + nl;        // nl: current reflector v
+  double* e2 = vv + nl;        // nl: e^2 for the Sturm counts
+  double* lam = e2 + nl;       // kl
+  const size_t nnl = (size_t)nl * nl;
+  const size_t per = nnl + (size_t)kl * nl + (size_t)kl * 5 * nl;  // global scratch per block
   double* gbase = scratch + (size_t)blockIdx.x * per;
-  double* W = use_smem ? (lam + k + n) : gbase;  // after lam and the FP32 copies (2n floats = n doubles)
-  double* Y = gbase + nn;
-  double* lu = Y + (size_t)k * n;
-  const double* A = Ag + (size_t)blockIdx.x * nn;
+  double* W = use_smem ? (lam + kl + nl) : gbase;  // after lam and the FP32 copies (2nl floats = nl doubles)
   const int tid = threadIdx.x, nthr = blockDim.x;
-
-  for (size_t t = tid; t < nn; t += nthr) W[t] = A[t];
+  double* wout = wg + (size_t)blockIdx.x * nl;
+  double* Vout = Vg + (size_t)blockIdx.x * (size_t)nl * ldv;
+  // the problem actually decomposed: n x n, k vectors
+  const int nA = nAg ? max(0, min(nl, nAg[blockIdx.x])) : nl;
+  const int nB = nBg ? max(0, min(nl, nBg[blockIdx.x])) : nl;
+  const bool viaB = (nAg != nullptr) && (A2g != nullptr) && (Bg != nullptr) && nB < nA;
+  const int n = viaB ? nB : nA;
+  const int k = min(kl, n);
+  const double* A = (viaB ? A2g : Ag) + (size_t)blockIdx.x * nnl;
+  double* Y = gbase + nnl;
+  double* lu = Y + (size_t)kl * nl;
+  for (int t = tid; t < kl; t += nthr) wout[t] = 0.0;
+  for (size_t q = tid; q < (size_t)nl * kl; q += nthr) {
+    const int i = (int)(q / kl), t = (int)(q - (q / kl) * kl);
+    Vout[(size_t)i * ldv + t] = 0.0;
+  }
+  if (n == 0) return;
+  for (size_t t = tid; t < (size_t)n * n; t += nthr) {
+    const int i = (int)(t / n), j = (int)(t - (t / n) * n);
+    W[t] = A[(size_t)i * nl + j];
+  }
   __syncthreads();
 
   // 1. tridiagonalisation
@@ -272,16 +296,13 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   __syncthreads();
   if (tnorm == 0.0) {
     // the zero matrix: eigenvalues 0, eigenvectors the unit vectors
-    double* w0 = wg + (size_t)blockIdx.x * n;
-    double* V0 = Vg + (size_t)blockIdx.x * (size_t)n * ldv;
-    for (int t = tid; t < k; t += nthr) w0[t] = 0.0;
+    for (int t = tid; t < k; t += nthr) lam[t] = 0.0;
     for (size_t q = tid; q < (size_t)k * n; q += nthr) {
-      int t = (int)(q / n), i = (int)(q - (q / n) * n);
-      V0[(size_t)i * ldv + t] = (i == t) ? 1.0 : 0.0;
+      const int t = (int)(q / n), i = (int)(q - (q / n) * n);
+      Y[q] = (i == t) ? 1.0 : 0.0;
     }
-    return;
-  }
-  // (a) FP32 localisation: 24 halvings of the Gershgorin interval, one thread per eigenvalue
+  } else {
+  // (a) FP32 localisation of each eigenvalue in the Gershgorin interval
   float* df = (float*)(lam + k);       // n floats (overlaps nothing: W starts after these when in smem)
   float* e2f = df + n;                 // n floats
   for (int i = tid; i < n; i += nthr) {
@@ -292,31 +313,60 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   double* bra = pv;  // reuse: bracket lower ends for the k eigenvalues (pv, vv are free now)
   double* brc = vv;  // bracket upper ends
   const double glo = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, ghi = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
-  for (int t = tid; t < k; t += nthr) {
-    const int idx = n - 1 - t;
-    float a = (float)glo, c = (float)ghi;
-    for (int it = 0; it < 24; ++it) {
-      float mid = 0.5f * (a + c);
-      if (!(mid > a && mid < c)) break;
-      if (sturm_count_f32(df, e2f, n, mid) > idx) c = mid; else a = mid;
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int t = warp; t < k; t += nw) {
+      const int idx = n - 1 - t;
+      float a = (float)glo, c = (float)ghi;
+      // five rounds of 32-way multisection (about 25 bits), one warp per eigenvalue
+      for (int it = 0; it < 5; ++it) {
+        const float h = (c - a) * (1.0f / 33.0f);
+        const float x = a + h * (float)(lane + 1);
+        const unsigned above = __ballot_sync(0xffffffff, sturm_count_f32(df, e2f, n, x) > idx);
+        const int f = above ? (__ffs(above) - 1) : 32;
+        const float na = (f == 0) ? a : a + h * (float)f;
+        const float nc = (f == 32) ? c : a + h * (float)(f + 1);
+        if (!(na < nc)) break;  // FP32 resolution reached
+        a = na;
+        c = nc;
+      }
+      if (lane == 0) {
+        const double w = (double)c - (double)a;
+        bra[t] = fmax(glo, (double)a - 4.0 * w - 1e-6 * tnorm);
+        brc[t] = fmin(ghi, (double)c + 4.0 * w + 1e-6 * tnorm);
+      }
     }
-    const double w = (double)c - (double)a;
-    bra[t] = fmax(glo, (double)a - 4.0 * w - 1e-6 * tnorm);
-    brc[t] = fmin(ghi, (double)c + 4.0 * w + 1e-6 * tnorm);
   }
   __syncthreads();
-  // (b) FP64: verify each bracket with FP64 counts (fall back to the Gershgorin interval), then bisect to
-  // the FP64 resolution, one thread per eigenvalue (about 30 halvings remain after the FP32 phase)
-  for (int t = tid; t < k; t += nthr) {
-    const int idx = n - 1 - t;
-    double a = bra[t], c = brc[t];
-    if (!(sturm_count(d, e2, n, a) <= idx && sturm_count(d, e2, n, c) > idx)) { a = glo; c = ghi; }
-    for (int it = 0; it < 200; ++it) {
-      if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 1e-3 * DBL_EPSILON * tnorm + 4.0 * pivmin) break;
-      const double mid = 0.5 * (a + c);
-      if (sturm_count(d, e2, n, mid) > idx) c = mid; else a = mid;
+  // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 32-way multisection by
+  // one warp per eigenvalue until the bracket is at the FP64 resolution: five bits per round of Sturm
+  // counts instead of one, so the serial FP64 recurrences (64-cycle latency per dependent operation on
+  // this part) run about six times instead of thirty
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int t = warp; t < k; t += nw) {
+      const int idx = n - 1 - t;
+      double a = bra[t], c = brc[t];
+      int ca = (lane == 0) ? sturm_count(d, e2, n, a) : 0;
+      int cc = (lane == 1) ? sturm_count(d, e2, n, c) : 0;
+      ca = __shfl_sync(0xffffffff, ca, 0);
+      cc = __shfl_sync(0xffffffff, cc, 1);
+      if (!(ca <= idx && cc > idx)) { a = glo; c = ghi; }
+      for (int it = 0; it < 16; ++it) {
+        if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 1e-3 * DBL_EPSILON * tnorm + 4.0 * pivmin) break;
+        const double h = (c - a) * (1.0 / 33.0);
+        const double x = a + h * (double)(lane + 1);  // 32 interior points
+        const int cnt = sturm_count(d, e2, n, x);
+        const unsigned above = __ballot_sync(0xffffffff, cnt > idx);
+        // the first point whose count exceeds idx bounds the eigenvalue from above
+        const int f = above ? (__ffs(above) - 1) : 32;
+        const double na = (f == 0) ? a : a + h * (double)f;
+        const double nc = (f == 32) ? c : a + h * (double)(f + 1);
+        a = na;
+        c = nc;
+      }
+      if (lane == 0) lam[t] = 0.5 * (a + c);
     }
-    lam[t] = 0.5 * (a + c);
   }
   __syncthreads();
   // separate exactly equal eigenvalues slightly so that their factorisations differ
@@ -403,17 +453,76 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   }
   __syncthreads();
 
+  }  // tnorm != 0
+  __syncthreads();
+
   // outputs: eigenvalues descending, eigenvectors as the first k columns of V (leading dimension ldv)
-  double* w = wg + (size_t)blockIdx.x * n;
-  double* V = Vg + (size_t)blockIdx.x * (size_t)n * ldv;
-  for (int t = tid; t < k; t += nthr) w[t] = lam[t];
-  for (size_t q = tid; q < (size_t)k * n; q += nthr) {
-    int t = (int)(q / n), i = (int)(q - (q / n) * n);
-    V[(size_t)i * ldv + t] = Y[(size_t)t * n + i];
+  for (int t = tid; t < k; t += nthr) wout[t] = lam[t];
+  if (!viaB) {
+    for (size_t q = tid; q < (size_t)k * n; q += nthr) {
+      int t = (int)(q / n), i = (int)(q - (q / n) * n);
+      Vout[(size_t)i * ldv + t] = Y[(size_t)t * n + i];
+    }
+    return;
+  }
+  // left vectors u_t = B w_t / sigma_t (length nA, vector-major in lu, which inverse iteration no longer
+  // needs), then modified Gram-Schmidt (twice) in descending order, completed by unit vectors where
+  // sigma_t vanishes or B has fewer than kl singular values; at most min(kl, nA) columns
+  double* U = lu;
+  const double* B = Bg + (size_t)blockIdx.x * nnl;
+  for (size_t q = tid; q < (size_t)k * nA; q += nthr) {
+    const int t = (int)(q / nA), i = (int)(q - (q / nA) * nA);
+    const double sg = lam[t] > 0.0 ? sqrt(lam[t]) : 0.0;
+    double acc = 0.0;
+    for (int l = 0; l < n; ++l) acc = fma(B[(size_t)i * nl + l], Y[(size_t)t * n + l], acc);
+    U[q] = sg > 0.0 ? acc / sg : 0.0;
+  }
+  __syncthreads();
+  const int kout = min(kl, nA);
+  if (tid < 32) {
+    int next_unit = 0;
+    for (int t = 0; t < kout; ++t) {
+      double* ut = U + (size_t)t * nA;
+      if (t >= k) {
+        for (int i = tid; i < nA; i += 32) ut[i] = 0.0;
+      }
+      for (int attempt = 0; attempt <= nA; ++attempt) {
+        double n0 = 0.0;
+        for (int i = tid; i < nA; i += 32) n0 += ut[i] * ut[i];
+        n0 = warp_sum(n0);
+        for (int pass = 0; pass < 2; ++pass)
+          for (int s2 = 0; s2 < t; ++s2) {
+            const double* us = U + (size_t)s2 * nA;
+            double dp = 0.0;
+            for (int i = tid; i < nA; i += 32) dp += us[i] * ut[i];
+            dp = warp_sum(dp);
+            for (int i = tid; i < nA; i += 32) ut[i] -= dp * us[i];
+          }
+        double n1 = 0.0;
+        for (int i = tid; i < nA; i += 32) n1 += ut[i] * ut[i];
+        n1 = warp_sum(n1);
+        if (n0 > 0.0 && n1 > 0.25 * n0) {
+          const double sc = 1.0 / sqrt(n1);
+          for (int i = tid; i < nA; i += 32) ut[i] *= sc;
+          break;
+        }
+        // no usable direction: restart from the next unit vector
+        const int uidx = next_unit++ % nA;
+        for (int i = tid; i < nA; i += 32) ut[i] = (i == uidx) ? 1.0 : 0.0;
+        __syncwarp();
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (size_t q = tid; q < (size_t)kout * nA; q += nthr) {
+    const int t = (int)(q / nA), i = (int)(q - (q / nA) * nA);
+    Vout[(size_t)i * ldv + t] = U[q];
   }
 }
 
-void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch) {
+static void syevx_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch,
+                         const int* nA, const int* nB, const double* A2, const double* B) {
   if (n <= 0 || batch <= 0 || k <= 0) return;
   k = std::min(k, n);
   const size_t head = sizeof(double) * (40 + 7 * (size_t)n + k);
@@ -423,9 +532,24 @@ void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, i
   const size_t per = (size_t)n * n + (size_t)k * n + (size_t)k * 5 * n;
   DBuf<double> scratch(ctx->pool, per * batch);
   LRFG_CUDA(cudaFuncSetAttribute(syevx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // algorithmic count at the launch size (the reduced problems are smaller)
   const double flops = (4.0 / 3.0 * n * (double)n * n + 4.0 * (double)k * n * n + 60.0 * k * n) * batch;
   LRFG_LAUNCH(ctx, KC_EIGEN, flops, sizeof(double) * (2.0 * n * n + (double)k * n) * batch,
-              syevx_kernel<<<batch, kSyevxThreads, smem, ctx->stream>>>(A, n, k, w, V, n, scratch.get(), use_smem));
+              syevx_kernel<<<batch, kSyevxThreads, smem, ctx->stream>>>(A, n, k, w, V, n, scratch.get(), use_smem,
+                                                                         nA, nB, A2, B));
+}
+
+void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch) {
+  syevx_launch(ctx, A, w, V, n, k, batch, nullptr, nullptr, nullptr, nullptr);
+}
+
+void syevx_sized(lrfg_ctx* ctx, const double* A, const int* n_eff, double* w, double* V, int n, int k, int batch) {
+  syevx_launch(ctx, A, w, V, n, k, batch, n_eff, nullptr, nullptr, nullptr);
+}
+
+void syevx_product(lrfg_ctx* ctx, const double* BBt, const double* BtB, const double* B, const int* nA,
+                   const int* nB, double* w, double* V, int n, int k, int batch) {
+  syevx_launch(ctx, BBt, w, V, n, k, batch, nA, nB, BtB, B);
 }
 
 }  // namespace lrfg
@@ -453,7 +577,7 @@ constexpr int kCholThreads = 512;
 __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double* __restrict__ Gg,
                                                                    const double* __restrict__ cg, int b, double tau,
                                                                    double* RAg, double* RAcg, double* Pcg,
-                                                                   double* scratch, int use_smem) {
+                                                                   int* rhog, double* scratch, int use_smem) {
   extern __shared__ __align__(16) double sm[];
   double* redv = sm;                   // 32 values
   int* redi = (int*)(redv + 32);       // 32 indices
@@ -463,10 +587,10 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
   double* W = use_smem ? (double*)(flag + 2 + ((b + 2) & 1) + 64) : scratch + (size_t)blockIdx.x * 2 * bb;
   double* Li = W + bb;                 // L11^{-1}
   const double* G = Gg + (size_t)blockIdx.x * bb;
-  const double* c = cg + (size_t)blockIdx.x * b;
+  const double* c = cg ? cg + (size_t)blockIdx.x * b : nullptr;
   double* RA = RAg + (size_t)blockIdx.x * bb;
-  double* RAc = RAcg + (size_t)blockIdx.x * bb;
-  double* Pc = Pcg + (size_t)blockIdx.x * bb;
+  double* RAc = RAcg ? RAcg + (size_t)blockIdx.x * bb : nullptr;
+  double* Pc = Pcg ? Pcg + (size_t)blockIdx.x * bb : nullptr;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   for (size_t t = tid; t < bb; t += nthr) W[t] = G[t];
   for (int i = tid; i < b; i += nthr) perm[i] = i;
@@ -544,6 +668,16 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
     __syncthreads();
   }
   const int rho = flag[0];
+  if (rhog && tid == 0) rhog[blockIdx.x] = rho;
+  // outputs
+  for (size_t t = tid; t < bb; t += nthr) {
+    int i = (int)(t / b), l = (int)(t - (t / b) * b);  // RA row i, permuted column l
+    double v = (i < rho && l >= i) ? W[(size_t)l * b + i] : 0.0;
+    int col = perm[l];
+    RA[(size_t)i * b + col] = v;
+    if (RAc) RAc[(size_t)i * b + col] = v / c[col];
+  }
+  if (!Pc) return;
   // L11^{-1}: one thread per column q, forward substitution
   for (int q = tid; q < rho; q += nthr) {
     for (int i = 0; i < q; ++i) Li[(size_t)i * b + q] = 0.0;
@@ -554,14 +688,6 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
     }
   }
   __syncthreads();
-  // outputs
-  for (size_t t = tid; t < bb; t += nthr) {
-    int i = (int)(t / b), l = (int)(t - (t / b) * b);  // RA row i, permuted column l
-    double v = (i < rho && l >= i) ? W[(size_t)l * b + i] : 0.0;
-    int col = perm[l];
-    RA[(size_t)i * b + col] = v;
-    RAc[(size_t)i * b + col] = v / c[col];
-  }
   for (size_t t = tid; t < bb; t += nthr) {
     int l = (int)(t / b), q = (int)(t - (t / b) * b);  // Pc row perm[l], column q
     double v = (l < rho && q < rho && q >= l) ? c[perm[l]] * Li[(size_t)q * b + l] : 0.0;
@@ -570,7 +696,7 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
 }
 
 void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
-                 double* Pc) {
+                 double* Pc, int* rho) {
   if (b <= 0 || batch <= 0) return;
   const size_t head = sizeof(double) * 32 + sizeof(int) * (32 + b + 2 + ((b + 2) & 1)) + sizeof(double) * 64;
   const size_t full = head + sizeof(double) * 2 * (size_t)b * b;
@@ -580,9 +706,9 @@ void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int bat
   if (!use_smem) scratch = DBuf<double>(ctx->pool, (size_t)2 * b * b * batch);
   LRFG_CUDA(cudaFuncSetAttribute(gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const double flops = (2.0 * b * (double)b * b / 3.0 + b * (double)b * b / 3.0) * batch;
-  LRFG_LAUNCH(ctx, KC_EIGEN, flops, sizeof(double) * 4.0 * b * b * batch,
+  LRFG_LAUNCH(ctx, KC_CHOL, flops, sizeof(double) * 4.0 * b * b * batch,
               gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-16, RA, RAc, Pc,
-                                                                               scratch.get(), use_smem));
+                                                                               rho, scratch.get(), use_smem));
 }
 
 }  // namespace lrfg

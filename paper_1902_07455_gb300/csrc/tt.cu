@@ -223,32 +223,18 @@ __global__ void balance_kernel(double* GAg, double* Rg, double* cg, int m) {
   }
 }
 
-// From the eigen-decomposition GA = V diag(lam) V^T (balanced):
-//   RA[i][col]  = sqrt(lam_i) V[col][i]            (for S = RA R RA^T)
-//   RAc[i][col] = sqrt(lam_i) V[col][i] / c_col     (transfer, undoes the balancing)
-//   Pc[row][i]  = c_row V[row][i] / sqrt(lam_i)     (left factor, undoes the balancing)
-// Directions with lam <= tau lam_max are dropped (rows/columns set to 0).  Batch index: blockIdx.y.
-__global__ void sqrt_scale_rows_kernel(const double* __restrict__ lamg, const double* __restrict__ Vg,
-                                       const double* __restrict__ cg, double* RAg, double* RAcg, double* Pcg, int m,
-                                       double tau) {
-  const size_t mm = (size_t)m * m, bo = blockIdx.y;
-  const double* lam = lamg + bo * m;
-  const double* V = Vg + bo * mm;
-  const double* c = cg + bo * m;
-  double* RA = RAg + bo * mm;
-  double* RAc = RAcg + bo * mm;
-  double* Pc = Pcg + bo * mm;
-  const double lmax = lam[0] > 0.0 ? lam[0] : 0.0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
-    int i = t / m, col = t - (t / m) * m;
-    double l = lam[i];
-    bool keep = l > tau * lmax && l > 0.0;
-    double sl = keep ? sqrt(l) : 0.0;
-    double v = V[(size_t)col * m + i];
-    RA[(size_t)i * m + col] = sl * v;
-    RAc[(size_t)i * m + col] = sl * v / c[col];
-    Pc[(size_t)col * m + i] = keep ? c[col] * v / sl : 0.0;
-  }
+// P[b][t] *= c[b] / sigma_t, sigma_t = sqrt(w_t) (0 where w_t <= 0); one batch item per blockIdx.y
+__global__ void scale_rows_cols_kernel(double* Pg, const double* __restrict__ cg, const double* __restrict__ wg,
+                                       int b, int k) {
+  const size_t item = blockIdx.y;
+  double* P = Pg + item * (size_t)b * k;
+  const double* c = cg + item * (size_t)b;
+  const double* w = wg + item * (size_t)b;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)b * k) return;
+  const int row = (int)(t / k), col = (int)(t - (t / k) * k);
+  const double sg = w[col] > 0.0 ? sqrt(w[col]) : 0.0;
+  P[t] = sg > 0.0 ? P[t] * c[row] / sg : 0.0;
 }
 
 void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out) {
@@ -268,8 +254,6 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
                               cudaMemcpyDeviceToDevice, ctx->stream));
     return;
   }
-  const double tau = 1e-30;
-
   // right Gram matrices R[j] (s_j x s_j per batch item) of the carriages j..d-1, j = 1..d-1
   DBuf<double> R[4];
   {
@@ -295,24 +279,59 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
     const int a = rr[j], n = x.N[j], b = x.r[j + 1], k = rr[j + 1];
     const int rows = a * n;
     const long long sz = (long long)rows * b, sbb = (long long)b * b, sout = (long long)out.elems(j);
+    const long long sbk = (long long)b * k, skk = (long long)k * k;
     DBuf<double> GA(ctx->pool, (size_t)sbb * nb), cb(ctx->pool, (size_t)b * nb);
     gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, sz, Z.get(), b, sz, 0.0, GA.get(), b, sbb, nb);
     LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
                 balance_kernel<<<nb, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
-    DBuf<double> RA(ctx->pool, (size_t)sbb * nb), RAc(ctx->pool, (size_t)sbb * nb), Pc(ctx->pool, (size_t)sbb * nb);
-    gram_factor(ctx, GA.get(), cb.get(), b, nb, RA.get(), RAc.get(), Pc.get());
-    // S = RA R RA^T (balanced)
-    DBuf<double> RAR(ctx->pool, (size_t)sbb * nb), S(ctx->pool, (size_t)sbb * nb);
-    gemm(ctx, 0, 0, b, b, b, 1.0, RA.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, RAR.get(), b, sbb, nb);
-    gemm(ctx, 0, 1, b, b, b, 1.0, RAR.get(), b, sbb, RA.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
+    // The unfolding X = M N (M: rows x b left part, N: b x cols right part) has the Gram matrices
+    // GA = M^T M and R = N N^T.  Only the side whose numerical rank is smaller is factored (pivoted
+    // Cholesky stops at that rank), and the eigenproblem has that rank as its size.  The left part's
+    // rank is at most `rows`, the right part's at most `cols`: the smaller of the two picks the side.
+    long long cols = 1;
+    for (int i = j + 1; i < d; ++i) cols *= x.N[i];
+    const bool left_side = (long long)rows <= cols;
+    DBuf<int> rk(ctx->pool, (size_t)nb);
+    DBuf<double> F(ctx->pool, (size_t)sbb * nb), F1(ctx->pool, (size_t)sbb * nb), S(ctx->pool, (size_t)sbb * nb);
     DBuf<double> sig(ctx->pool, (size_t)b * nb), US(ctx->pool, (size_t)sbb * nb);
-    syevx(ctx, S.get(), sig.get(), US.get(), b, k, nb);
-    // P = Pc U_k (b x k), Y = M P, T = U_k^T RAc (k x b)
-    const long long sbk = (long long)b * k;
     DBuf<double> P(ctx->pool, (size_t)sbk * nb), T(ctx->pool, (size_t)sbk * nb);
-    gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, sbb, US.get(), b, sbb, 0.0, P.get(), k, sbk, nb);
-    gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, sz, P.get(), k, sbk, 0.0, out.core[j].get(), k, sout, nb);
-    gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, sbb, RAc.get(), b, sbb, 0.0, T.get(), b, sbk, nb);
+    if (left_side) {
+      // GA ~ RA^T RA, Q = M Pc orthonormal; S = RA R RA^T (nonzero block rho_A x rho_A); Y = Q U_k,
+      // transfer T = U_k^T RAc
+      DBuf<double> RAc(ctx->pool, (size_t)sbb * nb), Pc(ctx->pool, (size_t)sbb * nb);
+      gram_factor(ctx, GA.get(), cb.get(), b, nb, F.get(), RAc.get(), Pc.get(), rk.get());
+      gemm(ctx, 0, 0, b, b, b, 1.0, F.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, F1.get(), b, sbb, nb);
+      gemm(ctx, 0, 1, b, b, b, 1.0, F1.get(), b, sbb, F.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
+      syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, k, nb);
+      gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, sbb, US.get(), b, sbb, 0.0, P.get(), k, sbk, nb);
+      gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, sz, P.get(), k, sbk, 0.0, out.core[j].get(), k, sout, nb);
+      gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, sbb, RAc.get(), b, sbb, 0.0, T.get(), b, sbk, nb);
+    } else {
+      // R ~ RB^T RB; the left singular vectors of X are those of M C RB^T (C the balancing): from the
+      // eigenvectors W of S' = RB GA RB^T (nonzero block rho_R x rho_R), Y = M C RB^T W Sigma^-1, made
+      // orthonormal again by a pivoted-Cholesky pass on Y^T Y (any orthonormal basis of the span gives
+      // the same truncation); transfer T = Y^T M, computed explicitly
+      gram_factor(ctx, R[j + 1].get(), nullptr, b, nb, F.get(), nullptr, nullptr, rk.get());
+      gemm(ctx, 0, 0, b, b, b, 1.0, F.get(), b, sbb, GA.get(), b, sbb, 0.0, F1.get(), b, sbb, nb);
+      gemm(ctx, 0, 1, b, b, b, 1.0, F1.get(), b, sbb, F.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
+      syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, k, nb);
+      DBuf<double> P0(ctx->pool, (size_t)sbk * nb);
+      gemm(ctx, 1, 0, b, k, b, 1.0, F.get(), b, sbb, US.get(), b, sbb, 0.0, P0.get(), k, sbk, nb);
+      LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbk * nb, 2.0 * sizeof(double) * sbk * nb,
+                  scale_rows_cols_kernel<<<dim3((unsigned)((sbk + 255) / 256), nb), 256, 0, ctx->stream>>>(
+                      P0.get(), cb.get(), sig.get(), b, k));
+      DBuf<double> Y0(ctx->pool, (size_t)rows * k * nb), G(ctx->pool, (size_t)skk * nb);
+      DBuf<double> GR(ctx->pool, (size_t)skk * nb), GP(ctx->pool, (size_t)skk * nb);
+      gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, sz, P0.get(), k, sbk, 0.0, Y0.get(), k, (long long)rows * k, nb);
+      gemm(ctx, 1, 0, k, k, rows, 1.0, Y0.get(), k, (long long)rows * k, Y0.get(), k, (long long)rows * k, 0.0,
+           G.get(), k, skk, nb);
+      DBuf<double> ones(ctx->pool, (size_t)k * nb);
+      fill(ctx, ones.get(), 1.0, (long long)k * nb);
+      gram_factor(ctx, G.get(), ones.get(), k, nb, GR.get(), nullptr, GP.get(), nullptr);
+      gemm(ctx, 0, 0, rows, k, k, 1.0, Y0.get(), k, (long long)rows * k, GP.get(), k, skk, 0.0, out.core[j].get(),
+           k, sout, nb);
+      gemm(ctx, 1, 0, k, b, rows, 1.0, out.core[j].get(), k, sout, Z.get(), b, sz, 0.0, T.get(), b, sbk, nb);
+    }
     // next left part: T (k x b) times carriage j+1 as b x (N s)
     const int n1 = x.N[j + 1], c1 = x.r[j + 2];
     const long long szn = (long long)k * n1 * c1;
