@@ -12,16 +12,23 @@
 
 namespace lrfg {
 
-FftPlan make_plan(int N) {
+FftPlan make_plan(int N, int max_radix) {
   FftPlan pl{};
   pl.N = N;
   pl.nst = 0;
   int n = N;
-  // radix 5 first, then 3 (any order is valid), then the remaining primes
-  const int pref[] = {5, 3};
-  for (int p : pref)
-    while (n % p == 0) { pl.radix[pl.nst++] = p; n /= p; }
-  for (int p = 7; n > 1; p += 2) {
+  // register radices first (27, 9 as allowed), then 5, 7, 3, then the remaining primes (generic passes);
+  // the order of the passes does not change the transform
+  const int pref[] = {27, 9, 5, 7, 3};
+  for (int p : pref) {
+    if (p > max_radix) continue;
+    while (n % p == 0) {
+      if (pl.nst >= kMaxStages) fail(LRFG_ENOTSUP, "grid size %d has too many factors", N);
+      pl.radix[pl.nst++] = p;
+      n /= p;
+    }
+  }
+  for (int p = 11; n > 1; p += 2) {
     while (n % p == 0) {
       if (p > kMaxGenericRadix) fail(LRFG_ENOTSUP, "grid size %d has a prime factor %d > %d", N, p, kMaxGenericRadix);
       if (pl.nst >= kMaxStages) fail(LRFG_ENOTSUP, "grid size %d has too many factors", N);
@@ -33,6 +40,7 @@ FftPlan make_plan(int N) {
 }
 
 const Twiddles& twiddles_for(lrfg_ctx* ctx, int N) {
+  LRFG_CUDA(ensure_roots(ctx->device));
   auto it = ctx->twiddles.find(N);
   if (it != ctx->twiddles.end()) return it->second;
   std::vector<double2> h(N);
@@ -88,35 +96,71 @@ static int tile_fibres(lrfg_ctx* ctx, int N, int rows_per_fibre_pair, size_t* sm
 // complex fibres
 // ----------------------------------------------------------------------------------------------------
 template <int SIGN, typename V>
-__global__ void __launch_bounds__(256) fft_fibres_kernel(const V* in, V* out, long long outer, int N, long long inner,
+__global__ void __launch_bounds__(256, 3) fft_fibres_kernel(const V* in, V* out, long long outer, int N, long long inner,
                                                          int TF, FftPlan pl, const V* __restrict__ Wg) {
   extern __shared__ __align__(16) unsigned char smraw_fib[];
   V* sm = (V*)smraw_fib;
   V* W = sm;
   V* a = sm + 2 * N;
   V* b = a + (size_t)TF * N;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
   const long long nfib = outer * inner;
   const long long g0 = (long long)blockIdx.x * TF;
   const int nf = (int)min((long long)TF, nfib - g0);
   const int total = nf * N;
   const bool across = inner >= TF;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int f, n;
-    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
-    long long g = g0 + f;
-    long long o = g / inner, i = g - o * inner;
-    a[(size_t)f * N + n] = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
+  if (across) {
+    // thread -> one fibre f of the tile and every step-th element of it: neighbouring threads take
+    // neighbouring fibres (contiguous addresses); all index division happens once per thread
+    const int step = blockDim.x / nf;
+    const int f = threadIdx.x % nf, n0 = threadIdx.x / nf;
+    const long long g = g0 + f;
+    const long long o = g / inner, i = g - o * inner;
+    const V* src = in + (size_t)o * N * (size_t)inner + (size_t)i;
+    if (n0 < step)
+      for (int n = n0; n < N; n += step) cp_async<sizeof(V)>(a + (size_t)f * N + n, src + (size_t)n * inner);
+  } else {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int f = small_div(t, N, 1.0f / (float)N), n = t - f * N;
+      const long long g = g0 + f;
+      const long long o = g / inner, i = g - o * inner;
+      cp_async<sizeof(V)>(a + (size_t)f * N + n, in + ((size_t)o * N + n) * (size_t)inner + (size_t)i);
+    }
   }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
+  cp_async_wait_all();
   __syncthreads();
   V* res = stockham_rows<SIGN>(a, b, nf, N, pl, (const V*)W);
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int f, n;
-    if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
-    long long g = g0 + f;
-    long long o = g / inner, i = g - o * inner;
-    out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = res[(size_t)f * N + n];
+  if (across) {
+    const int step = blockDim.x / nf;
+    const int f = threadIdx.x % nf, n0 = threadIdx.x / nf;
+    const long long g = g0 + f;
+    const long long o = g / inner, i = g - o * inner;
+    V* dst = out + (size_t)o * N * (size_t)inner + (size_t)i;
+    if (n0 < step)
+      for (int n = n0; n < N; n += step) dst[(size_t)n * inner] = res[(size_t)f * N + n];
+  } else {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int f = small_div(t, N, 1.0f / (float)N), n = t - f * N;
+      const long long g = g0 + f;
+      const long long o = g / inner, i = g - o * inner;
+      out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = res[(size_t)f * N + n];
+    }
   }
+}
+
+// Tile for the complex fibre FFT: whole 128-byte segments along the contiguous index (TF * sizeof(V) >=
+// 128) and at most 72 KB of shared memory, so that three blocks share an SM and one block's transform
+// overlaps the others' loads and stores.
+static int tile_complex(lrfg_ctx* ctx, int N, size_t elem, size_t* smem_out) {
+  const long long row = (long long)N * (long long)elem;
+  long long limit = 72 * 1024;
+  const long long tf_min = std::max<long long>(1, 128 / (long long)elem);
+  if (2 * row + 2 * tf_min * row > limit) limit = std::min<long long>(ctx->max_smem_optin, 200 * 1024);
+  long long tf = (limit - 2 * row) / (2 * row);
+  tf = std::max<long long>(1, std::min<long long>(tf, 32));
+  if (tf > tf_min) tf = (tf / tf_min) * tf_min;
+  *smem_out = (size_t)(2 * row + 2 * tf * row);
+  return (int)tf;
 }
 
 template <typename V>
@@ -125,10 +169,10 @@ void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long
   LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fft length must be odd (got %d)", N);
   LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
   if (outer == 0 || inner == 0) return;
-  FftPlan pl = make_plan(N);
+  FftPlan pl = make_plan(N, plan_radix<V>());
   const V* W = twiddle_table<R>(ctx, N);
   size_t smem;
-  int TF = tile_fibres(ctx, N, 1, &smem, sizeof(V));
+  int TF = tile_complex(ctx, N, sizeof(V), &smem);
   long long nfib = outer * inner;
   long long blocks = (nfib + TF - 1) / TF;
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
@@ -211,7 +255,7 @@ void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long oute
   LRFG_REQUIRE(kind == LRFG_MUL_IDENTITY || kind == LRFG_MUL_DERIV || kind == LRFG_MUL_GAUSS,
                "unknown multiplier %d", kind);
   if (outer == 0 || inner == 0) return;
-  FftPlan pl = make_plan(N);
+  FftPlan pl = make_plan(N, plan_radix<double2>());
   const Twiddles& tw = twiddles_for(ctx, N);
   size_t smem;
   int TF = tile_fibres(ctx, N, 2, &smem);
@@ -287,7 +331,7 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
                        int N, long long inner, const double* t, const double* scale, int nm) {
   LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
   if (outer == 0 || inner == 0 || nm == 0) return;
-  FftPlan pl = make_plan(N);
+  FftPlan pl = make_plan(N, plan_radix<double2>());
   const Twiddles& tw = twiddles_for(ctx, N);
   size_t limit = 100 * 1024;
   if (N > 300) limit = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);

@@ -34,11 +34,12 @@ FullGrid make_grid(int d, const int* N) {
 // real rows -> half spectra (forward), optional pre-multiplication by a coefficient
 // ------------------------------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) r2c_rows_kernel(const R* __restrict__ in, const R* __restrict__ coef, R scale,
+__global__ void __launch_bounds__(256, 3) r2c_rows_kernel(const R* __restrict__ in, const R* __restrict__ coef, R scale,
                                                        typename CplxOf<R>::T* __restrict__ out, long long rows, int N,
                                                        int H, int TF, FftPlan pl,
                                                        const typename CplxOf<R>::T* __restrict__ Wg) {
   using V = typename CplxOf<R>::T;
+  const float invN = 1.0f / (float)N, invH = 1.0f / (float)H;
   extern __shared__ __align__(16) unsigned char smraw_r2c[];
   V* sm = (V*)smraw_r2c;
   V* W = sm;
@@ -50,19 +51,36 @@ __global__ void __launch_bounds__(256) r2c_rows_kernel(const R* __restrict__ in,
   const int nrow = min(nr, TF);
   for (int t = threadIdx.x; t < nrow * N; t += blockDim.x) a[t] = mkc<V>(R(0), R(0));
   __syncthreads();
-  for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
-    int f = t / N, n = t - (t / N) * N;
-    size_t gi = (size_t)(r0 + f) * N + n;
-    R v = in[gi];
-    if (coef) v *= coef[gi];
-    v *= scale;
-    if (f < TF) a[(size_t)f * N + n].x = v; else a[(size_t)(f - TF) * N + n].y = v;
+  // the tile's rows are contiguous: issue kU loads per thread before using any of them
+  {
+    constexpr int kU = 8;
+    const R* src = in + (size_t)r0 * N;
+    const R* cs = coef ? coef + (size_t)r0 * N : nullptr;
+    const int total = nr * N;
+    for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+      R v[kU], c[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        v[u] = t < total ? src[t] : R(0);
+        c[u] = (cs && t < total) ? cs[t] : R(1);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        if (t < total) {
+          const int f = small_div(t, N, invN), n = t - f * N;
+          const R x = v[u] * c[u] * scale;
+          if (f < TF) a[(size_t)f * N + n].x = x; else a[(size_t)(f - TF) * N + n].y = x;
+        }
+      }
+    }
   }
   __syncthreads();
   V* Z = stockham_rows<-1>(a, b, nrow, N, pl, (const V*)W);
   // split: X[k] = (Z[k] + conj Z[N-k]) / 2,  Y[k] = (Z[k] - conj Z[N-k]) / (2i)
   for (int t = threadIdx.x; t < nr * H; t += blockDim.x) {
-    int f = t / H, k = t - (t / H) * H;
+    const int f = small_div(t, H, invH), k = t - f * H;
     int row = f < TF ? f : f - TF;
     V z = Z[(size_t)row * N + k];
     V zc = Z[(size_t)row * N + ((N - k) % N)];
@@ -75,11 +93,12 @@ __global__ void __launch_bounds__(256) r2c_rows_kernel(const R* __restrict__ in,
 
 // half spectra -> real rows (inverse, unnormalised), optional post-multiplication by a coefficient
 template <typename R>
-__global__ void __launch_bounds__(256) c2r_rows_kernel(const typename CplxOf<R>::T* __restrict__ in,
+__global__ void __launch_bounds__(256, 3) c2r_rows_kernel(const typename CplxOf<R>::T* __restrict__ in,
                                                        const R* __restrict__ coef, R scale, R* __restrict__ out,
                                                        long long rows, int N, int H, int TF, FftPlan pl,
                                                        const typename CplxOf<R>::T* __restrict__ Wg) {
   using V = typename CplxOf<R>::T;
+  const float invN = 1.0f / (float)N;
   extern __shared__ __align__(16) unsigned char smraw_c2r[];
   V* sm = (V*)smraw_c2r;
   V* W = sm;
@@ -91,24 +110,41 @@ __global__ void __launch_bounds__(256) c2r_rows_kernel(const typename CplxOf<R>:
   const int nrow = min(nr, TF);
   for (int t = threadIdx.x; t < nrow * N; t += blockDim.x) a[t] = mkc<V>(R(0), R(0));
   __syncthreads();
-  // Z[k] = X[k] + i Y[k] over the full range, X[N-k] = conj X[k]; one thread per (row, k)
-  for (int t = threadIdx.x; t < nrow * N; t += blockDim.x) {
-    int row = t / N, k = t - (t / N) * N;
-    V z = mkc<V>(R(0), R(0));
-    for (int half = 0; half < 2; ++half) {
-      int f = row + half * TF;
-      if (f >= nr) break;
-      V x;
-      if (k < H) x = in[(size_t)(r0 + f) * H + k];
-      else { x = in[(size_t)(r0 + f) * H + (N - k)]; x.y = -x.y; }
-      if (half == 0) { z.x += x.x; z.y += x.y; } else { z.x -= x.y; z.y += x.x; }
+  // Z[k] = X[k] + i Y[k] over the full range, X[N-k] = conj X[k]; one thread per (row, k), kU (row, k)
+  // pairs per thread loaded before any is used
+  {
+    constexpr int kU = 4;
+    const int total = nrow * N;
+    for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+      V x0[kU], x1[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        x0[u] = mkc<V>(R(0), R(0));
+        x1[u] = mkc<V>(R(0), R(0));
+        if (t < total) {
+          const int row = small_div(t, N, invN), k = t - row * N;
+          const int kk = k < H ? k : N - k;
+          x0[u] = in[(size_t)(r0 + row) * H + kk];
+          if (row + TF < nr) x1[u] = in[(size_t)(r0 + row + TF) * H + kk];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        if (t < total) {
+          const int row = small_div(t, N, invN), k = t - row * N;
+          V p = x0[u], q = x1[u];
+          if (k >= H) { p.y = -p.y; q.y = -q.y; }
+          a[(size_t)row * N + k] = mkc<V>(p.x - q.y, p.y + q.x);
+        }
+      }
     }
-    a[(size_t)row * N + k] = z;
   }
   __syncthreads();
   V* Z = stockham_rows<1>(a, b, nrow, N, pl, (const V*)W);
   for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
-    int f = t / N, n = t - (t / N) * N;
+    const int f = small_div(t, N, invN), n = t - f * N;
     int row = f < TF ? f : f - TF;
     V z = Z[(size_t)row * N + n];
     R v = (f < TF ? z.x : z.y) * scale;
@@ -121,7 +157,8 @@ __global__ void __launch_bounds__(256) c2r_rows_kernel(const typename CplxOf<R>:
 template <typename R>
 static int row_tile(lrfg_ctx* ctx, int N, size_t* smem) {
   using V = typename CplxOf<R>::T;
-  size_t limit = 100 * 1024;
+  // at most 72 KB for N <= 300, so that three blocks share an SM
+  size_t limit = 72 * 1024;
   if (N > 300) limit = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);
   long long per = 2LL * N * (long long)sizeof(V);
   long long tf = ((long long)limit - 2LL * N * (long long)sizeof(V)) / per;
@@ -135,7 +172,8 @@ void full_forward(lrfg_ctx* ctx, const FullGrid& g, const R* real_in, const R* c
                   typename CplxOf<R>::T* half_out) {
   using V = typename CplxOf<R>::T;
   const int N = g.N[g.d - 1];
-  FftPlan pl = make_plan(N);
+  FftPlan pl = make_plan(N, plan_radix<V>());
+  LRFG_CUDA(ensure_roots(ctx->device));
   const V* W = twiddle_table<R>(ctx, N);
   size_t smem;
   int TF = row_tile<R>(ctx, N, &smem);
@@ -166,7 +204,8 @@ void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_
     fft_fibres(ctx, half_inout, half_inout, outer, g.N[ax], inner, 1);
   }
   const int N = g.N[g.d - 1];
-  FftPlan pl = make_plan(N);
+  FftPlan pl = make_plan(N, plan_radix<V>());
+  LRFG_CUDA(ensure_roots(ctx->device));
   const V* W = twiddle_table<R>(ctx, N);
   size_t smem;
   int TF = row_tile<R>(ctx, N, &smem);

@@ -7,7 +7,11 @@
 namespace lrfg {
 
 // ---- fft.cu -------------------------------------------------------------------------------------
-FftPlan make_plan(int N);
+// passes for length N with register radices up to max_radix (27 for FP32 data, 9 for FP64, whose
+// larger register footprint would limit occupancy)
+FftPlan make_plan(int N, int max_radix);
+template <typename V>
+constexpr int plan_radix() { return sizeof(V) == sizeof(float2) ? 27 : 9; }
 // device twiddle table W[j] = exp(-2 pi i j / N) in FP64 (double) or rounded to FP32 (float)
 template <typename R>
 const typename CplxOf<R>::T* twiddle_table(lrfg_ctx* ctx, int N);
