@@ -159,6 +159,8 @@ struct lrfg_problem {
   FullGrid g{};
   DBuf<double2> wc;          // FULL workspace: one half spectrum
   DBuf<double> wr;           // FULL workspace: one real grid
+  DBuf<double> inv64;        // FULL: reciprocal tables of k.k (the grid g points at them)
+  DBuf<float> inv32;
   // LRFG_MIXED (FULL only): FP32 copies of the coefficient and FP32 workspaces
   DBuf<float> a_full_f;
   DBuf<float2> wcf;
@@ -454,11 +456,13 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
   const FullGrid& g = P->g;
   const long long n = g.n_half;
   DBuf<V> u(ctx->pool, n), r(ctx->pool, n), z(ctx->pool, n), p(ctx->pool, n), q(ctx->pool, n);
-  DBuf<double> s(ctx->pool, 4);  // rz, pq, zz, rz_new
+  DBuf<double> s(ctx->pool, 6);  // rz, pq, zz, rz_new, alpha, beta
   double* d_rz = s.get();
   double* d_pq = s.get() + 1;
   double* d_zz = s.get() + 2;
   double* d_rzn = s.get() + 3;
+  double* d_alpha = s.get() + 4;
+  double* d_beta = s.get() + 5;
   LRFG_CUDA(cudaMemsetAsync(u.get(), 0, sizeof(V) * n, ctx->stream));
   full_rhs<R>(P, E, r.get(), 0);
   half_precond(ctx, g, (const V*)r.get(), z.get());
@@ -475,8 +479,8 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
   while (nb > 0.0 && it < P->opts.maxit) {
     full_apply<R>(P, p.get(), q.get(), 0);
     ++applies;
-    half_dot(ctx, g, (const V*)p.get(), (const V*)q.get(), d_pq);
-    pcg_update(ctx, g, u.get(), r.get(), (const V*)p.get(), (const V*)q.get(), z.get(), d_rz, d_pq);
+    half_dot(ctx, g, (const V*)p.get(), (const V*)q.get(), d_pq, d_rz, d_alpha, 1);  // alpha = rz / pq
+    pcg_update(ctx, g, u.get(), r.get(), (const V*)p.get(), (const V*)q.get(), z.get(), (const double*)d_alpha);
     half_dot(ctx, g, (const V*)z.get(), (const V*)z.get(), d_zz);
     ++it;
     double zz = 0.0;
@@ -484,8 +488,8 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     rel = std::sqrt(std::max(zz, 0.0)) / nb;
     if (rel <= P->opts.tol) break;
-    half_dot(ctx, g, (const V*)r.get(), (const V*)z.get(), d_rzn);
-    pcg_direction(ctx, g, p.get(), (const V*)z.get(), d_rzn, d_rz);
+    half_dot(ctx, g, (const V*)r.get(), (const V*)z.get(), d_rzn, d_rz, d_beta, 2);  // beta = rz_new / rz
+    pcg_direction(ctx, g, p.get(), (const V*)z.get(), (const double*)d_beta);
     LRFG_CUDA(cudaMemcpyAsync(d_rz, d_rzn, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   }
   res->iters = it;
@@ -867,6 +871,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     }
     if (opts->fmt == LRFG_FULL) {
       P->g = make_grid(P->d, P->N);
+      make_inv_tables(ctx, P->g, P->inv64, P->inv32);
       P->wc = DBuf<double2>(ctx->pool, P->g.n_half);
       P->wr = DBuf<double>(ctx->pool, P->g.n_real);
       if (P->opts.prec == LRFG_MIXED) {

@@ -223,123 +223,209 @@ template void full_inverse<double>(lrfg_ctx*, const FullGrid&, double2*, const d
 template void full_inverse<float>(lrfg_ctx*, const FullGrid&, float2*, const float*, float, float*);
 
 // ------------------------------------------------------------------------------------------------
-// pointwise Fourier multipliers on the half spectrum (multipliers formed in FP64, applied in R)
+// pointwise Fourier multipliers on the half spectrum.  Launch map: blockIdx.x = row (all indices but
+// the last), blockIdx.y * blockDim.x + threadIdx.x = k_last, so a thread finds its frequencies without
+// per-element division.  Multipliers are formed in the storage precision R from R-rounded constants;
+// 1/(k.k) comes from a table of exactly rounded reciprocals (no per-element division).
 // ------------------------------------------------------------------------------------------------
-struct KIndex {
-  int d, N0, N1, N2, H;
+struct RowMap {
+  int d, N0, N1, H;
 };
 
-__device__ __forceinline__ void kvec(long long t, const KIndex& ki, int* k) {
-  int kl = (int)(t % ki.H);
-  long long rest = t / ki.H;
-  if (ki.d == 3) {
-    int i1 = (int)(rest % ki.N1), i0 = (int)(rest / ki.N1);
-    k[0] = freq_of(i0, ki.N0);
-    k[1] = freq_of(i1, ki.N1);
-    k[2] = kl;
-  } else {
-    k[0] = freq_of((int)rest, ki.N0);
-    k[1] = kl;
-    k[2] = 0;
-  }
+static RowMap rowmap(const FullGrid& g) {
+  RowMap m;
+  m.d = g.d;
+  m.N0 = g.N[0];
+  m.N1 = g.d == 3 ? g.N[1] : 1;
+  m.H = g.H;
+  return m;
 }
 
-// out = in * (2 pi i k_alpha) * scale
-template <typename V>
-__global__ void mul_grad_kernel(const V* __restrict__ in, V* out, long long n, KIndex ki, int alpha, double scale) {
-  using R = typename RealOf<V>::T;
-  const double two_pi = 6.283185307179586476925286766559;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    int k[3];
-    kvec(t, ki, k);
-    const R f = (R)(two_pi * (double)k[alpha] * scale);
-    V v = in[t];
-    out[t] = mkc<V>(-v.y * f, v.x * f);
+static dim3 row_block(const FullGrid& g) { return dim3((unsigned)std::min(256, ((g.H + 31) / 32) * 32)); }
+static dim3 row_grid(const FullGrid& g) {
+  const unsigned bx = row_block(g).x;
+  return dim3((unsigned)g.rows, (unsigned)((g.H + bx - 1) / bx));
+}
+
+// frequencies of (row, kl); returns false past the end of the row
+__device__ __forceinline__ bool row_k(const RowMap& m, int& k0, int& k1, int& k2, size_t& t) {
+  const int row = blockIdx.x;
+  const int kl = blockIdx.y * blockDim.x + threadIdx.x;
+  if (kl >= m.H) return false;
+  if (m.d == 3) {
+    const int i0 = row / m.N1, i1 = row - i0 * m.N1;
+    k0 = freq_of(i0, m.N0);
+    k1 = freq_of(i1, m.N1);
+    k2 = kl;
+  } else {
+    k0 = freq_of(row, m.N0);
+    k1 = kl;
+    k2 = 0;
   }
+  t = (size_t)row * m.H + kl;
+  return true;
+}
+
+// out = in * (2 pi i k_alpha) * scale   (c2 = 2 pi scale, rounded to R)
+template <typename V>
+__global__ void mul_grad_kernel(const V* __restrict__ in, V* out, RowMap m, int alpha,
+                                typename RealOf<V>::T c2) {
+  using R = typename RealOf<V>::T;
+  int k[3];
+  size_t t;
+  if (!row_k(m, k[0], k[1], k[2], t)) return;
+  const R f = c2 * (R)k[alpha];
+  const V v = in[t];
+  out[t] = mkc<V>(-v.y * f, v.x * f);
 }
 
 // acc = (init ? 0 : acc) + in * (-2 pi i k_alpha) * scale; if precond, then acc /= k.k (0 at k=0)
 template <typename V>
-__global__ void acc_div_kernel(const V* __restrict__ in, V* acc, long long n, KIndex ki, int alpha, double scale,
-                               int init, int precond) {
+__global__ void acc_div_kernel(const V* __restrict__ in, V* acc, RowMap m, int alpha, typename RealOf<V>::T c2,
+                               int init, int precond, const typename RealOf<V>::T* __restrict__ inv_kk) {
   using R = typename RealOf<V>::T;
-  const double two_pi = 6.283185307179586476925286766559;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    int k[3];
-    kvec(t, ki, k);
-    const R f = (R)(-two_pi * (double)k[alpha] * scale);
-    V v = in[t];
-    V r = mkc<V>(-v.y * f, v.x * f);
-    if (!init) { V o = acc[t]; r.x += o.x; r.y += o.y; }
-    if (precond) {
-      const int kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-      const R s = kk > 0 ? (R)(1.0 / (double)kk) : R(0);
-      r.x *= s;
-      r.y *= s;
-    }
-    acc[t] = r;
+  int k[3];
+  size_t t;
+  if (!row_k(m, k[0], k[1], k[2], t)) return;
+  const R f = -c2 * (R)k[alpha];
+  const V v = in[t];
+  V r = mkc<V>(-v.y * f, v.x * f);
+  if (!init) {
+    const V o = acc[t];
+    r.x += o.x;
+    r.y += o.y;
   }
+  if (precond) {
+    const R s = inv_kk[k[0] * k[0] + k[1] * k[1] + k[2] * k[2]];
+    r.x *= s;
+    r.y *= s;
+  }
+  acc[t] = r;
 }
 
 template <typename V>
-__global__ void precond_kernel(const V* __restrict__ in, V* out, long long n, KIndex ki) {
+__global__ void precond_kernel(const V* __restrict__ in, V* out, RowMap m,
+                               const typename RealOf<V>::T* __restrict__ inv_kk) {
   using R = typename RealOf<V>::T;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    int k[3];
-    kvec(t, ki, k);
-    const int kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-    const R s = kk > 0 ? (R)(1.0 / (double)kk) : R(0);
-    V v = in[t];
-    out[t] = mkc<V>(v.x * s, v.y * s);
+  int k[3];
+  size_t t;
+  if (!row_k(m, k[0], k[1], k[2], t)) return;
+  const R s = inv_kk[k[0] * k[0] + k[1] * k[1] + k[2] * k[2]];
+  const V v = in[t];
+  out[t] = mkc<V>(v.x * s, v.y * s);
+}
+
+template <typename R> static const R* inv_table(const FullGrid& g);
+template <> const double* inv_table<double>(const FullGrid& g) { return g.inv_kk64; }
+template <> const float* inv_table<float>(const FullGrid& g) { return g.inv_kk32; }
+
+__global__ void inv_table_kernel(double* t64, float* t32, int n) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    const double v = m > 0 ? 1.0 / (double)m : 0.0;
+    t64[m] = v;
+    t32[m] = m > 0 ? 1.0f / (float)m : 0.0f;
   }
 }
 
-static KIndex kindex(const FullGrid& g) {
-  KIndex ki;
-  ki.d = g.d;
-  ki.N0 = g.N[0];
-  ki.N1 = g.d == 3 ? g.N[1] : 1;
-  ki.N2 = g.d == 3 ? g.N[2] : g.N[1];
-  ki.H = g.H;
-  return ki;
+void make_inv_tables(lrfg_ctx* ctx, FullGrid& g, DBuf<double>& t64, DBuf<float>& t32) {
+  long long kmax = 0;
+  for (int j = 0; j < g.d; ++j) kmax += (long long)((g.N[j] - 1) / 2) * ((g.N[j] - 1) / 2);
+  const int n = (int)kmax + 1;
+  t64 = DBuf<double>(ctx->pool, n);
+  t32 = DBuf<float>(ctx->pool, n);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, n, 12.0 * n,
+              inv_table_kernel<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, ctx->stream>>>(t64.get(),
+                                                                                                      t32.get(), n));
+  g.inv_kk64 = t64.get();
+  g.inv_kk32 = t32.get();
 }
+
+static double two_pi_times(double scale) { return 6.283185307179586476925286766559 * scale; }
 
 template <typename V>
 void half_mul_grad(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out, int alpha, double scale) {
+  using R = typename RealOf<V>::T;
   LRFG_LAUNCH(ctx, KC_POINTWISE, 2.0 * g.n_half, 2.0 * sizeof(V) * g.n_half,
-              mul_grad_kernel<V><<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, out, g.n_half, kindex(g), alpha,
-                                                                                  scale));
+              mul_grad_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(in, out, rowmap(g), alpha,
+                                                                                 (R)two_pi_times(scale)));
 }
 
 template <typename V>
 void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alpha, double scale, int init,
                   int precond) {
+  using R = typename RealOf<V>::T;
+  LRFG_REQUIRE(!precond || inv_table<R>(g), "reciprocal table missing");
   LRFG_LAUNCH(ctx, KC_POINTWISE, 4.0 * g.n_half, (init ? 2.0 : 3.0) * sizeof(V) * g.n_half,
-              acc_div_kernel<V><<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, acc, g.n_half, kindex(g), alpha,
-                                                                                 scale, init, precond));
+              acc_div_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(
+                  in, acc, rowmap(g), alpha, (R)two_pi_times(scale), init, precond, inv_table<R>(g)));
 }
 
 template <typename V>
 void half_precond(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out) {
+  using R = typename RealOf<V>::T;
+  LRFG_REQUIRE(inv_table<R>(g), "reciprocal table missing");
   LRFG_LAUNCH(ctx, KC_POINTWISE, 2.0 * g.n_half, 2.0 * sizeof(V) * g.n_half,
-              precond_kernel<V><<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(in, out, g.n_half, kindex(g)));
+              precond_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(in, out, rowmap(g), inv_table<R>(g)));
 }
 
 // ------------------------------------------------------------------------------------------------
-// reductions (accumulated in FP64 whatever the storage type): Hermitian-weighted inner product of
-// half spectra, and the A_eff energy density
+// reductions: Hermitian-weighted inner product of half spectra, and the A_eff energy density.
+// FP64 data accumulate in FP64.  FP32 data: each product is split exactly (p + e, e = fma(a, b, -p))
+// and both parts are summed per thread with error-free two-sums (Knuth) in FP32, so the per-thread
+// partial is accurate to ~n eps32^2 of the sum of magnitudes (FP64 class) while the work runs on the
+// FP32 pipe; partials are combined in FP64.
 // ------------------------------------------------------------------------------------------------
-constexpr int kRedBlocks = 304;
+constexpr int kRedBlocks = 1216;  // 8 blocks per SM
+
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
 
 template <typename V>
 __global__ void __launch_bounds__(256) half_dot_kernel(const V* __restrict__ x, const V* __restrict__ y, long long n,
                                                        int H, double* partial) {
   __shared__ double red[8];
   double s = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    V a = x[t], b = y[t];
-    double w = (t % H) == 0 ? 1.0 : 2.0;
-    s += w * ((double)a.x * (double)b.x + (double)a.y * (double)b.y);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int kl = (int)(t % H);
+  const int kstep = (int)(stride % H);
+  if constexpr (sizeof(V) == sizeof(float2)) {
+    // four elements' loads in flight before any is used
+    constexpr int kU = 4;
+    float fs = 0.0f, fc = 0.0f;
+    for (; t < n; t += kU * stride) {
+      V a[kU], b[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long tu = t + u * stride;
+        a[u] = tu < n ? x[tu] : mkc<V>(0.0f, 0.0f);
+        b[u] = tu < n ? y[tu] : mkc<V>(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const float w = kl == 0 ? 1.0f : 2.0f;
+        const float p1 = a[u].x * b[u].x, e1 = fmaf(a[u].x, b[u].x, -p1);
+        const float p2 = a[u].y * b[u].y, e2 = fmaf(a[u].y, b[u].y, -p2);
+        two_sum_acc(fs, fc, w * p1);
+        two_sum_acc(fs, fc, w * p2);
+        fc += w * (e1 + e2);
+        kl += kstep;
+        if (kl >= H) kl -= H;
+      }
+    }
+    s = (double)fs + (double)fc;
+  } else {
+    for (; t < n; t += stride) {
+      const V a = x[t], b = y[t];
+      const double w = kl == 0 ? 1.0 : 2.0;
+      s += w * ((double)a.x * (double)b.x + (double)a.y * (double)b.y);
+      kl += kstep;
+      if (kl >= H) kl -= H;
+    }
   }
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -370,7 +456,10 @@ __global__ void __launch_bounds__(256) energy_kernel(const R* __restrict__ e, co
   }
 }
 
-__global__ void finish_sum_kernel(const double* __restrict__ partial, int n, double* out, int accumulate) {
+// *out (+)= sum of partials; then, if ratio: mode 1 -> *ratio = *aux / *out, mode 2 -> *out / *aux
+// (0 when the divisor is 0): the PCG step lengths, formed once on the device
+__global__ void finish_sum_kernel(const double* __restrict__ partial, int n, double* out, int accumulate,
+                                  const double* aux, double* ratio, int mode) {
   __shared__ double red[8];
   double s = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) s += partial[t];
@@ -380,17 +469,23 @@ __global__ void finish_sum_kernel(const double* __restrict__ partial, int n, dou
   if (threadIdx.x == 0) {
     double v = 0.0;
     for (int i = 0; i < 8; ++i) v += red[i];
-    *out = accumulate ? *out + v : v;
+    v = accumulate ? *out + v : v;
+    *out = v;
+    if (ratio) {
+      const double num = mode == 1 ? *aux : v, den = mode == 1 ? v : *aux;
+      *ratio = den != 0.0 ? num / den : 0.0;
+    }
   }
 }
 
 template <typename V>
-void half_dot(lrfg_ctx* ctx, const FullGrid& g, const V* x, const V* y, double* out_dev) {
+void half_dot(lrfg_ctx* ctx, const FullGrid& g, const V* x, const V* y, double* out_dev, const double* aux,
+              double* ratio, int mode) {
   DBuf<double> partial(ctx->pool, kRedBlocks);
   LRFG_LAUNCH(ctx, KC_REDUCE, 4.0 * g.n_half, 2.0 * sizeof(V) * g.n_half,
               half_dot_kernel<V><<<kRedBlocks, 256, 0, ctx->stream>>>(x, y, g.n_half, g.H, partial.get()));
   LRFG_LAUNCH(ctx, KC_REDUCE, kRedBlocks, kRedBlocks * sizeof(double),
-              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, 0));
+              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, 0, aux, ratio, mode));
 }
 
 template <typename R>
@@ -399,41 +494,38 @@ void energy_sum(lrfg_ctx* ctx, const FullGrid& g, const R* e, const R* a, double
   LRFG_LAUNCH(ctx, KC_REDUCE, 4.0 * g.n_real, 2.0 * sizeof(R) * g.n_real,
               energy_kernel<R><<<kRedBlocks, 256, 0, ctx->stream>>>(e, a, E, g.n_real, partial.get()));
   LRFG_LAUNCH(ctx, KC_REDUCE, kRedBlocks, kRedBlocks * sizeof(double),
-              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, accumulate));
+              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, accumulate, nullptr,
+                                                            nullptr, 0));
 }
 
 // ------------------------------------------------------------------------------------------------
-// PCG vector updates with device FP64 scalars: alpha = num / den
+// PCG vector updates with a device FP64 step length (rounded once to R)
 // ------------------------------------------------------------------------------------------------
 template <typename V>
-__global__ void pcg_update_kernel(V* u, V* r, const V* __restrict__ p, const V* __restrict__ q, V* z, long long n,
-                                  KIndex ki, const double* __restrict__ num, const double* __restrict__ den) {
+__global__ void pcg_update_kernel(V* u, V* r, const V* __restrict__ p, const V* __restrict__ q, V* z, RowMap m,
+                                  const double* __restrict__ alpha_dev,
+                                  const typename RealOf<V>::T* __restrict__ inv_kk) {
   using R = typename RealOf<V>::T;
-  const double ad = (*den != 0.0) ? (*num) / (*den) : 0.0;
-  const R alpha = (R)ad;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    V pv = p[t], qv = q[t], uv = u[t], rv = r[t];
-    uv.x += alpha * pv.x;
-    uv.y += alpha * pv.y;
-    rv.x -= alpha * qv.x;
-    rv.y -= alpha * qv.y;
-    u[t] = uv;
-    r[t] = rv;
-    int k[3];
-    kvec(t, ki, k);
-    const int kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-    const R s = kk > 0 ? (R)(1.0 / (double)kk) : R(0);
-    z[t] = mkc<V>(rv.x * s, rv.y * s);
-  }
+  int k[3];
+  size_t t;
+  if (!row_k(m, k[0], k[1], k[2], t)) return;
+  const R alpha = (R)(*alpha_dev);
+  V pv = p[t], qv = q[t], uv = u[t], rv = r[t];
+  uv.x += alpha * pv.x;
+  uv.y += alpha * pv.y;
+  rv.x -= alpha * qv.x;
+  rv.y -= alpha * qv.y;
+  u[t] = uv;
+  r[t] = rv;
+  const R s = inv_kk[k[0] * k[0] + k[1] * k[1] + k[2] * k[2]];
+  z[t] = mkc<V>(rv.x * s, rv.y * s);
 }
 
-// p = z + (num/den) p
+// p = z + beta p
 template <typename V>
-__global__ void pcg_direction_kernel(V* p, const V* __restrict__ z, long long n, const double* __restrict__ num,
-                                     const double* __restrict__ den) {
+__global__ void pcg_direction_kernel(V* p, const V* __restrict__ z, long long n, const double* __restrict__ beta_dev) {
   using R = typename RealOf<V>::T;
-  const double bd = (*den != 0.0) ? (*num) / (*den) : 0.0;
-  const R beta = (R)bd;
+  const R beta = (R)(*beta_dev);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     V pv = p[t], zv = z[t];
     p[t] = mkc<V>(zv.x + beta * pv.x, zv.y + beta * pv.y);
@@ -441,17 +533,18 @@ __global__ void pcg_direction_kernel(V* p, const V* __restrict__ z, long long n,
 }
 
 template <typename V>
-void pcg_update(lrfg_ctx* ctx, const FullGrid& g, V* u, V* r, const V* p, const V* q, V* z, const double* num,
-                const double* den) {
+void pcg_update(lrfg_ctx* ctx, const FullGrid& g, V* u, V* r, const V* p, const V* q, V* z, const double* alpha) {
+  using R = typename RealOf<V>::T;
+  LRFG_REQUIRE(inv_table<R>(g), "reciprocal table missing");
   LRFG_LAUNCH(ctx, KC_POINTWISE, 10.0 * g.n_half, 7.0 * sizeof(V) * g.n_half,
-              pcg_update_kernel<V><<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(u, r, p, q, z, g.n_half, kindex(g),
-                                                                                    num, den));
+              pcg_update_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(u, r, p, q, z, rowmap(g), alpha,
+                                                                                  inv_table<R>(g)));
 }
 
 template <typename V>
-void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, V* p, const V* z, const double* num, const double* den) {
+void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, V* p, const V* z, const double* beta) {
   LRFG_LAUNCH(ctx, KC_POINTWISE, 4.0 * g.n_half, 3.0 * sizeof(V) * g.n_half,
-              pcg_direction_kernel<V><<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(p, z, g.n_half, num, den));
+              pcg_direction_kernel<V><<<grid1d(ctx, g.n_half), 256, 0, ctx->stream>>>(p, z, g.n_half, beta));
 }
 
 // element-wise conversions between storage precisions (round to nearest)
@@ -477,11 +570,10 @@ void convert(lrfg_ctx* ctx, const A* in, B* out, long long n) {
   template void half_mul_grad<V>(lrfg_ctx*, const FullGrid&, const V*, V*, int, double);                  \
   template void half_acc_div<V>(lrfg_ctx*, const FullGrid&, const V*, V*, int, double, int, int);         \
   template void half_precond<V>(lrfg_ctx*, const FullGrid&, const V*, V*);                                \
-  template void half_dot<V>(lrfg_ctx*, const FullGrid&, const V*, const V*, double*);                    \
+  template void half_dot<V>(lrfg_ctx*, const FullGrid&, const V*, const V*, double*, const double*, double*, int); \
   template void energy_sum<R>(lrfg_ctx*, const FullGrid&, const R*, const R*, double, double*, int);      \
-  template void pcg_update<V>(lrfg_ctx*, const FullGrid&, V*, V*, const V*, const V*, V*, const double*,   \
-                              const double*);                                                             \
-  template void pcg_direction<V>(lrfg_ctx*, const FullGrid&, V*, const V*, const double*, const double*);
+  template void pcg_update<V>(lrfg_ctx*, const FullGrid&, V*, V*, const V*, const V*, V*, const double*);  \
+  template void pcg_direction<V>(lrfg_ctx*, const FullGrid&, V*, const V*, const double*);
 LRFG_FULL_INSTANTIATE(double2, double)
 LRFG_FULL_INSTANTIATE(float2, float)
 template void convert<double, float>(lrfg_ctx*, const double*, float*, long long);

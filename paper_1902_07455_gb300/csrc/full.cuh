@@ -12,9 +12,14 @@ struct FullGrid {
   long long rows;    // product of all but the last size
   long long n_real;  // N_0 ... N_{d-1}
   long long n_half;  // rows * H
+  // exactly rounded 1/m for m = 0..sum_a ((N_a-1)/2)^2 (0 at m = 0): the preconditioner 1/(k.k); set
+  // by make_inv_tables for grids that run the PCG kernels
+  const double* inv_kk64 = nullptr;
+  const float* inv_kk32 = nullptr;
 };
 
 FullGrid make_grid(int d, const int* N);
+void make_inv_tables(lrfg_ctx* ctx, FullGrid& g, DBuf<double>& t64, DBuf<float>& t32);
 // half_out = Phi(scale * coef .* real_in)   (coef may be null); Phi = unnormalised forward DFT
 template <typename R>
 void full_forward(lrfg_ctx* ctx, const FullGrid& g, const R* real_in, const R* coef, R scale,
@@ -31,16 +36,19 @@ void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alp
 template <typename V>
 void half_precond(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out);
 // Hermitian-weighted real inner product over the full spectrum (FP64 accumulation) into a device scalar
+// optional: *ratio = *aux / result (mode 1) or result / *aux (mode 2), 0 for a zero divisor
 template <typename V>
-void half_dot(lrfg_ctx* ctx, const FullGrid& g, const V* x, const V* y, double* out_dev);
+void half_dot(lrfg_ctx* ctx, const FullGrid& g, const V* x, const V* y, double* out_dev, const double* aux = nullptr,
+              double* ratio = nullptr, int mode = 0);
 // out_dev (+)= sum_k a_k (E + e_k)^2 (FP64 accumulation)
 template <typename R>
 void energy_sum(lrfg_ctx* ctx, const FullGrid& g, const R* e, const R* a, double E, double* out_dev, int accumulate);
+// u += alpha p, r -= alpha q, z = P^-1 r (alpha a device scalar)
 template <typename V>
-void pcg_update(lrfg_ctx* ctx, const FullGrid& g, V* u, V* r, const V* p, const V* q, V* z, const double* num,
-                const double* den);
+void pcg_update(lrfg_ctx* ctx, const FullGrid& g, V* u, V* r, const V* p, const V* q, V* z, const double* alpha);
+// p = z + beta p (beta a device scalar)
 template <typename V>
-void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, V* p, const V* z, const double* num, const double* den);
+void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, V* p, const V* z, const double* beta);
 template <typename A, typename B>
 void convert(lrfg_ctx* ctx, const A* in, B* out, long long n);
 
