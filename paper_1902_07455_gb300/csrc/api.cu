@@ -115,6 +115,18 @@ cudaEvent_t take_event(lrfg_ctx* ctx) {
   return e;
 }
 
+void fold_device_work(lrfg_ctx* ctx) {
+  if (!ctx->work_dev) return;
+  double h[2 * KC_COUNT];
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  LRFG_CUDA(cudaMemcpy(h, ctx->work_dev, sizeof(h), cudaMemcpyDeviceToHost));
+  LRFG_CUDA(cudaMemset(ctx->work_dev, 0, sizeof(h)));
+  for (int k = 0; k < KC_COUNT; ++k) {
+    ctx->stats[k].flops += h[2 * k];
+    ctx->stats[k].bytes += h[2 * k + 1];
+  }
+}
+
 void resolve_profile(lrfg_ctx* ctx) {
   if (ctx->pending.empty()) return;
   LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -620,6 +632,8 @@ lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget)
     LRFG_CUDA(cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
     ctx->pool = new DevicePool(budget);
+    LRFG_CUDA(cudaMalloc(&ctx->work_dev, sizeof(double) * 2 * KC_COUNT));
+    LRFG_CUDA(cudaMemset(ctx->work_dev, 0, sizeof(double) * 2 * KC_COUNT));
   });
   if (st != LRFG_OK) {
     delete ctx;
@@ -638,6 +652,7 @@ lrfg_status lrfg_destroy(lrfg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   delete ctx->pool;
+  if (ctx->work_dev) cudaFree(ctx->work_dev);
   for (auto& kv : ctx->twiddles) {
     cudaFree(kv.second.W);
     if (kv.second.Wf) cudaFree(kv.second.Wf);
@@ -674,6 +689,7 @@ lrfg_status lrfg_profile_reset(lrfg_ctx* ctx) {
   if (!ctx) return LRFG_EINVAL;
   return guard(ctx, [&] {
     resolve_profile(ctx);
+    fold_device_work(ctx);
     for (auto& st : ctx->stats) st = KStats{};
   });
 }
@@ -683,6 +699,7 @@ lrfg_status lrfg_profile_read(lrfg_ctx* ctx, int n, long long* launches, double*
   return guard(ctx, [&] {
     LRFG_REQUIRE(n >= 0 && n <= KC_COUNT, "n must be in [0, %d]", (int)KC_COUNT);
     resolve_profile(ctx);
+    fold_device_work(ctx);
     for (int k = 0; k < n; ++k) {
       if (launches) launches[k] = ctx->stats[k].launches;
       if (flops) flops[k] = ctx->stats[k].flops;

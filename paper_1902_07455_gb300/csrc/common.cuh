@@ -153,6 +153,9 @@ struct lrfg_ctx {
   lrfg::KStats stats[lrfg::KC_COUNT];
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;  // (class, (start, stop))
   std::vector<cudaEvent_t> event_pool;
+  // device-side work counters (flops, bytes per class) for kernels whose work depends on data (active
+  // sizes read on the device, e.g. numerical ranks); folded into stats when the profile is read
+  double* work_dev = nullptr;
 };
 
 namespace lrfg {
@@ -189,6 +192,17 @@ class KTimer {
   KClass kc_;
   cudaEvent_t start_ = nullptr;
 };
+
+// the device counter pair (flops, bytes) of class kc
+inline double* work_counter(lrfg_ctx* ctx, KClass kc) { return ctx->work_dev ? ctx->work_dev + 2 * (int)kc : nullptr; }
+// adds its work to stats: kernels with data-dependent sizes, counted once per batch item on the device
+__device__ __forceinline__ void add_work(double* counter, double flops, double bytes) {
+  if (counter) {
+    atomicAdd(counter, flops);
+    atomicAdd(counter + 1, bytes);
+  }
+}
+void fold_device_work(lrfg_ctx* ctx);
 }  // namespace lrfg
 
 // launch a kernel with accounting: LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, kernel<<<...>>>(args));

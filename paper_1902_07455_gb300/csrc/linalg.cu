@@ -9,79 +9,108 @@
 namespace lrfg {
 
 // ------------------------------------------------------------------------------------------------
-// GEMM: TILE x TILE output tile per block (64 or 32), k-step 16, 256 threads with (TILE/16)^2 outputs
-// each (rows ty+16i, columns tx+16j).  Small or long-K products split K across blocks (split-K) and
-// accumulate with atomics into C pre-scaled by beta.
+// GEMM, FP64.  On this part the FP64 pipe (2 FMA/clk/SM) is the bottleneck of every product here, so
+// the kernel is built to waste none of it: a block owns a 64 x 64 output block (clipped to the active
+// sizes, which may be read from the device), each of its 256 threads owns up to 16 outputs of that block
+// exactly (no padded tile rows or columns are computed), operands are staged through shared memory in
+// k-steps of 32, and long K is split across blocks (split-K, atomics into C pre-scaled by beta) until
+// about two blocks per SM are busy.  An output costs two shared-memory reads per FMA, far below the
+// shared-memory bandwidth at the FP64 rate.
 // ------------------------------------------------------------------------------------------------
-constexpr int GK = 16;
+constexpr int GB = 64;  // output block edge
+constexpr int GK = 32;  // k-step
 
-template <bool TA, bool TB, int TILE>
+// pk[j] = (row << 16) | column of output j within the block
+template <int NR>
+__device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[GB + 1], const double (*Bs)[GB + 1],
+                                              const int* pk, int kk_end) {
+  for (int kk = 0; kk < kk_end; ++kk) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[j] = fma(As[kk][pk[j] >> 16], Bs[kk][pk[j] & 0xffff], acc[j]);
+  }
+}
+
+// dynM / dynN (optional, per batch item): the product is computed only for rows < dynM[b] * mulM and
+// columns < dynN[b] * mulN (data-dependent active sizes, e.g. numerical ranks); the rest of C is not
+// written (beyond the zeroing of a split-K product).
+template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                     int lda, long long sA, const double* __restrict__ B, int ldb,
                                                     long long sB, double beta, double* C, int ldc, long long sC,
-                                                    int splits, int kchunk) {
-  constexpr int MT = TILE / 16;
-  __shared__ double As[GK][TILE + 1];
-  __shared__ double Bs[GK][TILE + 1];
-  const int batch = blockIdx.z / splits, split = blockIdx.z - (blockIdx.z / splits) * splits;
+                                                    int splits, int kchunk, const int* __restrict__ dynM, int mulM,
+                                                    const int* __restrict__ dynN, int mulN, double* work) {
+  __shared__ double As[GK][GB + 1];
+  __shared__ double Bs[GK][GB + 1];
+  const int batch = blockIdx.z;
+  const int bm = blockIdx.y / splits, split = blockIdx.y - (blockIdx.y / splits) * splits;
+  const int bn = blockIdx.x;
   A += (size_t)batch * sA;
   B += (size_t)batch * sB;
   C += (size_t)batch * sC;
-  const int m0 = blockIdx.y * TILE, n0 = blockIdx.x * TILE;
+  if (dynM) M = min(M, dynM[batch] * mulM);
+  if (dynN) N = min(N, dynN[batch] * mulN);
+  if (work && bm == 0 && bn == 0 && split == 0 && threadIdx.x == 0)
+    add_work(work, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+  const int m0 = bm * GB, n0 = bn * GB;
+  const int Mb = min(GB, M - m0), Nb = min(GB, N - n0);
+  if (Mb <= 0 || Nb <= 0) return;
   const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[MT][MT];
+  // this thread's outputs o = t + 256 j < Mb Nb, as (row, column) within the block
+  const int tot = Mb * Nb;
+  const int nact = tot > (int)threadIdx.x ? min(16, (tot - (int)threadIdx.x + 255) / 256) : 0;
+  int pk[16];
+  double acc[16];
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < MT; ++j) acc[i][j] = 0.0;
+  for (int j = 0; j < 16; ++j) {
+    const int o = threadIdx.x + 256 * j;
+    const int m = o / Nb;
+    pk[j] = j < nact ? (m << 16) | (o - m * Nb) : 0;
+    acc[j] = 0.0;
+  }
   for (int k0 = kbeg; k0 < kend; k0 += GK) {
-    for (int e = threadIdx.x; e < TILE * GK; e += 256) {
+    const int kc = min(GK, kend - k0);
+    for (int e = threadIdx.x; e < GB * GK; e += 256) {
       int mm, kk;
-      if (TA) { mm = e % TILE; kk = e / TILE; } else { kk = e % GK; mm = e / GK; }
-      int gm = m0 + mm, gk = k0 + kk;
+      if (TA) { mm = e % GB; kk = e / GB; } else { kk = e % GK; mm = e / GK; }
       double v = 0.0;
-      if (gm < M && gk < kend) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+      if (mm < Mb && kk < kc) v = TA ? A[(size_t)(k0 + kk) * lda + m0 + mm] : A[(size_t)(m0 + mm) * lda + k0 + kk];
       As[kk][mm] = v;
     }
-    for (int e = threadIdx.x; e < TILE * GK; e += 256) {
+    for (int e = threadIdx.x; e < GB * GK; e += 256) {
       int nn, kk;
-      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % TILE; kk = e / TILE; }
-      int gn = n0 + nn, gk = k0 + kk;
+      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % GB; kk = e / GB; }
       double v = 0.0;
-      if (gn < N && gk < kend) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+      if (nn < Nb && kk < kc) v = TB ? B[(size_t)(n0 + nn) * ldb + k0 + kk] : B[(size_t)(k0 + kk) * ldb + n0 + nn];
       Bs[kk][nn] = v;
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      double a[MT], b[MT];
-#pragma unroll
-      for (int i = 0; i < MT; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < MT; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    switch (nact) {
+      case 16: gemm_fma_rows<16>(acc, As, Bs, pk, kc); break;
+      case 15: gemm_fma_rows<15>(acc, As, Bs, pk, kc); break;
+      case 14: gemm_fma_rows<14>(acc, As, Bs, pk, kc); break;
+      case 13: gemm_fma_rows<13>(acc, As, Bs, pk, kc); break;
+      case 12: gemm_fma_rows<12>(acc, As, Bs, pk, kc); break;
+      case 11: gemm_fma_rows<11>(acc, As, Bs, pk, kc); break;
+      case 10: gemm_fma_rows<10>(acc, As, Bs, pk, kc); break;
+      case 9: gemm_fma_rows<9>(acc, As, Bs, pk, kc); break;
+      case 8: gemm_fma_rows<8>(acc, As, Bs, pk, kc); break;
+      case 7: gemm_fma_rows<7>(acc, As, Bs, pk, kc); break;
+      case 6: gemm_fma_rows<6>(acc, As, Bs, pk, kc); break;
+      case 5: gemm_fma_rows<5>(acc, As, Bs, pk, kc); break;
+      case 4: gemm_fma_rows<4>(acc, As, Bs, pk, kc); break;
+      case 3: gemm_fma_rows<3>(acc, As, Bs, pk, kc); break;
+      case 2: gemm_fma_rows<2>(acc, As, Bs, pk, kc); break;
+      case 1: gemm_fma_rows<1>(acc, As, Bs, pk, kc); break;
+      default: break;
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < MT; ++i) {
-    int gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < MT; ++j) {
-      int gn = n0 + tx + 16 * j;
-      if (gn >= N) continue;
-      double* c = C + (size_t)gm * ldc + gn;
-      if (splits > 1) {
-        atomicAdd(c, alpha * acc[i][j]);
-      } else {
-        *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
-      }
-    }
+  for (int j = 0; j < 16; ++j) {
+    if (j >= nact) break;
+    double* c = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
+    if (splits > 1) atomicAdd(c, alpha * acc[j]);
+    else *c = (beta == 0.0) ? alpha * acc[j] : alpha * acc[j] + beta * (*c);
   }
 }
 
@@ -96,29 +125,16 @@ __global__ void scale_matrix_kernel(double* C, int M, int N, int ldc, long long 
   }
 }
 
-template <int TILE>
-static void gemm_launch(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A,
-                        int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc,
-                        long long sC, int batch, int splits, int kchunk, double flops, double bytes) {
-  const int tm = (M + TILE - 1) / TILE, tn = (N + TILE - 1) / TILE;
-  dim3 grid(tn, tm, batch * splits);
-  if (!transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false, TILE><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
-  else if (transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false, TILE><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
-  else if (!transA && transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true, TILE><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
-  else
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true, TILE><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk));
-}
-
 void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
           long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
           int batch) {
+  gemm_dyn(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, nullptr, 1,
+           nullptr, 1);
+}
+
+void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+              long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+              int batch, const int* dynM, int mulM, const int* dynN, int mulN) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) {
     LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
@@ -126,34 +142,41 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
                     C, M, N, ldc, sC, batch, beta));
     return;
   }
-  // small outputs use 32x32 tiles (more blocks); K is split until about two blocks per SM are busy,
-  // with at least 64 of K per block
-  const int tile = ((long long)M * N <= 256LL * 256LL) ? 32 : 64;
-  const int tm = (M + tile - 1) / tile, tn = (N + tile - 1) / tile;
-  const long long tiles = (long long)tm * tn * batch;
+  LRFG_REQUIRE(batch < 65536, "gemm batch too large");
+  const int bmn = (M + GB - 1) / GB, bnn = (N + GB - 1) / GB;
+  // blocks expected to be active: the static count, or for data-dependent sizes a quarter of it (the
+  // numerical ranks are typically well below their bounds), at least one per item
+  long long active = (long long)bmn * bnn * batch;
+  if (dynM || dynN) active = std::max<long long>(batch, active / 4);
   const int target = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
   int splits = 1;
-  if (tiles < target) {
-    splits = (int)std::min<long long>((target + tiles - 1) / tiles, std::max(1, K / 64));
-    if (splits < 1) splits = 1;
-  }
+  if (active < target) splits = (int)std::min<long long>((target + active - 1) / active, std::max(1, K / GK));
   int kchunk = (K + splits - 1) / splits;
   kchunk = ((kchunk + GK - 1) / GK) * GK;
   splits = (K + kchunk - 1) / kchunk;
-  LRFG_REQUIRE((long long)batch * splits < 65535, "gemm batch too large");
+  LRFG_REQUIRE((long long)bmn * splits < 65536, "gemm too many row blocks x splits");
   if (splits > 1) {
     LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
                 scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
                     C, M, N, ldc, sC, batch, beta));
   }
-  const double flops = 2.0 * M * N * (double)K * batch;
-  const double bytes = sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
-  if (tile == 32)
-    gemm_launch<32>(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, splits,
-                    kchunk, flops, bytes);
+  // products with data-dependent sizes count their work on the device
+  double* work = (dynM || dynN) ? work_counter(ctx, KC_GEMM) : nullptr;
+  const double flops = work ? 0.0 : 2.0 * M * N * (double)K * batch;
+  const double bytes = work ? 0.0 : sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
+  dim3 grid(bnn, bmn * splits, batch);
+  if (!transA && !transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
+  else if (transA && !transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
+  else if (!transA && transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
   else
-    gemm_launch<64>(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, splits,
-                    kchunk, flops, bytes);
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -33,6 +33,12 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
 void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
           long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
           int batch = 1);
+// The same with data-dependent active sizes: rows < dynM[b] * mulM, columns < dynN[b] * mulN of item b
+// (either pointer may be null); the rest of C is left as it was (zeroed for split-K products).  The
+// algorithmic count uses the static sizes.
+void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+              long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+              int batch, const int* dynM, int mulM, const int* dynN, int mulN);
 // symmetric eigen-decomposition of `batch` m x m matrices (row-major, stride m*m): eigenvalues in
 // descending order into w (stride m), eigenvectors as the COLUMNS of V (row-major m x m, stride m*m).
 // A is left unchanged.  syevj: FP64 Jacobi (absolute accuracy eps64 ||A||).  syevj_mixed: FP32 Jacobi +

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
                                                               double* Vg, int ldv, double* scratch, int use_smem,
                                                               const int* __restrict__ nAg, const int* __restrict__ nBg,
                                                               const double* __restrict__ A2g,
-                                                              const double* __restrict__ Bg) {
+                                                              const double* __restrict__ Bg, double* work) {
   extern __shared__ __align__(16) double sm[];
   double* red = sm;            // 33 (32 partials + the result) + padding
   double* d = red + 40;        // nl
@@ -195,6 +195,9 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   const double* A = (viaB ? A2g : Ag) + (size_t)blockIdx.x * nnl;
   double* Y = gbase + nnl;
   double* lu = Y + (size_t)kl * nl;
+  if (tid == 0)
+    add_work(work, 4.0 / 3.0 * n * (double)n * n + 4.0 * (double)k * n * n + 60.0 * k * n,
+             sizeof(double) * (2.0 * n * n + (double)k * n));
   for (int t = tid; t < kl; t += nthr) wout[t] = 0.0;
   for (size_t q = tid; q < (size_t)nl * kl; q += nthr) {
     const int i = (int)(q / kl), t = (int)(q - (q / kl) * kl);
@@ -532,11 +535,10 @@ static void syevx_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, i
   const size_t per = (size_t)n * n + (size_t)k * n + (size_t)k * 5 * n;
   DBuf<double> scratch(ctx->pool, per * batch);
   LRFG_CUDA(cudaFuncSetAttribute(syevx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // algorithmic count at the launch size (the reduced problems are smaller)
-  const double flops = (4.0 / 3.0 * n * (double)n * n + 4.0 * (double)k * n * n + 60.0 * k * n) * batch;
-  LRFG_LAUNCH(ctx, KC_EIGEN, flops, sizeof(double) * (2.0 * n * n + (double)k * n) * batch,
+  // algorithmic work at the active size, counted by each block on the device
+  LRFG_LAUNCH(ctx, KC_EIGEN, 0.0, 0.0,
               syevx_kernel<<<batch, kSyevxThreads, smem, ctx->stream>>>(A, n, k, w, V, n, scratch.get(), use_smem,
-                                                                         nA, nB, A2, B));
+                                                                         nA, nB, A2, B, work_counter(ctx, KC_EIGEN)));
 }
 
 void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch) {
@@ -577,7 +579,8 @@ constexpr int kCholThreads = 512;
 __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double* __restrict__ Gg,
                                                                    const double* __restrict__ cg, int b, double tau,
                                                                    double* RAg, double* RAcg, double* Pcg,
-                                                                   int* rhog, double* scratch, int use_smem) {
+                                                                   int* rhog, double* scratch, int use_smem,
+                                                                   double* work) {
   extern __shared__ __align__(16) double sm[];
   double* redv = sm;                   // 32 values
   int* redi = (int*)(redv + 32);       // 32 indices
@@ -669,6 +672,12 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
   }
   const int rho = flag[0];
   if (rhog && tid == 0) rhog[blockIdx.x] = rho;
+  if (tid == 0) {
+    // rho pivots, each updating the trailing (b-k-1)^2 block, and the triangular inverse (rho^3/6)
+    double f = 0.0;
+    for (int q = 0; q < rho; ++q) f += (double)(b - q - 1) * (b - q - 1);
+    add_work(work, 2.0 * f + (Pc ? rho * (double)rho * rho / 3.0 : 0.0), sizeof(double) * 4.0 * bb);
+  }
   // outputs
   for (size_t t = tid; t < bb; t += nthr) {
     int i = (int)(t / b), l = (int)(t - (t / b) * b);  // RA row i, permuted column l
@@ -705,10 +714,11 @@ void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int bat
   DBuf<double> scratch;
   if (!use_smem) scratch = DBuf<double>(ctx->pool, (size_t)2 * b * b * batch);
   LRFG_CUDA(cudaFuncSetAttribute(gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const double flops = (2.0 * b * (double)b * b / 3.0 + b * (double)b * b / 3.0) * batch;
-  LRFG_LAUNCH(ctx, KC_CHOL, flops, sizeof(double) * 4.0 * b * b * batch,
-              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-16, RA, RAc, Pc,
-                                                                               rho, scratch.get(), use_smem));
+  // algorithmic work up to the numerical rank, counted by each block on the device
+  LRFG_LAUNCH(ctx, KC_CHOL, 0.0, 0.0,
+              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-16, RA, RAc, Pc, rho,
+                                                                               scratch.get(), use_smem,
+                                                                               work_counter(ctx, KC_CHOL)));
 }
 
 }  // namespace lrfg

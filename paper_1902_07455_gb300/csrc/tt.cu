@@ -223,6 +223,49 @@ __global__ void balance_kernel(double* GAg, double* Rg, double* cg, int m) {
   }
 }
 
+// Estimate of diag(R1) for R1 = C1 (R2 (x) I) C1^T without forming it: the terms with R2's diagonal,
+// sum_{i, b'} C1[a][i][b']^2 R2[b'][b'] (exact when R2 is diagonal).  It only sets the balancing
+// scales, which change rounding errors, not the truncation.  One block per (a, item).
+__global__ void diag_estimate_kernel(const double* __restrict__ C1g, const double* __restrict__ R2g, int a_dim, int n,
+                                     int b2, double* dg) {
+  const size_t item = blockIdx.y;
+  const double* C1 = C1g + item * (size_t)a_dim * n * b2 + (size_t)blockIdx.x * n * b2;
+  const double* R2 = R2g + item * (size_t)b2 * b2;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n * b2; t += blockDim.x) {
+    const int bp = t % b2;
+    const double v = C1[t];
+    s += v * v * R2[(size_t)bp * b2 + bp];
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i];
+    dg[item * a_dim + blockIdx.x] = v;
+  }
+}
+
+// balancing from GA's diagonal and a given right diagonal: c = (r_ii / GA_ii)^{1/4}, GA <- C GA C
+__global__ void balance_diag_kernel(double* GAg, const double* __restrict__ rdg, double* cg, int m) {
+  extern __shared__ double cs[];
+  double* GA = GAg + (size_t)blockIdx.x * m * m;
+  const double* rd = rdg + (size_t)blockIdx.x * m;
+  double* c = cg + (size_t)blockIdx.x * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double ga = GA[(size_t)i * m + i], rb = rd[i];
+    cs[i] = (ga > 0.0 && rb > 0.0) ? sqrt(sqrt(rb / ga)) : 1.0;
+    c[i] = cs[i];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t - (t / m) * m;
+    GA[t] *= cs[i] * cs[j];
+  }
+}
+
 // P[b][t] *= c[b] / sigma_t, sigma_t = sqrt(w_t) (0 where w_t <= 0); one batch item per blockIdx.y
 __global__ void scale_rows_cols_kernel(double* Pg, const double* __restrict__ cg, const double* __restrict__ wg,
                                        int b, int k) {
@@ -262,7 +305,10 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
     const long long sx = (long long)x.elems(j), ss = (long long)s * s;
     R[j] = DBuf<double>(ctx->pool, (size_t)ss * nb);
     gemm(ctx, 0, 1, s, s, n, 1.0, x.core[j], n, sx, x.core[j], n, sx, 0.0, R[j].get(), s, ss, nb);
-    for (int jj = d - 2; jj >= 1; --jj) {
+    // d = 3: bond 0 contracts carriage 1 with R[2] after projecting on its left basis (below), so the
+    // Gram of carriages 1..2 (the 2 N s^3 term that dominates the rounding of rank-s products) is not
+    // formed
+    for (int jj = d - 2; jj >= (d == 3 ? 2 : 1); --jj) {
       const int a = x.r[jj], nn = x.N[jj], b = x.r[jj + 1];
       const long long sxj = (long long)x.elems(jj), sb = (long long)b * b, sa = (long long)a * a;
       DBuf<double> T(ctx->pool, (size_t)sxj * nb);
@@ -282,15 +328,26 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
     const long long sbk = (long long)b * k, skk = (long long)k * k;
     DBuf<double> GA(ctx->pool, (size_t)sbb * nb), cb(ctx->pool, (size_t)b * nb);
     gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, sz, Z.get(), b, sz, 0.0, GA.get(), b, sbb, nb);
-    LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
-                balance_kernel<<<nb, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
+    const bool projected = (d == 3 && j == 0);
+    if (projected) {
+      const int n1 = x.N[1], b2 = x.r[2];
+      DBuf<double> rd(ctx->pool, (size_t)b * nb);
+      LRFG_LAUNCH(ctx, KC_TT_MISC, 3.0 * b * n1 * (double)b2 * nb, sizeof(double) * (double)x.elems(1) * nb,
+                  diag_estimate_kernel<<<dim3(b, nb), 256, 0, ctx->stream>>>(x.core[1], R[2].get(), b, n1, b2,
+                                                                           rd.get()));
+      LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbb * nb, 2.0 * sizeof(double) * sbb * nb,
+                  balance_diag_kernel<<<nb, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), rd.get(), cb.get(), b));
+    } else {
+      LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbb * nb, 4.0 * sizeof(double) * sbb * nb,
+                  balance_kernel<<<nb, 256, sizeof(double) * b, ctx->stream>>>(GA.get(), R[j + 1].get(), cb.get(), b));
+    }
     // The unfolding X = M N (M: rows x b left part, N: b x cols right part) has the Gram matrices
     // GA = M^T M and R = N N^T.  Only the side whose numerical rank is smaller is factored (pivoted
     // Cholesky stops at that rank), and the eigenproblem has that rank as its size.  The left part's
     // rank is at most `rows`, the right part's at most `cols`: the smaller of the two picks the side.
     long long cols = 1;
     for (int i = j + 1; i < d; ++i) cols *= x.N[i];
-    const bool left_side = (long long)rows <= cols;
+    const bool left_side = projected || (long long)rows <= cols;
     DBuf<int> rk(ctx->pool, (size_t)nb);
     DBuf<double> F(ctx->pool, (size_t)sbb * nb), F1(ctx->pool, (size_t)sbb * nb), S(ctx->pool, (size_t)sbb * nb);
     DBuf<double> sig(ctx->pool, (size_t)b * nb), US(ctx->pool, (size_t)sbb * nb);
@@ -300,8 +357,22 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
       // transfer T = U_k^T RAc
       DBuf<double> RAc(ctx->pool, (size_t)sbb * nb), Pc(ctx->pool, (size_t)sbb * nb);
       gram_factor(ctx, GA.get(), cb.get(), b, nb, F.get(), RAc.get(), Pc.get(), rk.get());
-      gemm(ctx, 0, 0, b, b, b, 1.0, F.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, F1.get(), b, sbb, nb);
-      gemm(ctx, 0, 1, b, b, b, 1.0, F1.get(), b, sbb, F.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
+      if (projected) {
+        // S = RAc C1 (R2 (x) I) C1^T RAc^T on the rho_A active rows: Wc = RAc C1 (rho x N1 x b2),
+        // Q = Wc R2, S = Q Wc^T over (N1, b2)
+        const int n1 = x.N[1], b2 = x.r[2];
+        const long long sw = (long long)b * n1 * b2, sr2 = (long long)b2 * b2;
+        DBuf<double> Wc(ctx->pool, (size_t)sw * nb), Qw(ctx->pool, (size_t)sw * nb);
+        gemm_dyn(ctx, 0, 0, b, n1 * b2, b, 1.0, RAc.get(), b, sbb, x.core[1], n1 * b2, (long long)x.elems(1), 0.0,
+                 Wc.get(), n1 * b2, sw, nb, rk.get(), 1, nullptr, 1);
+        gemm_dyn(ctx, 0, 0, b * n1, b2, b2, 1.0, Wc.get(), b2, sw, R[2].get(), b2, sr2, 0.0, Qw.get(), b2, sw, nb,
+                 rk.get(), n1, nullptr, 1);
+        gemm_dyn(ctx, 0, 1, b, b, n1 * b2, 1.0, Qw.get(), n1 * b2, sw, Wc.get(), n1 * b2, sw, 0.0, S.get(), b, sbb,
+                 nb, rk.get(), 1, rk.get(), 1);
+      } else {
+        gemm(ctx, 0, 0, b, b, b, 1.0, F.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, F1.get(), b, sbb, nb);
+        gemm(ctx, 0, 1, b, b, b, 1.0, F1.get(), b, sbb, F.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
+      }
       syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, k, nb);
       gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, sbb, US.get(), b, sbb, 0.0, P.get(), k, sbk, nb);
       gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, sz, P.get(), k, sbk, 0.0, out.core[j].get(), k, sout, nb);
