@@ -24,14 +24,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Block sum: warp partials, then warp 0 alone combines them (FP64 issue slots are scarce: 2 lanes/clk/SM)
-__device__ double block_reduce_sum(double v, double* red) {
-  v = warp_sum(v);
+// Sum over the block of v, where only threads < nact can hold nonzero values: only their warps shuffle
+// (every FP64 add of an idle warp would still cost the SM's FP64 pipe 16 cycles).  Result in red[32].
+__device__ double block_reduce_sum(double v, double* red, int nact) {
+  const int nwa = min((int)(blockDim.x >> 5), (nact + 31) >> 5);
+  const int warp = threadIdx.x >> 5;
+  if (warp < nwa) v = warp_sum(v);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0 && warp < nwa) red[warp] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    s = warp_sum(s);
+    double s = ((int)threadIdx.x < nwa) ? red[threadIdx.x] : 0.0;
+    if (nwa > 1) s = warp_sum(s);
     if (threadIdx.x == 0) red[32] = s;
   }
   __syncthreads();
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
       vv[i] = xi;
       if (i > 0) loc += xi * xi;
     }
-    const double tail2 = block_reduce_sum(loc, red);
+    const double tail2 = block_reduce_sum(loc, red, m);
     if (tail2 == 0.0) {
       if (tid == 0) {
         d[j] = W[(size_t)j * n + j];
@@ -230,16 +234,20 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
       __syncthreads();
       continue;
     }
-    const double alpha = -copysign(sqrt(x0 * x0 + tail2), x0);
-    const double v0 = x0 - alpha;
-    const double b = 2.0 / (tail2 + v0 * v0);
+    // the reflector's scalars once (a square root and a division are long FP64 sequences: computed by
+    // every thread they would occupy the FP64 pipe for thousands of cycles)
     if (tid == 0) {
+      const double alpha = -copysign(sqrt(x0 * x0 + tail2), x0);
+      const double v0 = x0 - alpha;
+      const double bb = 2.0 / (tail2 + v0 * v0);
       vv[0] = v0;
       d[j] = W[(size_t)j * n + j];
       e[j] = alpha;
-      beta[j] = b;
+      beta[j] = bb;
+      red[34] = bb;
     }
     __syncthreads();
+    const double b = red[34];
     // keep v in column j below the diagonal for the back-transformation
     for (int i = tid; i < m; i += nthr) W[(size_t)(j + 1 + i) * n + j] = vv[i];
     // p = b A22 v: thread i takes row i, reading column i of the symmetric trailing block so that
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
     __syncthreads();
     double kl = 0.0;
     for (int i = tid; i < m; i += nthr) kl += vv[i] * pv[i];
-    const double K = 0.5 * b * block_reduce_sum(kl, red);
+    const double K = 0.5 * b * block_reduce_sum(kl, red, m);
     for (int i = tid; i < m; i += nthr) pv[i] -= K * vv[i];
     __syncthreads();
     // A22 -= v w^T + w v^T (one warp per row)
@@ -286,13 +294,28 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   __syncthreads();
 
   // 2. bisection for the k largest eigenvalues (thread t: the t-th largest)
-  double lo = d[0], hi = d[0], emax2 = 0.0;
-  for (int i = 0; i < n; ++i) {
-    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
-    if (i < n - 1) emax2 = fmax(emax2, e[i] * e[i]);
+  // Gershgorin interval and max e^2 by warp 0 (lanes over the rows), broadcast through shared memory
+  if (tid < 32) {
+    double l0 = INFINITY, h0 = -INFINITY, em = 0.0;
+    for (int i = tid; i < n; i += 32) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+      l0 = fmin(l0, d[i] - r);
+      h0 = fmax(h0, d[i] + r);
+      if (i < n - 1) em = fmax(em, e[i] * e[i]);
+    }
+    for (int o = 16; o; o >>= 1) {
+      l0 = fmin(l0, __shfl_xor_sync(0xffffffff, l0, o));
+      h0 = fmax(h0, __shfl_xor_sync(0xffffffff, h0, o));
+      em = fmax(em, __shfl_xor_sync(0xffffffff, em, o));
+    }
+    if (tid == 0) {
+      red[35] = l0;
+      red[36] = h0;
+      red[37] = em;
+    }
   }
+  __syncthreads();
+  const double lo = red[35], hi = red[36], emax2 = red[37];
   const double tnorm = fmax(fabs(lo), fabs(hi));
   const double pivmin = DBL_MIN * fmax(1.0, emax2);
   for (int i = tid; i < n; i += nthr) e2[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
@@ -619,18 +642,22 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
       double v = W[(size_t)i * b + i];
       if (v > best) { best = v; bi = i; }
     }
-    for (int o = 16; o; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffff, best, o);
-      int oi = __shfl_xor_sync(0xffffffff, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    // only the warps that hold remaining diagonal entries reduce (FP64 compares cost FP64 issue)
+    const int nwa = min(nw, (b - k + 31) >> 5);
+    if (warp < nwa) {
+      for (int o = 16; o; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffff, best, o);
+        int oi = __shfl_xor_sync(0xffffffff, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
     }
     __syncthreads();
-    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    if (lane == 0 && warp < nwa) { redv[warp] = best; redi[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
       double bv = -1.0;
       int bx = k;
-      for (int i = 0; i < nw; ++i)
+      for (int i = 0; i < nwa; ++i)
         if (redv[i] > bv || (redv[i] == bv && redi[i] < bx)) { bv = redv[i]; bx = redi[i]; }
       flag[1] = bx;
       if (!(bv > tau * maxd0) || !(bv > 0.0)) flag[0] = k;
@@ -654,11 +681,16 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
       if (tid == 0) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
       __syncthreads();
     }
-    const double lkk = sqrt(W[(size_t)k * b + k]);
-    const double inv = 1.0 / lkk;
+    // the pivot's square root and reciprocal once, broadcast (see the eigensolver's reflector scalars)
+    if (tid == 0) {
+      const double lkk = sqrt(W[(size_t)k * b + k]);
+      redv[30] = 1.0 / lkk;
+      redv[29] = lkk;
+    }
     __syncthreads();
+    const double inv = redv[30];
     for (int i = k + 1 + tid; i < b; i += nthr) W[(size_t)i * b + k] *= inv;
-    if (tid == 0) W[(size_t)k * b + k] = lkk;
+    if (tid == 0) W[(size_t)k * b + k] = redv[29];
     __syncthreads();
     // Schur complement update of the whole trailing block (kept symmetric so that later interchanges
     // can swap full rows and columns)
