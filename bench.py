@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--pinv-eps", type=float, default=0.1)
     p.add_argument("--maxit", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--case", choices=["tt_apply", "full_apply", "full_apply_mixed"], default=None,
+                   help="run two operator applications of the workload and exit (a small program for profilers)")
     return p.parse_args()
 
 
@@ -440,8 +442,38 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_case(args):
+    """Two applications of one operator of the benchmark workload (coefficient compressed to rank
+    coeff-rank on the GPU): the launch sequence a profiler capture of one kernel needs, and nothing else."""
+    import torch
+    import paper_1902_07455_gb300 as lrfg
+    from paper_1902_07455_gb300 import build
+    build.build()
+    ctx = lrfg.Context(0)
+    A = torch.as_tensor(make_coefficient(args.N), device="cuda:0")
+    a_tt = ctx.tt_compress(A, args.coeff_rank)
+    if args.case == "tt_apply":
+        P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps)
+        x = P.rhs([1.0, 0.0, 0.0])
+    else:
+        prec = lrfg.MIXED if args.case == "full_apply_mixed" else lrfg.FP64
+        P = ctx.problem(ctx.tt_expand(a_tt), lrfg.FULL, prec=prec)
+        x = ctx.field_from_full(torch.randn((args.N,) * 3, dtype=torch.float64, device="cuda:0"))
+    for _ in range(2):
+        y = P.apply(x)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "N": args.N, "ok": True}))
+    y.free()
+    x.free()
+    P.free()
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         line = run_reference(args)
     else:

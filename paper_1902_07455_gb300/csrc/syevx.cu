@@ -364,34 +364,41 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
     }
   }
   __syncthreads();
-  // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 32-way multisection by
-  // one warp per eigenvalue until the bracket is at the FP64 resolution: five bits per round of Sturm
-  // counts instead of one, so the serial FP64 recurrences (64-cycle latency per dependent operation on
-  // this part) run about six times instead of thirty
+  // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 4-way multisection by
+  // groups of four lanes (eight eigenvalues per warp) until the bracket is at the FP64 resolution.  A
+  // warp-wide FP64 instruction occupies the SM's FP64 pipe for 16 cycles whatever the lane count, so the
+  // FP64 lane-work per bit is what matters: 4 points per 2 bits, against 32 per 5 bits for a warp-wide
+  // multisection, at about twice the rounds.
   {
-    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-    for (int t = warp; t < k; t += nw) {
-      const int idx = n - 1 - t;
-      double a = bra[t], c = brc[t];
-      int ca = (lane == 0) ? sturm_count(d, e2, n, a) : 0;
-      int cc = (lane == 1) ? sturm_count(d, e2, n, c) : 0;
-      ca = __shfl_sync(0xffffffff, ca, 0);
-      cc = __shfl_sync(0xffffffff, cc, 1);
+    const int lane = tid & 31, sub = lane & 3, grp = tid >> 2;  // four lanes per eigenvalue
+    const int ngrp = nthr >> 2;
+    const unsigned gmask = 0xfu << (lane & ~3);
+    for (int t0 = 0; t0 < k; t0 += ngrp) {
+      // whole warps take part; groups past k work on a dummy copy of eigenvalue t0
+      if ((tid & ~31) >= 4 * (k - t0)) break;
+      const int t = t0 + grp;
+      const int tt = t < k ? t : t0;
+      const int idx = n - 1 - tt;
+      double a = bra[tt], c = brc[tt];
+      int ca = (sub == 0) ? sturm_count(d, e2, n, a) : 0;
+      int cc = (sub == 1) ? sturm_count(d, e2, n, c) : 0;
+      ca = __shfl_sync(gmask, ca, (lane & ~3) | 0);
+      cc = __shfl_sync(gmask, cc, (lane & ~3) | 1);
       if (!(ca <= idx && cc > idx)) { a = glo; c = ghi; }
-      for (int it = 0; it < 16; ++it) {
+      for (int it = 0; it < 80; ++it) {
         if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 1e-3 * DBL_EPSILON * tnorm + 4.0 * pivmin) break;
-        const double h = (c - a) * (1.0 / 33.0);
-        const double x = a + h * (double)(lane + 1);  // 32 interior points
+        const double h = (c - a) * 0.2;
+        const double x = a + h * (double)(sub + 1);  // 4 interior points
         const int cnt = sturm_count(d, e2, n, x);
-        const unsigned above = __ballot_sync(0xffffffff, cnt > idx);
+        const unsigned above = (__ballot_sync(gmask, cnt > idx) >> (lane & ~3)) & 0xfu;
         // the first point whose count exceeds idx bounds the eigenvalue from above
-        const int f = above ? (__ffs(above) - 1) : 32;
+        const int f = above ? (__ffs(above) - 1) : 4;
         const double na = (f == 0) ? a : a + h * (double)f;
-        const double nc = (f == 32) ? c : a + h * (double)(f + 1);
+        const double nc = (f == 4) ? c : a + h * (double)(f + 1);
         a = na;
         c = nc;
       }
-      if (lane == 0) lam[t] = 0.5 * (a + c);
+      if (sub == 0 && t < k) lam[t] = 0.5 * (a + c);
     }
   }
   __syncthreads();
