@@ -51,6 +51,11 @@ def parse():
     p.add_argument("--pinv-eps", type=float, default=0.1)
     p.add_argument("--maxit", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["c2", "c3"], default="c2",
+                   help="c2: lognormal SE-GRF, coefficient TT rank 10 (default, N=243); c3: tanh-smoothed cube of "
+                        "contrast 100, coefficient rank 2 (N=1215 unless --N is given)")
+    p.add_argument("--c3-full", choices=["none", "mixed", "fp64"], default="mixed",
+                   help="c3: full-format anchor solve on the expanded coefficient")
     p.add_argument("--case", choices=["tt_apply", "full_apply", "full_apply_mixed"], default=None,
                    help="run two operator applications of the workload and exit (a small program for profilers)")
     return p.parse_args()
@@ -442,6 +447,92 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def c3_bounds(N, contrast):
+    """Voigt and Reuss bounds of the smoothed cube: arithmetic and harmonic means of the grid samples
+    (computed slice by slice; the grid is never held whole)."""
+    from synthetic import smoothed_cube
+    _, terms, w = smoothed_cube(3, N, contrast=contrast, full=False)
+    h = terms[1][0]
+    arith = 1.0 + (contrast - 1.0) * float(np.mean(h)) ** 3
+    hh = np.outer(h, h)
+    inv = 0.0
+    for i in range(N):
+        inv += float(np.sum(1.0 / (1.0 + (contrast - 1.0) * h[i] * hh)))
+    return arith, 1.0 / (inv / float(N) ** 3)
+
+
+def run_c3(args):
+    """Config 3: d = 3 tanh-smoothed cube (|x| < 0.3, width 2/N, contrast 100; coefficient of TT rank 2
+    built on the GPU from its two separable terms), TT MinRes solve at rank r; the full-format solve on
+    the expanded coefficient (FP32 storage, or FP64) as the anchor; Voigt-Reuss bounds."""
+    import torch
+    import paper_1902_07455_gb300 as lrfg
+    from paper_1902_07455_gb300 import build
+    from synthetic import smoothed_cube
+    build.build()
+    N = args.N
+    contrast = 100.0
+    ctx = lrfg.Context(0)
+    _, terms, w = smoothed_cube(3, N, contrast=contrast, full=False)
+    rank1 = [lrfg.TTensor.from_numpy([np.asarray(f, dtype=np.float64).reshape(1, N, 1) for f in t]) for t in terms]
+    a_tt = ctx.tt_add(w[0], rank1[0], w[1], rank1[1])
+    E = [1.0, 0.0, 0.0]
+    P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, tol=1e-12, maxit=args.maxit)
+    stream = ctx.stream
+    for _ in range(args.warmup):
+        P.solve(E, want_field=False)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ctx.profile_reset()
+    ctx.profile(True)
+    step_ms, results = [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            results.append(P.solve(E, want_field=False)[0])
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    ctx.profile(False)
+    stats = ctx.profile_read()
+    launches = ctx.launch_count() - launches0
+    res = results[-1]
+    arith, harm = c3_bounds(N, contrast)
+    anchor = None
+    if args.c3_full != "none":
+        a_full = ctx.tt_expand(a_tt)
+        prec = lrfg.MIXED if args.c3_full == "mixed" else lrfg.FP64
+        tol = 1e-5 if args.c3_full == "mixed" else 1e-8
+        Pf = ctx.problem(a_full, lrfg.FULL, tol=tol, maxit=5000, prec=prec)
+        del a_full
+        fr, _ = Pf.solve(E, want_field=False)
+        anchor = {"precision": args.c3_full, "tol": tol, "aeff": fr.Aeff, "iters": fr.iters, "seconds": fr.seconds,
+                  "solves_per_s": 1.0 / fr.seconds}
+        Pf.free()
+    total_ms = sum(step_ms)
+    line = {
+        "metric": METRIC, "value": args.steps / (total_ms * 1e-3), "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"d=3 N={N}^3 tanh-smoothed cube |x|<0.3 width 2/N contrast 100 (coefficient TT "
+                               f"rank 2), E=(1,0,0); TT rank {args.rank} MinRes", "d": 3, "N": N,
+                   "tt_rank": args.rank, "pinv_eps": args.pinv_eps, "precision": "fp64"},
+        "tt_iters": res.iters, "tt_applies_per_solve": sum(r.applies for r in results) / args.steps,
+        "tt_aeff": res.Aeff, "voigt": arith, "reuss": harm, "within_bounds": harm <= res.Aeff <= arith,
+        "full_anchor": anchor,
+        "aeff_rel_err_vs_anchor": abs(res.Aeff - anchor["aeff"]) / anchor["aeff"] if anchor else None,
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "gpu_launches": launches, "clocks": clk.summary(), "roofline": roofline(stats),
+        "kernel_classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in stats.items()
+                           if v["launches"]},
+    }
+    print(json.dumps(line))
+    P.free()
+    ctx.close()
+
+
 def run_case(args):
     """Two applications of one operator of the benchmark workload (coefficient compressed to rank
     coeff-rank on the GPU): the launch sequence a profiler capture of one kernel needs, and nothing else."""
@@ -471,8 +562,13 @@ def run_case(args):
 
 def main():
     args = parse()
+    if args.workload == "c3" and "--N" not in sys.argv:
+        args.N = 1215
     if args.case:
         run_case(args)
+        return
+    if args.workload == "c3" and args.impl == "ours":
+        run_c3(args)
         return
     if args.impl == "reference":
         line = run_reference(args)

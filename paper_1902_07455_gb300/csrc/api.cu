@@ -181,6 +181,26 @@ struct lrfg_problem {
 
 namespace {
 
+__global__ void first_nonpositive_kernel(const double* __restrict__ v, long long n, unsigned long long* first) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double x = v[t];
+    if (!(isfinite(x) && x > 0.0)) atomicMin(first, (unsigned long long)t);
+  }
+}
+
+// index of the first entry that is not positive and finite, or -1
+long long first_nonpositive(lrfg_ctx* ctx, const double* v, long long n) {
+  DBuf<unsigned long long> first(ctx->pool, 1);
+  LRFG_CUDA(cudaMemsetAsync(first.get(), 0xff, sizeof(unsigned long long), ctx->stream));
+  const long long blocks = std::max(1LL, std::min((n + 255) / 256, 16LL * (ctx->num_sms > 0 ? ctx->num_sms : 152)));
+  LRFG_LAUNCH(ctx, KC_REDUCE, (double)n, sizeof(double) * (double)n,
+              first_nonpositive_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(v, n, first.get()));
+  unsigned long long h = 0;
+  LRFG_CUDA(cudaMemcpyAsync(&h, first.get(), sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  return h == ~0ULL ? -1 : (long long)h;
+}
+
 template <class F>
 lrfg_status guard(lrfg_ctx* ctx, F&& f) {
   try {
@@ -856,18 +876,11 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     if (coeff->fmt == LRFG_FULL) {
       LRFG_REQUIRE(coeff->values != nullptr, "null coefficient values");
       DBuf<double> a(ctx->pool, n);
-      std::vector<double> h;
-      if (coeff->on_device) {
-        h.resize(n);
-        LRFG_CUDA(cudaMemcpyAsync(h.data(), coeff->values, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
-        LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
-        LRFG_CUDA(cudaMemcpyAsync(a.get(), coeff->values, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-      } else {
-        LRFG_CUDA(cudaMemcpyAsync(a.get(), coeff->values, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
-      }
-      const double* hv = coeff->on_device ? h.data() : coeff->values;
-      for (long long i = 0; i < n; ++i)
-        LRFG_REQUIRE(std::isfinite(hv[i]) && hv[i] > 0.0, "coefficient must be positive and finite (index %lld)", i);
+      LRFG_CUDA(cudaMemcpyAsync(a.get(), coeff->values, sizeof(double) * n,
+                                coeff->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+      // validated on the device (grids of 10^9 points and more)
+      const long long bad = first_nonpositive(ctx, a.get(), n);
+      LRFG_REQUIRE(bad < 0, "coefficient must be positive and finite (index %lld)", bad);
       if (opts->fmt == LRFG_FULL) {
         P->a_full = std::move(a);
       } else {

@@ -55,26 +55,27 @@ def square_inclusion(d: int, N: int, vf: float = 0.5, phases=(1.0, 10.0)):
     return a, terms, weights
 
 
-def smoothed_cube(d: int, N: int, contrast: float = 100.0, c: float = 0.3, width=None):
+def smoothed_cube(d: int, N: int, contrast: float = 100.0, c: float = 0.3, width=None, full: bool = True):
     """a = 1 + (contrast-1) prod_a h(x_a) with a tanh-smoothed indicator of |t| < c, width 2/N by
-    default.  Returns (a_full, terms, weights)."""
+    default.  Returns (a_full, terms, weights); a_full is None when full=False (large N)."""
     w = 2.0 / N if width is None else float(width)
     x = grid_points(N)
     h = 0.5 * (np.tanh((x + c) / w) - np.tanh((x - c) / w))
     one = np.ones(N)
     terms = [[one] * d, [h] * d]
     weights = [1.0, contrast - 1.0]
-    a = 1.0 + (contrast - 1.0) * _outer([h] * d)
+    a = 1.0 + (contrast - 1.0) * _outer([h] * d) if full else None
     return a, terms, weights
 
 
-def laminate(d: int, N: int, contrast: float = 10.0, c: float = 0.25):
-    """Layered medium a(x) = 1 + (contrast-1) [|x_1| < c].  Returns (a_full, terms, weights)."""
+def laminate(d: int, N: int, contrast: float = 10.0, c: float = 0.25, full: bool = True):
+    """Layered medium a(x) = 1 + (contrast-1) [|x_1| < c].  Returns (a_full, terms, weights); a_full is
+    None when full=False (large N)."""
     x = grid_points(N)
     f = 1.0 + (contrast - 1.0) * (np.abs(x) < c)
     one = np.ones(N)
     terms = [[f] + [one] * (d - 1)]
-    a = _outer([f] + [one] * (d - 1))
+    a = _outer([f] + [one] * (d - 1)) if full else None
     return a, terms, [1.0]
 
 
