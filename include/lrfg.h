@@ -5,11 +5,17 @@
  * d in {2,3}, as defined in arXiv:1902.07455 Sec. 2.1, Eq. (homog):
  *     A_eff E.E = min over zero-mean periodic v of  int_Y A(x)(E + grad v).(E + grad v) dx,
  * discretised by the Fourier–Galerkin method with numerical integration (GaNi, Sec. 2.2.2) on an odd
- * grid N^d, preconditioned by the Fourier Laplacian (Sec. 2.3, Eq. (Pls_fourier)).  Two solution formats:
- *   LRFG_FULL  the N^d grid; preconditioned CG (Sec. 3.3, Sec. 4);
- *   LRFG_TT    tensor train of fixed rank r; the truncated operator of Eq. (Pls_lowrank) and the
- *              minimal-residual iteration with truncation of Sec. 3.3.
- * The coefficient is isotropic, A(x) = a(x) I, given either as grid values or as a tensor train.
+ * grid N^d, preconditioned by the Fourier Laplacian (Sec. 2.3, Eq. (Pls_fourier)).  Solution formats:
+ *   LRFG_FULL    the N^d grid; preconditioned CG (Sec. 3.3, Sec. 4);
+ *   LRFG_TT      tensor train of fixed rank r; the truncated operator of Eq. (Pls_lowrank) and the
+ *                minimal-residual iteration with truncation of Sec. 3.3;
+ *   LRFG_TUCKER  Tucker tensor of fixed multilinear rank r (App. A.2), same operator and iteration,
+ *                truncation by factor orthonormalisation + HOSVD of the core (App. A.2.3).
+ * The coefficient is isotropic, A(x) = a(x) I, given as grid values, a tensor train or a Tucker tensor.
+ * A Tucker problem built from grid values or a TT compresses the coefficient by HOSVD of its grid,
+ * keeping singular values above 1e-7 of the largest in each mode (at most 64 per mode): the HOSVD
+ * takes them from FP64 Gram matrices, which resolve singular values down to about sqrt(eps) of the
+ * largest, so smaller ones are rounding noise.
  *
  * Conventions for every call:
  *   - every function returns an lrfg_status; no exception or signal crosses the ABI;
@@ -19,6 +25,7 @@
  *   - grid arrays are row-major with storage index i along an axis holding x = k/N,
  *     k = i for i <= (N-1)/2 and k = i - N otherwise (the DFT order);
  *   - TT carriage j has shape (r[j], N[j], r[j+1]) row-major, r[0] = r[d] = 1 (App. A.3, Eq. (TT));
+ *   - a Tucker core has shape (r[0], .., r[d-1]) row-major and factor j shape (N[j], r[j]) row-major;
  *   - "device" pointers are CUDA device addresses on the context's device; "host" pointers are
  *     ordinary host memory; inputs are caller-owned and not retained after the call returns;
  *     objects created by the library (lrfg_problem, lrfg_field) are freed by their *_free call;
@@ -51,7 +58,7 @@ typedef enum {
   LRFG_ENOTSUP = 6   /* valid but not supported by this build */
 } lrfg_status;
 
-typedef enum { LRFG_FULL = 0, LRFG_TT = 3 } lrfg_format;
+typedef enum { LRFG_FULL = 0, LRFG_TUCKER = 2, LRFG_TT = 3 } lrfg_format;
 typedef enum { LRFG_FP64 = 0, LRFG_MIXED = 1 } lrfg_prec;
 
 /* spectral multipliers m(k) applied along one mode by F^{-1} diag(m) F (Sec. 2.2.1, Sec. 3.2) */
@@ -73,18 +80,28 @@ typedef struct {
   double* cores[3];  /* carriage j: r[j] * N[j] * r[j+1] doubles, row-major (r[j], N[j], r[j+1]) */
 } lrfg_tt;
 
+/* A Tucker tensor (App. A.2, Eq. (tucker)) whose core and factors are caller-owned buffers. */
+typedef struct {
+  int d;
+  int N[3];
+  int r[3];             /* multilinear ranks r[0..d-1] */
+  double* core;         /* r[0] * .. * r[d-1] doubles, row-major */
+  double* factors[3];   /* factor j: N[j] * r[j] doubles, row-major (N[j], r[j]) */
+} lrfg_tucker;
+
 /* Coefficient a(x) of A(x) = a(x) I (Sec. 2.1, Eq. (A); GaNi samples a(x_k), Sec. 2.2.2). */
 typedef struct {
   int d;
   int N[3];
-  lrfg_format fmt;      /* LRFG_FULL: `values` (N^d grid values); LRFG_TT: `tt` */
+  lrfg_format fmt;      /* LRFG_FULL: `values` (N^d grid values); LRFG_TT: `tt`; LRFG_TUCKER: `tk` */
   const double* values; /* grid values, row-major, positive and finite */
   lrfg_tt tt;           /* carriages of a; the coefficient's TT ranks are its own (r_A) */
-  int on_device;        /* 1: values / tt.cores are device pointers; 0: host pointers */
+  int on_device;        /* 1: values / tt.cores / tk buffers are device pointers; 0: host pointers */
+  lrfg_tucker tk;       /* core and factors of a (LRFG_TUCKER) */
 } lrfg_coeff;
 
 typedef struct {
-  lrfg_format fmt;      /* solution format: LRFG_FULL (PCG) or LRFG_TT (minimal residual) */
+  lrfg_format fmt;      /* solution format: LRFG_FULL (PCG), LRFG_TT or LRFG_TUCKER (minimal residual) */
   lrfg_prec prec;       /* LRFG_FP64, or LRFG_MIXED with fmt == LRFG_FULL */
   int rank;             /* LRFG_TT: the fixed rank of every truncation T (Sec. 4.2) */
   double pinv_eps;      /* LRFG_TT: relative accuracy of the exponential-sum P~^-1 on [1, max k.k]
@@ -171,6 +188,11 @@ lrfg_status lrfg_tt_add(lrfg_ctx* ctx, double alpha, const lrfg_tt* x, double be
  * min(rmax, x->r[j]) N[j] min(rmax, x->r[j+1]) doubles.  Carriages 1..d-1 of out are
  * left-orthonormal. */
 lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out);
+/* Tucker truncation T (App. A.2.3) of a Tucker tensor with device buffers into out (device buffers of
+ * at least prod_j min(rmax, r_j) core and N_j min(rmax, r_j) factor doubles; out->r is set): every
+ * factor orthonormalised (unit-column balanced Gram matrix, pivoted Cholesky), its triangular factor
+ * moved into the core, then the HOSVD of the core keeps min(rmax, r_j) vectors per mode. */
+lrfg_status lrfg_tucker_round(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, lrfg_tucker* out);
 
 /* Euclidean inner product <x, y> = sum_k x[k] y[k] of two TTs (FP64 contraction). */
 lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);
@@ -251,6 +273,9 @@ lrfg_status lrfg_field_from_full(lrfg_ctx* ctx, int d, const int N[3], const dou
                                  lrfg_field** out);
 /* Field from TT carriages of real grid values (copied). */
 lrfg_status lrfg_field_from_tt(lrfg_ctx* ctx, const lrfg_tt* x, int on_device, lrfg_field** out);
+/* A Tucker field (for LRFG_TUCKER problems) from a Tucker tensor in host or device buffers. */
+lrfg_status lrfg_field_from_tucker(lrfg_ctx* ctx, const lrfg_tucker* x, int on_device, lrfg_field** out);
+/* r: TT ranks r[0..d] for TT fields, multilinear ranks r[0..d-1] for Tucker fields, 1 otherwise. */
 lrfg_status lrfg_field_info(const lrfg_field* f, lrfg_format* fmt, int* d, int N[3], int r[4]);
 /* Grid values of the field into `values` (N^d doubles, host or device as on_device says). */
 lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* values, int on_device);

@@ -22,10 +22,10 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Context", "TTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
+__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "TUCKER", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
            "MUL_GAUSS", "library_path"]
 
-FULL, TT = L.LRFG_FULL, L.LRFG_TT
+FULL, TUCKER, TT = L.LRFG_FULL, L.LRFG_TUCKER, L.LRFG_TT
 FP64, MIXED = L.LRFG_FP64, L.LRFG_MIXED
 MUL_IDENTITY, MUL_DERIV, MUL_GAUSS = L.LRFG_MUL_IDENTITY, L.LRFG_MUL_DERIV, L.LRFG_MUL_GAUSS
 
@@ -97,6 +97,48 @@ class TTensor:
 
     def numpy(self):
         return [c.detach().cpu().numpy() for c in self.cores]
+
+
+@dataclass
+class TuckerTensor:
+    """Tucker tensor with a CUDA float64 core (r_0, .., r_{d-1}) and factors of shapes (N_j, r_j)."""
+    core: object
+    factors: list
+
+    @property
+    def d(self):
+        return len(self.factors)
+
+    @property
+    def shape(self):
+        return tuple(int(f.shape[0]) for f in self.factors)
+
+    @property
+    def ranks(self):
+        return [int(f.shape[1]) for f in self.factors]
+
+    def to_struct(self) -> L.lrfg_tucker:
+        torch = _torch()
+        s = L.lrfg_tucker()
+        s.d = self.d
+        for t in [self.core] + list(self.factors):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("Tucker core and factors must be contiguous CUDA float64 tensors")
+        s.core = self.core.data_ptr()
+        for j, f in enumerate(self.factors):
+            s.N[j] = int(f.shape[0])
+            s.r[j] = int(f.shape[1])
+            s.factors[j] = f.data_ptr()
+        return s
+
+    @staticmethod
+    def from_numpy(core, factors, device="cuda"):
+        torch = _torch()
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+        return TuckerTensor(t(core), [t(f) for f in factors])
+
+    def numpy(self):
+        return self.core.detach().cpu().numpy(), [f.detach().cpu().numpy() for f in self.factors]
 
 
 class Context:
@@ -281,6 +323,23 @@ class Context:
         self.check(self.lib.lrfg_tt_expand(self.h, C.byref(xs), _ptr(out)))
         return out
 
+    def tucker_round(self, x: TuckerTensor, rmax: int) -> TuckerTensor:
+        torch = _torch()
+        k = [min(int(rmax), r) for r in x.ranks]
+        dev = f"cuda:{self.device}"
+        core = torch.empty(tuple(k), dtype=torch.float64, device=dev)
+        facs = [torch.empty((n, kk), dtype=torch.float64, device=dev) for n, kk in zip(x.shape, k)]
+        out = TuckerTensor(core, facs).to_struct()
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_tucker_round(self.h, C.byref(xs), int(rmax), C.byref(out)))
+        return TuckerTensor(core, facs)
+
+    def field_from_tucker(self, x: TuckerTensor) -> "Field":
+        h = C.c_void_p()
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_field_from_tucker(self.h, C.byref(xs), 1, C.byref(h)))
+        return Field(self, h)
+
     # ---- problems and fields ---------------------------------------------------------------------
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64) -> "Problem":
@@ -381,7 +440,15 @@ class Problem:
         self.fmt = fmt
         c = L.lrfg_coeff()
         keep = None
-        if isinstance(coeff, TTensor):
+        if isinstance(coeff, TuckerTensor):
+            c.d = coeff.d
+            for j, n in enumerate(coeff.shape):
+                c.N[j] = n
+            c.fmt = L.LRFG_TUCKER
+            c.tk = coeff.to_struct()
+            c.on_device = 1
+            keep = coeff
+        elif isinstance(coeff, TTensor):
             c.d = coeff.d
             for j, n in enumerate(coeff.shape):
                 c.N[j] = n

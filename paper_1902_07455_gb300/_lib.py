@@ -8,7 +8,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblrfg.so")
 
 LRFG_OK, LRFG_EINVAL, LRFG_ENOMEM, LRFG_ENOCONV, LRFG_ECUDA, LRFG_ETIMEOUT, LRFG_ENOTSUP = range(7)
-LRFG_FULL, LRFG_TT = 0, 3
+LRFG_FULL, LRFG_TUCKER, LRFG_TT = 0, 2, 3
 LRFG_FP64, LRFG_MIXED = 0, 1
 LRFG_MUL_IDENTITY, LRFG_MUL_DERIV, LRFG_MUL_GAUSS = 0, 1, 2
 
@@ -20,9 +20,14 @@ class lrfg_tt(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int * 3), ("r", C.c_int * 4), ("cores", C.c_void_p * 3)]
 
 
+class lrfg_tucker(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int * 3), ("r", C.c_int * 3), ("core", C.c_void_p),
+                ("factors", C.c_void_p * 3)]
+
+
 class lrfg_coeff(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int * 3), ("fmt", C.c_int), ("values", C.c_void_p),
-                ("tt", lrfg_tt), ("on_device", C.c_int)]
+                ("tt", lrfg_tt), ("on_device", C.c_int), ("tk", lrfg_tucker)]
 
 
 class lrfg_opts(C.Structure):
@@ -57,6 +62,8 @@ SIGNATURES = {
     "lrfg_fft_fibres": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
     "lrfg_fibre_operator": (_ST, [_P, _P, _P, _I, _I, _I, _I, _D, _D]),
     "lrfg_tt_hadamard": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
+    "lrfg_tucker_round": (_ST, [_P, C.POINTER(lrfg_tucker), _I, C.POINTER(lrfg_tucker)]),
+    "lrfg_field_from_tucker": (_ST, [_P, C.POINTER(lrfg_tucker), _I, C.POINTER(_P)]),
     "lrfg_tt_add": (_ST, [_P, _D, C.POINTER(lrfg_tt), _D, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
     "lrfg_tt_round": (_ST, [_P, C.POINTER(lrfg_tt), _I, C.POINTER(lrfg_tt)]),
     "lrfg_tt_dot": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(_D)]),

@@ -157,6 +157,7 @@ struct lrfg_field {
   int d = 0;
   int N[3] = {0, 0, 0};
   TT tt;              // TT: real-space carriages
+  TK tk;              // TUCKER: real-space core and factors
   DBuf<double2> half; // FULL: Phi u (unnormalised half spectrum)
 };
 
@@ -166,6 +167,7 @@ struct lrfg_problem {
   int d = 0;
   int N[3] = {0, 0, 0};
   TT a_tt;                   // TT coefficient (LRFG_TT)
+  TK a_tk;                   // Tucker coefficient (LRFG_TUCKER)
   DBuf<double> a_full;       // grid coefficient (LRFG_FULL)
   std::vector<double> pt, pw;  // exponential sum of P~^-1
   FullGrid g{};
@@ -240,6 +242,27 @@ void check_tt(const lrfg_tt* x) {
   LRFG_REQUIRE(x->r[0] == 1 && x->r[x->d] == 1, "TT boundary ranks must be 1");
   for (int j = 1; j < x->d; ++j) LRFG_REQUIRE(x->r[j] >= 1, "TT rank r[%d] = %d < 1", j, x->r[j]);
   for (int j = 0; j < x->d; ++j) LRFG_REQUIRE(x->cores[j] != nullptr, "null TT carriage %d", j);
+}
+
+void check_tucker(const lrfg_tucker* x) {
+  LRFG_REQUIRE(x != nullptr, "null Tucker tensor");
+  check_grid(x->d, x->N);
+  LRFG_REQUIRE(x->core != nullptr, "null Tucker core");
+  for (int j = 0; j < x->d; ++j) {
+    LRFG_REQUIRE(x->r[j] >= 1 && x->r[j] <= x->N[j] * 64, "Tucker rank r[%d] = %d out of range", j, x->r[j]);
+    LRFG_REQUIRE(x->factors[j] != nullptr, "null Tucker factor %d", j);
+  }
+}
+
+void upload_tucker(lrfg_ctx* ctx, const lrfg_tucker* src, int on_device, TK& dst) {
+  tk_alloc(ctx, dst, src->d, src->N, src->r);
+  size_t nc = 1;
+  for (int j = 0; j < src->d; ++j) nc *= (size_t)src->r[j];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  LRFG_CUDA(cudaMemcpyAsync(dst.core.get(), src->core, sizeof(double) * nc, kind, ctx->stream));
+  for (int j = 0; j < src->d; ++j)
+    LRFG_CUDA(cudaMemcpyAsync(dst.fac[j].get(), src->factors[j], sizeof(double) * src->N[j] * src->r[j], kind,
+                              ctx->stream));
 }
 
 size_t core_elems(const lrfg_tt* x, int j) { return (size_t)x->r[j] * x->N[j] * x->r[j + 1]; }
@@ -472,6 +495,10 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     } else {
       full_apply<double>(P, in->half.get(), out->half.get(), 1);
     }
+  } else if (P->opts.fmt == LRFG_TUCKER) {
+    TK res;
+    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res);
+    out->tk = std::move(res);
   } else {
     TT res;
     lr_apply(P, view_of(in->tt), res);
@@ -542,6 +569,24 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
     lrfg_field* f;
     new_field(ctx, LRFG_FULL, P->d, P->N, &f);
     f->half = std::move(u64);
+    *u_out = f;
+  }
+}
+
+void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
+  TK best;
+  const TKSolveResult r = tk_solve(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, P->opts.tol,
+                                   P->opts.maxit, P->opts.stop_on_increase, best);
+  res->iters = r.iters;
+  res->rel_resid = r.rel_resid;
+  res->converged = r.rel_resid <= P->opts.tol ? 1 : 0;
+  res->applies = r.applies;
+  res->Aeff = r.Aeff;
+  for (int j = 0; j < 4; ++j) res->ranks[j] = j < P->d ? best.r[j] : 1;
+  if (u_out) {
+    lrfg_field* f;
+    new_field(P->ctx, LRFG_TUCKER, P->d, P->N, &f);
+    f->tk = std::move(best);
     *u_out = f;
   }
 }
@@ -797,6 +842,39 @@ lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* ou
   });
 }
 
+lrfg_status lrfg_tucker_round(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, lrfg_tucker* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tucker(x);
+    LRFG_REQUIRE(out != nullptr && out->core != nullptr, "null output");
+    LRFG_REQUIRE(rmax >= 1, "rmax must be >= 1");
+    TKView v{};
+    v.d = x->d;
+    for (int j = 0; j < 3; ++j) {
+      v.N[j] = j < x->d ? x->N[j] : 1;
+      v.r[j] = j < x->d ? x->r[j] : 1;
+      v.fac[j] = j < x->d ? x->factors[j] : nullptr;
+    }
+    v.core = x->core;
+    TK res;
+    tk_round(ctx, v, rmax, res);
+    out->d = res.d;
+    size_t nc = 1;
+    for (int j = 0; j < 3; ++j) {
+      out->N[j] = x->N[j];
+      out->r[j] = res.r[j];
+      if (j < res.d) nc *= (size_t)res.r[j];
+    }
+    LRFG_CUDA(cudaMemcpyAsync(out->core, res.core.get(), sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int j = 0; j < res.d; ++j) {
+      LRFG_REQUIRE(out->factors[j] != nullptr, "null output factor %d", j);
+      LRFG_CUDA(cudaMemcpyAsync(out->factors[j], res.fac[j].get(), sizeof(double) * res.N[j] * res.r[j],
+                                cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
 lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result) {
   if (!ctx) return LRFG_EINVAL;
   return guard(ctx, [&] {
@@ -855,14 +933,16 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
   lrfg_status st = guard(ctx, [&] {
     LRFG_REQUIRE(coeff && opts && out, "null argument");
     check_grid(coeff->d, coeff->N);
-    LRFG_REQUIRE(opts->fmt == LRFG_FULL || opts->fmt == LRFG_TT, "solution format must be LRFG_FULL or LRFG_TT");
+    LRFG_REQUIRE(opts->fmt == LRFG_FULL || opts->fmt == LRFG_TT || opts->fmt == LRFG_TUCKER,
+                 "solution format must be LRFG_FULL, LRFG_TT or LRFG_TUCKER");
     LRFG_REQUIRE(opts->prec == LRFG_FP64 || opts->prec == LRFG_MIXED, "unknown precision %d", (int)opts->prec);
     if (opts->prec == LRFG_MIXED && opts->fmt != LRFG_FULL)
       fail(LRFG_ENOTSUP, "LRFG_MIXED is implemented for LRFG_FULL solutions only");
     LRFG_REQUIRE(opts->maxit >= 0, "maxit must be >= 0");
     LRFG_REQUIRE(opts->tol >= 0.0, "tol must be >= 0");
-    if (opts->fmt == LRFG_TT) LRFG_REQUIRE(opts->rank >= 1, "TT solve needs rank >= 1 (got %d)", opts->rank);
-    LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT, "coefficient format must be FULL or TT");
+    if (opts->fmt != LRFG_FULL) LRFG_REQUIRE(opts->rank >= 1, "low-rank solve needs rank >= 1 (got %d)", opts->rank);
+    LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
+                 "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();
     ctx->live_objects++;
     P->ctx = ctx;
@@ -883,8 +963,23 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       LRFG_REQUIRE(bad < 0, "coefficient must be positive and finite (index %lld)", bad);
       if (opts->fmt == LRFG_FULL) {
         P->a_full = std::move(a);
+      } else if (opts->fmt == LRFG_TUCKER) {
+        tk_compress(ctx, P->d, P->N, a.get(), 64, 1e-7, P->a_tk);
       } else {
         tt_compress(ctx, P->d, P->N, a.get(), opts->rank, 0.0, P->a_tt);
+      }
+    } else if (coeff->fmt == LRFG_TUCKER) {
+      LRFG_REQUIRE(coeff->tk.d == coeff->d, "coefficient Tucker order differs from d");
+      for (int j = 0; j < coeff->d; ++j) LRFG_REQUIRE(coeff->tk.N[j] == coeff->N[j], "coefficient Tucker grid differs");
+      check_tucker(&coeff->tk);
+      TK a;
+      upload_tucker(ctx, &coeff->tk, coeff->on_device, a);
+      if (opts->fmt == LRFG_TUCKER) {
+        P->a_tk = std::move(a);
+      } else {
+        P->a_full = DBuf<double>(ctx->pool, n);
+        tk_expand(ctx, tk_view(a), P->a_full.get());
+        if (opts->fmt == LRFG_TT) tt_compress(ctx, P->d, P->N, P->a_full.get(), opts->rank, 0.0, P->a_tt);
       }
     } else {
       LRFG_REQUIRE(coeff->tt.d == coeff->d, "coefficient TT order differs from d");
@@ -897,6 +992,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       } else {
         P->a_full = DBuf<double>(ctx->pool, n);
         tt_expand(ctx, view_of(a), P->a_full.get());
+        if (opts->fmt == LRFG_TUCKER) tk_compress(ctx, P->d, P->N, P->a_full.get(), 64, 1e-7, P->a_tk);
       }
     }
     if (opts->fmt == LRFG_FULL) {
@@ -937,7 +1033,8 @@ lrfg_status lrfg_problem_free(lrfg_problem* P) {
 
 lrfg_status lrfg_problem_coeff_ranks(const lrfg_problem* P, int ranks[4]) {
   if (!P || !ranks) return LRFG_EINVAL;
-  for (int j = 0; j < 4; ++j) ranks[j] = P->opts.fmt == LRFG_TT ? P->a_tt.r[j] : 1;
+  for (int j = 0; j < 4; ++j)
+    ranks[j] = P->opts.fmt == LRFG_TT ? P->a_tt.r[j] : (P->opts.fmt == LRFG_TUCKER && j < P->d ? P->a_tk.r[j] : 1);
   return LRFG_OK;
 }
 
@@ -979,6 +1076,8 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
       } else {
         full_rhs<double>(P, E, f->half.get(), 1);
       }
+    } else if (P->opts.fmt == LRFG_TUCKER) {
+      tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk);
     } else {
       lr_rhs(P, E, f->tt);
     }
@@ -1001,10 +1100,11 @@ lrfg_status lrfg_problem_solve(lrfg_problem* P, const double* E, lrfg_result* re
       if (P->opts.prec == LRFG_MIXED) solve_full<float>(P, E, res, u_out);
       else solve_full<double>(P, E, res, u_out);
     }
+    else if (P->opts.fmt == LRFG_TUCKER) solve_tucker(P, E, res, u_out);
     else solve_tt(P, E, res, u_out);
     LRFG_CUDA(cudaStreamSynchronize(P->ctx->stream));
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    noconv = !res->converged && !(P->opts.fmt == LRFG_TT && P->opts.stop_on_increase && res->applies > 0 &&
+    noconv = !res->converged && !(P->opts.fmt != LRFG_FULL && P->opts.stop_on_increase && res->applies > 0 &&
                                   res->iters < P->opts.maxit);
   });
   if (st == LRFG_OK && noconv) return LRFG_ENOCONV;
@@ -1016,7 +1116,9 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field
   return guard(P->ctx, [&] {
     LRFG_REQUIRE(E && Aeff, "null argument");
     check_field(P, u);
-    *Aeff = (P->opts.fmt == LRFG_FULL) ? full_aeff(P, E, u->half.get()) : lr_aeff(P, E, view_of(u->tt));
+    *Aeff = (P->opts.fmt == LRFG_FULL)     ? full_aeff(P, E, u->half.get())
+            : (P->opts.fmt == LRFG_TUCKER) ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk))
+                                           : lr_aeff(P, E, view_of(u->tt));
   });
 }
 
@@ -1066,12 +1168,29 @@ lrfg_status lrfg_field_from_tt(lrfg_ctx* ctx, const lrfg_tt* x, int on_device, l
   return st;
 }
 
+lrfg_status lrfg_field_from_tucker(lrfg_ctx* ctx, const lrfg_tucker* x, int on_device, lrfg_field** out) {
+  if (!ctx) return LRFG_EINVAL;
+  lrfg_field* f = nullptr;
+  lrfg_status st = guard(ctx, [&] {
+    check_tucker(x);
+    LRFG_REQUIRE(out != nullptr, "null output");
+    new_field(ctx, LRFG_TUCKER, x->d, x->N, &f);
+    upload_tucker(ctx, x, on_device, f->tk);
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = f;
+  });
+  if (st != LRFG_OK && f) discard_field(f);
+  return st;
+}
+
 lrfg_status lrfg_field_info(const lrfg_field* f, lrfg_format* fmt, int* d, int N[3], int r[4]) {
   if (!f) return LRFG_EINVAL;
   if (fmt) *fmt = f->fmt;
   if (d) *d = f->d;
   if (N) for (int j = 0; j < 3; ++j) N[j] = f->N[j];
-  if (r) for (int j = 0; j < 4; ++j) r[j] = f->fmt == LRFG_TT ? f->tt.r[j] : 1;
+  if (r)
+    for (int j = 0; j < 4; ++j)
+      r[j] = f->fmt == LRFG_TT ? f->tt.r[j] : (f->fmt == LRFG_TUCKER && j < f->d ? f->tk.r[j] : 1);
   return LRFG_OK;
 }
 
@@ -1089,6 +1208,8 @@ lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* v
       LRFG_CUDA(cudaMemcpyAsync(tmp.get(), f->half.get(), sizeof(double2) * g.n_half, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
       full_inverse<double>(ctx, g, tmp.get(), nullptr, 1.0 / (double)g.n_real, target);
+    } else if (f->fmt == LRFG_TUCKER) {
+      tk_expand(ctx, tk_view(f->tk), target);
     } else {
       tt_expand(ctx, view_of(f->tt), target);
     }

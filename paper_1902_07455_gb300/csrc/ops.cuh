@@ -121,4 +121,48 @@ void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w,
                 int rmax, TT& out);
 
+// ---- tucker.cu ----------------------------------------------------------------------------------
+// Tucker tensor on the device: core (r_0, .., r_{d-1}) row-major, factor j (N_j, r_j) row-major
+struct TK {
+  int d = 0;
+  int N[3] = {1, 1, 1};
+  int r[3] = {1, 1, 1};
+  DBuf<double> core;
+  DBuf<double> fac[3];
+};
+struct TKView {
+  int d;
+  int N[3];
+  int r[3];
+  const double* core;
+  const double* fac[3];
+};
+struct TKSolveResult {
+  double Aeff;
+  int iters;
+  double rel_resid;
+  int applies;
+};
+TKView tk_view(const TK& x);
+void tk_alloc(lrfg_ctx* ctx, TK& x, int d, const int* N, const int* r);
+void tk_copy(lrfg_ctx* ctx, const TKView& x, TK& out);
+void tk_mode_operator(lrfg_ctx* ctx, const TKView& x, int j, int kind, double param, double scale, TK& out);
+void tk_hadamard(lrfg_ctx* ctx, const TKView& x, const TKView& y, TK& out);
+void tk_add_many(lrfg_ctx* ctx, const TKView* xs, const double* scales, int nb, TK& out);
+void tk_round(lrfg_ctx* ctx, const TKView& x, int rmax, TK& out);
+void tk_dot_device(lrfg_ctx* ctx, const TKView& x, const TKView& y, double* out_dev);
+double tk_dot(lrfg_ctx* ctx, const TKView& x, const TKView& y);
+void tk_expand(lrfg_ctx* ctx, const TKView& x, double* values);
+void tk_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int rmax, double tol, TK& out);
+void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
+                TK& out);
+void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
+              const std::vector<double>& pw, int rank, TK& out);
+void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
+            const std::vector<double>& pw, int rank, TK& out);
+double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u);
+TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
+                       const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
+                       TK& best_u);
+
 }  // namespace lrfg
