@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--pinv-eps", type=float, default=0.1)
     p.add_argument("--maxit", type=int, default=60)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--format", choices=["tt", "tucker"], default="tt",
+                   help="low-rank solution format of the timed solve (the coefficient is the same rank-10 TT; a "
+                        "Tucker problem compresses it by HOSVD)")
     p.add_argument("--workload", choices=["c2", "c3"], default="c2",
                    help="c2: lognormal SE-GRF, coefficient TT rank 10 (default, N=243); c3: tanh-smoothed cube of "
                         "contrast 100, coefficient rank 2 (N=1215 unless --N is given)")
@@ -69,9 +72,10 @@ def dist_env():
 
 
 def workload_config(args):
+    fmt = "Tucker" if args.format == "tucker" else "TT"
     return {"workload": f"d=3 N={args.N}^3 lognormal SE-GRF (l=0.2, var=1, seed {SEED}), E=(1,0,0); "
-                        f"TT rank {args.rank} MinRes vs full FP64 PCG",
-            "d": 3, "N": args.N, "coeff_tt_rank": args.coeff_rank, "tt_rank": args.rank,
+                        f"{fmt} rank {args.rank} MinRes vs full FP64 PCG",
+            "d": 3, "N": args.N, "coeff_tt_rank": args.coeff_rank, "format": args.format, "tt_rank": args.rank,
             "pinv_eps": args.pinv_eps, "precision": "fp64", "l2": "flushed between steps (512 MiB write)"}
 
 
@@ -278,7 +282,8 @@ def run_ours(args):
     f_in.free()
     f_out.free()
 
-    Ptt = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, tol=1e-12, maxit=args.maxit,
+    lr_fmt = lrfg.TUCKER if args.format == "tucker" else lrfg.TT
+    Ptt = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=1e-12, maxit=args.maxit,
                       stop_on_increase=True)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     stream = ctx.stream
@@ -389,7 +394,8 @@ def solve_host(ctx, host_cores, args, E):
     for j in range(4):
         c.tt.r[j] = rr[j]
     o = L.lrfg_opts()
-    o.fmt, o.prec, o.rank, o.pinv_eps = L.LRFG_TT, L.LRFG_FP64, args.rank, args.pinv_eps
+    o.fmt = L.LRFG_TUCKER if args.format == "tucker" else L.LRFG_TT
+    o.prec, o.rank, o.pinv_eps = L.LRFG_FP64, args.rank, args.pinv_eps
     o.tol, o.maxit, o.stop_on_increase = 1e-12, args.maxit, 1
     res = L.lrfg_result()
     Ed = (C.c_double * 3)(*E)

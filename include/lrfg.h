@@ -10,7 +10,11 @@
  *   LRFG_TT      tensor train of fixed rank r; the truncated operator of Eq. (Pls_lowrank) and the
  *                minimal-residual iteration with truncation of Sec. 3.3;
  *   LRFG_TUCKER  Tucker tensor of fixed multilinear rank r (App. A.2), same operator and iteration,
- *                truncation by factor orthonormalisation + HOSVD of the core (App. A.2.3).
+ *                truncation by factor orthonormalisation + HOSVD of the core (App. A.2.3);
+ *   LRFG_CP      canonical format, d = 2 only (App. A.1; Sec. 3.1 leaves d >= 3 out as ill-posed):
+ *                there u = sum_i c_i x_i (x) y_i is a Tucker tensor and the CP truncation (QR of both
+ *                factors, SVD of R1 diag(c) R2^T, App. A.1.3) is the d = 2 Tucker truncation, so CP
+ *                problems run the Tucker path; their fields are Tucker fields (LRFG_ENOTSUP for d = 3).
  * The coefficient is isotropic, A(x) = a(x) I, given as grid values, a tensor train or a Tucker tensor.
  * A Tucker problem built from grid values or a TT compresses the coefficient by HOSVD of its grid,
  * keeping singular values above 1e-7 of the largest in each mode (at most 64 per mode): the HOSVD
@@ -58,7 +62,7 @@ typedef enum {
   LRFG_ENOTSUP = 6   /* valid but not supported by this build */
 } lrfg_status;
 
-typedef enum { LRFG_FULL = 0, LRFG_TUCKER = 2, LRFG_TT = 3 } lrfg_format;
+typedef enum { LRFG_FULL = 0, LRFG_CP = 1, LRFG_TUCKER = 2, LRFG_TT = 3 } lrfg_format;
 typedef enum { LRFG_FP64 = 0, LRFG_MIXED = 1 } lrfg_prec;
 
 /* spectral multipliers m(k) applied along one mode by F^{-1} diag(m) F (Sec. 2.2.1, Sec. 3.2) */

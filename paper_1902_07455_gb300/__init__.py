@@ -22,10 +22,10 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "TUCKER", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
+__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "TUCKER", "CP", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
            "MUL_GAUSS", "library_path"]
 
-FULL, TUCKER, TT = L.LRFG_FULL, L.LRFG_TUCKER, L.LRFG_TT
+FULL, CP, TUCKER, TT = L.LRFG_FULL, L.LRFG_CP, L.LRFG_TUCKER, L.LRFG_TT
 FP64, MIXED = L.LRFG_FP64, L.LRFG_MIXED
 MUL_IDENTITY, MUL_DERIV, MUL_GAUSS = L.LRFG_MUL_IDENTITY, L.LRFG_MUL_DERIV, L.LRFG_MUL_GAUSS
 

@@ -8,7 +8,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblrfg.so")
 
 LRFG_OK, LRFG_EINVAL, LRFG_ENOMEM, LRFG_ENOCONV, LRFG_ECUDA, LRFG_ETIMEOUT, LRFG_ENOTSUP = range(7)
-LRFG_FULL, LRFG_TUCKER, LRFG_TT = 0, 2, 3
+LRFG_FULL, LRFG_CP, LRFG_TUCKER, LRFG_TT = 0, 1, 2, 3
 LRFG_FP64, LRFG_MIXED = 0, 1
 LRFG_MUL_IDENTITY, LRFG_MUL_DERIV, LRFG_MUL_GAUSS = 0, 1, 2
 

@@ -244,6 +244,10 @@ void check_tt(const lrfg_tt* x) {
   for (int j = 0; j < x->d; ++j) LRFG_REQUIRE(x->cores[j] != nullptr, "null TT carriage %d", j);
 }
 
+// CP (canonical) solutions exist for d = 2 only, where they are Tucker tensors whose truncation (QR of
+// both factors, SVD of R1 diag(c) R2^T, App. A.1.3) is the d = 2 Tucker truncation: they share its path
+bool tucker_like(int fmt) { return fmt == LRFG_TUCKER || fmt == LRFG_CP; }
+
 void check_tucker(const lrfg_tucker* x) {
   LRFG_REQUIRE(x != nullptr, "null Tucker tensor");
   check_grid(x->d, x->N);
@@ -477,7 +481,8 @@ void discard_field(lrfg_field* f) {
 
 void check_field(const lrfg_problem* P, const lrfg_field* f) {
   LRFG_REQUIRE(f != nullptr, "null field");
-  LRFG_REQUIRE(f->fmt == P->opts.fmt, "field format does not match the problem");
+  LRFG_REQUIRE(f->fmt == P->opts.fmt || (tucker_like(f->fmt) && tucker_like(P->opts.fmt)),
+               "field format does not match the problem");
   LRFG_REQUIRE(f->d == P->d, "field order does not match the problem");
   for (int j = 0; j < P->d; ++j) LRFG_REQUIRE(f->N[j] == P->N[j], "field grid does not match the problem");
 }
@@ -495,7 +500,7 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     } else {
       full_apply<double>(P, in->half.get(), out->half.get(), 1);
     }
-  } else if (P->opts.fmt == LRFG_TUCKER) {
+  } else if (tucker_like(P->opts.fmt)) {
     TK res;
     tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res);
     out->tk = std::move(res);
@@ -585,7 +590,7 @@ void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field
   for (int j = 0; j < 4; ++j) res->ranks[j] = j < P->d ? best.r[j] : 1;
   if (u_out) {
     lrfg_field* f;
-    new_field(P->ctx, LRFG_TUCKER, P->d, P->N, &f);
+    new_field(P->ctx, P->opts.fmt, P->d, P->N, &f);
     f->tk = std::move(best);
     *u_out = f;
   }
@@ -933,8 +938,10 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
   lrfg_status st = guard(ctx, [&] {
     LRFG_REQUIRE(coeff && opts && out, "null argument");
     check_grid(coeff->d, coeff->N);
-    LRFG_REQUIRE(opts->fmt == LRFG_FULL || opts->fmt == LRFG_TT || opts->fmt == LRFG_TUCKER,
-                 "solution format must be LRFG_FULL, LRFG_TT or LRFG_TUCKER");
+    LRFG_REQUIRE(opts->fmt == LRFG_FULL || opts->fmt == LRFG_TT || tucker_like(opts->fmt),
+                 "solution format must be LRFG_FULL, LRFG_CP, LRFG_TUCKER or LRFG_TT");
+    if (opts->fmt == LRFG_CP && coeff->d != 2)
+      fail(LRFG_ENOTSUP, "LRFG_CP is provided for d = 2 (its truncation is ill-posed for d >= 3, App. A.1)");
     LRFG_REQUIRE(opts->prec == LRFG_FP64 || opts->prec == LRFG_MIXED, "unknown precision %d", (int)opts->prec);
     if (opts->prec == LRFG_MIXED && opts->fmt != LRFG_FULL)
       fail(LRFG_ENOTSUP, "LRFG_MIXED is implemented for LRFG_FULL solutions only");
@@ -963,7 +970,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       LRFG_REQUIRE(bad < 0, "coefficient must be positive and finite (index %lld)", bad);
       if (opts->fmt == LRFG_FULL) {
         P->a_full = std::move(a);
-      } else if (opts->fmt == LRFG_TUCKER) {
+      } else if (tucker_like(opts->fmt)) {
         tk_compress(ctx, P->d, P->N, a.get(), 64, 1e-7, P->a_tk);
       } else {
         tt_compress(ctx, P->d, P->N, a.get(), opts->rank, 0.0, P->a_tt);
@@ -974,7 +981,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       check_tucker(&coeff->tk);
       TK a;
       upload_tucker(ctx, &coeff->tk, coeff->on_device, a);
-      if (opts->fmt == LRFG_TUCKER) {
+      if (tucker_like(opts->fmt)) {
         P->a_tk = std::move(a);
       } else {
         P->a_full = DBuf<double>(ctx->pool, n);
@@ -992,7 +999,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       } else {
         P->a_full = DBuf<double>(ctx->pool, n);
         tt_expand(ctx, view_of(a), P->a_full.get());
-        if (opts->fmt == LRFG_TUCKER) tk_compress(ctx, P->d, P->N, P->a_full.get(), 64, 1e-7, P->a_tk);
+        if (tucker_like(opts->fmt)) tk_compress(ctx, P->d, P->N, P->a_full.get(), 64, 1e-7, P->a_tk);
       }
     }
     if (opts->fmt == LRFG_FULL) {
@@ -1034,7 +1041,7 @@ lrfg_status lrfg_problem_free(lrfg_problem* P) {
 lrfg_status lrfg_problem_coeff_ranks(const lrfg_problem* P, int ranks[4]) {
   if (!P || !ranks) return LRFG_EINVAL;
   for (int j = 0; j < 4; ++j)
-    ranks[j] = P->opts.fmt == LRFG_TT ? P->a_tt.r[j] : (P->opts.fmt == LRFG_TUCKER && j < P->d ? P->a_tk.r[j] : 1);
+    ranks[j] = P->opts.fmt == LRFG_TT ? P->a_tt.r[j] : (tucker_like(P->opts.fmt) && j < P->d ? P->a_tk.r[j] : 1);
   return LRFG_OK;
 }
 
@@ -1076,7 +1083,7 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
       } else {
         full_rhs<double>(P, E, f->half.get(), 1);
       }
-    } else if (P->opts.fmt == LRFG_TUCKER) {
+    } else if (tucker_like(P->opts.fmt)) {
       tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk);
     } else {
       lr_rhs(P, E, f->tt);
@@ -1100,7 +1107,7 @@ lrfg_status lrfg_problem_solve(lrfg_problem* P, const double* E, lrfg_result* re
       if (P->opts.prec == LRFG_MIXED) solve_full<float>(P, E, res, u_out);
       else solve_full<double>(P, E, res, u_out);
     }
-    else if (P->opts.fmt == LRFG_TUCKER) solve_tucker(P, E, res, u_out);
+    else if (tucker_like(P->opts.fmt)) solve_tucker(P, E, res, u_out);
     else solve_tt(P, E, res, u_out);
     LRFG_CUDA(cudaStreamSynchronize(P->ctx->stream));
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1117,7 +1124,7 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field
     LRFG_REQUIRE(E && Aeff, "null argument");
     check_field(P, u);
     *Aeff = (P->opts.fmt == LRFG_FULL)     ? full_aeff(P, E, u->half.get())
-            : (P->opts.fmt == LRFG_TUCKER) ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk))
+            : tucker_like(P->opts.fmt)     ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk))
                                            : lr_aeff(P, E, view_of(u->tt));
   });
 }
@@ -1190,7 +1197,7 @@ lrfg_status lrfg_field_info(const lrfg_field* f, lrfg_format* fmt, int* d, int N
   if (N) for (int j = 0; j < 3; ++j) N[j] = f->N[j];
   if (r)
     for (int j = 0; j < 4; ++j)
-      r[j] = f->fmt == LRFG_TT ? f->tt.r[j] : (f->fmt == LRFG_TUCKER && j < f->d ? f->tk.r[j] : 1);
+      r[j] = f->fmt == LRFG_TT ? f->tt.r[j] : (tucker_like(f->fmt) && j < f->d ? f->tk.r[j] : 1);
   return LRFG_OK;
 }
 
@@ -1208,7 +1215,7 @@ lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* v
       LRFG_CUDA(cudaMemcpyAsync(tmp.get(), f->half.get(), sizeof(double2) * g.n_half, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
       full_inverse<double>(ctx, g, tmp.get(), nullptr, 1.0 / (double)g.n_real, target);
-    } else if (f->fmt == LRFG_TUCKER) {
+    } else if (tucker_like(f->fmt)) {
       tk_expand(ctx, tk_view(f->tk), target);
     } else {
       tt_expand(ctx, view_of(f->tt), target);

@@ -105,3 +105,44 @@ def test_tucker_coefficient_from_grid(ctx):
     assert P.coeff_ranks()[:3] == [2, 2, 2]
     res, _ = P.solve(E, want_field=False)
     assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"]
+
+
+# ---- canonical (CP) format, d = 2 (App. A.1): the oracle's CP path against LRFG_CP --------------------
+def _cp_as_tucker(c, B1, B2):
+    return lrfg.TuckerTensor.from_numpy(np.diag(np.asarray(c, dtype=np.float64)), [B1, B2])
+
+
+@pytest.mark.parametrize("N,rank,kind", [(45, 6, "square"), (63, 8, "cube"), (31, 4, "cube")])
+def test_cp_solve_matches_oracle_minres(ctx, N, rank, kind):
+    d = 2
+    _, terms, w = square_inclusion(d, N) if kind == "square" else smoothed_cube(d, N, contrast=10.0)
+    op = lr.LowRankGaNi(lr.cp_from_separable(terms, w), (N, N), fmt="cp", rank=rank, pinv_eps=0.1)
+    E = np.eye(d)[0]
+    ref = lr.minres(op, E, tol=1e-10, maxit=60)
+    P = ctx.problem(_cp_as_tucker(*lr.cp_from_separable(terms, w)), lrfg.CP, rank=rank, pinv_eps=0.1, tol=1e-10,
+                    maxit=60)
+    res, u = P.solve(E)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"]
+    # fields agree up to a constant (P~^-1 does not vanish at k = 0, so rounding noise there can leave a
+    # tiny mean); compare the zero-mean parts
+    g, h = u.full(), np.real(lr.cp_full(lr.cp_idft(ref["u"])))
+    assert rel(g - g.mean(), h - h.mean()) <= 1e-6
+
+
+def test_cp_apply_matches_oracle(ctx):
+    N, rank = 45, 5
+    _, terms, w = smoothed_cube(2, N, contrast=10.0)
+    op = lr.LowRankGaNi(lr.cp_from_separable(terms, w), (N, N), fmt="cp", rank=rank, pinv_eps=0.1)
+    rng = np.random.default_rng(4)
+    x = (rng.standard_normal(3), rng.standard_normal((N, 3)), rng.standard_normal((N, 3)))
+    ref = np.real(lr.cp_full(lr.cp_idft(op.apply(lr.cp_dft(x)))))
+    P = ctx.problem(_cp_as_tucker(*lr.cp_from_separable(terms, w)), lrfg.CP, rank=rank, pinv_eps=0.1)
+    out = P.apply(ctx.field_from_tucker(_cp_as_tucker(*x))).full()
+    assert rel(out, ref) <= 1e-7
+
+
+def test_cp_three_dimensional_is_not_supported(ctx):
+    from paper_1902_07455_gb300 import _lib as L
+    with pytest.raises(lrfg.LrfgError) as e:
+        ctx.problem(np.ones((9, 9, 9)), lrfg.CP, rank=2)
+    assert e.value.status == L.LRFG_ENOTSUP
