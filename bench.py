@@ -54,9 +54,15 @@ def parse():
     p.add_argument("--format", choices=["tt", "tucker"], default="tt",
                    help="low-rank solution format of the timed solve (the coefficient is the same rank-10 TT; a "
                         "Tucker problem compresses it by HOSVD)")
-    p.add_argument("--workload", choices=["c2", "c3"], default="c2",
+    p.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
                    help="c2: lognormal SE-GRF, coefficient TT rank 10 (default, N=243); c3: tanh-smoothed cube of "
-                        "contrast 100, coefficient rank 2 (N=1215 unless --N is given)")
+                        "contrast 100, coefficient rank 2 (N=1215 unless --N is given); c4: a batch of seeded "
+                        "microstructures of mixed N and rank through the serving executor; c5: a Poisson stream "
+                        "of requests (d in {2,3}, N 63-729, rank tolerance 1e-6-1e-4) served as they arrive")
+    p.add_argument("--count", type=int, default=64, help="c4: requests in the batch")
+    p.add_argument("--workers", type=int, default=8, help="c4/c5: executor worker streams")
+    p.add_argument("--rate", type=float, default=200.0, help="c5: mean arrival rate (requests/s)")
+    p.add_argument("--rank-cap", type=int, default=30, help="c5: rank cap of the tolerance truncation")
     p.add_argument("--c3-full", choices=["none", "mixed", "fp64"], default="mixed",
                    help="c3: full-format anchor solve on the expanded coefficient")
     p.add_argument("--case", choices=["tt_apply", "full_apply", "full_apply_mixed"], default=None,
@@ -539,6 +545,223 @@ def run_c3(args):
     ctx.close()
 
 
+def c4_requests(count, seed=SEED):
+    """Seeded batch: half lognormal SE-GRF (l uniform in [0.1, 0.3], variance (ln(contrast)/4)^2 so that
+    exp(+-2 sigma) spans the contrast), half tanh-smoothed inclusions (sphere or cube, radius / half-side
+    uniform in [0.15, 0.35]); contrast log-uniform in [5, 100]; N uniform in {45, 81, 135, 243}; TT rank
+    uniform in [5, 30].  Grid coefficients (lognormal, sphere) are TT-compressed to rank 10 on the GPU
+    here, before timing; the cube is its exact rank-2 TT.  Each request: (TT carriages on the host, rank,
+    description)."""
+    import torch
+    import paper_1902_07455_gb300 as lrfg
+    from synthetic import lognormal_grf, smoothed_cube, smoothed_sphere
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ctx = lrfg.Context(0)
+    out = []
+    for i in range(count):
+        N = int(rng.choice([45, 81, 135, 243]))
+        r = int(rng.integers(5, 31))
+        contrast = float(np.exp(rng.uniform(np.log(5.0), np.log(100.0))))
+        if i % 2 == 0:
+            ell = float(rng.uniform(0.1, 0.3))
+            a = lognormal_grf(3, N, ell=ell, var=(np.log(contrast) / 4.0) ** 2, seed=seed + i)
+            desc = f"lognormal l={ell:.2f}"
+        else:
+            size = float(rng.uniform(0.15, 0.35))
+            if rng.integers(0, 2) == 0:
+                a = smoothed_sphere(3, N, contrast=contrast, radius=size)
+                desc = f"sphere R={size:.2f}"
+            else:
+                _, terms, w = smoothed_cube(3, N, contrast=contrast, c=size, full=False)
+                cores = [np.asarray(f, dtype=np.float64).reshape(1, N, 1) for f in terms[0]]
+                cores2 = [np.asarray(f, dtype=np.float64).reshape(1, N, 1) for f in terms[1]]
+                tt = ctx.tt_add(w[0], lrfg.TTensor.from_numpy(cores), w[1], lrfg.TTensor.from_numpy(cores2))
+                out.append((tt.numpy(), r, f"cube c={size:.2f} contrast={contrast:.1f} N={N} r={r}"))
+                continue
+        tt = ctx.tt_compress(torch.as_tensor(a, device="cuda:0"), 10)
+        out.append((tt.numpy(), r, f"{desc} contrast={contrast:.1f} N={N} r={r}"))
+    ctx.close()
+    return out
+
+
+def run_batch(B, reqs, maxit, pinv_eps):
+    """Submit every request at once to executor B; returns (seconds from first submission to last
+    completion, BatchResults)."""
+    import paper_1902_07455_gb300 as lrfg
+    t0 = time.perf_counter()
+    tickets = [B.submit(c, [1.0, 0.0, 0.0], lrfg.TT, rank=r, pinv_eps=pinv_eps, tol=1e-12, maxit=maxit)
+               for c, r, _ in reqs]
+    res = [B.wait(t) for t in tickets]
+    return time.perf_counter() - t0, res
+
+
+def run_c4(args):
+    """Batched throughput: `count` microstructures of mixed N and rank (c4_requests), every request
+    submitted at once to the executor; value = solves/s from first submission to last completion (host
+    clock, coefficient upload from host memory included: end to end by construction).  The same batch
+    through one worker gives the serial figure."""
+    from paper_1902_07455_gb300 import build
+    build.build()
+    t_gen = time.perf_counter()
+    reqs = c4_requests(args.count)
+    t_gen = time.perf_counter() - t_gen
+    import paper_1902_07455_gb300 as lrfg
+    # a warm pass (plans, twiddles and pools of every worker context), then the timed pass
+    with lrfg.Batch(0, workers=args.workers) as B:
+        run_batch(B, reqs, args.maxit, args.pinv_eps)
+        with ClockSampler(0) as clk:
+            dt, res = run_batch(B, reqs, args.maxit, args.pinv_eps)
+    # one worker: warmed on the largest requests, then the whole batch
+    big = sorted(reqs, key=lambda q: -q[0][1].shape[1] * q[1] ** 2)[:4]
+    with lrfg.Batch(0, workers=1) as B1:
+        run_batch(B1, big, args.maxit, args.pinv_eps)
+        dt1, res1 = run_batch(B1, reqs, args.maxit, args.pinv_eps)
+    lat = [b.total_s for b in res]
+    same = all(a.result.Aeff == b.result.Aeff and a.result.iters == b.result.iters for a, b in zip(res, res1))
+    line = {
+        "metric": METRIC, "value": len(reqs) / dt, "unit": "solves/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": 1e3 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(reqs)} seeded d=3 microstructures (half lognormal SE-GRF, half "
+                               f"tanh-smoothed sphere/cube inclusions, contrast 5-100), N in {{45,81,135,243}}, "
+                               f"TT rank 5-30, coefficient TT rank 10 (cube: exact 2), TT MinRes, FP64",
+                   "count": len(reqs), "workers": args.workers, "maxit": args.maxit, "pinv_eps": args.pinv_eps},
+        "serial_solves_per_s": len(reqs) / dt1, "overlap_speedup": dt1 / dt,
+        "bitwise_equal_to_serial": same,
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "run_s_sum": sum(b.run_s for b in res), "iters_mean": float(np.mean([b.result.iters for b in res])),
+        "e2e": {"value": len(reqs) / dt, "unit": "solves/s",
+                "h2d_bytes_per_step": int(sum(sum(c.nbytes for c in cs) for cs, _, _ in reqs)),
+                "d2h_bytes_per_step": 48 * len(reqs)},
+        "clocks": clk.summary(), "input_generation_s": t_gen,
+        "requests": [{"desc": d, "aeff": b.result.Aeff, "iters": b.result.iters, "run_s": round(b.run_s, 4)}
+                     for (_, _, d), b in zip(reqs, res)],
+    }
+    print(json.dumps(line), flush=True)
+
+
+SMOOTH_N = [63, 75, 81, 105, 125, 135, 147, 175, 189, 225, 243, 245, 315, 343, 375, 405, 441, 525, 567, 625, 675,
+            729]  # odd sizes in [63, 729] with prime factors 3, 5, 7 only
+
+
+def separable_tt(terms, weights):
+    """TT carriages of sum_i weights[i] * outer(terms[i]) (rank = number of terms): the first carriage
+    holds the weighted first factors, the others are block diagonal / block columns."""
+    R, d = len(terms), len(terms[0])
+    N = [len(v) for v in terms[0]]
+    cores = []
+    for j in range(d):
+        a = 1 if j == 0 else R
+        b = 1 if j == d - 1 else R
+        c = np.zeros((a, N[j], b))
+        for i in range(R):
+            v = np.asarray(terms[i][j], dtype=np.float64) * (weights[i] if j == 0 else 1.0)
+            c[0 if j == 0 else i, :, 0 if j == d - 1 else i] = v
+        cores.append(c)
+    return cores
+
+
+def c5_requests(count, rate, seed=SEED + 5):
+    """Seeded request stream: exponential gaps of mean 1/rate; d in {2, 3} with equal probability; N uniform
+    over SMOOTH_N; rank tolerance log-uniform in [1e-6, 1e-4]; contrast log-uniform in [5, 100].  d = 2:
+    lognormal SE-GRF (grid, variance (ln(contrast)/4)^2), tanh-smoothed square (separable) or disc
+    (grid); d = 3: tanh-smoothed cube (separable, exact TT rank 2), laminate (rank 1), or for N <= 135 a
+    lognormal SE-GRF (grid).  Grid coefficients go to the executor as grid values (TT-compressed with the
+    request's tolerance on the GPU, inside the request).  Each request: (arrival offset in s, coefficient,
+    d, rank_tol, description)."""
+    from synthetic import laminate, lognormal_grf, smoothed_cube, smoothed_sphere
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        d = int(rng.integers(2, 4))
+        N = int(rng.choice(SMOOTH_N))
+        rtol = float(10.0 ** rng.uniform(-6.0, -4.0))
+        contrast = float(np.exp(rng.uniform(np.log(5.0), np.log(100.0))))
+        size = float(rng.uniform(0.15, 0.35))
+        kind = int(rng.integers(0, 3))
+        if d == 2 and kind == 0:
+            coeff = lognormal_grf(2, N, ell=float(rng.uniform(0.1, 0.3)), var=(np.log(contrast) / 4.0) ** 2,
+                                  seed=seed + i)
+            desc = "lognormal"
+        elif d == 2 and kind == 1:
+            _, terms, w = smoothed_cube(2, N, contrast=contrast, c=size, full=False)
+            coeff, desc = separable_tt(terms, w), "square"
+        elif d == 2:
+            coeff, desc = smoothed_sphere(2, N, contrast=contrast, radius=size), "disc"
+        elif kind == 0 and N <= 135:
+            coeff = lognormal_grf(3, N, ell=float(rng.uniform(0.1, 0.3)), var=(np.log(contrast) / 4.0) ** 2,
+                                  seed=seed + i)
+            desc = "lognormal"
+        elif kind == 1:
+            _, terms, w = laminate(3, N, contrast=contrast, c=size, full=False)
+            coeff, desc = separable_tt(terms, w), "laminate"
+        else:
+            _, terms, w = smoothed_cube(3, N, contrast=contrast, c=size, full=False)
+            coeff, desc = separable_tt(terms, w), "cube"
+        out.append((t, coeff, d, rtol, f"d={d} N={N} {desc} contrast={contrast:.1f} rank_tol={rtol:.1e}"))
+    return out
+
+
+def run_c5(args):
+    """Serving: requests arrive on a seeded Poisson clock (c5_requests) and are submitted to the executor at
+    their arrival times by the host; each is a TT solve with the request's rank tolerance (rank cap
+    --rank-cap).  Latency = arrival to completion (queueing for a worker and HBM included); value =
+    completed requests / (last completion - first arrival)."""
+    import paper_1902_07455_gb300 as lrfg
+    from paper_1902_07455_gb300 import build
+    build.build()
+    t_gen = time.perf_counter()
+    reqs = c5_requests(args.count, args.rate)
+    t_gen = time.perf_counter() - t_gen
+
+    def serve(B, stream):
+        tickets = []
+        t0 = time.perf_counter()
+        for t_arr, coeff, d, rtol, _ in stream:
+            delay = t_arr - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            E = [1.0] + [0.0] * (d - 1)
+            tickets.append(B.submit(coeff, E, lrfg.TT, rank=args.rank_cap, pinv_eps=args.pinv_eps, tol=1e-10,
+                                    maxit=args.maxit, rank_tol=rtol, coeff_rank=args.coeff_rank))
+        res = []
+        for i, t in enumerate(tickets):
+            res.append(B.wait(t))
+            print(f"c5 {i} {stream[i][4]} run {res[-1].run_s:.3f} s latency {res[-1].total_s:.3f} s "
+                  f"ranks {res[-1].result.ranks} iters {res[-1].result.iters}", file=sys.stderr, flush=True)
+        return time.perf_counter() - t0, res
+
+    with lrfg.Batch(0, workers=args.workers) as B:
+        serve(B, [(0.0,) + r[1:] for r in reqs[: min(len(reqs), 2 * args.workers)]])  # warm the contexts
+        with ClockSampler(0) as clk:
+            span, res = serve(B, reqs)
+    lat = np.array([b.total_s for b in res])
+    queue = np.array([b.queue_s for b in res])
+    h2d = int(sum(sum(c.nbytes for c in q[1]) if isinstance(q[1], list) else q[1].nbytes for q in reqs))
+    line = {
+        "metric": METRIC, "value": len(res) / span, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"serving: {len(reqs)} requests, Poisson arrivals at {args.rate:g}/s, d in {{2,3}}, "
+                               f"N in 3-5-7-smooth sizes 63-729, TT MinRes with rank tolerance 1e-6-1e-4 "
+                               f"(cap {args.rank_cap}), grid coefficients TT-compressed to rank <= {args.coeff_rank}, "
+                               f"FP64", "count": len(reqs), "rate": args.rate, "coeff_rank": args.coeff_rank,
+                   "workers": args.workers, "maxit": args.maxit, "rank_cap": args.rank_cap},
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "queue_p50_s": float(np.percentile(queue, 50)), "queue_p99_s": float(np.percentile(queue, 99)),
+        "run_p50_s": float(np.percentile([b.run_s for b in res], 50)),
+        "offered_rate": len(reqs) / reqs[-1][0], "arrival_span_s": reqs[-1][0],
+        "e2e": {"value": len(res) / span, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 48 * len(res)},
+        "clocks": clk.summary(), "input_generation_s": t_gen,
+        "requests": [{"desc": q[4], "aeff": b.result.Aeff, "iters": b.result.iters, "ranks": b.result.ranks,
+                      "run_s": round(b.run_s, 4), "latency_s": round(b.total_s, 4)} for q, b in zip(reqs, res)],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_case(args):
     """Two applications of one operator of the benchmark workload (coefficient compressed to rank
     coeff-rank on the GPU): the launch sequence a profiler capture of one kernel needs, and nothing else."""
@@ -575,6 +798,14 @@ def main():
         return
     if args.workload == "c3" and args.impl == "ours":
         run_c3(args)
+        return
+    if args.workload == "c4" and args.impl == "ours":
+        run_c4(args)
+        return
+    if args.workload == "c5" and args.impl == "ours":
+        if "--count" not in sys.argv:
+            args.count = 200
+        run_c5(args)
         return
     if args.impl == "reference":
         line = run_reference(args)

@@ -107,12 +107,17 @@ typedef struct {
 typedef struct {
   lrfg_format fmt;      /* solution format: LRFG_FULL (PCG), LRFG_TT or LRFG_TUCKER (minimal residual) */
   lrfg_prec prec;       /* LRFG_FP64, or LRFG_MIXED with fmt == LRFG_FULL */
-  int rank;             /* LRFG_TT: the fixed rank of every truncation T (Sec. 4.2) */
+  int rank;             /* LRFG_TT: the fixed rank of every truncation T (Sec. 4.2), or the rank cap */
   double pinv_eps;      /* LRFG_TT: relative accuracy of the exponential-sum P~^-1 on [1, max k.k]
                            (0 selects 0.1) */
   double tol;           /* relative residual tolerance (preconditioned residual) */
   int maxit;            /* iteration cap */
   int stop_on_increase; /* LRFG_TT: stop when the residual norm fails to decrease (Sec. 4.3) */
+  double rank_tol;      /* LRFG_TT / LRFG_TUCKER: 0 = fixed rank `rank`.  > 0: every truncation T keeps the
+                           smallest ranks (at most `rank`) whose relative Frobenius error is <= rank_tol:
+                           tol / sqrt(d-1) per TT bond (App. A.3.3), tol / sqrt(d) per Tucker mode (App.
+                           A.2.3); a grid coefficient is TT-compressed with the same tolerance */
+  int coeff_rank;       /* LRFG_TT with grid values: rank cap r_A of the coefficient's TT-SVD (0: `rank`) */
 } lrfg_opts;
 
 typedef struct {
@@ -192,11 +197,19 @@ lrfg_status lrfg_tt_add(lrfg_ctx* ctx, double alpha, const lrfg_tt* x, double be
  * min(rmax, x->r[j]) N[j] min(rmax, x->r[j+1]) doubles.  Carriages 1..d-1 of out are
  * left-orthonormal. */
 lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out);
+/* The same with a tolerance (tol in [0, 1), 0 = lrfg_tt_round): the smallest ranks <= rmax whose
+ * relative Frobenius error is <= tol, tol / sqrt(d-1) per bond (App. A.3.3); the output ranks in out->r
+ * may be below the cap, the carriages are written contiguously with those ranks. */
+lrfg_status lrfg_tt_round_tol(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, double tol, lrfg_tt* out);
 /* Tucker truncation T (App. A.2.3) of a Tucker tensor with device buffers into out (device buffers of
  * at least prod_j min(rmax, r_j) core and N_j min(rmax, r_j) factor doubles; out->r is set): every
  * factor orthonormalised (unit-column balanced Gram matrix, pivoted Cholesky), its triangular factor
  * moved into the core, then the HOSVD of the core keeps min(rmax, r_j) vectors per mode. */
 lrfg_status lrfg_tucker_round(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, lrfg_tucker* out);
+/* The same with a tolerance: per mode the smallest rank <= rmax whose dropped singular values of the
+ * core unfolding have norm <= tol / sqrt(d) of the tensor's (App. A.2.3); out->r holds the ranks, the
+ * core and factors are written contiguously with them. */
+lrfg_status lrfg_tucker_round_tol(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, double tol, lrfg_tucker* out);
 
 /* Euclidean inner product <x, y> = sum_k x[k] y[k] of two TTs (FP64 contraction). */
 lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);
@@ -236,7 +249,8 @@ lrfg_status lrfg_tt_expand(lrfg_ctx* ctx, const lrfg_tt* x, double* values);
  * ------------------------------------------------------------------------------------------- */
 
 /* Make the coefficient device-resident for the given options (copies it; caller buffers may be
- * freed afterwards).  For LRFG_TT a FULL coefficient is compressed by TT-SVD to rank opts->rank. */
+ * freed afterwards).  For LRFG_TT a FULL coefficient is compressed by TT-SVD to rank opts->coeff_rank
+ * (opts->rank when 0), with the tolerance opts->rank_tol when it is > 0. */
 lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lrfg_opts* opts,
                                 lrfg_problem** problem);
 lrfg_status lrfg_problem_free(lrfg_problem* problem);
@@ -266,6 +280,48 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* problem, const double* E, const lrfg
 /* One-shot convenience: create a problem, solve, free it. */
 lrfg_status lrfg_solve(lrfg_ctx* ctx, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,
                        lrfg_result* res, lrfg_field** u_out);
+
+/* ---------------------------------------------------------------------------------------------
+ * batch / serving executor (an extension beyond the paper: many independent solves of Sec. 4's
+ * problems, of different d, N, format and rank, overlapped on one GPU)
+ *
+ * W worker threads, each with its own non-blocking stream and context, take submitted requests in
+ * FIFO order.  A request starts when a worker is free and its device footprint fits, beside the
+ * footprints of the requests running, in hbm_budget_bytes (0: no cap; a request larger than the
+ * budget runs alone).  The footprint is the pool high-water mark measured on the last solve of the
+ * same shape (d, N, coefficient format and rank, solution format, precision, rank), or an estimate
+ * from the sizes before one ran.  Each request is one lrfg_solve on its worker's context, so its
+ * result is that of the same solve run alone.
+ * ------------------------------------------------------------------------------------------- */
+
+typedef struct lrfg_batch lrfg_batch;
+
+typedef struct {
+  double queue_s;    /* submission to start (waiting for a worker and for HBM) */
+  double run_s;      /* start to completion */
+  double total_s;    /* submission to completion: the request's latency */
+  double peak_bytes; /* device pool high-water mark of the solve */
+  int worker;        /* worker that ran it */
+  char message[200]; /* lrfg_last_error of the failed solve ("" on success) */
+} lrfg_batch_report;
+
+/* Start `workers` (1..64) worker threads on `device`.  LRFG_ECUDA if a stream or context cannot be
+ * created (nothing is left behind). */
+lrfg_status lrfg_batch_create(lrfg_batch** out, int device, int workers, size_t hbm_budget_bytes);
+/* Queue one solve.  The coefficient must be in host memory (on_device = 0): its buffers are copied
+ * before the call returns, as are E (d doubles) and *opts.  *ticket identifies the request.  Invalid
+ * sizes give LRFG_EINVAL here; everything else lrfg_solve checks is reported by lrfg_batch_poll. */
+lrfg_status lrfg_batch_submit(lrfg_batch* batch, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,
+                              unsigned long long* ticket);
+/* *ready = 1 when the request has completed; then *solve_status (lrfg_solve's status), *res and
+ * *report (each may be NULL) are filled and the ticket is retired (a second poll gives LRFG_EINVAL).
+ * wait = 1 blocks until it completes.  LRFG_EINVAL for an unknown or retired ticket. */
+lrfg_status lrfg_batch_poll(lrfg_batch* batch, unsigned long long ticket, int wait, int* ready,
+                            lrfg_status* solve_status, lrfg_result* res, lrfg_batch_report* report);
+/* Requests waiting, running, and the footprint bytes admitted for the running ones (each may be NULL). */
+lrfg_status lrfg_batch_info(lrfg_batch* batch, int* queued, int* running, size_t* in_flight_bytes);
+/* Drop the requests not yet started, wait for the running ones, stop the workers, free everything. */
+lrfg_status lrfg_batch_destroy(lrfg_batch* batch);
 
 /* ---------------------------------------------------------------------------------------------
  * fields

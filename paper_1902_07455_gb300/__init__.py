@@ -11,6 +11,8 @@ Objects
 ``TTensor``   a tensor train held as a list of CUDA float64 carriages (r_j, N_j, r_{j+1}).
 ``Problem``   a resident coefficient with the operator and the solvers for one format (FULL or TT).
 ``Field``     a library-owned operand or solution (FULL half spectrum or TT carriages).
+``Batch``     the serving executor: worker threads with their own streams and contexts that run
+              submitted solves concurrently, admitted by HBM footprint.
 """
 from __future__ import annotations
 
@@ -22,7 +24,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "LrfgError", "FULL", "TT", "TUCKER", "CP", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
+__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "Batch", "BatchResult", "LrfgError", "FULL", "TT", "TUCKER", "CP", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
            "MUL_GAUSS", "library_path"]
 
 FULL, CP, TUCKER, TT = L.LRFG_FULL, L.LRFG_CP, L.LRFG_TUCKER, L.LRFG_TT
@@ -273,11 +275,12 @@ class Context:
         self.check(self.lib.lrfg_tt_add(self.h, float(alpha), C.byref(xs), float(beta), C.byref(ys), C.byref(s)))
         return self._shrink(bufs, s)
 
-    def tt_round(self, x: TTensor, rmax: int) -> TTensor:
+    def tt_round(self, x: TTensor, rmax: int, tol: float = 0.0) -> TTensor:
+        """TT rounding to rank rmax, or with tol > 0 to the smallest ranks <= rmax within tol."""
         cap = [min(int(rmax), r) for r in x.ranks]
         bufs, s = self._tt_out(x.shape, cap)
         xs = x.to_struct()
-        self.check(self.lib.lrfg_tt_round(self.h, C.byref(xs), int(rmax), C.byref(s)))
+        self.check(self.lib.lrfg_tt_round_tol(self.h, C.byref(xs), int(rmax), float(tol), C.byref(s)))
         return self._shrink(bufs, s)
 
     def tt_dot(self, x: TTensor, y: TTensor) -> float:
@@ -323,7 +326,8 @@ class Context:
         self.check(self.lib.lrfg_tt_expand(self.h, C.byref(xs), _ptr(out)))
         return out
 
-    def tucker_round(self, x: TuckerTensor, rmax: int) -> TuckerTensor:
+    def tucker_round(self, x: TuckerTensor, rmax: int, tol: float = 0.0) -> TuckerTensor:
+        """Tucker truncation to ranks rmax, or with tol > 0 to the smallest ranks <= rmax within tol."""
         torch = _torch()
         k = [min(int(rmax), r) for r in x.ranks]
         dev = f"cuda:{self.device}"
@@ -331,7 +335,10 @@ class Context:
         facs = [torch.empty((n, kk), dtype=torch.float64, device=dev) for n, kk in zip(x.shape, k)]
         out = TuckerTensor(core, facs).to_struct()
         xs = x.to_struct()
-        self.check(self.lib.lrfg_tucker_round(self.h, C.byref(xs), int(rmax), C.byref(out)))
+        self.check(self.lib.lrfg_tucker_round_tol(self.h, C.byref(xs), int(rmax), float(tol), C.byref(out)))
+        r = [int(out.r[j]) for j in range(x.d)]
+        core = core.reshape(-1)[: int(np.prod(r))].reshape(tuple(r))
+        facs = [f.reshape(-1)[: n * rj].reshape(n, rj) for f, n, rj in zip(facs, x.shape, r)]
         return TuckerTensor(core, facs)
 
     def field_from_tucker(self, x: TuckerTensor) -> "Field":
@@ -342,9 +349,12 @@ class Context:
 
     # ---- problems and fields ---------------------------------------------------------------------
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
-                stop_on_increase: bool = True, prec: int = L.LRFG_FP64) -> "Problem":
-        """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only)."""
-        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec)
+                stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
+                coeff_rank: int = 0) -> "Problem":
+        """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only).
+        ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
+        rank cap of a grid coefficient's TT compression (0: ``rank``)."""
+        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -434,7 +444,8 @@ class Problem:
     """Resident coefficient + operator + solver for one format.  ``coeff``: a numpy/torch grid array
     (isotropic a(x) samples) or a TTensor of the coefficient."""
 
-    def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64):
+    def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64,
+                 rank_tol=0.0, coeff_rank=0):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -476,6 +487,7 @@ class Problem:
         o = L.lrfg_opts()
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
+        o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
         h = C.c_void_p()
         ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))
         del keep
@@ -525,5 +537,128 @@ class Problem:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+def _host_coeff(coeff):
+    """lrfg_coeff over host buffers for `coeff`: a grid array (numpy or torch), a TTensor or a list of
+    TT carriages, or a TuckerTensor / (core, factors) pair.  Returns (struct, buffers to keep alive)."""
+    c = L.lrfg_coeff()
+    c.on_device = 0
+    f64 = lambda a: np.ascontiguousarray(a.detach().cpu().numpy() if hasattr(a, "detach") else a, dtype=np.float64)
+    if isinstance(coeff, TuckerTensor) or (isinstance(coeff, tuple) and len(coeff) == 2):
+        core, factors = (coeff.core, coeff.factors) if isinstance(coeff, TuckerTensor) else coeff
+        core, factors = f64(core), [f64(f) for f in factors]
+        d = len(factors)
+        c.d, c.fmt = d, L.LRFG_TUCKER
+        c.tk.d = d
+        c.tk.core = core.ctypes.data
+        for j, f in enumerate(factors):
+            c.N[j] = c.tk.N[j] = f.shape[0]
+            c.tk.r[j] = f.shape[1]
+            c.tk.factors[j] = f.ctypes.data
+        return c, [core] + factors
+    if isinstance(coeff, (TTensor, list)):
+        cores = [f64(x) for x in (coeff.cores if isinstance(coeff, TTensor) else coeff)]
+        d = len(cores)
+        c.d, c.fmt = d, L.LRFG_TT
+        c.tt.d = d
+        for j, x in enumerate(cores):
+            c.N[j] = c.tt.N[j] = x.shape[1]
+            c.tt.r[j] = x.shape[0]
+            c.tt.cores[j] = x.ctypes.data
+        c.tt.r[d] = 1
+        return c, cores
+    arr = f64(coeff)
+    if arr.ndim not in (2, 3):
+        raise ValueError("grid coefficient must have 2 or 3 axes")
+    c.d, c.fmt = arr.ndim, L.LRFG_FULL
+    for j, n in enumerate(arr.shape):
+        c.N[j] = n
+    c.values = arr.ctypes.data
+    return c, [arr]
+
+
+@dataclass
+class BatchResult:
+    result: Result
+    queue_s: float   # submission to start
+    run_s: float     # start to completion
+    total_s: float   # latency: submission to completion
+    peak_bytes: float
+    worker: int
+
+
+class Batch:
+    """The serving executor of the library (``lrfg_batch_*``): ``workers`` threads, each with its own
+    non-blocking stream and context, run submitted solves concurrently in FIFO order; a request starts
+    when a worker is free and its HBM footprint fits in ``budget`` bytes (0: no cap) beside the requests
+    running.  Coefficients are host arrays, copied at submission."""
+
+    def __init__(self, device: int = 0, workers: int = 4, budget: int = 0):
+        self.lib = L.load()
+        h = C.c_void_p()
+        st = self.lib.lrfg_batch_create(C.byref(h), int(device), int(workers), int(budget))
+        if st != L.LRFG_OK:
+            raise LrfgError(st, "lrfg_batch_create failed")
+        self.h = h
+        self.workers = int(workers)
+
+    def submit(self, coeff, E, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8,
+               maxit: int = 200, stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
+               coeff_rank: int = 0) -> int:
+        c, keep = _host_coeff(coeff)
+        o = L.lrfg_opts()
+        o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
+        o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
+        o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
+        t = C.c_ulonglong()
+        st = self.lib.lrfg_batch_submit(self.h, C.byref(c), _dvec(E), C.byref(o), C.byref(t))
+        del keep
+        if st != L.LRFG_OK:
+            raise LrfgError(st, "lrfg_batch_submit rejected the request")
+        return int(t.value)
+
+    def poll(self, ticket: int, wait: bool = False):
+        """The request's BatchResult once it has completed (None before); the ticket is then retired.
+        A solve that failed (other than by reaching maxit) raises LrfgError."""
+        ready, sst = C.c_int(), C.c_int()
+        res, tm = L.lrfg_result(), L.lrfg_batch_report()
+        st = self.lib.lrfg_batch_poll(self.h, C.c_ulonglong(ticket), int(bool(wait)), C.byref(ready), C.byref(sst),
+                                      C.byref(res), C.byref(tm))
+        if st != L.LRFG_OK:
+            raise LrfgError(st, f"unknown or retired ticket {ticket}")
+        if not ready.value:
+            return None
+        if sst.value not in (L.LRFG_OK, L.LRFG_ENOCONV):
+            raise LrfgError(sst.value, f"request {ticket}: {tm.message.decode(errors='replace')}")
+        r = Result(res.Aeff, res.iters, res.rel_resid, bool(res.converged), res.applies, list(res.ranks), res.seconds,
+                   sst.value)
+        return BatchResult(r, tm.queue_s, tm.run_s, tm.total_s, tm.peak_bytes, tm.worker)
+
+    def wait(self, ticket: int) -> BatchResult:
+        return self.poll(ticket, wait=True)
+
+    def info(self):
+        """(queued, running, admitted footprint bytes of the running requests)"""
+        q, r, b = C.c_int(), C.c_int(), C.c_size_t()
+        self.lib.lrfg_batch_info(self.h, C.byref(q), C.byref(r), C.byref(b))
+        return q.value, r.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrfg_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

@@ -32,12 +32,18 @@ class lrfg_coeff(C.Structure):
 
 class lrfg_opts(C.Structure):
     _fields_ = [("fmt", C.c_int), ("prec", C.c_int), ("rank", C.c_int), ("pinv_eps", C.c_double),
-                ("tol", C.c_double), ("maxit", C.c_int), ("stop_on_increase", C.c_int)]
+                ("tol", C.c_double), ("maxit", C.c_int), ("stop_on_increase", C.c_int), ("rank_tol", C.c_double),
+                ("coeff_rank", C.c_int)]
 
 
 class lrfg_result(C.Structure):
     _fields_ = [("Aeff", C.c_double), ("iters", C.c_int), ("rel_resid", C.c_double), ("converged", C.c_int),
                 ("applies", C.c_int), ("ranks", C.c_int * 4), ("seconds", C.c_double)]
+
+
+class lrfg_batch_report(C.Structure):
+    _fields_ = [("queue_s", C.c_double), ("run_s", C.c_double), ("total_s", C.c_double),
+                ("peak_bytes", C.c_double), ("worker", C.c_int), ("message", C.c_char * 200)]
 
 
 _P = C.c_void_p
@@ -63,9 +69,11 @@ SIGNATURES = {
     "lrfg_fibre_operator": (_ST, [_P, _P, _P, _I, _I, _I, _I, _D, _D]),
     "lrfg_tt_hadamard": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
     "lrfg_tucker_round": (_ST, [_P, C.POINTER(lrfg_tucker), _I, C.POINTER(lrfg_tucker)]),
+    "lrfg_tucker_round_tol": (_ST, [_P, C.POINTER(lrfg_tucker), _I, _D, C.POINTER(lrfg_tucker)]),
     "lrfg_field_from_tucker": (_ST, [_P, C.POINTER(lrfg_tucker), _I, C.POINTER(_P)]),
     "lrfg_tt_add": (_ST, [_P, _D, C.POINTER(lrfg_tt), _D, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
     "lrfg_tt_round": (_ST, [_P, C.POINTER(lrfg_tt), _I, C.POINTER(lrfg_tt)]),
+    "lrfg_tt_round_tol": (_ST, [_P, C.POINTER(lrfg_tt), _I, _D, C.POINTER(lrfg_tt)]),
     "lrfg_tt_dot": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(_D)]),
     "lrfg_tt_dot_noalloc": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), _P]),
     "lrfg_tt_precond": (_ST, [_P, C.POINTER(lrfg_tt), _D, _I, C.POINTER(lrfg_tt)]),
@@ -87,6 +95,13 @@ SIGNATURES = {
     "lrfg_field_export_full": (_ST, [_P, _P, _P, _I]),
     "lrfg_field_export_tt": (_ST, [_P, _P, C.POINTER(_P), _I]),
     "lrfg_field_free": (_ST, [_P]),
+    "lrfg_batch_create": (_ST, [C.POINTER(_P), _I, _I, C.c_size_t]),
+    "lrfg_batch_submit": (_ST, [_P, C.POINTER(lrfg_coeff), C.POINTER(_D), C.POINTER(lrfg_opts),
+                                C.POINTER(C.c_ulonglong)]),
+    "lrfg_batch_poll": (_ST, [_P, C.c_ulonglong, _I, C.POINTER(_I), C.POINTER(_ST), C.POINTER(lrfg_result),
+                              C.POINTER(lrfg_batch_report)]),
+    "lrfg_batch_info": (_ST, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_size_t)]),
+    "lrfg_batch_destroy": (_ST, [_P]),
 }
 
 _lib = None

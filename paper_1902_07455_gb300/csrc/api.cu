@@ -13,6 +13,8 @@
 #include <type_traits>
 #include <cstdarg>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -75,10 +77,11 @@ void* DevicePool::alloc(size_t bytes) {
   }
   live_size_[p] = sz;
   in_use_ += sz;
+  if (in_use_ > peak_) peak_ = in_use_;
   if (poison_) {
     cudaDeviceSynchronize();
     cudaMemset(p, 0xff, sz);
-    cudaDeviceSynchronize();
+    cudaDeviceSynchronize();  // the fill is complete before any stream uses the block
   }
   return p;
 }
@@ -119,12 +122,27 @@ void fold_device_work(lrfg_ctx* ctx) {
   if (!ctx->work_dev) return;
   double h[2 * KC_COUNT];
   LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
-  LRFG_CUDA(cudaMemcpy(h, ctx->work_dev, sizeof(h), cudaMemcpyDeviceToHost));
-  LRFG_CUDA(cudaMemset(ctx->work_dev, 0, sizeof(h)));
+  LRFG_CUDA(cudaMemcpyAsync(h, ctx->work_dev, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  LRFG_CUDA(cudaMemsetAsync(ctx->work_dev, 0, sizeof(h), ctx->stream));
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int k = 0; k < KC_COUNT; ++k) {
     ctx->stats[k].flops += h[2 * k];
     ctx->stats[k].bytes += h[2 * k + 1];
   }
+}
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, func}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 void resolve_profile(lrfg_ctx* ctx) {
@@ -326,6 +344,7 @@ void mode_replace(lrfg_ctx* ctx, const TTView& v, int alpha, double scale, ModeR
 void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
   lrfg_ctx* ctx = P->ctx;
   const int r = P->opts.rank;
+  const double tol = P->opts.rank_tol;
   const int d = P->d;
   const TTView a = view_of(P->a_tt);
   // gradient carriages D_a v_a (rank kept; the other carriages are shared with v)
@@ -346,7 +365,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
                  v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
   for (auto& g : grad) g.reset();
   TTBatch w;
-  tt_round_batch(ctx, batch_view(kr), r, w);                     // T, all components in one sweep
+  tt_round_batch(ctx, batch_view(kr), r, w, tol);                // T, all components in one sweep
   kr = TTBatch();
   // divergence terms: -D_a on carriage a of component a, then the block sum over a
   TTView terms[3];
@@ -358,8 +377,8 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
   TT acc;
   tt_add_many(ctx, terms, nullptr, d, acc);
   TT sdiv;
-  tt_round(ctx, view_of(acc), r, sdiv);                        // T after the sum
-  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out);        // T P~^-1
+  tt_round(ctx, view_of(acc), r, sdiv, tol);                   // T after the sum
+  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol);   // T P~^-1
 }
 
 void lr_rhs(lrfg_problem* P, const double* E, TT& out) {
@@ -385,7 +404,7 @@ void lr_rhs(lrfg_problem* P, const double* E, TT& out) {
     for (int j = 0; j < P->d; ++j) fill(ctx, out.core[j].get(), 0.0, P->N[j]);
     return;
   }
-  tt_precond(ctx, view_of(acc), P->pt, P->pw, P->opts.rank, out);  // T P~^-1 (one truncation)
+  tt_precond(ctx, view_of(acc), P->pt, P->pw, P->opts.rank, out, P->opts.rank_tol);  // T P~^-1 (one truncation)
 }
 
 double lr_aeff(lrfg_problem* P, const double* E, const TTView& u) {
@@ -502,7 +521,7 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     }
   } else if (tucker_like(P->opts.fmt)) {
     TK res;
-    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res);
+    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res, P->opts.rank_tol);
     out->tk = std::move(res);
   } else {
     TT res;
@@ -578,10 +597,13 @@ void solve_full(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field**
   }
 }
 
+// rank cap of a grid coefficient's TT compression: opts.coeff_rank, or the solution rank when 0
+int coeff_rank(const lrfg_opts& o) { return o.coeff_rank > 0 ? o.coeff_rank : o.rank; }
+
 void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
   TK best;
   const TKSolveResult r = tk_solve(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, P->opts.tol,
-                                   P->opts.maxit, P->opts.stop_on_increase, best);
+                                   P->opts.maxit, P->opts.stop_on_increase, best, P->opts.rank_tol);
   res->iters = r.iters;
   res->rel_resid = r.rel_resid;
   res->converged = r.rel_resid <= P->opts.tol ? 1 : 0;
@@ -599,6 +621,7 @@ void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field
 void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
   lrfg_ctx* ctx = P->ctx;
   const int rank = P->opts.rank;
+  const double rtol = P->opts.rank_tol;
   TT b;
   lr_rhs(P, E, b);
   const double nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
@@ -628,11 +651,11 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
       TT scaled;
       tt_copy(ctx, view_of(r), scaled);
       axpby(ctx, (long long)scaled.core_elems(0), omega, r.core[0].get(), 0.0, scaled.core[0].get());
-      tt_round(ctx, view_of(scaled), rank, un);
+      tt_round(ctx, view_of(scaled), rank, un, rtol);
     } else {
       TT s;
       tt_add(ctx, 1.0, nullptr, view_of(u), omega, nullptr, view_of(r), s);
-      tt_round(ctx, view_of(s), rank, un);
+      tt_round(ctx, view_of(s), rank, un, rtol);
     }
     u = std::move(un);
     have_u = true;
@@ -642,7 +665,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
     ++applies;
     tt_add(ctx, 1.0, nullptr, view_of(b), -1.0, nullptr, view_of(cu), diff);
     TT rn;
-    tt_round(ctx, view_of(diff), rank, rn);
+    tt_round(ctx, view_of(diff), rank, rn, rtol);
     r = std::move(rn);
   }
   if (!best_u.d) {
@@ -703,7 +726,8 @@ lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget)
     ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
     ctx->pool = new DevicePool(budget);
     LRFG_CUDA(cudaMalloc(&ctx->work_dev, sizeof(double) * 2 * KC_COUNT));
-    LRFG_CUDA(cudaMemset(ctx->work_dev, 0, sizeof(double) * 2 * KC_COUNT));
+    LRFG_CUDA(cudaMemsetAsync(ctx->work_dev, 0, sizeof(double) * 2 * KC_COUNT, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != LRFG_OK) {
     delete ctx;
@@ -834,25 +858,35 @@ lrfg_status lrfg_tt_add(lrfg_ctx* ctx, double alpha, const lrfg_tt* x, double be
   });
 }
 
-lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out) {
+lrfg_status lrfg_tt_round_tol(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, double tol, lrfg_tt* out) {
   if (!ctx) return LRFG_EINVAL;
   return guard(ctx, [&] {
     check_tt(x);
     LRFG_REQUIRE(out != nullptr, "null output");
     LRFG_REQUIRE(rmax >= 1, "rmax must be >= 1");
+    LRFG_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1) (got %g)", tol);
     TT res;
-    tt_round(ctx, view_of(*x), rmax, res);
+    tt_round(ctx, view_of(*x), rmax, res, tol);
     publish_tt(res, out);
     download_tt(ctx, res, out->cores, 1);
   });
 }
 
+lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out) {
+  return lrfg_tt_round_tol(ctx, x, rmax, 0.0, out);
+}
+
 lrfg_status lrfg_tucker_round(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, lrfg_tucker* out) {
+  return lrfg_tucker_round_tol(ctx, x, rmax, 0.0, out);
+}
+
+lrfg_status lrfg_tucker_round_tol(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, double tol, lrfg_tucker* out) {
   if (!ctx) return LRFG_EINVAL;
   return guard(ctx, [&] {
     check_tucker(x);
     LRFG_REQUIRE(out != nullptr && out->core != nullptr, "null output");
     LRFG_REQUIRE(rmax >= 1, "rmax must be >= 1");
+    LRFG_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1) (got %g)", tol);
     TKView v{};
     v.d = x->d;
     for (int j = 0; j < 3; ++j) {
@@ -862,7 +896,7 @@ lrfg_status lrfg_tucker_round(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, lrf
     }
     v.core = x->core;
     TK res;
-    tk_round(ctx, v, rmax, res);
+    tk_round(ctx, v, rmax, res, tol);
     out->d = res.d;
     size_t nc = 1;
     for (int j = 0; j < 3; ++j) {
@@ -948,6 +982,8 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->maxit >= 0, "maxit must be >= 0");
     LRFG_REQUIRE(opts->tol >= 0.0, "tol must be >= 0");
     if (opts->fmt != LRFG_FULL) LRFG_REQUIRE(opts->rank >= 1, "low-rank solve needs rank >= 1 (got %d)", opts->rank);
+    LRFG_REQUIRE(opts->rank_tol >= 0.0 && opts->rank_tol < 1.0, "rank_tol must be in [0, 1) (got %g)", opts->rank_tol);
+    LRFG_REQUIRE(opts->coeff_rank >= 0, "coeff_rank must be >= 0 (got %d)", opts->coeff_rank);
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
                  "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();
@@ -973,7 +1009,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       } else if (tucker_like(opts->fmt)) {
         tk_compress(ctx, P->d, P->N, a.get(), 64, 1e-7, P->a_tk);
       } else {
-        tt_compress(ctx, P->d, P->N, a.get(), opts->rank, 0.0, P->a_tt);
+        tt_compress(ctx, P->d, P->N, a.get(), coeff_rank(*opts), opts->rank_tol, P->a_tt);
       }
     } else if (coeff->fmt == LRFG_TUCKER) {
       LRFG_REQUIRE(coeff->tk.d == coeff->d, "coefficient Tucker order differs from d");
@@ -986,7 +1022,8 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       } else {
         P->a_full = DBuf<double>(ctx->pool, n);
         tk_expand(ctx, tk_view(a), P->a_full.get());
-        if (opts->fmt == LRFG_TT) tt_compress(ctx, P->d, P->N, P->a_full.get(), opts->rank, 0.0, P->a_tt);
+        if (opts->fmt == LRFG_TT)
+          tt_compress(ctx, P->d, P->N, P->a_full.get(), coeff_rank(*opts), opts->rank_tol, P->a_tt);
       }
     } else {
       LRFG_REQUIRE(coeff->tt.d == coeff->d, "coefficient TT order differs from d");
@@ -1084,7 +1121,7 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
         full_rhs<double>(P, E, f->half.get(), 1);
       }
     } else if (tucker_like(P->opts.fmt)) {
-      tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk);
+      tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk, P->opts.rank_tol);
     } else {
       lr_rhs(P, E, f->tt);
     }

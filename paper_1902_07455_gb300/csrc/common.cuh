@@ -58,11 +58,14 @@ class DevicePool {
   void trim();
   size_t in_use() const { return in_use_; }
   size_t reserved() const { return reserved_; }
+  // high-water mark of in_use() since the last reset_peak()
+  size_t peak() const { return peak_; }
+  void reset_peak() { peak_ = in_use_; }
 
  private:
   std::map<size_t, std::vector<void*>> sized_;  // free blocks by rounded size
   std::map<void*, size_t> live_size_;            // blocks handed out
-  size_t budget_, in_use_ = 0, reserved_ = 0;
+  size_t budget_, in_use_ = 0, reserved_ = 0, peak_ = 0;
   bool poison_ = false;
 };
 
@@ -203,6 +206,10 @@ __device__ __forceinline__ void add_work(double* counter, double flops, double b
   }
 }
 void fold_device_work(lrfg_ctx* ctx);
+// Raises the dynamic shared-memory limit of kernel `func` on the current device to at least `bytes`.
+// The limit only grows: contexts on other host threads may be launching the same kernel with a larger
+// tile, and lowering it under them would make their launches fail.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 }  // namespace lrfg
 
 // launch a kernel with accounting: LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, kernel<<<...>>>(args));

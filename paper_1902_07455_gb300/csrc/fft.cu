@@ -53,7 +53,9 @@ const Twiddles& twiddles_for(lrfg_ctx* ctx, int N) {
   Twiddles t;
   t.N = N;
   LRFG_CUDA(cudaMalloc(&t.W, sizeof(double2) * N));
-  LRFG_CUDA(cudaMemcpy(t.W, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+  // on the context's stream (ordered before its kernels, also when that stream is non-blocking)
+  LRFG_CUDA(cudaMemcpyAsync(t.W, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, ctx->stream));
+  LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   return ctx->twiddles.emplace(N, t).first->second;
 }
 
@@ -73,7 +75,8 @@ const float2* twiddle_table<float>(lrfg_ctx* ctx, int N) {
       h[j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
     }
     LRFG_CUDA(cudaMalloc(&t.Wf, sizeof(float2) * N));
-    LRFG_CUDA(cudaMemcpy(t.Wf, h.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+    LRFG_CUDA(cudaMemcpyAsync(t.Wf, h.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   }
   return t.Wf;
 }
@@ -179,11 +182,11 @@ void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long
   const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;   // radix-2-equivalent count
   const double bytes = 2.0 * sizeof(V) * (double)N * (double)nfib;
   if (sign < 0) {
-    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<-1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<-1, V>, smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
                 fft_fibres_kernel<-1, V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W));
   } else {
-    LRFG_CUDA(cudaFuncSetAttribute(fft_fibres_kernel<1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<1, V>, smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
                 fft_fibres_kernel<1, V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W));
   }
@@ -262,7 +265,7 @@ void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long oute
   long long nfib = outer * inner;
   long long blocks = (nfib + 2LL * TF - 1) / (2LL * TF);
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
-  LRFG_CUDA(cudaFuncSetAttribute(fibre_op_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)fibre_op_kernel, smem));
   // two complex transforms per pair of real fibres
   const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;
   const double bytes = 2.0 * sizeof(double) * (double)N * (double)nfib;
@@ -346,7 +349,7 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   LRFG_CUDA(cudaMemcpyAsync(ds.get(), scale, sizeof(double) * nm, cudaMemcpyHostToDevice, ctx->stream));
   long long nfib = outer * inner;
   long long blocks = (nfib + 2 * tf - 1) / (2 * tf);
-  LRFG_CUDA(cudaFuncSetAttribute(fibre_gauss_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)fibre_gauss_multi_kernel, smem));
   // one forward and nm inverse complex transforms per pair of real fibres
   const double flops = 2.5 * N * std::log2((double)N) * (double)nfib * (1.0 + nm);
   const double bytes = sizeof(double) * (double)N * (double)nfib * (1.0 + nm);

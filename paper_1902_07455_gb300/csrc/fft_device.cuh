@@ -48,6 +48,8 @@ static inline cudaError_t ensure_roots(int device) {
     }
   cudaError_t e = cudaMemcpyToSymbol(c_roots_d, hd, sizeof(hd));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_roots_f, hf, sizeof(hf));
+  // complete before kernels on any stream (non-blocking ones included) read the tables
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess && device >= 0 && device < 64) done |= 1ULL << device;
   return e;
 }

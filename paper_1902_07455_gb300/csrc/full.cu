@@ -178,7 +178,7 @@ void full_forward(lrfg_ctx* ctx, const FullGrid& g, const R* real_in, const R* c
   size_t smem;
   int TF = row_tile<R>(ctx, N, &smem);
   long long blocks = (g.rows + 2LL * TF - 1) / (2LL * TF);
-  LRFG_CUDA(cudaFuncSetAttribute(r2c_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)r2c_rows_kernel<R>, smem));
   LRFG_LAUNCH(ctx, KC_R2C, 2.5 * N * std::log2((double)N) * (double)g.rows,
               (double)g.rows * (N * sizeof(R) * (coef ? 2 : 1) + g.H * sizeof(V)),
               r2c_rows_kernel<R><<<(unsigned)blocks, 256, smem, ctx->stream>>>(real_in, coef, scale, half_out, g.rows, N,
@@ -210,7 +210,7 @@ void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_
   size_t smem;
   int TF = row_tile<R>(ctx, N, &smem);
   long long blocks = (g.rows + 2LL * TF - 1) / (2LL * TF);
-  LRFG_CUDA(cudaFuncSetAttribute(c2r_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)c2r_rows_kernel<R>, smem));
   LRFG_LAUNCH(ctx, KC_C2R, 2.5 * N * std::log2((double)N) * (double)g.rows,
               (double)g.rows * (N * sizeof(R) * (coef ? 2 : 1) + g.H * sizeof(V)),
               c2r_rows_kernel<R><<<(unsigned)blocks, 256, smem, ctx->stream>>>(half_inout, coef, scale, real_out, g.rows,

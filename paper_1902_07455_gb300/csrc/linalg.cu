@@ -13,8 +13,9 @@ namespace lrfg {
 // the kernel is built to waste none of it: a block owns a 64 x 64 output block (clipped to the active
 // sizes, which may be read from the device), each of its 256 threads owns up to 16 outputs of that block
 // exactly (no padded tile rows or columns are computed), operands are staged through shared memory in
-// k-steps of 32, and long K is split across blocks (split-K, atomics into C pre-scaled by beta) until
-// about two blocks per SM are busy.  An output costs two shared-memory reads per FMA, far below the
+// k-steps of 32, and long K is split across blocks until about two blocks per SM are busy (split-K: each
+// split writes its partial block to a workspace and a second kernel sums the splits in a fixed order,
+// so every product, and with it every solve, is bitwise reproducible whatever else runs on the GPU).  An output costs two shared-memory reads per FMA, far below the
 // shared-memory bandwidth at the FP64 rate.
 // ------------------------------------------------------------------------------------------------
 constexpr int GB = 64;  // output block edge
@@ -32,13 +33,15 @@ __device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[GB
 
 // dynM / dynN (optional, per batch item): the product is computed only for rows < dynM[b] * mulM and
 // columns < dynN[b] * mulN (data-dependent active sizes, e.g. numerical ranks); the rest of C is not
-// written (beyond the zeroing of a split-K product).
+// written (a split-K product scales it by beta).  With splits > 1 the partial sums go to
+// part[((split * batches + item) * M + row) * N + column] (M, N the static sizes).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                     int lda, long long sA, const double* __restrict__ B, int ldb,
                                                     long long sB, double beta, double* C, int ldc, long long sC,
                                                     int splits, int kchunk, const int* __restrict__ dynM, int mulM,
-                                                    const int* __restrict__ dynN, int mulN, double* work) {
+                                                    const int* __restrict__ dynN, int mulN, double* work,
+                                                    double* __restrict__ part) {
   __shared__ double As[GK][GB + 1];
   __shared__ double Bs[GK][GB + 1];
   const int batch = blockIdx.z;
@@ -47,6 +50,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   A += (size_t)batch * sA;
   B += (size_t)batch * sB;
   C += (size_t)batch * sC;
+  const int Ms = M, Ns = N;
   if (dynM) M = min(M, dynM[batch] * mulM);
   if (dynN) N = min(N, dynN[batch] * mulN);
   if (work && bm == 0 && bn == 0 && split == 0 && threadIdx.x == 0)
@@ -105,12 +109,41 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
     }
     __syncthreads();
   }
+  if (splits > 1) {
+    double* P = part + ((size_t)split * gridDim.z + batch) * (size_t)Ms * Ns;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j >= nact) break;
+      P[(size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff)] = acc[j];
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     if (j >= nact) break;
     double* c = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
-    if (splits > 1) atomicAdd(c, alpha * acc[j]);
-    else *c = (beta == 0.0) ? alpha * acc[j] : alpha * acc[j] + beta * (*c);
+    *c = (beta == 0.0) ? alpha * acc[j] : alpha * acc[j] + beta * (*c);
+  }
+}
+
+// C = alpha * (sum of the split partials, in split order) + beta * C on the active rows and columns,
+// C = beta * C (0 for beta = 0) elsewhere
+__global__ void splitk_reduce_kernel(const double* __restrict__ part, int splits, int M, int N, double alpha,
+                                     double beta, double* C, int ldc, long long sC, int batch,
+                                     const int* __restrict__ dynM, int mulM, const int* __restrict__ dynN, int mulN) {
+  const long long mn = (long long)M * N, total = mn * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / mn);
+    const long long rem = t - (long long)b * mn;
+    const int i = (int)(rem / N), j = (int)(rem - (long long)(rem / N) * N);
+    double* c = C + (size_t)b * sC + (size_t)i * ldc + j;
+    const bool act = (!dynM || i < dynM[b] * mulM) && (!dynN || j < dynN[b] * mulN);
+    double v = 0.0;
+    if (act) {
+      for (int s = 0; s < splits; ++s) v += part[((size_t)s * batch + b) * (size_t)mn + rem];
+      v *= alpha;
+    }
+    *c = (beta == 0.0) ? v : v + beta * (*c);
   }
 }
 
@@ -155,11 +188,8 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
   kchunk = ((kchunk + GK - 1) / GK) * GK;
   splits = (K + kchunk - 1) / kchunk;
   LRFG_REQUIRE((long long)bmn * splits < 65536, "gemm too many row blocks x splits");
-  if (splits > 1) {
-    LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
-                scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
-                    C, M, N, ldc, sC, batch, beta));
-  }
+  DBuf<double> part;
+  if (splits > 1) part = DBuf<double>(ctx->pool, (size_t)splits * M * N * batch);
   // products with data-dependent sizes count their work on the device
   double* work = (dynM || dynN) ? work_counter(ctx, KC_GEMM) : nullptr;
   const double flops = work ? 0.0 : 2.0 * M * N * (double)K * batch;
@@ -167,16 +197,23 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
   dim3 grid(bnn, bmn * splits, batch);
   if (!transA && !transB)
     LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
   else if (transA && !transB)
     LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
   else if (!transA && transB)
     LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
   else
     LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work));
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
+  if (splits > 1) {
+    const long long n = (long long)M * N * batch;
+    LRFG_LAUNCH(ctx, KC_GEMM, (double)splits * n, sizeof(double) * (double)(splits + 2) * n,
+                splitk_reduce_kernel<<<(unsigned)std::min(4LL * (ctx->num_sms > 0 ? ctx->num_sms : 152), (n + 255) / 256),
+                                       256, 0, ctx->stream>>>(part.get(), splits, M, N, alpha, beta, C, ldc, sC, batch,
+                                                              dynM, mulM, dynN, mulN));
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -348,7 +385,7 @@ static void jacobi_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, 
   DBuf<T> scratch;
   if (use_smem == 1) scratch = DBuf<T>(ctx->pool, (size_t)m * m * batch);
   if (use_smem == 0) scratch = DBuf<T>(ctx->pool, (size_t)2 * m * m * batch);
-  LRFG_CUDA(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)jacobi_kernel<T>, smem));
   const T eps = sizeof(T) == 4 ? (T)1.1920929e-07 : (T)2.220446049250313e-16;
   // one sweep of the two-sided cyclic Jacobi costs about 9 m^3 flops (rows, columns and V)
   LRFG_LAUNCH(ctx, KC_EIGEN, 9.0 * (double)m * m * m * batch, 3.0 * sizeof(double) * (double)m * m * batch,

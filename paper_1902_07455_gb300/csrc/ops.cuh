@@ -94,8 +94,9 @@ struct TTBatchView {
 void ttb_alloc(lrfg_ctx* ctx, TTBatch& x, int d, const int* N, const int* r, int nb);
 TTBatchView batch_view(const TTBatch& x);
 TTView item_view(const TTBatch& x, int b);
-// rank truncation of every item of a batch (one batched Gram-SVD sweep)
-void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out);
+// rank truncation of every item of a batch (one batched Gram-SVD sweep): rank rmax, or with tol > 0 the
+// smallest ranks <= rmax whose truncation error is <= tol ||x|| per item (tol / sqrt(d-1) per bond)
+void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out, double tol = 0.0);
 TTView view_of(const TT& x);
 TTView view_of(const lrfg_tt& x);
 void tt_alloc(lrfg_ctx* ctx, TT& x, int d, const int* N, const int* r);
@@ -108,7 +109,13 @@ void tt_add_many(lrfg_ctx* ctx, const TTView* xs, const double* scales, int nb, 
 // out = alpha x + beta y; alpha_dev / beta_dev (may be null) are device scalars multiplying alpha/beta
 void tt_add(lrfg_ctx* ctx, double alpha, const double* alpha_dev, const TTView& x, double beta,
             const double* beta_dev, const TTView& y, TT& out);
-void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out);
+void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out, double tol = 0.0);
+// Tolerance ranks of `nb` truncations: for item i, S (b x b, active block rk[i], may be null = b) with
+// its top eigenvalues w (stride b, min(kcap, active) of them) and eigenvectors V (b x b, columns):
+// k_dev[i] = the smallest k in [1, kcap] with trace(S) - sum_{t<k} w_t <= tol2 trace(S) (kcap if none);
+// V's columns k_dev[i] .. kcap-1 are zeroed.
+void tol_ranks(lrfg_ctx* ctx, const double* S, const int* rk, const double* w, double* V, int b, int kcap, double tol2,
+               int nb, int* k_dev);
 void tt_dot_device(lrfg_ctx* ctx, const TTView& x, const TTView& y, double* out_dev);
 double tt_dot(lrfg_ctx* ctx, const TTView& x, const TTView& y);
 void tt_expand(lrfg_ctx* ctx, const TTView& x, double* values);
@@ -119,7 +126,7 @@ void tt_mode_operator(lrfg_ctx* ctx, const TTView& x, int j, int kind, double pa
 void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector<double>& w);
 // out = T(P~^-1 x) with the exponential sum (t, w)
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w,
-                int rmax, TT& out);
+                int rmax, TT& out, double tol = 0.0);
 
 // ---- tucker.cu ----------------------------------------------------------------------------------
 // Tucker tensor on the device: core (r_0, .., r_{d-1}) row-major, factor j (N_j, r_j) row-major
@@ -149,20 +156,22 @@ void tk_copy(lrfg_ctx* ctx, const TKView& x, TK& out);
 void tk_mode_operator(lrfg_ctx* ctx, const TKView& x, int j, int kind, double param, double scale, TK& out);
 void tk_hadamard(lrfg_ctx* ctx, const TKView& x, const TKView& y, TK& out);
 void tk_add_many(lrfg_ctx* ctx, const TKView* xs, const double* scales, int nb, TK& out);
-void tk_round(lrfg_ctx* ctx, const TKView& x, int rmax, TK& out);
+// truncation to multilinear ranks <= rmax; with tol > 0 each mode keeps the smallest rank whose dropped
+// singular values of the core unfolding have norm <= tol / sqrt(d) ||x|| (App. A.2.3 HOSVD bound)
+void tk_round(lrfg_ctx* ctx, const TKView& x, int rmax, TK& out, double tol = 0.0);
 void tk_dot_device(lrfg_ctx* ctx, const TKView& x, const TKView& y, double* out_dev);
 double tk_dot(lrfg_ctx* ctx, const TKView& x, const TKView& y);
 void tk_expand(lrfg_ctx* ctx, const TKView& x, double* values);
 void tk_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int rmax, double tol, TK& out);
 void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
-                TK& out);
+                TK& out, double tol = 0.0);
 void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
-              const std::vector<double>& pw, int rank, TK& out);
+              const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0);
 void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
-            const std::vector<double>& pw, int rank, TK& out);
+            const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0);
 double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u);
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u);
+                       TK& best_u, double rtol = 0.0);
 
 }  // namespace lrfg

@@ -564,7 +564,7 @@ static void syevx_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, i
   const size_t smem = use_smem ? full : head;
   const size_t per = (size_t)n * n + (size_t)k * n + (size_t)k * 5 * n;
   DBuf<double> scratch(ctx->pool, per * batch);
-  LRFG_CUDA(cudaFuncSetAttribute(syevx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)syevx_kernel, smem));
   // algorithmic work at the active size, counted by each block on the device
   LRFG_LAUNCH(ctx, KC_EIGEN, 0.0, 0.0,
               syevx_kernel<<<batch, kSyevxThreads, smem, ctx->stream>>>(A, n, k, w, V, n, scratch.get(), use_smem,
@@ -752,7 +752,7 @@ void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int bat
   const size_t smem = use_smem ? full : head;
   DBuf<double> scratch;
   if (!use_smem) scratch = DBuf<double>(ctx->pool, (size_t)2 * b * b * batch);
-  LRFG_CUDA(cudaFuncSetAttribute(gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRFG_CUDA(raise_smem_limit((const void*)gram_factor_kernel, smem));
   // algorithmic work up to the numerical rank, counted by each block on the device
   LRFG_LAUNCH(ctx, KC_CHOL, 0.0, 0.0,
               gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-16, RA, RAc, Pc, rho,

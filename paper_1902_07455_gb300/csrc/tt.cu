@@ -280,19 +280,69 @@ __global__ void scale_rows_cols_kernel(double* Pg, const double* __restrict__ cg
   P[t] = sg > 0.0 ? P[t] * c[row] / sg : 0.0;
 }
 
-void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out) {
+// Tolerance truncation (App. A.3.3): at a bond with singular values sigma_i (eigenvalues w_i = sigma_i^2
+// of S, whose trace is the squared norm of the unfolding) keep the smallest k with
+// sum_{i >= k} w_i <= tol_j^2 trace(S), at least 1 and at most the cap kcap.  Each item gets its own k;
+// the columns of its eigenvector block beyond it are zeroed, so an item's truncation is exactly its own
+// rank-k one while the batch shares the storage rank max_b k_b.  One block per item.
+__global__ void tol_rank_kernel(const double* __restrict__ Sg, const int* __restrict__ rk, const double* __restrict__ wg,
+                                double* Vg, int b, int kcap, double tol2, int* kout) {
+  const size_t item = blockIdx.x;
+  const double* S = Sg + item * (size_t)b * b;
+  const double* w = wg + item * (size_t)b;
+  double* V = Vg + item * (size_t)b * b;
+  __shared__ int ks;
+  if (threadIdx.x == 0) {
+    const int act = rk ? min(rk[item], b) : b;
+    double tr = 0.0;
+    for (int i = 0; i < act; ++i) tr += S[(size_t)i * b + i];
+    int k = kcap;
+    double kept = 0.0;
+    for (int i = 0; i < min(kcap, act); ++i) {  // w holds min(kcap, act) eigenvalues
+      kept += fmax(w[i], 0.0);
+      if (tr - kept <= tol2 * tr) { k = i + 1; break; }
+    }
+    ks = max(k, 1);
+    kout[item] = ks;
+  }
+  __syncthreads();
+  const int k = ks;
+  for (int t = threadIdx.x; t < b * (kcap - k); t += blockDim.x) {
+    const int row = t / (kcap - k), col = k + t - (t / (kcap - k)) * (kcap - k);
+    V[(size_t)row * b + col] = 0.0;
+  }
+}
+
+void tol_ranks(lrfg_ctx* ctx, const double* S, const int* rk, const double* w, double* V, int b, int kcap, double tol2,
+               int nb, int* k_dev) {
+  LRFG_LAUNCH(ctx, KC_TT_MISC, (double)b * nb, sizeof(double) * ((double)b * kcap + 2.0 * b) * nb,
+              tol_rank_kernel<<<nb, 128, 0, ctx->stream>>>(S, rk, w, V, b, kcap, tol2, k_dev));
+}
+
+void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out, double tol) {
   LRFG_REQUIRE(rmax >= 1, "truncation rank must be >= 1 (got %d)", rmax);
+  LRFG_REQUIRE(tol >= 0.0 && tol < 1.0, "truncation tolerance must be in [0, 1) (got %g)", tol);
   const int d = x.d, nb = x.nb;
   LRFG_REQUIRE(d >= 1 && d <= 3 && nb >= 1, "TT order must be 1..3");
-  // ranks after the (implicit) right-to-left orthogonalisation and after truncation, as in TT rounding
+  // ranks after the (implicit) right-to-left orthogonalisation and after truncation, as in TT rounding;
+  // with a tolerance, rr[j+1] is the cap and the rank is decided at the bond
   int sp[4], rr[4];
   sp[d] = 1;
   for (int j = d - 1; j >= 1; --j) sp[j] = std::min(x.r[j], x.N[j] * sp[j + 1]);
   rr[0] = 1;
   for (int j = 0; j < d - 1; ++j) rr[j + 1] = std::min(rmax, std::min(rr[j] * x.N[j], sp[j + 1]));
   rr[d] = 1;
-  ttb_alloc(ctx, out, d, x.N, rr, nb);
+  const double tol_j = d > 1 ? tol / std::sqrt((double)(d - 1)) : 0.0;
+  if (tol > 0.0) {
+    out.d = d;
+    out.nb = nb;
+    for (int j = 0; j < 3; ++j) out.N[j] = j < d ? x.N[j] : 0;
+    for (int j = 0; j < 4; ++j) out.r[j] = 1;
+  } else {
+    ttb_alloc(ctx, out, d, x.N, rr, nb);
+  }
   if (d == 1) {
+    if (tol > 0.0) out.core[0] = DBuf<double>(ctx->pool, out.elems(0) * nb);
     LRFG_CUDA(cudaMemcpyAsync(out.core[0].get(), x.core[0], sizeof(double) * x.elems(0) * nb,
                               cudaMemcpyDeviceToDevice, ctx->stream));
     return;
@@ -322,10 +372,12 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
   LRFG_CUDA(cudaMemcpyAsync(Z.get(), x.core[0], sizeof(double) * x.elems(0) * nb, cudaMemcpyDeviceToDevice,
                             ctx->stream));
   for (int j = 0; j < d - 1; ++j) {
-    const int a = rr[j], n = x.N[j], b = x.r[j + 1], k = rr[j + 1];
+    if (tol > 0.0) rr[j + 1] = std::min(rmax, std::min(rr[j] * x.N[j], sp[j + 1]));  // cap after bond j-1
+    const int a = rr[j], n = x.N[j], b = x.r[j + 1], kcap = rr[j + 1];
     const int rows = a * n;
-    const long long sz = (long long)rows * b, sbb = (long long)b * b, sout = (long long)out.elems(j);
-    const long long sbk = (long long)b * k, skk = (long long)k * k;
+    const long long sz = (long long)rows * b, sbb = (long long)b * b;
+    long long sbk = (long long)b * kcap, skk = (long long)kcap * kcap, sout = 0;
+    int k = kcap;
     DBuf<double> GA(ctx->pool, (size_t)sbb * nb), cb(ctx->pool, (size_t)b * nb);
     gemm(ctx, 1, 0, b, b, rows, 1.0, Z.get(), b, sz, Z.get(), b, sz, 0.0, GA.get(), b, sbb, nb);
     const bool projected = (d == 3 && j == 0);
@@ -352,6 +404,25 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
     DBuf<double> F(ctx->pool, (size_t)sbb * nb), F1(ctx->pool, (size_t)sbb * nb), S(ctx->pool, (size_t)sbb * nb);
     DBuf<double> sig(ctx->pool, (size_t)b * nb), US(ctx->pool, (size_t)sbb * nb);
     DBuf<double> P(ctx->pool, (size_t)sbk * nb), T(ctx->pool, (size_t)sbk * nb);
+    // the bond's rank: the cap, or with a tolerance the largest of the items' own ranks (their
+    // eigenvector columns beyond their own rank zeroed); then the output carriage j
+    auto settle_rank = [&]() {
+      if (tol > 0.0) {
+        DBuf<int> kd(ctx->pool, (size_t)nb);
+        tol_ranks(ctx, S.get(), rk.get(), sig.get(), US.get(), b, kcap, tol_j * tol_j, nb, kd.get());
+        std::vector<int> kh(nb);
+        LRFG_CUDA(cudaMemcpyAsync(kh.data(), kd.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+        LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+        k = 1;
+        for (int v : kh) k = std::max(k, std::min(v, kcap));
+        rr[j + 1] = k;
+        out.r[j + 1] = k;
+        out.core[j] = DBuf<double>(ctx->pool, out.elems(j) * nb);
+        sbk = (long long)b * k;
+        skk = (long long)k * k;
+      }
+      sout = (long long)out.elems(j);
+    };
     if (left_side) {
       // GA ~ RA^T RA, Q = M Pc orthonormal; S = RA R RA^T (nonzero block rho_A x rho_A); Y = Q U_k,
       // transfer T = U_k^T RAc
@@ -373,7 +444,8 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
         gemm(ctx, 0, 0, b, b, b, 1.0, F.get(), b, sbb, R[j + 1].get(), b, sbb, 0.0, F1.get(), b, sbb, nb);
         gemm(ctx, 0, 1, b, b, b, 1.0, F1.get(), b, sbb, F.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
       }
-      syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, k, nb);
+      syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, kcap, nb);
+      settle_rank();
       gemm(ctx, 0, 0, b, k, b, 1.0, Pc.get(), b, sbb, US.get(), b, sbb, 0.0, P.get(), k, sbk, nb);
       gemm(ctx, 0, 0, rows, k, b, 1.0, Z.get(), b, sz, P.get(), k, sbk, 0.0, out.core[j].get(), k, sout, nb);
       gemm(ctx, 1, 0, k, b, b, 1.0, US.get(), b, sbb, RAc.get(), b, sbb, 0.0, T.get(), b, sbk, nb);
@@ -385,7 +457,8 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
       gram_factor(ctx, R[j + 1].get(), nullptr, b, nb, F.get(), nullptr, nullptr, rk.get());
       gemm(ctx, 0, 0, b, b, b, 1.0, F.get(), b, sbb, GA.get(), b, sbb, 0.0, F1.get(), b, sbb, nb);
       gemm(ctx, 0, 1, b, b, b, 1.0, F1.get(), b, sbb, F.get(), b, sbb, 0.0, S.get(), b, sbb, nb);
-      syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, k, nb);
+      syevx_sized(ctx, S.get(), rk.get(), sig.get(), US.get(), b, kcap, nb);
+      settle_rank();
       DBuf<double> P0(ctx->pool, (size_t)sbk * nb);
       gemm(ctx, 1, 0, b, k, b, 1.0, F.get(), b, sbb, US.get(), b, sbb, 0.0, P0.get(), k, sbk, nb);
       LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * sbk * nb, 2.0 * sizeof(double) * sbk * nb,
@@ -411,6 +484,7 @@ void tt_round_batch(lrfg_ctx* ctx, const TTBatchView& x, int rmax, TTBatch& out)
          Zn.get(), n1 * c1, szn, nb);
     Z = std::move(Zn);
   }
+  if (tol > 0.0) out.core[d - 1] = DBuf<double>(ctx->pool, out.elems(d - 1) * nb);
   LRFG_CUDA(cudaMemcpyAsync(out.core[d - 1].get(), Z.get(), sizeof(double) * out.elems(d - 1) * nb,
                             cudaMemcpyDeviceToDevice, ctx->stream));
 }
@@ -444,7 +518,7 @@ TTView item_view(const TTBatch& x, int b) {
   return v;
 }
 
-void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
+void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out, double tol) {
   if (x.d == 1) { tt_copy(ctx, x, out); return; }
   TTBatchView bv{};
   bv.d = x.d;
@@ -453,7 +527,7 @@ void tt_round(lrfg_ctx* ctx, const TTView& x, int rmax, TT& out) {
   for (int j = 0; j < 4; ++j) bv.r[j] = x.r[j];
   for (int j = 0; j < x.d; ++j) bv.core[j] = x.core[j];
   TTBatch ob;
-  tt_round_batch(ctx, bv, rmax, ob);
+  tt_round_batch(ctx, bv, rmax, ob, tol);
   out.d = ob.d;
   for (int j = 0; j < 3; ++j) out.N[j] = ob.N[j];
   for (int j = 0; j < 4; ++j) out.r[j] = ob.r[j];
@@ -635,7 +709,7 @@ void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector
 }
 
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
-                TT& out) {
+                TT& out, double tol) {
   // P~^-1 x = sum_m w_m (G_m x ... x G_m) x with G_m = F^-1 diag(exp(-t_m k^2)) F per mode: a TT whose
   // carriages are block rows (first), block diagonal (middle) and block columns (last) over m.
   const int d = x.d;
@@ -669,7 +743,7 @@ void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, co
       }
     }
   }
-  tt_round(ctx, view_of(big), rmax, out);
+  tt_round(ctx, view_of(big), rmax, out, tol);
 }
 
 }  // namespace lrfg

@@ -230,7 +230,7 @@ void tk_add_many(lrfg_ctx* ctx, const TKView* xs, const double* scales, int nb, 
   }
 }
 
-void tk_round(lrfg_ctx* ctx, const TKView& x, int rmax, TK& out) {
+void tk_round(lrfg_ctx* ctx, const TKView& x, int rmax, TK& out, double tol) {
   LRFG_REQUIRE(rmax >= 1, "truncation rank must be >= 1 (got %d)", rmax);
   const int d = x.d;
   int r[3], k[3];
@@ -256,15 +256,28 @@ void tk_round(lrfg_ctx* ctx, const TKView& x, int rmax, TK& out) {
     mode_mult(ctx, c1.get(), d, r, j, RAc[j].get(), r[j], r[j], 0, c2.get());
     std::swap(c1, c2);
   }
-  // 3. HOSVD of core': top k_j eigenvectors of each mode Gram (active size rho_j), new factors Q_j V_j
-  tk_alloc(ctx, out, d, x.N, k);
+  // 3. HOSVD of core': top k_j eigenvectors of each mode Gram (active size rho_j), new factors Q_j V_j;
+  // with a tolerance, k_j is decided from the eigenvalues of every mode (one synchronisation)
   DBuf<double> V[3];
+  DBuf<int> kd(ctx->pool, 3);
   for (int j = 0; j < d; ++j) {
     const int m = r[j];
-    DBuf<double> S(ctx->pool, (size_t)m * m), w(ctx->pool, m), P(ctx->pool, (size_t)m * k[j]);
+    DBuf<double> S(ctx->pool, (size_t)m * m), w(ctx->pool, m);
     V[j] = DBuf<double>(ctx->pool, (size_t)m * m);
     mode_gram(ctx, c1.get(), d, r, j, S.get());
     syevx_sized(ctx, S.get(), rho.get() + j, w.get(), V[j].get(), m, k[j], 1);
+    if (tol > 0.0) tol_ranks(ctx, S.get(), rho.get() + j, w.get(), V[j].get(), m, k[j], tol * tol / d, 1, kd.get() + j);
+  }
+  if (tol > 0.0) {
+    int kh[3] = {1, 1, 1};
+    LRFG_CUDA(cudaMemcpyAsync(kh, kd.get(), sizeof(int) * d, cudaMemcpyDeviceToHost, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < d; ++j) k[j] = std::max(1, std::min(kh[j], k[j]));
+  }
+  tk_alloc(ctx, out, d, x.N, k);
+  for (int j = 0; j < d; ++j) {
+    const int m = r[j];
+    DBuf<double> P(ctx->pool, (size_t)m * k[j]);
     gemm(ctx, 0, 0, m, k[j], m, 1.0, Pc[j].get(), m, 0, V[j].get(), m, 0, 0.0, P.get(), k[j], 0);
     gemm(ctx, 0, 0, x.N[j], k[j], m, 1.0, x.fac[j], m, 0, P.get(), k[j], 0, 0.0, out.fac[j].get(), k[j], 0);
   }
@@ -367,7 +380,7 @@ void tk_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int r
 // P~^-1 x = sum_m w_m (G_m x .. x G_m) x: factors [G_1 B_j, .., G_R B_j], core block-diagonal with the
 // blocks w_m c; then T
 void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
-                TK& out) {
+                TK& out, double tol) {
   const int d = x.d, R = (int)t.size();
   int r[3];
   for (int j = 0; j < d; ++j) r[j] = R * x.r[j];
@@ -392,7 +405,7 @@ void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, co
                 embed_core_kernel<<<grid_of(ctx, nbk), 256, 0, ctx->stream>>>(
                     x.core, dims3(d, x.r), big.core.get(), dims3(d, r), dims3(d, off), w[m], d));
   }
-  tk_round(ctx, tk_view(big), rmax, out);
+  tk_round(ctx, tk_view(big), rmax, out, tol);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -400,26 +413,26 @@ void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, co
 // (Eq. (Pls_lowrank), Sec. 3.3) -- the same steps as the TT path
 // ------------------------------------------------------------------------------------------------
 void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
-              const std::vector<double>& pw, int rank, TK& out) {
+              const std::vector<double>& pw, int rank, TK& out, double rtol) {
   const int d = v.d;
   TK w[3];
   for (int alpha = 0; alpha < d; ++alpha) {
     TK e, ae, wr;
     tk_mode_operator(ctx, v, alpha, LRFG_MUL_DERIV, 0.0, 1.0, e);                  // gradient, mode alpha
     tk_hadamard(ctx, a, tk_view(e), ae);                                          // A~ e_alpha
-    tk_round(ctx, tk_view(ae), rank, wr);                                         // T
+    tk_round(ctx, tk_view(ae), rank, wr, rtol);                                   // T
     tk_mode_operator(ctx, tk_view(wr), alpha, LRFG_MUL_DERIV, 0.0, -1.0, w[alpha]);  // divergence
   }
   TKView terms[3];
   for (int alpha = 0; alpha < d; ++alpha) terms[alpha] = tk_view(w[alpha]);
   TK acc, s;
   tk_add_many(ctx, terms, nullptr, d, acc);
-  tk_round(ctx, tk_view(acc), rank, s);  // T after the sum
-  tk_precond(ctx, tk_view(s), pt, pw, rank, out);
+  tk_round(ctx, tk_view(acc), rank, s, rtol);  // T after the sum
+  tk_precond(ctx, tk_view(s), pt, pw, rank, out, rtol);
 }
 
 void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
-            const std::vector<double>& pw, int rank, TK& out) {
+            const std::vector<double>& pw, int rank, TK& out, double rtol) {
   const int d = a.d;
   TK t[3];
   TKView terms[3];
@@ -439,7 +452,7 @@ void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<d
   }
   TK acc;
   tk_add_many(ctx, terms, nullptr, n, acc);
-  tk_precond(ctx, tk_view(acc), pt, pw, rank, out);  // T P~^-1
+  tk_precond(ctx, tk_view(acc), pt, pw, rank, out, rtol);  // T P~^-1
 }
 
 static void tk_ones(lrfg_ctx* ctx, int d, const int* N, TK& x) {
@@ -472,10 +485,10 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u)
 // when ||r|| fails to decrease (stop_on_increase), at tol or maxit; the iterate of smallest residual is kept
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u) {
+                       TK& best_u, double rtol) {
   TKSolveResult res{};
   TK b;
-  tk_rhs(ctx, a, E, pt, pw, rank, b);
+  tk_rhs(ctx, a, E, pt, pw, rank, b, rtol);
   const double nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
   TK u, r;
   bool have_u = false, have_best = false;
@@ -496,7 +509,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     }
     if (nr <= tol || it >= maxit) break;
     TK q;
-    tk_apply(ctx, a, tk_view(r), pt, pw, rank, q);
+    tk_apply(ctx, a, tk_view(r), pt, pw, rank, q, rtol);
     ++applies;
     const double qq = tk_dot(ctx, tk_view(q), tk_view(q));
     if (qq == 0.0) break;
@@ -506,24 +519,24 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
       TK scaled;
       tk_copy(ctx, tk_view(r), scaled);
       axpby(ctx, (long long)core_size(r.d, r.r), omega, r.core.get(), 0.0, scaled.core.get());
-      tk_round(ctx, tk_view(scaled), rank, un);
+      tk_round(ctx, tk_view(scaled), rank, un, rtol);
     } else {
       TKView xs[2] = {tk_view(u), tk_view(r)};
       const double sc[2] = {1.0, omega};
       TK s;
       tk_add_many(ctx, xs, sc, 2, s);
-      tk_round(ctx, tk_view(s), rank, un);
+      tk_round(ctx, tk_view(s), rank, un, rtol);
     }
     u = std::move(un);
     have_u = true;
     ++it;
     TK cu, diff, rn;
-    tk_apply(ctx, a, tk_view(u), pt, pw, rank, cu);
+    tk_apply(ctx, a, tk_view(u), pt, pw, rank, cu, rtol);
     ++applies;
     TKView xs[2] = {tk_view(b), tk_view(cu)};
     const double sc[2] = {1.0, -1.0};
     tk_add_many(ctx, xs, sc, 2, diff);
-    tk_round(ctx, tk_view(diff), rank, rn);
+    tk_round(ctx, tk_view(diff), rank, rn, rtol);
     r = std::move(rn);
   }
   if (!have_best) {

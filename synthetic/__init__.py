@@ -6,6 +6,6 @@ homogenisation method's arithmetic, imports neither ``oracle`` nor the product p
 only code both sides use.
 """
 from .microstructures import (  # noqa: F401
-    BASE_SEED, grid_points, square_inclusion, smoothed_cube, laminate, lognormal_grf, random_tt,
+    BASE_SEED, grid_points, square_inclusion, smoothed_cube, smoothed_sphere, laminate, lognormal_grf, random_tt,
     random_field,
 )

@@ -10,6 +10,7 @@ Workloads (recipes, with the paper's materials as the pattern, Sec. 4.1):
   inclusion material).
 * ``smoothed_cube``: a = 1 + (contrast - 1) prod_a h(x_a), h(t) = (tanh((t+c)/w) - tanh((t-c)/w))/2.
 * ``laminate``: a(x) = f(x_1), rank 1.
+* ``smoothed_sphere``: a = 1 + (contrast - 1) (1 - tanh((|x| - R)/w))/2 (not separable).
 * ``lognormal_grf``: a = exp(g), g a periodic Gaussian random field with squared-exponential covariance
   sigma^2 exp(-|x-y|^2 / (2 l^2)), realised through its spectral density
   lambda_k ~ prod_a exp(-2 pi^2 l^2 k_a^2) normalised to sum_k lambda_k = sigma^2 (modes with
@@ -77,6 +78,20 @@ def laminate(d: int, N: int, contrast: float = 10.0, c: float = 0.25, full: bool
     terms = [[f] + [one] * (d - 1)]
     a = _outer([f] + [one] * (d - 1)) if full else None
     return a, terms, [1.0]
+
+
+def smoothed_sphere(d: int, N: int, contrast: float = 10.0, radius: float = 0.3, width=None):
+    """a = 1 + (contrast-1) s(|x|), s a tanh-smoothed indicator of the ball |x| < radius (width 2/N by
+    default, distances periodic on the cell).  Returns the full grid array (not separable)."""
+    w = 2.0 / N if width is None else float(width)
+    x = grid_points(N)
+    r2 = np.zeros((N,) * d)
+    for a in range(d):
+        shape = [1] * d
+        shape[a] = N
+        r2 = r2 + (x ** 2).reshape(shape)
+    s = 0.5 * (1.0 - np.tanh((np.sqrt(r2) - radius) / w))
+    return 1.0 + (contrast - 1.0) * s
 
 
 def lognormal_grf(d: int, N: int, ell: float = 0.2, var: float = 1.0, seed: int = BASE_SEED,

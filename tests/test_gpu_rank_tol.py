@@ -1,0 +1,86 @@
+"""Tolerance truncation on the GPU (rank_tol) against the oracle's tolerance rounding and solver on the
+same seeded inputs.
+
+The test tensors are sums of rank-one terms with weights 10^-i, so their singular values fall off by
+about a decade each and no singular value lies near a truncation threshold: the kept ranks are unique
+and must equal the oracle's exactly; the truncated tensors then agree to the Gram-SVD accuracy (1e-8
+relative, as for fixed-rank truncation).  A solve with rank_tol meets the FP64-path tolerance against
+the oracle's minimal-residual iteration with the same truncation rule (1e-6 on A_eff)."""
+import numpy as np
+import pytest
+
+import paper_1902_07455_gb300 as lrfg
+from oracle import lowrank as lr
+from synthetic import smoothed_cube
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def decaying_terms(shape, n_terms, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    terms = [[v / np.linalg.norm(v) for v in (rng.standard_normal(n) for n in shape)] for _ in range(n_terms)]
+    return terms, 10.0 ** -np.arange(n_terms)
+
+
+@pytest.mark.parametrize("shape,tol,cap", [((9, 11, 13), 1e-3, 7), ((9, 11, 13), 1e-5, 7),
+                                           ((15, 13, 11), 3e-2, 5), ((21, 17), 1e-4, 6), ((9, 11, 13), 1e-5, 4)])
+def test_tt_round_tol(ctx, shape, tol, cap):
+    terms, w = decaying_terms(shape, 7, seed=31)
+    x = lr.tt_from_separable(terms, w)
+    ref = lr.tt_round(x, rmax=cap, tol=tol)
+    out = ctx.tt_round(lrfg.TTensor.from_numpy(x), cap, tol=tol)
+    assert out.ranks == lr.tt_ranks(ref), (out.ranks, lr.tt_ranks(ref))
+    assert rel(lr.tt_full(out.numpy()), lr.tt_full(ref)) <= 1e-8
+
+
+@pytest.mark.parametrize("shape,tol,cap", [((9, 11, 13), 1e-3, 7), ((15, 13, 11), 1e-5, 7), ((21, 17), 1e-4, 3)])
+def test_tucker_round_tol(ctx, shape, tol, cap):
+    terms, w = decaying_terms(shape, 7, seed=32)
+    x = lr.tucker_from_separable(terms, w)
+    ref_c, ref_f = lr.tucker_round(x, rmax=cap, tol=tol)
+    out = ctx.tucker_round(lrfg.TuckerTensor.from_numpy(*x), cap, tol=tol)
+    assert out.ranks == [f.shape[1] for f in ref_f]
+    c, f = out.numpy()
+    assert rel(lr.tucker_full(c, f), lr.tucker_full(ref_c, ref_f)) <= 1e-8
+
+
+def test_tt_round_tol_zero_is_fixed_rank(ctx):
+    terms, w = decaying_terms((9, 11, 13), 7, seed=33)
+    x = lrfg.TTensor.from_numpy(lr.tt_from_separable(terms, w))
+    a = ctx.tt_round(x, 4)
+    b = ctx.tt_round(x, 4, tol=0.0)
+    assert a.ranks == b.ranks == [1, 4, 4, 1]
+    assert rel(lr.tt_full(a.numpy()), lr.tt_full(b.numpy())) == 0.0
+
+
+@pytest.mark.parametrize("fmt,d,N,cap,rank_tol", [("tt", 2, 45, 20, 1e-4), ("tt", 2, 45, 20, 1e-6),
+                                                  ("tt", 3, 27, 12, 1e-4), ("tucker", 2, 45, 16, 1e-5)])
+def test_solve_rank_tol_matches_oracle(ctx, fmt, d, N, cap, rank_tol):
+    _, terms, w = smoothed_cube(d, N, contrast=10.0, full=False)
+    E = np.eye(d)[0]
+    a_lr = lr.FORMATS[fmt].sep(terms, w)
+    op = lr.LowRankGaNi(a_lr, (N,) * d, fmt=fmt, rank=cap, pinv_eps=0.1, rank_tol=rank_tol)
+    ref = lr.minres(op, E, tol=1e-10, maxit=40)
+    coeff = lrfg.TTensor.from_numpy(a_lr) if fmt == "tt" else lrfg.TuckerTensor.from_numpy(*a_lr)
+    P = ctx.problem(coeff, lrfg.TT if fmt == "tt" else lrfg.TUCKER, rank=cap, tol=1e-10, maxit=40,
+                    rank_tol=rank_tol)
+    res, u = P.solve(E)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    assert abs(res.iters - ref["iters"]) <= 2
+    ranks = u.info()[3]
+    assert max(ranks) <= cap
+    u.free()
+    P.free()
+
+
+def test_rank_tol_invalid(ctx):
+    _, terms, w = smoothed_cube(2, 15, contrast=10.0, full=False)
+    coeff = lrfg.TTensor.from_numpy(lr.tt_from_separable(terms, w))
+    with pytest.raises(lrfg.LrfgError):
+        ctx.problem(coeff, lrfg.TT, rank=5, rank_tol=1.5)
+    with pytest.raises(lrfg.LrfgError):
+        ctx.tt_round(coeff, 3, tol=-1.0)

@@ -181,3 +181,27 @@ def test_energy_identity_exact_for_any_field():
     e = np.real(fg.idft(fg.grad_hat(uh - full["uh"]), d))
     rhs = float(np.mean(A * np.sum(e * e, axis=0)))
     assert np.isclose(lhs, rhs, rtol=1e-10)
+
+
+@pytest.mark.parametrize("fmt", ["tt", "tucker"])
+def test_tolerance_truncation_bound_and_first_rank(fmt):
+    """Tolerance truncation (App. A.3.3 / A.2.3): the result lies within tol ||x||, and the first TT bond
+    (the mode-0 Tucker rank) is the smallest rank the full tensor's own mode-0 SVD allows with the
+    per-bond share tol / sqrt(d-1) (tol / sqrt(d))."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    shape = (9, 10, 11)
+    terms = [[v / np.linalg.norm(v) for v in (rng.standard_normal(n) for n in shape)] for _ in range(7)]
+    weights = 10.0 ** -np.arange(7)
+    f = lr.FORMATS[fmt]
+    x = f.sep(terms, weights)
+    X = f.full(x)
+    s = np.linalg.svd(X.reshape(shape[0], -1), compute_uv=False)
+    for tol in [3e-2, 1e-3, 1e-5]:
+        y = f.round(x, rmax=None, tol=tol)
+        assert np.linalg.norm(f.full(y) - X) <= tol * np.linalg.norm(X) * (1 + 1e-10)
+        loc = tol / np.sqrt(2.0 if fmt == "tt" else 3.0)
+        tails = np.sqrt(np.cumsum(s[::-1] ** 2))[::-1]
+        k_expected = next(k for k in range(1, len(s) + 1)
+                          if (tails[k] if k < len(s) else 0.0) <= loc * np.linalg.norm(s))
+        rank = y[0].shape[2] if fmt == "tt" else y[1][0].shape[1]
+        assert rank == k_expected, (tol, rank, k_expected)
