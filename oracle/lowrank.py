@@ -565,6 +565,64 @@ def minres(op: LowRankGaNi, E, tol=1e-10, maxit=200, stop_on_increase=True, call
     return dict(u=u, iters=itb, rel_resid=nr, history=hist, Aeff=op.homogenised_coefficient(u, E))
 
 
+def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, maxit=200):
+    """Rank-adapting minimal-residual iteration (the solver Sec. 4.3 proposes: start with a low solution
+    rank and raise it during the iterations).  Reading: the iteration of ``minres`` runs with every T at
+    the current rank r_c = rank_start; when the residual norm fails to decrease and r_c < op.rank (the
+    cap), r_c rises by rank_step (at most to the cap), the right-hand side is rebuilt at the new rank, and
+    the iteration restarts from the best iterate so far with its residual recomputed at the new rank
+    (the comparison for "fails to decrease" starts again from there).  At the cap a failure to decrease
+    ends the iteration, as in ``minres``; so do the relative tolerance and ``maxit`` (iterations summed
+    over all ranks).  Returns dict(u, iters, rel_resid, rank, history, Aeff) for the best iterate of the
+    last rank."""
+    f = op.f
+    E = np.asarray(E, dtype=np.float64)
+    rmax = op.rank
+    rc = min(int(rank_start), rmax)
+    op.rank = rc
+    try:
+        b = op.rhs(E)
+        nb = f.norm(b)
+        u, u_zero = f.zeros(op.shape), True
+        r = b
+        best = (np.inf, u, 0, True)
+        hist = []
+        it = 0
+        while True:
+            nr = f.norm(r) / nb if nb > 0 else 0.0
+            hist.append(nr)
+            if nr < best[0]:
+                best = (nr, u, it, u_zero)
+            elif rc < rmax:
+                # stagnation below the cap: raise the rank and restart from the best iterate
+                rc = min(rc + int(rank_step), rmax)
+                op.rank = rc
+                b = op.rhs(E)
+                nb = f.norm(b)
+                u, u_zero = best[1], best[3]
+                r = b if u_zero else op.T(f.add(b, f.scale(op.apply(u), -1.0)))
+                nr = f.norm(r) / nb if nb > 0 else 0.0
+                hist.append(nr)
+                best = (nr, u, best[2], u_zero)
+            else:
+                break
+            if nr <= tol or it >= maxit:
+                break
+            q = op.apply(r)
+            qq = np.real(f.dot(q, q))
+            if qq == 0.0:
+                break
+            omega = np.real(f.dot(q, r)) / qq
+            u = op.T(f.scale(r, omega)) if u_zero else op.T(f.add(u, f.scale(r, omega)))
+            u_zero = False
+            it += 1
+            r = op.T(f.add(b, f.scale(op.apply(u), -1.0)))
+        nr, u, itb, _ = best
+        return dict(u=u, iters=itb, rel_resid=nr, rank=rc, history=hist, Aeff=op.homogenised_coefficient(u, E))
+    finally:
+        op.rank = rmax
+
+
 def relative_error(A_full: float, A_lowrank: float) -> float:
     """|A_N - A_{N,r}| / A_N  (Eq. (rel_error), reported as an absolute value)."""
     return abs(A_full - A_lowrank) / abs(A_full)

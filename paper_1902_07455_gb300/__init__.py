@@ -350,11 +350,13 @@ class Context:
     # ---- problems and fields ---------------------------------------------------------------------
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
-                coeff_rank: int = 0) -> "Problem":
+                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1) -> "Problem":
         """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only).
         ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
-        rank cap of a grid coefficient's TT compression (0: ``rank``)."""
-        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank)
+        rank cap of a grid coefficient's TT compression (0: ``rank``).  ``rank_start`` > 0: rank-adapting
+        MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT)."""
+        return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank,
+                       rank_start, rank_step)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -445,7 +447,7 @@ class Problem:
     (isotropic a(x) samples) or a TTensor of the coefficient."""
 
     def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64,
-                 rank_tol=0.0, coeff_rank=0):
+                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -488,6 +490,7 @@ class Problem:
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
+        o.rank_start, o.rank_step = int(rank_start), int(rank_step)
         h = C.c_void_p()
         ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))
         del keep
@@ -607,12 +610,13 @@ class Batch:
 
     def submit(self, coeff, E, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8,
                maxit: int = 200, stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
-               coeff_rank: int = 0) -> int:
+               coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1) -> int:
         c, keep = _host_coeff(coeff)
         o = L.lrfg_opts()
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
+        o.rank_start, o.rank_step = int(rank_start), int(rank_step)
         t = C.c_ulonglong()
         st = self.lib.lrfg_batch_submit(self.h, C.byref(c), _dvec(E), C.byref(o), C.byref(t))
         del keep

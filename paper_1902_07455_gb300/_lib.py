@@ -33,7 +33,7 @@ class lrfg_coeff(C.Structure):
 class lrfg_opts(C.Structure):
     _fields_ = [("fmt", C.c_int), ("prec", C.c_int), ("rank", C.c_int), ("pinv_eps", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("stop_on_increase", C.c_int), ("rank_tol", C.c_double),
-                ("coeff_rank", C.c_int)]
+                ("coeff_rank", C.c_int), ("rank_start", C.c_int), ("rank_step", C.c_int)]
 
 
 class lrfg_result(C.Structure):

@@ -341,9 +341,9 @@ void mode_replace(lrfg_ctx* ctx, const TTView& v, int alpha, double scale, ModeR
   out.view.core[alpha] = out.core.get();
 }
 
-void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
+// rank r of every truncation (the problem's rank, or the current rank of a rank-adapting solve)
+void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
   lrfg_ctx* ctx = P->ctx;
-  const int r = P->opts.rank;
   const double tol = P->opts.rank_tol;
   const int d = P->d;
   const TTView a = view_of(P->a_tt);
@@ -381,7 +381,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out) {
   tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol);   // T P~^-1
 }
 
-void lr_rhs(lrfg_problem* P, const double* E, TT& out) {
+void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
   lrfg_ctx* ctx = P->ctx;
   TT acc;
   bool have = false;
@@ -404,7 +404,7 @@ void lr_rhs(lrfg_problem* P, const double* E, TT& out) {
     for (int j = 0; j < P->d; ++j) fill(ctx, out.core[j].get(), 0.0, P->N[j]);
     return;
   }
-  tt_precond(ctx, view_of(acc), P->pt, P->pw, P->opts.rank, out, P->opts.rank_tol);  // T P~^-1 (one truncation)
+  tt_precond(ctx, view_of(acc), P->pt, P->pw, rank, out, P->opts.rank_tol);  // T P~^-1 (one truncation)
 }
 
 double lr_aeff(lrfg_problem* P, const double* E, const TTView& u) {
@@ -525,7 +525,7 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     out->tk = std::move(res);
   } else {
     TT res;
-    lr_apply(P, view_of(in->tt), res);
+    lr_apply(P, view_of(in->tt), res, P->opts.rank);
     out->tt = std::move(res);
   }
 }
@@ -618,59 +618,88 @@ void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field
   }
 }
 
+// Minimal-residual iteration with truncation (Sec. 3.3), stopped when the residual fails to decrease
+// (Sec. 4.3), at tol or maxit; the iterate of smallest residual is returned.  Rank adaptation (the solver
+// Sec. 4.3 proposes; opts.rank_start > 0): every T truncates to the current rank r_c, starting at
+// rank_start; when the residual fails to decrease below the cap opts.rank, r_c rises by rank_step, the
+// right-hand side is rebuilt at r_c and the iteration restarts from the best iterate, whose residual is
+// recomputed at r_c and becomes the new reference.
 void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
   lrfg_ctx* ctx = P->ctx;
-  const int rank = P->opts.rank;
+  const int cap = P->opts.rank;
+  const bool adapt = P->opts.rank_start > 0;
+  int rc = adapt ? std::min(P->opts.rank_start, cap) : cap;
   const double rtol = P->opts.rank_tol;
   TT b;
-  lr_rhs(P, E, b);
-  const double nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
+  lr_rhs(P, E, b, rc);
+  double nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
   TT u, r, best_u;
-  bool have_u = false;
+  bool u_zero = true, best_zero = true;
   double best = INFINITY;
   int best_it = 0, it = 0, applies = 0;
   tt_copy(ctx, view_of(b), r);
+  // r <- T(b - C u) at the current rank
+  auto residual = [&]() {
+    TT cu, diff, rn;
+    lr_apply(P, view_of(u), cu, rc);
+    ++applies;
+    tt_add(ctx, 1.0, nullptr, view_of(b), -1.0, nullptr, view_of(cu), diff);
+    tt_round(ctx, view_of(diff), rc, rn, rtol);
+    r = std::move(rn);
+  };
   while (nb > 0.0) {
-    double nr = (it == 0) ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
+    double nr = std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
+    if (it == 0 && u_zero) nr = 1.0;  // r = b
     if (nr < best) {
       best = nr;
       best_it = it;
-      if (have_u) tt_copy(ctx, view_of(u), best_u);
-    } else if (P->opts.stop_on_increase) {
+      best_zero = u_zero;
+      if (!u_zero) tt_copy(ctx, view_of(u), best_u);
+    } else if (adapt && rc < cap) {
+      rc = std::min(cap, rc + std::max(1, P->opts.rank_step));
+      TT nbv;
+      lr_rhs(P, E, nbv, rc);
+      b = std::move(nbv);
+      nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
+      u_zero = best_zero;
+      if (u_zero) {
+        tt_copy(ctx, view_of(b), r);
+      } else {
+        tt_copy(ctx, view_of(best_u), u);
+        residual();
+      }
+      nr = u_zero ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
+      best = nr;
+    } else if (P->opts.stop_on_increase || adapt) {
       break;
     }
     if (nr <= P->opts.tol || it >= P->opts.maxit) break;
     TT q;
-    lr_apply(P, view_of(r), q);
+    lr_apply(P, view_of(r), q, rc);
     ++applies;
     const double qq = tt_dot(ctx, view_of(q), view_of(q));
     if (qq == 0.0) break;
     const double omega = tt_dot(ctx, view_of(q), view_of(r)) / qq;
     TT un;
-    if (!have_u) {
+    if (u_zero) {
       TT scaled;
       tt_copy(ctx, view_of(r), scaled);
       axpby(ctx, (long long)scaled.core_elems(0), omega, r.core[0].get(), 0.0, scaled.core[0].get());
-      tt_round(ctx, view_of(scaled), rank, un, rtol);
+      tt_round(ctx, view_of(scaled), rc, un, rtol);
     } else {
       TT s;
       tt_add(ctx, 1.0, nullptr, view_of(u), omega, nullptr, view_of(r), s);
-      tt_round(ctx, view_of(s), rank, un, rtol);
+      tt_round(ctx, view_of(s), rc, un, rtol);
     }
     u = std::move(un);
-    have_u = true;
+    u_zero = false;
     ++it;
-    TT cu, diff;
-    lr_apply(P, view_of(u), cu);
-    ++applies;
-    tt_add(ctx, 1.0, nullptr, view_of(b), -1.0, nullptr, view_of(cu), diff);
-    TT rn;
-    tt_round(ctx, view_of(diff), rank, rn, rtol);
-    r = std::move(rn);
+    residual();
   }
-  if (!best_u.d) {
+  if (best_zero || !best_u.d) {
     // the best iterate is u_0 = 0
     int rr[4] = {1, 1, 1, 1};
+    best_u = TT();
     tt_alloc(ctx, best_u, P->d, P->N, rr);
     for (int j = 0; j < P->d; ++j) fill(ctx, best_u.core[j].get(), 0.0, P->N[j]);
   }
@@ -984,6 +1013,9 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     if (opts->fmt != LRFG_FULL) LRFG_REQUIRE(opts->rank >= 1, "low-rank solve needs rank >= 1 (got %d)", opts->rank);
     LRFG_REQUIRE(opts->rank_tol >= 0.0 && opts->rank_tol < 1.0, "rank_tol must be in [0, 1) (got %g)", opts->rank_tol);
     LRFG_REQUIRE(opts->coeff_rank >= 0, "coeff_rank must be >= 0 (got %d)", opts->coeff_rank);
+    LRFG_REQUIRE(opts->rank_start >= 0 && opts->rank_step >= 0, "rank_start and rank_step must be >= 0");
+    if (opts->rank_start > 0 && opts->fmt != LRFG_TT)
+      fail(LRFG_ENOTSUP, "rank adaptation (rank_start > 0) is implemented for LRFG_TT solutions");
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
                  "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();
@@ -1123,7 +1155,7 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
     } else if (tucker_like(P->opts.fmt)) {
       tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk, P->opts.rank_tol);
     } else {
-      lr_rhs(P, E, f->tt);
+      lr_rhs(P, E, f->tt, P->opts.rank);
     }
     *out = f;
   });

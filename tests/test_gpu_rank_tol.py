@@ -84,3 +84,36 @@ def test_rank_tol_invalid(ctx):
         ctx.problem(coeff, lrfg.TT, rank=5, rank_tol=1.5)
     with pytest.raises(lrfg.LrfgError):
         ctx.tt_round(coeff, 3, tol=-1.0)
+
+
+@pytest.mark.parametrize("d,N,cap,start,step", [(2, 31, 8, 2, 2), (3, 21, 8, 2, 3)])
+def test_rank_adaptive_solve_matches_oracle(ctx, d, N, cap, start, step):
+    """Rank-adapting MinRes (rank_start/rank_step) against the oracle's minres_rank_adaptive: the same
+    rank schedule, so A_eff agrees to the FP64-path tolerance and the returned ranks match."""
+    _, terms, w = smoothed_cube(d, N, contrast=10.0, full=False)
+    E = np.eye(d)[0]
+    a_tt = lr.tt_from_separable(terms, w)
+    op = lr.LowRankGaNi(a_tt, (N,) * d, fmt="tt", rank=cap, pinv_eps=0.1)
+    ref = lr.minres_rank_adaptive(op, E, rank_start=start, rank_step=step, tol=1e-12, maxit=50)
+    P = ctx.problem(lrfg.TTensor.from_numpy(a_tt), lrfg.TT, rank=cap, tol=1e-12, maxit=50, rank_start=start,
+                    rank_step=step)
+    res, u = P.solve(E)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    assert abs(res.iters - ref["iters"]) <= 2, (res.iters, ref["iters"])
+    assert u.info()[3] == lr.tt_ranks(ref["u"])
+    u.free()
+    # started at the cap it is the fixed-rank solve, bit for bit
+    fixed, _ = ctx.problem(lrfg.TTensor.from_numpy(a_tt), lrfg.TT, rank=cap, tol=1e-12, maxit=50).solve(
+        E, want_field=False)
+    at_cap, _ = ctx.problem(lrfg.TTensor.from_numpy(a_tt), lrfg.TT, rank=cap, tol=1e-12, maxit=50,
+                            rank_start=cap, rank_step=step).solve(E, want_field=False)
+    assert at_cap.Aeff == fixed.Aeff and at_cap.iters == fixed.iters
+    P.free()
+
+
+def test_rank_adaptive_only_tt(ctx):
+    _, terms, w = smoothed_cube(2, 15, contrast=10.0, full=False)
+    with pytest.raises(lrfg.LrfgError) as e:
+        ctx.problem(lrfg.TuckerTensor.from_numpy(*lr.tucker_from_separable(terms, w)), lrfg.TUCKER, rank=5,
+                    rank_start=2)
+    assert e.value.status == 6  # LRFG_ENOTSUP

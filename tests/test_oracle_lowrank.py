@@ -205,3 +205,29 @@ def test_tolerance_truncation_bound_and_first_rank(fmt):
                           if (tails[k] if k < len(s) else 0.0) <= loc * np.linalg.norm(s))
         rank = y[0].shape[2] if fmt == "tt" else y[1][0].shape[1]
         assert rank == k_expected, (tol, rank, k_expected)
+
+
+def test_rank_adaptive_minres_pins():
+    """Rank-adapting MinRes (Sec. 4.3's proposal, oracle reading): started at the cap it is the fixed-rank
+    iteration; raising the rank beats the fixed starting rank; untruncated at the cap it reaches the
+    full-format Fourier-Galerkin solution (an independent solver) to 1e-10."""
+    d, N = 2, 31
+    A, terms, w = smoothed_cube(d, N, contrast=10.0)
+    E = np.eye(d)[0]
+    a_tt = lr.tt_from_separable(terms, w)
+    op = lr.LowRankGaNi(a_tt, (N,) * d, fmt="tt", rank=8, pinv_eps=0.1)
+    fixed8 = lr.minres(op, E, tol=1e-12, maxit=60)
+    ad8 = lr.minres_rank_adaptive(op, E, rank_start=8, rank_step=2, tol=1e-12, maxit=60)
+    assert ad8["Aeff"] == fixed8["Aeff"] and ad8["iters"] == fixed8["iters"] and ad8["rank"] == 8
+    op2 = lr.LowRankGaNi(a_tt, (N,) * d, fmt="tt", rank=2, pinv_eps=0.1)
+    fixed2 = lr.minres(op2, E, tol=1e-12, maxit=60)
+    ad = lr.minres_rank_adaptive(op, E, rank_start=2, rank_step=2, tol=1e-12, maxit=60)
+    assert ad["rank"] > 2 and ad["rel_resid"] < 0.5 * fixed2["rel_resid"]
+    assert op.rank == 8  # restored
+    Ns = 15
+    As, ts, ws = square_inclusion(2, Ns)
+    full = fg.solve_gani(As, E, tol=1e-13, maxit=3000)
+    opu = lr.LowRankGaNi(lr.tt_from_separable(ts, ws), (Ns, Ns), fmt="tt", rank=Ns, pinv_eps=0.1)
+    out = lr.minres_rank_adaptive(opu, E, rank_start=2, rank_step=4, tol=1e-13, maxit=400)
+    assert out["rank"] > 2 and out["rel_resid"] <= 1e-13
+    assert lr.relative_error(full["Aeff"], out["Aeff"]) <= 1e-10
