@@ -15,7 +15,8 @@
  *                there u = sum_i c_i x_i (x) y_i is a Tucker tensor and the CP truncation (QR of both
  *                factors, SVD of R1 diag(c) R2^T, App. A.1.3) is the d = 2 Tucker truncation, so CP
  *                problems run the Tucker path; their fields are Tucker fields (LRFG_ENOTSUP for d = 3).
- * The coefficient is isotropic, A(x) = a(x) I, given as grid values, a tensor train or a Tucker tensor.
+ * The coefficient is A(x) = a(x) I + B: a scalar field a given as grid values, a tensor train or a Tucker
+ * tensor, plus an optional constant symmetric positive semidefinite anisotropic part B (Sec. 4.4).
  * A Tucker problem built from grid values or a TT compresses the coefficient by HOSVD of its grid,
  * keeping singular values above 1e-7 of the largest in each mode (at most 64 per mode): the HOSVD
  * takes them from FP64 Gram matrices, which resolve singular values down to about sqrt(eps) of the
@@ -102,6 +103,10 @@ typedef struct {
   lrfg_tt tt;           /* carriages of a; the coefficient's TT ranks are its own (r_A) */
   int on_device;        /* 1: values / tt.cores / tk buffers are device pointers; 0: host pointers */
   lrfg_tucker tk;       /* core and factors of a (LRFG_TUCKER) */
+  double B[9];          /* constant anisotropic part, d x d row-major (leading d x d of the 3 x 3 array):
+                           A~(x) = a(x) I + B (the modified materials of Sec. 4.4).  All zero = isotropic.
+                           B must be symmetric and positive semidefinite (LRFG_EINVAL otherwise); LRFG_FULL
+                           and LRFG_TT solutions (LRFG_ENOTSUP for LRFG_TUCKER / LRFG_CP) */
 } lrfg_coeff;
 
 typedef struct {

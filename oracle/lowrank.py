@@ -461,10 +461,12 @@ class LowRankGaNi:
     the exponential-sum accuracy ``pinv_eps`` of P~^-1.  All tensors are Fourier coefficient tensors
     except the coefficient, which holds grid values (as in the paper's A~)."""
 
-    def __init__(self, a_lr, shape, fmt="tt", rank=10, pinv_eps=0.1, rank_tol=None):
+    def __init__(self, a_lr, shape, fmt="tt", rank=10, pinv_eps=0.1, rank_tol=None, B=None):
         self.f = FORMATS[fmt]
         self.fmt = fmt
         self.a = a_lr
+        # constant anisotropic part: A~(x) = a(x) I + B (the modified materials of Sec. 4.4)
+        self.B = None if B is None else np.asarray(B, dtype=np.float64)
         self.shape = tuple(int(n) for n in shape)
         self.d = len(self.shape)
         self.rank = rank
@@ -480,13 +482,22 @@ class LowRankGaNi:
         return self.f.round(x, rmax=self.rank, tol=self.rank_tol)
 
     def apply(self, vh):
-        """T P~^-1 T grad^* F T A~ F^-1 grad^ v  (Eq. (Pls_lowrank))."""
+        """T P~^-1 T grad^* F T A~ F^-1 grad^ v  (Eq. (Pls_lowrank)).  With the constant anisotropic part
+        B, component a of A~ e is a e_a + sum_b B[a, b] e_b (zero entries of B skipped)."""
         f = self.f
         acc = None
+        es = None
+        if self.B is not None:
+            es = [f.idft(f.mmul(vh, b, 2j * np.pi * self.K[b])) for b in range(self.d)]
         for a in range(self.d):
             g = f.mmul(vh, a, 2j * np.pi * self.K[a])      # gradient, mode a (rank unchanged)
             e = f.idft(g)                                   # F^-1, mode-wise
-            w = self.T(f.had(self.a, e))                    # T A~ e_a
+            ae = f.had(self.a, e)
+            if self.B is not None:
+                for b in range(self.d):
+                    if self.B[a, b] != 0.0:
+                        ae = f.add(ae, f.scale(es[b], float(self.B[a, b])))
+            w = self.T(ae)                                  # T A~ e_a
             wh = f.dft(w)                                   # F, mode-wise
             term = f.mmul(wh, a, -2j * np.pi * self.K[a])   # divergence, mode a
             acc = term if acc is None else f.add(acc, term)
@@ -494,7 +505,8 @@ class LowRankGaNi:
         return self.T(f.had(self.Pinv, s))                  # T P~^-1
 
     def rhs(self, E):
-        """b~ = - T P~^-1 grad^* F A~ E  (Eq. (Pls_lowrank))."""
+        """b~ = - T P~^-1 grad^* F A~ E  (Eq. (Pls_lowrank)).  A constant anisotropic part adds the constant
+        field B E, whose divergence is zero, so B does not enter."""
         f = self.f
         acc = None
         ah = f.dft(self.a)
@@ -508,19 +520,28 @@ class LowRankGaNi:
         return f.scale(self.T(f.had(self.Pinv, acc)), -1.0)
 
     def homogenised_coefficient(self, uh, E) -> float:
-        """A_eff E.E = (1/|N|) sum_k a(x_k) |E + e(x_k)|^2 with e_a = F^-1 grad^_a u^ (Eq. (homog)),
+        """A_eff E.E = (1/|N|) sum_k A~(x_k)(E + e(x_k)).(E + e(x_k)) with e_a = F^-1 grad^_a u^ (Eq. (homog)),
         evaluated by low-rank contractions without truncation:
-        |E|^2 <a,1> + 2 sum_a E_a <a, e_a> + sum_a <a * e_a, e_a>."""
+        |E|^2 <a,1> + 2 sum_a E_a <a, e_a> + sum_a <a * e_a, e_a>  (+ E.B E + sum_ab B_ab <e_a, e_b>)."""
         f = self.f
         size = float(np.prod(self.shape))
         ones = f.sep([[np.ones(n) for n in self.shape]])
         a_mean = np.real(f.dot(ones, self.a)) / size
         val = float(np.dot(E, E)) * a_mean
+        es = []
         for a in range(self.d):
             e = f.idft(f.mmul(uh, a, 2j * np.pi * self.K[a]))
+            es.append(e)
             ae = f.had(self.a, e)
             val += 2.0 * float(E[a]) * np.real(f.dot(ones, ae)) / size
             val += np.real(f.dot(e, ae)) / size
+        if self.B is not None:
+            # (E + e).B(E + e) averaged: E.B E + sum_ab B[a, b] <e_a, e_b> / |N| (e has zero mean)
+            val += float(E @ self.B @ E)
+            for a in range(self.d):
+                for b in range(self.d):
+                    if self.B[a, b] != 0.0:
+                        val += float(self.B[a, b]) * np.real(f.dot(es[a], es[b])) / size
         return float(val)
 
     def full_field(self, uh) -> np.ndarray:

@@ -350,13 +350,14 @@ class Context:
     # ---- problems and fields ---------------------------------------------------------------------
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
-                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1) -> "Problem":
+                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None) -> "Problem":
         """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only).
         ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
         rank cap of a grid coefficient's TT compression (0: ``rank``).  ``rank_start`` > 0: rank-adapting
-        MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT)."""
+        MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT).  ``B``: constant symmetric
+        positive semidefinite d x d anisotropic part, A~ = a I + B (FULL and TT)."""
         return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank,
-                       rank_start, rank_step)
+                       rank_start, rank_step, B)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -447,7 +448,7 @@ class Problem:
     (isotropic a(x) samples) or a TTensor of the coefficient."""
 
     def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64,
-                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1):
+                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1, B=None):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -486,6 +487,7 @@ class Problem:
             for j, n in enumerate(list(keep.shape)[:3]):  # the library rejects d outside {2, 3}
                 c.N[j] = int(n)
             c.fmt = L.LRFG_FULL
+        _set_b(c, B)
         o = L.lrfg_opts()
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
@@ -542,6 +544,18 @@ class Problem:
             self.free()
         except Exception:
             pass
+
+
+def _set_b(c, B):
+    """Copy a d x d anisotropic part into the coefficient struct's 3 x 3 row-major array."""
+    if B is None:
+        return
+    Bm = np.asarray(B, dtype=np.float64)
+    if Bm.ndim != 2 or Bm.shape[0] != Bm.shape[1] or Bm.shape[0] != c.d:
+        raise ValueError("B must be a d x d matrix")
+    for i in range(c.d):
+        for j in range(c.d):
+            c.B[3 * i + j] = float(Bm[i, j])
 
 
 def _host_coeff(coeff):
@@ -610,8 +624,9 @@ class Batch:
 
     def submit(self, coeff, E, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8,
                maxit: int = 200, stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
-               coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1) -> int:
+               coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None) -> int:
         c, keep = _host_coeff(coeff)
+        _set_b(c, B)
         o = L.lrfg_opts()
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))

@@ -27,7 +27,7 @@ class lrfg_tucker(C.Structure):
 
 class lrfg_coeff(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int * 3), ("fmt", C.c_int), ("values", C.c_void_p),
-                ("tt", lrfg_tt), ("on_device", C.c_int), ("tk", lrfg_tucker)]
+                ("tt", lrfg_tt), ("on_device", C.c_int), ("tk", lrfg_tucker), ("B", C.c_double * 9)]
 
 
 class lrfg_opts(C.Structure):

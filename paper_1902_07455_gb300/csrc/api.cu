@@ -197,6 +197,9 @@ struct lrfg_problem {
   DBuf<float> a_full_f;
   DBuf<float2> wcf;
   DBuf<float> wrf;
+  // constant anisotropic part B (d x d row-major, 3 x 3 storage) of A~ = a I + B; aniso = B != 0
+  double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  bool aniso = false;
 };
 
 namespace {
@@ -266,6 +269,54 @@ void check_tt(const lrfg_tt* x) {
 // both factors, SVD of R1 diag(c) R2^T, App. A.1.3) is the d = 2 Tucker truncation: they share its path
 bool tucker_like(int fmt) { return fmt == LRFG_TUCKER || fmt == LRFG_CP; }
 
+// B symmetric (to 1e-12 of its largest entry) and positive semidefinite: the eigenvalues of the d x d
+// matrix by cyclic Jacobi rotations (d <= 3) must be >= -1e-12 max|B|.  Returns true when B != 0.
+bool check_aniso(int d, const double* Bin, double* B) {
+  double bmax = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double v = Bin[i * 3 + j];
+      LRFG_REQUIRE(std::isfinite(v), "anisotropic part B must be finite");
+      bmax = std::max(bmax, std::fabs(v));
+    }
+  for (int t = 0; t < 9; ++t) B[t] = 0.0;
+  if (bmax == 0.0) return false;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      LRFG_REQUIRE(std::fabs(Bin[i * 3 + j] - Bin[j * 3 + i]) <= 1e-12 * bmax, "anisotropic part B must be symmetric");
+      B[i * 3 + j] = 0.5 * (Bin[i * 3 + j] + Bin[j * 3 + i]);
+    }
+  double M[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i][j] = (i < d && j < d) ? B[i * 3 + j] : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) off += M[p][q] * M[p][q];
+    if (off <= 1e-32 * bmax * bmax) break;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) {
+        if (M[p][q] == 0.0) continue;
+        const double th = 0.5 * (M[q][q] - M[p][p]) / M[p][q];
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < d; ++k) {  // columns p, q
+          const double mp = M[k][p], mq = M[k][q];
+          M[k][p] = c * mp - sn * mq;
+          M[k][q] = sn * mp + c * mq;
+        }
+        for (int k = 0; k < d; ++k) {  // rows p, q
+          const double mp = M[p][k], mq = M[q][k];
+          M[p][k] = c * mp - sn * mq;
+          M[q][k] = sn * mp + c * mq;
+        }
+      }
+  }
+  for (int i = 0; i < d; ++i)
+    LRFG_REQUIRE(M[i][i] >= -1e-12 * bmax, "anisotropic part B must be positive semidefinite (eigenvalue %g)", M[i][i]);
+  return true;
+}
+
 void check_tucker(const lrfg_tucker* x) {
   LRFG_REQUIRE(x != nullptr, "null Tucker tensor");
   check_grid(x->d, x->N);
@@ -324,6 +375,14 @@ void ones_tt(lrfg_ctx* ctx, int d, const int* N, TT& x) {
   for (int j = 0; j < d; ++j) fill(ctx, x.core[j].get(), 1.0, N[j]);
 }
 
+// E.B E for the 3 x 3 row-major storage of B
+double quad_form(const double* B, const double* E, int d) {
+  double v = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) v += E[i] * B[i * 3 + j] * E[j];
+  return v;
+}
+
 // ---- TT operator pieces -----------------------------------------------------------------------
 
 // e = D_alpha v (scaled): carriage alpha replaced, the others shared with v
@@ -363,16 +422,43 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
     for (int j = 0; j < d; ++j)
       khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1], (j == alpha) ? grad[j].get() : v.core[j], v.r[j],
                  v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
-  for (auto& g : grad) g.reset();
   TTBatch w;
-  tt_round_batch(ctx, batch_view(kr), r, w, tol);                // T, all components in one sweep
-  kr = TTBatch();
-  // divergence terms: -D_a on carriage a of component a, then the block sum over a
+  TT wa[3];
   TTView terms[3];
+  if (!P->aniso) {
+    for (auto& g : grad) g.reset();
+    tt_round_batch(ctx, batch_view(kr), r, w, tol);              // T, all components in one sweep
+    kr = TTBatch();
+    for (int alpha = 0; alpha < d; ++alpha) terms[alpha] = item_view(w, alpha);
+  } else {
+    // component a of A~ e with the constant anisotropic part: a (.) e_a + sum_b B[a][b] e_b (a TT sum in
+    // block form, zero entries of B skipped), then T
+    for (int alpha = 0; alpha < d; ++alpha) {
+      TTView xs[4];
+      double sc[4];
+      int m = 0;
+      xs[m] = item_view(kr, alpha);
+      sc[m++] = 1.0;
+      for (int beta = 0; beta < d; ++beta) {
+        const double bab = P->B[alpha * 3 + beta];
+        if (bab == 0.0) continue;
+        xs[m] = v;
+        xs[m].core[beta] = grad[beta].get();
+        sc[m++] = bab;
+      }
+      TT sum;
+      tt_add_many(ctx, xs, sc, m, sum);
+      tt_round(ctx, view_of(sum), r, wa[alpha], tol);             // T
+      terms[alpha] = view_of(wa[alpha]);
+    }
+    for (auto& g : grad) g.reset();
+    kr = TTBatch();
+  }
+  // divergence terms: -D_a on carriage a of component a, then the block sum over a
   for (int alpha = 0; alpha < d; ++alpha) {
-    terms[alpha] = item_view(w, alpha);
-    double* c = w.core[alpha].get() + (size_t)alpha * w.elems(alpha);
-    fibre_operator(ctx, c, c, w.r[alpha], w.N[alpha], w.r[alpha + 1], LRFG_MUL_DERIV, 0.0, -1.0);
+    double* c = const_cast<double*>(terms[alpha].core[alpha]);
+    fibre_operator(ctx, c, c, terms[alpha].r[alpha], terms[alpha].N[alpha], terms[alpha].r[alpha + 1], LRFG_MUL_DERIV,
+                   0.0, -1.0);
   }
   TT acc;
   tt_add_many(ctx, terms, nullptr, d, acc);
@@ -415,13 +501,22 @@ double lr_aeff(lrfg_problem* P, const double* E, const TTView& u) {
   double EE = 0.0;
   for (int j = 0; j < P->d; ++j) EE += E[j] * E[j];
   double val = EE * tt_dot(ctx, view_of(P->a_tt), view_of(ones)) / size;
+  ModeReplaced e[3];
   for (int alpha = 0; alpha < P->d; ++alpha) {
-    ModeReplaced e;
-    mode_replace(ctx, u, alpha, 1.0, e);
+    mode_replace(ctx, u, alpha, 1.0, e[alpha]);
     TT ae;
-    tt_hadamard(ctx, view_of(P->a_tt), e.view, ae);
+    tt_hadamard(ctx, view_of(P->a_tt), e[alpha].view, ae);
     if (E[alpha] != 0.0) val += 2.0 * E[alpha] * tt_dot(ctx, view_of(ae), view_of(ones)) / size;
-    val += tt_dot(ctx, view_of(ae), e.view) / size;
+    val += tt_dot(ctx, view_of(ae), e[alpha].view) / size;
+  }
+  if (P->aniso) {
+    // (E + e).B(E + e) averaged: E.B E + sum_ab B_ab <e_a, e_b> / |N| (e has zero mean)
+    val += quad_form(P->B, E, P->d);
+    for (int alpha = 0; alpha < P->d; ++alpha)
+      for (int beta = 0; beta < P->d; ++beta) {
+        const double bab = P->B[alpha * 3 + beta];
+        if (bab != 0.0) val += bab * tt_dot(ctx, e[alpha].view, e[beta].view) / size;
+      }
   }
   return val;
 }
@@ -452,8 +547,10 @@ void full_apply(lrfg_problem* P, const typename CplxOf<R>::T* v, typename CplxOf
     full_inverse<R>(ctx, g, w.wc, w.a, R(1), w.wr);         // A~ F^-1 grad^ v
     full_forward<R>(ctx, g, w.wr, nullptr, R(1), w.wc);     // F
     half_acc_div(ctx, g, (const typename CplxOf<R>::T*)w.wc, out, alpha, 1.0, alpha == 0,
-                 precond && alpha == g.d - 1);              // grad^*
+                 precond && alpha == g.d - 1 && !P->aniso);  // grad^*
   }
+  // constant anisotropic part: grad^* F B F^-1 grad^ is the multiplier 4 pi^2 k.B k
+  if (P->aniso) half_acc_aniso(ctx, g, v, out, P->B, precond);
 }
 
 template <typename R>
@@ -476,9 +573,12 @@ double full_aeff(lrfg_problem* P, const double* E, const double2* v) {
     full_inverse<double>(ctx, g, P->wc.get(), nullptr, 1.0, P->wr.get());
     energy_sum(ctx, g, (const double*)P->wr.get(), P->a_full.get(), E[alpha], acc.get(), alpha > 0);
   }
+  // (E + e).B(E + e) summed over the grid: |N| E.B E + sum_x e.B e (e has zero mean)
+  if (P->aniso) aniso_energy_sum(ctx, g, v, P->B, acc.get(), 1);
   double h = 0.0;
   LRFG_CUDA(cudaMemcpyAsync(&h, acc.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (P->aniso) h += (double)g.n_real * quad_form(P->B, E, g.d);
   return h / (double)g.n_real;
 }
 
@@ -1026,6 +1126,9 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(P->opts.pinv_eps < 1.0, "pinv_eps must be < 1");
     P->d = coeff->d;
     for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
+    P->aniso = check_aniso(P->d, coeff->B, P->B);
+    if (P->aniso && tucker_like(opts->fmt))
+      fail(LRFG_ENOTSUP, "an anisotropic part B is implemented for LRFG_FULL and LRFG_TT solutions");
     const long long n = grid_size(P->d, P->N);
     // coefficient -> device
     if (coeff->fmt == LRFG_FULL) {

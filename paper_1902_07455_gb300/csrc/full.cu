@@ -315,6 +315,51 @@ __global__ void precond_kernel(const V* __restrict__ in, V* out, RowMap m,
   out[t] = mkc<V>(v.x * s, v.y * s);
 }
 
+// the six distinct entries of a symmetric 3 x 3 B times a constant: (b00, b11, b22, b01, b02, b12)
+template <typename R>
+struct SymB {
+  R b[6];
+};
+
+template <typename R>
+static SymB<R> sym_b(const double* B, double c) {
+  SymB<R> s;
+  s.b[0] = (R)(c * B[0]);
+  s.b[1] = (R)(c * B[4]);
+  s.b[2] = (R)(c * B[8]);
+  s.b[3] = (R)(c * B[1]);
+  s.b[4] = (R)(c * B[2]);
+  s.b[5] = (R)(c * B[5]);
+  return s;
+}
+
+template <typename R>
+__device__ __forceinline__ R quad_b(const SymB<R>& s, int k0, int k1, int k2) {
+  const R x = (R)k0, y = (R)k1, z = (R)k2;
+  return s.b[0] * x * x + s.b[1] * y * y + s.b[2] * z * z + (R)2 * (s.b[3] * x * y + s.b[4] * x * z + s.b[5] * y * z);
+}
+
+// acc += (c k.B k) in; then, if precond, acc /= k.k (0 at k = 0)
+template <typename V>
+__global__ void acc_aniso_kernel(const V* __restrict__ in, V* acc, RowMap m, SymB<typename RealOf<V>::T> sb,
+                                 int precond, const typename RealOf<V>::T* __restrict__ inv_kk) {
+  using R = typename RealOf<V>::T;
+  int k[3];
+  size_t t;
+  if (!row_k(m, k[0], k[1], k[2], t)) return;
+  const R q = quad_b(sb, k[0], k[1], k[2]);
+  const V v = in[t];
+  V r = acc[t];
+  r.x += q * v.x;
+  r.y += q * v.y;
+  if (precond) {
+    const R s = inv_kk[k[0] * k[0] + k[1] * k[1] + k[2] * k[2]];
+    r.x *= s;
+    r.y *= s;
+  }
+  acc[t] = r;
+}
+
 template <typename R> static const R* inv_table(const FullGrid& g);
 template <> const double* inv_table<double>(const FullGrid& g) { return g.inv_kk64; }
 template <> const float* inv_table<float>(const FullGrid& g) { return g.inv_kk32; }
@@ -358,6 +403,16 @@ void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alp
   LRFG_LAUNCH(ctx, KC_POINTWISE, 4.0 * g.n_half, (init ? 2.0 : 3.0) * sizeof(V) * g.n_half,
               acc_div_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(
                   in, acc, rowmap(g), alpha, (R)two_pi_times(scale), init, precond, inv_table<R>(g)));
+}
+
+template <typename V>
+void half_acc_aniso(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, const double* B, int precond) {
+  using R = typename RealOf<V>::T;
+  LRFG_REQUIRE(!precond || inv_table<R>(g), "reciprocal table missing");
+  const double c = 4.0 * 9.869604401089358618834490999876;  // 4 pi^2
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 14.0 * g.n_half, 3.0 * sizeof(V) * g.n_half,
+              acc_aniso_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(
+                  in, acc, rowmap(g), sym_b<R>(B, c), precond, inv_table<R>(g)));
 }
 
 template <typename V>
@@ -456,6 +511,39 @@ __global__ void __launch_bounds__(256) energy_kernel(const R* __restrict__ e, co
   }
 }
 
+// sum over the full spectrum of (k.B k) |v_k|^2 (B pre-scaled), from the half spectrum with weights 1 / 2
+__global__ void __launch_bounds__(256) aniso_energy_kernel(const double2* __restrict__ v, long long n, int H, int d,
+                                                           int N0, int N1, SymB<double> sb, double* partial) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / H;
+    const int kl = (int)(t - row * H);
+    int k0, k1, k2;
+    if (d == 3) {
+      const int i0 = (int)(row / N1), i1 = (int)(row - (long long)i0 * N1);
+      k0 = freq_of(i0, N0);
+      k1 = freq_of(i1, N1);
+      k2 = kl;
+    } else {
+      k0 = freq_of((int)row, N0);
+      k1 = kl;
+      k2 = 0;
+    }
+    const double2 x = v[t];
+    const double w = kl == 0 ? 1.0 : 2.0;
+    s += w * quad_b(sb, k0, k1, k2) * (x.x * x.x + x.y * x.y);
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < 8; ++i) r += red[i];
+    partial[blockIdx.x] = r;
+  }
+}
+
 // *out (+)= sum of partials; then, if ratio: mode 1 -> *ratio = *aux / *out, mode 2 -> *out / *aux
 // (0 when the divisor is 0): the PCG step lengths, formed once on the device
 __global__ void finish_sum_kernel(const double* __restrict__ partial, int n, double* out, int accumulate,
@@ -486,6 +574,19 @@ void half_dot(lrfg_ctx* ctx, const FullGrid& g, const V* x, const V* y, double* 
               half_dot_kernel<V><<<kRedBlocks, 256, 0, ctx->stream>>>(x, y, g.n_half, g.H, partial.get()));
   LRFG_LAUNCH(ctx, KC_REDUCE, kRedBlocks, kRedBlocks * sizeof(double),
               finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, 0, aux, ratio, mode));
+}
+
+void aniso_energy_sum(lrfg_ctx* ctx, const FullGrid& g, const double2* v, const double* B, double* out_dev,
+                      int accumulate) {
+  DBuf<double> partial(ctx->pool, kRedBlocks);
+  const double c = 4.0 * 9.869604401089358618834490999876 / (double)g.n_real;  // 4 pi^2 / |N|
+  LRFG_LAUNCH(ctx, KC_REDUCE, 16.0 * g.n_half, sizeof(double2) * (double)g.n_half,
+              aniso_energy_kernel<<<kRedBlocks, 256, 0, ctx->stream>>>(v, g.n_half, g.H, g.d, g.N[0],
+                                                                         g.d == 3 ? g.N[1] : 1, sym_b<double>(B, c),
+                                                                         partial.get()));
+  LRFG_LAUNCH(ctx, KC_REDUCE, kRedBlocks, kRedBlocks * sizeof(double),
+              finish_sum_kernel<<<1, 256, 0, ctx->stream>>>(partial.get(), kRedBlocks, out_dev, accumulate, nullptr,
+                                                            nullptr, 0));
 }
 
 template <typename R>
@@ -570,6 +671,7 @@ void convert(lrfg_ctx* ctx, const A* in, B* out, long long n) {
   template void half_mul_grad<V>(lrfg_ctx*, const FullGrid&, const V*, V*, int, double);                  \
   template void half_acc_div<V>(lrfg_ctx*, const FullGrid&, const V*, V*, int, double, int, int);         \
   template void half_precond<V>(lrfg_ctx*, const FullGrid&, const V*, V*);                                \
+  template void half_acc_aniso<V>(lrfg_ctx*, const FullGrid&, const V*, V*, const double*, int);          \
   template void half_dot<V>(lrfg_ctx*, const FullGrid&, const V*, const V*, double*, const double*, double*, int); \
   template void energy_sum<R>(lrfg_ctx*, const FullGrid&, const R*, const R*, double, double*, int);      \
   template void pcg_update<V>(lrfg_ctx*, const FullGrid&, V*, V*, const V*, const V*, V*, const double*);  \

@@ -35,6 +35,14 @@ void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alp
                   int precond);
 template <typename V>
 void half_precond(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out);
+// the constant anisotropic part of A~ = a I + B: acc += 4 pi^2 (k.B k) in, then, if precond, acc /= k.k
+// (-div(B grad u) is the Fourier multiplier 4 pi^2 k.B k; B symmetric, 3 x 3 row-major storage)
+template <typename V>
+void half_acc_aniso(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, const double* B, int precond);
+// out_dev (+)= (4 pi^2 / |N|) sum over the full spectrum of (k.B k) |v_k|^2 = sum_x e(x).B e(x) for the
+// gradient field e of u with half spectrum v = Phi u (FP64)
+void aniso_energy_sum(lrfg_ctx* ctx, const FullGrid& g, const double2* v, const double* B, double* out_dev,
+                      int accumulate);
 // Hermitian-weighted real inner product over the full spectrum (FP64 accumulation) into a device scalar
 // optional: *ratio = *aux / result (mode 1) or result / *aux (mode 2), 0 for a zero divisor
 template <typename V>

@@ -187,3 +187,62 @@ def test_config1_square_63():
     assert res["rel_resid"] <= 1e-8
     harm = 1.0 / np.mean(1.0 / A)
     assert harm < res["Aeff"] < np.mean(A)
+
+
+# the constant anisotropic parts of the modified materials of Sec. 4.4 (eigenvalues (1, 10) and (1, 5, 10))
+B2 = np.array([[5.5, -4.5], [-4.5, 5.5]])
+B3 = np.array([[4.25, -3.25, -1.25 * np.sqrt(2.0)], [-3.25, 4.25, 1.25 * np.sqrt(2.0)],
+               [-1.25 * np.sqrt(2.0), 1.25 * np.sqrt(2.0), 7.5]])
+
+
+def test_anisotropic_parts_have_the_stated_eigenvalues():
+    assert np.allclose(np.linalg.eigvalsh(B2), [1.0, 10.0], atol=1e-13)
+    assert np.allclose(np.linalg.eigvalsh(B3), [1.0, 5.0, 10.0], atol=1e-13)
+
+
+def dense_direct_tensor(At, E):
+    """Minimise (1/|N|) sum_k (E + D u)_k.A_k (E + D u)_k for a tensor field At (d, d, N..) by a dense
+    least-squares solve: K = sum_ab D_a^T diag(A_ab) D_b, b = -sum_ab D_a^T (A_ab E_b)."""
+    d = At.shape[0]
+    N = At.shape[-1]
+    D1 = trefethen_D(N)
+    I = np.eye(N)
+    Ds = []
+    for ax in range(d):
+        mats = [I] * d
+        mats[ax] = D1
+        M = mats[0]
+        for m in mats[1:]:
+            M = np.kron(M, m)
+        Ds.append(M)
+    K = sum(Ds[a].T @ (At[a, b].ravel()[:, None] * Ds[b]) for a in range(d) for b in range(d))
+    rhs = -sum(Ds[a].T @ (At[a, b].ravel() * E[b]) for a in range(d) for b in range(d))
+    u = np.linalg.lstsq(K, rhs, rcond=1e-13)[0]
+    u -= u.mean()
+    f = np.stack([E[i] + Ds[i] @ u for i in range(d)])
+    dens = np.einsum("abk,ak,bk->k", At.reshape(d, d, -1), f, f)
+    return float(np.mean(dens)), u.reshape(At.shape[2:])
+
+
+@pytest.mark.parametrize("d,N", [(2, 9), (2, 13), (3, 5)])
+def test_anisotropic_pcg_matches_dense_direct_solve(d, N):
+    """The tensor-coefficient path of the full oracle (A~ = a I + B, Sec. 4.4) against a dense direct
+    solve of the same minimisation."""
+    a = square_inclusion(d, N)[0]
+    B = B2 if d == 2 else B3
+    At = a[None, None] * np.eye(d).reshape((d, d) + (1,) * d) + B.reshape((d, d) + (1,) * d)
+    for E in (np.eye(d)[0], np.ones(d)):
+        ref, u_ref = dense_direct_tensor(At, E)
+        res = fg.solve_gani(At, E, tol=1e-14, maxit=3000)
+        assert abs(res["Aeff"] - ref) <= 1e-12 * ref
+        u = np.real(fg.idft(res["uh"], d))
+        assert np.abs(u - u_ref).max() <= 1e-9 * max(1.0, np.abs(u_ref).max())
+
+
+def test_anisotropic_constant_coefficient_exact():
+    d, N = 3, 7
+    At = 2.0 * np.eye(d).reshape((d, d) + (1,) * d) + B3.reshape((d, d) + (1,) * d) + np.zeros((d, d) + (N,) * d)
+    E = np.array([1.0, -2.0, 0.5])
+    res = fg.solve_gani(At, E)
+    ref = float(E @ (2.0 * np.eye(d) + B3) @ E)
+    assert abs(res["Aeff"] - ref) <= 1e-13 * ref

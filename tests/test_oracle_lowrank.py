@@ -231,3 +231,20 @@ def test_rank_adaptive_minres_pins():
     out = lr.minres_rank_adaptive(opu, E, rank_start=2, rank_step=4, tol=1e-13, maxit=400)
     assert out["rank"] > 2 and out["rel_resid"] <= 1e-13
     assert lr.relative_error(full["Aeff"], out["Aeff"]) <= 1e-10
+
+
+@pytest.mark.parametrize("fmt,d,N", [("tt", 2, 15), ("tt", 3, 9), ("tucker", 2, 15)])
+def test_untruncated_anisotropic_lowrank_equals_full(fmt, d, N):
+    """Constant anisotropic part (Sec. 4.4's B): the untruncated low-rank solve equals the full-format
+    oracle's tensor-coefficient solve (an independent route: einsum over the full tensor field)."""
+    B = np.array([[5.5, -4.5], [-4.5, 5.5]]) if d == 2 else np.array(
+        [[4.25, -3.25, -1.25 * np.sqrt(2.0)], [-3.25, 4.25, 1.25 * np.sqrt(2.0)],
+         [-1.25 * np.sqrt(2.0), 1.25 * np.sqrt(2.0), 7.5]])
+    A, terms, weights = square_inclusion(d, N)
+    At = A[None, None] * np.eye(d).reshape((d, d) + (1,) * d) + B.reshape((d, d) + (1,) * d)
+    E = np.ones(d)
+    full = fg.solve_gani(At, E, tol=1e-13, maxit=3000)
+    op = lr.LowRankGaNi(lr.FORMATS[fmt].sep(terms, weights), (N,) * d, fmt=fmt, rank=None, pinv_eps=0.1,
+                        rank_tol=1e-15, B=B)
+    out = lr.minres(op, E, tol=1e-13, maxit=600, stop_on_increase=False)
+    assert lr.relative_error(full["Aeff"], out["Aeff"]) <= 1e-10
