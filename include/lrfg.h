@@ -105,8 +105,8 @@ typedef struct {
   lrfg_tucker tk;       /* core and factors of a (LRFG_TUCKER) */
   double B[9];          /* constant anisotropic part, d x d row-major (leading d x d of the 3 x 3 array):
                            A~(x) = a(x) I + B (the modified materials of Sec. 4.4).  All zero = isotropic.
-                           B must be symmetric and positive semidefinite (LRFG_EINVAL otherwise); LRFG_FULL
-                           and LRFG_TT solutions (LRFG_ENOTSUP for LRFG_TUCKER / LRFG_CP) */
+                           B must be symmetric and positive semidefinite (LRFG_EINVAL otherwise); every
+                           solution format */
 } lrfg_coeff;
 
 typedef struct {

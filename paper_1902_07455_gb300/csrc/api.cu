@@ -375,6 +375,9 @@ void ones_tt(lrfg_ctx* ctx, int d, const int* N, TT& x) {
   for (int j = 0; j < d; ++j) fill(ctx, x.core[j].get(), 1.0, N[j]);
 }
 
+// the anisotropic part for the Tucker path, or null when isotropic
+const double* aniso_b(const lrfg_problem* P) { return P->aniso ? P->B : nullptr; }
+
 // E.B E for the 3 x 3 row-major storage of B
 double quad_form(const double* B, const double* E, int d) {
   double v = 0.0;
@@ -621,7 +624,7 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     }
   } else if (tucker_like(P->opts.fmt)) {
     TK res;
-    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res, P->opts.rank_tol);
+    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res, P->opts.rank_tol, aniso_b(P));
     out->tk = std::move(res);
   } else {
     TT res;
@@ -703,7 +706,7 @@ int coeff_rank(const lrfg_opts& o) { return o.coeff_rank > 0 ? o.coeff_rank : o.
 void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
   TK best;
   const TKSolveResult r = tk_solve(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, P->opts.tol,
-                                   P->opts.maxit, P->opts.stop_on_increase, best, P->opts.rank_tol);
+                                   P->opts.maxit, P->opts.stop_on_increase, best, P->opts.rank_tol, aniso_b(P));
   res->iters = r.iters;
   res->rel_resid = r.rel_resid;
   res->converged = r.rel_resid <= P->opts.tol ? 1 : 0;
@@ -856,6 +859,8 @@ lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget)
     ctx->pool = new DevicePool(budget);
     LRFG_CUDA(cudaMalloc(&ctx->work_dev, sizeof(double) * 2 * KC_COUNT));
     LRFG_CUDA(cudaMemsetAsync(ctx->work_dev, 0, sizeof(double) * 2 * KC_COUNT, ctx->stream));
+    LRFG_CUDA(cudaMalloc(&ctx->splitk_cnt, sizeof(unsigned int) * kSplitKCounters));
+    LRFG_CUDA(cudaMemsetAsync(ctx->splitk_cnt, 0, sizeof(unsigned int) * kSplitKCounters, ctx->stream));
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != LRFG_OK) {
@@ -876,6 +881,7 @@ lrfg_status lrfg_destroy(lrfg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   delete ctx->pool;
   if (ctx->work_dev) cudaFree(ctx->work_dev);
+  if (ctx->splitk_cnt) cudaFree(ctx->splitk_cnt);
   for (auto& kv : ctx->twiddles) {
     cudaFree(kv.second.W);
     if (kv.second.Wf) cudaFree(kv.second.Wf);
@@ -1127,8 +1133,6 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     P->d = coeff->d;
     for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
     P->aniso = check_aniso(P->d, coeff->B, P->B);
-    if (P->aniso && tucker_like(opts->fmt))
-      fail(LRFG_ENOTSUP, "an anisotropic part B is implemented for LRFG_FULL and LRFG_TT solutions");
     const long long n = grid_size(P->d, P->N);
     // coefficient -> device
     if (coeff->fmt == LRFG_FULL) {
@@ -1296,7 +1300,7 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field
     LRFG_REQUIRE(E && Aeff, "null argument");
     check_field(P, u);
     *Aeff = (P->opts.fmt == LRFG_FULL)     ? full_aeff(P, E, u->half.get())
-            : tucker_like(P->opts.fmt)     ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk))
+            : tucker_like(P->opts.fmt)     ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk), aniso_b(P))
                                            : lr_aeff(P, E, view_of(u->tt));
   });
 }

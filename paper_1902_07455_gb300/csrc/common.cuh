@@ -159,6 +159,8 @@ struct lrfg_ctx {
   // device-side work counters (flops, bytes per class) for kernels whose work depends on data (active
   // sizes read on the device, e.g. numerical ranks); folded into stats when the profile is read
   double* work_dev = nullptr;
+  // split-K arrival counters, one per output tile of a split product (all zero between launches)
+  unsigned int* splitk_cnt = nullptr;
 };
 
 namespace lrfg {
@@ -195,6 +197,9 @@ class KTimer {
   KClass kc_;
   cudaEvent_t start_ = nullptr;
 };
+
+// capacity of the split-K arrival counters (a split product has fewer than 4 x 2 x 152 output tiles)
+constexpr int kSplitKCounters = 4096;
 
 // the device counter pair (flops, bytes) of class kc
 inline double* work_counter(lrfg_ctx* ctx, KClass kc) { return ctx->work_dev ? ctx->work_dev + 2 * (int)kc : nullptr; }

@@ -10,20 +10,20 @@ namespace lrfg {
 
 // ------------------------------------------------------------------------------------------------
 // GEMM, FP64.  On this part the FP64 pipe (2 FMA/clk/SM) is the bottleneck of every product here, so
-// the kernel is built to waste none of it: a block owns a 64 x 64 output block (clipped to the active
-// sizes, which may be read from the device), each of its 256 threads owns up to 16 outputs of that block
-// exactly (no padded tile rows or columns are computed), operands are staged through shared memory in
-// k-steps of 32, and long K is split across blocks until about two blocks per SM are busy (split-K: each
-// split writes its partial block to a workspace and a second kernel sums the splits in a fixed order,
-// so every product, and with it every solve, is bitwise reproducible whatever else runs on the GPU).  An output costs two shared-memory reads per FMA, far below the
-// shared-memory bandwidth at the FP64 rate.
+// the kernel is built to waste none of it: a block owns a 64 x 64 (small products: 32 x 32) output block
+// (clipped to the active sizes, which may be read from the device), each of its 256 threads owns up to 16
+// (4) outputs of that block exactly (no padded tile rows or columns are computed), operands are staged
+// through shared memory in k-steps of 32, and long K is split across blocks until about two blocks per SM are busy (split-K: each
+// split writes its partial block to a workspace; the last split of a tile to arrive, found by an arrival
+// counter, sums the partials in split order, so every product, and with it every solve, is bitwise
+// reproducible whatever else runs on the GPU, and no second launch is needed).  An output costs two
+// shared-memory reads per FMA, far below the shared-memory bandwidth at the FP64 rate.
 // ------------------------------------------------------------------------------------------------
-constexpr int GB = 64;  // output block edge
 constexpr int GK = 32;  // k-step
 
 // pk[j] = (row << 16) | column of output j within the block
-template <int NR>
-__device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[GB + 1], const double (*Bs)[GB + 1],
+template <int NR, int TILE>
+__device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[TILE + 1], const double (*Bs)[TILE + 1],
                                               const int* pk, int kk_end) {
   for (int kk = 0; kk < kk_end; ++kk) {
 #pragma unroll
@@ -33,17 +33,19 @@ __device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[GB
 
 // dynM / dynN (optional, per batch item): the product is computed only for rows < dynM[b] * mulM and
 // columns < dynN[b] * mulN (data-dependent active sizes, e.g. numerical ranks); the rest of C is not
-// written (a split-K product scales it by beta).  With splits > 1 the partial sums go to
-// part[((split * batches + item) * M + row) * N + column] (M, N the static sizes).
-template <bool TA, bool TB>
+// written.  With splits > 1 the partial sums go to part[((split * batches + item) * M + row) * N + column]
+// (M, N the static sizes).  TILE = 64 (16 outputs per thread) or 32 (4 per thread, for small products:
+// four times the blocks, so that a product of a few tiles still spreads over the SMs).
+template <bool TA, bool TB, int TILE>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                     int lda, long long sA, const double* __restrict__ B, int ldb,
                                                     long long sB, double beta, double* C, int ldc, long long sC,
                                                     int splits, int kchunk, const int* __restrict__ dynM, int mulM,
                                                     const int* __restrict__ dynN, int mulN, double* work,
-                                                    double* __restrict__ part) {
-  __shared__ double As[GK][GB + 1];
-  __shared__ double Bs[GK][GB + 1];
+                                                    double* __restrict__ part, unsigned int* __restrict__ cnt) {
+  constexpr int NMAX = TILE * TILE / 256;
+  __shared__ double As[GK][TILE + 1];
+  __shared__ double Bs[GK][TILE + 1];
   const int batch = blockIdx.z;
   const int bm = blockIdx.y / splits, split = blockIdx.y - (blockIdx.y / splits) * splits;
   const int bn = blockIdx.x;
@@ -55,17 +57,17 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   if (dynN) N = min(N, dynN[batch] * mulN);
   if (work && bm == 0 && bn == 0 && split == 0 && threadIdx.x == 0)
     add_work(work, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
-  const int m0 = bm * GB, n0 = bn * GB;
-  const int Mb = min(GB, M - m0), Nb = min(GB, N - n0);
+  const int m0 = bm * TILE, n0 = bn * TILE;
+  const int Mb = min(TILE, M - m0), Nb = min(TILE, N - n0);
   if (Mb <= 0 || Nb <= 0) return;
   const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
   // this thread's outputs o = t + 256 j < Mb Nb, as (row, column) within the block
   const int tot = Mb * Nb;
-  const int nact = tot > (int)threadIdx.x ? min(16, (tot - (int)threadIdx.x + 255) / 256) : 0;
-  int pk[16];
-  double acc[16];
+  const int nact = tot > (int)threadIdx.x ? min(NMAX, (tot - (int)threadIdx.x + 255) / 256) : 0;
+  int pk[NMAX];
+  double acc[NMAX];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NMAX; ++j) {
     const int o = threadIdx.x + 256 * j;
     const int m = o / Nb;
     pk[j] = j < nact ? (m << 16) | (o - m * Nb) : 0;
@@ -73,78 +75,113 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   }
   for (int k0 = kbeg; k0 < kend; k0 += GK) {
     const int kc = min(GK, kend - k0);
-    for (int e = threadIdx.x; e < GB * GK; e += 256) {
+    for (int e = threadIdx.x; e < TILE * GK; e += 256) {
       int mm, kk;
-      if (TA) { mm = e % GB; kk = e / GB; } else { kk = e % GK; mm = e / GK; }
+      if (TA) { mm = e % TILE; kk = e / TILE; } else { kk = e % GK; mm = e / GK; }
       double v = 0.0;
       if (mm < Mb && kk < kc) v = TA ? A[(size_t)(k0 + kk) * lda + m0 + mm] : A[(size_t)(m0 + mm) * lda + k0 + kk];
       As[kk][mm] = v;
     }
-    for (int e = threadIdx.x; e < GB * GK; e += 256) {
+    for (int e = threadIdx.x; e < TILE * GK; e += 256) {
       int nn, kk;
-      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % GB; kk = e / GB; }
+      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % TILE; kk = e / TILE; }
       double v = 0.0;
       if (nn < Nb && kk < kc) v = TB ? B[(size_t)(n0 + nn) * ldb + k0 + kk] : B[(size_t)(k0 + kk) * ldb + n0 + nn];
       Bs[kk][nn] = v;
     }
     __syncthreads();
-    switch (nact) {
-      case 16: gemm_fma_rows<16>(acc, As, Bs, pk, kc); break;
-      case 15: gemm_fma_rows<15>(acc, As, Bs, pk, kc); break;
-      case 14: gemm_fma_rows<14>(acc, As, Bs, pk, kc); break;
-      case 13: gemm_fma_rows<13>(acc, As, Bs, pk, kc); break;
-      case 12: gemm_fma_rows<12>(acc, As, Bs, pk, kc); break;
-      case 11: gemm_fma_rows<11>(acc, As, Bs, pk, kc); break;
-      case 10: gemm_fma_rows<10>(acc, As, Bs, pk, kc); break;
-      case 9: gemm_fma_rows<9>(acc, As, Bs, pk, kc); break;
-      case 8: gemm_fma_rows<8>(acc, As, Bs, pk, kc); break;
-      case 7: gemm_fma_rows<7>(acc, As, Bs, pk, kc); break;
-      case 6: gemm_fma_rows<6>(acc, As, Bs, pk, kc); break;
-      case 5: gemm_fma_rows<5>(acc, As, Bs, pk, kc); break;
-      case 4: gemm_fma_rows<4>(acc, As, Bs, pk, kc); break;
-      case 3: gemm_fma_rows<3>(acc, As, Bs, pk, kc); break;
-      case 2: gemm_fma_rows<2>(acc, As, Bs, pk, kc); break;
-      case 1: gemm_fma_rows<1>(acc, As, Bs, pk, kc); break;
-      default: break;
+    if constexpr (NMAX == 16) {
+      switch (nact) {
+        case 16: gemm_fma_rows<16, TILE>(acc, As, Bs, pk, kc); break;
+        case 15: gemm_fma_rows<15, TILE>(acc, As, Bs, pk, kc); break;
+        case 14: gemm_fma_rows<14, TILE>(acc, As, Bs, pk, kc); break;
+        case 13: gemm_fma_rows<13, TILE>(acc, As, Bs, pk, kc); break;
+        case 12: gemm_fma_rows<12, TILE>(acc, As, Bs, pk, kc); break;
+        case 11: gemm_fma_rows<11, TILE>(acc, As, Bs, pk, kc); break;
+        case 10: gemm_fma_rows<10, TILE>(acc, As, Bs, pk, kc); break;
+        case 9: gemm_fma_rows<9, TILE>(acc, As, Bs, pk, kc); break;
+        case 8: gemm_fma_rows<8, TILE>(acc, As, Bs, pk, kc); break;
+        case 7: gemm_fma_rows<7, TILE>(acc, As, Bs, pk, kc); break;
+        case 6: gemm_fma_rows<6, TILE>(acc, As, Bs, pk, kc); break;
+        case 5: gemm_fma_rows<5, TILE>(acc, As, Bs, pk, kc); break;
+        case 4: gemm_fma_rows<4, TILE>(acc, As, Bs, pk, kc); break;
+        case 3: gemm_fma_rows<3, TILE>(acc, As, Bs, pk, kc); break;
+        case 2: gemm_fma_rows<2, TILE>(acc, As, Bs, pk, kc); break;
+        case 1: gemm_fma_rows<1, TILE>(acc, As, Bs, pk, kc); break;
+        default: break;
+      }
+    } else {
+      switch (nact) {
+        case 4: gemm_fma_rows<4, TILE>(acc, As, Bs, pk, kc); break;
+        case 3: gemm_fma_rows<3, TILE>(acc, As, Bs, pk, kc); break;
+        case 2: gemm_fma_rows<2, TILE>(acc, As, Bs, pk, kc); break;
+        case 1: gemm_fma_rows<1, TILE>(acc, As, Bs, pk, kc); break;
+        default: break;
+      }
     }
     __syncthreads();
   }
   if (splits > 1) {
-    double* P = part + ((size_t)split * gridDim.z + batch) * (size_t)Ms * Ns;
+    const size_t pstride = (size_t)gridDim.z * Ms * Ns;  // between the splits of one output
+    double* P = part + (size_t)batch * Ms * Ns;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < NMAX; ++j) {
       if (j >= nact) break;
-      P[(size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff)] = acc[j];
+      P[split * pstride + (size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff)] = acc[j];
     }
+    // the last split of this tile to arrive sums all partials in split order
+    __shared__ unsigned int s_last;
+    __threadfence();
+    __syncthreads();
+    unsigned int* c = cnt + ((size_t)batch * gridDim.y / splits + bm) * gridDim.x + bn;
+    if (threadIdx.x == 0) {
+      const unsigned int prev = atomicAdd(c, 1u);
+      s_last = (prev == (unsigned int)splits - 1u) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j >= nact) break;
+      const size_t off = (size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff);
+      double v = 0.0;
+      for (int s = 0; s < splits; ++s) v += __ldcg(P + s * pstride + off);
+      double* cp = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
+      *cp = (beta == 0.0) ? alpha * v : alpha * v + beta * (*cp);
+    }
+    if (threadIdx.x == 0) *c = 0u;  // ready for the next product
     return;
   }
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NMAX; ++j) {
     if (j >= nact) break;
     double* c = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
     *c = (beta == 0.0) ? alpha * acc[j] : alpha * acc[j] + beta * (*c);
   }
 }
 
-// C = alpha * (sum of the split partials, in split order) + beta * C on the active rows and columns,
-// C = beta * C (0 for beta = 0) elsewhere
-__global__ void splitk_reduce_kernel(const double* __restrict__ part, int splits, int M, int N, double alpha,
-                                     double beta, double* C, int ldc, long long sC, int batch,
-                                     const int* __restrict__ dynM, int mulM, const int* __restrict__ dynN, int mulN) {
-  const long long mn = (long long)M * N, total = mn * batch;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / mn);
-    const long long rem = t - (long long)b * mn;
-    const int i = (int)(rem / N), j = (int)(rem - (long long)(rem / N) * N);
-    double* c = C + (size_t)b * sC + (size_t)i * ldc + j;
-    const bool act = (!dynM || i < dynM[b] * mulM) && (!dynN || j < dynN[b] * mulN);
-    double v = 0.0;
-    if (act) {
-      for (int s = 0; s < splits; ++s) v += part[((size_t)s * batch + b) * (size_t)mn + rem];
-      v *= alpha;
-    }
-    *c = (beta == 0.0) ? v : v + beta * (*c);
-  }
+template <int TILE>
+static void launch_dgemm(lrfg_ctx* ctx, int transA, int transB, dim3 grid, double flops, double bytes, int M, int N,
+                         int K, double alpha, const double* A, int lda, long long sA, const double* B, int ldb,
+                         long long sB, double beta, double* C, int ldc, long long sC, int splits, int kchunk,
+                         const int* dynM, int mulM, const int* dynN, int mulN, double* work, double* part) {
+  if (!transA && !transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
+        ctx->splitk_cnt));
+  else if (transA && !transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
+        ctx->splitk_cnt));
+  else if (!transA && transB)
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
+        ctx->splitk_cnt));
+  else
+    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true, TILE><<<grid, 256, 0, ctx->stream>>>(
+        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
+        ctx->splitk_cnt));
 }
 
 __global__ void scale_matrix_kernel(double* C, int M, int N, int ldc, long long sC, int batch, double beta) {
@@ -176,18 +213,27 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
     return;
   }
   LRFG_REQUIRE(batch < 65536, "gemm batch too large");
-  const int bmn = (M + GB - 1) / GB, bnn = (N + GB - 1) / GB;
+  const int nsm = ctx->num_sms > 0 ? ctx->num_sms : 152;
   // blocks expected to be active: the static count, or for data-dependent sizes a quarter of it (the
   // numerical ranks are typically well below their bounds), at least one per item
-  long long active = (long long)bmn * bnn * batch;
-  if (dynM || dynN) active = std::max<long long>(batch, active / 4);
-  const int target = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
+  auto active_tiles = [&](int tile) {
+    long long a = (long long)((M + tile - 1) / tile) * ((N + tile - 1) / tile) * batch;
+    if (dynM || dynN) a = std::max<long long>(batch, a / 4);
+    return a;
+  };
+  // 32 x 32 tiles when 64 x 64 ones would leave most SMs idle
+  const int tile = active_tiles(64) < nsm ? 32 : 64;
+  const int bmn = (M + tile - 1) / tile, bnn = (N + tile - 1) / tile;
+  const long long active = active_tiles(tile);
+  const int target = 2 * nsm;
   int splits = 1;
   if (active < target) splits = (int)std::min<long long>((target + active - 1) / active, std::max(1, K / GK));
   int kchunk = (K + splits - 1) / splits;
   kchunk = ((kchunk + GK - 1) / GK) * GK;
   splits = (K + kchunk - 1) / kchunk;
   LRFG_REQUIRE((long long)bmn * splits < 65536, "gemm too many row blocks x splits");
+  if (splits > 1)
+    LRFG_REQUIRE((long long)bmn * bnn * batch <= kSplitKCounters, "split-K product with too many output tiles");
   DBuf<double> part;
   if (splits > 1) part = DBuf<double>(ctx->pool, (size_t)splits * M * N * batch);
   // products with data-dependent sizes count their work on the device
@@ -195,25 +241,12 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
   const double flops = work ? 0.0 : 2.0 * M * N * (double)K * batch;
   const double bytes = work ? 0.0 : sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
   dim3 grid(bnn, bmn * splits, batch);
-  if (!transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
-  else if (transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
-  else if (!transA && transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
+  if (tile == 32)
+    launch_dgemm<32>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
   else
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true><<<grid, 256, 0, ctx->stream>>>(
-        M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get()));
-  if (splits > 1) {
-    const long long n = (long long)M * N * batch;
-    LRFG_LAUNCH(ctx, KC_GEMM, (double)splits * n, sizeof(double) * (double)(splits + 2) * n,
-                splitk_reduce_kernel<<<(unsigned)std::min(4LL * (ctx->num_sms > 0 ? ctx->num_sms : 152), (n + 255) / 256),
-                                       256, 0, ctx->stream>>>(part.get(), splits, M, N, alpha, beta, C, ldc, sC, batch,
-                                                              dynM, mulM, dynN, mulN));
-  }
+    launch_dgemm<64>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
 }
 
 // ------------------------------------------------------------------------------------------------

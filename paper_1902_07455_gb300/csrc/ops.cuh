@@ -166,12 +166,13 @@ void tk_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int r
 void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
                 TK& out, double tol = 0.0);
 void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
-              const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0);
+              const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0, const double* B = nullptr);
 void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
             const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0);
-double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u);
+// B: the constant anisotropic part (3 x 3 row-major storage) or null
+double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u, const double* B = nullptr);
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u, double rtol = 0.0);
+                       TK& best_u, double rtol = 0.0, const double* B = nullptr);
 
 }  // namespace lrfg

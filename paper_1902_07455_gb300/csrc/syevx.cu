@@ -46,7 +46,8 @@ __device__ double block_reduce_sum(double v, double* red, int nact) {
 // p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1} (Barth, Martin & Wilkinson, Numer. Math.
 // 9 (1967) 386-393), a zero term taking the sign opposite to its predecessor.  Division-free (FP64
 // division is a long dependent chain on this part); the pair (p_{i-1}, p_i) is rescaled by exact powers of
-// two to stay in range.
+// two every four steps to stay in range.  The caller scales T by a power of two to |T| < 1, so that four
+// steps change |p| by at most a factor 3^4 (growth) or 2^-212 (cancellation) within the 2^(+-600) window.
 __device__ __forceinline__ int sign_of(double p, int sprev) {
   // sign from the bit pattern (integer pipe): +1, -1, or opposite of the predecessor for a zero
   const long long bits = __double_as_longlong(p);
@@ -61,17 +62,20 @@ __device__ int sturm_count(const double* d, const double* e2, int n, double x) {
   int s = sign_of(p, sprev);
   c += s != sprev;
   sprev = s;
-  for (int i = 1; i < n; ++i) {
-    double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
-    pm = p;
-    p = pn;
-    // biased exponents of |p| and |pm| (integer pipe) for the range checks against 2^(+-600)
+  int i = 1;
+  while (i < n) {
+    const int iend = min(n, i + 4);
+    for (; i < iend; ++i) {
+      double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
+      pm = p;
+      p = pn;
+      s = sign_of(p, sprev);
+      c += s != sprev;
+      sprev = s;
+    }
     const int ep = (int)((__double_as_longlong(p) >> 52) & 0x7ff), epm = (int)((__double_as_longlong(pm) >> 52) & 0x7ff);
-    if (ep > 1023 + 600) { p *= down; pm *= down; }
+    if (ep > 1023 + 600 || epm > 1023 + 600) { p *= down; pm *= down; }
     else if (ep < 1023 - 600 && epm < 1023 - 600) { p *= up; pm *= up; }
-    s = sign_of(p, sprev);
-    c += s != sprev;
-    sprev = s;
   }
   return c;
 }
@@ -364,6 +368,17 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
     }
   }
   __syncthreads();
+  // scaled copy of the tridiagonal (exact power of two, |T| in [0.5, 1)) for the FP64 counts: the four
+  // steps between range checks cannot leave the 2^(+-600) window
+  int texp = 0;
+  frexp(tnorm, &texp);
+  const double sg = ldexp(1.0, -texp), sg2 = sg * sg;
+  double* ds = (double*)df;  // the FP32 copies are no longer needed
+  for (int i = tid; i < n; i += nthr) {
+    ds[i] = d[i] * sg;
+    e2[i] *= sg2;
+  }
+  __syncthreads();
   // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 4-way multisection by
   // groups of four lanes (eight eigenvalues per warp) until the bracket is at the FP64 resolution.  A
   // warp-wide FP64 instruction occupies the SM's FP64 pipe for 16 cycles whatever the lane count, so the
@@ -379,17 +394,20 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
       const int t = t0 + grp;
       const int tt = t < k ? t : t0;
       const int idx = n - 1 - tt;
-      double a = bra[tt], c = brc[tt];
-      int ca = (sub == 0) ? sturm_count(d, e2, n, a) : 0;
-      int cc = (sub == 1) ? sturm_count(d, e2, n, c) : 0;
+      double a = bra[tt] * sg, c = brc[tt] * sg;
+      int ca = (sub == 0) ? sturm_count(ds, e2, n, a) : 0;
+      int cc = (sub == 1) ? sturm_count(ds, e2, n, c) : 0;
       ca = __shfl_sync(gmask, ca, (lane & ~3) | 0);
       cc = __shfl_sync(gmask, cc, (lane & ~3) | 1);
-      if (!(ca <= idx && cc > idx)) { a = glo; c = ghi; }
+      if (!(ca <= idx && cc > idx)) { a = glo * sg; c = ghi * sg; }
+      // absolute resolution eps ||T||: the eigenvalues of an FP64 Gram core carry errors of that size,
+      // and inverse iteration only needs the shift to that accuracy
+      const double floor_s = (DBL_EPSILON * tnorm + 4.0 * pivmin) * sg;
       for (int it = 0; it < 80; ++it) {
-        if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + 1e-3 * DBL_EPSILON * tnorm + 4.0 * pivmin) break;
+        if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + floor_s) break;
         const double h = (c - a) * 0.2;
         const double x = a + h * (double)(sub + 1);  // 4 interior points
-        const int cnt = sturm_count(d, e2, n, x);
+        const int cnt = sturm_count(ds, e2, n, x);
         const unsigned above = (__ballot_sync(gmask, cnt > idx) >> (lane & ~3)) & 0xfu;
         // the first point whose count exceeds idx bounds the eigenvalue from above
         const int f = above ? (__ffs(above) - 1) : 4;
@@ -398,7 +416,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
         a = na;
         c = nc;
       }
-      if (sub == 0 && t < k) lam[t] = 0.5 * (a + c);
+      if (sub == 0 && t < k) lam[t] = 0.5 * (a + c) / sg;
     }
   }
   __syncthreads();

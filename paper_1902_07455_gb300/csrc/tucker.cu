@@ -413,13 +413,30 @@ void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, co
 // (Eq. (Pls_lowrank), Sec. 3.3) -- the same steps as the TT path
 // ------------------------------------------------------------------------------------------------
 void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
-              const std::vector<double>& pw, int rank, TK& out, double rtol) {
+              const std::vector<double>& pw, int rank, TK& out, double rtol, const double* B) {
   const int d = v.d;
-  TK w[3];
+  TK w[3], es[3];
+  for (int alpha = 0; alpha < d; ++alpha)
+    tk_mode_operator(ctx, v, alpha, LRFG_MUL_DERIV, 0.0, 1.0, es[alpha]);         // gradient, mode alpha
   for (int alpha = 0; alpha < d; ++alpha) {
-    TK e, ae, wr;
-    tk_mode_operator(ctx, v, alpha, LRFG_MUL_DERIV, 0.0, 1.0, e);                  // gradient, mode alpha
-    tk_hadamard(ctx, a, tk_view(e), ae);                                          // A~ e_alpha
+    TK ae, wr;
+    tk_hadamard(ctx, a, tk_view(es[alpha]), ae);                                  // a (.) e_alpha
+    if (B) {
+      // constant anisotropic part: + sum_beta B[alpha][beta] e_beta (zero entries skipped)
+      TKView xs[4];
+      double sc[4];
+      int m = 0;
+      xs[m] = tk_view(ae);
+      sc[m++] = 1.0;
+      for (int beta = 0; beta < d; ++beta)
+        if (B[alpha * 3 + beta] != 0.0) {
+          xs[m] = tk_view(es[beta]);
+          sc[m++] = B[alpha * 3 + beta];
+        }
+      TK sum;
+      tk_add_many(ctx, xs, sc, m, sum);
+      ae = std::move(sum);
+    }
     tk_round(ctx, tk_view(ae), rank, wr, rtol);                                   // T
     tk_mode_operator(ctx, tk_view(wr), alpha, LRFG_MUL_DERIV, 0.0, -1.0, w[alpha]);  // divergence
   }
@@ -462,7 +479,7 @@ static void tk_ones(lrfg_ctx* ctx, int d, const int* N, TK& x) {
   for (int j = 0; j < d; ++j) fill(ctx, x.fac[j].get(), 1.0, N[j]);
 }
 
-double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u) {
+double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u, const double* B) {
   const int d = a.d;
   double size = 1.0;
   for (int j = 0; j < d; ++j) size *= a.N[j];
@@ -471,12 +488,22 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u)
   double EE = 0.0;
   for (int j = 0; j < d; ++j) EE += E[j] * E[j];
   double val = EE * tk_dot(ctx, a, tk_view(ones)) / size;
+  TK e[3];
   for (int alpha = 0; alpha < d; ++alpha) {
-    TK e, ae;
-    tk_mode_operator(ctx, u, alpha, LRFG_MUL_DERIV, 0.0, 1.0, e);
-    tk_hadamard(ctx, a, tk_view(e), ae);
+    TK ae;
+    tk_mode_operator(ctx, u, alpha, LRFG_MUL_DERIV, 0.0, 1.0, e[alpha]);
+    tk_hadamard(ctx, a, tk_view(e[alpha]), ae);
     if (E[alpha] != 0.0) val += 2.0 * E[alpha] * tk_dot(ctx, tk_view(ae), tk_view(ones)) / size;
-    val += tk_dot(ctx, tk_view(ae), tk_view(e)) / size;
+    val += tk_dot(ctx, tk_view(ae), tk_view(e[alpha])) / size;
+  }
+  if (B) {
+    // (E + e).B(E + e) averaged: E.B E + sum_ab B_ab <e_a, e_b> / |N| (e has zero mean)
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        const double bij = B[i * 3 + j];
+        if (bij == 0.0) continue;
+        val += E[i] * bij * E[j] + bij * tk_dot(ctx, tk_view(e[i]), tk_view(e[j])) / size;
+      }
   }
   return val;
 }
@@ -485,7 +512,7 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u)
 // when ||r|| fails to decrease (stop_on_increase), at tol or maxit; the iterate of smallest residual is kept
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u, double rtol) {
+                       TK& best_u, double rtol, const double* B) {
   TKSolveResult res{};
   TK b;
   tk_rhs(ctx, a, E, pt, pw, rank, b, rtol);
@@ -509,7 +536,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     }
     if (nr <= tol || it >= maxit) break;
     TK q;
-    tk_apply(ctx, a, tk_view(r), pt, pw, rank, q, rtol);
+    tk_apply(ctx, a, tk_view(r), pt, pw, rank, q, rtol, B);
     ++applies;
     const double qq = tk_dot(ctx, tk_view(q), tk_view(q));
     if (qq == 0.0) break;
@@ -531,7 +558,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     have_u = true;
     ++it;
     TK cu, diff, rn;
-    tk_apply(ctx, a, tk_view(u), pt, pw, rank, cu, rtol);
+    tk_apply(ctx, a, tk_view(u), pt, pw, rank, cu, rtol, B);
     ++applies;
     TKView xs[2] = {tk_view(b), tk_view(cu)};
     const double sc[2] = {1.0, -1.0};
@@ -549,7 +576,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
   res.iters = best_it;
   res.rel_resid = nb > 0.0 ? best : 0.0;
   res.applies = applies;
-  res.Aeff = tk_aeff(ctx, a, E, tk_view(best_u));
+  res.Aeff = tk_aeff(ctx, a, E, tk_view(best_u), B);
   return res;
 }
 

@@ -113,7 +113,31 @@ def test_b_validation(ctx):
     with pytest.raises(lrfg.LrfgError) as e:
         ctx.problem(a, lrfg.FULL, B=np.array([[1.0, 2.0], [2.0, 1.0]]))  # eigenvalue -1
     assert e.value.status == 1 and "semidefinite" in str(e.value)
-    _, terms, w = smoothed_cube(2, 15, contrast=10.0)
-    with pytest.raises(lrfg.LrfgError) as e:
-        ctx.problem(lrfg.TuckerTensor.from_numpy(*lr.tucker_from_separable(terms, w)), lrfg.TUCKER, rank=4, B=B2)
-    assert e.value.status == 6
+
+
+@pytest.mark.parametrize("fmt,d,N,rank", [("tucker", 2, 31, 6), ("tucker", 3, 15, 4), ("cp", 2, 31, 6)])
+def test_tucker_cp_aniso(ctx, fmt, d, N, rank):
+    """Tucker and CP (d = 2, the Tucker path) with the anisotropic part: one application and a solve
+    against the oracle's anisotropic operator in that format."""
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    B = B2 if d == 2 else B3
+    shape = (N,) * d
+    a_tk = lr.tucker_from_separable(terms, w)
+    okfmt = "tucker" if fmt == "tucker" else "cp"
+    a_or = lr.FORMATS[okfmt].sep(terms, w)
+    op = lr.LowRankGaNi(a_or, shape, fmt=okfmt, rank=rank, pinv_eps=0.1, B=B)
+    E = np.ones(d)
+    ref = lr.minres(op, E, tol=1e-10, maxit=40)
+    P = ctx.problem(lrfg.TuckerTensor.from_numpy(*a_tk), lrfg.TUCKER if fmt == "tucker" else lrfg.CP, rank=rank,
+                    tol=1e-10, maxit=40, B=B)
+    res, u = P.solve(E)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    assert abs(P.aeff(E, u) - res.Aeff) <= 1e-12 * res.Aeff
+    if fmt == "tucker":
+        rng = np.random.default_rng(4)
+        core = rng.standard_normal((3,) * d)
+        facs = [rng.standard_normal((N, 3)) / np.sqrt(N) for _ in range(d)]
+        x = (core, facs)
+        refx = np.real(lr.tucker_full(*lr.tucker_idft(op.apply(lr.tucker_dft(x)))))
+        out = P.apply(ctx.field_from_tucker(lrfg.TuckerTensor.from_numpy(core, facs))).full()
+        assert rel(out, refx) <= 1e-7
