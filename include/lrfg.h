@@ -123,7 +123,7 @@ typedef struct {
                            tol / sqrt(d-1) per TT bond (App. A.3.3), tol / sqrt(d) per Tucker mode (App.
                            A.2.3); a grid coefficient is TT-compressed with the same tolerance */
   int coeff_rank;       /* LRFG_TT with grid values: rank cap r_A of the coefficient's TT-SVD (0: `rank`) */
-  int rank_start;       /* LRFG_TT: 0 = fixed rank.  > 0: rank-adapting MinRes (the solver Sec. 4.3
+  int rank_start;       /* low-rank formats: 0 = fixed rank.  > 0: rank-adapting MinRes (the solver Sec. 4.3
                            proposes): truncations start at rank_start; when the residual fails to decrease
                            below the cap `rank`, the rank rises by rank_step, the right-hand side is
                            rebuilt and the iteration restarts from the best iterate; at the cap a failure

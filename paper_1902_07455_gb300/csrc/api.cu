@@ -706,7 +706,8 @@ int coeff_rank(const lrfg_opts& o) { return o.coeff_rank > 0 ? o.coeff_rank : o.
 void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
   TK best;
   const TKSolveResult r = tk_solve(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, P->opts.tol,
-                                   P->opts.maxit, P->opts.stop_on_increase, best, P->opts.rank_tol, aniso_b(P));
+                                   P->opts.maxit, P->opts.stop_on_increase, best, P->opts.rank_tol, aniso_b(P),
+                                   P->opts.rank_start, P->opts.rank_step);
   res->iters = r.iters;
   res->rel_resid = r.rel_resid;
   res->converged = r.rel_resid <= P->opts.tol ? 1 : 0;
@@ -1120,8 +1121,6 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->rank_tol >= 0.0 && opts->rank_tol < 1.0, "rank_tol must be in [0, 1) (got %g)", opts->rank_tol);
     LRFG_REQUIRE(opts->coeff_rank >= 0, "coeff_rank must be >= 0 (got %d)", opts->coeff_rank);
     LRFG_REQUIRE(opts->rank_start >= 0 && opts->rank_step >= 0, "rank_start and rank_step must be >= 0");
-    if (opts->rank_start > 0 && opts->fmt != LRFG_TT)
-      fail(LRFG_ENOTSUP, "rank adaptation (rank_start > 0) is implemented for LRFG_TT solutions");
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
                  "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();

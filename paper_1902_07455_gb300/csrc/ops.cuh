@@ -173,6 +173,7 @@ void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<d
 double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u, const double* B = nullptr);
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u, double rtol = 0.0, const double* B = nullptr);
+                       TK& best_u, double rtol = 0.0, const double* B = nullptr, int rank_start = 0,
+                       int rank_step = 1);
 
 }  // namespace lrfg

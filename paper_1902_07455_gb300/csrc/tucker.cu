@@ -509,66 +509,89 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u,
 }
 
 // u_{i+1} = T(u_i + omega_i r_i), r_i = T(b - C u_i) (r_0 = b), omega_i = (C r_i, r_i) / ||C r_i||^2; stop
-// when ||r|| fails to decrease (stop_on_increase), at tol or maxit; the iterate of smallest residual is kept
+// when ||r|| fails to decrease (stop_on_increase), at tol or maxit; the iterate of smallest residual is kept.
+// Rank adaptation (rank_start > 0, the solver Sec. 4.3 proposes): truncations start at rank_start; when the
+// residual fails to decrease below the cap `rank`, the rank rises by rank_step, the right-hand side is
+// rebuilt and the iteration restarts from the best iterate with its residual recomputed at the new rank.
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u, double rtol, const double* B) {
+                       TK& best_u, double rtol, const double* B, int rank_start, int rank_step) {
   TKSolveResult res{};
+  const bool adapt = rank_start > 0;
+  int rc = adapt ? std::min(rank_start, rank) : rank;
   TK b;
-  tk_rhs(ctx, a, E, pt, pw, rank, b, rtol);
-  const double nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
+  tk_rhs(ctx, a, E, pt, pw, rc, b, rtol);
+  double nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
   TK u, r;
-  bool have_u = false, have_best = false;
+  bool u_zero = true, best_zero = true;
   double best = INFINITY;
   int best_it = 0, it = 0, applies = 0;
   tk_copy(ctx, tk_view(b), r);
+  auto residual = [&]() {  // r <- T(b - C u) at the current rank
+    TK cu, diff, rn;
+    tk_apply(ctx, a, tk_view(u), pt, pw, rc, cu, rtol, B);
+    ++applies;
+    TKView xs[2] = {tk_view(b), tk_view(cu)};
+    const double sc[2] = {1.0, -1.0};
+    tk_add_many(ctx, xs, sc, 2, diff);
+    tk_round(ctx, tk_view(diff), rc, rn, rtol);
+    r = std::move(rn);
+  };
   while (nb > 0.0) {
-    const double nr = (it == 0) ? 1.0 : std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
+    double nr = std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
+    if (it == 0 && u_zero) nr = 1.0;  // r = b
     if (nr < best) {
       best = nr;
       best_it = it;
-      if (have_u) {
-        tk_copy(ctx, tk_view(u), best_u);
-        have_best = true;
+      best_zero = u_zero;
+      if (!u_zero) tk_copy(ctx, tk_view(u), best_u);
+    } else if (adapt && rc < rank) {
+      rc = std::min(rank, rc + std::max(1, rank_step));
+      TK nbv;
+      tk_rhs(ctx, a, E, pt, pw, rc, nbv, rtol);
+      b = std::move(nbv);
+      nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
+      u_zero = best_zero;
+      if (u_zero) {
+        tk_copy(ctx, tk_view(b), r);
+      } else {
+        tk_copy(ctx, tk_view(best_u), u);
+        residual();
       }
-    } else if (stop_on_increase) {
+      nr = u_zero ? 1.0 : std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
+      best = nr;
+    } else if (stop_on_increase || adapt) {
       break;
     }
     if (nr <= tol || it >= maxit) break;
     TK q;
-    tk_apply(ctx, a, tk_view(r), pt, pw, rank, q, rtol, B);
+    tk_apply(ctx, a, tk_view(r), pt, pw, rc, q, rtol, B);
     ++applies;
     const double qq = tk_dot(ctx, tk_view(q), tk_view(q));
     if (qq == 0.0) break;
     const double omega = tk_dot(ctx, tk_view(q), tk_view(r)) / qq;
     TK un;
-    if (!have_u) {
+    if (u_zero) {
       TK scaled;
       tk_copy(ctx, tk_view(r), scaled);
       axpby(ctx, (long long)core_size(r.d, r.r), omega, r.core.get(), 0.0, scaled.core.get());
-      tk_round(ctx, tk_view(scaled), rank, un, rtol);
+      tk_round(ctx, tk_view(scaled), rc, un, rtol);
     } else {
       TKView xs[2] = {tk_view(u), tk_view(r)};
       const double sc[2] = {1.0, omega};
       TK s;
       tk_add_many(ctx, xs, sc, 2, s);
-      tk_round(ctx, tk_view(s), rank, un, rtol);
+      tk_round(ctx, tk_view(s), rc, un, rtol);
     }
     u = std::move(un);
-    have_u = true;
+    u_zero = false;
     ++it;
-    TK cu, diff, rn;
-    tk_apply(ctx, a, tk_view(u), pt, pw, rank, cu, rtol, B);
-    ++applies;
-    TKView xs[2] = {tk_view(b), tk_view(cu)};
-    const double sc[2] = {1.0, -1.0};
-    tk_add_many(ctx, xs, sc, 2, diff);
-    tk_round(ctx, tk_view(diff), rank, rn, rtol);
-    r = std::move(rn);
+    residual();
   }
-  if (!have_best) {
+  if (best_zero || !best_u.d) {
     // the best iterate is u_0 = 0
     int rr[3] = {1, 1, 1};
+    best_u = TK();
     tk_alloc(ctx, best_u, a.d, a.N, rr);
     fill(ctx, best_u.core.get(), 0.0, 1);
     for (int j = 0; j < a.d; ++j) fill(ctx, best_u.fac[j].get(), 0.0, a.N[j]);

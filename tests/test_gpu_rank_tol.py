@@ -111,9 +111,18 @@ def test_rank_adaptive_solve_matches_oracle(ctx, d, N, cap, start, step):
     P.free()
 
 
-def test_rank_adaptive_only_tt(ctx):
-    _, terms, w = smoothed_cube(2, 15, contrast=10.0, full=False)
-    with pytest.raises(lrfg.LrfgError) as e:
-        ctx.problem(lrfg.TuckerTensor.from_numpy(*lr.tucker_from_separable(terms, w)), lrfg.TUCKER, rank=5,
-                    rank_start=2)
-    assert e.value.status == 6  # LRFG_ENOTSUP
+@pytest.mark.parametrize("fmt,d,N,cap,start,step", [("tucker", 2, 31, 8, 2, 2), ("tucker", 3, 15, 6, 2, 2),
+                                                    ("cp", 2, 31, 8, 2, 3)])
+def test_rank_adaptive_tucker_cp_matches_oracle(ctx, fmt, d, N, cap, start, step):
+    _, terms, w = smoothed_cube(d, N, contrast=10.0, full=False)
+    E = np.eye(d)[0]
+    op = lr.LowRankGaNi(lr.FORMATS[fmt].sep(terms, w), (N,) * d, fmt=fmt, rank=cap, pinv_eps=0.1)
+    ref = lr.minres_rank_adaptive(op, E, rank_start=start, rank_step=step, tol=1e-12, maxit=40)
+    P = ctx.problem(lrfg.TuckerTensor.from_numpy(*lr.tucker_from_separable(terms, w)),
+                    lrfg.TUCKER if fmt == "tucker" else lrfg.CP, rank=cap, tol=1e-12, maxit=40, rank_start=start,
+                    rank_step=step)
+    res, _ = P.solve(E, want_field=False)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    # near stagnation at the cap the residual changes by parts in 1e6 per step, so "fails to decrease" may
+    # fire a few steps apart on the two sides (Gram-SVD vs QR+SVD rounding); the residual reached agrees
+    assert 0.5 <= res.rel_resid / ref["rel_resid"] <= 2.0, (res.rel_resid, ref["rel_resid"], res.iters, ref["iters"])
