@@ -65,6 +65,9 @@ typedef enum {
 
 typedef enum { LRFG_FULL = 0, LRFG_CP = 1, LRFG_TUCKER = 2, LRFG_TT = 3 } lrfg_format;
 typedef enum { LRFG_FP64 = 0, LRFG_MIXED = 1 } lrfg_prec;
+/* discretisation: numerical integration on the grid (GaNi, Sec. 2.2.2) or exact integration on the
+ * double grid 2N - 1 (Ga, Sec. 2.2.3) */
+typedef enum { LRFG_GANI = 0, LRFG_GA = 1 } lrfg_disc;
 
 /* spectral multipliers m(k) applied along one mode by F^{-1} diag(m) F (Sec. 2.2.1, Sec. 3.2) */
 typedef enum {
@@ -129,6 +132,12 @@ typedef struct {
                            rebuilt and the iteration restarts from the best iterate; at the cap a failure
                            to decrease ends it */
   int rank_step;        /* rank increment of the rank-adapting MinRes (0 selects 1) */
+  lrfg_disc disc;       /* LRFG_GANI (default), or LRFG_GA with LRFG_FULL / LRFG_FP64: the grid values of a
+                           are read as a pixel-wise constant material (a_p on the cell of side 1/N centred at
+                           x_p), its integrals against the double-grid basis are computed exactly (DoGIP), and
+                           A_eff is the exact integral of a |E + grad u|^2.  N_j and the double grid 2N_j - 1
+                           must have prime factors <= 31 (LRFG_ENOTSUP otherwise; e.g. N = 13, 25, 63, 81,
+                           189, 363) */
 } lrfg_opts;
 
 typedef struct {

@@ -24,11 +24,12 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "Batch", "BatchResult", "LrfgError", "FULL", "TT", "TUCKER", "CP", "FP64", "MIXED", "MUL_IDENTITY", "MUL_DERIV",
+__all__ = ["Context", "TTensor", "TuckerTensor", "Problem", "Field", "Batch", "BatchResult", "LrfgError", "FULL", "TT", "TUCKER", "CP", "FP64", "MIXED", "GANI", "GA", "MUL_IDENTITY", "MUL_DERIV",
            "MUL_GAUSS", "library_path"]
 
 FULL, CP, TUCKER, TT = L.LRFG_FULL, L.LRFG_CP, L.LRFG_TUCKER, L.LRFG_TT
 FP64, MIXED = L.LRFG_FP64, L.LRFG_MIXED
+GANI, GA = L.LRFG_GANI, L.LRFG_GA
 MUL_IDENTITY, MUL_DERIV, MUL_GAUSS = L.LRFG_MUL_IDENTITY, L.LRFG_MUL_DERIV, L.LRFG_MUL_GAUSS
 
 
@@ -350,14 +351,16 @@ class Context:
     # ---- problems and fields ---------------------------------------------------------------------
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
-                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None) -> "Problem":
+                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
+                disc: int = L.LRFG_GANI) -> "Problem":
         """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only).
         ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
         rank cap of a grid coefficient's TT compression (0: ``rank``).  ``rank_start`` > 0: rank-adapting
         MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT).  ``B``: constant symmetric
-        positive semidefinite d x d anisotropic part, A~ = a I + B (FULL and TT)."""
+        positive semidefinite d x d anisotropic part, A~ = a I + B.  ``disc``: GANI, or GA (exact integration
+        of the pixel-wise constant material on the double grid; FULL, FP64)."""
         return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank,
-                       rank_start, rank_step, B)
+                       rank_start, rank_step, B, disc)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -448,7 +451,7 @@ class Problem:
     (isotropic a(x) samples) or a TTensor of the coefficient."""
 
     def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64,
-                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1, B=None):
+                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1, B=None, disc=L.LRFG_GANI):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -492,7 +495,7 @@ class Problem:
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
-        o.rank_start, o.rank_step = int(rank_start), int(rank_step)
+        o.rank_start, o.rank_step, o.disc = int(rank_start), int(rank_step), int(disc)
         h = C.c_void_p()
         ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))
         del keep
@@ -624,14 +627,15 @@ class Batch:
 
     def submit(self, coeff, E, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8,
                maxit: int = 200, stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
-               coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None) -> int:
+               coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
+               disc: int = L.LRFG_GANI) -> int:
         c, keep = _host_coeff(coeff)
         _set_b(c, B)
         o = L.lrfg_opts()
         o.fmt, o.prec, o.rank, o.pinv_eps = int(fmt), int(prec), int(rank), float(pinv_eps)
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
-        o.rank_start, o.rank_step = int(rank_start), int(rank_step)
+        o.rank_start, o.rank_step, o.disc = int(rank_start), int(rank_step), int(disc)
         t = C.c_ulonglong()
         st = self.lib.lrfg_batch_submit(self.h, C.byref(c), _dvec(E), C.byref(o), C.byref(t))
         del keep

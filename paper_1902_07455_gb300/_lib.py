@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(_HERE, "liblrfg.so")
 LRFG_OK, LRFG_EINVAL, LRFG_ENOMEM, LRFG_ENOCONV, LRFG_ECUDA, LRFG_ETIMEOUT, LRFG_ENOTSUP = range(7)
 LRFG_FULL, LRFG_CP, LRFG_TUCKER, LRFG_TT = 0, 1, 2, 3
 LRFG_FP64, LRFG_MIXED = 0, 1
+LRFG_GANI, LRFG_GA = 0, 1
 LRFG_MUL_IDENTITY, LRFG_MUL_DERIV, LRFG_MUL_GAUSS = 0, 1, 2
 
 STATUS_NAMES = {0: "LRFG_OK", 1: "LRFG_EINVAL", 2: "LRFG_ENOMEM", 3: "LRFG_ENOCONV", 4: "LRFG_ECUDA",
@@ -33,7 +34,7 @@ class lrfg_coeff(C.Structure):
 class lrfg_opts(C.Structure):
     _fields_ = [("fmt", C.c_int), ("prec", C.c_int), ("rank", C.c_int), ("pinv_eps", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("stop_on_increase", C.c_int), ("rank_tol", C.c_double),
-                ("coeff_rank", C.c_int), ("rank_start", C.c_int), ("rank_step", C.c_int)]
+                ("coeff_rank", C.c_int), ("rank_start", C.c_int), ("rank_step", C.c_int), ("disc", C.c_int)]
 
 
 class lrfg_result(C.Structure):

@@ -200,6 +200,11 @@ struct lrfg_problem {
   // constant anisotropic part B (d x d row-major, 3 x 3 storage) of A~ = a I + B; aniso = B != 0
   double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   bool aniso = false;
+  // Ga (exact integration, FULL / FP64): the double grid M = 2N - 1, (|N| / |M|) A~ on it, workspaces
+  bool ga = false;
+  FullGrid gM{};
+  DBuf<double> a_ga, wrM;
+  DBuf<double2> wcM;
 };
 
 namespace {
@@ -539,8 +544,33 @@ template <> struct FullWork<float> {
   }
 };
 
+// Ga operator (FP64): per component, the gradient zero-padded to the double grid, multiplied there by the
+// modified coefficient, transformed back and projected on the frequencies of the grid, then grad^*
+void full_apply_ga(lrfg_problem* P, const double2* v, double2* out, int precond) {
+  lrfg_ctx* ctx = P->ctx;
+  const FullGrid& g = P->g;
+  const FullGrid& gM = P->gM;
+  const double inv = 1.0 / (double)g.n_real;
+  for (int alpha = 0; alpha < g.d; ++alpha) {
+    half_mul_grad(ctx, g, v, P->wc.get(), alpha, inv);                           // grad^ (1/|N| of Phi^-1)
+    half_inject(ctx, g, gM, P->wc.get(), P->wcM.get());                          // I
+    full_inverse<double>(ctx, gM, P->wcM.get(), P->a_ga.get(), 1.0, P->wrM.get());  // A~ F_M^-1
+    full_forward<double>(ctx, gM, P->wrM.get(), nullptr, 1.0, P->wcM.get());     // F_M
+    half_project(ctx, g, gM, P->wcM.get(), P->wc.get());                         // I*
+    half_acc_div(ctx, g, (const double2*)P->wc.get(), out, alpha, 1.0, alpha == 0,
+                 precond && alpha == g.d - 1 && !P->aniso);                       // grad^*
+  }
+  if (P->aniso) half_acc_aniso(ctx, g, v, out, P->B, precond);
+}
+
 template <typename R>
 void full_apply(lrfg_problem* P, const typename CplxOf<R>::T* v, typename CplxOf<R>::T* out, int precond) {
+  if constexpr (std::is_same<R, double>::value) {
+    if (P->ga) {
+      full_apply_ga(P, v, out, precond);
+      return;
+    }
+  }
   lrfg_ctx* ctx = P->ctx;
   const FullGrid& g = P->g;
   FullWork<R> w(P);
@@ -560,6 +590,16 @@ template <typename R>
 void full_rhs(lrfg_problem* P, const double* E, typename CplxOf<R>::T* b, int precond) {
   lrfg_ctx* ctx = P->ctx;
   const FullGrid& g = P->g;
+  if constexpr (std::is_same<R, double>::value) {
+    if (P->ga) {  // - grad^* I* F_M A~ E
+      full_forward<double>(ctx, P->gM, P->a_ga.get(), nullptr, 1.0, P->wcM.get());
+      half_project(ctx, g, P->gM, P->wcM.get(), P->wc.get());
+      for (int alpha = 0; alpha < g.d; ++alpha)
+        half_acc_div(ctx, g, (const double2*)P->wc.get(), b, alpha, -E[alpha], alpha == 0,
+                     precond && alpha == g.d - 1);
+      return;
+    }
+  }
   FullWork<R> w(P);
   full_forward<R>(ctx, g, w.a, nullptr, R(1), w.wc);
   for (int alpha = 0; alpha < g.d; ++alpha)
@@ -571,6 +611,25 @@ double full_aeff(lrfg_problem* P, const double* E, const double2* v) {
   lrfg_ctx* ctx = P->ctx;
   const FullGrid& g = P->g;
   DBuf<double> acc(ctx->pool, 1);
+  if (P->ga) {
+    // exact integration: sum over the double grid of A~ |E + e|^2, e the gradient there
+    for (int alpha = 0; alpha < g.d; ++alpha) {
+      half_mul_grad(ctx, g, v, P->wc.get(), alpha, 1.0 / (double)g.n_real);
+      half_inject(ctx, g, P->gM, P->wc.get(), P->wcM.get());
+      full_inverse<double>(ctx, P->gM, P->wcM.get(), nullptr, 1.0, P->wrM.get());
+      energy_sum(ctx, P->gM, (const double*)P->wrM.get(), P->a_ga.get(), E[alpha], acc.get(), alpha > 0);
+    }
+    DBuf<double> accB(ctx->pool, 1);
+    if (P->aniso) aniso_energy_sum(ctx, g, v, P->B, accB.get(), 0);  // sum over the grid of e.B e
+    double h = 0.0, hb = 0.0;
+    LRFG_CUDA(cudaMemcpyAsync(&h, acc.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (P->aniso) LRFG_CUDA(cudaMemcpyAsync(&hb, accB.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+    // the stored coefficient is (|N| / |M|) A~
+    double val = h * (double)P->gM.n_real / (double)g.n_real;
+    if (P->aniso) val += hb / (double)g.n_real + quad_form(P->B, E, g.d);
+    return val;
+  }
   for (int alpha = 0; alpha < g.d; ++alpha) {
     half_mul_grad(ctx, g, v, P->wc.get(), alpha, 1.0 / (double)g.n_real);
     full_inverse<double>(ctx, g, P->wc.get(), nullptr, 1.0, P->wr.get());
@@ -1121,6 +1180,9 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->rank_tol >= 0.0 && opts->rank_tol < 1.0, "rank_tol must be in [0, 1) (got %g)", opts->rank_tol);
     LRFG_REQUIRE(opts->coeff_rank >= 0, "coeff_rank must be >= 0 (got %d)", opts->coeff_rank);
     LRFG_REQUIRE(opts->rank_start >= 0 && opts->rank_step >= 0, "rank_start and rank_step must be >= 0");
+    LRFG_REQUIRE(opts->disc == LRFG_GANI || opts->disc == LRFG_GA, "unknown discretisation %d", (int)opts->disc);
+    if (opts->disc == LRFG_GA && (opts->fmt != LRFG_FULL || opts->prec != LRFG_FP64))
+      fail(LRFG_ENOTSUP, "LRFG_GA is implemented for LRFG_FULL solutions in LRFG_FP64");
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
                  "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();
@@ -1132,6 +1194,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     P->d = coeff->d;
     for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
     P->aniso = check_aniso(P->d, coeff->B, P->B);
+    P->ga = opts->disc == LRFG_GA;
     const long long n = grid_size(P->d, P->N);
     // coefficient -> device
     if (coeff->fmt == LRFG_FULL) {
@@ -1182,6 +1245,18 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       make_inv_tables(ctx, P->g, P->inv64, P->inv32);
       P->wc = DBuf<double2>(ctx->pool, P->g.n_half);
       P->wr = DBuf<double>(ctx->pool, P->g.n_real);
+      if (P->ga) {
+        int M[3] = {0, 0, 0};
+        for (int j = 0; j < P->d; ++j) {
+          M[j] = 2 * P->N[j] - 1;
+          make_plan(M[j], 27);  // LRFG_ENOTSUP when the double grid has a prime factor above 31
+        }
+        P->gM = make_grid(P->d, M);
+        P->a_ga = DBuf<double>(ctx->pool, P->gM.n_real);
+        P->wrM = DBuf<double>(ctx->pool, P->gM.n_real);
+        P->wcM = DBuf<double2>(ctx->pool, P->gM.n_half);
+        ga_coefficient(ctx, P->g, P->gM, P->a_full.get(), P->wc.get(), P->wcM.get(), P->a_ga.get());
+      }
       if (P->opts.prec == LRFG_MIXED) {
         P->a_full_f = DBuf<float>(ctx->pool, n);
         convert(ctx, (const double*)P->a_full.get(), P->a_full_f.get(), n);

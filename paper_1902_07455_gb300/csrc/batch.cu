@@ -25,7 +25,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 // the quantities that fix a solve's memory use
-using ShapeKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+using ShapeKey = std::tuple<int, int, int, int, int, int, int, int, int, int>;
 
 struct Request {
   unsigned long long id = 0;
@@ -68,6 +68,7 @@ size_t estimate_footprint(const lrfg_coeff& c, const lrfg_opts& o) {
     // the coefficient, two real work grids and eight half-spectrum vectors
     const size_t half = n / c.N[c.d - 1] * ((c.N[c.d - 1] + 1) / 2);
     const size_t b = 8 * n * 3 + 16 * half * 8;
+    if (o.disc == LRFG_GA) return b + (((size_t)24 * n) << c.d);  // double grid of about 2^d N^d points
     return o.prec == LRFG_MIXED ? b / 2 + 8 * n : b;
   }
   // low rank: the grid coefficient while it is compressed, and the Kronecker products of rank
@@ -262,7 +263,7 @@ lrfg_status lrfg_batch_submit(lrfg_batch* B, const lrfg_coeff* coeff, const doub
   for (int j = 0; j < coeff->d; ++j) req->E[j] = E[j];
   const int* N = coeff->N;
   req->key = ShapeKey(coeff->d, N[0], N[1], coeff->d == 3 ? N[2] : 1, (int)coeff->fmt, coeff_rank(*coeff),
-                      (int)opts->fmt, (int)opts->prec, opts->rank);
+                      (int)opts->fmt, (int)opts->prec, opts->rank, (int)opts->disc);
   req->footprint = estimate_footprint(*coeff, *opts);
   req->submitted = Clock::now();
   {

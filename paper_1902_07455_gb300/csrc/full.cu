@@ -405,6 +405,105 @@ void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alp
                   in, acc, rowmap(g), alpha, (R)two_pi_times(scale), init, precond, inv_table<R>(g)));
 }
 
+// ------------------------------------------------------------------------------------------------
+// Ga: injection / projection between the half spectra of the grid (N) and the double grid (M = 2N - 1)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int wrap(int k, int n) { return k >= 0 ? k : k + n; }
+
+// over the half spectrum of gM: the coefficient of the same frequency on g, or 0 outside Z_N
+__global__ void inject_kernel(const double2* __restrict__ in, double2* __restrict__ out, RowMap mN, RowMap mM) {
+  int k[3];
+  size_t t;
+  if (!row_k(mM, k[0], k[1], k[2], t)) return;
+  const int h0 = (mN.N0 - 1) / 2, h1 = (mN.N1 - 1) / 2;
+  double2 v = make_double2(0.0, 0.0);
+  if (mN.d == 3) {
+    if (abs(k[0]) <= h0 && abs(k[1]) <= h1 && k[2] < mN.H)
+      v = in[((size_t)wrap(k[0], mN.N0) * mN.N1 + wrap(k[1], mN.N1)) * mN.H + k[2]];
+  } else {
+    if (abs(k[0]) <= h0 && k[1] < mN.H) v = in[(size_t)wrap(k[0], mN.N0) * mN.H + k[1]];
+  }
+  out[t] = v;
+}
+
+// over the half spectrum of g: the coefficient of the same frequency on gM
+__global__ void project_kernel(const double2* __restrict__ in, double2* __restrict__ out, RowMap mN, RowMap mM) {
+  int k[3];
+  size_t t;
+  if (!row_k(mN, k[0], k[1], k[2], t)) return;
+  size_t tm;
+  if (mN.d == 3)
+    tm = ((size_t)wrap(k[0], mM.N0) * mM.N1 + wrap(k[1], mM.N1)) * mM.H + k[2];
+  else
+    tm = (size_t)wrap(k[0], mM.N0) * mM.H + k[1];
+  out[t] = in[tm];
+}
+
+// s(m) = int over a cell of width 1/n of e^{2 pi i m t} dt = sin(pi m / n) / (pi m), 1/n at m = 0
+__device__ __forceinline__ double cell_sinc(int m, int n) {
+  if (m == 0) return 1.0 / n;
+  const double x = 3.141592653589793238462643383279502884 * (double)m;
+  return sin(x / (double)n) / x;
+}
+
+// X[m] = scale * (Phi a)(m mod N) * prod_a s(m_a) over the half spectrum of gM (Phi a from its half
+// spectrum on g, by Hermitian symmetry where the last frequency wraps to a negative one)
+__global__ void ga_spectrum_kernel(const double2* __restrict__ pa, double2* __restrict__ X, RowMap mN, RowMap mM,
+                                   int NL, double scale) {
+  int m[3];
+  size_t t;
+  if (!row_k(mM, m[0], m[1], m[2], t)) return;
+  const int d = mN.d;
+  // representatives in Z_N of m mod N, per axis
+  const int n0 = mN.N0, n1 = d == 3 ? mN.N1 : NL, n2 = NL;
+  int k0 = ((m[0] % n0) + n0) % n0;
+  k0 = k0 <= (n0 - 1) / 2 ? k0 : k0 - n0;
+  int k1 = ((m[1] % n1) + n1) % n1;
+  k1 = k1 <= (n1 - 1) / 2 ? k1 : k1 - n1;
+  int k2 = 0;
+  if (d == 3) {
+    k2 = ((m[2] % n2) + n2) % n2;
+    k2 = k2 <= (n2 - 1) / 2 ? k2 : k2 - n2;
+  }
+  const int kl = d == 3 ? k2 : k1;  // last-axis frequency
+  bool cj = false;
+  if (kl < 0) {  // (Phi a)(k) = conj((Phi a)(-k)) for real a
+    k0 = -k0;
+    k1 = -k1;
+    k2 = -k2;
+    cj = true;
+  }
+  double2 v;
+  if (d == 3)
+    v = pa[((size_t)wrap(k0, n0) * mN.N1 + wrap(k1, mN.N1)) * mN.H + k2];
+  else
+    v = pa[(size_t)wrap(k0, n0) * mN.H + k1];
+  if (cj) v.y = -v.y;
+  double S = scale * cell_sinc(m[0], n0) * cell_sinc(m[1], n1);
+  if (d == 3) S *= cell_sinc(m[2], n2);
+  X[t] = make_double2(S * v.x, S * v.y);
+}
+
+void half_inject(lrfg_ctx* ctx, const FullGrid& g, const FullGrid& gM, const double2* in, double2* out) {
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 0.0, sizeof(double2) * (double)(g.n_half + gM.n_half),
+              inject_kernel<<<row_grid(gM), row_block(gM), 0, ctx->stream>>>(in, out, rowmap(g), rowmap(gM)));
+}
+
+void half_project(lrfg_ctx* ctx, const FullGrid& g, const FullGrid& gM, const double2* in, double2* out) {
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 0.0, 2.0 * sizeof(double2) * (double)g.n_half,
+              project_kernel<<<row_grid(g), row_block(g), 0, ctx->stream>>>(in, out, rowmap(g), rowmap(gM)));
+}
+
+void ga_coefficient(lrfg_ctx* ctx, const FullGrid& g, const FullGrid& gM, const double* a, double2* half_g,
+                    double2* half_m, double* out) {
+  full_forward<double>(ctx, g, a, nullptr, 1.0, half_g);  // Phi a on g
+  const double scale = (double)g.n_real / ((double)gM.n_real * (double)gM.n_real);
+  LRFG_LAUNCH(ctx, KC_POINTWISE, 20.0 * gM.n_half, sizeof(double2) * (double)(g.n_half + gM.n_half),
+              ga_spectrum_kernel<<<row_grid(gM), row_block(gM), 0, ctx->stream>>>(half_g, half_m, rowmap(g), rowmap(gM),
+                                                                                 g.N[g.d - 1], scale));
+  full_inverse<double>(ctx, gM, half_m, nullptr, 1.0, out);  // (|N| / |M|^2) Phi*_M X
+}
+
 template <typename V>
 void half_acc_aniso(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, const double* B, int precond) {
   using R = typename RealOf<V>::T;

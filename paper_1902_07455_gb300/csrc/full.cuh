@@ -59,5 +59,13 @@ template <typename V>
 void pcg_direction(lrfg_ctx* ctx, const FullGrid& g, V* p, const V* z, const double* beta);
 template <typename A, typename B>
 void convert(lrfg_ctx* ctx, const A* in, B* out, long long n);
+// Ga (exact integration on the double grid gM, M = 2N - 1 per axis): zero padding I of a half spectrum of
+// the grid g into one of gM, and its adjoint I* (the frequencies of g taken out of gM)
+void half_inject(lrfg_ctx* ctx, const FullGrid& g, const FullGrid& gM, const double2* in, double2* out);
+void half_project(lrfg_ctx* ctx, const FullGrid& g, const FullGrid& gM, const double2* in, double2* out);
+// Ga modified coefficient of a pixel-wise constant a (values on the cells of g): out = (|N| / |M|) A~ on gM,
+// A~[j] = int a phi^j_M dx; work: two half spectra (one of g, one of gM) and nothing else
+void ga_coefficient(lrfg_ctx* ctx, const FullGrid& g, const FullGrid& gM, const double* a, double2* half_g,
+                    double2* half_m, double* out);
 
 }  // namespace lrfg
