@@ -644,6 +644,124 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
         op.rank = rmax
 
 
+# ----------------------------------------------------------------------------------------------
+# Ga (exact integration on the double grid, Sec. 2.2.3) in TT format
+# ----------------------------------------------------------------------------------------------
+
+
+def tt_mode_map(x, j, L):
+    """Carriage j's fibres mapped by the matrix L (M x N): G_j[a, :, b] <- L G_j[a, :, b] — a linear map on
+    mode j only, which may change that mode's size (zero padding, projection)."""
+    out = [G.copy() for G in x]
+    out[j] = np.einsum("mn,anb->amb", L, x[j])
+    return out
+
+
+def ga_matrices(N: int):
+    """Per-mode matrices of Ga for one axis of N points and the double grid M = 2N - 1 (storage order):
+    inject (M x N) zero-pads Fourier coefficients, project (N x M) is its adjoint, and extend (M x N) maps
+    pixel values g_p of a pixel-wise constant factor to int g(t) phi^j_M(t) dt,
+        extend[j, p] = M^-1 sum_{m in Z_M} s(m) e^{2 pi i m (x_p - y_j)},  s(m) = sin(pi m / N) / (pi m),
+    the one-axis form of the modified coefficient of Sec. 2.2.3."""
+    M = 2 * N - 1
+    kN = _fg.frequencies(N)
+    inj = np.zeros((M, N))
+    inj[kN % M, np.arange(N)] = 1.0
+    ms = _fg.frequencies(M).astype(np.float64)
+    s = np.full(M, 1.0 / N)
+    nz = ms != 0
+    s[nz] = np.sin(np.pi * ms[nz] / N) / (np.pi * ms[nz])
+    xp = _fg.grid_points(N)
+    yj = _fg.grid_points(M)
+    ph = np.exp(2j * np.pi * ms[None, None, :] * (xp[None, :, None] - yj[:, None, None]))
+    ext = (ph * s[None, None, :]).sum(axis=2) / M
+    return inj, inj.T.copy(), np.real(ext)
+
+
+class LowRankGaTT:
+    """Ga in TT format: C~ v ~= T P~^-1 T grad^* I* F_M T A~ F_M^-1 I grad^ v and
+    b~ = - T P~^-1 grad^* I* F_M A~ E (Eq. (ls_Ga_fourier) with the truncations placed as in Eq.
+    (Pls_lowrank)), A~ the modified coefficient of a pixel-wise constant a given as a TT of pixel values on
+    the grid N; I, I* and the DFTs act mode by mode.  Interface of ``LowRankGaNi`` (for ``minres``)."""
+
+    def __init__(self, a_tt, shape, rank=10, pinv_eps=0.1, rank_tol=None):
+        self.f = FORMATS["tt"]
+        self.fmt = "tt"
+        self.shape = tuple(int(n) for n in shape)
+        self.d = len(self.shape)
+        self.rank = rank
+        self.rank_tol = rank_tol
+        self.B = None
+        self.K = [_fg.frequencies(n).astype(np.float64) for n in self.shape]
+        self.mats = [ga_matrices(n) for n in self.shape]
+        At = [np.asarray(G, dtype=np.float64) for G in a_tt]
+        for j in range(self.d):
+            At = tt_mode_map(At, j, self.mats[j][2])
+        self.At = At                                             # values on the double grid
+        xmax = float(sum(((n - 1) // 2) ** 2 for n in self.shape))
+        t, w = _expsum.expsum_inverse(xmax, pinv_eps)
+        self.pinv_t, self.pinv_w = t, w
+        self.Pinv = self.f.sep([[np.exp(-tm * K ** 2) for K in self.K] for tm in t], w)
+
+    def T(self, x):
+        return self.f.round(x, rmax=self.rank, tol=self.rank_tol)
+
+    def _inject(self, xh):
+        for j in range(self.d):
+            xh = tt_mode_map(xh, j, self.mats[j][0])
+        return xh
+
+    def _project(self, xh):
+        for j in range(self.d):
+            xh = tt_mode_map(xh, j, self.mats[j][1])
+        return xh
+
+    def _grad_double(self, vh, a):
+        """e_a on the double grid: F_M^-1 I grad^_a v^ (values)."""
+        return self.f.idft(self._inject(self.f.mmul(vh, a, 2j * np.pi * self.K[a])))
+
+    def apply(self, vh):
+        f = self.f
+        acc = None
+        for a in range(self.d):
+            w = self.T(f.had(self.At, self._grad_double(vh, a)))   # T A~ e_a on the double grid
+            wh = self._project(f.dft(w))                           # I* F_M
+            term = f.mmul(wh, a, -2j * np.pi * self.K[a])
+            acc = term if acc is None else f.add(acc, term)
+        s = self.T(acc)
+        return self.T(f.had(self.Pinv, s))
+
+    def rhs(self, E):
+        f = self.f
+        ah = self._project(f.dft(self.At))
+        acc = None
+        for a in range(self.d):
+            if E[a] == 0.0:
+                continue
+            term = f.mmul(f.scale(ah, float(E[a])), a, -2j * np.pi * self.K[a])
+            acc = term if acc is None else f.add(acc, term)
+        if acc is None:
+            return f.zeros(self.shape)
+        return f.scale(self.T(f.had(self.Pinv, acc)), -1.0)
+
+    def homogenised_coefficient(self, uh, E) -> float:
+        """sum over the double grid of A~ |E + e|^2 (exact integration), by TT contractions:
+        |E|^2 <A~, 1> + 2 sum_a E_a <A~, e_a> + sum_a <A~ e_a, e_a>."""
+        f = self.f
+        E = np.asarray(E, dtype=np.float64)
+        ones = f.sep([[np.ones(2 * n - 1) for n in self.shape]])
+        val = float(E @ E) * np.real(f.dot(ones, self.At))
+        for a in range(self.d):
+            e = self._grad_double(uh, a)
+            ae = f.had(self.At, e)
+            val += 2.0 * float(E[a]) * np.real(f.dot(ones, ae))
+            val += np.real(f.dot(e, ae))
+        return float(val)
+
+    def full_field(self, uh) -> np.ndarray:
+        return np.real(_fg.idft(self.f.full(uh), self.d))
+
+
 def relative_error(A_full: float, A_lowrank: float) -> float:
     """|A_N - A_{N,r}| / A_N  (Eq. (rel_error), reported as an absolute value)."""
     return abs(A_full - A_lowrank) / abs(A_full)

@@ -205,6 +205,8 @@ struct lrfg_problem {
   FullGrid gM{};
   DBuf<double> a_ga, wrM;
   DBuf<double2> wcM;
+  // Ga in TT: the modified coefficient on the double grid, and its projection on the grid (right-hand side)
+  TT a_ga_tt, a_down_tt;
 };
 
 namespace {
@@ -408,8 +410,73 @@ void mode_replace(lrfg_ctx* ctx, const TTView& v, int alpha, double scale, ModeR
   out.view.core[alpha] = out.core.get();
 }
 
+// copy of a TT (or each item of a batch stacked along the first rank index) with every carriage mapped by
+// a Ga mode map (sizes N <-> M)
+void tt_ga_map(lrfg_ctx* ctx, const TTView& x, int nb, const int* n_out, int mode, TTBatch& out) {
+  out.d = x.d;
+  out.nb = nb;
+  for (int j = 0; j < 3; ++j) out.N[j] = j < x.d ? n_out[j] : 0;
+  for (int j = 0; j < 4; ++j) out.r[j] = x.r[j];
+  for (int j = 0; j < x.d; ++j) {
+    out.core[j] = DBuf<double>(ctx->pool, out.elems(j) * nb);
+    ga_resample(ctx, x.core[j], out.core[j].get(), (long long)nb * x.r[j], x.N[j], x.r[j + 1], n_out[j], mode);
+  }
+}
+
+// Ga operator in TT (Eq. (ls_Ga_fourier) with the truncations of Eq. (Pls_lowrank)): the gradient components
+// interpolated to the double grid, the Khatri-Rao product with the modified coefficient and T there, the
+// projection back to the grid, then the divergence, the sum and the preconditioner as for GaNi
+void lr_apply_ga(lrfg_problem* P, const TTView& v, TT& out, int r) {
+  lrfg_ctx* ctx = P->ctx;
+  const double tol = P->opts.rank_tol;
+  const int d = P->d;
+  const TTView a = view_of(P->a_ga_tt);
+  int M[3] = {0, 0, 0};
+  for (int j = 0; j < d; ++j) M[j] = a.N[j];
+  TTBatch vu;  // v on the double grid
+  tt_ga_map(ctx, v, 1, M, GA_UP, vu);
+  DBuf<double> gu[3];  // gradient carriages D_a v_a on the double grid
+  for (int alpha = 0; alpha < d; ++alpha) {
+    DBuf<double> g(ctx->pool, (size_t)v.r[alpha] * v.N[alpha] * v.r[alpha + 1]);
+    fibre_operator(ctx, v.core[alpha], g.get(), v.r[alpha], v.N[alpha], v.r[alpha + 1], LRFG_MUL_DERIV, 0.0, 1.0);
+    gu[alpha] = DBuf<double>(ctx->pool, (size_t)v.r[alpha] * M[alpha] * v.r[alpha + 1]);
+    ga_resample(ctx, g.get(), gu[alpha].get(), v.r[alpha], v.N[alpha], v.r[alpha + 1], M[alpha], GA_UP);
+  }
+  int rk[4];
+  for (int j = 0; j <= d; ++j) rk[j] = a.r[j] * v.r[j];
+  TTBatch kr;
+  ttb_alloc(ctx, kr, d, M, rk, d);
+  for (int alpha = 0; alpha < d; ++alpha)
+    for (int j = 0; j < d; ++j)
+      khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1], (j == alpha) ? gu[j].get() : vu.core[j].get(), v.r[j],
+                 v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
+  for (auto& g : gu) g.reset();
+  vu = TTBatch();
+  TTBatch w;
+  tt_round_batch(ctx, batch_view(kr), r, w, tol);  // T on the double grid
+  kr = TTBatch();
+  TTBatch wd;  // I* F_M back to the grid, every item
+  tt_ga_map(ctx, item_view(w, 0), d, P->N, GA_DOWN, wd);
+  w = TTBatch();
+  TTView terms[3];
+  for (int alpha = 0; alpha < d; ++alpha) {
+    terms[alpha] = item_view(wd, alpha);
+    double* c = const_cast<double*>(terms[alpha].core[alpha]);
+    fibre_operator(ctx, c, c, wd.r[alpha], wd.N[alpha], wd.r[alpha + 1], LRFG_MUL_DERIV, 0.0, -1.0);
+  }
+  TT acc;
+  tt_add_many(ctx, terms, nullptr, d, acc);
+  TT sdiv;
+  tt_round(ctx, view_of(acc), r, sdiv, tol);
+  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol);
+}
+
 // rank r of every truncation (the problem's rank, or the current rank of a rank-adapting solve)
 void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
+  if (P->ga) {
+    lr_apply_ga(P, v, out, r);
+    return;
+  }
   lrfg_ctx* ctx = P->ctx;
   const double tol = P->opts.rank_tol;
   const int d = P->d;
@@ -482,7 +549,8 @@ void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
   for (int alpha = 0; alpha < P->d; ++alpha) {
     if (E[alpha] == 0.0) continue;
     ModeReplaced t;
-    mode_replace(ctx, view_of(P->a_tt), alpha, E[alpha], t);   // E_a D_a a
+    // E_a D_a a (Ga: the projection of the modified coefficient on the grid, I* F_M A~)
+    mode_replace(ctx, view_of(P->ga ? P->a_down_tt : P->a_tt), alpha, E[alpha], t);
     if (!have) {
       tt_copy(ctx, t.view, acc);
       have = true;
@@ -501,7 +569,37 @@ void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
   tt_precond(ctx, view_of(acc), P->pt, P->pw, rank, out, P->opts.rank_tol);  // T P~^-1 (one truncation)
 }
 
+// Ga: sum over the double grid of A~ |E + e|^2 (exact integration), e the gradient interpolated there
+double lr_aeff_ga(lrfg_problem* P, const double* E, const TTView& u) {
+  lrfg_ctx* ctx = P->ctx;
+  const int d = P->d;
+  const TTView a = view_of(P->a_ga_tt);
+  int M[3] = {0, 0, 0};
+  for (int j = 0; j < d; ++j) M[j] = a.N[j];
+  TT ones;
+  ones_tt(ctx, d, M, ones);
+  double EE = 0.0;
+  for (int j = 0; j < d; ++j) EE += E[j] * E[j];
+  double val = EE * tt_dot(ctx, a, view_of(ones));
+  TTBatch uu;
+  tt_ga_map(ctx, u, 1, M, GA_UP, uu);
+  for (int alpha = 0; alpha < d; ++alpha) {
+    DBuf<double> g(ctx->pool, (size_t)u.r[alpha] * u.N[alpha] * u.r[alpha + 1]);
+    fibre_operator(ctx, u.core[alpha], g.get(), u.r[alpha], u.N[alpha], u.r[alpha + 1], LRFG_MUL_DERIV, 0.0, 1.0);
+    DBuf<double> gu(ctx->pool, (size_t)u.r[alpha] * M[alpha] * u.r[alpha + 1]);
+    ga_resample(ctx, g.get(), gu.get(), u.r[alpha], u.N[alpha], u.r[alpha + 1], M[alpha], GA_UP);
+    TTView e = item_view(uu, 0);
+    e.core[alpha] = gu.get();
+    TT ae;
+    tt_hadamard(ctx, a, e, ae);
+    if (E[alpha] != 0.0) val += 2.0 * E[alpha] * tt_dot(ctx, view_of(ae), view_of(ones));
+    val += tt_dot(ctx, view_of(ae), e);
+  }
+  return val;
+}
+
 double lr_aeff(lrfg_problem* P, const double* E, const TTView& u) {
+  if (P->ga) return lr_aeff_ga(P, E, u);
   lrfg_ctx* ctx = P->ctx;
   const double size = (double)grid_size(P->d, P->N);
   TT ones;
@@ -1181,8 +1279,8 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->coeff_rank >= 0, "coeff_rank must be >= 0 (got %d)", opts->coeff_rank);
     LRFG_REQUIRE(opts->rank_start >= 0 && opts->rank_step >= 0, "rank_start and rank_step must be >= 0");
     LRFG_REQUIRE(opts->disc == LRFG_GANI || opts->disc == LRFG_GA, "unknown discretisation %d", (int)opts->disc);
-    if (opts->disc == LRFG_GA && (opts->fmt != LRFG_FULL || opts->prec != LRFG_FP64))
-      fail(LRFG_ENOTSUP, "LRFG_GA is implemented for LRFG_FULL solutions in LRFG_FP64");
+    if (opts->disc == LRFG_GA && ((opts->fmt != LRFG_FULL && opts->fmt != LRFG_TT) || opts->prec != LRFG_FP64))
+      fail(LRFG_ENOTSUP, "LRFG_GA is implemented for LRFG_FULL and LRFG_TT solutions in LRFG_FP64");
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
                  "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();
@@ -1195,6 +1293,8 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
     P->aniso = check_aniso(P->d, coeff->B, P->B);
     P->ga = opts->disc == LRFG_GA;
+    if (P->ga && P->aniso && opts->fmt == LRFG_TT)
+      fail(LRFG_ENOTSUP, "LRFG_GA with an anisotropic part is implemented for LRFG_FULL solutions");
     const long long n = grid_size(P->d, P->N);
     // coefficient -> device
     if (coeff->fmt == LRFG_FULL) {
@@ -1267,6 +1367,27 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
       double xmax = 0.0;
       for (int j = 0; j < P->d; ++j) xmax += (double)((P->N[j] - 1) / 2) * ((P->N[j] - 1) / 2);
       expsum_inverse(xmax, P->opts.pinv_eps, P->pt, P->pw);
+      if (P->ga) {
+        // the modified coefficient mode by mode from the TT of pixel values, and its projection
+        int M[3] = {0, 0, 0};
+        for (int j = 0; j < P->d; ++j) {
+          M[j] = 2 * P->N[j] - 1;
+          make_plan(M[j], 27);  // LRFG_ENOTSUP when the double grid has a prime factor above 31
+        }
+        TTBatch ag, ad;
+        tt_ga_map(ctx, view_of(P->a_tt), 1, M, GA_EXTEND, ag);
+        tt_ga_map(ctx, item_view(ag, 0), 1, P->N, GA_DOWN, ad);
+        P->a_ga_tt.d = P->a_down_tt.d = P->d;
+        for (int j = 0; j < 3; ++j) {
+          P->a_ga_tt.N[j] = ag.N[j];
+          P->a_down_tt.N[j] = ad.N[j];
+        }
+        for (int j = 0; j < 4; ++j) P->a_ga_tt.r[j] = P->a_down_tt.r[j] = ag.r[j];
+        for (int j = 0; j < P->d; ++j) {
+          P->a_ga_tt.core[j] = std::move(ag.core[j]);
+          P->a_down_tt.core[j] = std::move(ad.core[j]);
+        }
+      }
     }
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
     *out = P;

@@ -359,4 +359,71 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   // the pool hands these blocks out again only to later work on the same stream
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Ga mode maps (Sec. 2.2.3) on real fibres: forward transform on n_in points, a spectral map to n_out
+// points, inverse transform; the maps are exact in exact arithmetic (zero padding, truncation, periodic
+// extension with the cell sinc), the transforms the library's fibre FFTs.
+// ------------------------------------------------------------------------------------------------
+__global__ void real_to_complex_kernel(const double* __restrict__ in, double2* __restrict__ out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = make_double2(in[t], 0.0);
+}
+
+__global__ void complex_to_real_kernel(const double2* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = in[t].x;
+}
+
+__device__ __forceinline__ int freq_rep(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+
+// out[o][m][i] = weight(m) * in[o][src(m)][i] over (outer, n_out, inner)
+__global__ void ga_spectral_map_kernel(const double2* __restrict__ in, double2* __restrict__ out, long long outer,
+                                       int n_in, long long inner, int n_out, int mode, int n_grid) {
+  const long long total = outer * n_out * inner;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t % inner;
+    const long long q = t / inner;
+    const int m = (int)(q % n_out);
+    const long long o = q / n_out;
+    const int f = freq_rep(m, n_out);
+    int src = -1;
+    double wgt = 0.0;
+    if (mode == GA_UP) {  // zero padding, F_N = Phi_N / N
+      if (abs(f) <= (n_in - 1) / 2) { src = f < 0 ? f + n_in : f; wgt = 1.0 / n_in; }
+    } else if (mode == GA_DOWN) {  // the frequencies of the small grid, F_M = Phi_M / M
+      src = f < 0 ? f + n_in : f;
+      wgt = 1.0 / n_in;
+    } else {  // periodic extension times the cell sinc of the pixel grid n_grid, and M^-1
+      src = ((f % n_in) + n_in) % n_in;
+      const double x = 3.141592653589793238462643383279502884 * (double)f;
+      const double s = f == 0 ? 1.0 / n_grid : sin(x / (double)n_grid) / x;
+      wgt = s / n_out;
+    }
+    double2 v = make_double2(0.0, 0.0);
+    if (src >= 0) {
+      const double2 u = in[(o * n_in + src) * inner + i];
+      v = make_double2(wgt * u.x, wgt * u.y);
+    }
+    out[t] = v;
+  }
+}
+
+void ga_resample(lrfg_ctx* ctx, const double* in, double* out, long long outer, int n_in, long long inner, int n_out,
+                 int mode) {
+  const long long nin = outer * n_in * inner, nout = outer * n_out * inner;
+  if (nin == 0 || nout == 0) return;
+  const unsigned gin = (unsigned)std::min<long long>((nin + 255) / 256, 8LL * ctx->num_sms);
+  const unsigned gout = (unsigned)std::min<long long>((nout + 255) / 256, 8LL * ctx->num_sms);
+  DBuf<double2> a(ctx->pool, (size_t)nin), b(ctx->pool, (size_t)nout);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 0.0, 24.0 * nin, real_to_complex_kernel<<<gin, 256, 0, ctx->stream>>>(in, a.get(), nin));
+  fft_fibres<double2>(ctx, a.get(), a.get(), outer, n_in, inner, -1);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 2.0 * nout, 32.0 * nout,
+              ga_spectral_map_kernel<<<gout, 256, 0, ctx->stream>>>(a.get(), b.get(), outer, n_in, inner, n_out, mode,
+                                                                    mode == GA_EXTEND ? n_in : 0));
+  fft_fibres<double2>(ctx, b.get(), b.get(), outer, n_out, inner, 1);
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 0.0, 24.0 * nout,
+              complex_to_real_kernel<<<gout, 256, 0, ctx->stream>>>(b.get(), out, nout));
+}
+
 }  // namespace lrfg

@@ -19,6 +19,14 @@ const typename CplxOf<R>::T* twiddle_table(lrfg_ctx* ctx, int N);
 // (V = double2 or float2)
 template <typename V>
 void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long long inner, int sign);
+// Ga mode maps on real fibres (outer, n_in, inner) -> (outer, n_out, inner), M = 2N - 1 (Sec. 2.2.3):
+//  GA_UP      N -> M  band-limited interpolation to the double grid, F_M^-1 I F_N;
+//  GA_DOWN    M -> N  projection, F_N^-1 I* F_M;
+//  GA_EXTEND  N -> M  pixel values to the one-axis modified coefficient, M^-1 Phi*_M (s(m) (Phi_N g)(m mod N)),
+//             s(m) = sin(pi m / N) / (pi m)
+enum { GA_UP = 0, GA_DOWN = 1, GA_EXTEND = 2 };
+void ga_resample(lrfg_ctx* ctx, const double* in, double* out, long long outer, int n_in, long long inner, int n_out,
+                 int mode);
 // real fibres: out = scale * F^-1 diag(m) F in, m given by kind/param (lrfg_multiplier)
 void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
                     int kind, double param, double scale);

@@ -67,8 +67,51 @@ def test_ga_not_supported(ctx):
         ctx.problem(a, lrfg.FULL, disc=lrfg.GA)
     assert e.value.status == 6
     a = random_field((13, 13), seed=1)
-    for kw in (dict(fmt=lrfg.TT, rank=3), dict(fmt=lrfg.FULL, prec=lrfg.MIXED)):
+    for kw in (dict(fmt=lrfg.TUCKER, rank=3), dict(fmt=lrfg.FULL, prec=lrfg.MIXED)):
         fmt = kw.pop("fmt")
         with pytest.raises(lrfg.LrfgError) as e:
             ctx.problem(a, fmt, disc=lrfg.GA, **kw)
         assert e.value.status == 6
+
+
+# ---- Ga in TT format (the low-rank Ga of the paper's timing study) ------------------------------------
+from oracle import lowrank as lr  # noqa: E402
+from synthetic import random_tt, smoothed_cube  # noqa: E402
+
+
+@pytest.mark.parametrize("d,N,rank,rx", [(2, 13, 4, [3]), (3, 13, 3, [2, 3]), (2, 25, 6, [4])])
+def test_tt_ga_apply_and_rhs(ctx, d, N, rank, rx):
+    shape = (N,) * d
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    a_tt = lr.tt_from_separable(terms, w)
+    op = lr.LowRankGaTT(a_tt, shape, rank=rank, pinv_eps=0.1)
+    x = random_tt(shape, rx, seed=21)
+    ref = np.real(lr.tt_full(lr.tt_idft(op.apply(lr.tt_dft(x)))))
+    P = ctx.problem(lrfg.TTensor.from_numpy(a_tt), lrfg.TT, rank=rank, pinv_eps=0.1, disc=lrfg.GA)
+    out = P.apply(ctx.field_from_tt(lrfg.TTensor.from_numpy(x))).full()
+    assert rel(out, ref) <= 1e-7
+    E = np.eye(d)[0]
+    refb = np.real(lr.tt_full(lr.tt_idft(op.rhs(E))))
+    assert rel(P.rhs(E).full(), refb) <= 1e-7
+
+
+@pytest.mark.parametrize("d,N,rank", [(2, 25, 8), (3, 13, 5)])
+def test_tt_ga_solve(ctx, d, N, rank):
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    a_tt = lr.tt_from_separable(terms, w)
+    E = np.eye(d)[0]
+    ref = lr.minres(lr.LowRankGaTT(a_tt, (N,) * d, rank=rank, pinv_eps=0.1), E, tol=1e-10, maxit=40)
+    P = ctx.problem(lrfg.TTensor.from_numpy(a_tt), lrfg.TT, rank=rank, tol=1e-10, maxit=40, disc=lrfg.GA)
+    res, u = P.solve(E)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    assert abs(P.aeff(E, u) - res.Aeff) <= 1e-12 * res.Aeff
+
+
+def test_untruncated_tt_ga_equals_full_ga(ctx):
+    d, N = 2, 13
+    a, terms, w = square_inclusion(d, N)
+    E = np.eye(d)[0]
+    full, _ = ctx.problem(a, lrfg.FULL, disc=lrfg.GA, tol=1e-12, maxit=3000).solve(E, want_field=False)
+    tt, _ = ctx.problem(lrfg.TTensor.from_numpy(lr.tt_from_separable(terms, w)), lrfg.TT, rank=N, tol=1e-12,
+                        maxit=400, stop_on_increase=False, disc=lrfg.GA).solve(E, want_field=False)
+    assert abs(tt.Aeff - full.Aeff) <= 1e-9 * full.Aeff

@@ -8,7 +8,8 @@ import pytest
 
 from oracle import fourier_galerkin as fg
 from oracle import galerkin_exact as ga
-from synthetic import random_field
+from oracle import lowrank as lr
+from synthetic import random_field, smoothed_cube, square_inclusion
 
 GL_X, GL_W = np.polynomial.legendre.leggauss(12)
 
@@ -134,3 +135,23 @@ def test_galerkin_bounds_on_nested_spaces():
     assert coarse - fine > 1e-6 * coarse  # the bigger space lowers the energy
     harm = 1.0 / np.mean(1.0 / a)
     assert harm <= fine and coarse <= a.mean()
+
+
+def test_tt_modified_coefficient_matches_the_full_one():
+    """The mode-wise (dense matrix) route of the TT Ga coefficient against the FFT route of the full one."""
+    N = 9
+    a, terms, w = smoothed_cube(3, N, contrast=10.0)
+    op = lr.LowRankGaTT(lr.tt_from_separable(terms, w), (N,) * 3, rank=None)
+    ref = ga.ga_coefficient(a)
+    assert np.abs(lr.tt_full(op.At) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("d,N", [(2, 13), (3, 9)])
+def test_untruncated_tt_ga_equals_full_ga(d, N):
+    """Untruncated TT Ga MinRes reaches the full-format Ga solution (pinned above) to 1e-10."""
+    a, terms, w = square_inclusion(d, N)
+    E = np.eye(d)[0]
+    full = ga.solve_ga(a, E, tol=1e-13, maxit=3000)
+    op = lr.LowRankGaTT(lr.tt_from_separable(terms, w), (N,) * d, rank=None, rank_tol=1e-15)
+    out = lr.minres(op, E, tol=1e-13, maxit=600, stop_on_increase=False)
+    assert abs(out["Aeff"] - full["Aeff"]) <= 1e-10 * full["Aeff"]
