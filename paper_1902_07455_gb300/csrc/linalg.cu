@@ -221,8 +221,9 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
     if (dynM || dynN) a = std::max<long long>(batch, a / 4);
     return a;
   };
-  // 32 x 32 tiles when 64 x 64 ones would leave most SMs idle
-  const int tile = active_tiles(64) < nsm ? 32 : 64;
+  // 32 x 32 tiles when 64 x 64 ones would leave most SMs idle (static sizes only: with data-dependent sizes
+  // the active tiles are not known here, and the split count is what spreads those products)
+  const int tile = (!dynM && !dynN && active_tiles(64) < nsm) ? 32 : 64;
   const int bmn = (M + tile - 1) / tile, bnn = (N + tile - 1) / tile;
   const long long active = active_tiles(tile);
   const int target = 2 * nsm;
