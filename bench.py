@@ -70,6 +70,23 @@ def parse():
     return p.parse_args()
 
 
+def reduce_max(value: float, device) -> float:
+    """Max of value over the ranks of the default process group (the value itself without one): the timing
+    rule for N > 1 replicas (every rank times its own steps; the job takes as long as the slowest)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of N independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -323,9 +340,7 @@ def run_ours(args):
     launches = ctx.launch_count() - launches0
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max(total_ms, f"cuda:{local}")
         dist.barrier()
     res = results[-1]
     applies = sum(r.applies for r in results)
@@ -346,7 +361,7 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        solves_per_s = world * args.steps / (total_ms * 1e-3)
+        solves_per_s = job_throughput(args.steps, world, total_ms * 1e-3)
         line = {
             "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -58,3 +58,14 @@ def test_product_package_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_batch_entry_points_check_arguments_without_gpu(lib):
+    # argument checks of the serving executor that need no device
+    out = ctypes.c_void_p()
+    assert lib.lrfg_batch_create(None, 0, 2, ctypes.c_size_t(0)) == 1          # null out pointer
+    assert lib.lrfg_batch_create(ctypes.byref(out), 0, 0, ctypes.c_size_t(0)) == 1  # no workers
+    assert lib.lrfg_batch_submit(None, None, None, None, None) == 1
+    ready = ctypes.c_int()
+    assert lib.lrfg_batch_poll(None, ctypes.c_ulonglong(1), 0, ctypes.byref(ready), None, None, None) == 1
+    assert lib.lrfg_batch_destroy(None) == 1
