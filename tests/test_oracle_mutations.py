@@ -108,3 +108,80 @@ def test_wrong_minres_step(monkeypatch):
         return dict(u=u, iters=maxit, rel_resid=0.0, history=[], Aeff=op.homogenised_coefficient(u, E))
     monkeypatch.setattr(lr, "minres", bad_minres)
     _must_fail(tl.test_untruncated_lowrank_equals_full, "tt", 2, 15)
+
+
+# ---- planted mistakes in the oracle's extensions (Ga, anisotropy, tolerance truncation, rank adaptation)
+import tests.test_oracle_ga as tg  # noqa: E402
+from oracle import galerkin_exact as ga  # noqa: E402
+
+
+def test_ga_cell_sinc_with_the_wrong_width(monkeypatch):
+    """s(m) of a cell of width 2/N instead of 1/N: the quadrature pin of the modified coefficient fails."""
+    def bad(m, N):
+        m = np.asarray(m, dtype=np.float64)
+        out = np.full(m.shape, 2.0 / N)
+        nz = m != 0
+        out[nz] = np.sin(2.0 * np.pi * m[nz] / N) / (np.pi * m[nz])
+        return out
+    monkeypatch.setattr(ga, "_sinc_cell", bad)
+    _must_fail(tg.test_coefficient_matches_quadrature_of_the_dirichlet_kernel)
+
+
+def test_ga_injection_without_wrapping(monkeypatch):
+    """Negative frequencies placed at their N-grid storage index on the double grid: the dense Galerkin pin
+    fails."""
+    def bad(vh, M, d):
+        N = vh.shape[-1]
+        out = np.zeros(vh.shape[:-d] + (M,) * d, dtype=np.complex128)
+        idx = np.ix_(*([np.arange(N)] * d))
+        out[(Ellipsis,) + idx] = vh
+        return out
+    monkeypatch.setattr(ga, "inject", bad)
+    with pytest.raises((AssertionError, ZeroDivisionError)):  # a wrong (here singular) operator
+        tg.test_ga_solve_matches_dense_galerkin(5, 1)
+
+
+def test_ga_aeff_on_the_grid_instead_of_the_double_grid(monkeypatch):
+    """A_eff by the rectangle rule of the grid (the GaNi formula) instead of the exact double-grid sum."""
+    monkeypatch.setattr(ga, "homogenised_coefficient_ga",
+                        lambda uh, At, E: fg.homogenised_coefficient(uh, np.full(uh.shape, At.sum()), E))
+    _must_fail(tg.test_ga_solve_matches_dense_galerkin, 5, 1)
+
+
+def test_anisotropic_part_with_the_wrong_sign(monkeypatch):
+    """a e_a - sum_b B_ab e_b in the low-rank material product: untruncated low rank no longer equals the
+    full-format tensor solve."""
+    orig = lr.LowRankGaNi.apply
+
+    def bad(self, vh):
+        self.B = -self.B
+        try:
+            return orig(self, vh)
+        finally:
+            self.B = -self.B
+    monkeypatch.setattr(lr.LowRankGaNi, "apply", bad)
+    _must_fail(tl.test_untruncated_anisotropic_lowrank_equals_full, "tt", 2, 15)
+
+
+def test_tolerance_not_split_over_the_bonds(monkeypatch):
+    """tol per TT bond instead of tol / sqrt(d - 1): the first-bond rank pin fails."""
+    orig = lr.tt_round
+    monkeypatch.setattr(lr, "tt_round", lambda x, rmax=None, tol=None: orig(
+        x, rmax=rmax, tol=None if tol is None else tol * np.sqrt(max(len(x) - 1, 1))))
+    monkeypatch.setitem(lr.FORMATS["tt"].__dict__, "round", lr.tt_round)
+    _must_fail(tl.test_tolerance_truncation_bound_and_first_rank, "tt")
+
+
+def test_rank_adaptation_without_rebuilding_the_rhs(monkeypatch):
+    """The right-hand side kept at the starting rank after a raise: the untruncated pin (A_eff of the full
+    solve) fails."""
+    orig_rhs = lr.LowRankGaNi.rhs
+    cache = {}
+
+    def frozen(self, E):
+        key = id(self)
+        if key not in cache:
+            cache[key] = orig_rhs(self, E)
+        return cache[key]
+    monkeypatch.setattr(lr.LowRankGaNi, "rhs", frozen)
+    _must_fail(tl.test_rank_adaptive_minres_pins)
