@@ -624,6 +624,18 @@ namespace lrfg {
 // ------------------------------------------------------------------------------------------------
 constexpr int kCholThreads = 512;
 
+// shared-memory layout of gram_factor_kernel: bytes of the header before the two b x b work matrices
+__host__ __device__ inline size_t chol_head_bytes(int b) {
+  size_t bytes = sizeof(double) * (32 + 2 * (size_t)b) + sizeof(int) * (32 + 3 * (size_t)b + 2);
+  return (bytes + 255) / 256 * 256;
+}
+
+// Left-looking form (Golub & Van Loan Sec. 4.2.8 ordering with diagonal pivoting): pivot k takes the
+// largest remaining diagonal of the Schur complement, kept as a vector, and only column k of L is formed,
+// L[i][k] = (G[i][p] - sum_{l<k} L[i][l] L[p][l]) / L[p][k], for the rows not yet pivots; b rho^2 / 2
+// multiply-adds up to the numerical rank instead of the b^2 rho of updating the whole trailing block.
+// Column k of L is stored over column p = perm[k] of the working copy of G (that column is read only at
+// this step), so L[j][l] sits at W[j][perm[l]].
 __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double* __restrict__ Gg,
                                                                    const double* __restrict__ cg, int b, double tau,
                                                                    double* RAg, double* RAcg, double* Pcg,
@@ -631,11 +643,15 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
                                                                    double* work) {
   extern __shared__ __align__(16) double sm[];
   double* redv = sm;                   // 32 values
-  int* redi = (int*)(redv + 32);       // 32 indices
-  int* perm = redi + 32;               // b
-  int* flag = perm + b;                // 2: rho, pivot
+  double* dv = redv + 32;              // b: remaining diagonal of the Schur complement
+  double* rd = dv + b;                 // b: reciprocals of the diagonal of L11
+  int* redi = (int*)(rd + b);          // 32 indices
+  int* perm = redi + 32;               // b: perm[k] = row of pivot k
+  int* done = perm + b;                // b: 1 once a row is a pivot
+  int* pos = done + b;                 // b: pivot position of a row
+  int* flag = pos + b;                 // 2: rho, pivot
   const size_t bb = (size_t)b * b;
-  double* W = use_smem ? (double*)(flag + 2 + ((b + 2) & 1) + 64) : scratch + (size_t)blockIdx.x * 2 * bb;
+  double* W = use_smem ? (double*)((unsigned char*)sm + chol_head_bytes(b)) : scratch + (size_t)blockIdx.x * 2 * bb;
   double* Li = W + bb;                 // L11^{-1}
   const double* G = Gg + (size_t)blockIdx.x * bb;
   const double* c = cg ? cg + (size_t)blockIdx.x * b : nullptr;
@@ -644,10 +660,15 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
   double* Pc = Pcg ? Pcg + (size_t)blockIdx.x * bb : nullptr;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   for (size_t t = tid; t < bb; t += nthr) W[t] = G[t];
-  for (int i = tid; i < b; i += nthr) perm[i] = i;
-  __syncthreads();
   double md = 0.0;
-  for (int i = tid; i < b; i += nthr) md = fmax(md, W[(size_t)i * b + i]);
+  for (int i = tid; i < b; i += nthr) {
+    const double gi = G[(size_t)i * b + i];
+    dv[i] = gi;
+    done[i] = 0;
+    pos[i] = b;
+    perm[i] = i;
+    md = fmax(md, gi);
+  }
   for (int o = 16; o; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffff, md, o));
   if (lane == 0) redv[warp] = md;
   __syncthreads();
@@ -659,112 +680,121 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
   }
   __syncthreads();
   const double maxd0 = redv[31];
+  const int nwa = min(nw, (b + 31) >> 5);  // warps that hold rows
   for (int k = 0; k < b; ++k) {
-    // pivot: largest remaining diagonal
+    // pivot: largest remaining diagonal (ties: smallest row)
     double best = -1.0;
-    int bi = k;
-    for (int i = k + tid; i < b; i += nthr) {
-      double v = W[(size_t)i * b + i];
-      if (v > best) { best = v; bi = i; }
+    int bi = b;
+    for (int i = tid; i < b; i += nthr) {
+      if (done[i]) continue;
+      const double v = dv[i];
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
     }
-    // only the warps that hold remaining diagonal entries reduce (FP64 compares cost FP64 issue)
-    const int nwa = min(nw, (b - k + 31) >> 5);
     if (warp < nwa) {
       for (int o = 16; o; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffff, best, o);
-        int oi = __shfl_xor_sync(0xffffffff, bi, o);
+        const double ov = __shfl_xor_sync(0xffffffff, best, o);
+        const int oi = __shfl_xor_sync(0xffffffff, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
+      if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
     }
-    __syncthreads();
-    if (lane == 0 && warp < nwa) { redv[warp] = best; redi[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
       double bv = -1.0;
-      int bx = k;
+      int bx = b;
       for (int i = 0; i < nwa; ++i)
         if (redv[i] > bv || (redv[i] == bv && redi[i] < bx)) { bv = redv[i]; bx = redi[i]; }
-      flag[1] = bx;
-      if (!(bv > tau * maxd0) || !(bv > 0.0)) flag[0] = k;
+      if (!(bv > tau * maxd0) || !(bv > 0.0) || bx >= b) {
+        flag[0] = k;
+      } else {
+        // the pivot's square root and reciprocal once, broadcast (see the eigensolver's reflector scalars)
+        const double lkk = sqrt(bv);
+        flag[1] = bx;
+        done[bx] = 1;
+        pos[bx] = k;
+        perm[k] = bx;
+        redv[29] = lkk;
+        redv[30] = 1.0 / lkk;
+      }
     }
     __syncthreads();
     if (flag[0] == k) break;
     const int p = flag[1];
-    if (p != k) {
-      // symmetric interchange of rows/columns k and p
-      for (int j = tid; j < b; j += nthr) {
-        double t = W[(size_t)k * b + j];
-        W[(size_t)k * b + j] = W[(size_t)p * b + j];
-        W[(size_t)p * b + j] = t;
-      }
-      __syncthreads();
-      for (int i = tid; i < b; i += nthr) {
-        double t = W[(size_t)i * b + k];
-        W[(size_t)i * b + k] = W[(size_t)i * b + p];
-        W[(size_t)i * b + p] = t;
-      }
-      if (tid == 0) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
-      __syncthreads();
-    }
-    // the pivot's square root and reciprocal once, broadcast (see the eigensolver's reflector scalars)
-    if (tid == 0) {
-      const double lkk = sqrt(W[(size_t)k * b + k]);
-      redv[30] = 1.0 / lkk;
-      redv[29] = lkk;
-    }
-    __syncthreads();
     const double inv = redv[30];
-    for (int i = k + 1 + tid; i < b; i += nthr) W[(size_t)i * b + k] *= inv;
-    if (tid == 0) W[(size_t)k * b + k] = redv[29];
-    __syncthreads();
-    // Schur complement update of the whole trailing block (kept symmetric so that later interchanges
-    // can swap full rows and columns)
-    const int m = b - k - 1;
-    for (int i = warp; i < m; i += nw) {
-      const double li = W[(size_t)(k + 1 + i) * b + k];
-      for (int j = lane; j < m; j += 32)
-        W[(size_t)(k + 1 + i) * b + (k + 1 + j)] -= li * W[(size_t)(k + 1 + j) * b + k];
+    const double* rowp = W + (size_t)p * b;
+    // column k of L for the rows that are not pivots (four independent accumulators: FP64 FMA latency)
+    for (int i = tid; i < b; i += nthr) {
+      if (done[i]) continue;
+      const double* rowi = W + (size_t)i * b;
+      double s0 = rowi[p], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int l = 0;
+      for (; l + 3 < k; l += 4) {
+        const int c0 = perm[l], c1 = perm[l + 1], c2 = perm[l + 2], c3 = perm[l + 3];
+        s0 = fma(-rowi[c0], rowp[c0], s0);
+        s1 = fma(-rowi[c1], rowp[c1], s1);
+        s2 = fma(-rowi[c2], rowp[c2], s2);
+        s3 = fma(-rowi[c3], rowp[c3], s3);
+      }
+      for (; l < k; ++l) s0 = fma(-rowi[perm[l]], rowp[perm[l]], s0);
+      const double lik = ((s0 + s1) + (s2 + s3)) * inv;
+      W[(size_t)i * b + p] = lik;
+      dv[i] = fma(-lik, lik, dv[i]);
     }
+    if (tid == 0) W[(size_t)p * b + p] = redv[29];
     __syncthreads();
   }
   const int rho = flag[0];
   if (rhog && tid == 0) rhog[blockIdx.x] = rho;
   if (tid == 0) {
-    // rho pivots, each updating the trailing (b-k-1)^2 block, and the triangular inverse (rho^3/6)
+    // column q of L: (b - q - 1) rows of q multiply-adds; the triangular inverse (rho^3/6)
     double f = 0.0;
-    for (int q = 0; q < rho; ++q) f += (double)(b - q - 1) * (b - q - 1);
+    for (int q = 0; q < rho; ++q) f += (double)(b - q - 1) * q;
     add_work(work, 2.0 * f + (Pc ? rho * (double)rho * rho / 3.0 : 0.0), sizeof(double) * 4.0 * bb);
   }
-  // outputs
+  // outputs: RA row k < rho, column j = L[j][k] for rows j that are not earlier pivots (upper triangular in
+  // pivot order), RAc = RA with column j divided by c_j
   for (size_t t = tid; t < bb; t += nthr) {
-    int i = (int)(t / b), l = (int)(t - (t / b) * b);  // RA row i, permuted column l
-    double v = (i < rho && l >= i) ? W[(size_t)l * b + i] : 0.0;
-    int col = perm[l];
-    RA[(size_t)i * b + col] = v;
-    if (RAc) RAc[(size_t)i * b + col] = v / c[col];
+    const int k = (int)(t / b), j = (int)(t - (t / b) * b);
+    double v = 0.0;
+    if (k < rho && pos[j] >= k) v = W[(size_t)j * b + perm[k]];
+    RA[t] = v;
+    if (RAc) RAc[t] = v / c[j];
   }
   if (!Pc) return;
-  // L11^{-1}: one thread per column q, forward substitution
+  // L11^{-1} in pivot order: L11[i][l] = W[perm[i]][perm[l]]; reciprocal diagonal first, then one thread per
+  // column q, forward substitution with four accumulators
+  for (int i = tid; i < rho; i += nthr) rd[i] = 1.0 / W[(size_t)perm[i] * b + perm[i]];
+  __syncthreads();
   for (int q = tid; q < rho; q += nthr) {
     for (int i = 0; i < q; ++i) Li[(size_t)i * b + q] = 0.0;
     for (int i = q; i < rho; ++i) {
-      double s = (i == q) ? 1.0 : 0.0;
-      for (int l = q; l < i; ++l) s -= W[(size_t)i * b + l] * Li[(size_t)l * b + q];
-      Li[(size_t)i * b + q] = s / W[(size_t)i * b + i];
+      const double* rowi = W + (size_t)perm[i] * b;
+      double s0 = (i == q) ? 1.0 : 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int l = q;
+      for (; l + 3 < i; l += 4) {
+        s0 = fma(-rowi[perm[l]], Li[(size_t)l * b + q], s0);
+        s1 = fma(-rowi[perm[l + 1]], Li[(size_t)(l + 1) * b + q], s1);
+        s2 = fma(-rowi[perm[l + 2]], Li[(size_t)(l + 2) * b + q], s2);
+        s3 = fma(-rowi[perm[l + 3]], Li[(size_t)(l + 3) * b + q], s3);
+      }
+      for (; l < i; ++l) s0 = fma(-rowi[perm[l]], Li[(size_t)l * b + q], s0);
+      Li[(size_t)i * b + q] = ((s0 + s1) + (s2 + s3)) * rd[i];
     }
   }
   __syncthreads();
+  // Pc[perm[l]][q] = c[perm[l]] (L11^{-1})[q][l]
   for (size_t t = tid; t < bb; t += nthr) {
-    int l = (int)(t / b), q = (int)(t - (t / b) * b);  // Pc row perm[l], column q
-    double v = (l < rho && q < rho && q >= l) ? c[perm[l]] * Li[(size_t)q * b + l] : 0.0;
-    Pc[(size_t)perm[l] * b + q] = v;
+    const int r = (int)(t / b), q = (int)(t - (t / b) * b);  // Pc row r (original index), column q
+    const int l = pos[r];
+    const double v = (l < rho && q < rho && q >= l) ? c[r] * Li[(size_t)q * b + l] : 0.0;
+    Pc[t] = v;
   }
 }
 
 void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
                  double* Pc, int* rho) {
   if (b <= 0 || batch <= 0) return;
-  const size_t head = sizeof(double) * 32 + sizeof(int) * (32 + b + 2 + ((b + 2) & 1)) + sizeof(double) * 64;
+  const size_t head = chol_head_bytes(b);
   const size_t full = head + sizeof(double) * 2 * (size_t)b * b;
   const int use_smem = full <= (size_t)std::min(ctx->max_smem_optin, 220 * 1024) ? 1 : 0;
   const size_t smem = use_smem ? full : head;
