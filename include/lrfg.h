@@ -5,9 +5,11 @@
  * d in {2,3}, as defined in arXiv:1902.07455 Sec. 2.1, Eq. (homog):
  *     A_eff E.E = min over zero-mean periodic v of  int_Y A(x)(E + grad v).(E + grad v) dx,
  * discretised by the Fourier–Galerkin method with numerical integration (GaNi, Sec. 2.2.2) on an odd
- * grid N^d, preconditioned by the Fourier Laplacian (Sec. 2.3, Eq. (Pls_fourier)).  Solution formats:
+ * grid N^d, or with exact integration on the double grid 2N - 1 (Ga, Sec. 2.2.3; lrfg_opts.disc),
+ * preconditioned by the Fourier Laplacian (Sec. 2.3, Eq. (Pls_fourier)).  Solution formats:
  *   LRFG_FULL    the N^d grid; preconditioned CG (Sec. 3.3, Sec. 4);
- *   LRFG_TT      tensor train of fixed rank r; the truncated operator of Eq. (Pls_lowrank) and the
+ *   LRFG_TT      tensor train of rank r (fixed, or chosen by a tolerance, or raised during the iteration:
+ *                lrfg_opts.rank_tol, rank_start); the truncated operator of Eq. (Pls_lowrank) and the
  *                minimal-residual iteration with truncation of Sec. 3.3;
  *   LRFG_TUCKER  Tucker tensor of fixed multilinear rank r (App. A.2), same operator and iteration,
  *                truncation by factor orthonormalisation + HOSVD of the core (App. A.2.3);
@@ -36,10 +38,11 @@
  *     objects created by the library (lrfg_problem, lrfg_field) are freed by their *_free call;
  *   - all device work is issued on the context's stream; calls that return host values
  *     (A_eff, dots, solve results) synchronise that stream, the others are asynchronous;
- *   - one context per host thread; a context is not thread-safe;
+ *   - one context per host thread; a context is not thread-safe (the lrfg_batch executor runs many
+ *     solves concurrently, each worker thread with its own context and stream);
  *   - LRFG_ENOMEM means the context's HBM budget (or the device) cannot hold the request.
- * Arithmetic: FP64 throughout (LRFG_FP64).  LRFG_MIXED (LRFG_FULL solutions only; LRFG_ENOTSUP for
- * LRFG_TT) stores the PCG vectors, the coefficient and the FFT work in FP32 and keeps every inner
+ * Arithmetic: FP64 throughout (LRFG_FP64); results are bitwise reproducible (no floating-point atomics).
+ * LRFG_MIXED (LRFG_FULL GaNi solutions only; LRFG_ENOTSUP otherwise) stores the PCG vectors, the coefficient and the FFT work in FP32 and keeps every inner
  * product, step length, residual test and the A_eff evaluation in FP64; the solution field it hands
  * out is FP64.  It is an extension of the paper's FP64 method (the paper fixes no precision), for
  * tolerances down to about 1e-5.
