@@ -343,7 +343,9 @@ lrfg_status lrfg_batch_poll(lrfg_batch* batch, unsigned long long ticket, int wa
                             lrfg_status* solve_status, lrfg_result* res, lrfg_batch_report* report);
 /* Requests waiting, running, and the footprint bytes admitted for the running ones (each may be NULL). */
 lrfg_status lrfg_batch_info(lrfg_batch* batch, int* queued, int* running, size_t* in_flight_bytes);
-/* Drop the requests not yet started, wait for the running ones, stop the workers, free everything. */
+/* Drop the requests not yet started (a poll waiting on one returns it with solve status LRFG_EINVAL),
+ * wait for the running ones and for threads inside lrfg_batch_poll, stop the workers, free everything.
+ * No call may use the executor after this one has started. */
 lrfg_status lrfg_batch_destroy(lrfg_batch* batch);
 
 /* ---------------------------------------------------------------------------------------------

@@ -86,6 +86,7 @@ struct lrfg_batch {
   size_t budget = 0;
   size_t in_flight_bytes = 0;
   int running = 0;
+  int pollers = 0;  // threads inside lrfg_batch_poll
   bool stopping = false;
   unsigned long long next_id = 1;
   std::mutex mu;
@@ -283,14 +284,18 @@ lrfg_status lrfg_batch_poll(lrfg_batch* B, unsigned long long ticket, int wait, 
   if (!B || !ready) return LRFG_EINVAL;
   std::unique_lock<std::mutex> lock(B->mu);
   if (B->done.find(ticket) == B->done.end()) return LRFG_EINVAL;
+  ++B->pollers;
   if (wait) B->cv_done.wait(lock, [&] { return B->done[ticket].ready; });
   const Done d = B->done[ticket];
   *ready = d.ready ? 1 : 0;
-  if (!d.ready) return LRFG_OK;
-  if (solve_status) *solve_status = d.status;
-  if (res) *res = d.result;
-  if (report) *report = d.report;
-  B->done.erase(ticket);  // a completed result is handed out once
+  if (d.ready) {
+    if (solve_status) *solve_status = d.status;
+    if (res) *res = d.result;
+    if (report) *report = d.report;
+    B->done.erase(ticket);  // a completed result is handed out once
+  }
+  --B->pollers;
+  B->cv_done.notify_all();  // lrfg_batch_destroy waits for the pollers to leave
   return LRFG_OK;
 }
 
@@ -308,10 +313,25 @@ lrfg_status lrfg_batch_destroy(lrfg_batch* B) {
   {
     std::lock_guard<std::mutex> lock(B->mu);
     B->stopping = true;
-    B->queue.clear();  // requests not yet started are dropped; those running finish first
+    // requests not yet started are dropped (a waiting poll returns them with LRFG_EINVAL); those running
+    // finish first
+    for (auto& r : B->queue) {
+      Done& d = B->done[r->id];
+      d.ready = true;
+      d.status = LRFG_EINVAL;
+      std::snprintf(d.report.message, sizeof(d.report.message), "%s",
+                    "dropped: the executor was destroyed before the request started");
+    }
+    B->queue.clear();
   }
   B->cv_work.notify_all();
+  B->cv_done.notify_all();
   for (auto& t : B->workers) t.join();
+  {
+    // no thread may still be inside lrfg_batch_poll when the executor is freed
+    std::unique_lock<std::mutex> lock(B->mu);
+    B->cv_done.wait(lock, [&] { return B->pollers == 0; });
+  }
   cudaSetDevice(B->device);
   for (size_t w = 0; w < B->ctxs.size(); ++w) {
     lrfg_destroy(B->ctxs[w]);

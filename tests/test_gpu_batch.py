@@ -137,3 +137,32 @@ def test_batch_errors_and_recovery():
                 break
             time.sleep(0.001)
         assert r is not None and r.result.converged
+
+
+def test_destroy_drops_queued_requests_and_releases_waiting_polls():
+    """Destroying the executor while a poll waits on a request that has not started: the poll returns it
+    as dropped (solve status LRFG_EINVAL), the running request finishes, nothing hangs."""
+    import ctypes as C
+    import threading
+    from paper_1902_07455_gb300 import _lib as L
+    _, t3, w3 = smoothed_cube(3, 45, contrast=10.0, full=False)
+    c = lr.tt_from_separable(t3, w3)
+    B = lrfg.Batch(0, workers=1)
+    tickets = [B.submit(c, [1.0, 0.0, 0.0], lrfg.TT, rank=8, maxit=30) for _ in range(4)]
+    out = {}
+
+    def waiter():
+        ready, sst = C.c_int(), C.c_int()
+        rep = L.lrfg_batch_report()
+        st = B.lib.lrfg_batch_poll(B.h, C.c_ulonglong(tickets[-1]), 1, C.byref(ready), C.byref(sst), None,
+                                   C.byref(rep))
+        out.update(st=st, ready=ready.value, sst=sst.value, msg=rep.message.decode())
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    time.sleep(0.05)
+    B.close()
+    th.join(timeout=120)
+    assert not th.is_alive()
+    assert out["st"] == 0 and out["ready"] == 1
+    assert out["sst"] == 1 and "dropped" in out["msg"]
