@@ -63,7 +63,7 @@ typedef enum {
   LRFG_ENOCONV = 3,  /* iteration cap reached before the tolerance; results are still filled */
   LRFG_ECUDA = 4,    /* a CUDA runtime error; the message names the call */
   LRFG_ETIMEOUT = 5, /* reserved for bounded device-side waits */
-  LRFG_ENOTSUP = 6   /* valid but not supported by this build */
+  LRFG_ENOTSUP = 6   /* valid but not supported by the library */
 } lrfg_status;
 
 typedef enum { LRFG_FULL = 0, LRFG_CP = 1, LRFG_TUCKER = 2, LRFG_TT = 3 } lrfg_format;
