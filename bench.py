@@ -489,9 +489,9 @@ def c3_bounds(N, contrast):
 
 
 def run_c3(args):
-    """The large smoothed-cube workload: d = 3 tanh-smoothed cube (|x| < 0.3, width 2/N, contrast 100; coefficient of TT rank 2
-    built on the GPU from its two separable terms), TT MinRes solve at rank r; the full-format solve on
-    the expanded coefficient (FP32 storage, or FP64) as the anchor; Voigt-Reuss bounds."""
+    """The large smoothed-cube workload: d = 3 tanh-smoothed cube (|x| < 0.3, width 2/N, contrast 100;
+    coefficient of TT rank 2 built on the GPU from its two separable terms), TT MinRes solve at rank r; the
+    full-format solve on the expanded coefficient (FP32 storage, or FP64) as the anchor; Voigt-Reuss bounds."""
     import torch
     import paper_1902_07455_gb300 as lrfg
     from paper_1902_07455_gb300 import build
