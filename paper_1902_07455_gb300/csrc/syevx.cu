@@ -635,7 +635,8 @@ __host__ __device__ inline size_t chol_head_bytes(int b) {
 // L[i][k] = (G[i][p] - sum_{l<k} L[i][l] L[p][l]) / L[p][k], for the rows not yet pivots; b rho^2 / 2
 // multiply-adds up to the numerical rank instead of the b^2 rho of updating the whole trailing block.
 // Column k of L is stored over column p = perm[k] of the working copy of G (that column is read only at
-// this step), so L[j][l] sits at W[j][perm[l]].
+// this step), so L[j][l] sits at W[j][perm[l]].  The search for the next pivot runs in the same phase as
+// the column (each warp over the rows it has just updated), so a pivot costs two barriers.
 __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double* __restrict__ Gg,
                                                                    const double* __restrict__ cg, int b, double tau,
                                                                    double* RAg, double* RAcg, double* Pcg,
@@ -681,8 +682,9 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
   __syncthreads();
   const double maxd0 = redv[31];
   const int nwa = min(nw, (b + 31) >> 5);  // warps that hold rows
-  for (int k = 0; k < b; ++k) {
-    // pivot: largest remaining diagonal (ties: smallest row)
+  // per-warp candidates for the next pivot (largest remaining diagonal; ties: smallest row) from the rows
+  // this thread holds, after its own updates (two barriers per pivot)
+  auto warp_candidates = [&]() {
     double best = -1.0;
     int bi = b;
     for (int i = tid; i < b; i += nthr) {
@@ -698,7 +700,10 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
       }
       if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
     }
-    __syncthreads();
+  };
+  warp_candidates();
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
     if (tid == 0) {
       double bv = -1.0;
       int bx = b;
@@ -741,6 +746,7 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
       dv[i] = fma(-lik, lik, dv[i]);
     }
     if (tid == 0) W[(size_t)p * b + p] = redv[29];
+    warp_candidates();
     __syncthreads();
   }
   const int rho = flag[0];
