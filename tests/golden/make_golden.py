@@ -4,7 +4,7 @@
 
 Workload: d = 3, N^3 grid, lognormal SE-GRF coefficient (l = 0.2, variance 1, seed 19020745) compressed
 by the oracle's TT-SVD to rank 10; the full-format reference solves the expansion of that TT coefficient
-(the comparison protocol of Sec. 4.1); E = (1, 0, 0).  Output: tests/golden/config2_lognormal_<N>.json with
+(the comparison protocol of Sec. 4.1); E = (1, 0, 0).  Output: tests/golden/lognormal_<N>.json with
 the full PCG A_eff (tolerance 1e-8), its iteration count, and the TT minimal-residual A_eff at each rank
 (exponential-sum accuracy 0.1, stop when the residual fails to decrease, at most 60 iterations).
 """
@@ -51,7 +51,7 @@ def main():
         out["tt"][str(r)] = {"Aeff": res["Aeff"], "iters": res["iters"], "rel_resid": res["rel_resid"],
                              "seconds": time.time() - t0}
         print("tt", r, out["tt"][str(r)], flush=True)
-    path = os.path.join(HERE, f"config2_lognormal_{N}.json")
+    path = os.path.join(HERE, f"lognormal_{N}.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(path)

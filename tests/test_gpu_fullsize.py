@@ -1,6 +1,6 @@
 """Parity at the benchmark's full size (d = 3, N = 243, lognormal SE-GRF, coefficient TT rank 10): the GPU
 FULL PCG and TT minimal-residual solves against A_eff values the oracle produced for the same seeded
-input (tests/golden/config2_lognormal_243.json, written by tests/golden/make_golden.py, which calls only the
+input (tests/golden/lognormal_243.json, written by tests/golden/make_golden.py, which calls only the
 oracle).  The oracle takes minutes here, so its values are stored; the launch configuration is the one
 bench.py times (same problem construction, same options).  Tolerance: 1e-6 relative (FP64 path)."""
 import json
@@ -14,7 +14,7 @@ import paper_1902_07455_gb300 as lrfg
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "config2_lognormal_243.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "lognormal_243.json")
 
 
 @pytest.fixture(scope="module")
