@@ -69,3 +69,32 @@ def test_batch_entry_points_check_arguments_without_gpu(lib):
     ready = ctypes.c_int()
     assert lib.lrfg_batch_poll(None, ctypes.c_ulonglong(1), 0, ctypes.byref(ready), None, None, None) == 1
     assert lib.lrfg_batch_destroy(None) == 1
+
+
+def test_batch_binding_without_gpu_raises():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1902_07455_gb300 as lrfg
+    with pytest.raises(lrfg.LrfgError):
+        lrfg.Batch(0, workers=2)
+
+
+def test_host_coefficient_marshalling():
+    """The executor's request structs (host buffers) for the three coefficient forms and the B array."""
+    import numpy as np
+    from paper_1902_07455_gb300 import _host_coeff, _set_b
+    from paper_1902_07455_gb300 import _lib as L
+    grid = np.ones((5, 7))
+    c, keep = _host_coeff(grid)
+    assert (c.d, c.fmt, c.N[0], c.N[1], c.on_device) == (2, L.LRFG_FULL, 5, 7, 0)
+    _set_b(c, [[2.0, 1.0], [1.0, 3.0]])
+    assert list(c.B)[:5] == [2.0, 1.0, 0.0, 1.0, 3.0]
+    cores = [np.ones((1, 5, 3)), np.ones((3, 7, 2)), np.ones((2, 9, 1))]
+    c, keep = _host_coeff(cores)
+    assert (c.d, c.fmt, list(c.tt.r), list(c.tt.N)) == (3, L.LRFG_TT, [1, 3, 2, 1], [5, 7, 9])
+    core, facs = np.ones((2, 3)), [np.ones((5, 2)), np.ones((7, 3))]
+    c, keep = _host_coeff((core, facs))
+    assert (c.d, c.fmt, list(c.tk.r)[:2], list(c.tk.N)[:2]) == (2, L.LRFG_TUCKER, [2, 3], [5, 7])
+    with pytest.raises(ValueError):
+        _set_b(c, np.ones((3, 3)))
