@@ -537,6 +537,12 @@ class Problem:
         self.ctx.check(self.ctx.lib.lrfg_problem_aeff(self.h, _dvec(E), field.h, C.byref(out)))
         return out.value
 
+    def aeff_tensor(self) -> np.ndarray:
+        """The homogenised tensor A_eff (d x d): the diagonal from the solves with E = e_a, the off-diagonal
+        entries by polarisation, A_ab = (A_eff(e_a + e_b) - A_aa - A_bb) / 2 (A_eff E.E is a quadratic form
+        in E, Sec. 2.1), so d (d + 1) / 2 solves."""
+        return polarised_tensor(self.d, lambda E: self.solve(E, want_field=False)[0].Aeff)
+
     def free(self):
         if self.h and self.ctx.h:
             self.ctx.lib.lrfg_problem_free(self.h)
@@ -547,6 +553,19 @@ class Problem:
             self.free()
         except Exception:
             pass
+
+
+def polarised_tensor(d: int, quad) -> np.ndarray:
+    """Symmetric d x d tensor from its quadratic form quad(E) = E.A E: quad(e_a) on the diagonal and
+    (quad(e_a + e_b) - quad(e_a) - quad(e_b)) / 2 off it."""
+    A = np.zeros((d, d))
+    eye = np.eye(d)
+    for a in range(d):
+        A[a, a] = quad(eye[a])
+    for a in range(d):
+        for b in range(a + 1, d):
+            A[a, b] = A[b, a] = 0.5 * (quad(eye[a] + eye[b]) - A[a, a] - A[b, b])
+    return A
 
 
 def _set_b(c, B):

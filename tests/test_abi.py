@@ -98,3 +98,21 @@ def test_host_coefficient_marshalling():
     assert (c.d, c.fmt, list(c.tk.r)[:2], list(c.tk.N)[:2]) == (2, L.LRFG_TUCKER, [2, 3], [5, 7])
     with pytest.raises(ValueError):
         _set_b(c, np.ones((3, 3)))
+
+
+def test_polarised_tensor_recovers_a_symmetric_matrix():
+    """Host logic of Problem.aeff_tensor: the tensor from its quadratic form by polarisation."""
+    import numpy as np
+    from paper_1902_07455_gb300 import polarised_tensor
+    rng = np.random.default_rng(3)
+    for d in (2, 3):
+        M = rng.standard_normal((d, d))
+        A = M @ M.T + d * np.eye(d)
+        calls = []
+
+        def quad(E):
+            calls.append(tuple(E))
+            return float(E @ A @ E)
+        T = polarised_tensor(d, quad)
+        assert np.allclose(T, A, rtol=1e-14, atol=1e-14)
+        assert len(calls) == d * (d + 1) // 2

@@ -144,3 +144,16 @@ def test_energy_bound_lowrank_above_full(ctx):
         assert res.Aeff >= full.Aeff * (1 - 1e-10)
         prev = res.Aeff
     assert prev - full.Aeff < 1e-2 * full.Aeff
+
+
+def test_aeff_tensor_by_polarisation(ctx):
+    """The homogenised tensor from d (d + 1) / 2 solves against the oracle's solves for the same E."""
+    d, N = 2, 31
+    A = lognormal_grf(d, N, ell=0.2, seed=5)
+    T = ctx.problem(A, lrfg.FULL, tol=1e-10, maxit=2000).aeff_tensor()
+    ref11 = fg.solve_gani(A, [1.0, 0.0], tol=1e-10)["Aeff"]
+    ref22 = fg.solve_gani(A, [0.0, 1.0], tol=1e-10)["Aeff"]
+    ref_s = fg.solve_gani(A, [1.0, 1.0], tol=1e-10)["Aeff"]
+    assert abs(T[0, 0] - ref11) <= 1e-8 * ref11 and abs(T[1, 1] - ref22) <= 1e-8 * ref22
+    assert abs(T[0, 1] - 0.5 * (ref_s - ref11 - ref22)) <= 1e-8 * ref11
+    assert T[0, 1] == T[1, 0]
