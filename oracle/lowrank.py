@@ -33,9 +33,12 @@ stopped when the residual norm fails to decrease (Sec. 4.3) — the iterate with
 is returned — or when it drops below a relative tolerance, or after ``maxit`` iterations.
 
 Readings (listed in the design notes): every T truncates to the fixed solution rank r (Sec. 4.2 fixes
-the rank); the residual is recomputed from its definition each iteration and truncated; inner products
-of Fourier tensors take the real part; the relative error of Eq. (rel_error) is reported as an absolute
-value.
+the rank), or with ``rank_tol`` to the smallest ranks within that relative tolerance (tol / sqrt(d - 1) per
+TT bond, tol / sqrt(d) per Tucker mode); the residual is recomputed from its definition each iteration
+and truncated; inner products of Fourier tensors take the real part; the relative error of Eq.
+(rel_error) is reported as an absolute value.  Also here: a constant anisotropic part B of the material
+(Sec. 4.4), the rank-adapting iteration Sec. 4.3 proposes (``minres_rank_adaptive``), and Ga in TT format
+(``LowRankGaTT``, Sec. 2.2.3 with the truncations of Eq. (Pls_lowrank)).
 """
 from __future__ import annotations
 
