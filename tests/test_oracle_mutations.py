@@ -185,3 +185,78 @@ def test_rank_adaptation_without_rebuilding_the_rhs(monkeypatch):
         return cache[key]
     monkeypatch.setattr(lr.LowRankGaNi, "rhs", frozen)
     _must_fail(tl.test_rank_adaptive_minres_pins)
+
+
+# ---- planted mistakes in the placement of the truncations and in the stopping rule ------------------
+import tests.test_oracle_truncation_placement as tp  # noqa: E402
+
+
+def _gani_apply_variant(drop_sum_T=False, T_before_material=False, T_before_pinv=False):
+    def apply(self, vh):
+        f = self.f
+        acc = None
+        for a in range(self.d):
+            e = f.idft(f.mmul(vh, a, 2j * np.pi * self.K[a]))
+            w = f.had(self.a, self.T(e)) if T_before_material else self.T(f.had(self.a, e))
+            term = f.mmul(f.dft(w), a, -2j * np.pi * self.K[a])
+            acc = term if acc is None else f.add(acc, term)
+        s = acc if drop_sum_T else self.T(acc)
+        return f.had(self.Pinv, self.T(s)) if T_before_pinv else self.T(f.had(self.Pinv, s))
+    return apply
+
+
+@pytest.mark.parametrize("variant", [dict(drop_sum_T=True), dict(T_before_material=True),
+                                     dict(T_before_pinv=True)])
+def test_misplaced_truncation_in_the_operator(monkeypatch, variant):
+    monkeypatch.setattr(lr.LowRankGaNi, "apply", _gani_apply_variant(**variant))
+    _must_fail(tp.test_gani_apply_truncations_where_eq_pls_lowrank_puts_them, 3, 7, 2, 2)
+
+
+def test_right_hand_side_truncated_before_the_preconditioner(monkeypatch):
+    def bad(self, E):
+        f = self.f
+        ah = f.dft(self.a)
+        acc = None
+        for a in range(self.d):
+            term = f.mmul(f.scale(ah, float(E[a])), a, -2j * np.pi * self.K[a])
+            acc = term if acc is None else f.add(acc, term)
+        return f.scale(f.had(self.Pinv, self.T(acc)), -1.0)
+    monkeypatch.setattr(lr.LowRankGaNi, "rhs", bad)
+    _must_fail(tp.test_gani_rhs_truncation_after_the_preconditioner, 2, 15, 3, 3)
+
+
+def test_ga_tt_without_the_truncation_on_the_double_grid(monkeypatch):
+    def bad(self, vh):
+        f = self.f
+        acc = None
+        for a in range(self.d):
+            w = f.had(self.At, self._grad_double(vh, a))      # T dropped
+            term = f.mmul(self._project(f.dft(w)), a, -2j * np.pi * self.K[a])
+            acc = term if acc is None else f.add(acc, term)
+        return self.T(f.had(self.Pinv, self.T(acc)))
+    monkeypatch.setattr(lr.LowRankGaTT, "apply", bad)
+    _must_fail(tp.test_ga_tt_apply_and_rhs_by_full_grids, 2, 9, 2, 2)
+
+
+def test_minres_returning_the_last_iterate():
+    """The iteration stops when the residual rises but hands back the last iterate, not the best."""
+    def bad_minres(op, E, tol=1e-10, maxit=200, stop_on_increase=True, callback=None):
+        f = op.f
+        b = op.rhs(E)
+        nb = f.norm(b)
+        u, hist, it, best = f.zeros(op.shape), [], 0, np.inf
+        while True:
+            r = op.T(f.add(b, f.scale(op.apply(u), -1.0))) if it > 0 else b
+            nr = f.norm(r) / nb
+            hist.append(nr)
+            if callback is not None:
+                callback(it, u, nr)
+            if nr >= best or nr <= tol or it >= maxit:
+                break
+            best = nr
+            q = op.apply(r)
+            omega = np.real(f.dot(q, r)) / np.real(f.dot(q, q))
+            u = op.T(f.add(u, f.scale(r, omega))) if it > 0 else op.T(f.scale(r, omega))
+            it += 1
+        return dict(u=u, iters=it, rel_resid=nr, history=hist, Aeff=op.homogenised_coefficient(u, E))
+    _must_fail(tp.minres_stop_pin, bad_minres)
