@@ -238,11 +238,13 @@ lrfg_status lrfg_tucker_round_tol(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax,
 lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);
 
 /* The same inner product as lrfg_tt_dot, for callers that cannot allocate device memory when they need
- * it: code running while a stream is captured into a CUDA graph, applications whose own allocator owns
- * all device memory, loops that must not wait on the driver's allocator.  (The paper has no counterpart:
- * this is a calling convention of the library, not part of the method.)
+ * it: applications whose own allocator owns all device memory, and loops that must not wait on the
+ * driver's allocator.  (The paper has no counterpart: this is a calling convention of the library, not
+ * part of the method.)
  *   - allocates nothing: the contraction intermediates live in one file-scope 4 MiB device array
- *     (524288 doubles) that every GPU loading the library holds until the process exits;
+ *     (524288 doubles) that every GPU loading the library holds until the process exits; its products
+ *     run in one pass over the contracted index (no split-K partial sums), and nothing is taken from the
+ *     context's pool; no profiling events are recorded (launches are still counted);
  *   - x, y: device carriages as for lrfg_tt_dot; `result` is a DEVICE pointer to one double, written
  *     asynchronously on the context's stream (nothing is synchronised or copied to the host);
  *   - the intermediates must fit: 2 max_j(r_x[j] r_y[j]) + max_j(r_y[j] N[j] r_x[j+1]) <= 524288
@@ -299,6 +301,16 @@ lrfg_status lrfg_problem_solve(lrfg_problem* problem, const double* E, lrfg_resu
 
 /* A_eff E.E = (1/|N|) sum_k a(x_k) |E + e(x_k)|^2, e = F^{-1} grad^ u (Eq. (homog), Sec. 2.2.2). */
 lrfg_status lrfg_problem_aeff(lrfg_problem* problem, const double* E, const lrfg_field* u, double* Aeff);
+
+/* The homogenised tensor A_eff (d x d, symmetric) of Eq. (homog): the diagonal A_aa from the solves with
+ * E = e_a, each off-diagonal entry by polarisation of the quadratic form q(E) = A_eff E.E (Sec. 2.1),
+ * A_ab = (q(e_a + e_b) - q(e_a) - q(e_b)) / 2 — d (d + 1) / 2 solves with the problem's options.
+ *   A        host array of d * d doubles, row-major, written on return (caller-owned);
+ *   results  NULL, or a host array of d (d + 1) / 2 lrfg_result, one per solve in the order
+ *            (a, b) = (0,0), (0,1), .., (0,d-1), (1,1), .., (d-1,d-1) with E = e_a (+ e_b when b != a).
+ * Returns the first failing solve's status (A is then not written), LRFG_ENOCONV when some solve
+ * reached its iteration cap above the tolerance (A is still written), else LRFG_OK. */
+lrfg_status lrfg_problem_aeff_tensor(lrfg_problem* problem, double* A, lrfg_result* results);
 
 /* One-shot convenience: create a problem, solve, free it. */
 lrfg_status lrfg_solve(lrfg_ctx* ctx, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,

@@ -292,8 +292,9 @@ class Context:
 
     def tt_dot_noalloc(self, x: TTensor, y: TTensor, out):
         """<x, y> into the CUDA float64 tensor ``out`` (one element) without any device allocation by the
-        library: for callers that cannot allocate at that point (stream capture, a foreign allocator).
-        Asynchronous on the context's stream; intermediates live in a fixed 4 MiB device array."""
+        library: for callers that cannot allocate at that point (an application-owned allocator, loops that
+        must not wait on the driver's allocator).  Asynchronous on the context's stream; intermediates live
+        in a fixed 4 MiB device array shared by all calls."""
         torch = _torch()
         if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
             raise ValueError("out must be a CUDA float64 tensor with at least one element")
@@ -537,11 +538,21 @@ class Problem:
         self.ctx.check(self.ctx.lib.lrfg_problem_aeff(self.h, _dvec(E), field.h, C.byref(out)))
         return out.value
 
-    def aeff_tensor(self) -> np.ndarray:
-        """The homogenised tensor A_eff (d x d): the diagonal from the solves with E = e_a, the off-diagonal
-        entries by polarisation, A_ab = (A_eff(e_a + e_b) - A_aa - A_bb) / 2 (A_eff E.E is a quadratic form
-        in E, Sec. 2.1), so d (d + 1) / 2 solves."""
-        return polarised_tensor(self.d, lambda E: self.solve(E, want_field=False)[0].Aeff)
+    def aeff_tensor(self, with_results: bool = False):
+        """The homogenised tensor A_eff (d x d) of Eq. (homog) by lrfg_problem_aeff_tensor: d (d + 1) / 2
+        solves in the library, the off-diagonal entries by polarisation of the quadratic form A_eff E.E
+        (Sec. 2.1).  ``with_results``: also return the per-solve results."""
+        d = self.d
+        A = (C.c_double * (d * d))()
+        res = (L.lrfg_result * (d * (d + 1) // 2))()
+        st = self.ctx.lib.lrfg_problem_aeff_tensor(self.h, A, res)
+        if st not in (L.LRFG_OK, L.LRFG_ENOCONV):
+            self.ctx.check(st)
+        T = np.array(list(A)).reshape(d, d)
+        if not with_results:
+            return T
+        return T, [Result(r.Aeff, r.iters, r.rel_resid, bool(r.converged), r.applies, list(r.ranks)[: d + 1],
+                          r.seconds, st) for r in res]
 
     def free(self):
         if self.h and self.ctx.h:
@@ -553,19 +564,6 @@ class Problem:
             self.free()
         except Exception:
             pass
-
-
-def polarised_tensor(d: int, quad) -> np.ndarray:
-    """Symmetric d x d tensor from its quadratic form quad(E) = E.A E: quad(e_a) on the diagonal and
-    (quad(e_a + e_b) - quad(e_a) - quad(e_b)) / 2 off it."""
-    A = np.zeros((d, d))
-    eye = np.eye(d)
-    for a in range(d):
-        A[a, a] = quad(eye[a])
-    for a in range(d):
-        for b in range(a + 1, d):
-            A[a, b] = A[b, a] = 0.5 * (quad(eye[a] + eye[b]) - A[a, a] - A[b, b])
-    return A
 
 
 def _set_b(c, B):

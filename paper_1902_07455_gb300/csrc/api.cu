@@ -1500,6 +1500,39 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field
   });
 }
 
+// The homogenised tensor of Eq. (homog): A_eff E.E is a quadratic form in E (Sec. 2.1), so its diagonal comes
+// from the solves with E = e_a and every off-diagonal entry from one more solve by polarisation,
+// A_ab = (q(e_a + e_b) - q(e_a) - q(e_b)) / 2, q(E) = A_eff E.E: d (d + 1) / 2 solves in all.
+lrfg_status lrfg_problem_aeff_tensor(lrfg_problem* P, double* A, lrfg_result* results) {
+  if (!P) return LRFG_EINVAL;
+  if (!A) {
+    P->ctx->last_error = "null argument";
+    return LRFG_EINVAL;
+  }
+  const int d = P->d;
+  double q[3][3] = {};
+  bool noconv = false;
+  int k = 0;
+  for (int a = 0; a < d; ++a)
+    for (int b = a; b < d; ++b, ++k) {
+      double E[3] = {0.0, 0.0, 0.0};
+      E[a] = 1.0;
+      if (b != a) E[b] = 1.0;
+      lrfg_result r{};
+      const lrfg_status st = lrfg_problem_solve(P, E, &r, nullptr);
+      if (st == LRFG_ENOCONV) noconv = true;
+      else if (st != LRFG_OK) return st;
+      if (results) results[k] = r;
+      q[a][b] = r.Aeff;
+    }
+  for (int a = 0; a < d; ++a) {
+    A[a * d + a] = q[a][a];
+    for (int b = a + 1; b < d; ++b) A[a * d + b] = A[b * d + a] = 0.5 * (q[a][b] - q[a][a] - q[b][b]);
+  }
+  P->ctx->last_error.clear();
+  return noconv ? LRFG_ENOCONV : LRFG_OK;
+}
+
 lrfg_status lrfg_solve(lrfg_ctx* ctx, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,
                        lrfg_result* res, lrfg_field** u_out) {
   lrfg_problem* P = nullptr;

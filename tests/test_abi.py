@@ -100,19 +100,12 @@ def test_host_coefficient_marshalling():
         _set_b(c, np.ones((3, 3)))
 
 
-def test_polarised_tensor_recovers_a_symmetric_matrix():
-    """Host logic of Problem.aeff_tensor: the tensor from its quadratic form by polarisation."""
-    import numpy as np
-    from paper_1902_07455_gb300 import polarised_tensor
-    rng = np.random.default_rng(3)
-    for d in (2, 3):
-        M = rng.standard_normal((d, d))
-        A = M @ M.T + d * np.eye(d)
-        calls = []
-
-        def quad(E):
-            calls.append(tuple(E))
-            return float(E @ A @ E)
-        T = polarised_tensor(d, quad)
-        assert np.allclose(T, A, rtol=1e-14, atol=1e-14)
-        assert len(calls) == d * (d + 1) // 2
+def test_aeff_tensor_entry_point_rejects_a_null_problem(lib):
+    """lrfg_problem_aeff_tensor, called directly through ctypes without a GPU: a null problem is an invalid
+    argument, and nothing is written to the output array."""
+    from paper_1902_07455_gb300 import _lib as L
+    f = lib.lrfg_problem_aeff_tensor
+    f.restype, f.argtypes = L.SIGNATURES["lrfg_problem_aeff_tensor"]
+    A = (ctypes.c_double * 9)(*([7.0] * 9))
+    assert f(None, A, None) == L.LRFG_EINVAL
+    assert list(A) == [7.0] * 9

@@ -146,14 +146,27 @@ def test_energy_bound_lowrank_above_full(ctx):
     assert prev - full.Aeff < 1e-2 * full.Aeff
 
 
-def test_aeff_tensor_by_polarisation(ctx):
-    """The homogenised tensor from d (d + 1) / 2 solves against the oracle's solves for the same E."""
-    d, N = 2, 31
+@pytest.mark.parametrize("d,N", [(2, 31), (3, 9)])
+def test_aeff_tensor_by_polarisation(ctx, d, N):
+    """The homogenised tensor from d (d + 1) / 2 solves in lrfg_problem_aeff_tensor against the oracle's
+    solves for the same E: the diagonal from E = e_a, the off-diagonal entries by polarisation."""
     A = lognormal_grf(d, N, ell=0.2, seed=5)
-    T = ctx.problem(A, lrfg.FULL, tol=1e-10, maxit=2000).aeff_tensor()
-    ref11 = fg.solve_gani(A, [1.0, 0.0], tol=1e-10)["Aeff"]
-    ref22 = fg.solve_gani(A, [0.0, 1.0], tol=1e-10)["Aeff"]
-    ref_s = fg.solve_gani(A, [1.0, 1.0], tol=1e-10)["Aeff"]
-    assert abs(T[0, 0] - ref11) <= 1e-8 * ref11 and abs(T[1, 1] - ref22) <= 1e-8 * ref22
-    assert abs(T[0, 1] - 0.5 * (ref_s - ref11 - ref22)) <= 1e-8 * ref11
-    assert T[0, 1] == T[1, 0]
+    P = ctx.problem(A, lrfg.FULL, tol=1e-10, maxit=2000)
+    T, results = P.aeff_tensor(with_results=True)
+    assert len(results) == d * (d + 1) // 2
+    eye = np.eye(d)
+    q = {(a, a): fg.solve_gani(A, eye[a], tol=1e-10)["Aeff"] for a in range(d)}
+    for a in range(d):
+        assert abs(T[a, a] - q[a, a]) <= 1e-8 * q[a, a]
+        for b in range(a + 1, d):
+            s = fg.solve_gani(A, eye[a] + eye[b], tol=1e-10)["Aeff"]
+            assert abs(T[a, b] - 0.5 * (s - q[a, a] - q[b, b])) <= 1e-8 * q[a, a]
+            assert T[a, b] == T[b, a]
+    assert np.all(np.linalg.eigvalsh(T) > 0)
+    # the same call straight through ctypes, without results
+    from paper_1902_07455_gb300 import _lib as L
+    import ctypes
+    out = (ctypes.c_double * (d * d))()
+    assert ctx.lib.lrfg_problem_aeff_tensor(P.h, out, None) == L.LRFG_OK
+    assert np.array_equal(np.array(list(out)).reshape(d, d), T)
+    P.free()

@@ -124,6 +124,8 @@ def test_rank_adaptive_tucker_cp_matches_oracle(ctx, fmt, d, N, cap, start, step
     res, _ = P.solve(E, want_field=False)
     assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
     # near stagnation at the cap the residual changes by parts in 1e6 per step, so "fails to decrease" may
-    # fire a few steps apart on the two sides (Gram-SVD vs QR+SVD rounding); the residual reached is no worse
-    # than the oracle's (up to a factor 2), and may be lower when the GPU side iterates longer
-    assert res.rel_resid <= 2.0 * ref["rel_resid"], (res.rel_resid, ref["rel_resid"], res.iters, ref["iters"])
+    # fire a few steps apart on the two sides (Gram-SVD vs QR+SVD rounding).  The floor the residual stagnates
+    # at is set by the truncation to the cap, which both sides share, so iterating a few steps longer moves
+    # the residual reached by a modest factor either way, never by orders of magnitude
+    ratio = res.rel_resid / ref["rel_resid"]
+    assert 0.25 <= ratio <= 2.0, (res.rel_resid, ref["rel_resid"], res.iters, ref["iters"])
