@@ -250,6 +250,36 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
                      sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
 }
 
+// The same product in one pass over K (no split-K): it needs no partial-sum workspace, so it takes nothing
+// from the context's pool.  For callers that must not allocate.
+void gemm_nosplit(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+                  long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+                  int batch) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (K <= 0) {
+    LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
+                scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
+                    C, M, N, ldc, sC, batch, beta));
+    return;
+  }
+  LRFG_REQUIRE(batch < 65536, "gemm batch too large");
+  const int nsm = ctx->num_sms > 0 ? ctx->num_sms : 152;
+  const long long tiles64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * batch;
+  const int tile = tiles64 < nsm ? 32 : 64;
+  const int bmn = (M + tile - 1) / tile, bnn = (N + tile - 1) / tile;
+  LRFG_REQUIRE(bmn < 65536, "gemm too many row blocks");
+  const int kchunk = ((K + GK - 1) / GK) * GK;
+  const double flops = 2.0 * M * N * (double)K * batch;
+  const double bytes = sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
+  dim3 grid(bnn, bmn, batch);
+  if (tile == 32)
+    launch_dgemm<32>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                     sC, 1, kchunk, nullptr, 1, nullptr, 1, nullptr, nullptr);
+  else
+    launch_dgemm<64>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                     sC, 1, kchunk, nullptr, 1, nullptr, 1, nullptr, nullptr);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Symmetric eigensolver, two stages:
 //  1. cyclic two-sided Jacobi with the round-robin (circle) ordering, so that each round applies m'/2

@@ -1,11 +1,11 @@
 // Tensor-train inner product that allocates no device memory.
 //
-// Some callers cannot allocate device memory at the point where they need an inner product: code that
-// runs while a CUDA stream is being captured into a graph (where a cudaMalloc would break or end the
-// capture), host applications that hand all device memory to their own allocator and forbid libraries
-// from taking more, and real-time loops that must not block on the driver's allocator.  For them,
-// lrfg_tt_dot_noalloc computes the same contraction as lrfg_tt_dot with its intermediates in one
-// file-scope device array of fixed size instead of the context's pool.
+// Some callers cannot allocate device memory at the point where they need an inner product: host
+// applications that hand all device memory to their own allocator and forbid libraries from taking more,
+// and real-time loops that must not block on the driver's allocator.  For them, lrfg_tt_dot_noalloc
+// computes the same contraction as lrfg_tt_dot with its intermediates in one file-scope device array of
+// fixed size instead of the context's pool.  Its products run in one pass over the contracted index (no
+// split-K partial sums, which would need a workspace from the pool), and it records no profiling events.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -63,14 +63,22 @@ extern "C" lrfg_status lrfg_tt_dot_noalloc(lrfg_ctx* ctx, const lrfg_tt* x, cons
     double* scratch = tt_dot_scratch_address(ctx->device);
     double* Wbuf[2] = {scratch, scratch + maxW};
     double* V = scratch + 2 * maxW;
+    // no events while it runs: a profiled context would otherwise record a pair per launch
+    const bool profiling = ctx->profiling;
+    ctx->profiling = false;
+    struct Restore {
+      lrfg_ctx* c;
+      bool p;
+      ~Restore() { c->profiling = p; }
+    } restore{ctx, profiling};
     // W_0 = [1]; each carriage: V = W^T x_j (c x n b), W' = V^T y_j (b x e) contracting over (c n)
     fill(ctx, Wbuf[0], 1.0, 1);
     for (int j = 0; j < d; ++j) {
       const int a = x->r[j], b = x->r[j + 1], c = y->r[j], e = y->r[j + 1], n = x->N[j];
       double* W = Wbuf[j & 1];
       double* Wn = (j == d - 1) ? result : Wbuf[(j + 1) & 1];
-      gemm(ctx, 1, 0, c, n * b, a, 1.0, W, c, 0, x->cores[j], n * b, 0, 0.0, V, n * b, 0);
-      gemm(ctx, 1, 0, b, e, c * n, 1.0, V, b, 0, y->cores[j], e, 0, 0.0, Wn, e, 0);
+      gemm_nosplit(ctx, 1, 0, c, n * b, a, 1.0, W, c, 0, x->cores[j], n * b, 0, 0.0, V, n * b, 0);
+      gemm_nosplit(ctx, 1, 0, b, e, c * n, 1.0, V, b, 0, y->cores[j], e, 0, 0.0, Wn, e, 0);
     }
     ctx->last_error.clear();
     return LRFG_OK;

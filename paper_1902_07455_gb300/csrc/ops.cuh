@@ -47,6 +47,10 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
 void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
               long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
               int batch, const int* dynM, int mulM, const int* dynN, int mulN);
+// The same product in one pass over K (never split): no partial-sum workspace, nothing taken from the pool.
+void gemm_nosplit(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+                  long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+                  int batch = 1);
 // symmetric eigen-decomposition of `batch` m x m matrices (row-major, stride m*m): eigenvalues in
 // descending order into w (stride m), eigenvectors as the COLUMNS of V (row-major m x m, stride m*m).
 // A is left unchanged.  syevj: FP64 Jacobi (absolute accuracy eps64 ||A||).  syevj_mixed: FP32 Jacobi +
