@@ -464,9 +464,16 @@ class LowRankGaNi:
     the exponential-sum accuracy ``pinv_eps`` of P~^-1.  All tensors are Fourier coefficient tensors
     except the coefficient, which holds grid values (as in the paper's A~)."""
 
-    def __init__(self, a_lr, shape, fmt="tt", rank=10, pinv_eps=0.1, rank_tol=None, B=None):
+    def __init__(self, a_lr, shape, fmt="tt", rank=10, pinv_eps=0.1, rank_tol=None, B=None, sketch=None):
         self.f = FORMATS[fmt]
         self.fmt = fmt
+        # randomised rounding of the products (TT only): (oversampling p, seed) or None.  The material
+        # products and the P~^-1 product are then truncated by ``sketch.tt_round_sketch`` with a sketch of
+        # ranks rank + p, acting on grid values (the material product is formed there; the P~^-1 product
+        # is mapped there by F^-1 and back by F); every other T stays the deterministic rounding.
+        if sketch is not None and fmt != "tt":
+            raise ValueError("the randomised rounding is defined for the TT format")
+        self.sketch = None if sketch is None else (int(sketch[0]), int(sketch[1]))
         self.a = a_lr
         # constant anisotropic part: A~(x) = a(x) I + B (the modified materials of Sec. 4.4)
         self.B = None if B is None else np.asarray(B, dtype=np.float64)
@@ -484,6 +491,22 @@ class LowRankGaNi:
     def T(self, x):
         return self.f.round(x, rmax=self.rank, tol=self.rank_tol)
 
+    def T_values(self, x):
+        """T of a product held as grid values: the randomised rounding when ``sketch`` is set, else T."""
+        if self.sketch is None:
+            return self.T(x)
+        from . import sketch as _sk
+        over, seed = self.sketch
+        omega = _sk.sketch_tt(self.shape, self.rank + over, seed)
+        return _sk.tt_round_sketch(x, omega, rmax=self.rank, tol=self.rank_tol)
+
+    def T_pinv(self, sh):
+        """T P~^-1 s for a Fourier tensor s: with ``sketch`` the product is truncated as grid values."""
+        f = self.f
+        if self.sketch is None:
+            return self.T(f.had(self.Pinv, sh))
+        return f.dft(self.T_values(f.idft(f.had(self.Pinv, sh))))
+
     def apply(self, vh):
         """T P~^-1 T grad^* F T A~ F^-1 grad^ v  (Eq. (Pls_lowrank)).  With the constant anisotropic part
         B, component a of A~ e is a e_a + sum_b B[a, b] e_b (zero entries of B skipped)."""
@@ -500,12 +523,12 @@ class LowRankGaNi:
                 for b in range(self.d):
                     if self.B[a, b] != 0.0:
                         ae = f.add(ae, f.scale(es[b], float(self.B[a, b])))
-            w = self.T(ae)                                  # T A~ e_a
+            w = self.T_values(ae)                           # T A~ e_a
             wh = f.dft(w)                                   # F, mode-wise
             term = f.mmul(wh, a, -2j * np.pi * self.K[a])   # divergence, mode a
             acc = term if acc is None else f.add(acc, term)
         s = self.T(acc)                                     # T after the sum
-        return self.T(f.had(self.Pinv, s))                  # T P~^-1
+        return self.T_pinv(s)                               # T P~^-1
 
     def rhs(self, E):
         """b~ = - T P~^-1 grad^* F A~ E  (Eq. (Pls_lowrank)).  A constant anisotropic part adds the constant
@@ -520,7 +543,7 @@ class LowRankGaNi:
             acc = term if acc is None else f.add(acc, term)
         if acc is None:
             return f.zeros(self.shape)
-        return f.scale(self.T(f.had(self.Pinv, acc)), -1.0)
+        return f.scale(self.T_pinv(acc), -1.0)
 
     def homogenised_coefficient(self, uh, E) -> float:
         """A_eff E.E = (1/|N|) sum_k A~(x_k)(E + e(x_k)).(E + e(x_k)) with e_a = F^-1 grad^_a u^ (Eq. (homog)),

@@ -260,3 +260,37 @@ def test_minres_returning_the_last_iterate():
             it += 1
         return dict(u=u, iters=it, rel_resid=nr, history=hist, Aeff=op.homogenised_coefficient(u, E))
     _must_fail(tp.minres_stop_pin, bad_minres)
+
+
+# ---- planted mistakes in the randomised rounding ------------------------------------------------------
+import tests.test_oracle_sketch as tsk  # noqa: E402
+from oracle import sketch as sk_mod  # noqa: E402
+
+
+def _bad_round_sketch(carry=True, final=True, right_sweep_from_left=False):
+    def bad(y, omega, rmax=None, tol=None):
+        d = len(y)
+        W = [None] * d
+        W[d - 1] = np.ones((1, 1))
+        for j in range(d - 1, 0, -1):
+            src = y[d - j] if right_sweep_from_left and y[d - j].shape == y[j].shape else y[j]
+            W[j - 1] = np.einsum("anb,bm,lnm->al", src, W[j], omega[j], optimize=True)
+        x = [np.array(G, copy=True) for G in y]
+        for j in range(d - 1):
+            a, n, b = x[j].shape
+            X = x[j].reshape(a * n, b)
+            Q, _ = np.linalg.qr(X @ W[j])
+            M = Q.conj().T @ X
+            x[j] = Q.reshape(a, n, Q.shape[1])
+            if carry:
+                x[j + 1] = np.tensordot(M, x[j + 1], axes=([1], [0]))
+            else:
+                x[j + 1] = np.tensordot(np.eye(Q.shape[1], b), x[j + 1], axes=([1], [0]))
+        return lr.tt_round(x, rmax=rmax, tol=tol) if final else x
+    return bad
+
+
+@pytest.mark.parametrize("variant", [dict(carry=False), dict(final=False)])
+def test_randomised_rounding_slips(monkeypatch, variant):
+    monkeypatch.setattr(sk_mod, "tt_round_sketch", _bad_round_sketch(**variant))
+    _must_fail(tsk.test_exact_when_the_sketch_covers_the_ranks, (7, 9, 11), [4, 5], 6, 3)

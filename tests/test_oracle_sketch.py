@@ -1,0 +1,106 @@
+"""Pins of the oracle's randomised TT rounding (oracle/sketch.py) and of its use in the operator (CPU only).
+
+* SplitMix64 reproduces the published first outputs of stream 0.
+* When the input's TT ranks do not exceed the sketch ranks, the sketch spans every unfolding exactly and the
+  randomised rounding equals the deterministic TT rounding of App. A.3.3 (expanded, to rounding).
+* Above that, it is near-optimal: its error stays within a small factor of the deterministic rounding's
+  (the probabilistic bound of the randomised range finder with oversampling), and its output is
+  left-orthonormal with the requested ranks.
+* In the operator of Eq. (Pls_lowrank): with product ranks below the sketch ranks the sketched operator and
+  right-hand side equal the deterministic ones, and a minimal-residual solve with the sketched rounding
+  reaches the deterministic solve's A_eff.
+"""
+import numpy as np
+import pytest
+
+from oracle import lowrank as lr
+from oracle import sketch as sk
+from synthetic import random_tt, smoothed_cube
+
+
+def test_splitmix64_published_outputs():
+    # first three outputs of SplitMix64 seeded with 0 (the reference implementation's test values)
+    v = sk.splitmix64(0, np.arange(3, dtype=np.uint64))
+    assert [int(x) for x in v] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_sketch_entries_are_rademacher_and_reproducible():
+    om = sk.sketch_tt((9, 11, 13), 7, seed=5)
+    assert [G.shape for G in om] == [(1, 9, 7), (7, 11, 7), (7, 13, 1)]
+    allv = np.concatenate([G.ravel() for G in om])
+    assert set(np.unique(allv)) == {-1.0, 1.0}
+    assert abs(allv.mean()) < 0.1
+    again = sk.sketch_tt((9, 11, 13), 7, seed=5)
+    assert all(np.array_equal(a, b) for a, b in zip(om, again))
+    other = sk.sketch_tt((9, 11, 13), 7, seed=6)
+    assert not np.array_equal(om[1], other[1])
+
+
+def _rel(x, y):
+    return np.linalg.norm(lr.tt_full(x) - lr.tt_full(y)) / np.linalg.norm(lr.tt_full(y))
+
+
+@pytest.mark.parametrize("shape,ranks,ell,rmax", [((9, 11), [5], 7, 3), ((7, 9, 11), [4, 5], 6, 3),
+                                                  ((7, 9, 11), [4, 5], 5, 5)])
+def test_exact_when_the_sketch_covers_the_ranks(shape, ranks, ell, rmax):
+    y = random_tt(shape, ranks, seed=3)
+    om = sk.sketch_tt(shape, ell, seed=19)
+    got = sk.tt_round_sketch(y, om, rmax=rmax)
+    ref = lr.tt_round(y, rmax=rmax)
+    # (a bond where the tensor's rank is below rmax may carry zero singular values on either side)
+    assert all(r <= rmax for r in lr.tt_ranks(got))
+    assert _rel(got, ref) <= 1e-11
+
+
+def test_near_optimal_above_the_sketch_ranks():
+    # a Khatri-Rao product of rank 6 x 6 = 36 (the kind of tensor the solver rounds) truncated to rank 6
+    shape = (15, 17, 19)
+    x = random_tt(shape, [6, 6], seed=1)
+    y = random_tt(shape, [6, 6], seed=2)
+    z = lr.tt_hadamard(x, y)
+    ref = lr.tt_round(z, rmax=6)
+    e_det = _rel(ref, z)
+    for seed in range(4):
+        got = sk.tt_round_sketch(z, sk.sketch_tt(shape, 6 + 8, seed=seed), rmax=6)
+        assert lr.tt_ranks(got) == [1, 6, 6, 1]
+        e = _rel(got, z)
+        assert e <= 1.5 * e_det, (e, e_det)
+        for G in got[:-1]:  # left-orthonormal carriages
+            a, n, b = G.shape
+            M = G.reshape(a * n, b)
+            assert np.allclose(M.T @ M, np.eye(b), atol=1e-12)
+
+
+def test_sketch_with_tolerance_keeps_the_bound():
+    shape = (13, 15, 17)
+    z = lr.tt_hadamard(random_tt(shape, [5, 5], seed=7), random_tt(shape, [5, 5], seed=8))
+    tol = 0.05
+    got = sk.tt_round_sketch(z, sk.sketch_tt(shape, 30, seed=1), rmax=20, tol=tol)
+    assert _rel(got, z) <= tol * 1.0001
+    assert max(lr.tt_ranks(got)) <= 20
+
+
+def _ops(d, N, rank, over):
+    _, terms, w = smoothed_cube(d, N, contrast=10.0, full=False)
+    a = lr.tt_from_separable(terms, w)
+    det = lr.LowRankGaNi(a, (N,) * d, fmt="tt", rank=rank, pinv_eps=0.3)
+    skt = lr.LowRankGaNi(a, (N,) * d, fmt="tt", rank=rank, pinv_eps=0.3, sketch=(over, 11))
+    return det, skt
+
+
+def test_sketched_operator_equals_deterministic_when_the_sketch_covers_the_products():
+    # coefficient rank 2, operand rank 2: material products of rank 4, P~^-1 products of rank R * 2, all
+    # below the sketch ranks rank + p, so every sketched T is the deterministic one
+    det, skt = _ops(2, 15, rank=2, over=40)
+    v = [np.asarray(G, dtype=np.complex128) for G in random_tt((15, 15), [2], seed=4)]
+    assert _rel(skt.apply(v), det.apply(v)) <= 1e-10
+    E = np.array([1.0, 0.0])
+    assert _rel(skt.rhs(E), det.rhs(E)) <= 1e-10
+
+
+def test_sketched_minres_reaches_the_deterministic_aeff():
+    det, skt = _ops(2, 31, rank=6, over=8)
+    E = np.array([1.0, 0.0])
+    a = lr.minres(det, E, maxit=40)
+    b = lr.minres(skt, E, maxit=40)
+    assert abs(a["Aeff"] - b["Aeff"]) <= 1e-5 * a["Aeff"], (a["Aeff"], b["Aeff"])
