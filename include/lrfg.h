@@ -141,6 +141,12 @@ typedef struct {
                            A_eff is the exact integral of a |E + grad u|^2.  N_j and the double grid 2N_j - 1
                            must have prime factors <= 31 (LRFG_ENOTSUP otherwise; e.g. N = 13, 25, 63, 81,
                            189, 363) */
+  int sketch_over;      /* LRFG_TT with LRFG_GANI: 0 = every T is the deterministic TT rounding (App. A.3.3).
+                           p > 0: the material products and the P~^-1 product (the truncations whose input rank
+                           is r_A r and R_P r) use the randomised rounding of lrfg_tt_round_sketch with a sketch
+                           of ranks rank + p (products never formed); the other truncations stay deterministic.
+                           An extension of the paper's method (Al Daas et al. 2023); LRFG_ENOTSUP elsewhere */
+  unsigned int sketch_seed; /* SplitMix64 stream of that sketch */
 } lrfg_opts;
 
 typedef struct {
@@ -233,6 +239,25 @@ lrfg_status lrfg_tucker_round(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, lrf
  * core unfolding have norm <= tol / sqrt(d) of the tensor's (App. A.2.3); out->r holds the ranks, the
  * core and factors are written contiguously with them. */
 lrfg_status lrfg_tucker_round_tol(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax, double tol, lrfg_tucker* out);
+
+/* Randomised truncation of a TT with device carriages ("randomize-then-orthogonalize", Al Daas, Ballard, Cazeaux,
+ * Hallman, Miedlar, Pasha, Reid, Saibaba, SIAM J. Sci. Comput. 45 (2023) A74-A95; an extension of the paper's
+ * deterministic rounding of App. A.3.3, whose cost grows like N s^3 in the input rank s):
+ *   1. the sketch Omega: a TT of inner ranks `ell` with entries +-1, entry t of carriage j the sign (top bit) of
+ *      output (j + 1) 2^40 + t of the SplitMix64 stream `seed` (Steele, Lea, Flood, OOPSLA 2014);
+ *   2. W_{d-1} = x_{d-1} Omega_{d-1}^T, W_{j-1} = sum_n x_j[:, n, :] W_j Omega_j[:, n, :]^T (right to left);
+ *   3. left to right: A = X_j W_j, Q = orth(A) (CholeskyQR2, directions below ~1e-6 of the largest singular
+ *      value at the bond dropped), X_j <- Q, X_{j+1} <- (Q^T X_j) x_{j+1};
+ *   4. the rank-ell result rounded deterministically to ranks <= rmax (tol > 0: the smallest such ranks within
+ *      the relative tolerance tol, as lrfg_tt_round_tol).
+ * When x's ranks do not exceed ell the result equals lrfg_tt_round's (up to rounding).  d = 2 or 3.  out->r is
+ * set; out->cores must each hold min(rmax, ..) N[j] min(rmax, ..) doubles. */
+lrfg_status lrfg_tt_round_sketch(lrfg_ctx* ctx, const lrfg_tt* x, int ell, unsigned long long seed, int rmax,
+                                 double tol, lrfg_tt* out);
+/* The same truncation of the element-wise product x (.) y (App. A.3.1) without forming it: the Khatri–Rao middle
+ * carriage enters steps 2 and 3 through contractions with x's and y's carriages in turn. */
+lrfg_status lrfg_tt_hadamard_round_sketch(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, int ell,
+                                          unsigned long long seed, int rmax, double tol, lrfg_tt* out);
 
 /* Euclidean inner product <x, y> = sum_k x[k] y[k] of two TTs (FP64 contraction). */
 lrfg_status lrfg_tt_dot(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, double* result);

@@ -284,6 +284,26 @@ class Context:
         self.check(self.lib.lrfg_tt_round_tol(self.h, C.byref(xs), int(rmax), float(tol), C.byref(s)))
         return self._shrink(bufs, s)
 
+    def tt_round_sketch(self, x: TTensor, ell: int, seed: int, rmax: int, tol: float = 0.0) -> TTensor:
+        """Randomised truncation (lrfg_tt_round_sketch): sketch of inner ranks ``ell`` from SplitMix64 stream
+        ``seed``, then the deterministic rounding to rank rmax (tol > 0: within tol)."""
+        cap = [1] + [int(rmax)] * (x.d - 1) + [1]
+        bufs, s = self._tt_out(x.shape, cap)
+        xs = x.to_struct()
+        self.check(self.lib.lrfg_tt_round_sketch(self.h, C.byref(xs), int(ell), int(seed), int(rmax), float(tol),
+                                                 C.byref(s)))
+        return self._shrink(bufs, s)
+
+    def tt_hadamard_round_sketch(self, x: TTensor, y: TTensor, ell: int, seed: int, rmax: int,
+                                 tol: float = 0.0) -> TTensor:
+        """The randomised truncation of x (.) y without forming the product (lrfg_tt_hadamard_round_sketch)."""
+        cap = [1] + [int(rmax)] * (x.d - 1) + [1]
+        bufs, s = self._tt_out(x.shape, cap)
+        xs, ys = x.to_struct(), y.to_struct()
+        self.check(self.lib.lrfg_tt_hadamard_round_sketch(self.h, C.byref(xs), C.byref(ys), int(ell), int(seed),
+                                                          int(rmax), float(tol), C.byref(s)))
+        return self._shrink(bufs, s)
+
     def tt_dot(self, x: TTensor, y: TTensor) -> float:
         out = C.c_double()
         xs, ys = x.to_struct(), y.to_struct()
@@ -353,15 +373,17 @@ class Context:
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
                 coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
-                disc: int = L.LRFG_GANI) -> "Problem":
+                disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0) -> "Problem":
         """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only).
         ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
         rank cap of a grid coefficient's TT compression (0: ``rank``).  ``rank_start`` > 0: rank-adapting
         MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT).  ``B``: constant symmetric
         positive semidefinite d x d anisotropic part, A~ = a I + B.  ``disc``: GANI, or GA (exact integration
-        of the pixel-wise constant material on the double grid; FULL, FP64)."""
+        of the pixel-wise constant material on the double grid; FULL, FP64).  ``sketch_over`` > 0 (TT, GaNi):
+        the material and P~^-1 products are truncated by the randomised rounding with a sketch of ranks
+        rank + sketch_over from SplitMix64 stream ``sketch_seed``."""
         return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank,
-                       rank_start, rank_step, B, disc)
+                       rank_start, rank_step, B, disc, sketch_over, sketch_seed)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -452,7 +474,8 @@ class Problem:
     (isotropic a(x) samples) or a TTensor of the coefficient."""
 
     def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64,
-                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1, B=None, disc=L.LRFG_GANI):
+                 rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1, B=None, disc=L.LRFG_GANI, sketch_over=0,
+                 sketch_seed=0):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -497,6 +520,7 @@ class Problem:
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
         o.rank_start, o.rank_step, o.disc = int(rank_start), int(rank_step), int(disc)
+        o.sketch_over, o.sketch_seed = int(sketch_over), int(sketch_seed)
         h = C.c_void_p()
         ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))
         del keep

@@ -160,7 +160,7 @@ void resolve_profile(lrfg_ctx* ctx) {
 
 static const char* kClassNames[KC_COUNT] = {
     "fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "pointwise",
-    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor"};
+    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor", "sketch"};
 
 }  // namespace lrfg
 
@@ -207,6 +207,8 @@ struct lrfg_problem {
   DBuf<double2> wcM;
   // Ga in TT: the modified coefficient on the double grid, and its projection on the grid (right-hand side)
   TT a_ga_tt, a_down_tt;
+  // randomised rounding (opts.sketch_over > 0): the sketch TT of ranks rank + sketch_over, by rank
+  std::map<int, TT> sketches;
 };
 
 namespace {
@@ -395,6 +397,21 @@ double quad_form(const double* B, const double* E, int d) {
 
 // ---- TT operator pieces -----------------------------------------------------------------------
 
+// the sketch of the randomised rounding at truncation rank r (null: deterministic rounding)
+const TTView* sketch_for(lrfg_problem* P, int r, TTView& view) {
+  if (P->opts.sketch_over <= 0 || P->ga) return nullptr;
+  const int ell = r + P->opts.sketch_over;
+  auto it = P->sketches.find(ell);
+  if (it == P->sketches.end()) {
+    TT om;
+    sketch_tt(P->ctx, P->d, P->N, ell, (unsigned long long)P->opts.sketch_seed, om);
+    it = P->sketches.emplace(ell, std::move(om)).first;
+  }
+  view = view_of(it->second);
+  return &view;
+}
+
+
 // e = D_alpha v (scaled): carriage alpha replaced, the others shared with v
 struct ModeReplaced {
   DBuf<double> core;
@@ -491,16 +508,39 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
   // material products A~ e_a for all components at once (Khatri–Rao carriages), one batch of d TTs
   int rk[4];
   for (int j = 0; j <= d; ++j) rk[j] = a.r[j] * v.r[j];
+  TTView omv;
+  const TTView* om = sketch_for(P, r, omv);
   TTBatch kr;
-  ttb_alloc(ctx, kr, d, v.N, rk, d);
-  for (int alpha = 0; alpha < d; ++alpha)
-    for (int j = 0; j < d; ++j)
-      khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1], (j == alpha) ? grad[j].get() : v.core[j], v.r[j],
-                 v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
   TTBatch w;
   TT wa[3];
   TTView terms[3];
-  if (!P->aniso) {
+  if (om && !P->aniso) {
+    // randomised rounding of the d products, which are never formed
+    SketchSource z;
+    z.kind = SketchSource::KHATRI_RAO;
+    z.d = d;
+    z.nb = d;
+    z.x = a;
+    for (int j = 0; j < 3; ++j) z.N[j] = v.N[j];
+    for (int j = 0; j <= d; ++j) {
+      z.s[j] = rk[j];
+      z.ry[j] = v.r[j];
+    }
+    for (int alpha = 0; alpha < d; ++alpha)
+      for (int j = 0; j < d; ++j) z.y[j][alpha] = (j == alpha) ? grad[j].get() : v.core[j];
+    tt_round_sketch(ctx, z, *om, r, w, tol);                     // T, all components in one sweep
+    for (auto& g : grad) g.reset();
+    for (int alpha = 0; alpha < d; ++alpha) terms[alpha] = item_view(w, alpha);
+  } else {
+    ttb_alloc(ctx, kr, d, v.N, rk, d);
+    for (int alpha = 0; alpha < d; ++alpha)
+      for (int j = 0; j < d; ++j)
+        khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1], (j == alpha) ? grad[j].get() : v.core[j], v.r[j],
+                   v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
+  }
+  if (om && !P->aniso) {
+    // done above
+  } else if (!P->aniso) {
     for (auto& g : grad) g.reset();
     tt_round_batch(ctx, batch_view(kr), r, w, tol);              // T, all components in one sweep
     kr = TTBatch();
@@ -539,7 +579,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
   tt_add_many(ctx, terms, nullptr, d, acc);
   TT sdiv;
   tt_round(ctx, view_of(acc), r, sdiv, tol);                   // T after the sum
-  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol);   // T P~^-1
+  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol, om);  // T P~^-1
 }
 
 void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
@@ -566,7 +606,9 @@ void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
     for (int j = 0; j < P->d; ++j) fill(ctx, out.core[j].get(), 0.0, P->N[j]);
     return;
   }
-  tt_precond(ctx, view_of(acc), P->pt, P->pw, rank, out, P->opts.rank_tol);  // T P~^-1 (one truncation)
+  TTView omv;
+  tt_precond(ctx, view_of(acc), P->pt, P->pw, rank, out, P->opts.rank_tol,
+             sketch_for(P, rank, omv));                                           // T P~^-1 (one truncation)
 }
 
 // Ga: sum over the double grid of A~ |E + e|^2 (exact integration), e the gradient interpolated there
@@ -1165,6 +1207,62 @@ lrfg_status lrfg_tt_round_tol(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, double 
   });
 }
 
+static void round_sketch_common(lrfg_ctx* ctx, SketchSource& z, int d, const int* N, int ell, unsigned long long seed,
+                                int rmax, double tol, lrfg_tt* out) {
+  LRFG_REQUIRE(out != nullptr, "null output");
+  LRFG_REQUIRE(d >= 2, "randomised rounding needs d = 2 or 3");
+  LRFG_REQUIRE(rmax >= 1 && ell >= 1, "rmax and ell must be >= 1");
+  LRFG_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1) (got %g)", tol);
+  TT om;
+  sketch_tt(ctx, d, N, ell, seed, om);
+  TTBatch ob;
+  tt_round_sketch(ctx, z, view_of(om), rmax, ob, tol);
+  TT res;
+  res.d = ob.d;
+  for (int j = 0; j < 3; ++j) res.N[j] = ob.N[j];
+  for (int j = 0; j < 4; ++j) res.r[j] = ob.r[j];
+  for (int j = 0; j < ob.d; ++j) res.core[j] = std::move(ob.core[j]);
+  publish_tt(res, out);
+  download_tt(ctx, res, out->cores, 1);
+}
+
+lrfg_status lrfg_tt_round_sketch(lrfg_ctx* ctx, const lrfg_tt* x, int ell, unsigned long long seed, int rmax,
+                                 double tol, lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    SketchSource z;
+    z.kind = SketchSource::DENSE;
+    z.d = x->d;
+    for (int j = 0; j < 3; ++j) z.N[j] = j < x->d ? x->N[j] : 0;
+    for (int j = 0; j <= x->d; ++j) z.s[j] = x->r[j];
+    for (int j = 0; j < x->d; ++j) z.dense[j] = x->cores[j];
+    round_sketch_common(ctx, z, x->d, x->N, ell, seed, rmax, tol, out);
+  });
+}
+
+lrfg_status lrfg_tt_hadamard_round_sketch(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, int ell,
+                                          unsigned long long seed, int rmax, double tol, lrfg_tt* out) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    check_tt(x);
+    check_tt(y);
+    LRFG_REQUIRE(x->d == y->d, "Hadamard of TTs of different order");
+    for (int j = 0; j < x->d; ++j) LRFG_REQUIRE(x->N[j] == y->N[j], "Hadamard of TTs on different grids");
+    SketchSource z;
+    z.kind = SketchSource::KHATRI_RAO;
+    z.d = x->d;
+    z.x = view_of(*x);
+    for (int j = 0; j < 3; ++j) z.N[j] = j < x->d ? x->N[j] : 0;
+    for (int j = 0; j <= x->d; ++j) {
+      z.s[j] = x->r[j] * y->r[j];
+      z.ry[j] = y->r[j];
+    }
+    for (int j = 0; j < x->d; ++j) z.y[j][0] = y->cores[j];
+    round_sketch_common(ctx, z, x->d, x->N, ell, seed, rmax, tol, out);
+  });
+}
+
 lrfg_status lrfg_tt_round(lrfg_ctx* ctx, const lrfg_tt* x, int rmax, lrfg_tt* out) {
   return lrfg_tt_round_tol(ctx, x, rmax, 0.0, out);
 }
@@ -1279,6 +1377,9 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->coeff_rank >= 0, "coeff_rank must be >= 0 (got %d)", opts->coeff_rank);
     LRFG_REQUIRE(opts->rank_start >= 0 && opts->rank_step >= 0, "rank_start and rank_step must be >= 0");
     LRFG_REQUIRE(opts->disc == LRFG_GANI || opts->disc == LRFG_GA, "unknown discretisation %d", (int)opts->disc);
+    LRFG_REQUIRE(opts->sketch_over >= 0, "sketch_over must be >= 0 (got %d)", opts->sketch_over);
+    if (opts->sketch_over > 0 && (opts->fmt != LRFG_TT || opts->disc != LRFG_GANI))
+      fail(LRFG_ENOTSUP, "the randomised rounding (sketch_over > 0) is implemented for LRFG_TT GaNi solutions");
     if (opts->disc == LRFG_GA && ((opts->fmt != LRFG_FULL && opts->fmt != LRFG_TT) || opts->prec != LRFG_FP64))
       fail(LRFG_ENOTSUP, "LRFG_GA is implemented for LRFG_FULL and LRFG_TT solutions in LRFG_FP64");
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,

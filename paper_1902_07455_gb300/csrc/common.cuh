@@ -131,6 +131,7 @@ enum KClass {
   KC_KHATRI_RAO,      // TT Hadamard (Khatri–Rao carriages)
   KC_TT_MISC,         // block embedding, balancing, scaling, transposes, fills
   KC_CHOL,            // pivoted Cholesky factors of the Gram matrices (TT rounding)
+  KC_SKETCH,          // fused Khatri-Rao contractions of the randomised rounding
   KC_COUNT
 };
 struct KStats {

@@ -72,8 +72,9 @@ void syevx_product(lrfg_ctx* ctx, const double* BBt, const double* BtB, const do
 // Gram-SVD factors from a balanced Gram matrix G (b x b per item) and the balancing c: pivoted
 // Cholesky; writes RA (G ~ RA^T RA, nonzero rows first), RAc and Pc (b x b each per item; skipped when
 // null, and then c may be null), and the numerical rank into rho (may be null).
+// tau: the pivoted Cholesky stops when the largest remaining pivot is below tau times the largest diagonal.
 void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
-                 double* Pc, int* rho = nullptr);
+                 double* Pc, int* rho = nullptr, double tau = 1e-16);
 // elementwise helpers
 void fill(lrfg_ctx* ctx, double* x, double v, long long n);
 void axpby(lrfg_ctx* ctx, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y
@@ -136,9 +137,41 @@ void tt_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int r
 void tt_mode_operator(lrfg_ctx* ctx, const TTView& x, int j, int kind, double param, double scale, TT& out);
 // exponential sum of 1/x on [1, xmax]: nodes t and weights w (host)
 void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector<double>& w);
-// out = T(P~^-1 x) with the exponential sum (t, w)
+// out = T(P~^-1 x) with the exponential sum (t, w); omega non-null: T is the randomised rounding with that sketch
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w,
-                int rmax, TT& out, double tol = 0.0);
+                int rmax, TT& out, double tol = 0.0, const TTView* omega = nullptr);
+
+// block copy of a carriage (a x n x b) into a larger one (A x n x B) at rank offsets (oa, ob)
+void tt_embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double* dst, int A, int B, int oa, int ob);
+
+// ---- sketch.cu ----------------------------------------------------------------------------------
+// Randomised rounding (randomize-then-orthogonalize) of products that are never formed.  A source describes
+// nb tensor trains z_b of order d with ranks s: DENSE carriages (item after item), KHATRI_RAO products
+// z_b = x (.) y_b (x shared, y_b's carriages given per item, ranks ry), or BLOCKS (nb = 1): the exponential-sum
+// product whose carriage j holds nblocks blocks of shape (ry[j], N, ry[j+1]) at blocks[j] + m * block size,
+// first carriage block-concatenated along its last index, last along its first, middle block-diagonal.
+constexpr int kMaxSketchItems = 4;
+struct SketchSource {
+  enum Kind { DENSE = 0, KHATRI_RAO = 1, BLOCKS = 2 };
+  Kind kind = DENSE;
+  int d = 0, nb = 1;
+  int N[3] = {0, 0, 0};
+  int s[4] = {1, 1, 1, 1};
+  const double* dense[3] = {nullptr, nullptr, nullptr};
+  TTView x{};
+  const double* y[3][kMaxSketchItems] = {};
+  int ry[4] = {1, 1, 1, 1};
+  int nblocks = 0;
+  const double* blocks[3] = {nullptr, nullptr, nullptr};
+  void materialise(lrfg_ctx* ctx, int j, double* dst) const;                      // first or last carriage
+  void right_middle(lrfg_ctx* ctx, const double* W, int ell, double* T) const;     // T = Z_1 x_3 W
+  void left_middle(lrfg_ctx* ctx, const double* M, int ell, double* X) const;      // X = M x_1 Z_1
+};
+// Rademacher sketch TT of inner ranks ell (SplitMix64 stream `seed`)
+void sketch_tt(lrfg_ctx* ctx, int d, const int* N, int ell, unsigned long long seed, TT& out);
+// randomised rounding of every item to rank rmax (tolerance tol > 0: the smallest ranks <= rmax within it)
+void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out,
+                     double tol = 0.0);
 
 // ---- tucker.cu ----------------------------------------------------------------------------------
 // Tucker tensor on the device: core (r_0, .., r_{d-1}) row-major, factor j (N_j, r_j) row-major

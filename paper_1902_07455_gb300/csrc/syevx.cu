@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(kCholThreads) gram_factor_kernel(const double*
 }
 
 void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int batch, double* RA, double* RAc,
-                 double* Pc, int* rho) {
+                 double* Pc, int* rho, double tau) {
   if (b <= 0 || batch <= 0) return;
   const size_t head = chol_head_bytes(b);
   const size_t full = head + sizeof(double) * 2 * (size_t)b * b;
@@ -809,7 +809,7 @@ void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int bat
   LRFG_CUDA(raise_smem_limit((const void*)gram_factor_kernel, smem));
   // algorithmic work up to the numerical rank, counted by each block on the device
   LRFG_LAUNCH(ctx, KC_CHOL, 0.0, 0.0,
-              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, 1e-16, RA, RAc, Pc, rho,
+              gram_factor_kernel<<<batch, kCholThreads, smem, ctx->stream>>>(G, c, b, tau, RA, RAc, Pc, rho,
                                                                                scratch.get(), use_smem,
                                                                                work_counter(ctx, KC_CHOL)));
 }

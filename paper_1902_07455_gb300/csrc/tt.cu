@@ -117,6 +117,10 @@ static void embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double*
               block_embed_kernel<<<grid1d(ctx, total), 256, 0, ctx->stream>>>(src, a, n, b, dst, A, B, oa, ob, s, s_dev));
 }
 
+void tt_embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double* dst, int A, int B, int oa, int ob) {
+  embed(ctx, src, a, n, b, dst, A, B, oa, ob, 1.0, nullptr);
+}
+
 void tt_add_many(lrfg_ctx* ctx, const TTView* xs, const double* scales, int nb, TT& out) {
   LRFG_REQUIRE(nb >= 1, "empty sum");
   const int d = xs[0].d;
@@ -709,7 +713,7 @@ void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector
 }
 
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
-                TT& out, double tol) {
+                TT& out, double tol, const TTView* omega) {
   // P~^-1 x = sum_m w_m (G_m x ... x G_m) x with G_m = F^-1 diag(exp(-t_m k^2)) F per mode: a TT whose
   // carriages are block rows (first), block diagonal (middle) and block columns (last) over m.
   const int d = x.d;
@@ -718,9 +722,38 @@ void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, co
   r[0] = 1;
   r[d] = 1;
   for (int j = 1; j < d; ++j) r[j] = R * x.r[j];
+  std::vector<double> ones(R, 1.0);
+  if (omega && d >= 2) {
+    // randomised rounding: the blocks G_m x_j enter the sketch contractions as they are (never embedded in the
+    // block-diagonal carriage)
+    SketchSource z;
+    z.kind = SketchSource::BLOCKS;
+    z.d = d;
+    z.nb = 1;
+    z.nblocks = R;
+    DBuf<double> terms[3];
+    for (int j = 0; j < d; ++j) {
+      z.N[j] = x.N[j];
+      const size_t e = (size_t)x.r[j] * x.N[j] * x.r[j + 1];
+      terms[j] = DBuf<double>(ctx->pool, e * R);
+      fibre_gauss_multi(ctx, x.core[j], terms[j].get(), (long long)e, x.r[j], x.N[j], x.r[j + 1], t.data(),
+                        (j == 0) ? w.data() : ones.data(), R);
+      z.blocks[j] = terms[j].get();
+    }
+    for (int j = 0; j <= d; ++j) {
+      z.s[j] = r[j];
+      z.ry[j] = x.r[j];
+    }
+    TTBatch ob;
+    tt_round_sketch(ctx, z, *omega, rmax, ob, tol);
+    out.d = ob.d;
+    for (int j = 0; j < 3; ++j) out.N[j] = ob.N[j];
+    for (int j = 0; j < 4; ++j) out.r[j] = ob.r[j];
+    for (int j = 0; j < ob.d; ++j) out.core[j] = std::move(ob.core[j]);
+    return;
+  }
   TT big;
   tt_alloc(ctx, big, d, x.N, r);
-  std::vector<double> ones(R, 1.0);
   for (int j = 0; j < d; ++j) {
     const int a = x.r[j], n = x.N[j], b = x.r[j + 1];
     const size_t e = (size_t)a * n * b;
