@@ -6,18 +6,22 @@ seed 19020745), E = (1, 0, 0).  The coefficient is compressed on the GPU to TT r
 the coefficient rank the paper uses for its stochastic material) and the full-format solver gets the
 expansion of that TT coefficient, so both solve the same problem.
 
-One step = one complete TT solve from u = 0 (minimal-residual iteration with truncation to rank r until
-the residual stops decreasing, then A_eff): every hot-path stage — mode-wise gradient FFTs, Khatri–Rao
-material products, Gram-SVD truncations, divergence sums, exponential-sum preconditioner, TT inner
-products, A_eff.  value = TT solves per second over the timed steps (whole job: summed over ranks
-under torchrun, timed by the slowest rank).  The full-format FP64 PCG solve of the same problem is
-timed beside it (full_solves_per_s, op-applies/s of both) and gives the A_eff reference.
+One step = one complete TT solve from u = 0 at the metric's accuracy: the minimal-residual iteration with
+truncation to rank 20 (the material and P~^-1 products truncated by the randomised rounding, every other
+truncation deterministic), stopped when the relative residual reaches 2.5e-4 (A_eff's error is quadratic in
+the field's, about 10 x the squared residual here, so this reaches A_eff within 1e-6), then A_eff: every
+hot-path stage — mode-wise gradient FFTs, material products, truncations, divergence sums, exponential-sum
+preconditioner, TT inner products, A_eff.  value = TT solves per second over the timed steps (whole job:
+summed over ranks under torchrun, timed by the slowest rank), uninstrumented; one extra profiled solve gives
+the kernel classes and the roofline.  The full-format FP64 PCG solve (tol 1e-8) of the same problem is timed
+beside it (p50/p99) and gives the A_eff reference; so is the LRFG_MIXED full solve.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the library's stream,
 with a 512 MiB buffer written between steps to flush L2 (the TT state is a few MiB and would otherwise
 stay in L2).  nvidia-smi samples clocks during the timed region.
 
-    python bench.py [--steps K] [--warmup W] [--rank r] [--N 243] [--impl ours|reference]
+    python bench.py [--steps K] [--warmup W] [--rank r] [--sketch-over p] [--tt-tol t] [--N 243]
+                    [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -46,10 +50,16 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--N", type=int, default=243)
-    p.add_argument("--rank", type=int, default=10)
+    p.add_argument("--rank", type=int, default=20)
     p.add_argument("--coeff-rank", type=int, default=10)
     p.add_argument("--pinv-eps", type=float, default=0.1)
-    p.add_argument("--maxit", type=int, default=60)
+    p.add_argument("--maxit", type=int, default=80)
+    p.add_argument("--sketch-over", type=int, default=10,
+                   help="oversampling of the randomised rounding of the products (0: deterministic rounding)")
+    p.add_argument("--tt-tol", type=float, default=2.5e-4,
+                   help="relative residual at which the TT solve stops (A_eff error ~ 10 x its square)")
+    p.add_argument("--stop-on-increase", action="store_true",
+                   help="also stop when the residual fails to decrease (the paper's rule, Sec. 4.3)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--format", choices=["tt", "tucker"], default="tt",
                    help="low-rank solution format of the timed solve (the coefficient is the same rank-10 TT; a "
@@ -96,9 +106,13 @@ def dist_env():
 
 def workload_config(args):
     fmt = "Tucker" if args.format == "tucker" else "TT"
+    rnd = (f"randomised rounding of the products (oversampling {args.sketch_over})" if args.sketch_over > 0
+           else "deterministic rounding")
     return {"workload": f"d=3 N={args.N}^3 lognormal SE-GRF (l=0.2, var=1, seed {SEED}), E=(1,0,0); "
-                        f"{fmt} rank {args.rank} MinRes vs full FP64 PCG",
+                        f"{fmt} rank {args.rank} MinRes ({rnd}, stop at relative residual {args.tt_tol:g}) "
+                        f"vs full FP64 PCG (tol 1e-8)",
             "d": 3, "N": args.N, "coeff_tt_rank": args.coeff_rank, "format": args.format, "tt_rank": args.rank,
+            "sketch_over": args.sketch_over, "tt_tol": args.tt_tol, "stop_on_increase": args.stop_on_increase,
             "pinv_eps": args.pinv_eps, "precision": "fp64", "l2": "flushed between steps (512 MiB write)"}
 
 
@@ -172,10 +186,12 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 arithmetic classes are bound by the FP64 pipe: GB300 issues 2 FP64 FMA per clock per SM
-# (4 flop/clk/SM), i.e. 152 SMs x 2.07 GHz x 4 = 1.26 TFLOP/s at the maximum SM clock.
-FP64_PEAK_TFLOPS = 152 * 2.070 * 4 / 1e3
-ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen", "gram_factor"}
+# FP64 arithmetic classes are bound by the FP64 pipe.  Its rate is measured on the device at run time
+# (lrfg_probe_fp64: FMA loops over 8 blocks per SM); the derived figure, 2 FP64 FMA per clock per SM (4 flop/clk/SM)
+# x 152 SMs x 2.07 GHz = 1.26 TFLOP/s, is the fallback when no measurement is passed in.
+FP64_DERIVED_TFLOPS = 152 * 2.070 * 4 / 1e3
+ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen", "gram_factor",
+               "sketch"}
 
 
 def class_rooflines(stats, classes):
@@ -192,16 +208,18 @@ def class_rooflines(stats, classes):
     return out
 
 
-def roofline(stats):
+def roofline(stats, fp64_peak=None):
     peaks, src = measured_peaks()
     dom = max(stats, key=lambda k: stats[k]["ms"])
     s = stats[dom]
     per_launch_ms = s["ms"] / max(s["launches"], 1)
     if dom in ALU_CLASSES:
         achieved = s["flops"] / (s["ms"] * 1e-3) / 1e12 if s["ms"] > 0 else 0.0
-        peak = FP64_PEAK_TFLOPS
+        peak = fp64_peak if fp64_peak else FP64_DERIVED_TFLOPS
+        source = ("measured FP64 FMA rate of this GPU (lrfg_probe_fp64, in this run)" if fp64_peak else
+                  "derived FP64 pipe rate (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)")
         out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-               "peak_source": "derived FP64 pipe rate (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)"}
+               "peak_source": source}
     else:
         achieved = s["bytes"] / (s["ms"] * 1e-3) / 1e9 if s["ms"] > 0 else 0.0
         peak = float(peaks["hbm_gbs"])
@@ -216,20 +234,39 @@ def roofline(stats):
 # -------------------------------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands
 # -------------------------------------------------------------------------------------------------
-def oracle_apply_seconds(N, coeff_rank, rank, pinv_eps, n_applies=1):
-    """Time oracle applications of the truncated TT operator (Eq. (Pls_lowrank)) on a rank-r operand."""
+GOLDEN = os.path.join(ROOT, "tests", "golden", "lognormal_243.json")
+
+
+def oracle_apply_seconds(args, n_applies):
+    """Time oracle applications of the truncated TT operator (Eq. (Pls_lowrank)) of the workload, with the
+    randomised rounding of the products when the workload uses it, starting from the right-hand side."""
     from oracle import lowrank as lr
-    A = make_coefficient(N)
-    a_tt = lr.tt_svd(A, rmax=coeff_rank)
-    op = lr.LowRankGaNi(a_tt, (N, N, N), fmt="tt", rank=rank, pinv_eps=pinv_eps)
-    b = op.rhs(np.array([1.0, 0.0, 0.0]))
+    A = make_coefficient(args.N)
+    a_tt = lr.tt_svd(A, rmax=args.coeff_rank)
+    sketch = (args.sketch_over, 0) if args.sketch_over > 0 else None
+    op = lr.LowRankGaNi(a_tt, (args.N,) * 3, fmt="tt", rank=args.rank, pinv_eps=args.pinv_eps, sketch=sketch)
+    x = op.rhs(np.array([1.0, 0.0, 0.0]))
     times = []
-    x = b
     for _ in range(n_applies):
         t0 = time.perf_counter()
         x = op.apply(x)
         times.append(time.perf_counter() - t0)
     return times
+
+
+def oracle_applies_per_solve(args):
+    """Operator applications of one oracle solve of this workload, from the oracle's own complete run stored
+    in tests/golden/lognormal_243.json (written by tests/golden/make_golden.py, which calls only the oracle);
+    None when the stored run is not this configuration."""
+    try:
+        g = json.load(open(GOLDEN))["tt_sketch"][str(args.rank)]
+    except (OSError, KeyError, ValueError):
+        return None
+    o = g["opts"]
+    same = (args.N == 243 and args.coeff_rank == 10 and o["rank"] == args.rank and o["sketch_over"] == args.sketch_over
+            and o["tol"] == args.tt_tol and o["pinv_eps"] == args.pinv_eps and o["maxit"] == args.maxit
+            and bool(o["stop_on_increase"]) == bool(args.stop_on_increase))
+    return (g["applies"], g) if same else None
 
 
 def cpu_cores():
@@ -244,6 +281,27 @@ def cpu_cores():
 # -------------------------------------------------------------------------------------------------
 # our arm
 # -------------------------------------------------------------------------------------------------
+def timed_solves(P, E, n, stream, flush, clk=None):
+    """n solves, each bracketed by CUDA events on the library's stream with L2 flushed before it; returns
+    (per-solve ms, results)."""
+    import torch
+    ms, res = [], []
+    for _ in range(n):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res.append(P.solve(E, want_field=False)[0])
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, res
+
+
+def pct(v, q):
+    return float(np.percentile(v, q))
+
+
 def run_ours(args):
     import torch
     import paper_1902_07455_gb300 as lrfg
@@ -256,21 +314,20 @@ def run_ours(args):
     from paper_1902_07455_gb300 import build
     build.build()
     ctx = lrfg.Context(local)
+    fp64_fma, fp64_dmma = ctx.probe_fp64()
     E = [1.0, 0.0, 0.0]
     A = make_coefficient(args.N)
     A_dev = torch.as_tensor(A, device=f"cuda:{local}")
     a_tt = ctx.tt_compress(A_dev, args.coeff_rank)
     a_full = ctx.tt_expand(a_tt)
     del A_dev
+    stream = ctx.stream
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
-    # full-format reference solve (FP64 PCG, tol 1e-8) on the same coefficient
+    # full-format FP64 PCG (tol 1e-8) on the same coefficient: the A_eff reference and the comparison solver
     Pfull = ctx.problem(a_full, lrfg.FULL, tol=1e-8, maxit=2000)
     full_res, _ = Pfull.solve(E, want_field=False)
-    full_times = []
-    for _ in range(2):
-        r, _ = Pfull.solve(E, want_field=False)
-        full_times.append(r.seconds)
-    # full-format operator applications
+    full_ms, _ = timed_solves(Pfull, E, 3, stream, flush)
     f_in = ctx.field_from_full(torch.randn((args.N,) * 3, dtype=torch.float64, device=f"cuda:{local}"))
     f_out = Pfull.apply(f_in)
     torch.cuda.synchronize()
@@ -282,10 +339,7 @@ def run_ours(args):
     # the same solve with LRFG_MIXED: FP32 storage and FFTs, FP64 scalars, to a 1e-5 residual
     Pmix = ctx.problem(a_full, lrfg.FULL, tol=1e-5, maxit=2000, prec=lrfg.MIXED)
     mix_res, _ = Pmix.solve(E, want_field=False)
-    mix_times = []
-    for _ in range(2):
-        r, _ = Pmix.solve(E, want_field=False)
-        mix_times.append(r.seconds)
+    mix_ms, _ = timed_solves(Pmix, E, 3, stream, flush)
     Pmix.apply_into(f_in, f_out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -305,38 +359,20 @@ def run_ours(args):
     f_in.free()
     f_out.free()
 
+    # the low-rank solve that is timed (the workload's step): TT rank r, randomised rounding of the products,
+    # stopped at the residual tolerance
     lr_fmt = lrfg.TUCKER if args.format == "tucker" else lrfg.TT
-    Ptt = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=1e-12, maxit=args.maxit,
-                      stop_on_increase=True)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
-    stream = ctx.stream
-
-    def step():
-        res, _ = Ptt.solve(E, want_field=False)
-        return res
-
+    Ptt = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
+                      stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over)
     for _ in range(args.warmup):
-        step()
+        Ptt.solve(E, want_field=False)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launch_count()
-    ctx.profile_reset()
-    ctx.profile(True)
-    step_ms, results = [], []
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            results.append(step())
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
+        step_ms, results = timed_solves(Ptt, E, args.steps, stream, flush)
     torch.cuda.synchronize()
-    ctx.profile(False)
-    stats = ctx.profile_read()
     launches = ctx.launch_count() - launches0
     total_ms = sum(step_ms)
     if world > 1:
@@ -345,6 +381,18 @@ def run_ours(args):
     res = results[-1]
     applies = sum(r.applies for r in results)
     rel_err = abs(res.Aeff - full_res.Aeff) / full_res.Aeff
+    # one more solve, profiled (CUDA events around every launch), for the kernel classes and the roofline
+    ctx.profile_reset()
+    ctx.profile(True)
+    prof_res, _ = Ptt.solve(E, want_field=False)
+    ctx.profile(False)
+    stats = ctx.profile_read()
+
+    # the configuration of the previous measurements: TT rank 10, deterministic rounding, stop on increase
+    P10 = ctx.problem(a_tt, lr_fmt, rank=10, pinv_eps=args.pinv_eps, tol=1e-12, maxit=60, stop_on_increase=True)
+    P10.solve(E, want_field=False)
+    ms10, r10 = timed_solves(P10, E, 2, stream, flush)
+    P10.free()
 
     # end to end through the C ABI with host buffers: lrfg_solve with the coefficient carriages in host
     # memory (copied in each call) and the result read back to the host
@@ -369,23 +417,32 @@ def run_ours(args):
             "config": workload_config(args),
             "tt_op_applies_per_s": world * applies / (total_ms * 1e-3),
             "tt_applies_per_solve": applies / args.steps,
-            "tt_iters": res.iters, "tt_aeff": res.Aeff, "full_aeff": full_res.Aeff, "aeff_rel_err": rel_err,
-            "meets_1e-6": rel_err <= 1e-6,
-            "full_solves_per_s": 1.0 / statistics.median(full_times), "full_iters": full_res.iters,
-            "full_op_applies_per_s": 1.0 / full_apply_s,
-            "full_mixed": {"solves_per_s": 1.0 / statistics.median(mix_times), "iters": mix_res.iters,
-                           "op_applies_per_s": 1.0 / mix_apply_s, "tol": 1e-5, "aeff": mix_res.Aeff,
+            "tt_iters": res.iters, "tt_rel_resid": res.rel_resid, "tt_aeff": res.Aeff, "full_aeff": full_res.Aeff,
+            "aeff_rel_err": rel_err, "meets_1e-6": rel_err <= 1e-6,
+            "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
+            "full": {"solves_per_s": 1e3 / statistics.median(full_ms), "p50_ms": pct(full_ms, 50),
+                     "p99_ms": pct(full_ms, 99), "iters": full_res.iters, "tol": 1e-8,
+                     "op_applies_per_s": 1.0 / full_apply_s},
+            "full_solves_per_s": 1e3 / statistics.median(full_ms),
+            "full_mixed": {"solves_per_s": 1e3 / statistics.median(mix_ms), "p50_ms": pct(mix_ms, 50),
+                           "p99_ms": pct(mix_ms, 99), "iters": mix_res.iters, "op_applies_per_s": 1.0 / mix_apply_s,
+                           "tol": 1e-5, "aeff": mix_res.Aeff,
                            "aeff_rel_err_vs_f64": abs(mix_res.Aeff - full_res.Aeff) / full_res.Aeff},
+            "tt_vs_full_fp64": solves_per_s / world / (1e3 / statistics.median(full_ms)),
+            "tt_rank10_deterministic": {"solves_per_s": 1e3 / statistics.median(ms10), "iters": r10[-1].iters,
+                                        "aeff_rel_err": abs(r10[-1].Aeff - full_res.Aeff) / full_res.Aeff},
             "full_class_rooflines": full_roof,
-            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "coeff_ranks": Ptt.coeff_ranks(),
             "e2e": {"value": 1e3 / statistics.median(e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "aeff": r_e2e},
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "roofline": roofline(stats),
-            "kernel_classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in stats.items()
-                               if v["launches"]},
+            "fp64_measured_tflops": {"fma": fp64_fma, "dmma": fp64_dmma},
+            "roofline": roofline(stats, fp64_fma),
+            "profiled_solve": {"note": "one extra solve with CUDA events around every launch (not timed above)",
+                               "iters": prof_res.iters, "applies": prof_res.applies},
+            "kernel_classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                                   "gflop": round(v["flops"] / 1e9, 3)} for k, v in stats.items() if v["launches"]},
         }
     Ptt.free()
     Pfull.free()
@@ -417,7 +474,8 @@ def solve_host(ctx, host_cores, args, E):
     o = L.lrfg_opts()
     o.fmt = L.LRFG_TUCKER if args.format == "tucker" else L.LRFG_TT
     o.prec, o.rank, o.pinv_eps = L.LRFG_FP64, args.rank, args.pinv_eps
-    o.tol, o.maxit, o.stop_on_increase = 1e-12, args.maxit, 1
+    o.tol, o.maxit, o.stop_on_increase = args.tt_tol, args.maxit, int(args.stop_on_increase)
+    o.sketch_over, o.sketch_seed = args.sketch_over, 0
     res = L.lrfg_result()
     Ed = (C.c_double * 3)(*E)
     st = ctx.lib.lrfg_solve(ctx.h, C.byref(c), Ed, C.byref(o), C.byref(res), None)
@@ -427,15 +485,19 @@ def solve_host(ctx, host_cores, args, E):
 
 
 def add_cpu_baseline(line, args):
-    # a bounded sample: oracle applications of the same truncated operator (about 10-30 s of CPU work),
-    # scaled to solves/s with the applies per solve of the GPU run (the same algorithm)
-    t = oracle_apply_seconds(args.N, args.coeff_rank, args.rank, args.pinv_eps, n_applies=2)
+    # a bounded sample: oracle applications of the same truncated operator (about 10-30 s of CPU work), scaled
+    # to solves/s by the applications per solve of the oracle's own complete solve of this workload (stored),
+    # or else by the GPU run's count of the same algorithm
+    t = oracle_apply_seconds(args, 8)
     per_apply = statistics.median(t)
-    per_solve = per_apply * line["tt_applies_per_solve"]
-    line["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                            "sample": f"{len(t)} oracle applications of the rank-{args.rank} TT operator at "
-                                      f"N={args.N}^3 ({per_apply:.2f} s each), scaled by "
-                                      f"{line['tt_applies_per_solve']:.1f} applications per solve"}
+    stored = oracle_applies_per_solve(args)
+    n_app, src = (stored[0], "the oracle's own complete solve of this workload (tests/golden)") if stored else \
+        (line["tt_applies_per_solve"], "the GPU run's solves (same algorithm)")
+    line["cpu_baseline"] = {"value": 1.0 / (per_apply * n_app), "unit": "solves/s", "cores": cpu_cores(),
+                            "kind": "oracle",
+                            "sample": f"{len(t)} oracle applications of the rank-{args.rank} TT operator at N={args.N}^3 "
+                                      f"({per_apply:.2f} s each, median), times {n_app} applications per solve from "
+                                      f"{src}"}
 
 
 # -------------------------------------------------------------------------------------------------
@@ -445,32 +507,25 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    # applications per solve of this algorithm at this workload (measured on the GPU arm); without a GPU
-    # run at hand, the oracle's own count on a short solve is not affordable at N=243, so the step is one
-    # oracle application and the value is scaled by a fixed applies-per-solve figure stated in the line
-    applies_per_solve = 16.0
-    times = []
-    from oracle import lowrank as lr
-    A = make_coefficient(args.N)
-    a_tt = lr.tt_svd(A, rmax=args.coeff_rank)
-    op = lr.LowRankGaNi(a_tt, (args.N,) * 3, fmt="tt", rank=args.rank, pinv_eps=args.pinv_eps)
-    x = op.rhs(np.array([1.0, 0.0, 0.0]))
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        x = op.apply(x)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-    per_solve = statistics.median(times) * applies_per_solve
-    value = 1.0 / per_solve
+    # each step: one oracle application of the workload's operator; the value scales the median step by the
+    # applications per solve of the oracle's own complete solve of this workload (stored in tests/golden)
+    stored = oracle_applies_per_solve(args)
+    if stored is None:
+        return {"impl": "reference", "unavailable": "no stored oracle solve of this configuration (run "
+                                                   "tests/golden/make_golden.py for it)"}
+    n_app, g = stored
+    times = oracle_apply_seconds(args, args.warmup + args.steps)[args.warmup:]
+    value = 1.0 / (statistics.median(times) * n_app)
     cores = cpu_cores()
     return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(args),
+            "oracle_solve": {"applies": n_app, "iters": g["iters"], "aeff": g["Aeff"]},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step one oracle application of the rank-{args.rank} TT operator at "
-                                       f"N={args.N}^3, scaled by {applies_per_solve:.0f} applications per solve"},
+                                       f"N={args.N}^3; median times {n_app} applications per solve (the oracle's own "
+                                       f"complete solve of this workload, tests/golden)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -788,7 +843,7 @@ def run_case(args):
     A = torch.as_tensor(make_coefficient(args.N), device="cuda:0")
     a_tt = ctx.tt_compress(A, args.coeff_rank)
     if args.case == "tt_apply":
-        P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps)
+        P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, sketch_over=args.sketch_over)
         x = P.rhs([1.0, 0.0, 0.0])
     else:
         prec = lrfg.MIXED if args.case == "full_apply_mixed" else lrfg.FP64

@@ -174,6 +174,11 @@ const char* lrfg_last_error(const lrfg_ctx* ctx);
 lrfg_status lrfg_sync(lrfg_ctx* ctx);
 /* Number of kernels this context has launched so far (instrumentation). */
 long long lrfg_launch_count(const lrfg_ctx* ctx);
+/* Measured FP64 rates of the context's device in TFLOP/s (instrumentation: the roofline denominator of the
+ * FP64-bound kernels): fused multiply-add on the FP64 pipe (8 independent chains per thread, 8 blocks of 256
+ * threads per SM) and the FP64 tensor-core instruction mma.sync m8n8k4 (4 accumulators per warp); each timed
+ * over one launch with CUDA events after a warm-up launch.  Synchronises the stream. */
+lrfg_status lrfg_probe_fp64(lrfg_ctx* ctx, double* fma_tflops, double* dmma_tflops);
 /* Bytes currently held by the context's device pool (in use, and reserved including cached). */
 lrfg_status lrfg_pool_bytes(const lrfg_ctx* ctx, size_t* in_use, size_t* reserved);
 

@@ -210,6 +210,12 @@ class Context:
         return {self.lib.lrfg_profile_class_name(k).decode(): dict(launches=L_[k], flops=f[k], bytes=b[k], ms=m[k])
                 for k in range(n)}
 
+    def probe_fp64(self):
+        """Measured FP64 rates of the device, TFLOP/s: (fused multiply-add pipe, mma.sync FP64)."""
+        a, b = C.c_double(), C.c_double()
+        self.check(self.lib.lrfg_probe_fp64(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def pool_bytes(self):
         a, b = C.c_size_t(), C.c_size_t()
         self.check(self.lib.lrfg_pool_bytes(self.h, C.byref(a), C.byref(b)))

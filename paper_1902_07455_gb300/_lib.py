@@ -79,6 +79,7 @@ SIGNATURES = {
     "lrfg_tt_round_sketch": (_ST, [_P, C.POINTER(lrfg_tt), _I, C.c_ulonglong, _I, _D, C.POINTER(lrfg_tt)]),
     "lrfg_tt_hadamard_round_sketch": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), _I, C.c_ulonglong, _I, _D,
                                             C.POINTER(lrfg_tt)]),
+    "lrfg_probe_fp64": (_ST, [_P, C.POINTER(_D), C.POINTER(_D)]),
     "lrfg_tt_dot": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(_D)]),
     "lrfg_tt_dot_noalloc": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), _P]),
     "lrfg_tt_precond": (_ST, [_P, C.POINTER(lrfg_tt), _D, _I, C.POINTER(lrfg_tt)]),

@@ -60,3 +60,21 @@ def test_full_mixed_pcg_at_243(ctx, problem_setup):
     res, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
     assert res.converged
     assert abs(res.Aeff - gold["full"]["Aeff"]) <= 1e-5 * gold["full"]["Aeff"]
+
+
+def test_tt_sketched_solve_at_243(ctx, problem_setup):
+    """The benchmark's TT solve (rank 20, randomised rounding of the material and P~^-1 products, stopped at the
+    stored residual tolerance): A_eff within the FP64-path target 1e-6 of the oracle's full solve, within 2e-6 of
+    the oracle's own solve with the same options (two approximations each within 1e-6 of the full value; the two
+    iterations part ways at the rounding level, so their stopping points differ), never below the full value."""
+    gold, a_tt, _ = problem_setup
+    g = gold["tt_sketch"]["20"]
+    o = g["opts"]
+    P = ctx.problem(a_tt, lrfg.TT, rank=o["rank"], pinv_eps=o["pinv_eps"], tol=o["tol"], maxit=o["maxit"],
+                    stop_on_increase=o["stop_on_increase"], sketch_over=o["sketch_over"], sketch_seed=o["sketch_seed"])
+    res, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
+    full = gold["full"]["Aeff"]
+    assert abs(res.Aeff - full) <= 1e-6 * full, (res.Aeff, full, res.iters, res.rel_resid)
+    assert abs(res.Aeff - g["Aeff"]) <= 2e-6 * g["Aeff"]
+    assert res.Aeff >= full * (1 - 1e-12)
+    P.free()
