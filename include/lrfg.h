@@ -332,9 +332,18 @@ lrfg_status lrfg_problem_solve(lrfg_problem* problem, const double* E, lrfg_resu
 /* A_eff E.E = (1/|N|) sum_k a(x_k) |E + e(x_k)|^2, e = F^{-1} grad^ u (Eq. (homog), Sec. 2.2.2). */
 lrfg_status lrfg_problem_aeff(lrfg_problem* problem, const double* E, const lrfg_field* u, double* Aeff);
 
+/* Solve for nb macroscopic fields at once: E is a host array of nb x d doubles (row i = E_i), res receives nb
+ * results (res[i].seconds is the wall time of the whole call).  For LRFG_TT problems with an isotropic GaNi
+ * coefficient at a fixed rank (rank_tol = 0, rank_start = 0) and nb d <= 32, the minimal-residual iterations of
+ * the nb right-hand sides run in lockstep: every operator application, truncation and inner product takes one
+ * launch sequence for all of them (each keeps its own step length, best iterate and stopping test; the results
+ * equal separate solves up to the rounding order of the batched products).  Otherwise the nb solves run one
+ * after the other.  Status as lrfg_problem_solve (LRFG_ENOCONV if any right-hand side reached maxit). */
+lrfg_status lrfg_problem_solve_many(lrfg_problem* problem, int nb, const double* E, lrfg_result* res);
 /* The homogenised tensor A_eff (d x d, symmetric) of Eq. (homog): the diagonal A_aa from the solves with
  * E = e_a, each off-diagonal entry by polarisation of the quadratic form q(E) = A_eff E.E (Sec. 2.1),
- * A_ab = (q(e_a + e_b) - q(e_a) - q(e_b)) / 2 — d (d + 1) / 2 solves with the problem's options.
+ * A_ab = (q(e_a + e_b) - q(e_a) - q(e_b)) / 2 — d (d + 1) / 2 solves with the problem's options, run
+ * through lrfg_problem_solve_many (in lockstep where it allows).
  *   A        host array of d * d doubles, row-major, written on return (caller-owned);
  *   results  NULL, or a host array of d (d + 1) / 2 lrfg_result, one per solve in the order
  *            (a, b) = (0,0), (0,1), .., (0,d-1), (1,1), .., (d-1,d-1) with E = e_a (+ e_b when b != a).

@@ -563,6 +563,18 @@ class Problem:
                      res.seconds, st)
         return out, (Field(self.ctx, h) if want_field and h.value else None)
 
+    def solve_many(self, Es):
+        """Solve for every row of Es (nb x d) through lrfg_problem_solve_many (in lockstep for TT problems that
+        allow it); returns the list of Results."""
+        Es = np.ascontiguousarray(np.asarray(Es, dtype=np.float64).reshape(-1, self.d))
+        nb = Es.shape[0]
+        res = (L.lrfg_result * nb)()
+        st = self.ctx.lib.lrfg_problem_solve_many(self.h, nb, Es.ctypes.data_as(C.POINTER(C.c_double)), res)
+        if st not in (L.LRFG_OK, L.LRFG_ENOCONV):
+            self.ctx.check(st)
+        return [Result(r.Aeff, r.iters, r.rel_resid, bool(r.converged), r.applies, list(r.ranks)[: self.d + 1],
+                       r.seconds, st) for r in res]
+
     def aeff(self, E, field: Field) -> float:
         out = C.c_double()
         self.ctx.check(self.ctx.lib.lrfg_problem_aeff(self.h, _dvec(E), field.h, C.byref(out)))
@@ -675,7 +687,7 @@ class Batch:
     def submit(self, coeff, E, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8,
                maxit: int = 200, stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
-               disc: int = L.LRFG_GANI) -> int:
+               disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0) -> int:
         c, keep = _host_coeff(coeff)
         _set_b(c, B)
         o = L.lrfg_opts()
@@ -683,6 +695,7 @@ class Batch:
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
         o.rank_start, o.rank_step, o.disc = int(rank_start), int(rank_step), int(disc)
+        o.sketch_over, o.sketch_seed = int(sketch_over), int(sketch_seed)
         t = C.c_ulonglong()
         st = self.lib.lrfg_batch_submit(self.h, C.byref(c), _dvec(E), C.byref(o), C.byref(t))
         del keep

@@ -93,6 +93,7 @@ SIGNATURES = {
     "lrfg_problem_rhs": (_ST, [_P, C.POINTER(_D), C.POINTER(_P)]),
     "lrfg_problem_solve": (_ST, [_P, C.POINTER(_D), C.POINTER(lrfg_result), C.POINTER(_P)]),
     "lrfg_problem_aeff": (_ST, [_P, C.POINTER(_D), _P, C.POINTER(_D)]),
+    "lrfg_problem_solve_many": (_ST, [_P, _I, C.POINTER(_D), C.POINTER(lrfg_result)]),
     "lrfg_problem_aeff_tensor": (_ST, [_P, C.POINTER(_D), C.POINTER(lrfg_result)]),
     "lrfg_solve": (_ST, [_P, C.POINTER(lrfg_coeff), C.POINTER(_D), C.POINTER(lrfg_opts), C.POINTER(lrfg_result),
                          C.POINTER(_P)]),

@@ -13,6 +13,7 @@
 #include <type_traits>
 #include <cstdarg>
 #include <cstdlib>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -1020,6 +1021,230 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
   }
 }
 
+// ---- several right-hand sides of one TT problem in lockstep --------------------------------------
+
+// whether solve_tt_many can run the problem's options (isotropic GaNi TT at a fixed rank)
+bool lockstep_ok(const lrfg_problem* P) {
+  return P->opts.fmt == LRFG_TT && !P->ga && !P->aniso && P->opts.rank_start == 0 && P->opts.rank_tol == 0.0 &&
+         P->d >= 2;
+}
+
+// The operator of lr_apply on nb items at once (items of identical ranks, stored item after item): the gradient,
+// material, divergence, sum and preconditioner stages each take one launch sequence for all items.
+void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r) {
+  lrfg_ctx* ctx = P->ctx;
+  const int d = P->d, nb = v.nb;
+  const TTView a = view_of(P->a_tt);
+  TTView omv;
+  const TTView* om = sketch_for(P, r, omv);
+  // gradient carriages D_a v_a of every item (items contiguous: one launch per mode)
+  DBuf<double> grad[3];
+  for (int al = 0; al < d; ++al) {
+    grad[al] = DBuf<double>(ctx->pool, v.elems(al) * nb);
+    fibre_operator(ctx, v.core[al], grad[al].get(), (long long)v.r[al] * nb, v.N[al], v.r[al + 1], LRFG_MUL_DERIV,
+                   0.0, 1.0);
+  }
+  // material products, item (al, b) = a (.) e_al of item b at al * nb + b, truncated together
+  int rk[4];
+  for (int j = 0; j <= d; ++j) rk[j] = a.r[j] * v.r[j];
+  const int m = d * nb;
+  TTBatch w;
+  if (om) {
+    LRFG_REQUIRE(m <= kMaxSketchItems, "too many right-hand sides for one lockstep batch (%d)", nb);
+    SketchSource z;
+    z.kind = SketchSource::KHATRI_RAO;
+    z.d = d;
+    z.nb = m;
+    z.x = a;
+    for (int j = 0; j < 3; ++j) z.N[j] = v.N[j];
+    for (int j = 0; j <= d; ++j) {
+      z.s[j] = rk[j];
+      z.ry[j] = v.r[j];
+    }
+    for (int al = 0; al < d; ++al)
+      for (int b = 0; b < nb; ++b)
+        for (int j = 0; j < d; ++j)
+          z.y[j][al * nb + b] = (j == al ? grad[j].get() : v.core[j]) + (size_t)b * v.elems(j);
+    tt_round_sketch(ctx, z, *om, r, w, 0.0);
+  } else {
+    TTBatch kr;
+    ttb_alloc(ctx, kr, d, v.N, rk, m);
+    for (int al = 0; al < d; ++al)
+      for (int b = 0; b < nb; ++b)
+        for (int j = 0; j < d; ++j)
+          khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1],
+                     (j == al ? grad[j].get() : v.core[j]) + (size_t)b * v.elems(j), v.r[j], v.r[j + 1],
+                     kr.core[j].get() + (size_t)(al * nb + b) * kr.elems(j));
+    tt_round_batch(ctx, batch_view(kr), r, w, 0.0);
+  }
+  for (auto& g : grad) g.reset();
+  // divergence: -D_al on carriage al of the items of component al (contiguous), then the block sum over al
+  TTBatchView terms[3];
+  for (int al = 0; al < d; ++al) {
+    double* c = w.core[al].get() + (size_t)al * nb * w.elems(al);
+    fibre_operator(ctx, c, c, (long long)w.r[al] * nb, w.N[al], w.r[al + 1], LRFG_MUL_DERIV, 0.0, -1.0);
+    TTBatchView t = batch_view(w);
+    t.nb = nb;
+    for (int j = 0; j < d; ++j) t.core[j] = w.core[j].get() + (size_t)al * nb * w.elems(j);
+    terms[al] = t;
+  }
+  TTBatch acc;
+  ttb_add_many(ctx, terms, d, nullptr, nullptr, acc);
+  w = TTBatch();
+  TTBatch sdiv;
+  tt_round_batch(ctx, batch_view(acc), r, sdiv, 0.0);          // T after the sum
+  acc = TTBatch();
+  ttb_precond(ctx, batch_view(sdiv), P->pt, P->pw, r, out, 0.0, om);  // T P~^-1
+}
+
+// copy of item b of `src` into item b of `dst` (same shapes)
+void ttb_copy_item(lrfg_ctx* ctx, const TTBatch& src, TTBatch& dst, int b) {
+  for (int j = 0; j < src.d; ++j)
+    LRFG_CUDA(cudaMemcpyAsync(dst.core[j].get() + (size_t)b * dst.elems(j), src.core[j].get() + (size_t)b * src.elems(j),
+                              sizeof(double) * src.elems(j), cudaMemcpyDeviceToDevice, ctx->stream));
+}
+
+// The minimal-residual iteration of solve_tt for nb right-hand sides E_i (row i of E, d entries each) in
+// lockstep: the same steps, the operator applied to all residuals (and iterates) in one launch sequence.  Each
+// item keeps its own step length, best iterate and stopping test; items that have stopped ride along until
+// the last one stops, their results frozen.  The results equal solve_tt's up to the rounding order of the
+// batched products.
+void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
+  lrfg_ctx* ctx = P->ctx;
+  const int d = P->d, rk = P->opts.rank;
+  // right-hand sides (item by item: once per solve), packed into one batch of rank-rk trains
+  std::vector<TT> bs(nb);
+  for (int i = 0; i < nb; ++i) lr_rhs(P, E + (size_t)i * d, bs[i], rk);
+  int rr[4] = {1, 1, 1, 1};
+  for (int j = 0; j <= d; ++j) rr[j] = bs[0].r[j];
+  for (int i = 1; i < nb; ++i)
+    for (int j = 0; j <= d; ++j) rr[j] = std::max(rr[j], bs[i].r[j]);
+  TTBatch b;
+  ttb_alloc(ctx, b, d, P->N, rr, nb);
+  for (int i = 0; i < nb; ++i) {
+    // right-hand sides of lower rank (e.g. E = 0) are embedded with zero blocks
+    TTBatchView one{};
+    one.d = d;
+    one.nb = 1;
+    for (int j = 0; j < 3; ++j) one.N[j] = P->N[j];
+    for (int j = 0; j <= d; ++j) one.r[j] = bs[i].r[j];
+    for (int j = 0; j < d; ++j) one.core[j] = bs[i].core[j].get();
+    TTBatch packed;
+    if (std::equal(one.r, one.r + d + 1, rr)) {
+      for (int j = 0; j < d; ++j)
+        LRFG_CUDA(cudaMemcpyAsync(b.core[j].get() + (size_t)i * b.elems(j), bs[i].core[j].get(),
+                                  sizeof(double) * b.elems(j), cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      for (int j = 0; j < d; ++j) {
+        const int A = rr[j], B = rr[j + 1];
+        fill(ctx, b.core[j].get() + (size_t)i * b.elems(j), 0.0, (long long)b.elems(j));
+        tt_embed(ctx, bs[i].core[j].get(), one.r[j], P->N[j], one.r[j + 1], b.core[j].get() + (size_t)i * b.elems(j),
+                 A, B, 0, 0);
+      }
+    }
+  }
+  bs.clear();
+  DBuf<double> dots(ctx->pool, (size_t)2 * nb);
+  std::vector<double> h(2 * nb);
+  auto host_dots = [&](const TTBatch& x, const TTBatch& y, const TTBatch* x2, const TTBatch* y2) {
+    ttb_dot_device(ctx, batch_view(x), batch_view(y), dots.get());
+    if (x2) ttb_dot_device(ctx, batch_view(*x2), batch_view(*y2), dots.get() + nb);
+    LRFG_CUDA(cudaMemcpyAsync(h.data(), dots.get(), sizeof(double) * (x2 ? 2 : 1) * nb, cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+  };
+  host_dots(b, b, nullptr, nullptr);
+  std::vector<double> nb2(nb), best(nb, INFINITY);
+  for (int i = 0; i < nb; ++i) nb2[i] = std::sqrt(std::max(h[i], 0.0));
+  std::vector<int> best_it(nb, 0), active(nb, 1), best_zero(nb, 1);
+  std::vector<double> omega(nb);
+  DBuf<double> om_dev(ctx->pool, (size_t)nb);
+  TTBatch u, r;
+  std::vector<TT> best_u(nb);  // each item's best iterate (its ranks may differ from the current ones)
+  bool u_zero = true;
+  int it = 0, applies = 0;
+  // r = b
+  ttb_alloc(ctx, r, d, P->N, rr, nb);
+  for (int i = 0; i < nb; ++i) ttb_copy_item(ctx, b, r, i);
+  auto any_active = [&]() { return std::any_of(active.begin(), active.end(), [](int a) { return a != 0; }); };
+  // nr: relative residuals of the current iterates (1 for u = 0)
+  std::vector<double> nr(nb, 1.0);
+  for (int i = 0; i < nb; ++i)
+    if (nb2[i] == 0.0) { active[i] = 0; best[i] = 0.0; }
+  while (true) {
+    for (int i = 0; i < nb; ++i) {
+      if (!active[i]) continue;
+      if (nr[i] < best[i]) {
+        best[i] = nr[i];
+        best_it[i] = it;
+        best_zero[i] = u_zero ? 1 : 0;
+        if (!u_zero) tt_copy(ctx, item_view(u, i), best_u[i]);
+      } else if (P->opts.stop_on_increase) {
+        active[i] = 0;
+        continue;
+      }
+      if (nr[i] <= P->opts.tol || it >= P->opts.maxit) active[i] = 0;
+    }
+    if (!any_active()) break;
+    // q = C r; omega = (q, r) / (q, q)
+    TTBatch q;
+    apply_batch(P, batch_view(r), q, rk);
+    ++applies;
+    host_dots(q, q, &q, &r);
+    for (int i = 0; i < nb; ++i) omega[i] = (h[i] > 0.0) ? h[nb + i] / h[i] : 0.0;
+    LRFG_CUDA(cudaMemcpyAsync(om_dev.get(), omega.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, ctx->stream));
+    // u <- T(u + omega r)
+    TTBatch sum;
+    if (u_zero) {
+      TTBatchView t = batch_view(r);
+      const double* ds[1] = {om_dev.get()};
+      ttb_add_many(ctx, &t, 1, nullptr, ds, sum);
+    } else {
+      TTBatchView t[2] = {batch_view(u), batch_view(r)};
+      const double* ds[2] = {nullptr, om_dev.get()};
+      ttb_add_many(ctx, t, 2, nullptr, ds, sum);
+    }
+    TTBatch un;
+    tt_round_batch(ctx, batch_view(sum), rk, un, 0.0);
+    u = std::move(un);
+    u_zero = false;
+    ++it;
+    // r <- T(b - C u)
+    TTBatch cu;
+    apply_batch(P, batch_view(u), cu, rk);
+    ++applies;
+    TTBatchView t[2] = {batch_view(b), batch_view(cu)};
+    const double hs[2] = {1.0, -1.0};
+    TTBatch diff;
+    ttb_add_many(ctx, t, 2, hs, nullptr, diff);
+    TTBatch rn;
+    tt_round_batch(ctx, batch_view(diff), rk, rn, 0.0);
+    r = std::move(rn);
+    host_dots(r, r, nullptr, nullptr);
+    for (int i = 0; i < nb; ++i) nr[i] = nb2[i] > 0.0 ? std::sqrt(std::max(h[i], 0.0)) / nb2[i] : 0.0;
+  }
+  for (int i = 0; i < nb; ++i) {
+    lrfg_result& o = res[i];
+    o = lrfg_result{};
+    o.iters = best_it[i];
+    o.rel_resid = nb2[i] > 0.0 ? best[i] : 0.0;
+    o.converged = o.rel_resid <= P->opts.tol ? 1 : 0;
+    o.applies = 2 * it;
+    if (best_zero[i] || !best_u[i].d) {
+      TT z;
+      int r1[4] = {1, 1, 1, 1};
+      tt_alloc(ctx, z, d, P->N, r1);
+      for (int j = 0; j < d; ++j) fill(ctx, z.core[j].get(), 0.0, P->N[j]);
+      o.Aeff = lr_aeff(P, E + (size_t)i * d, view_of(z));
+      for (int j = 0; j < 4; ++j) o.ranks[j] = 1;
+    } else {
+      o.Aeff = lr_aeff(P, E + (size_t)i * d, view_of(best_u[i]));
+      for (int j = 0; j < 4; ++j) o.ranks[j] = j <= d ? best_u[i].r[j] : 1;
+    }
+  }
+  (void)applies;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
@@ -1601,6 +1826,34 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field
   });
 }
 
+lrfg_status lrfg_problem_solve_many(lrfg_problem* P, int nb, const double* E, lrfg_result* res) {
+  if (!P) return LRFG_EINVAL;
+  bool noconv = false;
+  lrfg_status st = guard(P->ctx, [&] {
+    LRFG_REQUIRE(E && res && nb >= 1, "null argument or nb < 1");
+    for (int i = 0; i < nb * P->d; ++i) LRFG_REQUIRE(std::isfinite(E[i]), "E must be finite");
+    auto t0 = std::chrono::steady_clock::now();
+    if (lockstep_ok(P) && nb * P->d <= kMaxSketchItems) {
+      solve_tt_many(P, E, nb, res);
+      LRFG_CUDA(cudaStreamSynchronize(P->ctx->stream));
+    } else {
+      for (int i = 0; i < nb; ++i) {
+        const lrfg_status s1 = lrfg_problem_solve(P, E + (size_t)i * P->d, res + i, nullptr);
+        if (s1 != LRFG_OK && s1 != LRFG_ENOCONV) fail(s1, "%s", P->ctx->last_error.c_str());
+      }
+    }
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < nb; ++i) {
+      res[i].seconds = sec;
+      if (!res[i].converged && !(P->opts.fmt != LRFG_FULL && P->opts.stop_on_increase && res[i].applies > 0 &&
+                                 res[i].iters < P->opts.maxit))
+        noconv = true;
+    }
+  });
+  if (st == LRFG_OK && noconv) return LRFG_ENOCONV;
+  return st;
+}
+
 // The homogenised tensor of Eq. (homog): A_eff E.E is a quadratic form in E (Sec. 2.1), so its diagonal comes
 // from the solves with E = e_a and every off-diagonal entry from one more solve by polarisation,
 // A_ab = (q(e_a + e_b) - q(e_a) - q(e_b)) / 2, q(E) = A_eff E.E: d (d + 1) / 2 solves in all.
@@ -1612,19 +1865,21 @@ lrfg_status lrfg_problem_aeff_tensor(lrfg_problem* P, double* A, lrfg_result* re
   }
   const int d = P->d;
   double q[3][3] = {};
-  bool noconv = false;
+  // the d (d + 1) / 2 right-hand sides, solved together (in lockstep where the problem allows it)
+  std::vector<double> Es;
+  for (int a = 0; a < d; ++a)
+    for (int b = a; b < d; ++b)
+      for (int j = 0; j < d; ++j) Es.push_back((j == a || j == b) ? 1.0 : 0.0);
+  const int ns = (int)Es.size() / d;
+  std::vector<lrfg_result> rs(ns);
+  const lrfg_status st = lrfg_problem_solve_many(P, ns, Es.data(), rs.data());
+  if (st != LRFG_OK && st != LRFG_ENOCONV) return st;
+  const bool noconv = st == LRFG_ENOCONV;
   int k = 0;
   for (int a = 0; a < d; ++a)
     for (int b = a; b < d; ++b, ++k) {
-      double E[3] = {0.0, 0.0, 0.0};
-      E[a] = 1.0;
-      if (b != a) E[b] = 1.0;
-      lrfg_result r{};
-      const lrfg_status st = lrfg_problem_solve(P, E, &r, nullptr);
-      if (st == LRFG_ENOCONV) noconv = true;
-      else if (st != LRFG_OK) return st;
-      if (results) results[k] = r;
-      q[a][b] = r.Aeff;
+      if (results) results[k] = rs[k];
+      q[a][b] = rs[k].Aeff;
     }
   for (int a = 0; a < d; ++a) {
     A[a * d + a] = q[a][a];

@@ -149,8 +149,9 @@ void tt_embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double* dst
 // nb tensor trains z_b of order d with ranks s: DENSE carriages (item after item), KHATRI_RAO products
 // z_b = x (.) y_b (x shared, y_b's carriages given per item, ranks ry), or BLOCKS (nb = 1): the exponential-sum
 // product whose carriage j holds nblocks blocks of shape (ry[j], N, ry[j+1]) at blocks[j] + m * block size,
-// first carriage block-concatenated along its last index, last along its first, middle block-diagonal.
-constexpr int kMaxSketchItems = 4;
+// first carriage block-concatenated along its last index, last along its first, middle block-diagonal (nb items:
+// bstride apart between blocks, one block size apart between items).
+constexpr int kMaxSketchItems = 32;
 struct SketchSource {
   enum Kind { DENSE = 0, KHATRI_RAO = 1, BLOCKS = 2 };
   Kind kind = DENSE;
@@ -163,6 +164,8 @@ struct SketchSource {
   int ry[4] = {1, 1, 1, 1};
   int nblocks = 0;
   const double* blocks[3] = {nullptr, nullptr, nullptr};
+  long long bstride[3] = {0, 0, 0};  // BLOCKS: elements between blocks m and m+1 (0: one block's size); item b's
+                                     // blocks start b block sizes further on
   void materialise(lrfg_ctx* ctx, int j, double* dst) const;                      // first or last carriage
   void right_middle(lrfg_ctx* ctx, const double* W, int ell, double* T) const;     // T = Z_1 x_3 W
   void left_middle(lrfg_ctx* ctx, const double* M, int ell, double* X) const;      // X = M x_1 Z_1
@@ -172,6 +175,18 @@ void sketch_tt(lrfg_ctx* ctx, int d, const int* N, int ell, unsigned long long s
 // randomised rounding of every item to rank rmax (tolerance tol > 0: the smallest ranks <= rmax within it)
 void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out,
                      double tol = 0.0);
+
+// ---- ttbatch.cu ---------------------------------------------------------------------------------
+TTView item_view_of(const TTBatchView& x, int b);
+// out_i = sum_t s_t,i x_t,i in block form for every item i (s_t,i = hs[t] * ds[t][i], either may be null; the
+// scale multiplies the first carriage)
+void ttb_add_many(lrfg_ctx* ctx, const TTBatchView* xs, int m, const double* hs, const double* const* ds,
+                  TTBatch& out);
+// out_dev[i] = <x_i, y_i>
+void ttb_dot_device(lrfg_ctx* ctx, const TTBatchView& x, const TTBatchView& y, double* out_dev);
+// out_i = T(P~^-1 x_i) (omega non-null: randomised rounding, one launch sequence for all items)
+void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>& t, const std::vector<double>& w,
+                 int rmax, TTBatch& out, double tol, const TTView* omega);
 
 // ---- tucker.cu ----------------------------------------------------------------------------------
 // Tucker tensor on the device: core (r_0, .., r_{d-1}) row-major, factor j (N_j, r_j) row-major

@@ -70,7 +70,8 @@ struct ItemPtrs {
 
 // T[b][(i,k), n, l] = sum_{i',k'} x[i,n,i'] y_b[k,n,k'] W_b[(i',k'), l]: one block per (n, l-chunk, item);
 // U[i',k,c] = sum_k' y[k,k'] W[(i',k'), c], then T[(i,k),c] = sum_i' x[i,i'] U[i',k,c]
-__global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict__ x, int a0, int a1, ItemPtrs y,
+__global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict__ x, int a0, int a1,
+                                                       const __grid_constant__ ItemPtrs y,
                                                        int r0, int r1, int N, const double* __restrict__ W,
                                                        long long sW, int ell, int LC, double* T, long long sT) {
   extern __shared__ __align__(16) double sm[];
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict_
 
 // Out[b][l, n, (i',k')] = sum_{i,k} M_b[l, (i,k)] x[i,n,i'] y_b[k,n,k']: one block per (n, l-chunk, item);
 // V[c,i,k'] = sum_k M[c,(i,k)] y[k,k'], then Out[c,(i',k')] = sum_i V[c,i,k'] x[i,i']
-__global__ void __launch_bounds__(256) kr_left_kernel(const double* __restrict__ x, int a0, int a1, ItemPtrs y,
+__global__ void __launch_bounds__(256) kr_left_kernel(const double* __restrict__ x, int a0, int a1,
+                                                      const __grid_constant__ ItemPtrs y,
                                                       int r0, int r1, int N, const double* __restrict__ M,
                                                       long long sM, int ell, int LC, double* Out, long long sO) {
   extern __shared__ __align__(16) double sm[];
@@ -173,6 +175,23 @@ __global__ void __launch_bounds__(256) kr_left_kernel(const double* __restrict__
     double s = 0.0;
     for (int i = 0; i < a0; ++i) s = fma(v[(size_t)i * r1], Xs[(size_t)i * a1 + ip], s);
     Ob[((size_t)(l0 + c) * N + n) * s1w + col] = s;
+  }
+}
+
+// Khatri-Rao carriage of every item: out[b][(i,k), n, (i',k')] = x[i,n,i'] y_b[k,n,k'] (first and last carriages of
+// the product, which the rounding needs explicitly; they are small)
+__global__ void kr_items_kernel(const double* __restrict__ x, int a0, int a1, const __grid_constant__ ItemPtrs y, int r0,
+                                int r1, int N, int nb, double* out) {
+  const long long per = (long long)a0 * r0 * N * a1 * r1, total = per * nb;
+  const int s1w = a1 * r1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    const long long q = t - b * per;
+    const int col = (int)(q % s1w);
+    const long long rest = q / s1w;
+    const int n = (int)(rest % N), row = (int)(rest / N);
+    const int i = row / r0, k = row - i * r0, ip = col / r1, kp = col - ip * r1;
+    out[t] = x[((size_t)i * N + n) * a1 + ip] * y.p[b][((size_t)k * N + n) * r1 + kp];
   }
 }
 
@@ -341,6 +360,16 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
 // ------------------------------------------------------------------------------------------------
 void SketchSource::materialise(lrfg_ctx* ctx, int j, double* dst) const {
   const long long e = (long long)s[j] * N[j] * s[j + 1];
+  if (kind == KHATRI_RAO) {
+    ItemPtrs p{};
+    for (int b = 0; b < nb; ++b) p.p[b] = y[j][b];
+    const long long total = e * nb;
+    LRFG_LAUNCH(ctx, KC_KHATRI_RAO, (double)total,
+                sizeof(double) * ((double)total + (double)x.r[j] * N[j] * x.r[j + 1] + (double)nb * ry[j] * N[j] * ry[j + 1]),
+                kr_items_kernel<<<grid_of(ctx, total), 256, 0, ctx->stream>>>(x.core[j], x.r[j], x.r[j + 1], p, ry[j],
+                                                                            ry[j + 1], N[j], nb, dst));
+    return;
+  }
   for (int b = 0; b < nb; ++b) {
     double* o = dst + (size_t)b * e;
     if (kind == DENSE) {
@@ -351,13 +380,12 @@ void SketchSource::materialise(lrfg_ctx* ctx, int j, double* dst) const {
     } else {
       // exponential-sum blocks F_m of carriage j (r_j x N x r_{j+1} each, weights already in carriage 0)
       const int R = nblocks, a = ry[j], c = ry[j + 1];
-      const long long be = (long long)a * N[j] * c;
+      const long long be = (long long)a * N[j] * c, bs = bstride[j] ? bstride[j] : be;
+      const double* src = blocks[j] + (size_t)b * be;
       if (j == 0) {
-        for (int m = 0; m < R; ++m)
-          tt_embed(ctx, blocks[j] + m * be, 1, N[j], c, o, 1, R * c, 0, m * c);
+        for (int m = 0; m < R; ++m) tt_embed(ctx, src + m * bs, 1, N[j], c, o, 1, R * c, 0, m * c);
       } else {
-        for (int m = 0; m < R; ++m)
-          tt_embed(ctx, blocks[j] + m * be, a, N[j], 1, o, R * a, 1, m * a, 0);
+        for (int m = 0; m < R; ++m) tt_embed(ctx, src + m * bs, a, N[j], 1, o, R * a, 1, m * a, 0);
       }
     }
   }
@@ -374,10 +402,12 @@ void SketchSource::right_middle(lrfg_ctx* ctx, const double* W, int ell, double*
     for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
     kr_right(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
   } else {
-    // T[(m,k), n, l] = sum_k' F_m[k, n, k'] W[(m,k'), l]: one product per block (nb = 1)
+    // T[(m,k), n, l] = sum_k' F_m[k, n, k'] W[(m,k'), l]: for each item, one product per block
     const int R = nblocks, a = ry[1], c = ry[2];
-    gemm(ctx, 0, 0, a * n, ell, c, 1.0, blocks[1], c, (long long)a * n * c, W, ell, (long long)c * ell, 0.0, T, ell,
-         (long long)a * n * ell, R);
+    const long long be = (long long)a * n * c, bs = bstride[1] ? bstride[1] : be;
+    for (int b = 0; b < nb; ++b)
+      gemm(ctx, 0, 0, a * n, ell, c, 1.0, blocks[1] + (size_t)b * be, c, bs, W + (size_t)b * s[2] * ell, ell,
+           (long long)c * ell, 0.0, T + (size_t)b * s[1] * n * ell, ell, (long long)a * n * ell, R);
   }
 }
 
@@ -392,14 +422,18 @@ void SketchSource::left_middle(lrfg_ctx* ctx, const double* M, int ell, double* 
     for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
     kr_left(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, M, ell, X);
   } else {
-    // tmp[m][l, n, k'] = sum_k M[l, (m,k)] F_m[k, n, k'], then interleaved into X[l, n, (m,k')]
+    // tmp[m][l, n, k'] = sum_k M[l, (m,k)] F_m[k, n, k'], then interleaved into X[l, n, (m,k')], item by item
     const int R = nblocks, a = ry[1], c = ry[2];
+    const long long be = (long long)a * n * c, bs = bstride[1] ? bstride[1] : be;
     DBuf<double> tmp(ctx->pool, (size_t)R * ell * n * c);
-    gemm(ctx, 0, 0, ell, n * c, a, 1.0, M, R * a, (long long)a, blocks[1], n * c, (long long)a * n * c, 0.0, tmp.get(),
-         n * c, (long long)ell * n * c, R);
     const long long total = (long long)R * ell * n * c;
-    LRFG_LAUNCH(ctx, KC_TT_MISC, 0.0, 16.0 * total,
-                block_interleave_kernel<<<grid_of(ctx, total), 256, 0, ctx->stream>>>(tmp.get(), R, ell, n, c, X));
+    for (int b = 0; b < nb; ++b) {
+      gemm(ctx, 0, 0, ell, n * c, a, 1.0, M + (size_t)b * ell * s[1], R * a, (long long)a, blocks[1] + (size_t)b * be,
+           n * c, bs, 0.0, tmp.get(), n * c, (long long)ell * n * c, R);
+      LRFG_LAUNCH(ctx, KC_TT_MISC, 0.0, 16.0 * total,
+                  block_interleave_kernel<<<grid_of(ctx, total), 256, 0, ctx->stream>>>(
+                      tmp.get(), R, ell, n, c, X + (size_t)b * ell * n * s[2]));
+    }
   }
 }
 
