@@ -95,6 +95,13 @@ static int tile_fibres(lrfg_ctx* ctx, int N, int rows_per_fibre_pair, size_t* sm
   return (int)tf;
 }
 
+// Fewer rows per tile when the fibres are few (the carriages of a low-rank tensor: r^2 fibres of one length),
+// so that the launch still spreads over about `target` blocks instead of leaving most SMs idle.
+static int spread_tf(int tf_max, long long nfib, long long target) {
+  long long tf = (nfib + 2 * target - 1) / (2 * target);
+  return (int)std::max(1LL, std::min((long long)tf_max, tf));
+}
+
 // ----------------------------------------------------------------------------------------------------
 // complex fibres
 // ----------------------------------------------------------------------------------------------------
@@ -263,6 +270,9 @@ void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long oute
   size_t smem;
   int TF = tile_fibres(ctx, N, 2, &smem);
   long long nfib = outer * inner;
+  const int nsm = ctx->num_sms > 0 ? ctx->num_sms : 152;
+  TF = spread_tf(TF, nfib, 2LL * nsm);
+  smem = (size_t)(2LL * N * sizeof(double2) + (long long)TF * 2LL * N * sizeof(double2));
   long long blocks = (nfib + 2LL * TF - 1) / (2LL * TF);
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
   LRFG_CUDA(raise_smem_limit((const void*)fibre_op_kernel, smem));
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __
                                                                 long long inner, int TF, FftPlan pl,
                                                                 const double2* __restrict__ Wg,
                                                                 const double* __restrict__ tm,
-                                                                const double* __restrict__ sc, int nm) {
+                                                                const double* __restrict__ sc, int nm, int mper) {
   extern __shared__ double2 sm[];
   double2* W = sm;
   double2* spec = sm + N;              // TF rows: the shared forward spectrum
@@ -308,7 +318,8 @@ __global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __
   double2* res = stockham_rows<-1>(a, b, rows, N, pl, W);
   for (int t = threadIdx.x; t < rows * N; t += blockDim.x) spec[t] = res[t];
   __syncthreads();
-  for (int m = 0; m < nm; ++m) {
+  const int m_end = min(nm, (int)(blockIdx.y + 1) * mper);
+  for (int m = blockIdx.y * mper; m < m_end; ++m) {
     const double t_m = tm[m];
     for (int t = threadIdx.x; t < rows * N; t += blockDim.x) {
       int k = freq_of(t % N, N);
@@ -342,6 +353,14 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   long long tf = ((long long)limit - (long long)N * (long long)sizeof(double2)) / per;
   if (tf > 64) tf = 64;
   if (tf < 1) tf = 1;
+  // few fibres (low-rank carriages): smaller tiles, and the terms split over grid.y (each block redoes the
+  // shared forward transform of its tile), so that the launch covers the SMs
+  const int nsm = ctx->num_sms > 0 ? ctx->num_sms : 152;
+  const long long nfib0 = outer * inner;
+  tf = spread_tf((int)tf, nfib0, 2LL * nsm);
+  const long long bx = (nfib0 + 2 * tf - 1) / (2 * tf);
+  const int mchunks = (int)std::max(1LL, std::min((long long)nm, (4LL * nsm + bx - 1) / bx));
+  const int mper = (nm + mchunks - 1) / mchunks;
   size_t smem = (size_t)(N * sizeof(double2) + tf * per);
   // device copies of the node and scale tables
   DBuf<double> dt(ctx->pool, nm), ds(ctx->pool, nm);
@@ -349,13 +368,15 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   LRFG_CUDA(cudaMemcpyAsync(ds.get(), scale, sizeof(double) * nm, cudaMemcpyHostToDevice, ctx->stream));
   long long nfib = outer * inner;
   long long blocks = (nfib + 2 * tf - 1) / (2 * tf);
+  LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
   LRFG_CUDA(raise_smem_limit((const void*)fibre_gauss_multi_kernel, smem));
-  // one forward and nm inverse complex transforms per pair of real fibres
+  // one forward and nm inverse complex transforms per pair of real fibres (algorithmic count)
   const double flops = 2.5 * N * std::log2((double)N) * (double)nfib * (1.0 + nm);
   const double bytes = sizeof(double) * (double)N * (double)nfib * (1.0 + nm);
+  const int mgrid = (nm + mper - 1) / mper;
   LRFG_LAUNCH(ctx, KC_GAUSS_MULTI, flops, bytes,
-              fibre_gauss_multi_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(
-                  in, out, out_stride, outer, N, inner, (int)tf, pl, tw.W, dt.get(), ds.get(), nm));
+              fibre_gauss_multi_kernel<<<dim3((unsigned)blocks, (unsigned)mgrid), 256, smem, ctx->stream>>>(
+                  in, out, out_stride, outer, N, inner, (int)tf, pl, tw.W, dt.get(), ds.get(), nm, mper));
   // the pool hands these blocks out again only to later work on the same stream
 }
 
