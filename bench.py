@@ -388,6 +388,14 @@ def run_ours(args):
     ctx.profile(False)
     stats = ctx.profile_read()
 
+    # the same TT solve with LRFG_MIXED (FP32 fibre transforms and sketch side in the steps, FP64 residual)
+    Pmx = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
+                      stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=lrfg.MIXED)
+    Pmx.solve(E, want_field=False)
+    mx_ms, mx_res = timed_solves(Pmx, E, 2, stream, flush)
+    tt_mixed = {"solves_per_s": 1e3 / statistics.median(mx_ms), "p50_ms": pct(mx_ms, 50), "p99_ms": pct(mx_ms, 99),
+                "iters": mx_res[-1].iters, "aeff": mx_res[-1].Aeff,
+                "aeff_rel_err": abs(mx_res[-1].Aeff - full_res.Aeff) / full_res.Aeff}
     # the homogenised tensor (Eq. (homog)): the d (d + 1) / 2 = 6 solves of the polarisation fields, TT in
     # lockstep (lrfg_problem_solve_many: one launch sequence for all six) against six full FP64 solves
     Es6 = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 1.0]]
@@ -412,6 +420,18 @@ def run_ours(args):
               "full_fp64": {"solves_per_s": 6e3 / full6_ms, "seconds": full6_ms / 1e3},
               "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(tensor_tt, full6))}
     tensor["tt_vs_full_fp64"] = tensor["tt_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
+    Pmx.solve_many(Es6)
+    flush.fill_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mx6 = Pmx.solve_many(Es6)
+    e1.record(stream)
+    e1.synchronize()
+    tensor["tt_mixed_lockstep"] = {"solves_per_s": 6e3 / e0.elapsed_time(e1),
+                                   "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(mx6, full6))}
+    tensor["tt_mixed_vs_full_fp64"] = tensor["tt_mixed_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
+    Pmx.free()
 
     # the configuration of the previous measurements: TT rank 10, deterministic rounding, stop on increase
     P10 = ctx.problem(a_tt, lr_fmt, rank=10, pinv_eps=args.pinv_eps, tol=1e-12, maxit=60, stop_on_increase=True)
@@ -454,6 +474,7 @@ def run_ours(args):
                            "tol": 1e-5, "aeff": mix_res.Aeff,
                            "aeff_rel_err_vs_f64": abs(mix_res.Aeff - full_res.Aeff) / full_res.Aeff},
             "tt_vs_full_fp64": solves_per_s / world / (1e3 / statistics.median(full_ms)),
+            "tt_mixed": tt_mixed,
             "homogenised_tensor_6_solves": tensor,
             "tt_rank10_deterministic": {"solves_per_s": 1e3 / statistics.median(ms10), "iters": r10[-1].iters,
                                         "aeff_rel_err": abs(r10[-1].Aeff - full_res.Aeff) / full_res.Aeff},

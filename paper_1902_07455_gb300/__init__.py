@@ -380,7 +380,8 @@ class Context:
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
                 coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
                 disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0) -> "Problem":
-        """``prec``: LRFG_FP64, or LRFG_MIXED (FP32 storage and FFTs, FP64 scalars; FULL only).
+        """``prec``: LRFG_FP64, or LRFG_MIXED (FULL: FP32 storage and FFTs, FP64 scalars; TT: FP32 fibre transforms
+        and sketch side in the solve's steps, FP64 residual, values, eigen-decompositions, dots and A_eff).
         ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
         rank cap of a grid coefficient's TT compression (0: ``rank``).  ``rank_start`` > 0: rank-adapting
         MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT).  ``B``: constant symmetric

@@ -161,7 +161,7 @@ void resolve_profile(lrfg_ctx* ctx) {
 
 static const char* kClassNames[KC_COUNT] = {
     "fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "pointwise",
-    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor", "sketch"};
+    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor", "sketch", "gemm_f32"};
 
 }  // namespace lrfg
 
@@ -489,8 +489,10 @@ void lr_apply_ga(lrfg_problem* P, const TTView& v, TT& out, int r) {
   tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol);
 }
 
-// rank r of every truncation (the problem's rank, or the current rank of a rank-adapting solve)
-void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
+// rank r of every truncation (the problem's rank, or the current rank of a rank-adapting solve).  mixed: the
+// operator of the mixed-precision path (FP32 fibre transforms and FP32 sketch side of the randomised rounding;
+// carriages, projections, eigen-decompositions and inner products in FP64)
+void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r, bool mixed = false) {
   if (P->ga) {
     lr_apply_ga(P, v, out, r);
     return;
@@ -504,7 +506,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
   for (int alpha = 0; alpha < d; ++alpha) {
     grad[alpha] = DBuf<double>(ctx->pool, (size_t)v.r[alpha] * v.N[alpha] * v.r[alpha + 1]);
     fibre_operator(ctx, v.core[alpha], grad[alpha].get(), v.r[alpha], v.N[alpha], v.r[alpha + 1], LRFG_MUL_DERIV,
-                   0.0, 1.0);
+                   0.0, 1.0, mixed);
   }
   // material products A~ e_a for all components at once (Khatri–Rao carriages), one batch of d TTs
   int rk[4];
@@ -529,7 +531,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
     }
     for (int alpha = 0; alpha < d; ++alpha)
       for (int j = 0; j < d; ++j) z.y[j][alpha] = (j == alpha) ? grad[j].get() : v.core[j];
-    tt_round_sketch(ctx, z, *om, r, w, tol);                     // T, all components in one sweep
+    tt_round_sketch(ctx, z, *om, r, w, tol, mixed);              // T, all components in one sweep
     for (auto& g : grad) g.reset();
     for (int alpha = 0; alpha < d; ++alpha) terms[alpha] = item_view(w, alpha);
   } else {
@@ -574,13 +576,13 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r) {
   for (int alpha = 0; alpha < d; ++alpha) {
     double* c = const_cast<double*>(terms[alpha].core[alpha]);
     fibre_operator(ctx, c, c, terms[alpha].r[alpha], terms[alpha].N[alpha], terms[alpha].r[alpha + 1], LRFG_MUL_DERIV,
-                   0.0, -1.0);
+                   0.0, -1.0, mixed);
   }
   TT acc;
   tt_add_many(ctx, terms, nullptr, d, acc);
   TT sdiv;
   tt_round(ctx, view_of(acc), r, sdiv, tol);                   // T after the sum
-  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol, om);  // T P~^-1
+  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol, om, mixed);  // T P~^-1
 }
 
 void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
@@ -828,7 +830,7 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     out->tk = std::move(res);
   } else {
     TT res;
-    lr_apply(P, view_of(in->tt), res, P->opts.rank);
+    lr_apply(P, view_of(in->tt), res, P->opts.rank, P->opts.prec == LRFG_MIXED);
     out->tt = std::move(res);
   }
 }
@@ -927,7 +929,9 @@ void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field
 // Sec. 4.3 proposes; opts.rank_start > 0): every T truncates to the current rank r_c, starting at
 // rank_start; when the residual fails to decrease below the cap opts.rank, r_c rises by rank_step, the
 // right-hand side is rebuilt at r_c and the iteration restarts from the best iterate, whose residual is
-// recomputed at r_c and becomes the new reference.
+// recomputed at r_c and becomes the new reference.  LRFG_MIXED: the step q = C r uses the mixed-precision operator,
+// the residual r = T(b - C u) the FP64 one, so the iteration is a defect correction whose fixed point is the FP64
+// solution (the step length only has to reduce the FP64 residual).
 void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u_out) {
   lrfg_ctx* ctx = P->ctx;
   const int cap = P->opts.rank;
@@ -979,7 +983,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
     }
     if (nr <= P->opts.tol || it >= P->opts.maxit) break;
     TT q;
-    lr_apply(P, view_of(r), q, rc);
+    lr_apply(P, view_of(r), q, rc, P->opts.prec == LRFG_MIXED);  // (mixed: the search direction's operator)
     ++applies;
     const double qq = tt_dot(ctx, view_of(q), view_of(q));
     if (qq == 0.0) break;
@@ -1031,7 +1035,7 @@ bool lockstep_ok(const lrfg_problem* P) {
 
 // The operator of lr_apply on nb items at once (items of identical ranks, stored item after item): the gradient,
 // material, divergence, sum and preconditioner stages each take one launch sequence for all items.
-void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r) {
+void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, bool mixed = false) {
   lrfg_ctx* ctx = P->ctx;
   const int d = P->d, nb = v.nb;
   const TTView a = view_of(P->a_tt);
@@ -1042,7 +1046,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r) {
   for (int al = 0; al < d; ++al) {
     grad[al] = DBuf<double>(ctx->pool, v.elems(al) * nb);
     fibre_operator(ctx, v.core[al], grad[al].get(), (long long)v.r[al] * nb, v.N[al], v.r[al + 1], LRFG_MUL_DERIV,
-                   0.0, 1.0);
+                   0.0, 1.0, mixed);
   }
   // material products, item (al, b) = a (.) e_al of item b at al * nb + b, truncated together
   int rk[4];
@@ -1065,7 +1069,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r) {
       for (int b = 0; b < nb; ++b)
         for (int j = 0; j < d; ++j)
           z.y[j][al * nb + b] = (j == al ? grad[j].get() : v.core[j]) + (size_t)b * v.elems(j);
-    tt_round_sketch(ctx, z, *om, r, w, 0.0);
+    tt_round_sketch(ctx, z, *om, r, w, 0.0, mixed);
   } else {
     TTBatch kr;
     ttb_alloc(ctx, kr, d, v.N, rk, m);
@@ -1082,7 +1086,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r) {
   TTBatchView terms[3];
   for (int al = 0; al < d; ++al) {
     double* c = w.core[al].get() + (size_t)al * nb * w.elems(al);
-    fibre_operator(ctx, c, c, (long long)w.r[al] * nb, w.N[al], w.r[al + 1], LRFG_MUL_DERIV, 0.0, -1.0);
+    fibre_operator(ctx, c, c, (long long)w.r[al] * nb, w.N[al], w.r[al + 1], LRFG_MUL_DERIV, 0.0, -1.0, mixed);
     TTBatchView t = batch_view(w);
     t.nb = nb;
     for (int j = 0; j < d; ++j) t.core[j] = w.core[j].get() + (size_t)al * nb * w.elems(j);
@@ -1094,7 +1098,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r) {
   TTBatch sdiv;
   tt_round_batch(ctx, batch_view(acc), r, sdiv, 0.0);          // T after the sum
   acc = TTBatch();
-  ttb_precond(ctx, batch_view(sdiv), P->pt, P->pw, r, out, 0.0, om);  // T P~^-1
+  ttb_precond(ctx, batch_view(sdiv), P->pt, P->pw, r, out, 0.0, om, mixed);  // T P~^-1
 }
 
 // copy of item b of `src` into item b of `dst` (same shapes)
@@ -1188,7 +1192,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
     if (!any_active()) break;
     // q = C r; omega = (q, r) / (q, q)
     TTBatch q;
-    apply_batch(P, batch_view(r), q, rk);
+    apply_batch(P, batch_view(r), q, rk, P->opts.prec == LRFG_MIXED);
     ++applies;
     host_dots(q, q, &q, &r);
     for (int i = 0; i < nb; ++i) omega[i] = (h[i] > 0.0) ? h[nb + i] / h[i] : 0.0;
@@ -1593,8 +1597,8 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     if (opts->fmt == LRFG_CP && coeff->d != 2)
       fail(LRFG_ENOTSUP, "LRFG_CP is provided for d = 2 (its truncation is ill-posed for d >= 3, App. A.1)");
     LRFG_REQUIRE(opts->prec == LRFG_FP64 || opts->prec == LRFG_MIXED, "unknown precision %d", (int)opts->prec);
-    if (opts->prec == LRFG_MIXED && opts->fmt != LRFG_FULL)
-      fail(LRFG_ENOTSUP, "LRFG_MIXED is implemented for LRFG_FULL solutions only");
+    if (opts->prec == LRFG_MIXED && opts->fmt != LRFG_FULL && !(opts->fmt == LRFG_TT && opts->disc == LRFG_GANI))
+      fail(LRFG_ENOTSUP, "LRFG_MIXED is implemented for LRFG_FULL and LRFG_TT (GaNi) solutions");
     LRFG_REQUIRE(opts->maxit >= 0, "maxit must be >= 0");
     LRFG_REQUIRE(opts->tol >= 0.0, "tol must be >= 0");
     if (opts->fmt != LRFG_FULL) LRFG_REQUIRE(opts->rank >= 1, "low-rank solve needs rank >= 1 (got %d)", opts->rank);

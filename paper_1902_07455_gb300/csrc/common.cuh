@@ -132,6 +132,7 @@ enum KClass {
   KC_TT_MISC,         // block embedding, balancing, scaling, transposes, fills
   KC_CHOL,            // pivoted Cholesky factors of the Gram matrices (TT rounding)
   KC_SKETCH,          // fused Khatri-Rao contractions of the randomised rounding
+  KC_GEMM32,          // FP32 products (the sketch side of the mixed-precision randomised rounding)
   KC_COUNT
 };
 struct KStats {
@@ -217,6 +218,14 @@ void fold_device_work(lrfg_ctx* ctx);
 // tile, and lowering it under them would make their launches fail.
 cudaError_t raise_smem_limit(const void* func, size_t bytes);
 }  // namespace lrfg
+
+// the same with the class given as an expression
+#define LRFG_LAUNCH_KC(ctx, kcexpr, flops, bytes, ...)                        \
+  do {                                                                        \
+    ::lrfg::KTimer kt_((ctx), (kcexpr), (double)(flops), (double)(bytes));    \
+    __VA_ARGS__;                                                              \
+    LRFG_CHECK_LAUNCH();                                                      \
+  } while (0)
 
 // launch a kernel with accounting: LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, kernel<<<...>>>(args));
 #define LRFG_LAUNCH(ctx, kc, flops, bytes, ...)                 \

@@ -210,24 +210,30 @@ __device__ __forceinline__ double2 multiplier(int kind, int k, double param) {
   return make_double2(1.0, 0.0);
 }
 
+// V = double2 (FP64 transforms) or float2 (FP32 transforms of FP64 data: the mixed-precision path); the fibres
+// are read and written in FP64 either way.
+template <typename V>
 __global__ void __launch_bounds__(256) fibre_op_kernel(const double* in, double* out, long long outer,
                                                        int N, long long inner, int TF, FftPlan pl,
-                                                       const double2* __restrict__ Wg, int kind, double param,
+                                                       const V* __restrict__ Wg, int kind, double param,
                                                        double scale) {
-  extern __shared__ double2 sm[];
-  double2* W = sm;
-  double2* M = sm + N;
-  double2* a = sm + 2 * N;
-  double2* b = a + (size_t)TF * N;
+  using R = typename RealOf<V>::T;
+  extern __shared__ __align__(16) unsigned char smraw_op[];
+  V* sm = (V*)smraw_op;
+  V* W = sm;
+  V* M = sm + N;
+  V* a = sm + 2 * N;
+  V* b = a + (size_t)TF * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     W[j] = Wg[j];
-    M[j] = multiplier(kind, freq_of(j, N), param);
+    const double2 m = multiplier(kind, freq_of(j, N), param);
+    M[j] = mkc<V>((R)m.x, (R)m.y);
   }
   const long long nfib = outer * inner;
   const long long g0 = (long long)blockIdx.x * (2LL * TF);
   const int nf = (int)min(2LL * TF, nfib - g0);   // real fibres in this tile
   const int rows = min(nf, TF);
-  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) a[t] = make_double2(0.0, 0.0);
+  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) a[t] = mkc<V>((R)0, (R)0);
   __syncthreads();
   const int total = nf * N;
   const bool across = inner >= 2 * TF;
@@ -236,12 +242,12 @@ __global__ void __launch_bounds__(256) fibre_op_kernel(const double* in, double*
     if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
     long long g = g0 + f;
     long long o = g / inner, i = g - o * inner;
-    double v = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
+    const R v = (R)in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
     if (f < TF) a[(size_t)f * N + n].x = v; else a[(size_t)(f - TF) * N + n].y = v;
   }
   __syncthreads();
-  double2* res = stockham_rows<-1>(a, b, rows, N, pl, W);
-  double2* other = (res == a) ? b : a;
+  V* res = stockham_rows<-1>(a, b, rows, N, pl, W);
+  V* other = (res == a) ? b : a;
   for (int t = threadIdx.x; t < rows * N; t += blockDim.x) {
     int n = t % N;
     res[t] = cmul(res[t], M[n]);
@@ -254,55 +260,65 @@ __global__ void __launch_bounds__(256) fibre_op_kernel(const double* in, double*
     if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
     long long g = g0 + f;
     long long o = g / inner, i = g - o * inner;
-    double2 v = (f < TF) ? res[(size_t)f * N + n] : res[(size_t)(f - TF) * N + n];
-    out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = s * ((f < TF) ? v.x : v.y);
+    V v = (f < TF) ? res[(size_t)f * N + n] : res[(size_t)(f - TF) * N + n];
+    out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = s * (double)((f < TF) ? v.x : v.y);
   }
 }
 
-void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
-                    int kind, double param, double scale) {
-  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
-  LRFG_REQUIRE(kind == LRFG_MUL_IDENTITY || kind == LRFG_MUL_DERIV || kind == LRFG_MUL_GAUSS,
-               "unknown multiplier %d", kind);
-  if (outer == 0 || inner == 0) return;
-  FftPlan pl = make_plan(N, plan_radix<double2>());
-  const Twiddles& tw = twiddles_for(ctx, N);
+template <typename V>
+static void fibre_operator_t(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
+                             int kind, double param, double scale) {
+  FftPlan pl = make_plan(N, plan_radix<V>());
+  const V* W = twiddle_table<typename RealOf<V>::T>(ctx, N);
   size_t smem;
-  int TF = tile_fibres(ctx, N, 2, &smem);
+  int TF = tile_fibres(ctx, N, 2, &smem, sizeof(V));
   long long nfib = outer * inner;
   const int nsm = ctx->num_sms > 0 ? ctx->num_sms : 152;
   TF = spread_tf(TF, nfib, 2LL * nsm);
-  smem = (size_t)(2LL * N * sizeof(double2) + (long long)TF * 2LL * N * sizeof(double2));
+  smem = (size_t)(2LL * N * sizeof(V) + (long long)TF * 2LL * N * sizeof(V));
   long long blocks = (nfib + 2LL * TF - 1) / (2LL * TF);
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
-  LRFG_CUDA(raise_smem_limit((const void*)fibre_op_kernel, smem));
+  LRFG_CUDA(raise_smem_limit((const void*)fibre_op_kernel<V>, smem));
   // two complex transforms per pair of real fibres
   const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;
   const double bytes = 2.0 * sizeof(double) * (double)N * (double)nfib;
   LRFG_LAUNCH(ctx, KC_FIBRE_OP, flops, bytes,
-              fibre_op_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, tw.W,
-                                                                             kind, param, scale));
+              fibre_op_kernel<V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W,
+                                                                                kind, param, scale));
+}
+
+void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
+                    int kind, double param, double scale, bool fp32) {
+  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
+  LRFG_REQUIRE(kind == LRFG_MUL_IDENTITY || kind == LRFG_MUL_DERIV || kind == LRFG_MUL_GAUSS,
+               "unknown multiplier %d", kind);
+  if (outer == 0 || inner == 0) return;
+  if (fp32) fibre_operator_t<float2>(ctx, in, out, outer, N, inner, kind, param, scale);
+  else fibre_operator_t<double2>(ctx, in, out, outer, N, inner, kind, param, scale);
 }
 
 // Many Gaussian multipliers of one input: the forward transform is shared, each term m gets its own
 // multiply + inverse transform and is written to out + m * out_stride.
+template <typename V>
 __global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __restrict__ in, double* out,
                                                                 long long out_stride, long long outer, int N,
                                                                 long long inner, int TF, FftPlan pl,
-                                                                const double2* __restrict__ Wg,
+                                                                const V* __restrict__ Wg,
                                                                 const double* __restrict__ tm,
                                                                 const double* __restrict__ sc, int nm, int mper) {
-  extern __shared__ double2 sm[];
-  double2* W = sm;
-  double2* spec = sm + N;              // TF rows: the shared forward spectrum
-  double2* a = spec + (size_t)TF * N;  // TF rows
-  double2* b = a + (size_t)TF * N;     // TF rows
+  using R = typename RealOf<V>::T;
+  extern __shared__ __align__(16) unsigned char smraw_gm[];
+  V* sm = (V*)smraw_gm;
+  V* W = sm;
+  V* spec = sm + N;              // TF rows: the shared forward spectrum
+  V* a = spec + (size_t)TF * N;  // TF rows
+  V* b = a + (size_t)TF * N;     // TF rows
   for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
   const long long nfib = outer * inner;
   const long long g0 = (long long)blockIdx.x * (2LL * TF);
   const int nf = (int)min(2LL * TF, nfib - g0);
   const int rows = min(nf, TF);
-  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) a[t] = make_double2(0.0, 0.0);
+  for (int t = threadIdx.x; t < rows * N; t += blockDim.x) a[t] = mkc<V>((R)0, (R)0);
   __syncthreads();
   const int total = nf * N;
   const bool across = inner >= 2 * TF;
@@ -311,11 +327,11 @@ __global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __
     if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
     long long g = g0 + f;
     long long o = g / inner, i = g - o * inner;
-    double v = in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
+    const R v = (R)in[((size_t)o * N + n) * (size_t)inner + (size_t)i];
     if (f < TF) a[(size_t)f * N + n].x = v; else a[(size_t)(f - TF) * N + n].y = v;
   }
   __syncthreads();
-  double2* res = stockham_rows<-1>(a, b, rows, N, pl, W);
+  V* res = stockham_rows<-1>(a, b, rows, N, pl, W);
   for (int t = threadIdx.x; t < rows * N; t += blockDim.x) spec[t] = res[t];
   __syncthreads();
   const int m_end = min(nm, (int)(blockIdx.y + 1) * mper);
@@ -323,10 +339,10 @@ __global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __
     const double t_m = tm[m];
     for (int t = threadIdx.x; t < rows * N; t += blockDim.x) {
       int k = freq_of(t % N, N);
-      a[t] = cscale(spec[t], exp(-t_m * (double)k * (double)k));
+      a[t] = cscale(spec[t], (R)exp(-t_m * (double)k * (double)k));
     }
     __syncthreads();
-    double2* r2 = stockham_rows<1>(a, b, rows, N, pl, W);
+    V* r2 = stockham_rows<1>(a, b, rows, N, pl, W);
     const double s = sc[m] / (double)N;
     double* o_m = out + (size_t)m * (size_t)out_stride;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -334,23 +350,22 @@ __global__ void __launch_bounds__(256) fibre_gauss_multi_kernel(const double* __
       if (across) { f = t % nf; n = t / nf; } else { f = t / N; n = t % N; }
       long long g = g0 + f;
       long long o = g / inner, i = g - o * inner;
-      double2 v = (f < TF) ? r2[(size_t)f * N + n] : r2[(size_t)(f - TF) * N + n];
-      o_m[((size_t)o * N + n) * (size_t)inner + (size_t)i] = s * ((f < TF) ? v.x : v.y);
+      V v = (f < TF) ? r2[(size_t)f * N + n] : r2[(size_t)(f - TF) * N + n];
+      o_m[((size_t)o * N + n) * (size_t)inner + (size_t)i] = s * (double)((f < TF) ? v.x : v.y);
     }
     __syncthreads();
   }
 }
 
-void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long out_stride, long long outer,
-                       int N, long long inner, const double* t, const double* scale, int nm) {
-  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
-  if (outer == 0 || inner == 0 || nm == 0) return;
-  FftPlan pl = make_plan(N, plan_radix<double2>());
-  const Twiddles& tw = twiddles_for(ctx, N);
+template <typename V>
+static void fibre_gauss_multi_t(lrfg_ctx* ctx, const double* in, double* out, long long out_stride, long long outer,
+                                int N, long long inner, const double* t, const double* scale, int nm) {
+  FftPlan pl = make_plan(N, plan_radix<V>());
+  const V* Wt = twiddle_table<typename RealOf<V>::T>(ctx, N);
   size_t limit = 100 * 1024;
   if (N > 300) limit = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);
-  long long per = 3LL * N * (long long)sizeof(double2);
-  long long tf = ((long long)limit - (long long)N * (long long)sizeof(double2)) / per;
+  long long per = 3LL * N * (long long)sizeof(V);
+  long long tf = ((long long)limit - (long long)N * (long long)sizeof(V)) / per;
   if (tf > 64) tf = 64;
   if (tf < 1) tf = 1;
   // few fibres (low-rank carriages): smaller tiles, and the terms split over grid.y (each block redoes the
@@ -361,7 +376,7 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   const long long bx = (nfib0 + 2 * tf - 1) / (2 * tf);
   const int mchunks = (int)std::max(1LL, std::min((long long)nm, (4LL * nsm + bx - 1) / bx));
   const int mper = (nm + mchunks - 1) / mchunks;
-  size_t smem = (size_t)(N * sizeof(double2) + tf * per);
+  size_t smem = (size_t)(N * sizeof(V) + tf * per);
   // device copies of the node and scale tables
   DBuf<double> dt(ctx->pool, nm), ds(ctx->pool, nm);
   LRFG_CUDA(cudaMemcpyAsync(dt.get(), t, sizeof(double) * nm, cudaMemcpyHostToDevice, ctx->stream));
@@ -369,15 +384,23 @@ void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long o
   long long nfib = outer * inner;
   long long blocks = (nfib + 2 * tf - 1) / (2 * tf);
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
-  LRFG_CUDA(raise_smem_limit((const void*)fibre_gauss_multi_kernel, smem));
+  LRFG_CUDA(raise_smem_limit((const void*)fibre_gauss_multi_kernel<V>, smem));
   // one forward and nm inverse complex transforms per pair of real fibres (algorithmic count)
   const double flops = 2.5 * N * std::log2((double)N) * (double)nfib * (1.0 + nm);
   const double bytes = sizeof(double) * (double)N * (double)nfib * (1.0 + nm);
   const int mgrid = (nm + mper - 1) / mper;
   LRFG_LAUNCH(ctx, KC_GAUSS_MULTI, flops, bytes,
-              fibre_gauss_multi_kernel<<<dim3((unsigned)blocks, (unsigned)mgrid), 256, smem, ctx->stream>>>(
-                  in, out, out_stride, outer, N, inner, (int)tf, pl, tw.W, dt.get(), ds.get(), nm, mper));
+              fibre_gauss_multi_kernel<V><<<dim3((unsigned)blocks, (unsigned)mgrid), 256, smem, ctx->stream>>>(
+                  in, out, out_stride, outer, N, inner, (int)tf, pl, Wt, dt.get(), ds.get(), nm, mper));
   // the pool hands these blocks out again only to later work on the same stream
+}
+
+void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long out_stride, long long outer,
+                       int N, long long inner, const double* t, const double* scale, int nm, bool fp32) {
+  LRFG_REQUIRE(N >= 1 && (N % 2 == 1), "fibre length must be odd (got %d)", N);
+  if (outer == 0 || inner == 0 || nm == 0) return;
+  if (fp32) fibre_gauss_multi_t<float2>(ctx, in, out, out_stride, outer, N, inner, t, scale, nm);
+  else fibre_gauss_multi_t<double2>(ctx, in, out, out_stride, outer, N, inner, t, scale, nm);
 }
 
 

@@ -3,6 +3,7 @@
 // and reductions.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "ops.cuh"
 
@@ -22,8 +23,8 @@ namespace lrfg {
 constexpr int GK = 32;  // k-step
 
 // pk[j] = (row << 16) | column of output j within the block
-template <int NR, int TILE>
-__device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[TILE + 1], const double (*Bs)[TILE + 1],
+template <int NR, int TILE, typename T>
+__device__ __forceinline__ void gemm_fma_rows(T* acc, const T (*As)[TILE + 1], const T (*Bs)[TILE + 1],
                                               const int* pk, int kk_end) {
   for (int kk = 0; kk < kk_end; ++kk) {
 #pragma unroll
@@ -36,16 +37,18 @@ __device__ __forceinline__ void gemm_fma_rows(double* acc, const double (*As)[TI
 // written.  With splits > 1 the partial sums go to part[((split * batches + item) * M + row) * N + column]
 // (M, N the static sizes).  TILE = 64 (16 outputs per thread) or 32 (4 per thread, for small products:
 // four times the blocks, so that a product of a few tiles still spreads over the SMs).
-template <bool TA, bool TB, int TILE>
-__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
-                                                    int lda, long long sA, const double* __restrict__ B, int ldb,
-                                                    long long sB, double beta, double* C, int ldc, long long sC,
+// T = double (the FP64 products) or float (the FP32 sketch products of the mixed-precision path).
+template <bool TA, bool TB, int TILE, typename T>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha_d, const T* __restrict__ A,
+                                                    int lda, long long sA, const T* __restrict__ B, int ldb,
+                                                    long long sB, double beta_d, T* C, int ldc, long long sC,
                                                     int splits, int kchunk, const int* __restrict__ dynM, int mulM,
                                                     const int* __restrict__ dynN, int mulN, double* work,
-                                                    double* __restrict__ part, unsigned int* __restrict__ cnt) {
+                                                    T* __restrict__ part, unsigned int* __restrict__ cnt) {
   constexpr int NMAX = TILE * TILE / 256;
-  __shared__ double As[GK][TILE + 1];
-  __shared__ double Bs[GK][TILE + 1];
+  const T alpha = (T)alpha_d, beta = (T)beta_d;
+  __shared__ T As[GK][TILE + 1];
+  __shared__ T Bs[GK][TILE + 1];
   const int batch = blockIdx.z;
   const int bm = blockIdx.y / splits, split = blockIdx.y - (blockIdx.y / splits) * splits;
   const int bn = blockIdx.x;
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   if (dynM) M = min(M, dynM[batch] * mulM);
   if (dynN) N = min(N, dynN[batch] * mulN);
   if (work && bm == 0 && bn == 0 && split == 0 && threadIdx.x == 0)
-    add_work(work, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    add_work(work, 2.0 * M * N * (double)K, (double)sizeof(T) * ((double)M * K + (double)K * N + (double)M * N));
   const int m0 = bm * TILE, n0 = bn * TILE;
   const int Mb = min(TILE, M - m0), Nb = min(TILE, N - n0);
   if (Mb <= 0 || Nb <= 0) return;
@@ -65,27 +68,27 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   const int tot = Mb * Nb;
   const int nact = tot > (int)threadIdx.x ? min(NMAX, (tot - (int)threadIdx.x + 255) / 256) : 0;
   int pk[NMAX];
-  double acc[NMAX];
+  T acc[NMAX];
 #pragma unroll
   for (int j = 0; j < NMAX; ++j) {
     const int o = threadIdx.x + 256 * j;
     const int m = o / Nb;
     pk[j] = j < nact ? (m << 16) | (o - m * Nb) : 0;
-    acc[j] = 0.0;
+    acc[j] = (T)0;
   }
   for (int k0 = kbeg; k0 < kend; k0 += GK) {
     const int kc = min(GK, kend - k0);
     for (int e = threadIdx.x; e < TILE * GK; e += 256) {
       int mm, kk;
       if (TA) { mm = e % TILE; kk = e / TILE; } else { kk = e % GK; mm = e / GK; }
-      double v = 0.0;
+      T v = (T)0;
       if (mm < Mb && kk < kc) v = TA ? A[(size_t)(k0 + kk) * lda + m0 + mm] : A[(size_t)(m0 + mm) * lda + k0 + kk];
       As[kk][mm] = v;
     }
     for (int e = threadIdx.x; e < TILE * GK; e += 256) {
       int nn, kk;
       if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % TILE; kk = e / TILE; }
-      double v = 0.0;
+      T v = (T)0;
       if (nn < Nb && kk < kc) v = TB ? B[(size_t)(n0 + nn) * ldb + k0 + kk] : B[(size_t)(k0 + kk) * ldb + n0 + nn];
       Bs[kk][nn] = v;
     }
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   }
   if (splits > 1) {
     const size_t pstride = (size_t)gridDim.z * Ms * Ns;  // between the splits of one output
-    double* P = part + (size_t)batch * Ms * Ns;
+    T* P = part + (size_t)batch * Ms * Ns;
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) {
       if (j >= nact) break;
@@ -145,10 +148,10 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
     for (int j = 0; j < NMAX; ++j) {
       if (j >= nact) break;
       const size_t off = (size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff);
-      double v = 0.0;
+      T v = (T)0;
       for (int s = 0; s < splits; ++s) v += __ldcg(P + s * pstride + off);
-      double* cp = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
-      *cp = (beta == 0.0) ? alpha * v : alpha * v + beta * (*cp);
+      T* cp = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
+      *cp = (beta_d == 0.0) ? alpha * v : alpha * v + beta * (*cp);
     }
     if (threadIdx.x == 0) *c = 0u;  // ready for the next product
     return;
@@ -156,30 +159,30 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
 #pragma unroll
   for (int j = 0; j < NMAX; ++j) {
     if (j >= nact) break;
-    double* c = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
-    *c = (beta == 0.0) ? alpha * acc[j] : alpha * acc[j] + beta * (*c);
+    T* c = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
+    *c = (beta_d == 0.0) ? alpha * acc[j] : alpha * acc[j] + beta * (*c);
   }
 }
 
-template <int TILE>
+template <int TILE, typename T>
 static void launch_dgemm(lrfg_ctx* ctx, int transA, int transB, dim3 grid, double flops, double bytes, int M, int N,
-                         int K, double alpha, const double* A, int lda, long long sA, const double* B, int ldb,
-                         long long sB, double beta, double* C, int ldc, long long sC, int splits, int kchunk,
-                         const int* dynM, int mulM, const int* dynN, int mulN, double* work, double* part) {
+                         int K, double alpha, const T* A, int lda, long long sA, const T* B, int ldb,
+                         long long sB, double beta, T* C, int ldc, long long sC, int splits, int kchunk,
+                         const int* dynM, int mulM, const int* dynN, int mulN, double* work, T* part) {
   if (!transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, false, TILE><<<grid, 256, 0, ctx->stream>>>(
+    LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<false, false, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
         ctx->splitk_cnt));
   else if (transA && !transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, false, TILE><<<grid, 256, 0, ctx->stream>>>(
+    LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<true, false, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
         ctx->splitk_cnt));
   else if (!transA && transB)
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<false, true, TILE><<<grid, 256, 0, ctx->stream>>>(
+    LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<false, true, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
         ctx->splitk_cnt));
   else
-    LRFG_LAUNCH(ctx, KC_GEMM, flops, bytes, dgemm_kernel<true, true, TILE><<<grid, 256, 0, ctx->stream>>>(
+    LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<true, true, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
         ctx->splitk_cnt));
 }
@@ -202,14 +205,16 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
            nullptr, 1);
 }
 
-void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
-              long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
-              int batch, const int* dynM, int mulM, const int* dynN, int mulN) {
+template <typename T>
+static void gemm_impl(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const T* A, int lda,
+                      long long sA, const T* B, int ldb, long long sB, double beta, T* C, int ldc, long long sC,
+                      int batch, const int* dynM, int mulM, const int* dynN, int mulN) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) {
+    LRFG_REQUIRE((std::is_same<T, double>::value), "FP32 product with an empty inner dimension");
     LRFG_LAUNCH(ctx, KC_GEMM, (double)M * N * batch, 2.0 * sizeof(double) * M * N * batch,
                 scale_matrix_kernel<<<std::min(1024LL, ((long long)M * N * batch + 255) / 256), 256, 0, ctx->stream>>>(
-                    C, M, N, ldc, sC, batch, beta));
+                    (double*)C, M, N, ldc, sC, batch, beta));
     return;
   }
   LRFG_REQUIRE(batch < 65536, "gemm batch too large");
@@ -235,19 +240,33 @@ void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double
   LRFG_REQUIRE((long long)bmn * splits < 65536, "gemm too many row blocks x splits");
   if (splits > 1)
     LRFG_REQUIRE((long long)bmn * bnn * batch <= kSplitKCounters, "split-K product with too many output tiles");
-  DBuf<double> part;
-  if (splits > 1) part = DBuf<double>(ctx->pool, (size_t)splits * M * N * batch);
+  DBuf<T> part;
+  if (splits > 1) part = DBuf<T>(ctx->pool, (size_t)splits * M * N * batch);
   // products with data-dependent sizes count their work on the device
   double* work = (dynM || dynN) ? work_counter(ctx, KC_GEMM) : nullptr;
   const double flops = work ? 0.0 : 2.0 * M * N * (double)K * batch;
-  const double bytes = work ? 0.0 : sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
+  const double bytes = work ? 0.0 : sizeof(T) * ((double)M * K + (double)K * N + (double)M * N) * batch;
   dim3 grid(bnn, bmn * splits, batch);
   if (tile == 32)
-    launch_dgemm<32>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+    launch_dgemm<32, T>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
                      sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
   else
-    launch_dgemm<64>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+    launch_dgemm<64, T>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
                      sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
+}
+
+void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+              long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+              int batch, const int* dynM, int mulM, const int* dynN, int mulN) {
+  gemm_impl<double>(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, dynM, mulM,
+                    dynN, mulN);
+}
+
+void gemm_f32(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const float* A, int lda,
+              long long sA, const float* B, int ldb, long long sB, double beta, float* C, int ldc, long long sC,
+              int batch) {
+  gemm_impl<float>(ctx, transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, nullptr, 1,
+                   nullptr, 1);
 }
 
 // The same product in one pass over K (no split-K): it needs no partial-sum workspace, so it takes nothing
@@ -273,11 +292,11 @@ void gemm_nosplit(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, do
   const double bytes = sizeof(double) * ((double)M * K + (double)K * N + (double)M * N) * batch;
   dim3 grid(bnn, bmn, batch);
   if (tile == 32)
-    launch_dgemm<32>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                     sC, 1, kchunk, nullptr, 1, nullptr, 1, nullptr, nullptr);
+    launch_dgemm<32, double>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                             ldc, sC, 1, kchunk, nullptr, 1, nullptr, 1, nullptr, nullptr);
   else
-    launch_dgemm<64>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                     sC, 1, kchunk, nullptr, 1, nullptr, 1, nullptr, nullptr);
+    launch_dgemm<64, double>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                             ldc, sC, 1, kchunk, nullptr, 1, nullptr, 1, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -600,6 +619,26 @@ double dot_host(lrfg_ctx* ctx, const double* x, const double* y, long long n) {
   LRFG_CUDA(cudaMemcpyAsync(&h, d.get(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   return h;
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = (float)in[t];
+}
+
+__global__ void to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = (double)in[t];
+}
+
+void to_f32(lrfg_ctx* ctx, const double* in, float* out, long long n) {
+  if (n <= 0) return;
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 0.0, 12.0 * n, to_f32_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(in, out, n));
+}
+
+void to_f64(lrfg_ctx* ctx, const float* in, double* out, long long n) {
+  if (n <= 0) return;
+  LRFG_LAUNCH(ctx, KC_TT_MISC, 0.0, 12.0 * n, to_f64_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(in, out, n));
 }
 
 }  // namespace lrfg

@@ -27,13 +27,14 @@ void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long
 enum { GA_UP = 0, GA_DOWN = 1, GA_EXTEND = 2 };
 void ga_resample(lrfg_ctx* ctx, const double* in, double* out, long long outer, int n_in, long long inner, int n_out,
                  int mode);
-// real fibres: out = scale * F^-1 diag(m) F in, m given by kind/param (lrfg_multiplier)
+// real fibres: out = scale * F^-1 diag(m) F in, m given by kind/param (lrfg_multiplier); fp32: the transforms
+// in FP32 (data read and written in FP64)
 void fibre_operator(lrfg_ctx* ctx, const double* in, double* out, long long outer, int N, long long inner,
-                    int kind, double param, double scale);
+                    int kind, double param, double scale, bool fp32 = false);
 // real fibres, many Gaussian multipliers at once: out_m = scale_m F^-1 diag(exp(-t_m k^2)) F in,
 // written to out + m * out_stride for m = 0..nm-1 (the exponential-sum preconditioner terms)
 void fibre_gauss_multi(lrfg_ctx* ctx, const double* in, double* out, long long out_stride, long long outer,
-                       int N, long long inner, const double* t, const double* scale, int nm);
+                       int N, long long inner, const double* t, const double* scale, int nm, bool fp32 = false);
 
 // ---- linalg.cu ----------------------------------------------------------------------------------
 // C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b], row-major, op = transpose when trans* != 0.
@@ -47,6 +48,12 @@ void gemm(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alp
 void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
               long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
               int batch, const int* dynM, int mulM, const int* dynN, int mulN);
+// FP32 product (same layout rules, FP32 operands and accumulation)
+void gemm_f32(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const float* A, int lda,
+              long long sA, const float* B, int ldb, long long sB, double beta, float* C, int ldc, long long sC,
+              int batch = 1);
+void to_f32(lrfg_ctx* ctx, const double* in, float* out, long long n);
+void to_f64(lrfg_ctx* ctx, const float* in, double* out, long long n);
 // The same product in one pass over K (never split): no partial-sum workspace, nothing taken from the pool.
 void gemm_nosplit(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
                   long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc, long long sC,
@@ -139,7 +146,7 @@ void tt_mode_operator(lrfg_ctx* ctx, const TTView& x, int j, int kind, double pa
 void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector<double>& w);
 // out = T(P~^-1 x) with the exponential sum (t, w); omega non-null: T is the randomised rounding with that sketch
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w,
-                int rmax, TT& out, double tol = 0.0, const TTView* omega = nullptr);
+                int rmax, TT& out, double tol = 0.0, const TTView* omega = nullptr, bool fp32 = false);
 
 // block copy of a carriage (a x n x b) into a larger one (A x n x B) at rank offsets (oa, ob)
 void tt_embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double* dst, int A, int B, int oa, int ob);
@@ -168,13 +175,16 @@ struct SketchSource {
                                      // blocks start b block sizes further on
   void materialise(lrfg_ctx* ctx, int j, double* dst) const;                      // first or last carriage
   void right_middle(lrfg_ctx* ctx, const double* W, int ell, double* T) const;     // T = Z_1 x_3 W
+  void right_middle_f32(lrfg_ctx* ctx, const float* W, int ell, float* T) const;   // the same in FP32
   void left_middle(lrfg_ctx* ctx, const double* M, int ell, double* X) const;      // X = M x_1 Z_1
 };
 // Rademacher sketch TT of inner ranks ell (SplitMix64 stream `seed`)
 void sketch_tt(lrfg_ctx* ctx, int d, const int* N, int ell, unsigned long long seed, TT& out);
 // randomised rounding of every item to rank rmax (tolerance tol > 0: the smallest ranks <= rmax within it)
+// fp32: the right sweep and the sketched products in FP32 (they only choose the subspaces; every projection of
+// the tensor's values stays FP64)
 void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out,
-                     double tol = 0.0);
+                     double tol = 0.0, bool fp32 = false);
 
 // ---- ttbatch.cu ---------------------------------------------------------------------------------
 TTView item_view_of(const TTBatchView& x, int b);
@@ -186,7 +196,7 @@ void ttb_add_many(lrfg_ctx* ctx, const TTBatchView* xs, int m, const double* hs,
 void ttb_dot_device(lrfg_ctx* ctx, const TTBatchView& x, const TTBatchView& y, double* out_dev);
 // out_i = T(P~^-1 x_i) (omega non-null: randomised rounding, one launch sequence for all items)
 void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>& t, const std::vector<double>& w,
-                 int rmax, TTBatch& out, double tol, const TTView* omega);
+                 int rmax, TTBatch& out, double tol, const TTView* omega, bool fp32 = false);
 
 // ---- tucker.cu ----------------------------------------------------------------------------------
 // Tucker tensor on the device: core (r_0, .., r_{d-1}) row-major, factor j (N_j, r_j) row-major

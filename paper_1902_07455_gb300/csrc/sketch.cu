@@ -70,38 +70,41 @@ struct ItemPtrs {
 
 // T[b][(i,k), n, l] = sum_{i',k'} x[i,n,i'] y_b[k,n,k'] W_b[(i',k'), l]: one block per (n, l-chunk, item);
 // U[i',k,c] = sum_k' y[k,k'] W[(i',k'), c], then T[(i,k),c] = sum_i' x[i,i'] U[i',k,c]
+// S = double, or float on the sketch side of the mixed-precision path (x, y read in FP64 and rounded)
+template <typename S>
 __global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict__ x, int a0, int a1,
                                                        const __grid_constant__ ItemPtrs y,
-                                                       int r0, int r1, int N, const double* __restrict__ W,
-                                                       long long sW, int ell, int LC, double* T, long long sT) {
-  extern __shared__ __align__(16) double sm[];
+                                                       int r0, int r1, int N, const S* __restrict__ W,
+                                                       long long sW, int ell, int LC, S* T, long long sT) {
+  extern __shared__ __align__(16) unsigned char smraw_kr[];
+  S* sm = (S*)smraw_kr;
   const int n = blockIdx.x, l0 = blockIdx.y * LC, b = blockIdx.z;
   const int lc = min(LC, ell - l0);
-  double* Ws = sm;                               // (a1 r1) x LC
-  double* Us = Ws + (size_t)a1 * r1 * LC;        // (a1 r0) x LC
-  double* Xs = Us + (size_t)a1 * r0 * LC;        // a0 x a1
-  double* Ys = Xs + (size_t)a0 * a1;             // r0 x r1
+  S* Ws = sm;                               // (a1 r1) x LC
+  S* Us = Ws + (size_t)a1 * r1 * LC;        // (a1 r0) x LC
+  S* Xs = Us + (size_t)a1 * r0 * LC;        // a0 x a1
+  S* Ys = Xs + (size_t)a0 * a1;             // r0 x r1
   const double* yb = y.p[b];
-  const double* Wb = W + (size_t)b * sW;
+  const S* Wb = W + (size_t)b * sW;
   for (int t = threadIdx.x; t < a0 * a1; t += blockDim.x) {
     const int i = t / a1, ip = t - i * a1;
-    Xs[t] = x[((size_t)i * N + n) * a1 + ip];
+    Xs[t] = (S)x[((size_t)i * N + n) * a1 + ip];
   }
   for (int t = threadIdx.x; t < r0 * r1; t += blockDim.x) {
     const int k = t / r1, kp = t - k * r1;
-    Ys[t] = yb[((size_t)k * N + n) * r1 + kp];
+    Ys[t] = (S)yb[((size_t)k * N + n) * r1 + kp];
   }
   for (int t = threadIdx.x; t < a1 * r1 * LC; t += blockDim.x) {
     const int row = t / LC, c = t - row * LC;
-    Ws[t] = c < lc ? Wb[(size_t)row * ell + l0 + c] : 0.0;
+    Ws[t] = c < lc ? Wb[(size_t)row * ell + l0 + c] : (S)0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < a1 * r0 * LC; t += blockDim.x) {
     const int row = t / LC, c = t - row * LC;  // row = i' r0 + k
     const int ip = row / r0, k = row - ip * r0;
-    const double* yk = Ys + (size_t)k * r1;
-    const double* wc = Ws + (size_t)ip * r1 * LC + c;
-    double s0 = 0.0, s1 = 0.0;
+    const S* yk = Ys + (size_t)k * r1;
+    const S* wc = Ws + (size_t)ip * r1 * LC + c;
+    S s0 = 0, s1 = 0;
     int kp = 0;
     for (; kp + 1 < r1; kp += 2) {
       s0 = fma(yk[kp], wc[(size_t)kp * LC], s0);
@@ -111,13 +114,13 @@ __global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict_
     Us[t] = s0 + s1;
   }
   __syncthreads();
-  double* Tb = T + (size_t)b * sT;
+  S* Tb = T + (size_t)b * sT;
   for (int t = threadIdx.x; t < a0 * r0 * LC; t += blockDim.x) {
     const int row = t / LC, c = t - row * LC;  // row = i r0 + k
     if (c >= lc) continue;
     const int i = row / r0, k = row - i * r0;
-    const double* xi = Xs + (size_t)i * a1;
-    double s = 0.0;
+    const S* xi = Xs + (size_t)i * a1;
+    S s = 0;
     for (int ip = 0; ip < a1; ++ip) s = fma(xi[ip], Us[((size_t)ip * r0 + k) * LC + c], s);
     Tb[((size_t)row * N + n) * ell + l0 + c] = s;
   }
@@ -202,22 +205,23 @@ static int chunk_for(size_t per_col, size_t fixed, int ell, size_t budget) {
   return 1;
 }
 
+template <typename S>
 static void kr_right(lrfg_ctx* ctx, const double* x, int a0, int a1, const ItemPtrs& y, int r0, int r1, int N, int nb,
-                     const double* W, int ell, double* T) {
+                     const S* W, int ell, S* T) {
   const size_t budget = 100 * 1024;
-  const size_t fixed = sizeof(double) * ((size_t)a0 * a1 + (size_t)r0 * r1);
-  const size_t per = sizeof(double) * ((size_t)a1 * r1 + (size_t)a1 * r0);
+  const size_t fixed = sizeof(S) * ((size_t)a0 * a1 + (size_t)r0 * r1);
+  const size_t per = sizeof(S) * ((size_t)a1 * r1 + (size_t)a1 * r0);
   const int LC = chunk_for(per, fixed, ell, budget);
   const size_t smem = fixed + per * LC;
   LRFG_REQUIRE(smem <= 200 * 1024, "sketch contraction too large for shared memory (ranks %d x %d)", a1, r1);
-  LRFG_CUDA(raise_smem_limit((const void*)kr_right_kernel, smem));
+  LRFG_CUDA(raise_smem_limit((const void*)kr_right_kernel<S>, smem));
   dim3 grid(N, (ell + LC - 1) / LC, nb);
   const double flops = 2.0 * nb * N * (double)ell * ((double)a1 * r0 * r1 + (double)a0 * r0 * a1);
-  const double bytes = sizeof(double) * nb * ((double)a0 * r0 * N * ell + (double)r0 * N * r1) +
-                       sizeof(double) * ((double)a0 * N * a1 + (double)nb * a1 * r1 * ell);
+  const double bytes = sizeof(S) * nb * ((double)a0 * r0 * N * ell + (double)a1 * r1 * ell) +
+                       sizeof(double) * ((double)a0 * N * a1 + (double)nb * r0 * N * r1);
   LRFG_LAUNCH(ctx, KC_SKETCH, flops, bytes,
-              kr_right_kernel<<<grid, 256, smem, ctx->stream>>>(x, a0, a1, y, r0, r1, N, W, (long long)a1 * r1 * ell,
-                                                               ell, LC, T, (long long)a0 * r0 * N * ell));
+              kr_right_kernel<S><<<grid, 256, smem, ctx->stream>>>(x, a0, a1, y, r0, r1, N, W, (long long)a1 * r1 * ell,
+                                                                  ell, LC, T, (long long)a0 * r0 * N * ell));
 }
 
 static void kr_left(lrfg_ctx* ctx, const double* x, int a0, int a1, const ItemPtrs& y, int r0, int r1, int N, int nb,
@@ -275,7 +279,22 @@ static void cholqr2(lrfg_ctx* ctx, const double* A, int m, int l, int nb, double
 // ------------------------------------------------------------------------------------------------
 // the rounding driver
 // ------------------------------------------------------------------------------------------------
-void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out, double tol) {
+// A = X W for the left sweep: in FP64, or (fp32) X rounded to FP32 times the FP32 W, the result widened again
+static void sketch_product(lrfg_ctx* ctx, bool fp32, int m, int l, int k, const double* X, long long sx,
+                           const double* W64, const float* W32, long long sw, double* A, int nb) {
+  const long long sa = (long long)m * l;
+  if (!fp32) {
+    gemm(ctx, 0, 0, m, l, k, 1.0, X, k, sx, W64, l, sw, 0.0, A, l, sa, nb);
+    return;
+  }
+  DBuf<float> X32(ctx->pool, (size_t)sx * nb), A32(ctx->pool, (size_t)sa * nb);
+  to_f32(ctx, X, X32.get(), sx * nb);
+  gemm_f32(ctx, 0, 0, m, l, k, 1.0, X32.get(), k, sx, W32, l, sw, 0.0, A32.get(), l, sa, nb);
+  to_f64(ctx, A32.get(), A, sa * nb);
+}
+
+void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out, double tol,
+                     bool fp32) {
   const int d = z.d, nb = z.nb;
   LRFG_REQUIRE(d >= 2 && d <= 3, "randomised rounding needs d = 2 or 3");
   LRFG_REQUIRE(nb >= 1 && nb <= kMaxSketchItems, "randomised rounding batch of %d items", nb);
@@ -289,24 +308,46 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
   DBuf<double> Z0(ctx->pool, (size_t)e0 * nb), Zl(ctx->pool, (size_t)el * nb);
   z.materialise(ctx, 0, Z0.get());
   z.materialise(ctx, d - 1, Zl.get());
-  // right sweep: W[d-1] = Zl Omega_{d-1}^T  (s_{d-1} x l_{d-1})
+  // right sweep: W[d-1] = Zl Omega_{d-1}^T  (s_{d-1} x l_{d-1}), then W[1] = (Z1 x_3 W2) Omega_1^T.  With fp32 the
+  // sweep runs in FP32: it only decides the subspaces the left sweep projects on (in FP64)
   DBuf<double> W[3];
+  DBuf<float> W32[3], om32[3];
+  if (fp32)
+    for (int j = 0; j < d; ++j) {
+      const long long e = (long long)omega.r[j] * N[j] * omega.r[j + 1];
+      om32[j] = DBuf<float>(ctx->pool, (size_t)e);
+      to_f32(ctx, omega.core[j], om32[j].get(), e);
+    }
   {
     const int j = d - 1;
-    W[j] = DBuf<double>(ctx->pool, (size_t)s[j] * l[j] * nb);
-    gemm(ctx, 0, 1, s[j], l[j], N[j], 1.0, Zl.get(), N[j], el, omega.core[j], N[j], 0, 0.0, W[j].get(), l[j],
-         (long long)s[j] * l[j], nb);
+    if (fp32) {
+      W32[j] = DBuf<float>(ctx->pool, (size_t)s[j] * l[j] * nb);
+      DBuf<float> Zl32(ctx->pool, (size_t)el * nb);
+      to_f32(ctx, Zl.get(), Zl32.get(), el * nb);
+      gemm_f32(ctx, 0, 1, s[j], l[j], N[j], 1.0, Zl32.get(), N[j], el, om32[j].get(), N[j], 0, 0.0, W32[j].get(), l[j],
+               (long long)s[j] * l[j], nb);
+    } else {
+      W[j] = DBuf<double>(ctx->pool, (size_t)s[j] * l[j] * nb);
+      gemm(ctx, 0, 1, s[j], l[j], N[j], 1.0, Zl.get(), N[j], el, omega.core[j], N[j], 0, 0.0, W[j].get(), l[j],
+           (long long)s[j] * l[j], nb);
+    }
   }
-  DBuf<double> T1;
   if (d == 3) {
     // T1 = Z1 x_3 W2 (s1 x N1 x l2), W1 = T1 Omega_1^T over (n, l2)
     const long long st = (long long)s[1] * N[1] * l[2];
-    T1 = DBuf<double>(ctx->pool, (size_t)st * nb);
-    z.right_middle(ctx, W[2].get(), l[2], T1.get());
-    W[1] = DBuf<double>(ctx->pool, (size_t)s[1] * l[1] * nb);
-    gemm(ctx, 0, 1, s[1], l[1], N[1] * l[2], 1.0, T1.get(), N[1] * l[2], st, omega.core[1], N[1] * l[2], 0, 0.0,
-         W[1].get(), l[1], (long long)s[1] * l[1], nb);
-    T1.reset();
+    if (fp32) {
+      DBuf<float> T1(ctx->pool, (size_t)st * nb);
+      z.right_middle_f32(ctx, W32[2].get(), l[2], T1.get());
+      W32[1] = DBuf<float>(ctx->pool, (size_t)s[1] * l[1] * nb);
+      gemm_f32(ctx, 0, 1, s[1], l[1], N[1] * l[2], 1.0, T1.get(), N[1] * l[2], st, om32[1].get(), N[1] * l[2], 0, 0.0,
+               W32[1].get(), l[1], (long long)s[1] * l[1], nb);
+    } else {
+      DBuf<double> T1(ctx->pool, (size_t)st * nb);
+      z.right_middle(ctx, W[2].get(), l[2], T1.get());
+      W[1] = DBuf<double>(ctx->pool, (size_t)s[1] * l[1] * nb);
+      gemm(ctx, 0, 1, s[1], l[1], N[1] * l[2], 1.0, T1.get(), N[1] * l[2], st, omega.core[1], N[1] * l[2], 0, 0.0,
+           W[1].get(), l[1], (long long)s[1] * l[1], nb);
+    }
   }
   // left sweep
   TTBatch y;
@@ -322,8 +363,8 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
   DBuf<double> M(ctx->pool, (size_t)l[1] * s[1] * nb);
   {
     DBuf<double> A(ctx->pool, (size_t)sq0 * nb);
-    gemm(ctx, 0, 0, N[0], l[1], s[1], 1.0, Z0.get(), s[1], e0, W[1].get(), l[1], (long long)s[1] * l[1], 0.0,
-         A.get(), l[1], sq0, nb);
+    sketch_product(ctx, fp32, N[0], l[1], s[1], Z0.get(), e0, W[1].get(), W32[1].get(), (long long)s[1] * l[1],
+                   A.get(), nb);
     cholqr2(ctx, A.get(), N[0], l[1], nb, y.core[0].get());
     gemm(ctx, 1, 0, l[1], s[1], N[0], 1.0, y.core[0].get(), l[1], sq0, Z0.get(), s[1], e0, 0.0, M.get(), s[1],
          (long long)l[1] * s[1], nb);
@@ -337,8 +378,8 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
     y.core[1] = DBuf<double>(ctx->pool, (size_t)sq1 * nb);
     {
       DBuf<double> A(ctx->pool, (size_t)sq1 * nb);
-      gemm(ctx, 0, 0, l[1] * N[1], l[2], s[2], 1.0, X1.get(), s[2], sx, W[2].get(), l[2], (long long)s[2] * l[2], 0.0,
-           A.get(), l[2], sq1, nb);
+      sketch_product(ctx, fp32, l[1] * N[1], l[2], s[2], X1.get(), sx, W[2].get(), W32[2].get(),
+                     (long long)s[2] * l[2], A.get(), nb);
       cholqr2(ctx, A.get(), l[1] * N[1], l[2], nb, y.core[1].get());
     }
     M = DBuf<double>(ctx->pool, (size_t)l[2] * s[2] * nb);
@@ -400,7 +441,7 @@ void SketchSource::right_middle(lrfg_ctx* ctx, const double* W, int ell, double*
   } else if (kind == KHATRI_RAO) {
     ItemPtrs p{};
     for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
-    kr_right(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
+    kr_right<double>(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
   } else {
     // T[(m,k), n, l] = sum_k' F_m[k, n, k'] W[(m,k'), l]: for each item, one product per block
     const int R = nblocks, a = ry[1], c = ry[2];
@@ -408,6 +449,30 @@ void SketchSource::right_middle(lrfg_ctx* ctx, const double* W, int ell, double*
     for (int b = 0; b < nb; ++b)
       gemm(ctx, 0, 0, a * n, ell, c, 1.0, blocks[1] + (size_t)b * be, c, bs, W + (size_t)b * s[2] * ell, ell,
            (long long)c * ell, 0.0, T + (size_t)b * s[1] * n * ell, ell, (long long)a * n * ell, R);
+  }
+}
+
+void SketchSource::right_middle_f32(lrfg_ctx* ctx, const float* W, int ell, float* T) const {
+  const int n = N[1];
+  if (kind == KHATRI_RAO) {
+    ItemPtrs p{};
+    for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
+    kr_right<float>(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
+  } else if (kind == DENSE) {
+    const long long e = (long long)s[1] * n * s[2];
+    DBuf<float> Z32(ctx->pool, (size_t)e * nb);
+    to_f32(ctx, dense[1], Z32.get(), e * nb);
+    gemm_f32(ctx, 0, 0, s[1] * n, ell, s[2], 1.0, Z32.get(), s[2], e, W, ell, (long long)s[2] * ell, 0.0, T, ell,
+             (long long)s[1] * n * ell, nb);
+  } else {
+    const int R = nblocks, a = ry[1], c = ry[2];
+    const long long be = (long long)a * n * c, bs = bstride[1] ? bstride[1] : be;
+    const long long extent = (R - 1) * bs + nb * be;
+    DBuf<float> B32(ctx->pool, (size_t)extent);
+    to_f32(ctx, blocks[1], B32.get(), extent);
+    for (int b = 0; b < nb; ++b)
+      gemm_f32(ctx, 0, 0, a * n, ell, c, 1.0, B32.get() + (size_t)b * be, c, bs, W + (size_t)b * s[2] * ell, ell,
+               (long long)c * ell, 0.0, T + (size_t)b * s[1] * n * ell, ell, (long long)a * n * ell, R);
   }
 }
 

@@ -713,7 +713,7 @@ void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector
 }
 
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
-                TT& out, double tol, const TTView* omega) {
+                TT& out, double tol, const TTView* omega, bool fp32) {
   // P~^-1 x = sum_m w_m (G_m x ... x G_m) x with G_m = F^-1 diag(exp(-t_m k^2)) F per mode: a TT whose
   // carriages are block rows (first), block diagonal (middle) and block columns (last) over m.
   const int d = x.d;
@@ -737,7 +737,7 @@ void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, co
       const size_t e = (size_t)x.r[j] * x.N[j] * x.r[j + 1];
       terms[j] = DBuf<double>(ctx->pool, e * R);
       fibre_gauss_multi(ctx, x.core[j], terms[j].get(), (long long)e, x.r[j], x.N[j], x.r[j + 1], t.data(),
-                        (j == 0) ? w.data() : ones.data(), R);
+                        (j == 0) ? w.data() : ones.data(), R, fp32);
       z.blocks[j] = terms[j].get();
     }
     for (int j = 0; j <= d; ++j) {
@@ -745,7 +745,7 @@ void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, co
       z.ry[j] = x.r[j];
     }
     TTBatch ob;
-    tt_round_sketch(ctx, z, *omega, rmax, ob, tol);
+    tt_round_sketch(ctx, z, *omega, rmax, ob, tol, fp32);
     out.d = ob.d;
     for (int j = 0; j < 3; ++j) out.N[j] = ob.N[j];
     for (int j = 0; j < 4; ++j) out.r[j] = ob.r[j];
@@ -758,7 +758,8 @@ void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, co
     const int a = x.r[j], n = x.N[j], b = x.r[j + 1];
     const size_t e = (size_t)a * n * b;
     DBuf<double> terms(ctx->pool, e * R);
-    fibre_gauss_multi(ctx, x.core[j], terms.get(), (long long)e, a, n, b, t.data(), (j == 0) ? w.data() : ones.data(), R);
+    fibre_gauss_multi(ctx, x.core[j], terms.get(), (long long)e, a, n, b, t.data(), (j == 0) ? w.data() : ones.data(), R,
+                      fp32);
     double* dst = big.core[j].get();
     if (d > 1 && j != 0 && j != d - 1) fill(ctx, dst, 0.0, (long long)r[j] * n * r[j + 1]);
     for (int m = 0; m < R; ++m) {

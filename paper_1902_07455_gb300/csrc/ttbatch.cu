@@ -90,13 +90,13 @@ void ttb_dot_device(lrfg_ctx* ctx, const TTBatchView& x, const TTBatchView& y, d
 }
 
 void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>& t, const std::vector<double>& w,
-                 int rmax, TTBatch& out, double tol, const TTView* omega) {
+                 int rmax, TTBatch& out, double tol, const TTView* omega, bool fp32) {
   const int d = x.d, nb = x.nb;
   const int R = (int)t.size();
   if (!omega || d < 2) {
     // deterministic rounding: item by item, packed into one batch
     std::vector<TT> parts(nb);
-    for (int b = 0; b < nb; ++b) tt_precond(ctx, item_view_of(x, b), t, w, rmax, parts[b], tol, nullptr);
+    for (int b = 0; b < nb; ++b) tt_precond(ctx, item_view_of(x, b), t, w, rmax, parts[b], tol, nullptr, fp32);
     int r[4] = {1, 1, 1, 1};
     for (int j = 0; j <= d; ++j) r[j] = parts[0].r[j];
     for (int b = 1; b < nb; ++b)
@@ -121,7 +121,7 @@ void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>&
     const size_t e = x.elems(j);
     terms[j] = DBuf<double>(ctx->pool, e * nb * R);
     fibre_gauss_multi(ctx, x.core[j], terms[j].get(), (long long)(e * nb), (long long)x.r[j] * nb, x.N[j], x.r[j + 1],
-                      t.data(), (j == 0) ? w.data() : ones.data(), R);
+                      t.data(), (j == 0) ? w.data() : ones.data(), R, fp32);
     z.blocks[j] = terms[j].get();
     z.bstride[j] = (long long)(e * nb);
   }
@@ -129,7 +129,7 @@ void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>&
     z.s[j] = (j == 0 || j == d) ? 1 : R * x.r[j];
     z.ry[j] = x.r[j];
   }
-  tt_round_sketch(ctx, z, *omega, rmax, out, tol);
+  tt_round_sketch(ctx, z, *omega, rmax, out, tol, fp32);
 }
 
 TTView item_view_of(const TTBatchView& x, int b) {

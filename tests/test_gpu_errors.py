@@ -32,14 +32,14 @@ def test_bad_rank_and_coefficients(ctx):
     assert _status(lambda: ctx.problem(np.ones((9, 9, 9, 9)), lrfg.FULL)) == L.LRFG_EINVAL
 
 
-def test_mixed_precision_only_for_full(ctx):
+def test_mixed_precision_only_for_full_and_tt(ctx):
     lib = ctx.lib
     c = L.lrfg_coeff()
     arr = np.ones((9, 9))
     c.d, c.fmt, c.values, c.on_device = 2, L.LRFG_FULL, arr.ctypes.data, 0
     c.N[0] = c.N[1] = 9
     o = L.lrfg_opts()
-    o.fmt, o.prec, o.rank, o.tol, o.maxit = L.LRFG_TT, L.LRFG_MIXED, 1, 1e-8, 10
+    o.fmt, o.prec, o.rank, o.tol, o.maxit = L.LRFG_TUCKER, L.LRFG_MIXED, 1, 1e-8, 10
     h = C.c_void_p()
     assert lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)) == L.LRFG_ENOTSUP
     assert b"LRFG_FULL" in lib.lrfg_last_error(ctx.h)

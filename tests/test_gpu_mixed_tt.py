@@ -1,0 +1,79 @@
+"""LRFG_MIXED for tensor trains: the operator with FP32 fibre transforms and the FP32 sketch side of the randomised
+rounding (carriages, projections, eigen-decompositions, inner products and A_eff in FP64), and the solve that uses
+it for its steps while its residual stays FP64 (a defect correction, whose fixed point is the FP64 solution).
+
+Tolerances: one mixed application vs the oracle's FP64 operator 1e-5 relative (FP32 transforms: a few u32 log2 N
+of the operator's norm, u32 = 6e-8, with margin); a mixed solve vs the FP64 oracle's solve with the same number of
+iterations 1e-6 on A_eff (the FP32 steps change the step lengths at the 1e-7 level, and A_eff of an iterate moves
+with them to first order); at 243^3 the mixed solve of the benchmark's options meets the FP64 path's 1e-6 against
+the oracle's full solve (the path's own target is 1e-4)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1902_07455_gb300 as lrfg
+from oracle import lowrank as lr
+from synthetic import lognormal_grf, random_tt, smoothed_cube
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("d,N,rank,rx,over", [(2, 15, 4, [3], 4), (3, 9, 3, [2, 3], 3), (3, 27, 5, [4, 4], 6),
+                                              (2, 63, 6, [5], 0)])
+def test_mixed_apply_matches_fp64_oracle(ctx, d, N, rank, rx, over):
+    shape = (N,) * d
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    a = lr.tt_from_separable(terms, w)
+    op = lr.LowRankGaNi(a, shape, fmt="tt", rank=rank, pinv_eps=0.1, sketch=(over, 41) if over else None)
+    x = random_tt(shape, rx, seed=21)
+    ref = np.real(lr.tt_full(lr.tt_idft(op.apply(lr.tt_dft(x)))))
+    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, sketch_over=over, sketch_seed=41,
+                    prec=lrfg.MIXED)
+    out = P.apply(ctx.field_from_tt(lrfg.TTensor.from_numpy(x))).full()
+    assert rel(out, ref) <= 1e-5, rel(out, ref)
+    P.free()
+
+
+@pytest.mark.parametrize("d,N,rank,over", [(3, 21, 6, 6), (2, 45, 8, 0), (3, 27, 8, 8)])
+def test_mixed_solve_matches_fp64_oracle(ctx, d, N, rank, over):
+    a = lr.tt_svd(lognormal_grf(d, N, ell=0.2, var=0.25, seed=7), rmax=8)
+    E = np.eye(d)[0]
+    op = lr.LowRankGaNi(a, (N,) * d, fmt="tt", rank=rank, pinv_eps=0.1, sketch=(over, 0) if over else None)
+    ref = lr.minres(op, E, tol=1e-14, maxit=12, stop_on_increase=False)
+    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-14, maxit=12,
+                    stop_on_increase=False, sketch_over=over, prec=lrfg.MIXED)
+    res, _ = P.solve(E, want_field=False)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    # the lockstep path takes the same steps
+    many = P.solve_many([E, np.eye(d)[1]])
+    assert abs(many[0].Aeff - res.Aeff) <= 1e-9 * res.Aeff
+    P.free()
+
+
+def test_mixed_tt_at_243(ctx):
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "lognormal_243.json")))
+    o = gold["tt_sketch"]["20"]["opts"]
+    A = lognormal_grf(3, 243, ell=0.2, var=1.0, seed=19020745)
+    a_tt = ctx.tt_compress(torch.as_tensor(A, device="cuda"), 10)
+    P = ctx.problem(a_tt, lrfg.TT, rank=o["rank"], pinv_eps=o["pinv_eps"], tol=o["tol"], maxit=o["maxit"],
+                    stop_on_increase=o["stop_on_increase"], sketch_over=o["sketch_over"], prec=lrfg.MIXED)
+    res, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
+    full = gold["full"]["Aeff"]
+    assert abs(res.Aeff - full) <= 1e-6 * full, (res.Aeff, full, res.iters, res.rel_resid)
+    P.free()
+
+
+def test_mixed_rejected_for_tucker_and_ga(ctx):
+    _, terms, w = smoothed_cube(2, 15, contrast=10.0)
+    with pytest.raises(lrfg.LrfgError):
+        ctx.problem(lrfg.TuckerTensor.from_numpy(*lr.tucker_from_separable(terms, w)), lrfg.TUCKER, prec=lrfg.MIXED)
+    A = lognormal_grf(2, 13, ell=0.2, seed=3)
+    with pytest.raises(lrfg.LrfgError):
+        ctx.problem(A, lrfg.TT, prec=lrfg.MIXED, disc=lrfg.GA)
