@@ -58,8 +58,9 @@ def parse():
                    help="oversampling of the randomised rounding of the products (0: deterministic rounding)")
     p.add_argument("--tt-tol", type=float, default=2.5e-4,
                    help="relative residual at which the TT solve stops (A_eff error ~ 10 x its square)")
-    p.add_argument("--stop-on-increase", action="store_true",
-                   help="also stop when the residual fails to decrease (the paper's rule, Sec. 4.3)")
+    p.add_argument("--stop-on-increase", type=int, default=8,
+                   help="also stop after this many iterations without a new smallest residual (1: the paper's rule, "
+                        "Sec. 4.3; 0: off)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--format", choices=["tt", "tucker"], default="tt",
                    help="low-rank solution format of the timed solve (the coefficient is the same rank-10 TT; a "
@@ -75,8 +76,9 @@ def parse():
     p.add_argument("--rank-cap", type=int, default=30, help="c5: rank cap of the tolerance truncation")
     p.add_argument("--c3-full", choices=["none", "mixed", "fp64"], default="mixed",
                    help="c3: full-format anchor solve on the expanded coefficient")
-    p.add_argument("--case", choices=["tt_apply", "full_apply", "full_apply_mixed"], default=None,
-                   help="run two operator applications of the workload and exit (a small program for profilers)")
+    p.add_argument("--case", choices=["tt_apply", "tt_solve", "full_apply", "full_apply_mixed"], default=None,
+                   help="run two operator applications (tt_solve: one TT solve, the timed step) of the workload and "
+                        "exit (a small program for profilers)")
     return p.parse_args()
 
 
@@ -265,7 +267,7 @@ def oracle_applies_per_solve(args):
     o = g["opts"]
     same = (args.N == 243 and args.coeff_rank == 10 and o["rank"] == args.rank and o["sketch_over"] == args.sketch_over
             and o["tol"] == args.tt_tol and o["pinv_eps"] == args.pinv_eps and o["maxit"] == args.maxit
-            and bool(o["stop_on_increase"]) == bool(args.stop_on_increase))
+            and int(o["stop_on_increase"]) == int(args.stop_on_increase))
     return (g["applies"], g) if same else None
 
 
@@ -521,7 +523,7 @@ def solve_host(ctx, host_cores, args, E):
     o = L.lrfg_opts()
     o.fmt = L.LRFG_TUCKER if args.format == "tucker" else L.LRFG_TT
     o.prec, o.rank, o.pinv_eps = L.LRFG_FP64, args.rank, args.pinv_eps
-    o.tol, o.maxit, o.stop_on_increase = args.tt_tol, args.maxit, int(args.stop_on_increase)
+    o.tol, o.maxit, o.stop_on_increase = args.tt_tol, args.maxit, args.stop_on_increase
     o.sketch_over, o.sketch_seed = args.sketch_over, 0
     res = L.lrfg_result()
     Ed = (C.c_double * 3)(*E)
@@ -889,6 +891,14 @@ def run_case(args):
     ctx = lrfg.Context(0)
     A = torch.as_tensor(make_coefficient(args.N), device="cuda:0")
     a_tt = ctx.tt_compress(A, args.coeff_rank)
+    if args.case == "tt_solve":
+        P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
+                        stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over)
+        r, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
+        print(json.dumps({"case": args.case, "N": args.N, "iters": r.iters, "aeff": r.Aeff, "ok": True}))
+        P.free()
+        ctx.close()
+        return
     if args.case == "tt_apply":
         P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, sketch_over=args.sketch_over)
         x = P.rhs([1.0, 0.0, 0.0])

@@ -123,7 +123,9 @@ typedef struct {
                            (0 selects 0.1) */
   double tol;           /* relative residual tolerance (preconditioned residual) */
   int maxit;            /* iteration cap */
-  int stop_on_increase; /* LRFG_TT: stop when the residual norm fails to decrease (Sec. 4.3) */
+  int stop_on_increase; /* low-rank formats: 1 = stop when the residual norm fails to decrease (Sec. 4.3);
+                           k > 1 = stop after k consecutive iterations without a new smallest residual (the
+                           patience: the randomised rounding's residual wanders near its floor); 0 = off */
   double rank_tol;      /* LRFG_TT / LRFG_TUCKER: 0 = fixed rank `rank`.  > 0: every truncation T keeps the
                            smallest ranks (at most `rank`) whose relative Frobenius error is <= rank_tol:
                            tol / sqrt(d-1) per TT bond (App. A.3.3), tol / sqrt(d) per Tucker mode (App.

@@ -579,8 +579,9 @@ def minres(op: LowRankGaNi, E, tol=1e-10, maxit=200, stop_on_increase=True, call
     """Minimal-residual iteration with truncation (Sec. 3.3):
         r_i = T(b - C u_i),  omega_i = Re(C r_i, r_i) / ||C r_i||^2,  u_{i+1} = T(u_i + omega_i r_i).
     Stops when ||r_i|| fails to decrease (returning the iterate with the smallest residual, Sec. 4.3),
-    when ||r_i|| <= tol ||b||, or after maxit iterations.  Returns dict(u, iters, rel_resid, history,
-    Aeff)."""
+    when ||r_i|| <= tol ||b||, or after maxit iterations.  ``stop_on_increase`` = k > 1 (an int) stops after k
+    consecutive iterations without a new smallest residual instead of at the first failure.  Returns dict(u,
+    iters, rel_resid, history, Aeff)."""
     f = op.f
     E = np.asarray(E, dtype=np.float64)
     b = op.rhs(E)
@@ -589,6 +590,8 @@ def minres(op: LowRankGaNi, E, tol=1e-10, maxit=200, stop_on_increase=True, call
     best = (np.inf, u, 0)
     hist = []
     it = 0
+    patience = int(stop_on_increase)
+    since_best = 0
     while True:
         r = op.T(f.add(b, f.scale(op.apply(u), -1.0))) if it > 0 else b
         nr = f.norm(r) / nb if nb > 0 else 0.0
@@ -597,8 +600,11 @@ def minres(op: LowRankGaNi, E, tol=1e-10, maxit=200, stop_on_increase=True, call
             callback(it, u, nr)
         if nr < best[0]:
             best = (nr, u, it)
-        elif stop_on_increase:
-            break
+            since_best = 0
+        elif patience:
+            since_best += 1
+            if since_best >= patience:
+                break
         if nr <= tol or it >= maxit:
             break
         q = op.apply(r)

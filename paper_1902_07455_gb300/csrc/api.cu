@@ -955,6 +955,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
     tt_round(ctx, view_of(diff), rc, rn, rtol);
     r = std::move(rn);
   };
+  int since_best = 0;  // iterations since the last new smallest residual (stop_on_increase > 1: the patience)
   while (nb > 0.0) {
     double nr = std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
     if (it == 0 && u_zero) nr = 1.0;  // r = b
@@ -962,6 +963,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
       best = nr;
       best_it = it;
       best_zero = u_zero;
+      since_best = 0;
       if (!u_zero) tt_copy(ctx, view_of(u), best_u);
     } else if (adapt && rc < cap) {
       rc = std::min(cap, rc + std::max(1, P->opts.rank_step));
@@ -978,7 +980,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
       }
       nr = u_zero ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
       best = nr;
-    } else if (P->opts.stop_on_increase || adapt) {
+    } else if (adapt || (P->opts.stop_on_increase && ++since_best >= P->opts.stop_on_increase)) {
       break;
     }
     if (nr <= P->opts.tol || it >= P->opts.maxit) break;
@@ -1160,7 +1162,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
   host_dots(b, b, nullptr, nullptr);
   std::vector<double> nb2(nb), best(nb, INFINITY);
   for (int i = 0; i < nb; ++i) nb2[i] = std::sqrt(std::max(h[i], 0.0));
-  std::vector<int> best_it(nb, 0), active(nb, 1), best_zero(nb, 1);
+  std::vector<int> best_it(nb, 0), active(nb, 1), best_zero(nb, 1), since_best(nb, 0);
   std::vector<double> omega(nb);
   DBuf<double> om_dev(ctx->pool, (size_t)nb);
   TTBatch u, r;
@@ -1182,8 +1184,9 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
         best[i] = nr[i];
         best_it[i] = it;
         best_zero[i] = u_zero ? 1 : 0;
+        since_best[i] = 0;
         if (!u_zero) tt_copy(ctx, item_view(u, i), best_u[i]);
-      } else if (P->opts.stop_on_increase) {
+      } else if (P->opts.stop_on_increase && ++since_best[i] >= P->opts.stop_on_increase) {
         active[i] = 0;
         continue;
       }

@@ -537,6 +537,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     tk_round(ctx, tk_view(diff), rc, rn, rtol);
     r = std::move(rn);
   };
+  int since_best = 0;  // iterations since the last new smallest residual (stop_on_increase > 1: the patience)
   while (nb > 0.0) {
     double nr = std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
     if (it == 0 && u_zero) nr = 1.0;  // r = b
@@ -544,6 +545,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
       best = nr;
       best_it = it;
       best_zero = u_zero;
+      since_best = 0;
       if (!u_zero) tk_copy(ctx, tk_view(u), best_u);
     } else if (adapt && rc < rank) {
       rc = std::min(rank, rc + std::max(1, rank_step));
@@ -560,7 +562,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
       }
       nr = u_zero ? 1.0 : std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
       best = nr;
-    } else if (stop_on_increase || adapt) {
+    } else if (adapt || (stop_on_increase && ++since_best >= stop_on_increase)) {
       break;
     }
     if (nr <= tol || it >= maxit) break;

@@ -149,7 +149,7 @@ class ScriptedOperator:
     identity except on one scripted call, where it scales its argument up; A_eff is replaced by a marker
     that identifies the iterate it is evaluated on."""
 
-    def __init__(self, bump_call):
+    def __init__(self, bump_call, factor=100.0):
         rng = np.random.Generator(np.random.PCG64(7))
         Q, _ = np.linalg.qr(rng.standard_normal((9, 9)))
         self.C = Q @ np.diag(np.linspace(1.0, 4.0, 9)) @ Q.T
@@ -158,6 +158,7 @@ class ScriptedOperator:
         self.shape = (3, 3)
         self.calls = 0
         self.bump_call = bump_call
+        self.factor = factor
 
     def _tt(self, x):
         return [np.asarray(G, dtype=np.complex128) for G in lr.tt_svd(np.asarray(x).reshape(3, 3))]
@@ -174,7 +175,7 @@ class ScriptedOperator:
     def T(self, x):
         self.calls += 1
         y = self._vec(x)
-        return self._tt(100.0 * y if self.calls == self.bump_call else y)
+        return self._tt(self.factor * y if self.calls == self.bump_call else y)
 
     def homogenised_coefficient(self, uh, E):
         return float(np.real(np.sum(self._vec(uh) * np.arange(1, 10))))
@@ -205,3 +206,19 @@ def test_minres_without_the_rise_runs_on():
     op = ScriptedOperator(bump_call=-1)
     out = lr.minres(op, np.zeros(2), tol=1e-14, maxit=5)
     assert out["iters"] == 5 and all(b < a for a, b in zip(out["history"], out["history"][1:]))
+
+
+def test_minres_patience_continues_past_one_rise():
+    """stop_on_increase = k > 1: the iteration survives fewer than k consecutive failures to decrease and returns the
+    best iterate seen; after the scripted rise at step 3 the next steps improve on step 2 again."""
+    # a residual scaled by 3 at step 3: a rise, then the next steps (an overshot step, then recovery) pass below
+    # step 2's residual within the patience
+    op = ScriptedOperator(bump_call=6, factor=3.0)
+    out = lr.minres(op, np.zeros(2), tol=1e-14, maxit=8, stop_on_increase=3)
+    h = out["history"]
+    assert h[3] > h[2]
+    assert out["iters"] > 3 and out["rel_resid"] < h[2]
+    assert out["rel_resid"] == min(h)
+    # patience 1 is the paper's rule: stop at the first rise
+    one = lr.minres(ScriptedOperator(bump_call=6, factor=3.0), np.zeros(2), tol=1e-14, maxit=8, stop_on_increase=1)
+    assert one["iters"] == 2
