@@ -149,6 +149,10 @@ typedef struct {
                            of ranks rank + p (products never formed); the other truncations stay deterministic.
                            An extension of the paper's method (Al Daas et al. 2023); LRFG_ENOTSUP elsewhere */
   unsigned int sketch_seed; /* SplitMix64 stream of that sketch */
+  int sketch_keep;      /* with sketch_over > 0: 0 = the randomised truncations of the products end with the
+                           deterministic rounding to `rank`; 1 = they return the sketch's rank rank + sketch_over
+                           (the intermediate rank of the product truncations, the other truncations unchanged:
+                           the operator's output then has rank rank + sketch_over) */
 } lrfg_opts;
 
 typedef struct {
@@ -226,6 +230,16 @@ lrfg_status lrfg_tt_hadamard(lrfg_ctx* ctx, const lrfg_tt* x, const lrfg_tt* y, 
  * out->cores must each hold (rx[j]+ry[j]) N[j] (rx[j+1]+ry[j+1]) doubles (first/last: one side 1). */
 lrfg_status lrfg_tt_add(lrfg_ctx* ctx, double alpha, const lrfg_tt* x, double beta, const lrfg_tt* y,
                         lrfg_tt* out);
+
+/* The eigenproblem inside every truncation T (App. A.3.3): the Gram-SVD rounding truncates each bond through
+ * the k largest eigenpairs of a small symmetric positive semidefinite Gram core.  For `batch` symmetric FP64
+ * matrices A (device, n x n row-major each, only symmetric input is meaningful, left unchanged): w (device,
+ * n doubles per item) receives the k largest eigenvalues in descending order in w[0..k); V (device, n x n
+ * row-major per item) the matching orthonormal eigenvectors in its first k columns.  Entries of w past k and
+ * columns of V past k are not written.  Absolute accuracy about eps ||A|| (Householder tridiagonalisation, bisection, inverse
+ * iteration with re-orthogonalisation of eigenvalues closer than 1e-3 ||A||; one thread block per matrix).
+ * k >= 1 (k > n is clamped to n); n >= 1, batch >= 1.  Asynchronous on the context's stream. */
+lrfg_status lrfg_sym_eig(lrfg_ctx* ctx, const double* A, int n, int k, int batch, double* w, double* V);
 
 /* Rank truncation T (App. A.3.3) to ranks <= rmax: the result equals TT rounding (right-to-left
  * orthogonalisation, then left-to-right truncated SVDs) up to rounding; computed from Gram matrices

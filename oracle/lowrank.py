@@ -467,13 +467,15 @@ class LowRankGaNi:
     def __init__(self, a_lr, shape, fmt="tt", rank=10, pinv_eps=0.1, rank_tol=None, B=None, sketch=None):
         self.f = FORMATS[fmt]
         self.fmt = fmt
-        # randomised rounding of the products (TT only): (oversampling p, seed) or None.  The material
+        # randomised rounding of the products (TT only): (oversampling p, seed[, keep]) or None.  The material
         # products and the P~^-1 product are then truncated by ``sketch.tt_round_sketch`` with a sketch of
         # ranks rank + p, acting on grid values (the material product is formed there; the P~^-1 product
-        # is mapped there by F^-1 and back by F); every other T stays the deterministic rounding.
+        # is mapped there by F^-1 and back by F); every other T stays the deterministic rounding.  keep: those
+        # two truncations return the sketch's rank rank + p (no final rounding to rank).
         if sketch is not None and fmt != "tt":
             raise ValueError("the randomised rounding is defined for the TT format")
-        self.sketch = None if sketch is None else (int(sketch[0]), int(sketch[1]))
+        self.sketch = None if sketch is None else (int(sketch[0]), int(sketch[1]),
+                                                   bool(sketch[2]) if len(sketch) > 2 else False)
         self.a = a_lr
         # constant anisotropic part: A~(x) = a(x) I + B (the modified materials of Sec. 4.4)
         self.B = None if B is None else np.asarray(B, dtype=np.float64)
@@ -496,9 +498,9 @@ class LowRankGaNi:
         if self.sketch is None:
             return self.T(x)
         from . import sketch as _sk
-        over, seed = self.sketch
+        over, seed, keep = self.sketch
         omega = _sk.sketch_tt(self.shape, self.rank + over, seed)
-        return _sk.tt_round_sketch(x, omega, rmax=self.rank, tol=self.rank_tol)
+        return _sk.tt_round_sketch(x, omega, rmax=self.rank, tol=self.rank_tol, final=not keep)
 
     def T_pinv(self, sh):
         """T P~^-1 s for a Fourier tensor s: with ``sketch`` the product is truncated as grid values."""

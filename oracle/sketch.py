@@ -60,9 +60,10 @@ def sketch_tt(shape, ell, seed: int):
     return out
 
 
-def tt_round_sketch(y, omega, rmax=None, tol=None):
+def tt_round_sketch(y, omega, rmax=None, tol=None, final=True):
     """Randomised TT rounding of y with the sketch TT omega (randomize-then-orthogonalize, then the
-    deterministic rounding of App. A.3.3 to rank rmax / tolerance tol)."""
+    deterministic rounding of App. A.3.3 to rank rmax / tolerance tol; final=False: the left-orthonormal
+    result of the sketch, of the sketch's ranks, without that last step)."""
     d = len(y)
     if d == 1:
         return [y[0].copy()]
@@ -79,4 +80,6 @@ def tt_round_sketch(y, omega, rmax=None, tol=None):
         M = Q.conj().T @ X
         x[j] = Q.reshape(a, n, Q.shape[1])
         x[j + 1] = np.tensordot(M, x[j + 1], axes=([1], [0]))
+    if not final:
+        return x
     return _lr.tt_round(x, rmax=rmax, tol=tol)

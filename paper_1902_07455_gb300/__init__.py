@@ -245,6 +245,22 @@ class Context:
                                                 float(scale)))
         return out
 
+    def sym_eig(self, A, k: int):
+        """k largest eigenpairs of a batch of symmetric float64 CUDA matrices (batch, n, n) or (n, n):
+        (w (batch, k) descending, V (batch, n, k) orthonormal columns) — the eigensolver of the truncations."""
+        torch = _torch()
+        if A.dtype != torch.float64 or A.dim() not in (2, 3) or A.shape[-1] != A.shape[-2]:
+            raise ValueError("A must be a float64 tensor (n, n) or (batch, n, n)")
+        single = A.dim() == 2
+        A = (A[None] if single else A).contiguous()
+        b, n, _ = A.shape
+        k = min(int(k), n)
+        w = torch.empty((b, n), dtype=torch.float64, device=A.device)
+        V = torch.empty((b, n, n), dtype=torch.float64, device=A.device)
+        self.check(self.lib.lrfg_sym_eig(self.h, _ptr(A), n, k, b, _ptr(w), _ptr(V)))
+        w, V = w[:, :k], V[:, :, :k]
+        return (w[0], V[0]) if single else (w, V)
+
     # ---- TT operations (rows a3..a7) -------------------------------------------------------------
     def _alloc_tt(self, shape, ranks):
         torch = _torch()
@@ -379,7 +395,8 @@ class Context:
     def problem(self, coeff, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8, maxit: int = 200,
                 stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
                 coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
-                disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0) -> "Problem":
+                disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0,
+                sketch_keep: bool = False) -> "Problem":
         """``prec``: LRFG_FP64, or LRFG_MIXED (FULL: FP32 storage and FFTs, FP64 scalars; TT: FP32 fibre transforms
         and sketch side in the solve's steps, FP64 residual, values, eigen-decompositions, dots and A_eff).
         ``rank_tol`` > 0: tolerance truncation with ``rank`` as the cap (0: fixed rank).  ``coeff_rank``:
@@ -388,9 +405,10 @@ class Context:
         positive semidefinite d x d anisotropic part, A~ = a I + B.  ``disc``: GANI, or GA (exact integration
         of the pixel-wise constant material on the double grid; FULL, FP64).  ``sketch_over`` > 0 (TT, GaNi):
         the material and P~^-1 products are truncated by the randomised rounding with a sketch of ranks
-        rank + sketch_over from SplitMix64 stream ``sketch_seed``."""
+        rank + sketch_over from SplitMix64 stream ``sketch_seed``; ``sketch_keep``: those truncations keep the
+        sketch's rank (no final rounding to ``rank``)."""
         return Problem(self, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec, rank_tol, coeff_rank,
-                       rank_start, rank_step, B, disc, sketch_over, sketch_seed)
+                       rank_start, rank_step, B, disc, sketch_over, sketch_seed, sketch_keep)
 
     def field_from_full(self, values) -> "Field":
         torch = _torch()
@@ -482,7 +500,7 @@ class Problem:
 
     def __init__(self, ctx: Context, coeff, fmt, rank, pinv_eps, tol, maxit, stop_on_increase, prec=L.LRFG_FP64,
                  rank_tol=0.0, coeff_rank=0, rank_start=0, rank_step=1, B=None, disc=L.LRFG_GANI, sketch_over=0,
-                 sketch_seed=0):
+                 sketch_seed=0, sketch_keep=False):
         torch = _torch()
         self.ctx = ctx
         self.fmt = fmt
@@ -527,7 +545,7 @@ class Problem:
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
         o.rank_start, o.rank_step, o.disc = int(rank_start), int(rank_step), int(disc)
-        o.sketch_over, o.sketch_seed = int(sketch_over), int(sketch_seed)
+        o.sketch_over, o.sketch_seed, o.sketch_keep = int(sketch_over), int(sketch_seed), int(bool(sketch_keep))
         h = C.c_void_p()
         ctx.check(ctx.lib.lrfg_problem_create(ctx.h, C.byref(c), C.byref(o), C.byref(h)))
         del keep

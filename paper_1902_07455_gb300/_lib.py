@@ -35,7 +35,7 @@ class lrfg_opts(C.Structure):
     _fields_ = [("fmt", C.c_int), ("prec", C.c_int), ("rank", C.c_int), ("pinv_eps", C.c_double),
                 ("tol", C.c_double), ("maxit", C.c_int), ("stop_on_increase", C.c_int), ("rank_tol", C.c_double),
                 ("coeff_rank", C.c_int), ("rank_start", C.c_int), ("rank_step", C.c_int), ("disc", C.c_int),
-                ("sketch_over", C.c_int), ("sketch_seed", C.c_uint)]
+                ("sketch_over", C.c_int), ("sketch_seed", C.c_uint), ("sketch_keep", C.c_int)]
 
 
 class lrfg_result(C.Structure):
@@ -80,6 +80,7 @@ SIGNATURES = {
     "lrfg_tt_hadamard_round_sketch": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), _I, C.c_ulonglong, _I, _D,
                                             C.POINTER(lrfg_tt)]),
     "lrfg_probe_fp64": (_ST, [_P, C.POINTER(_D), C.POINTER(_D)]),
+    "lrfg_sym_eig": (_ST, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "lrfg_tt_dot": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(_D)]),
     "lrfg_tt_dot_noalloc": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), _P]),
     "lrfg_tt_precond": (_ST, [_P, C.POINTER(lrfg_tt), _D, _I, C.POINTER(lrfg_tt)]),

@@ -531,7 +531,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r, bool mixed = fal
     }
     for (int alpha = 0; alpha < d; ++alpha)
       for (int j = 0; j < d; ++j) z.y[j][alpha] = (j == alpha) ? grad[j].get() : v.core[j];
-    tt_round_sketch(ctx, z, *om, r, w, tol, mixed);              // T, all components in one sweep
+    tt_round_sketch(ctx, z, *om, r, w, tol, mixed, !P->opts.sketch_keep);  // T, all components in one sweep
     for (auto& g : grad) g.reset();
     for (int alpha = 0; alpha < d; ++alpha) terms[alpha] = item_view(w, alpha);
   } else {
@@ -582,7 +582,7 @@ void lr_apply(lrfg_problem* P, const TTView& v, TT& out, int r, bool mixed = fal
   tt_add_many(ctx, terms, nullptr, d, acc);
   TT sdiv;
   tt_round(ctx, view_of(acc), r, sdiv, tol);                   // T after the sum
-  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol, om, mixed);  // T P~^-1
+  tt_precond(ctx, view_of(sdiv), P->pt, P->pw, r, out, tol, om, mixed, !(om && P->opts.sketch_keep));  // T P~^-1
 }
 
 void lr_rhs(lrfg_problem* P, const double* E, TT& out, int rank) {
@@ -1071,7 +1071,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, boo
       for (int b = 0; b < nb; ++b)
         for (int j = 0; j < d; ++j)
           z.y[j][al * nb + b] = (j == al ? grad[j].get() : v.core[j]) + (size_t)b * v.elems(j);
-    tt_round_sketch(ctx, z, *om, r, w, 0.0, mixed);
+    tt_round_sketch(ctx, z, *om, r, w, 0.0, mixed, !P->opts.sketch_keep);
   } else {
     TTBatch kr;
     ttb_alloc(ctx, kr, d, v.N, rk, m);
@@ -1100,7 +1100,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, boo
   TTBatch sdiv;
   tt_round_batch(ctx, batch_view(acc), r, sdiv, 0.0);          // T after the sum
   acc = TTBatch();
-  ttb_precond(ctx, batch_view(sdiv), P->pt, P->pw, r, out, 0.0, om, mixed);  // T P~^-1
+  ttb_precond(ctx, batch_view(sdiv), P->pt, P->pw, r, out, 0.0, om, mixed, !(om && P->opts.sketch_keep));
 }
 
 // copy of item b of `src` into item b of `dst` (same shapes)
@@ -1610,6 +1610,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->rank_start >= 0 && opts->rank_step >= 0, "rank_start and rank_step must be >= 0");
     LRFG_REQUIRE(opts->disc == LRFG_GANI || opts->disc == LRFG_GA, "unknown discretisation %d", (int)opts->disc);
     LRFG_REQUIRE(opts->sketch_over >= 0, "sketch_over must be >= 0 (got %d)", opts->sketch_over);
+    LRFG_REQUIRE(opts->sketch_keep == 0 || opts->sketch_over > 0, "sketch_keep needs sketch_over > 0");
     if (opts->sketch_over > 0 && (opts->fmt != LRFG_TT || opts->disc != LRFG_GANI))
       fail(LRFG_ENOTSUP, "the randomised rounding (sketch_over > 0) is implemented for LRFG_TT GaNi solutions");
     if (opts->disc == LRFG_GA && ((opts->fmt != LRFG_FULL && opts->fmt != LRFG_TT) || opts->prec != LRFG_FP64))

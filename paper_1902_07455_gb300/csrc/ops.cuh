@@ -146,7 +146,8 @@ void tt_mode_operator(lrfg_ctx* ctx, const TTView& x, int j, int kind, double pa
 void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector<double>& w);
 // out = T(P~^-1 x) with the exponential sum (t, w); omega non-null: T is the randomised rounding with that sketch
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w,
-                int rmax, TT& out, double tol = 0.0, const TTView* omega = nullptr, bool fp32 = false);
+                int rmax, TT& out, double tol = 0.0, const TTView* omega = nullptr, bool fp32 = false,
+                bool final = true);
 
 // block copy of a carriage (a x n x b) into a larger one (A x n x B) at rank offsets (oa, ob)
 void tt_embed(lrfg_ctx* ctx, const double* src, int a, int n, int b, double* dst, int A, int B, int oa, int ob);
@@ -182,9 +183,10 @@ struct SketchSource {
 void sketch_tt(lrfg_ctx* ctx, int d, const int* N, int ell, unsigned long long seed, TT& out);
 // randomised rounding of every item to rank rmax (tolerance tol > 0: the smallest ranks <= rmax within it)
 // fp32: the right sweep and the sketched products in FP32 (they only choose the subspaces; every projection of
-// the tensor's values stays FP64)
+// the tensor's values stays FP64).  final = false: return the rank-l left-orthonormal result of the sketch
+// without the deterministic rounding to rmax / tol.
 void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out,
-                     double tol = 0.0, bool fp32 = false);
+                     double tol = 0.0, bool fp32 = false, bool final = true);
 
 // ---- ttbatch.cu ---------------------------------------------------------------------------------
 TTView item_view_of(const TTBatchView& x, int b);
@@ -196,7 +198,7 @@ void ttb_add_many(lrfg_ctx* ctx, const TTBatchView* xs, int m, const double* hs,
 void ttb_dot_device(lrfg_ctx* ctx, const TTBatchView& x, const TTBatchView& y, double* out_dev);
 // out_i = T(P~^-1 x_i) (omega non-null: randomised rounding, one launch sequence for all items)
 void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>& t, const std::vector<double>& w,
-                 int rmax, TTBatch& out, double tol, const TTView* omega, bool fp32 = false);
+                 int rmax, TTBatch& out, double tol, const TTView* omega, bool fp32 = false, bool final = true);
 
 // ---- tucker.cu ----------------------------------------------------------------------------------
 // Tucker tensor on the device: core (r_0, .., r_{d-1}) row-major, factor j (N_j, r_j) row-major

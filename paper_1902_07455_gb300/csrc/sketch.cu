@@ -294,7 +294,7 @@ static void sketch_product(lrfg_ctx* ctx, bool fp32, int m, int l, int k, const 
 }
 
 void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, int rmax, TTBatch& out, double tol,
-                     bool fp32) {
+                     bool fp32, bool final) {
   const int d = z.d, nb = z.nb;
   LRFG_REQUIRE(d >= 2 && d <= 3, "randomised rounding needs d = 2 or 3");
   LRFG_REQUIRE(nb >= 1 && nb <= kMaxSketchItems, "randomised rounding batch of %d items", nb);
@@ -392,7 +392,11 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
   y.core[jl] = DBuf<double>(ctx->pool, (size_t)sy * nb);
   gemm(ctx, 0, 0, l[jl], N[jl], s[jl], 1.0, M.get(), s[jl], (long long)l[jl] * s[jl], Zl.get(), N[jl], el, 0.0,
        y.core[jl].get(), N[jl], sy, nb);
-  // deterministic rounding of the rank-l result
+  // deterministic rounding of the rank-l result (or, without `final`, the rank-l result itself)
+  if (!final) {
+    out = std::move(y);
+    return;
+  }
   tt_round_batch(ctx, batch_view(y), rmax, out, tol);
 }
 

@@ -166,6 +166,139 @@ __device__ void trid_solve(int n, const double* dl, const double* dd, const doub
   }
 }
 
+// Gershgorin interval of the tridiagonal (d, e) and the largest e_i^2, by warp 0 (lanes over the rows), left in
+// red[35] (lower end), red[36] (upper end), red[37]; e2 <- e^2 (e2[n-1] = 0).  All threads of the block call it.
+__device__ void trid_gershgorin(const double* d, const double* e, double* e2, int n, double* red) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid < 32) {
+    double l0 = INFINITY, h0 = -INFINITY, em = 0.0;
+    for (int i = tid; i < n; i += 32) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+      l0 = fmin(l0, d[i] - r);
+      h0 = fmax(h0, d[i] + r);
+      if (i < n - 1) em = fmax(em, e[i] * e[i]);
+    }
+    for (int o = 16; o; o >>= 1) {
+      l0 = fmin(l0, __shfl_xor_sync(0xffffffff, l0, o));
+      h0 = fmax(h0, __shfl_xor_sync(0xffffffff, h0, o));
+      em = fmax(em, __shfl_xor_sync(0xffffffff, em, o));
+    }
+    if (tid == 0) {
+      red[35] = l0;
+      red[36] = h0;
+      red[37] = em;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nthr) e2[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
+  __syncthreads();
+}
+
+// The k largest eigenvalues of the symmetric tridiagonal with diagonal d and squared off-diagonal e2 into lam, in
+// descending order, given its Gershgorin interval [lo, hi] (tnorm = max(|lo|, |hi|) > 0) and max e_i^2 (emax2):
+// (a) FP32 localisation, (b) FP64 multisection to the absolute resolution eps ||T||, then exactly equal values
+// separated slightly so that the inverse iterations' factorisations differ.  Scratch: bra, brc (k doubles each),
+// fb (n doubles: 2n floats, then the scaled diagonal); e2 is scaled in place.  All threads of the block call it.
+__device__ void trid_bisect(const double* d, double* e2, int n, int k, double lo, double hi, double emax2,
+                            double* lam, double* bra, double* brc, double* fb) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  // (a) FP32 localisation of each eigenvalue in the Gershgorin interval
+  float* df = (float*)fb;  // n floats
+  float* e2f = df + n;     // n floats
+  for (int i = tid; i < n; i += nthr) {
+    df[i] = (float)d[i];
+    e2f[i] = (float)e2[i];
+  }
+  __syncthreads();
+  const double glo = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, ghi = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int t = warp; t < k; t += nw) {
+      const int idx = n - 1 - t;
+      float a = (float)glo, c = (float)ghi;
+      // five rounds of 32-way multisection (about 25 bits), one warp per eigenvalue
+      for (int it = 0; it < 5; ++it) {
+        const float h = (c - a) * (1.0f / 33.0f);
+        const float x = a + h * (float)(lane + 1);
+        const unsigned above = __ballot_sync(0xffffffff, sturm_count_f32(df, e2f, n, x) > idx);
+        const int f = above ? (__ffs(above) - 1) : 32;
+        const float na = (f == 0) ? a : a + h * (float)f;
+        const float nc = (f == 32) ? c : a + h * (float)(f + 1);
+        if (!(na < nc)) break;  // FP32 resolution reached
+        a = na;
+        c = nc;
+      }
+      if (lane == 0) {
+        const double w = (double)c - (double)a;
+        bra[t] = fmax(glo, (double)a - 4.0 * w - 1e-6 * tnorm);
+        brc[t] = fmin(ghi, (double)c + 4.0 * w + 1e-6 * tnorm);
+      }
+    }
+  }
+  __syncthreads();
+  // scaled copy of the tridiagonal (exact power of two, |T| in [0.5, 1)) for the FP64 counts: the four
+  // steps between range checks cannot leave the 2^(+-600) window
+  int texp = 0;
+  frexp(tnorm, &texp);
+  const double sg = ldexp(1.0, -texp), sg2 = sg * sg;
+  double* ds = (double*)df;  // the FP32 copies are no longer needed
+  for (int i = tid; i < n; i += nthr) {
+    ds[i] = d[i] * sg;
+    e2[i] *= sg2;
+  }
+  __syncthreads();
+  // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 4-way multisection by
+  // groups of four lanes (eight eigenvalues per warp) until the bracket is at the FP64 resolution.  A
+  // warp-wide FP64 instruction occupies the SM's FP64 pipe for 16 cycles whatever the lane count, so the
+  // FP64 lane-work per bit is what matters: 4 points per 2 bits, against 32 per 5 bits for a warp-wide
+  // multisection, at about twice the rounds.
+  {
+    const int lane = tid & 31, sub = lane & 3, grp = tid >> 2;  // four lanes per eigenvalue
+    const int ngrp = nthr >> 2;
+    const unsigned gmask = 0xfu << (lane & ~3);
+    for (int t0 = 0; t0 < k; t0 += ngrp) {
+      // whole warps take part; groups past k work on a dummy copy of eigenvalue t0
+      if ((tid & ~31) >= 4 * (k - t0)) break;
+      const int t = t0 + grp;
+      const int tt = t < k ? t : t0;
+      const int idx = n - 1 - tt;
+      double a = bra[tt] * sg, c = brc[tt] * sg;
+      int ca = (sub == 0) ? sturm_count(ds, e2, n, a) : 0;
+      int cc = (sub == 1) ? sturm_count(ds, e2, n, c) : 0;
+      ca = __shfl_sync(gmask, ca, (lane & ~3) | 0);
+      cc = __shfl_sync(gmask, cc, (lane & ~3) | 1);
+      if (!(ca <= idx && cc > idx)) { a = glo * sg; c = ghi * sg; }
+      // absolute resolution eps ||T||: the eigenvalues of an FP64 Gram core carry errors of that size,
+      // and inverse iteration only needs the shift to that accuracy
+      const double floor_s = (DBL_EPSILON * tnorm + 4.0 * pivmin) * sg;
+      for (int it = 0; it < 80; ++it) {
+        if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + floor_s) break;
+        const double h = (c - a) * 0.2;
+        const double x = a + h * (double)(sub + 1);  // 4 interior points
+        const int cnt = sturm_count(ds, e2, n, x);
+        const unsigned above = (__ballot_sync(gmask, cnt > idx) >> (lane & ~3)) & 0xfu;
+        // the first point whose count exceeds idx bounds the eigenvalue from above
+        const int f = above ? (__ffs(above) - 1) : 4;
+        const double na = (f == 0) ? a : a + h * (double)f;
+        const double nc = (f == 4) ? c : a + h * (double)(f + 1);
+        a = na;
+        c = nc;
+      }
+      if (sub == 0 && t < k) lam[t] = 0.5 * (a + c) / sg;
+    }
+  }
+  __syncthreads();
+  // separate exactly equal eigenvalues slightly so that their factorisations differ
+  if (tid == 0) {
+    const double sep = 10.0 * DBL_EPSILON * tnorm;
+    for (int t = 1; t < k; ++t)
+      if (lam[t - 1] - lam[t] < sep) lam[t] = lam[t - 1] - sep;
+  }
+  __syncthreads();
+}
+
 // W: n x n work matrix (shared or global), Y: k vectors of length n (vector-major), lu: per-vector LU
 // scratch (4n doubles + n ints as doubles), all per block.  nl, kl: the launch sizes (strides of the
 // inputs and outputs).  Optional reduced problem (nAg != null): the symmetric input A = B B^T has its
@@ -297,33 +430,10 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   }
   __syncthreads();
 
-  // 2. bisection for the k largest eigenvalues (thread t: the t-th largest)
-  // Gershgorin interval and max e^2 by warp 0 (lanes over the rows), broadcast through shared memory
-  if (tid < 32) {
-    double l0 = INFINITY, h0 = -INFINITY, em = 0.0;
-    for (int i = tid; i < n; i += 32) {
-      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-      l0 = fmin(l0, d[i] - r);
-      h0 = fmax(h0, d[i] + r);
-      if (i < n - 1) em = fmax(em, e[i] * e[i]);
-    }
-    for (int o = 16; o; o >>= 1) {
-      l0 = fmin(l0, __shfl_xor_sync(0xffffffff, l0, o));
-      h0 = fmax(h0, __shfl_xor_sync(0xffffffff, h0, o));
-      em = fmax(em, __shfl_xor_sync(0xffffffff, em, o));
-    }
-    if (tid == 0) {
-      red[35] = l0;
-      red[36] = h0;
-      red[37] = em;
-    }
-  }
-  __syncthreads();
+  // 2. bisection for the k largest eigenvalues
+  trid_gershgorin(d, e, e2, n, red);
   const double lo = red[35], hi = red[36], emax2 = red[37];
   const double tnorm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = DBL_MIN * fmax(1.0, emax2);
-  for (int i = tid; i < n; i += nthr) e2[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
-  __syncthreads();
   if (tnorm == 0.0) {
     // the zero matrix: eigenvalues 0, eigenvectors the unit vectors
     for (int t = tid; t < k; t += nthr) lam[t] = 0.0;
@@ -332,101 +442,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
       Y[q] = (i == t) ? 1.0 : 0.0;
     }
   } else {
-  // (a) FP32 localisation of each eigenvalue in the Gershgorin interval
-  float* df = (float*)(lam + k);       // n floats (overlaps nothing: W starts after these when in smem)
-  float* e2f = df + n;                 // n floats
-  for (int i = tid; i < n; i += nthr) {
-    df[i] = (float)d[i];
-    e2f[i] = (float)e2[i];
-  }
-  __syncthreads();
-  double* bra = pv;  // reuse: bracket lower ends for the k eigenvalues (pv, vv are free now)
-  double* brc = vv;  // bracket upper ends
-  const double glo = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, ghi = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
-  {
-    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-    for (int t = warp; t < k; t += nw) {
-      const int idx = n - 1 - t;
-      float a = (float)glo, c = (float)ghi;
-      // five rounds of 32-way multisection (about 25 bits), one warp per eigenvalue
-      for (int it = 0; it < 5; ++it) {
-        const float h = (c - a) * (1.0f / 33.0f);
-        const float x = a + h * (float)(lane + 1);
-        const unsigned above = __ballot_sync(0xffffffff, sturm_count_f32(df, e2f, n, x) > idx);
-        const int f = above ? (__ffs(above) - 1) : 32;
-        const float na = (f == 0) ? a : a + h * (float)f;
-        const float nc = (f == 32) ? c : a + h * (float)(f + 1);
-        if (!(na < nc)) break;  // FP32 resolution reached
-        a = na;
-        c = nc;
-      }
-      if (lane == 0) {
-        const double w = (double)c - (double)a;
-        bra[t] = fmax(glo, (double)a - 4.0 * w - 1e-6 * tnorm);
-        brc[t] = fmin(ghi, (double)c + 4.0 * w + 1e-6 * tnorm);
-      }
-    }
-  }
-  __syncthreads();
-  // scaled copy of the tridiagonal (exact power of two, |T| in [0.5, 1)) for the FP64 counts: the four
-  // steps between range checks cannot leave the 2^(+-600) window
-  int texp = 0;
-  frexp(tnorm, &texp);
-  const double sg = ldexp(1.0, -texp), sg2 = sg * sg;
-  double* ds = (double*)df;  // the FP32 copies are no longer needed
-  for (int i = tid; i < n; i += nthr) {
-    ds[i] = d[i] * sg;
-    e2[i] *= sg2;
-  }
-  __syncthreads();
-  // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 4-way multisection by
-  // groups of four lanes (eight eigenvalues per warp) until the bracket is at the FP64 resolution.  A
-  // warp-wide FP64 instruction occupies the SM's FP64 pipe for 16 cycles whatever the lane count, so the
-  // FP64 lane-work per bit is what matters: 4 points per 2 bits, against 32 per 5 bits for a warp-wide
-  // multisection, at about twice the rounds.
-  {
-    const int lane = tid & 31, sub = lane & 3, grp = tid >> 2;  // four lanes per eigenvalue
-    const int ngrp = nthr >> 2;
-    const unsigned gmask = 0xfu << (lane & ~3);
-    for (int t0 = 0; t0 < k; t0 += ngrp) {
-      // whole warps take part; groups past k work on a dummy copy of eigenvalue t0
-      if ((tid & ~31) >= 4 * (k - t0)) break;
-      const int t = t0 + grp;
-      const int tt = t < k ? t : t0;
-      const int idx = n - 1 - tt;
-      double a = bra[tt] * sg, c = brc[tt] * sg;
-      int ca = (sub == 0) ? sturm_count(ds, e2, n, a) : 0;
-      int cc = (sub == 1) ? sturm_count(ds, e2, n, c) : 0;
-      ca = __shfl_sync(gmask, ca, (lane & ~3) | 0);
-      cc = __shfl_sync(gmask, cc, (lane & ~3) | 1);
-      if (!(ca <= idx && cc > idx)) { a = glo * sg; c = ghi * sg; }
-      // absolute resolution eps ||T||: the eigenvalues of an FP64 Gram core carry errors of that size,
-      // and inverse iteration only needs the shift to that accuracy
-      const double floor_s = (DBL_EPSILON * tnorm + 4.0 * pivmin) * sg;
-      for (int it = 0; it < 80; ++it) {
-        if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + floor_s) break;
-        const double h = (c - a) * 0.2;
-        const double x = a + h * (double)(sub + 1);  // 4 interior points
-        const int cnt = sturm_count(ds, e2, n, x);
-        const unsigned above = (__ballot_sync(gmask, cnt > idx) >> (lane & ~3)) & 0xfu;
-        // the first point whose count exceeds idx bounds the eigenvalue from above
-        const int f = above ? (__ffs(above) - 1) : 4;
-        const double na = (f == 0) ? a : a + h * (double)f;
-        const double nc = (f == 4) ? c : a + h * (double)(f + 1);
-        a = na;
-        c = nc;
-      }
-      if (sub == 0 && t < k) lam[t] = 0.5 * (a + c) / sg;
-    }
-  }
-  __syncthreads();
-  // separate exactly equal eigenvalues slightly so that their factorisations differ
-  if (tid == 0) {
-    const double sep = 10.0 * DBL_EPSILON * tnorm;
-    for (int t = 1; t < k; ++t)
-      if (lam[t - 1] - lam[t] < sep) lam[t] = lam[t - 1] - sep;
-  }
-  __syncthreads();
+  trid_bisect(d, e2, n, k, lo, hi, emax2, lam, pv, vv, lam + k);
 
   // 3. inverse iteration, three passes with cluster re-orthogonalisation
   const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
@@ -815,3 +831,23 @@ void gram_factor(lrfg_ctx* ctx, const double* G, const double* c, int b, int bat
 }
 
 }  // namespace lrfg
+
+using namespace lrfg;
+
+extern "C" lrfg_status lrfg_sym_eig(lrfg_ctx* ctx, const double* A, int n, int k, int batch, double* w, double* V) {
+  if (!ctx) return LRFG_EINVAL;
+  try {
+    LRFG_CUDA(cudaSetDevice(ctx->device));
+    LRFG_REQUIRE(A && w && V, "null argument");
+    LRFG_REQUIRE(n >= 1 && k >= 1 && batch >= 1, "need n >= 1, k >= 1, batch >= 1 (got %d, %d, %d)", n, k, batch);
+    syevx(ctx, A, w, V, n, std::min(k, n), batch);
+    ctx->last_error.clear();
+    return LRFG_OK;
+  } catch (const Error& e) {
+    ctx->last_error = e.msg;
+    return e.status;
+  } catch (...) {
+    ctx->last_error = "unexpected internal error";
+    return LRFG_ECUDA;
+  }
+}

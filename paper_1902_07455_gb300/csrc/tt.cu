@@ -713,7 +713,7 @@ void expsum_inverse(double xmax, double eps, std::vector<double>& t, std::vector
 }
 
 void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
-                TT& out, double tol, const TTView* omega, bool fp32) {
+                TT& out, double tol, const TTView* omega, bool fp32, bool final) {
   // P~^-1 x = sum_m w_m (G_m x ... x G_m) x with G_m = F^-1 diag(exp(-t_m k^2)) F per mode: a TT whose
   // carriages are block rows (first), block diagonal (middle) and block columns (last) over m.
   const int d = x.d;
@@ -745,7 +745,7 @@ void tt_precond(lrfg_ctx* ctx, const TTView& x, const std::vector<double>& t, co
       z.ry[j] = x.r[j];
     }
     TTBatch ob;
-    tt_round_sketch(ctx, z, *omega, rmax, ob, tol, fp32);
+    tt_round_sketch(ctx, z, *omega, rmax, ob, tol, fp32, final);
     out.d = ob.d;
     for (int j = 0; j < 3; ++j) out.N[j] = ob.N[j];
     for (int j = 0; j < 4; ++j) out.r[j] = ob.r[j];

@@ -90,7 +90,7 @@ void ttb_dot_device(lrfg_ctx* ctx, const TTBatchView& x, const TTBatchView& y, d
 }
 
 void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>& t, const std::vector<double>& w,
-                 int rmax, TTBatch& out, double tol, const TTView* omega, bool fp32) {
+                 int rmax, TTBatch& out, double tol, const TTView* omega, bool fp32, bool final) {
   const int d = x.d, nb = x.nb;
   const int R = (int)t.size();
   if (!omega || d < 2) {
@@ -129,7 +129,7 @@ void ttb_precond(lrfg_ctx* ctx, const TTBatchView& x, const std::vector<double>&
     z.s[j] = (j == 0 || j == d) ? 1 : R * x.r[j];
     z.ry[j] = x.r[j];
   }
-  tt_round_sketch(ctx, z, *omega, rmax, out, tol, fp32);
+  tt_round_sketch(ctx, z, *omega, rmax, out, tol, fp32, final);
 }
 
 TTView item_view_of(const TTBatchView& x, int b) {

@@ -23,12 +23,15 @@ def _coeff(d, N, kind):
 
 # tol: a residual each right-hand side reaches well above its truncation floor, where the iterates depend smoothly
 # on the rounding order (stagnating near the floor, the "best iterate" can move with it; see the oracle test below)
-@pytest.mark.parametrize("d,N,rank,over,kind,tol", [(3, 27, 12, 6, "grf", 5e-2), (3, 15, 5, 0, "cube", 5e-2),
-                                                    (2, 45, 8, 8, "grf", 5e-2), (2, 31, 6, 0, "cube", 5e-2)])
-def test_lockstep_equals_separate_solves(ctx, d, N, rank, over, kind, tol):
+@pytest.mark.parametrize("d,N,rank,over,kind,tol,keep", [(3, 27, 12, 6, "grf", 5e-2, False),
+                                                         (3, 15, 5, 0, "cube", 5e-2, False),
+                                                         (2, 45, 8, 8, "grf", 5e-2, False),
+                                                         (2, 31, 6, 0, "cube", 5e-2, False),
+                                                         (2, 45, 8, 8, "grf", 5e-2, True)])
+def test_lockstep_equals_separate_solves(ctx, d, N, rank, over, kind, tol, keep):
     a = _coeff(d, N, kind)
     Es = np.eye(d).tolist() + [[1.0] * d, [0.0] * d]
-    kw = dict(rank=rank, pinv_eps=0.1, tol=tol, maxit=40, stop_on_increase=False, sketch_over=over)
+    kw = dict(rank=rank, pinv_eps=0.1, tol=tol, maxit=40, stop_on_increase=False, sketch_over=over, sketch_keep=keep)
     P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, **kw)
     n0 = ctx.launch_count()
     many = P.solve_many(Es)

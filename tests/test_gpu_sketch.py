@@ -92,6 +92,56 @@ def test_sketched_solve_matches_oracle_minres(ctx, d, N, rank, over, kind):
     assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"], res.iters, ref["iters"])
 
 
+@pytest.mark.parametrize("d,N,rank,rx,over", [(2, 15, 4, [3], 4), (3, 27, 5, [4, 4], 6), (2, 63, 6, [5], 8)])
+def test_kept_sketch_rank_apply_and_rhs_match_oracle(ctx, d, N, rank, rx, over):
+    # sketch_keep: the two sketched truncations return their rank + over result (no final rounding to rank)
+    shape = (N,) * d
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    a = lr.tt_from_separable(terms, w)
+    op = lr.LowRankGaNi(a, shape, fmt="tt", rank=rank, pinv_eps=0.1, sketch=(over, 41, True))
+    x = random_tt(shape, rx, seed=21)
+    ref = np.real(lr.tt_full(lr.tt_idft(op.apply(lr.tt_dft(x)))))
+    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, sketch_over=over, sketch_seed=41,
+                    sketch_keep=True)
+    y = P.apply(ctx.field_from_tt(lrfg.TTensor.from_numpy(x)))
+    assert rel(y.full(), ref) <= 1e-7
+    assert max(y.tt().ranks) <= rank + over
+    E = np.eye(d)[0]
+    refb = np.real(lr.tt_full(lr.tt_idft(op.rhs(E))))
+    assert rel(P.rhs(E).full(), refb) <= 1e-7
+
+
+# a fixed number of iterations in the range where the residual still falls at every step on both sides (near
+# stagnation the truncation to rank picks among near-equal singular values, so that the stop could move)
+@pytest.mark.parametrize("d,N,rank,over,kind,its", [(2, 63, 10, 6, "grf", 10), (3, 27, 6, 6, "cube", 8)])
+def test_kept_sketch_rank_solve_matches_oracle(ctx, d, N, rank, over, kind, its):
+    shape = (N,) * d
+    if kind == "grf":
+        a = lr.tt_svd(lognormal_grf(d, N, ell=0.2, seed=4), rmax=5)
+    else:
+        _, terms, w = smoothed_cube(d, N, contrast=20.0, full=False)
+        a = lr.tt_from_separable(terms, w)
+    E = np.eye(d)[0]
+    op = lr.LowRankGaNi(a, shape, fmt="tt", rank=rank, pinv_eps=0.1, sketch=(over, 5, True))
+    ref = lr.minres(op, E, maxit=its, tol=1e-14, stop_on_increase=False)
+    assert ref["iters"] == its  # still falling at the last step
+    P = ctx.problem(lrfg.TTensor.from_numpy([np.ascontiguousarray(np.real(G)) for G in a]), lrfg.TT, rank=rank,
+                    pinv_eps=0.1, tol=1e-14, maxit=its, stop_on_increase=False, sketch_over=over, sketch_seed=5,
+                    sketch_keep=True)
+    res, _ = P.solve(E, want_field=False)
+    assert res.iters == its
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"], res.iters, ref["iters"])
+    # the residual norm, near the truncation floor, follows the rounding order more than A_eff (quadratic in it)
+    assert abs(res.rel_resid - ref["rel_resid"]) <= 5e-2 * ref["rel_resid"]
+
+
+def test_sketch_keep_needs_the_sketch(ctx):
+    A = lognormal_grf(2, 15, ell=0.2, seed=3)
+    a = lr.tt_svd(A, rmax=4)
+    with pytest.raises(lrfg.LrfgError):
+        ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=4, sketch_keep=True)
+
+
 def test_sketch_option_rejected_outside_tt_gani(ctx):
     A = lognormal_grf(2, 15, ell=0.2, seed=3)
     with pytest.raises(lrfg.LrfgError):

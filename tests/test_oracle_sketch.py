@@ -104,3 +104,19 @@ def test_sketched_minres_reaches_the_deterministic_aeff():
     a = lr.minres(det, E, maxit=40)
     b = lr.minres(skt, E, maxit=40)
     assert abs(a["Aeff"] - b["Aeff"]) <= 1e-5 * a["Aeff"], (a["Aeff"], b["Aeff"])
+
+
+def test_kept_sketch_rank_is_the_sketch_projection():
+    # final=False returns the rank-l left-orthonormal projection of the sketch: its deterministic rounding to r is
+    # the full randomised rounding, and with ranks covered it reproduces the input
+    shape = (9, 11, 13)
+    y = random_tt(shape, [4, 5], seed=3)
+    om = sk.sketch_tt(shape, 7, seed=2)
+    kept = sk.tt_round_sketch(y, om, rmax=3, final=False)
+    assert lr.tt_ranks(kept)[1:-1] == [7, 7] or max(lr.tt_ranks(kept)) <= 7
+    assert _rel(kept, y) <= 1e-12
+    assert _rel(lr.tt_round(kept, rmax=3), sk.tt_round_sketch(y, om, rmax=3)) <= 1e-12
+    for G in kept[:-1]:
+        a, n, b = G.shape
+        M = G.reshape(a * n, b)
+        assert np.allclose(M.T @ M, np.eye(b), atol=1e-12)
