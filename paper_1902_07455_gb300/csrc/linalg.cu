@@ -226,17 +226,30 @@ static void gemm_impl(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K
     if (dynM || dynN) a = std::max<long long>(batch, a / 4);
     return a;
   };
-  // 32 x 32 tiles when 64 x 64 ones would leave most SMs idle (static sizes only: with data-dependent sizes
-  // the active tiles are not known here, and the split count is what spreads those products)
-  const int tile = (!dynM && !dynN && active_tiles(64) < nsm) ? 32 : 64;
-  const int bmn = (M + tile - 1) / tile, bnn = (N + tile - 1) / tile;
+  // 32 x 32 tiles for thin products (one side <= 32: the 64-row staging would be mostly padding), when
+  // 64 x 64 ones would leave most SMs idle, or when they fill the SMs more evenly: the FP64 pipe is shared by
+  // the blocks of an SM, so a product takes as long as its busiest SM, ceil(blocks / SMs) blocks (static
+  // sizes only: with data-dependent sizes the active tiles are not known here, and the split count is what
+  // spreads those products)
+  auto fill = [&](long long blocks) { return (double)blocks / (double)(((blocks + nsm - 1) / nsm) * nsm); };
+  const bool dyn = dynM || dynN;
+  const int tile = (!dyn && (std::min(M, N) <= 32 || active_tiles(64) < nsm ||
+                             fill(active_tiles(32)) > fill(active_tiles(64)) + 0.05))
+                       ? 32
+                       : 64;
   const long long active = active_tiles(tile);
+  // split long K until about two blocks per SM are busy, without passing that (a second, partial round of
+  // blocks would cost as much as the first)
   const int target = 2 * nsm;
   int splits = 1;
-  if (active < target) splits = (int)std::min<long long>((target + active - 1) / active, std::max(1, K / GK));
+  if (active < target) {
+    splits = (int)std::min<long long>((target + active - 1) / active, std::max(1, K / GK));
+    if (active * splits > target) splits = (int)std::max<long long>(1, target / active);
+  }
   int kchunk = (K + splits - 1) / splits;
   kchunk = ((kchunk + GK - 1) / GK) * GK;
   splits = (K + kchunk - 1) / kchunk;
+  const int bmn = (M + tile - 1) / tile, bnn = (N + tile - 1) / tile;
   LRFG_REQUIRE((long long)bmn * splits < 65536, "gemm too many row blocks x splits");
   if (splits > 1)
     LRFG_REQUIRE((long long)bmn * bnn * batch <= kSplitKCounters, "split-K product with too many output tiles");
