@@ -8,8 +8,8 @@ by the oracle's TT-SVD to rank 10; the full-format reference solves the expansio
 the full PCG A_eff (tolerance 1e-8), its iteration count, and the TT minimal-residual A_eff at each rank
 (exponential-sum accuracy 0.1, stop when the residual fails to decrease, at most 60 iterations); and the
 benchmark's TT solve: rank 20 with the randomised rounding of the material and P~^-1 products (oversampling 10,
-SplitMix64 stream 0), stopped at the relative residual 2.5e-4 or after 8 iterations without a new smallest
-residual, at most 80 iterations,
+SplitMix64 stream 0), stopped at the relative residual 3e-4 (no stop on a rise of the residual), at most 80
+iterations,
 with its iterations, operator applications and run time (``--sketch-only`` adds just that entry to an existing
 file).
 """
@@ -62,8 +62,8 @@ def main():
                                  "seconds": time.time() - t0}
             print("tt", r, out["tt"][str(r)], flush=True)
     # the benchmark's TT solve (randomised rounding of the products, residual tolerance)
-    opts = {"rank": 20, "pinv_eps": 0.1, "sketch_over": 10, "sketch_seed": 0, "tol": 2.5e-4,
-            "stop_on_increase": 8, "maxit": 80}
+    opts = {"rank": 20, "pinv_eps": 0.1, "sketch_over": 10, "sketch_seed": 0, "tol": 3e-4,
+            "stop_on_increase": 0, "maxit": 80}
     op = lr.LowRankGaNi(a_tt, (N, N, N), fmt="tt", rank=opts["rank"], pinv_eps=opts["pinv_eps"],
                         sketch=(opts["sketch_over"], opts["sketch_seed"]))
     count = {"applies": 0}
