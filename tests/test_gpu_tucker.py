@@ -64,7 +64,12 @@ def test_tucker_apply_and_rhs(ctx, d, N, rank, rx):
     a_tk = lrfg.TuckerTensor.from_numpy(*lr.tucker_from_separable(terms, w))
     P = ctx.problem(a_tk, lrfg.TUCKER, rank=rank, pinv_eps=0.1)
     out = P.apply(ctx.field_from_tucker(lrfg.TuckerTensor.from_numpy(core, factors))).full()
-    assert rel(out, ref) <= 1e-7
+    # The Gram-SVD truncation drops the pivots of a factor's Gram matrix below eps = 1e-16 of its largest
+    # diagonal, i.e. directions of norm up to sqrt(eps) = 1e-8 of a column (the oracle's QR+SVD keeps them).
+    # The P~^-1 product's factors [G_1 B .. G_R B] are R r nearly collinear columns (R = 8 here), so the
+    # operator carries such differences from up to R r dropped directions: 7e-9..3e-7 across rounding orders
+    # of the same build for (2, 45, 6) — a bound of 1e-6, not a rounding-level one.
+    assert rel(out, ref) <= 1e-6
     E = np.eye(d)[0]
     assert rel(P.rhs(E).full(), real_full(op.rhs(E))) <= 1e-7
 
@@ -126,7 +131,9 @@ def test_cp_solve_matches_oracle_minres(ctx, N, rank, kind):
     # fields agree up to a constant (P~^-1 does not vanish at k = 0, so rounding noise there can leave a
     # tiny mean); compare the zero-mean parts
     g, h = u.full(), np.real(lr.cp_full(lr.cp_idft(ref["u"])))
-    assert rel(g - g.mean(), h - h.mean()) <= 1e-6
+    # the field carries the truncations' sqrt(eps)-level differences (see test_tucker_apply_and_rhs) through the
+    # iterations; A_eff, quadratic in the field's error, is the tight check above
+    assert rel(g - g.mean(), h - h.mean()) <= 1e-5
 
 
 def test_cp_apply_matches_oracle(ctx):
