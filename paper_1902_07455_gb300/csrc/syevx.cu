@@ -1,7 +1,8 @@
-// FP64 symmetric eigensolver for the k largest eigenpairs (k = n: all of them), one block per matrix:
+// FP64 symmetric eigensolver for the k largest eigenpairs (k = n: all of them) of a batch of matrices:
 //  1. Householder tridiagonalisation  Q^T A Q = T  (Golub & Van Loan, "Matrix Computations", 4th ed.,
 //     Alg. 8.3.1), reflectors kept in the columns below the diagonal;
-//  2. eigenvalues of T by bisection on Sturm counts of the LDL^T recurrence (G&VL Sec. 8.4.1);
+//  2. eigenvalues of T by bisection on Sturm counts of the LDL^T recurrence (G&VL Sec. 8.4.1), one warp per
+//     eigenvalue in a launch of its own;
 //  3. eigenvectors of T by inverse iteration (G&VL Sec. 8.2.2) with the tridiagonal LU factorisation
 //     of T - lambda I with partial pivoting (G&VL Sec. 4.3), three passes, vectors of eigenvalues closer
 //     than 1e-3 ||T|| re-orthogonalised against each other by modified Gram-Schmidt after each pass;
@@ -194,123 +195,50 @@ __device__ void trid_gershgorin(const double* d, const double* e, double* e2, in
   __syncthreads();
 }
 
-// The k largest eigenvalues of the symmetric tridiagonal with diagonal d and squared off-diagonal e2 into lam, in
-// descending order, given its Gershgorin interval [lo, hi] (tnorm = max(|lo|, |hi|) > 0) and max e_i^2 (emax2):
-// (a) FP32 localisation, (b) FP64 multisection to the absolute resolution eps ||T||, then exactly equal values
-// separated slightly so that the inverse iterations' factorisations differ.  Scratch: bra, brc (k doubles each),
-// fb (n doubles: 2n floats, then the scaled diagonal); e2 is scaled in place.  All threads of the block call it.
-__device__ void trid_bisect(const double* d, double* e2, int n, int k, double lo, double hi, double emax2,
-                            double* lam, double* bra, double* brc, double* fb) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const double tnorm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = DBL_MIN * fmax(1.0, emax2);
-  // (a) FP32 localisation of each eigenvalue in the Gershgorin interval
-  float* df = (float*)fb;  // n floats
-  float* e2f = df + n;     // n floats
-  for (int i = tid; i < n; i += nthr) {
-    df[i] = (float)d[i];
-    e2f[i] = (float)e2[i];
-  }
-  __syncthreads();
-  const double glo = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, ghi = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
-  {
-    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-    for (int t = warp; t < k; t += nw) {
-      const int idx = n - 1 - t;
-      float a = (float)glo, c = (float)ghi;
-      // five rounds of 32-way multisection (about 25 bits), one warp per eigenvalue
-      for (int it = 0; it < 5; ++it) {
-        const float h = (c - a) * (1.0f / 33.0f);
-        const float x = a + h * (float)(lane + 1);
-        const unsigned above = __ballot_sync(0xffffffff, sturm_count_f32(df, e2f, n, x) > idx);
-        const int f = above ? (__ffs(above) - 1) : 32;
-        const float na = (f == 0) ? a : a + h * (float)f;
-        const float nc = (f == 32) ? c : a + h * (float)(f + 1);
-        if (!(na < nc)) break;  // FP32 resolution reached
-        a = na;
-        c = nc;
-      }
-      if (lane == 0) {
-        const double w = (double)c - (double)a;
-        bra[t] = fmax(glo, (double)a - 4.0 * w - 1e-6 * tnorm);
-        brc[t] = fmin(ghi, (double)c + 4.0 * w + 1e-6 * tnorm);
-      }
-    }
-  }
-  __syncthreads();
-  // scaled copy of the tridiagonal (exact power of two, |T| in [0.5, 1)) for the FP64 counts: the four
-  // steps between range checks cannot leave the 2^(+-600) window
-  int texp = 0;
-  frexp(tnorm, &texp);
-  const double sg = ldexp(1.0, -texp), sg2 = sg * sg;
-  double* ds = (double*)df;  // the FP32 copies are no longer needed
-  for (int i = tid; i < n; i += nthr) {
-    ds[i] = d[i] * sg;
-    e2[i] *= sg2;
-  }
-  __syncthreads();
-  // (b) FP64: verify each bracket (fall back to the Gershgorin interval), then 4-way multisection by
-  // groups of four lanes (eight eigenvalues per warp) until the bracket is at the FP64 resolution.  A
-  // warp-wide FP64 instruction occupies the SM's FP64 pipe for 16 cycles whatever the lane count, so the
-  // FP64 lane-work per bit is what matters: 4 points per 2 bits, against 32 per 5 bits for a warp-wide
-  // multisection, at about twice the rounds.
-  {
-    const int lane = tid & 31, sub = lane & 3, grp = tid >> 2;  // four lanes per eigenvalue
-    const int ngrp = nthr >> 2;
-    const unsigned gmask = 0xfu << (lane & ~3);
-    for (int t0 = 0; t0 < k; t0 += ngrp) {
-      // whole warps take part; groups past k work on a dummy copy of eigenvalue t0
-      if ((tid & ~31) >= 4 * (k - t0)) break;
-      const int t = t0 + grp;
-      const int tt = t < k ? t : t0;
-      const int idx = n - 1 - tt;
-      double a = bra[tt] * sg, c = brc[tt] * sg;
-      int ca = (sub == 0) ? sturm_count(ds, e2, n, a) : 0;
-      int cc = (sub == 1) ? sturm_count(ds, e2, n, c) : 0;
-      ca = __shfl_sync(gmask, ca, (lane & ~3) | 0);
-      cc = __shfl_sync(gmask, cc, (lane & ~3) | 1);
-      if (!(ca <= idx && cc > idx)) { a = glo * sg; c = ghi * sg; }
-      // absolute resolution eps ||T||: the eigenvalues of an FP64 Gram core carry errors of that size,
-      // and inverse iteration only needs the shift to that accuracy
-      const double floor_s = (DBL_EPSILON * tnorm + 4.0 * pivmin) * sg;
-      for (int it = 0; it < 80; ++it) {
-        if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + floor_s) break;
-        const double h = (c - a) * 0.2;
-        const double x = a + h * (double)(sub + 1);  // 4 interior points
-        const int cnt = sturm_count(ds, e2, n, x);
-        const unsigned above = (__ballot_sync(gmask, cnt > idx) >> (lane & ~3)) & 0xfu;
-        // the first point whose count exceeds idx bounds the eigenvalue from above
-        const int f = above ? (__ffs(above) - 1) : 4;
-        const double na = (f == 0) ? a : a + h * (double)f;
-        const double nc = (f == 4) ? c : a + h * (double)(f + 1);
-        a = na;
-        c = nc;
-      }
-      if (sub == 0 && t < k) lam[t] = 0.5 * (a + c) / sg;
-    }
-  }
-  __syncthreads();
-  // separate exactly equal eigenvalues slightly so that their factorisations differ
-  if (tid == 0) {
-    const double sep = 10.0 * DBL_EPSILON * tnorm;
-    for (int t = 1; t < k; ++t)
-      if (lam[t - 1] - lam[t] < sep) lam[t] = lam[t - 1] - sep;
-  }
-  __syncthreads();
+// ---- the decomposition in three launches -----------------------------------------------------------------
+// K1 (one block per matrix) tridiagonalises and bounds the spectrum; K2 (one warp per wanted eigenvalue, all
+// matrices) bisects; K3 (one block per matrix) runs inverse iteration, re-orthogonalises within clusters,
+// back-transforms and writes the outputs.  The bisection is a chain of dependent FP64 Sturm recurrences per
+// point; inside one block the k eigenvalues shared one SM's FP64 pipe (2 FMA/clk), one warp each they get one
+// SM each, so every lane can take its own point (33-way multisection, about 5 bits per count instead of 2).
+// Per-item global scratch (doubles): a header (active size, Gershgorin interval, largest e_i^2, reduced-problem
+// flag and nA), d, e, beta (nl each), lam (kl), the reflectors W (n x n, leading dimension n), the vectors Y
+// (kl x nl, vector-major) and the inverse-iteration LU factors (kl x 5 nl).
+constexpr int kHdr = 8;
+
+static size_t syevx_scratch_per(int nl, int kl) {
+  return kHdr + 3 * (size_t)nl + kl + (size_t)nl * nl + (size_t)kl * nl + (size_t)kl * 5 * nl;
 }
 
-// W: n x n work matrix (shared or global), Y: k vectors of length n (vector-major), lu: per-vector LU
-// scratch (4n doubles + n ints as doubles), all per block.  nl, kl: the launch sizes (strides of the
-// inputs and outputs).  Optional reduced problem (nAg != null): the symmetric input A = B B^T has its
-// nonzero block in the leading nA x nA corner, and A2 = B^T B (B: nl x nl, nonzero block nA x nB) has
-// it in the leading nB x nB corner.  The smaller of the two is decomposed; when that is A2, the left
-// vectors are mapped back as u = B w / sigma and re-orthonormalised (modified Gram-Schmidt), and
-// completed by unit vectors when B has fewer than k nonzero singular values.
-__global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __restrict__ Ag, int nl, int kl, double* wg,
-                                                              double* Vg, int ldv, double* scratch, int use_smem,
-                                                              const int* __restrict__ nAg, const int* __restrict__ nBg,
-                                                              const double* __restrict__ A2g,
-                                                              const double* __restrict__ Bg, double* work) {
+struct SyevxScratch {
+  double *hdr, *d, *e, *beta, *lam, *W, *Y, *lu;
+};
+
+__device__ __forceinline__ SyevxScratch syevx_scratch(double* scratch, int nl, int kl, int item) {
+  SyevxScratch g;
+  g.hdr = scratch + (size_t)item * (kHdr + 3 * (size_t)nl + kl + (size_t)nl * nl + (size_t)kl * nl +
+                                    (size_t)kl * 5 * nl);
+  g.d = g.hdr + kHdr;
+  g.e = g.d + nl;
+  g.beta = g.e + nl;
+  g.lam = g.beta + nl;
+  g.W = g.lam + kl;
+  g.Y = g.W + (size_t)nl * nl;
+  g.lu = g.Y + (size_t)kl * nl;
+  return g;
+}
+
+// K1.  nl, kl: the launch sizes (strides of the inputs and outputs).  Optional reduced problem (nAg != null):
+// the symmetric input A = B B^T has its nonzero block in the leading nA x nA corner, and A2 = B^T B (B: nl x nl,
+// nonzero block nA x nB) has it in the leading nB x nB corner.  The smaller of the two is decomposed; when that
+// is A2, K3 maps the left vectors back as u = B w / sigma, re-orthonormalises them (modified Gram-Schmidt) and
+// completes them by unit vectors when B has fewer than k nonzero singular values.
+__global__ void __launch_bounds__(kSyevxThreads) syevx_tri_kernel(const double* __restrict__ Ag, int nl, int kl,
+                                                                  double* wg, double* Vg, int ldv, double* scratch,
+                                                                  int use_smem, const int* __restrict__ nAg,
+                                                                  const int* __restrict__ nBg,
+                                                                  const double* __restrict__ A2g,
+                                                                  const double* __restrict__ Bg, double* work) {
   extern __shared__ __align__(16) double sm[];
   double* red = sm;            // 33 (32 partials + the result) + padding
   double* d = red + 40;        // nl
@@ -318,12 +246,10 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   double* beta = e + nl;       // nl
   double* pv = beta + nl;      // nl: p / w of the current reflector
   double* vv = pv + nl;        // nl: current reflector v
-  double* e2 = vv + nl;        // nl: e^2 for the Sturm counts
-  double* lam = e2 + nl;       // kl
+  double* e2 = vv + nl;        // nl
   const size_t nnl = (size_t)nl * nl;
-  const size_t per = nnl + (size_t)kl * nl + (size_t)kl * 5 * nl;  // global scratch per block
-  double* gbase = scratch + (size_t)blockIdx.x * per;
-  double* W = use_smem ? (lam + kl + nl) : gbase;  // after lam and the FP32 copies (2nl floats = nl doubles)
+  const SyevxScratch g = syevx_scratch(scratch, nl, kl, blockIdx.x);
+  double* W = use_smem ? (e2 + nl) : g.W;
   const int tid = threadIdx.x, nthr = blockDim.x;
   double* wout = wg + (size_t)blockIdx.x * nl;
   double* Vout = Vg + (size_t)blockIdx.x * (size_t)nl * ldv;
@@ -334,11 +260,13 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   const int n = viaB ? nB : nA;
   const int k = min(kl, n);
   const double* A = (viaB ? A2g : Ag) + (size_t)blockIdx.x * nnl;
-  double* Y = gbase + nnl;
-  double* lu = Y + (size_t)kl * nl;
-  if (tid == 0)
+  if (tid == 0) {
     add_work(work, 4.0 / 3.0 * n * (double)n * n + 4.0 * (double)k * n * n + 60.0 * k * n,
              sizeof(double) * (2.0 * n * n + (double)k * n));
+    g.hdr[0] = (double)n;
+    g.hdr[4] = viaB ? 1.0 : 0.0;
+    g.hdr[5] = (double)nA;
+  }
   for (int t = tid; t < kl; t += nthr) wout[t] = 0.0;
   for (size_t q = tid; q < (size_t)nl * kl; q += nthr) {
     const int i = (int)(q / kl), t = (int)(q - (q / kl) * kl);
@@ -430,19 +358,153 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   }
   __syncthreads();
 
-  // 2. bisection for the k largest eigenvalues
   trid_gershgorin(d, e, e2, n, red);
-  const double lo = red[35], hi = red[36], emax2 = red[37];
+  if (tid == 0) {
+    g.hdr[1] = red[35];
+    g.hdr[2] = red[36];
+    g.hdr[3] = red[37];
+  }
+  for (int i = tid; i < n; i += nthr) {
+    g.d[i] = d[i];
+    g.e[i] = e[i];
+    g.beta[i] = beta[i];
+  }
+  if (use_smem)
+    for (size_t t = tid; t < (size_t)n * n; t += nthr) g.W[t] = W[t];
+}
+
+// K2.  Eigenvalue t (the t-th largest) of the tridiagonal of item blockIdx.y, one warp: (a) FP32 localisation
+// in the Gershgorin interval by five rounds of 33-way multisection (about 25 bits); (b) that bracket, widened
+// and verified with FP64 counts (else the Gershgorin interval), then 33-way FP64 multisection on a copy of T
+// scaled by a power of two to |T| in [0.5, 1) (the counts' range window) down to the absolute resolution
+// eps ||T||: the eigenvalues of an FP64 Gram core carry errors of that size, and inverse iteration only needs
+// the shift to that accuracy.
+__global__ void __launch_bounds__(32) syevx_bisect_kernel(int nl, int kl, double* scratch) {
+  extern __shared__ __align__(16) double sm[];
+  const SyevxScratch g = syevx_scratch(scratch, nl, kl, blockIdx.y);
+  const int n = (int)g.hdr[0];
+  const int t = blockIdx.x, lane = threadIdx.x;
+  if (t >= min(kl, n)) return;
+  const double lo = g.hdr[1], hi = g.hdr[2], emax2 = g.hdr[3];
   const double tnorm = fmax(fabs(lo), fabs(hi));
   if (tnorm == 0.0) {
+    if (lane == 0) g.lam[t] = 0.0;
+    return;
+  }
+  float* df = (float*)sm;   // n floats
+  float* e2f = df + n;      // n floats
+  double* ds = sm + n;      // n: the scaled diagonal
+  double* e2s = ds + n;     // n: the scaled e^2
+  int texp = 0;
+  frexp(tnorm, &texp);
+  const double sg = ldexp(1.0, -texp), sg2 = sg * sg;
+  for (int i = lane; i < n; i += 32) {
+    const double ei = (i < n - 1) ? g.e[i] : 0.0;
+    const double di = g.d[i];
+    df[i] = (float)di;
+    e2f[i] = (float)(ei * ei);
+    ds[i] = di * sg;
+    e2s[i] = (ei * ei) * sg2;
+  }
+  __syncwarp();
+  const int idx = n - 1 - t;
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  const double glo = lo - 2.0 * DBL_EPSILON * tnorm - pivmin, ghi = hi + 2.0 * DBL_EPSILON * tnorm + pivmin;
+  float af = (float)glo, cf = (float)ghi;
+  for (int it = 0; it < 5; ++it) {
+    const float h = (cf - af) * (1.0f / 33.0f);
+    const float x = af + h * (float)(lane + 1);
+    const unsigned above = __ballot_sync(0xffffffff, sturm_count_f32(df, e2f, n, x) > idx);
+    const int f = above ? (__ffs(above) - 1) : 32;
+    const float na = (f == 0) ? af : af + h * (float)f;
+    const float nc = (f == 32) ? cf : af + h * (float)(f + 1);
+    if (!(na < nc)) break;  // FP32 resolution reached
+    af = na;
+    cf = nc;
+  }
+  const double wf = (double)cf - (double)af;
+  double a = fmax(glo, (double)af - 4.0 * wf - 1e-6 * tnorm) * sg;
+  double c = fmin(ghi, (double)cf + 4.0 * wf + 1e-6 * tnorm) * sg;
+  int ca = (lane == 0) ? sturm_count(ds, e2s, n, a) : 0;
+  int cc = (lane == 1) ? sturm_count(ds, e2s, n, c) : 0;
+  ca = __shfl_sync(0xffffffff, ca, 0);
+  cc = __shfl_sync(0xffffffff, cc, 1);
+  if (!(ca <= idx && cc > idx)) {
+    a = glo * sg;
+    c = ghi * sg;
+  }
+  const double floor_s = (DBL_EPSILON * tnorm + 4.0 * pivmin) * sg;
+  for (int it = 0; it < 40; ++it) {
+    if (c - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(c)) + floor_s) break;
+    const double h = (c - a) * (1.0 / 33.0);
+    const double x = a + h * (double)(lane + 1);
+    const unsigned above = __ballot_sync(0xffffffff, sturm_count(ds, e2s, n, x) > idx);
+    // the first point whose count exceeds idx bounds the eigenvalue from above
+    const int f = above ? (__ffs(above) - 1) : 32;
+    const double na = (f == 0) ? a : a + h * (double)f;
+    const double nc = (f == 32) ? c : a + h * (double)(f + 1);
+    if (!(na < nc)) break;
+    a = na;
+    c = nc;
+  }
+  if (lane == 0) g.lam[t] = 0.5 * (a + c) / sg;
+}
+
+// K3.  Eigenvectors of T by inverse iteration (three passes; vectors of eigenvalues closer than 1e-3 ||T||
+// re-orthogonalised after each pass), the back-transformation and the outputs.
+__global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl, double* wg, double* Vg, int ldv,
+                                                                  double* scratch, int smem_flags,
+                                                                  const double* __restrict__ Bg) {
+  extern __shared__ __align__(16) double sm[];
+  const SyevxScratch g = syevx_scratch(scratch, nl, kl, blockIdx.x);
+  const int n = (int)g.hdr[0];
+  if (n == 0) return;
+  double* red = sm;            // 40
+  double* d = red + 40;        // nl
+  double* e = d + nl;          // nl
+  double* beta = e + nl;       // nl
+  double* lam = beta + nl;     // kl
+  // the vectors, their LU factors and the reflectors in shared memory where they fit (flags 1, 2, 4): the
+  // solves, the re-orthogonalisation and the back-transformation are dependent chains of their loads
+  double* next = lam + kl;
+  double* Y = g.Y;
+  double* lu = g.lu;
+  double* W = g.W;
+  if (smem_flags & 1) { Y = next; next += (size_t)kl * nl; }
+  if (smem_flags & 2) { lu = next; next += (size_t)kl * 5 * nl; }
+  if (smem_flags & 4) W = next;
+  const size_t nnl = (size_t)nl * nl;
+  const bool viaB = g.hdr[4] != 0.0;
+  const int nA = (int)g.hdr[5];
+  const int k = min(kl, n);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+  double* wout = wg + (size_t)blockIdx.x * nl;
+  double* Vout = Vg + (size_t)blockIdx.x * (size_t)nl * ldv;
+  for (int i = tid; i < n; i += nthr) {
+    d[i] = g.d[i];
+    e[i] = g.e[i];
+    beta[i] = g.beta[i];
+  }
+  for (int t = tid; t < k; t += nthr) lam[t] = g.lam[t];
+  if (smem_flags & 4)
+    for (size_t t = tid; t < (size_t)n * n; t += nthr) W[t] = g.W[t];
+  __syncthreads();
+  const double tnorm = fmax(fabs(g.hdr[1]), fabs(g.hdr[2]));
+  if (tnorm == 0.0) {
     // the zero matrix: eigenvalues 0, eigenvectors the unit vectors
-    for (int t = tid; t < k; t += nthr) lam[t] = 0.0;
     for (size_t q = tid; q < (size_t)k * n; q += nthr) {
       const int t = (int)(q / n), i = (int)(q - (q / n) * n);
       Y[q] = (i == t) ? 1.0 : 0.0;
     }
   } else {
-  trid_bisect(d, e2, n, k, lo, hi, emax2, lam, pv, vv, lam + k);
+  // separate exactly equal eigenvalues slightly so that their factorisations differ
+  if (tid == 0) {
+    const double sep = 10.0 * DBL_EPSILON * tnorm;
+    for (int t = 1; t < k; ++t)
+      if (lam[t - 1] - lam[t] < sep) lam[t] = lam[t - 1] - sep;
+  }
+  __syncthreads();
 
   // 3. inverse iteration, three passes with cluster re-orthogonalisation
   const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
@@ -476,13 +538,14 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
       }
     }
     __syncthreads();
-    // modified Gram-Schmidt within clusters, by warp 0, in descending order of the eigenvalues
+    // modified Gram-Schmidt within clusters, by warp 0, in descending order of the eigenvalues (one warp and no
+    // block barrier: the pairs are a dependent chain, and barriers between them cost more than the warp's sums)
     if (tid < 32) {
       for (int t = 1; t < k; ++t) {
         double* yt = Y + (size_t)t * n;
         bool touched = false;
-        for (int s = t - 1; s >= 0 && lam[s] - lam[t] <= ortol; --s) {
-          const double* ys = Y + (size_t)s * n;
+        for (int s2 = t - 1; s2 >= 0 && lam[s2] - lam[t] <= ortol; --s2) {
+          const double* ys = Y + (size_t)s2 * n;
           double dp = 0.0;
           for (int i = tid; i < n; i += 32) dp += ys[i] * yt[i];
           dp = warp_sum(dp);
@@ -490,10 +553,10 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
           touched = true;
         }
         if (touched) {
-          double s2 = 0.0;
-          for (int i = tid; i < n; i += 32) s2 += yt[i] * yt[i];
-          s2 = warp_sum(s2);
-          const double sc = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+          double q2 = 0.0;
+          for (int i = tid; i < n; i += 32) q2 += yt[i] * yt[i];
+          q2 = warp_sum(q2);
+          const double sc = q2 > 0.0 ? 1.0 / sqrt(q2) : 0.0;
           for (int i = tid; i < n; i += 32) yt[i] *= sc;
         }
         __syncwarp();
@@ -503,7 +566,6 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   }
 
   // 4. back-transformation x = H_0 H_1 ... H_{n-3} y (one warp per vector; the reflectors are read-only)
-  const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
   for (int t = warp; t < k; t += nw) {
     double* yv = Y + (size_t)t * n;
     for (int j = n - 3; j >= 0; --j) {
@@ -588,21 +650,44 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_kernel(const double* __re
   }
 }
 
+
 static void syevx_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch,
                          const int* nA, const int* nB, const double* A2, const double* B) {
   if (n <= 0 || batch <= 0 || k <= 0) return;
   k = std::min(k, n);
-  const size_t head = sizeof(double) * (40 + 7 * (size_t)n + k);
-  const size_t full = head + sizeof(double) * (size_t)n * n;
-  const int use_smem = full <= (size_t)std::min(ctx->max_smem_optin, 200 * 1024) ? 1 : 0;
-  const size_t smem = use_smem ? full : head;
-  const size_t per = (size_t)n * n + (size_t)k * n + (size_t)k * 5 * n;
-  DBuf<double> scratch(ctx->pool, per * batch);
-  LRFG_CUDA(raise_smem_limit((const void*)syevx_kernel, smem));
+  LRFG_REQUIRE(k < 65536 && batch < 65536, "eigensolver grid too large (k = %d, batch = %d)", k, batch);
+  DBuf<double> scratch(ctx->pool, syevx_scratch_per(n, k) * batch);
+  const size_t lim = (size_t)std::min(ctx->max_smem_optin, 200 * 1024);
+  const size_t wbytes = sizeof(double) * (size_t)n * n;
+  // K1: the reflectors in shared memory when they fit
+  const size_t head1 = sizeof(double) * (40 + 6 * (size_t)n);
+  const int smem_w1 = head1 + wbytes <= lim ? 1 : 0;
+  const size_t smem1 = head1 + (smem_w1 ? wbytes : 0);
+  LRFG_CUDA(raise_smem_limit((const void*)syevx_tri_kernel, smem1));
   // algorithmic work at the active size, counted by each block on the device
   LRFG_LAUNCH(ctx, KC_EIGEN, 0.0, 0.0,
-              syevx_kernel<<<batch, kSyevxThreads, smem, ctx->stream>>>(A, n, k, w, V, n, scratch.get(), use_smem,
-                                                                         nA, nB, A2, B, work_counter(ctx, KC_EIGEN)));
+              syevx_tri_kernel<<<batch, kSyevxThreads, smem1, ctx->stream>>>(A, n, k, w, V, n, scratch.get(),
+                                                                             smem_w1, nA, nB, A2, B,
+                                                                             work_counter(ctx, KC_EIGEN)));
+  // K2: one warp per wanted eigenvalue of every item
+  const size_t smem2 = sizeof(double) * 3 * (size_t)n;
+  LRFG_CUDA(raise_smem_limit((const void*)syevx_bisect_kernel, smem2));
+  LRFG_LAUNCH(ctx, KC_EIGEN, 0.0, 0.0,
+              syevx_bisect_kernel<<<dim3((unsigned)k, (unsigned)batch), 32, smem2, ctx->stream>>>(n, k,
+                                                                                                scratch.get()));
+  // K3: the vectors, then their LU factors, then the reflectors in shared memory while they fit
+  size_t smem3 = sizeof(double) * (40 + 3 * (size_t)n + (size_t)k);
+  int flags3 = 0;
+  const size_t parts[3] = {sizeof(double) * (size_t)k * n, sizeof(double) * (size_t)k * 5 * n, wbytes};
+  for (int q = 0; q < 3; ++q)
+    if (smem3 + parts[q] <= lim) {
+      smem3 += parts[q];
+      flags3 |= 1 << q;
+    }
+  LRFG_CUDA(raise_smem_limit((const void*)syevx_vec_kernel, smem3));
+  LRFG_LAUNCH(ctx, KC_EIGEN, 0.0, 0.0,
+              syevx_vec_kernel<<<batch, kSyevxThreads, smem3, ctx->stream>>>(n, k, w, V, n, scratch.get(), flags3,
+                                                                             B));
 }
 
 void syevx(lrfg_ctx* ctx, const double* A, double* w, double* V, int n, int k, int batch) {
