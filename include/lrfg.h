@@ -132,10 +132,11 @@ typedef struct {
                            A.2.3); a grid coefficient is TT-compressed with the same tolerance */
   int coeff_rank;       /* LRFG_TT with grid values: rank cap r_A of the coefficient's TT-SVD (0: `rank`) */
   int rank_start;       /* low-rank formats: 0 = fixed rank.  > 0: rank-adapting MinRes (the solver Sec. 4.3
-                           proposes): truncations start at rank_start; when the residual fails to decrease
-                           below the cap `rank`, the rank rises by rank_step, the right-hand side is
-                           rebuilt and the iteration restarts from the best iterate; at the cap a failure
-                           to decrease ends it */
+                           proposes): truncations start at rank_start; when the residual fails to decrease,
+                           or meets tol, below the cap `rank`, the rank rises by rank_step, the right-hand
+                           side is rebuilt and the iteration restarts from the best iterate (tol is read as a
+                           statement about the cap's solution: below it the residual is truncated at the
+                           lower rank); at the cap a failure to decrease ends it */
   int rank_step;        /* rank increment of the rank-adapting MinRes (0 selects 1) */
   lrfg_disc disc;       /* LRFG_GANI (default), or LRFG_GA with LRFG_FULL / LRFG_FP64: the grid values of a
                            are read as a pixel-wise constant material (a_p on the cell of side 1/N centred at
@@ -350,11 +351,13 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* problem, const double* E, const lrfg
 
 /* Solve for nb macroscopic fields at once: E is a host array of nb x d doubles (row i = E_i), res receives nb
  * results (res[i].seconds is the wall time of the whole call).  For LRFG_TT problems with an isotropic GaNi
- * coefficient at a fixed rank (rank_tol = 0, rank_start = 0) and nb d <= 32, the minimal-residual iterations of
- * the nb right-hand sides run in lockstep: every operator application, truncation and inner product takes one
+ * coefficient without tolerance truncation (rank_tol = 0) and nb d <= 32, the minimal-residual iterations of the
+ * nb right-hand sides run in lockstep: every operator application, truncation and inner product takes one
  * launch sequence for all of them (each keeps its own step length, best iterate and stopping test; the results
- * equal separate solves up to the rounding order of the batched products).  Otherwise the nb solves run one
- * after the other.  Status as lrfg_problem_solve (LRFG_ENOCONV if any right-hand side reached maxit). */
+ * equal separate solves up to the rounding order of the batched products).  With rank adaptation the items share
+ * the current rank: an item that would raise it waits (frozen) until all unfinished items would, then all
+ * restart from their best iterates at the next rank, which leaves each item's sequence that of its own solve.
+ * Otherwise the nb solves run one after the other.  Status as lrfg_problem_solve (LRFG_ENOCONV if any right-hand side reached maxit). */
 lrfg_status lrfg_problem_solve_many(lrfg_problem* problem, int nb, const double* E, lrfg_result* res);
 /* The homogenised tensor A_eff (d x d, symmetric) of Eq. (homog): the diagonal A_aa from the solves with
  * E = e_a, each off-diagonal entry by polarisation of the quadratic form q(E) = A_eff E.E (Sec. 2.1),

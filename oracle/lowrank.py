@@ -628,7 +628,11 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
     the iteration restarts from the best iterate so far with its residual recomputed at the new rank
     (the comparison for "fails to decrease" starts again from there).  At the cap a failure to decrease
     ends the iteration, as in ``minres``; so do the relative tolerance and ``maxit`` (iterations summed
-    over all ranks).  Returns dict(u, iters, rel_resid, rank, history, Aeff) for the best iterate of the
+    over all ranks).  The tolerance is read as a statement about the solution at the cap: below it, a
+    residual within the tolerance raises the rank like a stagnation does (that residual is truncated at the
+    lower rank and understates the one the cap gives), again after a raise while it stays within it; at the
+    cap it ends the iteration only for an iterate of a step taken there (not for the restart point, which
+    has the lower rank).  Returns dict(u, iters, rel_resid, rank, history, Aeff) for the best iterate of the
     last rank."""
     f = op.f
     E = np.asarray(E, dtype=np.float64)
@@ -643,25 +647,31 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
         best = (np.inf, u, 0, True)
         hist = []
         it = 0
+        cap_steps = 0  # steps taken at the cap
         while True:
             nr = f.norm(r) / nb if nb > 0 else 0.0
             hist.append(nr)
-            if nr < best[0]:
+            improved = nr < best[0]
+            if improved:
                 best = (nr, u, it, u_zero)
-            elif rc < rmax:
-                # stagnation below the cap: raise the rank and restart from the best iterate
-                rc = min(rc + int(rank_step), rmax)
-                op.rank = rc
-                b = op.rhs(E)
-                nb = f.norm(b)
-                u, u_zero = best[1], best[3]
-                r = b if u_zero else op.T(f.add(b, f.scale(op.apply(u), -1.0)))
-                nr = f.norm(r) / nb if nb > 0 else 0.0
-                hist.append(nr)
-                best = (nr, u, best[2], u_zero)
-            else:
+            if rc < rmax and (not improved or nr <= tol):
+                # stagnation, or the tolerance met, below the cap: raise the rank and restart from the best
+                # iterate (again while the restarted residual is within the tolerance below the cap)
+                while True:
+                    rc = min(rc + int(rank_step), rmax)
+                    op.rank = rc
+                    b = op.rhs(E)
+                    nb = f.norm(b)
+                    u, u_zero = best[1], best[3]
+                    r = b if u_zero else op.T(f.add(b, f.scale(op.apply(u), -1.0)))
+                    nr = f.norm(r) / nb if nb > 0 else 0.0
+                    hist.append(nr)
+                    best = (nr, u, best[2], u_zero)
+                    if not (rc < rmax and nr <= tol):
+                        break
+            elif not improved:
                 break
-            if nr <= tol or it >= maxit:
+            if (nr <= tol and rc >= rmax and cap_steps > 0) or it >= maxit:
                 break
             q = op.apply(r)
             qq = np.real(f.dot(q, q))
@@ -671,6 +681,7 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
             u = op.T(f.scale(r, omega)) if u_zero else op.T(f.add(u, f.scale(r, omega)))
             u_zero = False
             it += 1
+            cap_steps += rc >= rmax
             r = op.T(f.add(b, f.scale(op.apply(u), -1.0)))
         nr, u, itb, _ = best
         return dict(u=u, iters=itb, rel_resid=nr, rank=rc, history=hist, Aeff=op.homogenised_coefficient(u, E))

@@ -956,34 +956,41 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
     r = std::move(rn);
   };
   int since_best = 0;  // iterations since the last new smallest residual (stop_on_increase > 1: the patience)
+  int cap_steps = 0;   // steps taken at the cap (the tolerance ends a rank-adapting solve only after one)
   while (nb > 0.0) {
     double nr = std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
     if (it == 0 && u_zero) nr = 1.0;  // r = b
-    if (nr < best) {
+    const bool improved = nr < best;
+    if (improved) {
       best = nr;
       best_it = it;
       best_zero = u_zero;
       since_best = 0;
       if (!u_zero) tt_copy(ctx, view_of(u), best_u);
-    } else if (adapt && rc < cap) {
-      rc = std::min(cap, rc + std::max(1, P->opts.rank_step));
-      TT nbv;
-      lr_rhs(P, E, nbv, rc);
-      b = std::move(nbv);
-      nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
-      u_zero = best_zero;
-      if (u_zero) {
-        tt_copy(ctx, view_of(b), r);
-      } else {
-        tt_copy(ctx, view_of(best_u), u);
-        residual();
-      }
-      nr = u_zero ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
-      best = nr;
-    } else if (adapt || (P->opts.stop_on_increase && ++since_best >= P->opts.stop_on_increase)) {
+    }
+    if (adapt && rc < cap && (!improved || nr <= P->opts.tol)) {
+      // stagnation, or the tolerance met, below the cap (the residual there is truncated at the lower rank):
+      // raise the rank and restart from the best iterate, again while the restarted residual is within it
+      do {
+        rc = std::min(cap, rc + std::max(1, P->opts.rank_step));
+        TT nbv;
+        lr_rhs(P, E, nbv, rc);
+        b = std::move(nbv);
+        nb = std::sqrt(std::max(tt_dot(ctx, view_of(b), view_of(b)), 0.0));
+        u_zero = best_zero;
+        if (u_zero) {
+          tt_copy(ctx, view_of(b), r);
+        } else {
+          tt_copy(ctx, view_of(best_u), u);
+          residual();
+        }
+        nr = u_zero ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
+        best = nr;
+      } while (rc < cap && nr <= P->opts.tol);
+    } else if (!improved && (adapt || (P->opts.stop_on_increase && ++since_best >= P->opts.stop_on_increase))) {
       break;
     }
-    if (nr <= P->opts.tol || it >= P->opts.maxit) break;
+    if ((nr <= P->opts.tol && (!adapt || (rc >= cap && cap_steps > 0))) || it >= P->opts.maxit) break;
     TT q;
     lr_apply(P, view_of(r), q, rc, P->opts.prec == LRFG_MIXED);  // (mixed: the search direction's operator)
     ++applies;
@@ -1004,6 +1011,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
     u = std::move(un);
     u_zero = false;
     ++it;
+    if (rc >= cap) ++cap_steps;
     residual();
   }
   if (best_zero || !best_u.d) {
@@ -1031,8 +1039,7 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
 
 // whether solve_tt_many can run the problem's options (isotropic GaNi TT at a fixed rank)
 bool lockstep_ok(const lrfg_problem* P) {
-  return P->opts.fmt == LRFG_TT && !P->ga && !P->aniso && P->opts.rank_start == 0 && P->opts.rank_tol == 0.0 &&
-         P->d >= 2;
+  return P->opts.fmt == LRFG_TT && !P->ga && !P->aniso && P->opts.rank_tol == 0.0 && P->d >= 2;
 }
 
 // The operator of lr_apply on nb items at once (items of identical ranks, stored item after item): the gradient,
@@ -1115,41 +1122,41 @@ void ttb_copy_item(lrfg_ctx* ctx, const TTBatch& src, TTBatch& dst, int b) {
 // item keeps its own step length, best iterate and stopping test; items that have stopped ride along until
 // the last one stops, their results frozen.  The results equal solve_tt's up to the rounding order of the
 // batched products.
+// Rank adaptation in lockstep (opts.rank_start > 0): the items share one current rank.  An item whose residual
+// fails to decrease, or meets the tolerance, below the cap is frozen (its best iterate kept, its later iterates
+// ignored, its iteration count not advanced); once every unfinished item is frozen the common rank rises by
+// rank_step (to the cap), the
+// right-hand sides are rebuilt at it and every unfinished item restarts from its best iterate with its residual
+// recomputed.  Each item thus follows the rank-adapting iteration of solve_tt, only waiting for the others before
+// a rise.  At the cap a failure to decrease ends the item, as there.
 void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
   lrfg_ctx* ctx = P->ctx;
-  const int d = P->d, rk = P->opts.rank;
-  // right-hand sides (item by item: once per solve), packed into one batch of rank-rk trains
-  std::vector<TT> bs(nb);
-  for (int i = 0; i < nb; ++i) lr_rhs(P, E + (size_t)i * d, bs[i], rk);
-  int rr[4] = {1, 1, 1, 1};
-  for (int j = 0; j <= d; ++j) rr[j] = bs[0].r[j];
-  for (int i = 1; i < nb; ++i)
-    for (int j = 0; j <= d; ++j) rr[j] = std::max(rr[j], bs[i].r[j]);
-  TTBatch b;
-  ttb_alloc(ctx, b, d, P->N, rr, nb);
-  for (int i = 0; i < nb; ++i) {
-    // right-hand sides of lower rank (e.g. E = 0) are embedded with zero blocks
-    TTBatchView one{};
-    one.d = d;
-    one.nb = 1;
-    for (int j = 0; j < 3; ++j) one.N[j] = P->N[j];
-    for (int j = 0; j <= d; ++j) one.r[j] = bs[i].r[j];
-    for (int j = 0; j < d; ++j) one.core[j] = bs[i].core[j].get();
-    TTBatch packed;
-    if (std::equal(one.r, one.r + d + 1, rr)) {
-      for (int j = 0; j < d; ++j)
-        LRFG_CUDA(cudaMemcpyAsync(b.core[j].get() + (size_t)i * b.elems(j), bs[i].core[j].get(),
-                                  sizeof(double) * b.elems(j), cudaMemcpyDeviceToDevice, ctx->stream));
-    } else {
+  const int d = P->d, cap = P->opts.rank;
+  const bool adapt = P->opts.rank_start > 0;
+  int rk = adapt ? std::min(P->opts.rank_start, cap) : cap;
+  // trains of possibly different ranks packed into one batch at the largest ranks (zero blocks elsewhere);
+  // null entries are zero trains
+  auto pack = [&](const std::vector<const TT*>& xs, TTBatch& out) {
+    int rr[4] = {1, 1, 1, 1};
+    for (const TT* x : xs)
+      if (x)
+        for (int j = 0; j <= d; ++j) rr[j] = std::max(rr[j], x->r[j]);
+    ttb_alloc(ctx, out, d, P->N, rr, nb);
+    for (int i = 0; i < nb; ++i) {
+      const TT* x = xs[i];
+      const bool same = x && std::equal(x->r, x->r + d + 1, rr);
       for (int j = 0; j < d; ++j) {
-        const int A = rr[j], B = rr[j + 1];
-        fill(ctx, b.core[j].get() + (size_t)i * b.elems(j), 0.0, (long long)b.elems(j));
-        tt_embed(ctx, bs[i].core[j].get(), one.r[j], P->N[j], one.r[j + 1], b.core[j].get() + (size_t)i * b.elems(j),
-                 A, B, 0, 0);
+        double* dst = out.core[j].get() + (size_t)i * out.elems(j);
+        if (same) {
+          LRFG_CUDA(cudaMemcpyAsync(dst, x->core[j].get(), sizeof(double) * out.elems(j), cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+          continue;
+        }
+        fill(ctx, dst, 0.0, (long long)out.elems(j));
+        if (x) tt_embed(ctx, x->core[j].get(), x->r[j], P->N[j], x->r[j + 1], dst, rr[j], rr[j + 1], 0, 0);
       }
     }
-  }
-  bs.clear();
+  };
   DBuf<double> dots(ctx->pool, (size_t)2 * nb);
   std::vector<double> h(2 * nb);
   auto host_dots = [&](const TTBatch& x, const TTBatch& y, const TTBatch* x2, const TTBatch* y2) {
@@ -1159,40 +1166,117 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
                               ctx->stream));
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   };
-  host_dots(b, b, nullptr, nullptr);
-  std::vector<double> nb2(nb), best(nb, INFINITY);
-  for (int i = 0; i < nb; ++i) nb2[i] = std::sqrt(std::max(h[i], 0.0));
-  std::vector<int> best_it(nb, 0), active(nb, 1), best_zero(nb, 1), since_best(nb, 0);
+  // right-hand sides at the current rank (item by item), packed, and their norms
+  TTBatch b;
+  std::vector<double> nb2(nb);
+  auto build_rhs = [&]() {
+    std::vector<TT> bs(nb);
+    std::vector<const TT*> ptr(nb);
+    for (int i = 0; i < nb; ++i) {
+      lr_rhs(P, E + (size_t)i * d, bs[i], rk);
+      ptr[i] = &bs[i];
+    }
+    pack(ptr, b);
+    host_dots(b, b, nullptr, nullptr);
+    for (int i = 0; i < nb; ++i) nb2[i] = std::sqrt(std::max(h[i], 0.0));
+  };
+  build_rhs();
+  std::vector<double> best(nb, INFINITY);
+  std::vector<int> best_it(nb, 0), active(nb, 1), best_zero(nb, 1), since_best(nb, 0), frozen(nb, 0), its(nb, 0);
+  std::vector<int> cap_steps(nb, 0);  // steps each item took at the cap
   std::vector<double> omega(nb);
   DBuf<double> om_dev(ctx->pool, (size_t)nb);
   TTBatch u, r;
   std::vector<TT> best_u(nb);  // each item's best iterate (its ranks may differ from the current ones)
   bool u_zero = true;
-  int it = 0, applies = 0;
+  int applies = 0;
   // r = b
-  ttb_alloc(ctx, r, d, P->N, rr, nb);
+  ttb_alloc(ctx, r, d, P->N, b.r, nb);
   for (int i = 0; i < nb; ++i) ttb_copy_item(ctx, b, r, i);
   auto any_active = [&]() { return std::any_of(active.begin(), active.end(), [](int a) { return a != 0; }); };
-  // nr: relative residuals of the current iterates (1 for u = 0)
+  // r <- T(b - C u) and the relative residuals
   std::vector<double> nr(nb, 1.0);
+  auto residual = [&]() {
+    TTBatch cu;
+    apply_batch(P, batch_view(u), cu, rk);
+    ++applies;
+    TTBatchView t[2] = {batch_view(b), batch_view(cu)};
+    const double hs[2] = {1.0, -1.0};
+    TTBatch diff;
+    ttb_add_many(ctx, t, 2, hs, nullptr, diff);
+    TTBatch rn;
+    tt_round_batch(ctx, batch_view(diff), rk, rn, 0.0);
+    r = std::move(rn);
+    host_dots(r, r, nullptr, nullptr);
+    for (int i = 0; i < nb; ++i) nr[i] = nb2[i] > 0.0 ? std::sqrt(std::max(h[i], 0.0)) / nb2[i] : 0.0;
+  };
   for (int i = 0; i < nb; ++i)
     if (nb2[i] == 0.0) { active[i] = 0; best[i] = 0.0; }
+  bool restarted = false;
   while (true) {
     for (int i = 0; i < nb; ++i) {
-      if (!active[i]) continue;
-      if (nr[i] < best[i]) {
+      if (!active[i] || frozen[i]) continue;
+      bool improved = false;
+      if (restarted) {
+        // the recomputed residual at the new rank is the new reference
         best[i] = nr[i];
-        best_it[i] = it;
+      } else if (nr[i] < best[i]) {
+        improved = true;
+        best[i] = nr[i];
+        best_it[i] = its[i];
         best_zero[i] = u_zero ? 1 : 0;
         since_best[i] = 0;
         if (!u_zero) tt_copy(ctx, item_view(u, i), best_u[i]);
-      } else if (P->opts.stop_on_increase && ++since_best[i] >= P->opts.stop_on_increase) {
+      } else if (!adapt && P->opts.stop_on_increase && ++since_best[i] >= P->opts.stop_on_increase) {
         active[i] = 0;
         continue;
       }
-      if (nr[i] <= P->opts.tol || it >= P->opts.maxit) active[i] = 0;
+      const bool failed = !restarted && !improved;
+      if (adapt && rk < cap && (failed || nr[i] <= P->opts.tol)) {
+        // stagnation, or the tolerance met, below the cap: wait for the next rise
+        frozen[i] = 1;
+        continue;
+      }
+      if (adapt && failed) {
+        active[i] = 0;  // at the cap a failure to decrease ends the item
+        continue;
+      }
+      if ((nr[i] <= P->opts.tol && (!adapt || cap_steps[i] > 0)) || its[i] >= P->opts.maxit) active[i] = 0;
     }
+    restarted = false;
     if (!any_active()) break;
+    bool all_frozen = true;
+    for (int i = 0; i < nb; ++i)
+      if (active[i] && !frozen[i]) all_frozen = false;
+    if (all_frozen) {
+      // raise the common rank; every unfinished item restarts from its best iterate
+      rk = std::min(cap, rk + std::max(1, P->opts.rank_step));
+      build_rhs();
+      std::vector<const TT*> ptr(nb, nullptr);
+      bool all_zero = true;
+      for (int i = 0; i < nb; ++i) {
+        frozen[i] = 0;
+        if (!best_zero[i] && best_u[i].d) {
+          ptr[i] = &best_u[i];
+          all_zero = false;
+        }
+      }
+      if (all_zero) {
+        u_zero = true;
+        u = TTBatch();
+        ttb_alloc(ctx, r, d, P->N, b.r, nb);
+        for (int i = 0; i < nb; ++i) ttb_copy_item(ctx, b, r, i);
+        std::fill(nr.begin(), nr.end(), 1.0);
+      } else {
+        u_zero = false;
+        pack(ptr, u);
+        residual();
+        for (int i = 0; i < nb; ++i)
+          if (!ptr[i]) nr[i] = 1.0;  // u = 0: r = b (up to the rounding of b at its own rank)
+      }
+      restarted = true;
+      continue;
+    }
     // q = C r; omega = (q, r) / (q, q)
     TTBatch q;
     apply_batch(P, batch_view(r), q, rk, P->opts.prec == LRFG_MIXED);
@@ -1215,20 +1299,12 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
     tt_round_batch(ctx, batch_view(sum), rk, un, 0.0);
     u = std::move(un);
     u_zero = false;
-    ++it;
-    // r <- T(b - C u)
-    TTBatch cu;
-    apply_batch(P, batch_view(u), cu, rk);
-    ++applies;
-    TTBatchView t[2] = {batch_view(b), batch_view(cu)};
-    const double hs[2] = {1.0, -1.0};
-    TTBatch diff;
-    ttb_add_many(ctx, t, 2, hs, nullptr, diff);
-    TTBatch rn;
-    tt_round_batch(ctx, batch_view(diff), rk, rn, 0.0);
-    r = std::move(rn);
-    host_dots(r, r, nullptr, nullptr);
-    for (int i = 0; i < nb; ++i) nr[i] = nb2[i] > 0.0 ? std::sqrt(std::max(h[i], 0.0)) / nb2[i] : 0.0;
+    for (int i = 0; i < nb; ++i)
+      if (active[i] && !frozen[i]) {
+        ++its[i];
+        if (rk >= cap) ++cap_steps[i];
+      }
+    residual();
   }
   for (int i = 0; i < nb; ++i) {
     lrfg_result& o = res[i];
@@ -1236,7 +1312,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
     o.iters = best_it[i];
     o.rel_resid = nb2[i] > 0.0 ? best[i] : 0.0;
     o.converged = o.rel_resid <= P->opts.tol ? 1 : 0;
-    o.applies = 2 * it;
+    o.applies = applies;
     if (best_zero[i] || !best_u[i].d) {
       TT z;
       int r1[4] = {1, 1, 1, 1};
@@ -1249,7 +1325,6 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
       for (int j = 0; j < 4; ++j) o.ranks[j] = j <= d ? best_u[i].r[j] : 1;
     }
   }
-  (void)applies;
 }
 
 }  // namespace

@@ -511,7 +511,8 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u,
 // u_{i+1} = T(u_i + omega_i r_i), r_i = T(b - C u_i) (r_0 = b), omega_i = (C r_i, r_i) / ||C r_i||^2; stop
 // when ||r|| fails to decrease (stop_on_increase), at tol or maxit; the iterate of smallest residual is kept.
 // Rank adaptation (rank_start > 0, the solver Sec. 4.3 proposes): truncations start at rank_start; when the
-// residual fails to decrease below the cap `rank`, the rank rises by rank_step, the right-hand side is
+// residual fails to decrease, or meets tol, below the cap `rank` (tol is a statement about the cap's solution;
+// the residual below it is truncated at the lower rank), the rank rises by rank_step, the right-hand side is
 // rebuilt and the iteration restarts from the best iterate with its residual recomputed at the new rank.
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
@@ -538,34 +539,40 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     r = std::move(rn);
   };
   int since_best = 0;  // iterations since the last new smallest residual (stop_on_increase > 1: the patience)
+  int cap_steps = 0;   // steps taken at the cap (the tolerance ends a rank-adapting solve only after one)
   while (nb > 0.0) {
     double nr = std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
     if (it == 0 && u_zero) nr = 1.0;  // r = b
-    if (nr < best) {
+    const bool improved = nr < best;
+    if (improved) {
       best = nr;
       best_it = it;
       best_zero = u_zero;
       since_best = 0;
       if (!u_zero) tk_copy(ctx, tk_view(u), best_u);
-    } else if (adapt && rc < rank) {
-      rc = std::min(rank, rc + std::max(1, rank_step));
-      TK nbv;
-      tk_rhs(ctx, a, E, pt, pw, rc, nbv, rtol);
-      b = std::move(nbv);
-      nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
-      u_zero = best_zero;
-      if (u_zero) {
-        tk_copy(ctx, tk_view(b), r);
-      } else {
-        tk_copy(ctx, tk_view(best_u), u);
-        residual();
-      }
-      nr = u_zero ? 1.0 : std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
-      best = nr;
-    } else if (adapt || (stop_on_increase && ++since_best >= stop_on_increase)) {
+    }
+    if (adapt && rc < rank && (!improved || nr <= tol)) {
+      // stagnation, or the tolerance met, below the cap: raise the rank, restart from the best iterate
+      do {
+        rc = std::min(rank, rc + std::max(1, rank_step));
+        TK nbv;
+        tk_rhs(ctx, a, E, pt, pw, rc, nbv, rtol);
+        b = std::move(nbv);
+        nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
+        u_zero = best_zero;
+        if (u_zero) {
+          tk_copy(ctx, tk_view(b), r);
+        } else {
+          tk_copy(ctx, tk_view(best_u), u);
+          residual();
+        }
+        nr = u_zero ? 1.0 : std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
+        best = nr;
+      } while (rc < rank && nr <= tol);
+    } else if (!improved && (adapt || (stop_on_increase && ++since_best >= stop_on_increase))) {
       break;
     }
-    if (nr <= tol || it >= maxit) break;
+    if ((nr <= tol && (!adapt || (rc >= rank && cap_steps > 0))) || it >= maxit) break;
     TK q;
     tk_apply(ctx, a, tk_view(r), pt, pw, rc, q, rtol, B);
     ++applies;
@@ -588,6 +595,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     u = std::move(un);
     u_zero = false;
     ++it;
+    if (rc >= rank) ++cap_steps;
     residual();
   }
   if (best_zero || !best_u.d) {

@@ -83,3 +83,48 @@ def test_tt_homogenised_tensor_in_lockstep(ctx):
     assert abs(T[0, 1] - 0.5 * (s01 - q[0] - q[1])) <= 1e-6 * q[0]
     assert np.array_equal(T, T.T)
     P.free()
+
+
+# rank adaptation in lockstep: each item follows the rank-adapting iteration of its own solve (frozen while
+# others still improve at the current rank, restarted from its best iterate at every rise).  Batched and single
+# launches round differently, and a rise is decided by "the residual fails to decrease", which can be a near-tie
+# (rises below 1 % occur here): the counts may differ by a step or two, A_eff (deep below the tolerance) may not.
+@pytest.mark.parametrize("d,N,rank,start,step,over", [(2, 31, 8, 2, 2, 0), (3, 21, 8, 2, 3, 0), (3, 21, 8, 2, 3, 4)])
+def test_rank_adaptive_lockstep_equals_separate_solves(ctx, d, N, rank, start, step, over):
+    # the axis fields of the symmetric cube: items of like behaviour, which is where lockstep pays (unlike items
+    # wait for one another at each rise); and one E = 0
+    a = _coeff(d, N, "cube")
+    Es = np.eye(d).tolist() + [[0.0] * d]
+    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-12, maxit=50,
+                    rank_start=start, rank_step=step, sketch_over=over)
+    n0 = ctx.launch_count()
+    many = P.solve_many(Es)
+    n_many = ctx.launch_count() - n0
+    n0 = ctx.launch_count()
+    alone = [P.solve(E, want_field=False)[0] for E in Es]
+    n_alone = ctx.launch_count() - n0
+    for m, s, E in zip(many, alone, Es):
+        if not any(E):
+            assert m.Aeff == 0.0 and s.Aeff == 0.0
+            continue
+        assert abs(m.Aeff - s.Aeff) <= 1e-7 * s.Aeff, (E, m.Aeff, s.Aeff, m.iters, s.iters)
+        assert abs(m.iters - s.iters) <= 2 and m.ranks == s.ranks, (E, m.iters, s.iters, m.ranks, s.ranks)
+    # fewer launches than the separate solves (by less than at a fixed rank: the items wait for one another at
+    # each rise, and without the sketch the P~^-1 truncation runs item by item)
+    assert n_many < n_alone, (n_many, n_alone)
+    P.free()
+
+
+@pytest.mark.parametrize("d,N,rank,start,step", [(2, 31, 8, 2, 2), (3, 21, 8, 2, 3)])
+def test_rank_adaptive_lockstep_matches_oracle(ctx, d, N, rank, start, step):
+    a = _coeff(d, N, "cube")
+    Es = [np.eye(d)[0], np.eye(d)[1]]
+    op = lr.LowRankGaNi(a, (N,) * d, fmt="tt", rank=rank, pinv_eps=0.1)
+    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-12, maxit=50,
+                    rank_start=start, rank_step=step)
+    many = P.solve_many([list(E) for E in Es])
+    for m, E in zip(many, Es):
+        ref = lr.minres_rank_adaptive(op, E, start, step, tol=1e-12, maxit=50)
+        assert abs(m.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (E, m.Aeff, ref["Aeff"], m.iters, ref["iters"])
+        assert list(m.ranks[:d + 1]) == lr.tt_ranks(ref["u"])
+    P.free()

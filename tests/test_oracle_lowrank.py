@@ -224,6 +224,14 @@ def test_rank_adaptive_minres_pins():
     ad = lr.minres_rank_adaptive(op, E, rank_start=2, rank_step=2, tol=1e-12, maxit=60)
     assert ad["rank"] > 2 and ad["rel_resid"] < 0.5 * fixed2["rel_resid"]
     assert op.rank == 8  # restored
+    # a tolerance met below the cap raises the rank: the result is the cap's, within the tolerance there
+    loose = lr.minres_rank_adaptive(op, E, rank_start=2, rank_step=2, tol=2e-2, maxit=60)
+    fixed2_loose = lr.minres(op2, E, tol=2e-2, maxit=60)
+    assert fixed2_loose["rel_resid"] <= 2e-2  # the tolerance is reachable at rank 2 alone
+    assert loose["rank"] == 8 and loose["rel_resid"] <= 2e-2
+    assert lr.tt_ranks(loose["u"])[1] > 2
+    # and it stops there only for an iterate of a step at the cap: more iterations than the rises alone take
+    assert loose["iters"] > fixed2_loose["iters"]
     Ns = 15
     As, ts, ws = square_inclusion(2, Ns)
     full = fg.solve_gani(As, E, tol=1e-13, maxit=3000)
