@@ -6,13 +6,13 @@ seed 19020745), E = (1, 0, 0).  The coefficient is compressed on the GPU to TT r
 the coefficient rank the paper uses for its stochastic material) and the full-format solver gets the
 expansion of that TT coefficient, so both solve the same problem.
 
-One step = one complete TT solve from u = 0 at the metric's accuracy: the minimal-residual iteration with
-truncation to rank 20 (the material and P~^-1 products truncated by the randomised rounding, every other
-truncation deterministic), stopped when the relative residual reaches 3e-4 (A_eff's error is quadratic in
-the field's, 4-6 x the squared residual here, so this reaches A_eff within 1e-6; no stop on a rise of the
-residual, which near this level rises and falls again), then A_eff: every
-hot-path stage — mode-wise gradient FFTs, material products, truncations, divergence sums, exponential-sum
-preconditioner, TT inner products, A_eff.  value = TT solves per second over the timed steps (whole job:
+One step = one complete TT solve from u = 0 at the metric's accuracy: the rank-adapting minimal-residual
+iteration Sec. 4.3 proposes (truncation rank 10, raised by 5 up to the cap 20 whenever the residual stagnates,
+restarting from the best iterate; the material and P~^-1 products truncated by the randomised rounding, every
+other truncation deterministic), stopped when the relative residual reaches 3e-4 at the cap (A_eff's error is
+quadratic in the field's, about 6 x the squared residual for E = e_1 here, so this reaches A_eff within 1e-6),
+then A_eff: every hot-path stage — mode-wise gradient FFTs, material products, truncations, divergence sums,
+exponential-sum preconditioner, TT inner products, A_eff.  value = TT solves per second over the timed steps (whole job:
 summed over ranks under torchrun, timed by the slowest rank), uninstrumented; one extra profiled solve gives
 the kernel classes and the roofline.  The full-format FP64 PCG solve (tol 1e-8) of the same problem is timed
 beside it (p50/p99) and gives the A_eff reference; so is the LRFG_MIXED full solve.
@@ -51,7 +51,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--N", type=int, default=243)
-    p.add_argument("--rank", type=int, default=20)
+    p.add_argument("--rank", type=int, default=20, help="the rank cap of the TT solve")
+    p.add_argument("--rank-start", type=int, default=10,
+                   help="rank-adapting MinRes (Sec. 4.3): start rank (0: the fixed rank --rank throughout)")
+    p.add_argument("--rank-step", type=int, default=5, help="rank increase when the residual stagnates")
     p.add_argument("--coeff-rank", type=int, default=10)
     p.add_argument("--pinv-eps", type=float, default=0.1)
     p.add_argument("--maxit", type=int, default=80)
@@ -59,6 +62,9 @@ def parse():
                    help="oversampling of the randomised rounding of the products (0: deterministic rounding)")
     p.add_argument("--tt-tol", type=float, default=3e-4,
                    help="relative residual at which the TT solve stops (A_eff error ~ 4-6 x its square)")
+    p.add_argument("--tensor-tol", type=float, default=2e-4,
+                   help="relative residual of the six solves of the homogenised tensor (the ratio of A_eff's error "
+                        "to the squared residual depends on E: about 6 for E = e_1, up to about 18 for e_2 here)")
     p.add_argument("--stop-on-increase", type=int, default=0,
                    help="also stop after this many iterations without a new smallest residual (1: the paper's rule, "
                         "Sec. 4.3; 0: off)")
@@ -111,10 +117,13 @@ def workload_config(args):
     fmt = "Tucker" if args.format == "tucker" else "TT"
     rnd = (f"randomised rounding of the products (oversampling {args.sketch_over})" if args.sketch_over > 0
            else "deterministic rounding")
+    sched = (f"rank-adapting MinRes, rank {args.rank_start} -> {args.rank} in steps of {args.rank_step}"
+             if args.rank_start > 0 else f"rank {args.rank} MinRes")
     return {"workload": f"d=3 N={args.N}^3 lognormal SE-GRF (l=0.2, var=1, seed {SEED}), E=(1,0,0); "
-                        f"{fmt} rank {args.rank} MinRes ({rnd}, stop at relative residual {args.tt_tol:g}) "
+                        f"{fmt} {sched} ({rnd}, stop at relative residual {args.tt_tol:g}) "
                         f"vs full FP64 PCG (tol 1e-8)",
             "d": 3, "N": args.N, "coeff_tt_rank": args.coeff_rank, "format": args.format, "tt_rank": args.rank,
+            "rank_start": args.rank_start, "rank_step": args.rank_step,
             "sketch_over": args.sketch_over, "tt_tol": args.tt_tol, "stop_on_increase": args.stop_on_increase,
             "pinv_eps": args.pinv_eps, "precision": "fp64", "l2": "flushed between steps (512 MiB write)"}
 
@@ -240,15 +249,30 @@ def roofline(stats, fp64_peak=None):
 GOLDEN = os.path.join(ROOT, "tests", "golden", "lognormal_243.json")
 
 
-def oracle_apply_seconds(args, n_applies):
-    """Time oracle applications of the truncated TT operator (Eq. (Pls_lowrank)) of the workload, with the
-    randomised rounding of the products when the workload uses it, starting from the right-hand side."""
+_ORACLE_CACHE = {}
+
+
+def _oracle_operator(args, rank):
+    """The oracle's truncated operator of the workload at truncation rank `rank` and its right-hand side (the
+    coefficient compressed once by the oracle's TT-SVD, one operator per rank, kept for later samples)."""
     from oracle import lowrank as lr
-    A = make_coefficient(args.N)
-    a_tt = lr.tt_svd(A, rmax=args.coeff_rank)
-    sketch = (args.sketch_over, 0) if args.sketch_over > 0 else None
-    op = lr.LowRankGaNi(a_tt, (args.N,) * 3, fmt="tt", rank=args.rank, pinv_eps=args.pinv_eps, sketch=sketch)
-    x = op.rhs(np.array([1.0, 0.0, 0.0]))
+    key = ("coeff", args.N, args.coeff_rank)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = lr.tt_svd(make_coefficient(args.N), rmax=args.coeff_rank)
+    okey = ("op", args.N, args.coeff_rank, rank, args.sketch_over, args.pinv_eps)
+    if okey not in _ORACLE_CACHE:
+        sketch = (args.sketch_over, 0) if args.sketch_over > 0 else None
+        op = lr.LowRankGaNi(_ORACLE_CACHE[key], (args.N,) * 3, fmt="tt", rank=rank, pinv_eps=args.pinv_eps,
+                            sketch=sketch)
+        _ORACLE_CACHE[okey] = (op, op.rhs(np.array([1.0, 0.0, 0.0])))
+    return _ORACLE_CACHE[okey]
+
+
+def oracle_apply_seconds(args, n_applies, rank=None):
+    """Time oracle applications of the truncated TT operator (Eq. (Pls_lowrank)) of the workload at truncation
+    rank `rank` (default the cap), with the randomised rounding of the products when the workload uses it,
+    starting from the right-hand side."""
+    op, x = _oracle_operator(args, rank or args.rank)
     times = []
     for _ in range(n_applies):
         t0 = time.perf_counter()
@@ -268,8 +292,21 @@ def oracle_applies_per_solve(args):
     o = g["opts"]
     same = (args.N == 243 and args.coeff_rank == 10 and o["rank"] == args.rank and o["sketch_over"] == args.sketch_over
             and o["tol"] == args.tt_tol and o["pinv_eps"] == args.pinv_eps and o["maxit"] == args.maxit
-            and int(o["stop_on_increase"]) == int(args.stop_on_increase))
+            and int(o["stop_on_increase"]) == int(args.stop_on_increase)
+            and int(o.get("rank_start", 0)) == args.rank_start and int(o.get("rank_step", 0)) == args.rank_step)
     return (g["applies"], g) if same else None
+
+
+def oracle_solve_seconds(args, g, per_rank):
+    """Seconds of one oracle solve of the workload: per_rank oracle applications timed at each truncation rank
+    the stored solve used, times its applications at that rank (the median of each rank's sample)."""
+    by_rank = g.get("applies_by_rank") or {str(args.rank): g["applies"]}
+    total, parts = 0.0, []
+    for r, n in sorted(by_rank.items(), key=lambda kv: int(kv[0])):
+        t = statistics.median(oracle_apply_seconds(args, per_rank, rank=int(r)))
+        total += n * t
+        parts.append(f"{n} at rank {r} ({t:.2f} s each)")
+    return total, parts
 
 
 def cpu_cores():
@@ -366,7 +403,8 @@ def run_ours(args):
     # stopped at the residual tolerance
     lr_fmt = lrfg.TUCKER if args.format == "tucker" else lrfg.TT
     Ptt = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
-                      stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over)
+                      stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over,
+                      rank_start=args.rank_start, rank_step=args.rank_step)
     for _ in range(args.warmup):
         Ptt.solve(E, want_field=False)
     if world > 1:
@@ -393,7 +431,8 @@ def run_ours(args):
 
     # the same TT solve with LRFG_MIXED (FP32 fibre transforms and sketch side in the steps, FP64 residual)
     Pmx = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
-                      stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=lrfg.MIXED)
+                      stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=lrfg.MIXED,
+                      rank_start=args.rank_start, rank_step=args.rank_step)
     Pmx.solve(E, want_field=False)
     mx_ms, mx_res = timed_solves(Pmx, E, 2, stream, flush)
     tt_mixed = {"solves_per_s": 1e3 / statistics.median(mx_ms), "p50_ms": pct(mx_ms, 50), "p99_ms": pct(mx_ms, 99),
@@ -402,14 +441,17 @@ def run_ours(args):
     # the homogenised tensor (Eq. (homog)): the d (d + 1) / 2 = 6 solves of the polarisation fields, TT in
     # lockstep (lrfg_problem_solve_many: one launch sequence for all six) against six full FP64 solves
     Es6 = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 1.0]]
-    Ptt.solve_many(Es6)
+    P6 = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tensor_tol, maxit=args.maxit,
+                     stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over,
+                     rank_start=args.rank_start, rank_step=args.rank_step)
+    P6.solve_many(Es6)
     tensor_ms, tensor_tt = [], None
     for _ in range(2):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        tensor_tt = Ptt.solve_many(Es6)
+        tensor_tt = P6.solve_many(Es6)
         e1.record(stream)
         e1.synchronize()
         tensor_ms.append(e0.elapsed_time(e1))
@@ -418,22 +460,29 @@ def run_ours(args):
         ms1, r1 = timed_solves(Pfull, E6, 1, stream, flush)
         full6_ms += ms1[0]
         full6.append(r1[0])
-    tensor = {"tt_lockstep": {"solves_per_s": 6e3 / min(tensor_ms), "seconds": min(tensor_ms) / 1e3,
+    tensor = {"tol": args.tensor_tol,
+              "tt_lockstep": {"solves_per_s": 6e3 / min(tensor_ms), "seconds": min(tensor_ms) / 1e3,
                               "iters": [r.iters for r in tensor_tt]},
               "full_fp64": {"solves_per_s": 6e3 / full6_ms, "seconds": full6_ms / 1e3},
               "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(tensor_tt, full6))}
     tensor["tt_vs_full_fp64"] = tensor["tt_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
-    Pmx.solve_many(Es6)
+    P6.free()
+    Pmx6 = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tensor_tol, maxit=args.maxit,
+                       stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=lrfg.MIXED,
+                       rank_start=args.rank_start, rank_step=args.rank_step)
+    Pmx6.solve_many(Es6)
     flush.fill_(1.0)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    mx6 = Pmx.solve_many(Es6)
+    mx6 = Pmx6.solve_many(Es6)
     e1.record(stream)
     e1.synchronize()
     tensor["tt_mixed_lockstep"] = {"solves_per_s": 6e3 / e0.elapsed_time(e1),
                                    "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(mx6, full6))}
     tensor["tt_mixed_vs_full_fp64"] = tensor["tt_mixed_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
+    tensor["meets_1e-6"] = max(tensor["max_rel_err_vs_full"], tensor["tt_mixed_lockstep"]["max_rel_err_vs_full"]) <= 1e-6
+    Pmx6.free()
     Pmx.free()
 
     # the configuration of the previous measurements: TT rank 10, deterministic rounding, stop on increase
@@ -526,6 +575,7 @@ def solve_host(ctx, host_cores, args, E):
     o.prec, o.rank, o.pinv_eps = L.LRFG_FP64, args.rank, args.pinv_eps
     o.tol, o.maxit, o.stop_on_increase = args.tt_tol, args.maxit, args.stop_on_increase
     o.sketch_over, o.sketch_seed = args.sketch_over, 0
+    o.rank_start, o.rank_step = args.rank_start, args.rank_step
     res = L.lrfg_result()
     Ed = (C.c_double * 3)(*E)
     st = ctx.lib.lrfg_solve(ctx.h, C.byref(c), Ed, C.byref(o), C.byref(res), None)
@@ -538,16 +588,22 @@ def add_cpu_baseline(line, args):
     # a bounded sample: oracle applications of the same truncated operator (about 10-30 s of CPU work), scaled
     # to solves/s by the applications per solve of the oracle's own complete solve of this workload (stored),
     # or else by the GPU run's count of the same algorithm
+    stored = oracle_applies_per_solve(args)
+    if stored:
+        sec, parts = oracle_solve_seconds(args, stored[1], 3)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"3 oracle applications of the TT operator at N={args.N}^3 at each truncation "
+                                          f"rank of the oracle's own complete solve of this workload (tests/golden), "
+                                          f"weighted by its applications there: " + ", ".join(parts)}
+        return
     t = oracle_apply_seconds(args, 8)
     per_apply = statistics.median(t)
-    stored = oracle_applies_per_solve(args)
-    n_app, src = (stored[0], "the oracle's own complete solve of this workload (tests/golden)") if stored else \
-        (line["tt_applies_per_solve"], "the GPU run's solves (same algorithm)")
+    n_app = line["tt_applies_per_solve"]
     line["cpu_baseline"] = {"value": 1.0 / (per_apply * n_app), "unit": "solves/s", "cores": cpu_cores(),
                             "kind": "oracle",
                             "sample": f"{len(t)} oracle applications of the rank-{args.rank} TT operator at N={args.N}^3 "
                                       f"({per_apply:.2f} s each, median), times {n_app} applications per solve from "
-                                      f"{src}"}
+                                      f"the GPU run's solves (same algorithm)"}
 
 
 # -------------------------------------------------------------------------------------------------
@@ -557,15 +613,21 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    # each step: one oracle application of the workload's operator; the value scales the median step by the
-    # applications per solve of the oracle's own complete solve of this workload (stored in tests/golden)
+    # each step: one oracle application of the workload's operator at every truncation rank of the oracle's own
+    # complete solve of this workload (stored in tests/golden), weighted by its applications at that rank: the
+    # seconds of one oracle solve; the value is the inverse of the median step
     stored = oracle_applies_per_solve(args)
     if stored is None:
         return {"impl": "reference", "unavailable": "no stored oracle solve of this configuration (run "
                                                    "tests/golden/make_golden.py for it)"}
     n_app, g = stored
-    times = oracle_apply_seconds(args, args.warmup + args.steps)[args.warmup:]
-    value = 1.0 / (statistics.median(times) * n_app)
+    by_rank = g.get("applies_by_rank") or {str(args.rank): n_app}
+    times = []
+    for step in range(args.warmup + args.steps):
+        sec = sum(n * oracle_apply_seconds(args, 1, rank=int(r))[0] for r, n in by_rank.items())
+        if step >= args.warmup:
+            times.append(sec)
+    value = 1.0 / statistics.median(times)
     cores = cpu_cores()
     return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
@@ -573,9 +635,10 @@ def run_reference(args):
             "config": workload_config(args),
             "oracle_solve": {"applies": n_app, "iters": g["iters"], "aeff": g["Aeff"]},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step one oracle application of the rank-{args.rank} TT operator at "
-                                       f"N={args.N}^3; median times {n_app} applications per solve (the oracle's own "
-                                       f"complete solve of this workload, tests/golden)"},
+                             "sample": f"each step one oracle application of the TT operator at N={args.N}^3 at each "
+                                       f"truncation rank of the oracle's own complete solve of this workload "
+                                       f"(tests/golden), times its {n_app} applications split by rank "
+                                       f"{dict(sorted(by_rank.items(), key=lambda kv: int(kv[0])))}"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -894,7 +957,8 @@ def run_case(args):
     a_tt = ctx.tt_compress(A, args.coeff_rank)
     if args.case == "tt_solve":
         P = ctx.problem(a_tt, lrfg.TT, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
-                        stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over)
+                        stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over,
+                        rank_start=args.rank_start, rank_step=args.rank_step)
         r, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
         print(json.dumps({"case": args.case, "N": args.N, "iters": r.iters, "aeff": r.Aeff, "ok": True}))
         P.free()

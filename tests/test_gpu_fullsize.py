@@ -63,15 +63,17 @@ def test_full_mixed_pcg_at_243(ctx, problem_setup):
 
 
 def test_tt_sketched_solve_at_243(ctx, problem_setup):
-    """The benchmark's TT solve (rank 20, randomised rounding of the material and P~^-1 products, stopped at the
-    stored residual tolerance): A_eff within the FP64-path target 1e-6 of the oracle's full solve, within 2e-6 of
-    the oracle's own solve with the same options (two approximations each within 1e-6 of the full value; the two
-    iterations part ways at the rounding level, so their stopping points differ), never below the full value."""
+    """The benchmark's TT solve (rank-adapting to the cap 20, randomised rounding of the material and P~^-1
+    products, stopped at the stored residual tolerance): A_eff within the FP64-path target 1e-6 of the oracle's
+    full solve, within 2e-6 of the oracle's own solve with the same options (two approximations each within 1e-6
+    of the full value; the two iterations part ways at the rounding level, so their stopping points differ),
+    never below the full value."""
     gold, a_tt, _ = problem_setup
     g = gold["tt_sketch"]["20"]
     o = g["opts"]
     P = ctx.problem(a_tt, lrfg.TT, rank=o["rank"], pinv_eps=o["pinv_eps"], tol=o["tol"], maxit=o["maxit"],
-                    stop_on_increase=o["stop_on_increase"], sketch_over=o["sketch_over"], sketch_seed=o["sketch_seed"])
+                    stop_on_increase=o["stop_on_increase"], sketch_over=o["sketch_over"], sketch_seed=o["sketch_seed"],
+                    rank_start=o.get("rank_start", 0), rank_step=o.get("rank_step", 0))
     res, _ = P.solve([1.0, 0.0, 0.0], want_field=False)
     full = gold["full"]["Aeff"]
     assert abs(res.Aeff - full) <= 1e-6 * full, (res.Aeff, full, res.iters, res.rel_resid)
