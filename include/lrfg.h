@@ -136,7 +136,7 @@ typedef struct {
                            or meets tol, below the cap `rank`, the rank rises by rank_step, the right-hand
                            side is rebuilt and the iteration restarts from the best iterate (tol is read as a
                            statement about the cap's solution: below it the residual is truncated at the
-                           lower rank); at the cap a failure to decrease ends it */
+                           lower rank); at the cap it stops as the fixed-rank iteration, by stop_on_increase */
   int rank_step;        /* rank increment of the rank-adapting MinRes (0 selects 1) */
   lrfg_disc disc;       /* LRFG_GANI (default), or LRFG_GA with LRFG_FULL / LRFG_FP64: the grid values of a
                            are read as a pixel-wise constant material (a_p on the cell of side 1/N centred at

@@ -620,15 +620,16 @@ def minres(op: LowRankGaNi, E, tol=1e-10, maxit=200, stop_on_increase=True, call
     return dict(u=u, iters=itb, rel_resid=nr, history=hist, Aeff=op.homogenised_coefficient(u, E))
 
 
-def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, maxit=200):
+def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, maxit=200, stop_on_increase=True):
     """Rank-adapting minimal-residual iteration (the solver Sec. 4.3 proposes: start with a low solution
     rank and raise it during the iterations).  Reading: the iteration of ``minres`` runs with every T at
     the current rank r_c = rank_start; when the residual norm fails to decrease and r_c < op.rank (the
     cap), r_c rises by rank_step (at most to the cap), the right-hand side is rebuilt at the new rank, and
     the iteration restarts from the best iterate so far with its residual recomputed at the new rank
-    (the comparison for "fails to decrease" starts again from there).  At the cap a failure to decrease
-    ends the iteration, as in ``minres``; so do the relative tolerance and ``maxit`` (iterations summed
-    over all ranks).  The tolerance is read as a statement about the solution at the cap: below it, a
+    (the comparison for "fails to decrease" starts again from there).  At the cap it is the fixed-rank
+    iteration and stops as ``minres`` does: a failure to decrease ends it (``stop_on_increase`` = True),
+    or k consecutive iterations without a new smallest residual (an int k > 1), or never (False / 0); so do
+    the relative tolerance and ``maxit`` (iterations summed over all ranks).  The tolerance is read as a statement about the solution at the cap: below it, a
     residual within the tolerance raises the rank like a stagnation does (that residual is truncated at the
     lower rank and understates the one the cap gives), again after a raise while it stays within it; at the
     cap it ends the iteration only for an iterate of a step taken there (not for the restart point, which
@@ -648,12 +649,15 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
         hist = []
         it = 0
         cap_steps = 0  # steps taken at the cap
+        patience = int(stop_on_increase)
+        since_best = 0  # iterations at the cap since the last new smallest residual
         while True:
             nr = f.norm(r) / nb if nb > 0 else 0.0
             hist.append(nr)
             improved = nr < best[0]
             if improved:
                 best = (nr, u, it, u_zero)
+                since_best = 0
             if rc < rmax and (not improved or nr <= tol):
                 # stagnation, or the tolerance met, below the cap: raise the rank and restart from the best
                 # iterate (again while the restarted residual is within the tolerance below the cap)
@@ -667,10 +671,13 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
                     nr = f.norm(r) / nb if nb > 0 else 0.0
                     hist.append(nr)
                     best = (nr, u, best[2], u_zero)
+                    since_best = 0
                     if not (rc < rmax and nr <= tol):
                         break
-            elif not improved:
-                break
+            elif not improved and patience:
+                since_best += 1
+                if since_best >= patience:
+                    break
             if (nr <= tol and rc >= rmax and cap_steps > 0) or it >= maxit:
                 break
             q = op.apply(r)

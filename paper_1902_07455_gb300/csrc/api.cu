@@ -986,9 +986,10 @@ void solve_tt(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field** u
         }
         nr = u_zero ? 1.0 : std::sqrt(std::max(tt_dot(ctx, view_of(r), view_of(r)), 0.0)) / nb;
         best = nr;
+        since_best = 0;
       } while (rc < cap && nr <= P->opts.tol);
-    } else if (!improved && (adapt || (P->opts.stop_on_increase && ++since_best >= P->opts.stop_on_increase))) {
-      break;
+    } else if (!improved && P->opts.stop_on_increase && ++since_best >= P->opts.stop_on_increase) {
+      break;  // (at the cap the rank-adapting iteration stops as the fixed-rank one)
     }
     if ((nr <= P->opts.tol && (!adapt || (rc >= cap && cap_steps > 0))) || it >= P->opts.maxit) break;
     TT q;
@@ -1227,9 +1228,6 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
         best_zero[i] = u_zero ? 1 : 0;
         since_best[i] = 0;
         if (!u_zero) tt_copy(ctx, item_view(u, i), best_u[i]);
-      } else if (!adapt && P->opts.stop_on_increase && ++since_best[i] >= P->opts.stop_on_increase) {
-        active[i] = 0;
-        continue;
       }
       const bool failed = !restarted && !improved;
       if (adapt && rk < cap && (failed || nr[i] <= P->opts.tol)) {
@@ -1237,8 +1235,9 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
         frozen[i] = 1;
         continue;
       }
-      if (adapt && failed) {
-        active[i] = 0;  // at the cap a failure to decrease ends the item
+      // at the cap (or at a fixed rank) the stop rule on a rise of the residual
+      if (failed && P->opts.stop_on_increase && ++since_best[i] >= P->opts.stop_on_increase) {
+        active[i] = 0;
         continue;
       }
       if ((nr[i] <= P->opts.tol && (!adapt || cap_steps[i] > 0)) || its[i] >= P->opts.maxit) active[i] = 0;
@@ -1256,6 +1255,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
       bool all_zero = true;
       for (int i = 0; i < nb; ++i) {
         frozen[i] = 0;
+        since_best[i] = 0;
         if (!best_zero[i] && best_u[i].d) {
           ptr[i] = &best_u[i];
           all_zero = false;

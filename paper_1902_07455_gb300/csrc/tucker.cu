@@ -568,9 +568,10 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
         }
         nr = u_zero ? 1.0 : std::sqrt(std::max(tk_dot(ctx, tk_view(r), tk_view(r)), 0.0)) / nb;
         best = nr;
+        since_best = 0;
       } while (rc < rank && nr <= tol);
-    } else if (!improved && (adapt || (stop_on_increase && ++since_best >= stop_on_increase))) {
-      break;
+    } else if (!improved && stop_on_increase && ++since_best >= stop_on_increase) {
+      break;  // (at the cap the rank-adapting iteration stops as the fixed-rank one)
     }
     if ((nr <= tol && (!adapt || (rc >= rank && cap_steps > 0))) || it >= maxit) break;
     TK q;

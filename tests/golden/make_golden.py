@@ -76,7 +76,8 @@ def main():
         return plain_apply(v)
     op.apply = counted
     t0 = time.time()
-    res = lr.minres_rank_adaptive(op, E, opts["rank_start"], opts["rank_step"], tol=opts["tol"], maxit=opts["maxit"])
+    res = lr.minres_rank_adaptive(op, E, opts["rank_start"], opts["rank_step"], tol=opts["tol"], maxit=opts["maxit"],
+                                  stop_on_increase=opts["stop_on_increase"])
     out["tt_sketch"] = {"20": {"Aeff": res["Aeff"], "iters": res["iters"], "rel_resid": res["rel_resid"],
                                "rank": res["rank"], "applies": count["applies"], "applies_by_rank": count["by_rank"],
                                "seconds": time.time() - t0, "opts": opts}}

@@ -223,6 +223,10 @@ def test_rank_adaptive_minres_pins():
     fixed2 = lr.minres(op2, E, tol=1e-12, maxit=60)
     ad = lr.minres_rank_adaptive(op, E, rank_start=2, rank_step=2, tol=1e-12, maxit=60)
     assert ad["rank"] > 2 and ad["rel_resid"] < 0.5 * fixed2["rel_resid"]
+    # at the cap it stops as the fixed-rank iteration does: on the first rise (True), not on a rise (False)
+    ad_on = lr.minres_rank_adaptive(op, E, rank_start=2, rank_step=2, tol=1e-12, maxit=60, stop_on_increase=False)
+    assert ad_on["rank"] == ad["rank"] and len(ad_on["history"]) > len(ad["history"])
+    assert ad_on["rel_resid"] <= ad["rel_resid"]
     assert op.rank == 8  # restored
     # a tolerance met below the cap raises the rank: the result is the cap's, within the tolerance there
     loose = lr.minres_rank_adaptive(op, E, rank_start=2, rank_step=2, tol=2e-2, maxit=60)
