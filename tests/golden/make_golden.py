@@ -35,6 +35,8 @@ def main():
     p.add_argument("--ranks", type=int, nargs="*", default=[5, 10])
     p.add_argument("--coeff-rank", type=int, default=10)
     p.add_argument("--sketch-only", action="store_true")
+    p.add_argument("--tensor-only", action="store_true",
+                   help="add the full-format homogenised tensor (Eq. (homog)) to an existing file")
     args = p.parse_args()
     N = args.N
     E = np.array([1.0, 0.0, 0.0])
@@ -42,6 +44,26 @@ def main():
     a_tt = lr.tt_svd(A, rmax=args.coeff_rank)
     A_r = lr.tt_full(a_tt)
     path = os.path.join(HERE, f"lognormal_{N}.json")
+    if args.tensor_only:
+        # the full-format fields of E = e_1, e_2, e_3 (tol 1e-8); the problem is linear in E, so the field of
+        # e_a + e_b is u_a + u_b and every entry of the tensor follows from the three solves
+        out = json.load(open(path))
+        t0 = time.time()
+        fields = [fg.solve_gani(A_r, np.eye(3)[a], tol=1e-8, maxit=2000)["uh"] for a in range(3)]
+        T = np.zeros((3, 3))
+        for a in range(3):
+            T[a, a] = fg.homogenised_coefficient(fields[a], A_r, np.eye(3)[a])
+        for a in range(3):
+            for b in range(a + 1, 3):
+                Eab = np.eye(3)[a] + np.eye(3)[b]
+                q = fg.homogenised_coefficient(fields[a] + fields[b], A_r, Eab)
+                T[a, b] = T[b, a] = 0.5 * (q - T[a, a] - T[b, b])
+        out["full_tensor"] = {"A": T.tolist(), "tol": 1e-8, "seconds": time.time() - t0}
+        print("full_tensor", out["full_tensor"], flush=True)
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+        print(path)
+        return
     if args.sketch_only:
         out = json.load(open(path))
     else:

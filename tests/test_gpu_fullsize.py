@@ -80,3 +80,26 @@ def test_tt_sketched_solve_at_243(ctx, problem_setup):
     assert abs(res.Aeff - g["Aeff"]) <= 2e-6 * g["Aeff"]
     assert res.Aeff >= full * (1 - 1e-12)
     P.free()
+
+
+def test_tt_homogenised_tensor_at_243(ctx, problem_setup):
+    """The homogenised tensor of the benchmark workload (Eq. (homog)) by lrfg_problem_aeff_tensor with the
+    benchmark's tensor options (rank-adapting 10 -> 20 in lockstep, randomised rounding, residual 2e-4 at the
+    cap) against the full-format tensor the oracle produced from its three PCG fields (stored): the diagonal
+    entries within the FP64-path target 1e-6 (each is one solve's A_eff), the off-diagonal ones, assembled by
+    polarisation from three solves, within 2e-6 of the mean diagonal; symmetric."""
+    gold, a_tt, _ = problem_setup
+    if "full_tensor" not in gold:
+        pytest.skip("no stored full-format tensor (tests/golden/make_golden.py --tensor-only)")
+    ref = np.array(gold["full_tensor"]["A"])
+    P = ctx.problem(a_tt, lrfg.TT, rank=20, pinv_eps=0.1, tol=2e-4, maxit=80, stop_on_increase=0, sketch_over=10,
+                    rank_start=10, rank_step=5)
+    T, results = P.aeff_tensor(with_results=True)
+    assert len(results) == 6 and all(r.converged for r in results), [(r.iters, r.rel_resid) for r in results]
+    scale = float(np.mean(np.diag(ref)))
+    for a in range(3):
+        assert abs(T[a, a] - ref[a, a]) <= 1e-6 * ref[a, a], (a, T[a, a], ref[a, a])
+        for b in range(a + 1, 3):
+            assert abs(T[a, b] - ref[a, b]) <= 2e-6 * scale, (a, b, T[a, b], ref[a, b])
+    assert np.array_equal(T, T.T)
+    P.free()
