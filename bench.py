@@ -202,8 +202,8 @@ def measured_peaks():
 # (lrfg_probe_fp64: FMA loops over 8 blocks per SM); the derived figure, 2 FP64 FMA per clock per SM (4 flop/clk/SM)
 # x 152 SMs x 2.07 GHz = 1.26 TFLOP/s, is the fallback when no measurement is passed in.
 FP64_DERIVED_TFLOPS = 152 * 2.070 * 4 / 1e3
-ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "gemm", "eigen", "gram_factor",
-               "sketch"}
+ALU_CLASSES = {"fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "rows_fused", "gemm", "eigen",
+               "gram_factor", "sketch"}
 
 
 def class_rooflines(stats, classes):
@@ -388,7 +388,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     mix_apply_s = (time.perf_counter() - t0) / 5
     # per-class HBM rooflines of one solve in each precision
-    full_classes = ["r2c_rows", "c2r_rows", "fft_fibres", "pointwise", "reduce"]
+    full_classes = ["rows_fused", "r2c_rows", "c2r_rows", "fft_fibres", "pointwise", "reduce"]
     full_roof = {}
     for name, P in (("f64", Pfull), ("mixed", Pmix)):
         ctx.profile_reset()

@@ -161,7 +161,7 @@ void resolve_profile(lrfg_ctx* ctx) {
 
 static const char* kClassNames[KC_COUNT] = {
     "fft_fibres", "fibre_operator", "gauss_multi", "r2c_rows", "c2r_rows", "pointwise",
-    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor", "sketch", "gemm_f32"};
+    "reduce", "gemm", "eigen", "khatri_rao", "tt_misc", "gram_factor", "sketch", "gemm_f32", "rows_fused"};
 
 }  // namespace lrfg
 
@@ -720,8 +720,9 @@ void full_apply(lrfg_problem* P, const typename CplxOf<R>::T* v, typename CplxOf
   const double inv = 1.0 / (double)g.n_real;
   for (int alpha = 0; alpha < g.d; ++alpha) {
     half_mul_grad(ctx, g, v, w.wc, alpha, inv);             // grad^, with 1/|N| of Phi^-1
-    full_inverse<R>(ctx, g, w.wc, w.a, R(1), w.wr);         // A~ F^-1 grad^ v
-    full_forward<R>(ctx, g, w.wr, nullptr, R(1), w.wc);     // F
+    full_fibres_inverse(ctx, g, w.wc);                      // F^-1 on the complex axes,
+    full_rows_mul<R>(ctx, g, w.wc, w.a, R(1));              // then on the rows fused with A~ and F there
+    full_fibres_forward(ctx, g, w.wc);                      // F on the complex axes
     half_acc_div(ctx, g, (const typename CplxOf<R>::T*)w.wc, out, alpha, 1.0, alpha == 0,
                  precond && alpha == g.d - 1 && !P->aniso);  // grad^*
   }

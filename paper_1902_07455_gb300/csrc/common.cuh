@@ -133,6 +133,7 @@ enum KClass {
   KC_CHOL,            // pivoted Cholesky factors of the Gram matrices (TT rounding)
   KC_SKETCH,          // fused Khatri-Rao contractions of the randomised rounding
   KC_GEMM32,          // FP32 products (the sketch side of the mixed-precision randomised rounding)
+  KC_ROWS_FUSED,      // full format: half spectra -> real rows -> times the coefficient -> half spectra
   KC_COUNT
 };
 struct KStats {

@@ -154,6 +154,103 @@ __global__ void __launch_bounds__(256, 3) c2r_rows_kernel(const typename CplxOf<
   }
 }
 
+// half spectra -> real rows -> times the coefficient -> half spectra, in one pass over the rows: the C2R pass,
+// the material product and the R2C pass of the operator fused, so the real grid never goes to memory.  Both
+// directions pair rows f and f + TF in one complex FFT (real and imaginary parts), so after the inverse
+// transform the product acts on the two parts in place and the forward transform runs on the result as is.
+// `in` and `out` may alias (a block reads all of its rows before it writes them).
+template <typename R>
+__global__ void __launch_bounds__(256, 3) c2r_mul_r2c_rows_kernel(const typename CplxOf<R>::T* in,
+                                                               const R* __restrict__ coef, R scale,
+                                                               typename CplxOf<R>::T* out, long long rows, int N,
+                                                               int H, int TF, FftPlan pl,
+                                                               const typename CplxOf<R>::T* __restrict__ Wg) {
+  using V = typename CplxOf<R>::T;
+  const float invN = 1.0f / (float)N, invH = 1.0f / (float)H;
+  extern __shared__ __align__(16) unsigned char smraw_fused[];
+  V* sm = (V*)smraw_fused;
+  V* W = sm;
+  V* a = sm + 2 * N;
+  V* b = a + (size_t)TF * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
+  const long long r0 = (long long)blockIdx.x * 2 * TF;
+  const int nr = (int)min(2LL * TF, rows - r0);
+  const int nrow = min(nr, TF);
+  // Z[k] = X[k] + i Y[k] over the full range from the two half spectra (X[N-k] = conj X[k])
+  {
+    constexpr int kU = 4;
+    const int total = nrow * N;
+    for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+      V x0[kU], x1[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        x0[u] = mkc<V>(R(0), R(0));
+        x1[u] = mkc<V>(R(0), R(0));
+        if (t < total) {
+          const int row = small_div(t, N, invN), k = t - row * N;
+          const int kk = k < H ? k : N - k;
+          x0[u] = in[(size_t)(r0 + row) * H + kk];
+          if (row + TF < nr) x1[u] = in[(size_t)(r0 + row + TF) * H + kk];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        if (t < total) {
+          const int row = small_div(t, N, invN), k = t - row * N;
+          V p = x0[u], q = x1[u];
+          if (k >= H) { p.y = -p.y; q.y = -q.y; }
+          a[(size_t)row * N + k] = mkc<V>(p.x - q.y, p.y + q.x);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  V* Z = stockham_rows<1>(a, b, nrow, N, pl, (const V*)W);
+  // the product with the coefficient on both real rows of each complex row, in place
+  {
+    constexpr int kU = 4;
+    const int total = nrow * N;
+    const R* c0 = coef + (size_t)r0 * N;
+    for (int base = threadIdx.x; base < total; base += kU * blockDim.x) {
+      R ca[kU], cb[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        ca[u] = R(0);
+        cb[u] = R(0);
+        if (t < total) {
+          const int row = small_div(t, N, invN);
+          ca[u] = c0[t];
+          if (row + TF < nr) cb[u] = c0[t + (size_t)TF * N];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int t = base + u * blockDim.x;
+        if (t < total) {
+          const V z = Z[t];
+          Z[t] = mkc<V>(z.x * scale * ca[u], z.y * scale * cb[u]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  V* Z2 = stockham_rows<-1>(Z, Z == a ? b : a, nrow, N, pl, (const V*)W);
+  // split: X[k] = (Z[k] + conj Z[N-k]) / 2,  Y[k] = (Z[k] - conj Z[N-k]) / (2i)
+  for (int t = threadIdx.x; t < nr * H; t += blockDim.x) {
+    const int f = small_div(t, H, invH), k = t - f * H;
+    const int row = f < TF ? f : f - TF;
+    const V z = Z2[(size_t)row * N + k];
+    const V zc = Z2[(size_t)row * N + ((N - k) % N)];
+    V v;
+    if (f < TF) v = mkc<V>(R(0.5) * (z.x + zc.x), R(0.5) * (z.y - zc.y));
+    else v = mkc<V>(R(0.5) * (z.y + zc.y), R(-0.5) * (z.x - zc.x));
+    out[(size_t)(r0 + f) * H + k] = v;
+  }
+}
+
 template <typename R>
 static int row_tile(lrfg_ctx* ctx, int N, size_t* smem) {
   using V = typename CplxOf<R>::T;
@@ -216,6 +313,52 @@ void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_
               c2r_rows_kernel<R><<<(unsigned)blocks, 256, smem, ctx->stream>>>(half_inout, coef, scale, real_out, g.rows,
                                                                                 N, g.H, TF, pl, W));
 }
+
+// the complex-axis passes of full_forward (after its rows) and of full_inverse (before its rows)
+template <typename V>
+void full_fibres_forward(lrfg_ctx* ctx, const FullGrid& g, V* half) {
+  long long inner = g.H;
+  for (int ax = g.d - 2; ax >= 0; --ax) {
+    long long outer = 1;
+    for (int j = 0; j < ax; ++j) outer *= g.N[j];
+    fft_fibres(ctx, half, half, outer, g.N[ax], inner, -1);
+    inner *= g.N[ax];
+  }
+}
+
+template <typename V>
+void full_fibres_inverse(lrfg_ctx* ctx, const FullGrid& g, V* half) {
+  long long inner = g.n_half;
+  for (int ax = 0; ax <= g.d - 2; ++ax) {
+    inner /= g.N[ax];
+    long long outer = g.n_half / (inner * g.N[ax]);
+    fft_fibres(ctx, half, half, outer, g.N[ax], inner, 1);
+  }
+}
+
+template <typename R>
+void full_rows_mul(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale) {
+  using V = typename CplxOf<R>::T;
+  const int N = g.N[g.d - 1];
+  FftPlan pl = make_plan(N, plan_radix<V>());
+  LRFG_CUDA(ensure_roots(ctx->device));
+  const V* W = twiddle_table<R>(ctx, N);
+  size_t smem;
+  int TF = row_tile<R>(ctx, N, &smem);
+  long long blocks = (g.rows + 2LL * TF - 1) / (2LL * TF);
+  LRFG_CUDA(raise_smem_limit((const void*)c2r_mul_r2c_rows_kernel<R>, smem));
+  LRFG_LAUNCH(ctx, KC_ROWS_FUSED, 5.0 * N * std::log2((double)N) * (double)g.rows,
+              (double)g.rows * (2.0 * g.H * sizeof(V) + N * sizeof(R)),
+              c2r_mul_r2c_rows_kernel<R><<<(unsigned)blocks, 256, smem, ctx->stream>>>(
+                  half_inout, coef, scale, half_inout, g.rows, N, g.H, TF, pl, W));
+}
+
+template void full_fibres_forward<double2>(lrfg_ctx*, const FullGrid&, double2*);
+template void full_fibres_forward<float2>(lrfg_ctx*, const FullGrid&, float2*);
+template void full_fibres_inverse<double2>(lrfg_ctx*, const FullGrid&, double2*);
+template void full_fibres_inverse<float2>(lrfg_ctx*, const FullGrid&, float2*);
+template void full_rows_mul<double>(lrfg_ctx*, const FullGrid&, double2*, const double*, double);
+template void full_rows_mul<float>(lrfg_ctx*, const FullGrid&, float2*, const float*, float);
 
 template void full_forward<double>(lrfg_ctx*, const FullGrid&, const double*, const double*, double, double2*);
 template void full_forward<float>(lrfg_ctx*, const FullGrid&, const float*, const float*, float, float2*);

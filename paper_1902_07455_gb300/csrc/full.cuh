@@ -28,6 +28,15 @@ void full_forward(lrfg_ctx* ctx, const FullGrid& g, const R* real_in, const R* c
 template <typename R>
 void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale,
                   R* real_out);
+// the complex-axis passes alone of full_forward (applied after its rows) and of full_inverse (before its rows)
+template <typename V>
+void full_fibres_forward(lrfg_ctx* ctx, const FullGrid& g, V* half);
+template <typename V>
+void full_fibres_inverse(lrfg_ctx* ctx, const FullGrid& g, V* half);
+// the last-axis passes of full_inverse and full_forward fused around a product with the real coefficient:
+// half <- R2C(scale * coef (.) C2R(half)) along the rows (unnormalised transforms, in place)
+template <typename R>
+void full_rows_mul(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale);
 template <typename V>
 void half_mul_grad(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* out, int alpha, double scale);
 template <typename V>
