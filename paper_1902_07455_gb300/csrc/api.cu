@@ -719,12 +719,11 @@ void full_apply(lrfg_problem* P, const typename CplxOf<R>::T* v, typename CplxOf
   FullWork<R> w(P);
   const double inv = 1.0 / (double)g.n_real;
   for (int alpha = 0; alpha < g.d; ++alpha) {
-    half_mul_grad(ctx, g, v, w.wc, alpha, inv);             // grad^, with 1/|N| of Phi^-1
-    full_fibres_inverse(ctx, g, w.wc);                      // F^-1 on the complex axes,
-    full_rows_mul<R>(ctx, g, w.wc, w.a, R(1));              // then on the rows fused with A~ and F there
-    full_fibres_forward(ctx, g, w.wc);                      // F on the complex axes
-    half_acc_div(ctx, g, (const typename CplxOf<R>::T*)w.wc, out, alpha, 1.0, alpha == 0,
-                 precond && alpha == g.d - 1 && !P->aniso);  // grad^*
+    // grad^ (with 1/|N| of Phi^-1) and F^-1 on the complex axes, then on the rows fused with A~ and F there,
+    // then F on the complex axes and grad^* (P~^-1 after the last component)
+    half_grad_fibres_inverse(ctx, g, v, w.wc, alpha, inv);
+    full_rows_mul<R>(ctx, g, w.wc, w.a, R(1));
+    half_fibres_forward_div(ctx, g, w.wc, out, alpha, 1.0, alpha == 0, precond && alpha == g.d - 1 && !P->aniso);
   }
   // constant anisotropic part: grad^* F B F^-1 grad^ is the multiplier 4 pi^2 k.B k
   if (P->aniso) half_acc_aniso(ctx, g, v, out, P->B, precond);

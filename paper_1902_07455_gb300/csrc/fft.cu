@@ -105,9 +105,51 @@ static int spread_tf(int tf_max, long long nfib, long long target) {
 // ----------------------------------------------------------------------------------------------------
 // complex fibres
 // ----------------------------------------------------------------------------------------------------
-template <int SIGN, typename V>
+// frequencies (k1, k2) of fibre i of the axis-0 pass over a d = 2 or 3 half spectrum
+template <typename R>
+__device__ __forceinline__ void fibre_freqs(const FibreMul<R>& fm, long long i, int& k1, int& k2) {
+  if (fm.d == 3) {
+    const int i1 = (int)(i / fm.H);
+    k1 = freq_of(i1, fm.N1);
+    k2 = (int)(i - (long long)i1 * fm.H);
+  } else {
+    k1 = (int)i;
+    k2 = 0;
+  }
+}
+
+// v * (2 pi i k) * scale, f = c2 k
+template <typename V>
+__device__ __forceinline__ V times_2pi_ik(V v, typename RealOf<V>::T f) {
+  return mkc<V>(-v.y * f, v.x * f);
+}
+
+// mode 2 of FibreMul: the divergence term of element (k0, k1, k2) accumulated into *dst
+template <typename V>
+__device__ __forceinline__ void acc_div_store(const FibreMul<typename RealOf<V>::T>& fm, V* dst, V x, int k0, int k1,
+                                              int k2) {
+  using R = typename RealOf<V>::T;
+  const int ka = fm.alpha == 0 ? k0 : (fm.alpha == 1 ? k1 : k2);
+  V r = times_2pi_ik<V>(x, -fm.c2 * (R)ka);
+  if (!fm.init) {
+    const V o = *dst;
+    r.x += o.x;
+    r.y += o.y;
+  }
+  if (fm.precond) {
+    const R s = fm.inv_kk[k0 * k0 + k1 * k1 + k2 * k2];
+    r.x *= s;
+    r.y *= s;
+  }
+  *dst = r;
+}
+
+// OP 0: plain transform; OP 1 and 2: the modes of FibreMul (outer = 1)
+template <int SIGN, typename V, int OP>
 __global__ void __launch_bounds__(256, 3) fft_fibres_kernel(const V* in, V* out, long long outer, int N, long long inner,
-                                                         int TF, FftPlan pl, const V* __restrict__ Wg) {
+                                                         int TF, FftPlan pl, const V* __restrict__ Wg,
+                                                         FibreMul<typename RealOf<V>::T> fm) {
+  using R = typename RealOf<V>::T;
   extern __shared__ __align__(16) unsigned char smraw_fib[];
   V* sm = (V*)smraw_fib;
   V* W = sm;
@@ -138,6 +180,29 @@ __global__ void __launch_bounds__(256, 3) fft_fibres_kernel(const V* in, V* out,
   }
   for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
   cp_async_wait_all();
+  if constexpr (OP == 1) {
+    // each thread scales the elements it copied itself (its own copies are complete after the wait)
+    if (across) {
+      const int step = blockDim.x / nf;
+      const int f = threadIdx.x % nf, n0 = threadIdx.x / nf;
+      int k1, k2;
+      fibre_freqs(fm, g0 + f, k1, k2);
+      const R fc = fm.c2 * (R)(fm.alpha == 1 ? k1 : k2);
+      if (n0 < step)
+        for (int n = n0; n < N; n += step) {
+          V* p = a + (size_t)f * N + n;
+          *p = times_2pi_ik<V>(*p, fm.alpha == 0 ? fm.c2 * (R)freq_of(n, N) : fc);
+        }
+    } else {
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int f = small_div(t, N, 1.0f / (float)N), n = t - f * N;
+        int k1, k2;
+        fibre_freqs(fm, g0 + f, k1, k2);
+        const int ka = fm.alpha == 0 ? freq_of(n, N) : (fm.alpha == 1 ? k1 : k2);
+        a[t] = times_2pi_ik<V>(a[t], fm.c2 * (R)ka);
+      }
+    }
+  }
   __syncthreads();
   V* res = stockham_rows<SIGN>(a, b, nf, N, pl, (const V*)W);
   if (across) {
@@ -146,14 +211,29 @@ __global__ void __launch_bounds__(256, 3) fft_fibres_kernel(const V* in, V* out,
     const long long g = g0 + f;
     const long long o = g / inner, i = g - o * inner;
     V* dst = out + (size_t)o * N * (size_t)inner + (size_t)i;
-    if (n0 < step)
-      for (int n = n0; n < N; n += step) dst[(size_t)n * inner] = res[(size_t)f * N + n];
+    if constexpr (OP == 2) {
+      int k1, k2;
+      fibre_freqs(fm, i, k1, k2);
+      if (n0 < step)
+        for (int n = n0; n < N; n += step)
+          acc_div_store<V>(fm, dst + (size_t)n * inner, res[(size_t)f * N + n], freq_of(n, N), k1, k2);
+    } else {
+      if (n0 < step)
+        for (int n = n0; n < N; n += step) dst[(size_t)n * inner] = res[(size_t)f * N + n];
+    }
   } else {
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int f = small_div(t, N, 1.0f / (float)N), n = t - f * N;
       const long long g = g0 + f;
       const long long o = g / inner, i = g - o * inner;
-      out[((size_t)o * N + n) * (size_t)inner + (size_t)i] = res[(size_t)f * N + n];
+      V* dst = out + ((size_t)o * N + n) * (size_t)inner + (size_t)i;
+      if constexpr (OP == 2) {
+        int k1, k2;
+        fibre_freqs(fm, i, k1, k2);
+        acc_div_store<V>(fm, dst, res[(size_t)f * N + n], freq_of(n, N), k1, k2);
+      } else {
+        *dst = res[(size_t)f * N + n];
+      }
     }
   }
 }
@@ -188,18 +268,55 @@ void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long
   LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
   const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;   // radix-2-equivalent count
   const double bytes = 2.0 * sizeof(V) * (double)N * (double)nfib;
+  const FibreMul<R> none{};
   if (sign < 0) {
-    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<-1, V>, smem));
+    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<-1, V, 0>, smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
-                fft_fibres_kernel<-1, V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W));
+                fft_fibres_kernel<-1, V, 0><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF,
+                                                                                         pl, W, none));
   } else {
-    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<1, V>, smem));
+    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<1, V, 0>, smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
-                fft_fibres_kernel<1, V><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF, pl, W));
+                fft_fibres_kernel<1, V, 0><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, outer, N, inner, TF,
+                                                                                        pl, W, none));
   }
 }
 template void fft_fibres<double2>(lrfg_ctx*, const double2*, double2*, long long, int, long long, int);
 template void fft_fibres<float2>(lrfg_ctx*, const float2*, float2*, long long, int, long long, int);
+
+template <typename V>
+void fft_fibres_mul(lrfg_ctx* ctx, const V* in, V* out, int N0, long long inner, const FibreMul<typename RealOf<V>::T>& fm) {
+  using R = typename RealOf<V>::T;
+  LRFG_REQUIRE(N0 >= 1 && (N0 % 2 == 1), "fft length must be odd (got %d)", N0);
+  LRFG_REQUIRE(fm.mode == 1 || fm.mode == 2, "multiplier mode %d", fm.mode);
+  LRFG_REQUIRE(fm.d == 2 || fm.d == 3, "d = %d", fm.d);
+  LRFG_REQUIRE(inner == (long long)(fm.d == 3 ? fm.N1 : 1) * fm.H, "axis-0 fibres of a half spectrum expected");
+  LRFG_REQUIRE(fm.mode == 1 || in != out, "the accumulator cannot hold the input");
+  LRFG_REQUIRE(!(fm.mode == 2 && fm.precond) || fm.inv_kk, "reciprocal table missing");
+  if (inner == 0) return;
+  FftPlan pl = make_plan(N0, plan_radix<V>());
+  const V* W = twiddle_table<R>(ctx, N0);
+  size_t smem;
+  int TF = tile_complex(ctx, N0, sizeof(V), &smem);
+  long long blocks = (inner + TF - 1) / TF;
+  LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
+  const double n_el = (double)N0 * (double)inner;
+  const double flops = 5.0 * N0 * std::log2((double)N0) * (double)inner + (fm.mode == 1 ? 2.0 : 4.0) * n_el;
+  const double bytes = (fm.mode == 1 || fm.init ? 2.0 : 3.0) * sizeof(V) * n_el;
+  if (fm.mode == 1) {
+    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<1, V, 1>, smem));
+    LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
+                fft_fibres_kernel<1, V, 1><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, 1, N0, inner, TF, pl,
+                                                                                        W, fm));
+  } else {
+    LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<-1, V, 2>, smem));
+    LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
+                fft_fibres_kernel<-1, V, 2><<<(unsigned)blocks, 256, smem, ctx->stream>>>(in, out, 1, N0, inner, TF, pl,
+                                                                                         W, fm));
+  }
+}
+template void fft_fibres_mul<double2>(lrfg_ctx*, const double2*, double2*, int, long long, const FibreMul<double>&);
+template void fft_fibres_mul<float2>(lrfg_ctx*, const float2*, float2*, int, long long, const FibreMul<float>&);
 
 // ----------------------------------------------------------------------------------------------------
 // real fibres under a multiplier: rows hold fibre f (real part) and fibre f + TF (imaginary part)

@@ -314,28 +314,6 @@ void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_
                                                                                 N, g.H, TF, pl, W));
 }
 
-// the complex-axis passes of full_forward (after its rows) and of full_inverse (before its rows)
-template <typename V>
-void full_fibres_forward(lrfg_ctx* ctx, const FullGrid& g, V* half) {
-  long long inner = g.H;
-  for (int ax = g.d - 2; ax >= 0; --ax) {
-    long long outer = 1;
-    for (int j = 0; j < ax; ++j) outer *= g.N[j];
-    fft_fibres(ctx, half, half, outer, g.N[ax], inner, -1);
-    inner *= g.N[ax];
-  }
-}
-
-template <typename V>
-void full_fibres_inverse(lrfg_ctx* ctx, const FullGrid& g, V* half) {
-  long long inner = g.n_half;
-  for (int ax = 0; ax <= g.d - 2; ++ax) {
-    inner /= g.N[ax];
-    long long outer = g.n_half / (inner * g.N[ax]);
-    fft_fibres(ctx, half, half, outer, g.N[ax], inner, 1);
-  }
-}
-
 template <typename R>
 void full_rows_mul(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale) {
   using V = typename CplxOf<R>::T;
@@ -353,10 +331,6 @@ void full_rows_mul(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half
                   half_inout, coef, scale, half_inout, g.rows, N, g.H, TF, pl, W));
 }
 
-template void full_fibres_forward<double2>(lrfg_ctx*, const FullGrid&, double2*);
-template void full_fibres_forward<float2>(lrfg_ctx*, const FullGrid&, float2*);
-template void full_fibres_inverse<double2>(lrfg_ctx*, const FullGrid&, double2*);
-template void full_fibres_inverse<float2>(lrfg_ctx*, const FullGrid&, float2*);
 template void full_rows_mul<double>(lrfg_ctx*, const FullGrid&, double2*, const double*, double);
 template void full_rows_mul<float>(lrfg_ctx*, const FullGrid&, float2*, const float*, float);
 
@@ -547,6 +521,53 @@ void half_acc_div(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* acc, int alp
               acc_div_kernel<V><<<row_grid(g), row_block(g), 0, ctx->stream>>>(
                   in, acc, rowmap(g), alpha, (R)two_pi_times(scale), init, precond, inv_table<R>(g)));
 }
+
+// The complex-axis passes of the operator around its fused rows, with grad^ folded into the first
+// inverse pass (axis 0) and grad^* (with P~^-1 on the last component) into the last forward one.
+template <typename R>
+static FibreMul<R> fibre_mul(const FullGrid& g, int mode, int alpha, double scale, int init, int precond) {
+  FibreMul<R> fm{};
+  fm.mode = mode;
+  fm.alpha = alpha;
+  fm.d = g.d;
+  fm.N1 = g.d == 3 ? g.N[1] : 1;
+  fm.H = g.H;
+  fm.init = init;
+  fm.precond = precond;
+  fm.c2 = (R)two_pi_times(scale);
+  fm.inv_kk = inv_table<R>(g);
+  return fm;
+}
+
+template <typename V>
+void half_grad_fibres_inverse(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* half, int alpha, double scale) {
+  using R = typename RealOf<V>::T;
+  long long inner = g.n_half / g.N[0];
+  fft_fibres_mul(ctx, in, half, g.N[0], inner, fibre_mul<R>(g, 1, alpha, scale, 0, 0));
+  for (int ax = 1; ax <= g.d - 2; ++ax) {
+    inner /= g.N[ax];
+    fft_fibres(ctx, half, half, g.n_half / (inner * g.N[ax]), g.N[ax], inner, 1);
+  }
+}
+
+template <typename V>
+void half_fibres_forward_div(lrfg_ctx* ctx, const FullGrid& g, V* half, V* acc, int alpha, double scale, int init,
+                             int precond) {
+  using R = typename RealOf<V>::T;
+  long long inner = g.H;
+  for (int ax = g.d - 2; ax >= 1; --ax) {
+    long long outer = 1;
+    for (int j = 0; j < ax; ++j) outer *= g.N[j];
+    fft_fibres(ctx, half, half, outer, g.N[ax], inner, -1);
+    inner *= g.N[ax];
+  }
+  fft_fibres_mul(ctx, (const V*)half, acc, g.N[0], inner, fibre_mul<R>(g, 2, alpha, scale, init, precond));
+}
+
+template void half_grad_fibres_inverse<double2>(lrfg_ctx*, const FullGrid&, const double2*, double2*, int, double);
+template void half_grad_fibres_inverse<float2>(lrfg_ctx*, const FullGrid&, const float2*, float2*, int, double);
+template void half_fibres_forward_div<double2>(lrfg_ctx*, const FullGrid&, double2*, double2*, int, double, int, int);
+template void half_fibres_forward_div<float2>(lrfg_ctx*, const FullGrid&, float2*, float2*, int, double, int, int);
 
 // ------------------------------------------------------------------------------------------------
 // Ga: injection / projection between the half spectra of the grid (N) and the double grid (M = 2N - 1)

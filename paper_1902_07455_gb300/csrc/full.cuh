@@ -28,11 +28,15 @@ void full_forward(lrfg_ctx* ctx, const FullGrid& g, const R* real_in, const R* c
 template <typename R>
 void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale,
                   R* real_out);
-// the complex-axis passes alone of full_forward (applied after its rows) and of full_inverse (before its rows)
+// the complex-axis passes of full_inverse (before its rows) with grad^ folded into the first of them:
+// half = Phi^{-1} on axes 0..d-2 of (in * 2 pi i k_alpha * scale)
 template <typename V>
-void full_fibres_forward(lrfg_ctx* ctx, const FullGrid& g, V* half);
+void half_grad_fibres_inverse(lrfg_ctx* ctx, const FullGrid& g, const V* in, V* half, int alpha, double scale);
+// the complex-axis passes of full_forward (after its rows) with grad^* folded into the last of them, as
+// half_acc_div does with the transformed half (which is left in an intermediate state)
 template <typename V>
-void full_fibres_inverse(lrfg_ctx* ctx, const FullGrid& g, V* half);
+void half_fibres_forward_div(lrfg_ctx* ctx, const FullGrid& g, V* half, V* acc, int alpha, double scale, int init,
+                             int precond);
 // the last-axis passes of full_inverse and full_forward fused around a product with the real coefficient:
 // half <- R2C(scale * coef (.) C2R(half)) along the rows (unnormalised transforms, in place)
 template <typename R>

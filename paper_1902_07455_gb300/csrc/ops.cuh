@@ -19,6 +19,22 @@ const typename CplxOf<R>::T* twiddle_table(lrfg_ctx* ctx, int N);
 // (V = double2 or float2)
 template <typename V>
 void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long long inner, int sign);
+// The gradient and divergence multipliers of the full-format operator (Eq. 2.10) folded into its axis-0
+// fibre pass over the half spectrum (N0, inner) of a d = 2 or 3 grid, inner = N1 * H or H, so that fibre i
+// holds the frequencies (k0 = n, i / H, i % H) or (n, i):
+//  mode 1, inverse DFT: out = F^-1 (in * 2 pi i k_alpha * scale), the product taken on the staged tile;
+//  mode 2, forward DFT: acc = ((init ? 0 : acc) - 2 pi i k_alpha * scale * F in) * (precond ? 1/(k.k) : 1),
+//  the result of the transform never stored.
+// The products are the ones of the separate pointwise kernels, in the same order and precision.
+template <typename R>
+struct FibreMul {
+  int mode, alpha, d, N1, H, init, precond;
+  R c2;             // 2 pi scale, rounded to R
+  const R* inv_kk;  // 1/(k.k) indexed by k.k, 0 at k = 0 (mode 2 with precond)
+};
+template <typename V>
+void fft_fibres_mul(lrfg_ctx* ctx, const V* in, V* out, int N0, long long inner,
+                    const FibreMul<typename RealOf<V>::T>& fm);
 // Ga mode maps on real fibres (outer, n_in, inner) -> (outer, n_out, inner), M = 2N - 1 (Sec. 2.2.3):
 //  GA_UP      N -> M  band-limited interpolation to the double grid, F_M^-1 I F_N;
 //  GA_DOWN    M -> N  projection, F_N^-1 I* F_M;
