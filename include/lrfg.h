@@ -211,6 +211,12 @@ lrfg_status lrfg_profile_read(lrfg_ctx* ctx, int n, long long* launches, double*
 lrfg_status lrfg_fft_fibres(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner,
                             int sign);
 
+/* The same transform of a complex FP32 device array (re,im interleaved floats), in FP32 arithmetic with
+ * FP32-rounded twiddles: the fibre passes of the LRFG_MIXED full format.  Relative error a few
+ * u_32 log2(N) of the fibre's norm. */
+lrfg_status lrfg_fft_fibres_f32(lrfg_ctx* ctx, const float* in, float* out, int outer, int N, int inner,
+                                int sign);
+
 /* out = scale * F_N^{-1} diag(m) F_N in along the middle axis of a REAL FP64 device array of shape
  * (outer, N, inner): the real-space form of a Fourier multiplier acting on one mode.  With
  * LRFG_MUL_DERIV this is one component of F^{-1} grad^ F (Sec. 2.2.1, Eq. (grad_trig)) applied to TT

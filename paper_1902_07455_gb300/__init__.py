@@ -223,14 +223,18 @@ class Context:
 
     # ---- fibre operators (rows a1, a2) ---------------------------------------------------------
     def fft_fibres(self, x, sign: int, out=None):
-        """Batched DFT along dim 1 of a complex128 CUDA tensor of shape (outer, N, inner)."""
+        """Batched DFT along dim 1 of a complex128 (FP64) or complex64 (FP32 arithmetic) CUDA tensor of
+        shape (outer, N, inner)."""
         torch = _torch()
-        if x.dtype != torch.complex128 or x.dim() != 3:
-            raise ValueError("x must be a complex128 tensor (outer, N, inner)")
+        if x.dtype not in (torch.complex128, torch.complex64) or x.dim() != 3:
+            raise ValueError("x must be a complex128 or complex64 tensor (outer, N, inner)")
         x = x.contiguous()
         out = torch.empty_like(x) if out is None else out
+        if out.dtype != x.dtype or out.shape != x.shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous tensor of the input's shape and type")
         outer, N, inner = x.shape
-        self.check(self.lib.lrfg_fft_fibres(self.h, _ptr(x), _ptr(out), outer, N, inner, int(sign)))
+        fn = self.lib.lrfg_fft_fibres if x.dtype == torch.complex128 else self.lib.lrfg_fft_fibres_f32
+        self.check(fn(self.h, _ptr(x), _ptr(out), outer, N, inner, int(sign)))
         return out
 
     def fibre_operator(self, x, kind: int, param: float = 0.0, scale: float = 1.0, out=None):

@@ -68,6 +68,7 @@ SIGNATURES = {
     "lrfg_profile_reset": (_ST, [_P]),
     "lrfg_profile_read": (_ST, [_P, _I, C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)]),
     "lrfg_fft_fibres": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
+    "lrfg_fft_fibres_f32": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
     "lrfg_fibre_operator": (_ST, [_P, _P, _P, _I, _I, _I, _I, _D, _D]),
     "lrfg_tt_hadamard": (_ST, [_P, C.POINTER(lrfg_tt), C.POINTER(lrfg_tt), C.POINTER(lrfg_tt)]),
     "lrfg_tucker_round": (_ST, [_P, C.POINTER(lrfg_tucker), _I, C.POINTER(lrfg_tucker)]),

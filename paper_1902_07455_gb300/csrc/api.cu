@@ -1463,6 +1463,17 @@ lrfg_status lrfg_fft_fibres(lrfg_ctx* ctx, const double* in, double* out, int ou
   });
 }
 
+lrfg_status lrfg_fft_fibres_f32(lrfg_ctx* ctx, const float* in, float* out, int outer, int N, int inner, int sign) {
+  if (!ctx) return LRFG_EINVAL;
+  return guard(ctx, [&] {
+    LRFG_REQUIRE(outer >= 0 && inner >= 0, "negative batch");
+    LRFG_REQUIRE((in && out) || (long long)outer * inner == 0, "null buffer");
+    LRFG_REQUIRE(sign == 1 || sign == -1, "sign must be +1 or -1");
+    LRFG_REQUIRE(N >= 1 && N % 2 == 1, "N must be odd");
+    fft_fibres<float2>(ctx, (const float2*)in, (float2*)out, outer, N, inner, sign);
+  });
+}
+
 lrfg_status lrfg_fibre_operator(lrfg_ctx* ctx, const double* in, double* out, int outer, int N, int inner,
                                 lrfg_multiplier kind, double param, double scale) {
   if (!ctx) return LRFG_EINVAL;

@@ -238,6 +238,149 @@ __global__ void __launch_bounds__(256, 3) fft_fibres_kernel(const V* in, V* out,
   }
 }
 
+// ----------------------------------------------------------------------------------------------------
+// FP32 complex fibres of length N = P1 P2 in two register passes with one trip through shared memory.
+// A block takes 32 consecutive fibres, lane = fibre, so every global access of a warp touches 32
+// neighbouring inner indices.  The two Stockham stages of the header of fft_device.cuh, written out:
+//  pass 1 (radix P1, L = 1; warp w = c < P2): x[c + P2 r], r < P1, loaded straight from global memory,
+//         a P1-point DFT in registers, Z[c P1 + q] (q < P1) to shared memory;
+//  pass 2 (radix P2, L = P1; f = w, w + P2, ... < P1): Z[r P1 + f] (r < P2) times w_N^{f r}, a P2-point
+//         DFT, X[f + P1 q] (q < P2) stored straight to global memory.
+// Against the staged kernel this saves the staging round trips through shared memory, one of its
+// two buffers and the per-butterfly index arithmetic.  A block reads all of its fibres before it
+// writes any, and fibres belong to one block, so in == out is allowed.  OP as in fft_fibres_kernel.
+// ----------------------------------------------------------------------------------------------------
+// three blocks per SM where their shared memory fits
+template <int P1, int P2, int OP>
+constexpr int fft2_min_blocks() {
+  return P1 * P2 * 32 * 8 * 3 <= 200 * 1024 ? 3 : 2;
+}
+
+template <int SIGN, int P1, int P2, int OP>
+__global__ void __launch_bounds__(32 * P2, fft2_min_blocks<P1, P2, OP>()) fft2_fibres_kernel(
+    const float2* in, float2* out, long long outer, long long inner, const float2* __restrict__ Wg, FibreMul<float> fm) {
+  static_assert(P1 % P2 == 0, "pass 2 takes P1 / P2 butterflies per warp");
+  constexpr int N = P1 * P2;
+  extern __shared__ __align__(16) unsigned char smraw_fib2[];
+  float2* Z = (float2*)smraw_fib2;  // [N][32]
+  float2* W = Z + N * 32;           // w_N^j, j < N
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long g = (long long)blockIdx.x * 32 + lane;
+  const bool valid = g < outer * inner;
+  long long o = 0, i = 0;
+  if (valid) {
+    o = g / inner;
+    i = g - o * inner;
+  }
+  int k1 = 0, k2 = 0;
+  if constexpr (OP != 0) fibre_freqs(fm, i, k1, k2);
+  const size_t base = (size_t)o * N * (size_t)inner + (size_t)i;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) W[j] = Wg[j];
+
+  float2 x[P1];
+#pragma unroll
+  for (int r = 0; r < P1; ++r) x[r] = valid ? in[base + (size_t)(w + P2 * r) * (size_t)inner] : make_float2(0.f, 0.f);
+  if constexpr (OP == 1) {
+    // k_0 varies along the fibre: multiply before the transform; k_1 and k_2 are constant on it and
+    // the product commutes with the transform, so it is taken after pass 2 (fewer live registers)
+    if (fm.alpha == 0) {
+#pragma unroll
+      for (int r = 0; r < P1; ++r) x[r] = times_2pi_ik<float2>(x[r], fm.c2 * (float)freq_of(w + P2 * r, N));
+    }
+  }
+  RegDFT<P1, SIGN, float2>::run(x);
+#pragma unroll
+  for (int q = 0; q < P1; ++q) Z[(w * P1 + q) * 32 + lane] = x[q];
+  __syncthreads();
+
+#pragma unroll
+  for (int jb = 0; jb < P1 / P2; ++jb) {
+    const int f = w + P2 * jb;
+    float2 y[P2], prev[P2];
+    if constexpr (OP == 2) {
+      // the accumulator's old values, all requested before the transform so that their latencies overlap
+#pragma unroll
+      for (int q = 0; q < P2; ++q)
+        prev[q] = valid && !fm.init ? out[base + (size_t)(f + P1 * q) * (size_t)inner] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < P2; ++r) {
+      y[r] = Z[(r * P1 + f) * 32 + lane];
+      if (r) y[r] = cmul(y[r], tw<SIGN>((const float2*)W, f * r));
+    }
+    RegDFT<P2, SIGN, float2>::run(y);
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < P2; ++q) {
+        const int n = f + P1 * q;
+        float2* dst = out + base + (size_t)n * (size_t)inner;
+        if constexpr (OP == 2) {
+          const int k0 = freq_of(n, N);
+          const int ka = fm.alpha == 0 ? k0 : (fm.alpha == 1 ? k1 : k2);
+          float2 r = times_2pi_ik<float2>(y[q], -fm.c2 * (float)ka);
+          if (!fm.init) {
+            r.x += prev[q].x;
+            r.y += prev[q].y;
+          }
+          if (fm.precond) {
+            // the correctly rounded reciprocal, the value the table holds, without its scattered gather
+            const int kk = k0 * k0 + k1 * k1 + k2 * k2;
+            const float sc = kk ? __frcp_rn((float)kk) : 0.f;
+            r.x *= sc;
+            r.y *= sc;
+          }
+          *dst = r;
+        } else if constexpr (OP == 1) {
+          *dst = fm.alpha == 0 ? y[q] : times_2pi_ik<float2>(y[q], fm.c2 * (float)(fm.alpha == 1 ? k1 : k2));
+        } else {
+          *dst = y[q];
+        }
+      }
+    }
+  }
+}
+
+// N = P1 P2 served by fft2_fibres_kernel (FP32), else 0
+static int fft2_split(int N) {
+  if (N == 243) return 27;
+  if (N == 81) return 9;
+  return 0;
+}
+
+template <int SIGN, int P1, int P2, int OP>
+static void fft2_launch(lrfg_ctx* ctx, const float2* in, float2* out, long long outer, long long inner,
+                        const FibreMul<float>& fm, double flops, double bytes) {
+  constexpr int N = P1 * P2;
+  const size_t smem = sizeof(float2) * (size_t)N * 33;
+  const long long blocks = (outer * inner + 31) / 32;
+  LRFG_REQUIRE(blocks < (1LL << 31), "too many fibres");
+  const float2* W = twiddle_table<float>(ctx, N);
+  LRFG_CUDA(raise_smem_limit((const void*)fft2_fibres_kernel<SIGN, P1, P2, OP>, smem));
+  LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
+              fft2_fibres_kernel<SIGN, P1, P2, OP><<<(unsigned)blocks, 32 * P2, smem, ctx->stream>>>(in, out, outer,
+                                                                                                 inner, W, fm));
+}
+
+template <int SIGN, int OP>
+static bool fft2_dispatch(lrfg_ctx* ctx, const float2* in, float2* out, long long outer, int N, long long inner,
+                          const FibreMul<float>& fm, double flops, double bytes) {
+  switch (fft2_split(N)) {
+    case 27: fft2_launch<SIGN, 27, 9, OP>(ctx, in, out, outer, inner, fm, flops, bytes); return true;
+    case 9: fft2_launch<SIGN, 9, 9, OP>(ctx, in, out, outer, inner, fm, flops, bytes); return true;
+    default: return false;
+  }
+}
+
+template <typename V, int SIGN, int OP>
+static bool fft2_try(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long long inner,
+                     const FibreMul<typename RealOf<V>::T>& fm, double flops, double bytes) {
+  if constexpr (sizeof(V) == sizeof(float2)) {
+    return fft2_dispatch<SIGN, OP>(ctx, (const float2*)in, (float2*)out, outer, N, inner, fm, flops, bytes);
+  } else {
+    return false;
+  }
+}
+
 // Tile for the complex fibre FFT: whole 128-byte segments along the contiguous index (TF * sizeof(V) >=
 // 128) and at most 72 KB of shared memory, so that three blocks share an SM and one block's transform
 // overlaps the others' loads and stores.
@@ -269,6 +412,9 @@ void fft_fibres(lrfg_ctx* ctx, const V* in, V* out, long long outer, int N, long
   const double flops = 5.0 * N * std::log2((double)N) * (double)nfib;   // radix-2-equivalent count
   const double bytes = 2.0 * sizeof(V) * (double)N * (double)nfib;
   const FibreMul<R> none{};
+  if (sign < 0 ? fft2_try<V, -1, 0>(ctx, in, out, outer, N, inner, none, flops, bytes)
+               : fft2_try<V, 1, 0>(ctx, in, out, outer, N, inner, none, flops, bytes))
+    return;
   if (sign < 0) {
     LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<-1, V, 0>, smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,
@@ -303,6 +449,9 @@ void fft_fibres_mul(lrfg_ctx* ctx, const V* in, V* out, int N0, long long inner,
   const double n_el = (double)N0 * (double)inner;
   const double flops = 5.0 * N0 * std::log2((double)N0) * (double)inner + (fm.mode == 1 ? 2.0 : 4.0) * n_el;
   const double bytes = (fm.mode == 1 || fm.init ? 2.0 : 3.0) * sizeof(V) * n_el;
+  if (fm.mode == 1 ? fft2_try<V, 1, 1>(ctx, in, out, 1, N0, inner, fm, flops, bytes)
+                   : fft2_try<V, -1, 2>(ctx, in, out, 1, N0, inner, fm, flops, bytes))
+    return;
   if (fm.mode == 1) {
     LRFG_CUDA(raise_smem_limit((const void*)fft_fibres_kernel<1, V, 1>, smem));
     LRFG_LAUNCH(ctx, KC_FFT_FIBRES, flops, bytes,

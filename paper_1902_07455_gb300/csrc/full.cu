@@ -251,6 +251,132 @@ __global__ void __launch_bounds__(256, 3) c2r_mul_r2c_rows_kernel(const typename
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// FP32 rows of length N = P1 P2: the fused C2R -> product -> R2C pass of the operator with the two
+// register passes of fft2_fibres_kernel per direction, over a tile of 32 complex rows (real rows r0 + j
+// and r0 + 32 + j in the real and imaginary parts of complex row j).  The tile lives once in shared
+// memory as Z[n][j] with row stride 33 (conflict-free both along n and along j); every pass reads its
+// inputs to registers, waits at a barrier and writes its outputs in place, so no second buffer is needed
+// and three blocks fit an SM.  Global traffic is coalesced along each row: the half spectra in, the
+// coefficient rows, the half spectra out.  `in` and `out` may alias (a block reads all its rows first).
+// ------------------------------------------------------------------------------------------------
+constexpr int kRowsLd = 33;
+
+// one Stockham pass pair of the transform of the tile, in place (see the header of fft_device.cuh):
+// pass 1 radix P1 (warp w = c < P2 takes x[c + P2 r]), pass 2 radix P2 with w_N^{f r} (f = w + P2 jb)
+template <int SIGN, int P1, int P2>
+__device__ __forceinline__ void rows2_transform(float2* Z, const float2* W, int w, int lane) {
+  constexpr int N = P1 * P2;
+  {
+    float2 x[P1];
+#pragma unroll
+    for (int r = 0; r < P1; ++r) x[r] = Z[(w + P2 * r) * kRowsLd + lane];
+    __syncthreads();
+    RegDFT<P1, SIGN, float2>::run(x);
+#pragma unroll
+    for (int q = 0; q < P1; ++q) Z[(w * P1 + q) * kRowsLd + lane] = x[q];
+  }
+  __syncthreads();
+  {
+    float2 y[P1 / P2][P2];
+#pragma unroll
+    for (int jb = 0; jb < P1 / P2; ++jb)
+#pragma unroll
+      for (int r = 0; r < P2; ++r) y[jb][r] = Z[(r * P1 + w + P2 * jb) * kRowsLd + lane];
+    __syncthreads();
+#pragma unroll
+    for (int jb = 0; jb < P1 / P2; ++jb) {
+      const int f = w + P2 * jb;
+#pragma unroll
+      for (int r = 1; r < P2; ++r) y[jb][r] = cmul(y[jb][r], tw<SIGN>(W, f * r));
+      RegDFT<P2, SIGN, float2>::run(y[jb]);
+#pragma unroll
+      for (int q = 0; q < P2; ++q) Z[(f + P1 * q) * kRowsLd + lane] = y[jb][q];
+    }
+  }
+  __syncthreads();
+  (void)N;
+}
+
+template <int P1, int P2>
+__global__ void __launch_bounds__(32 * P2, 3) rows2_mul_kernel(const float2* in, const float* __restrict__ coef,
+                                                              float scale, float2* out, long long rows,
+                                                              const float2* __restrict__ Wg) {
+  constexpr int N = P1 * P2, H = (N + 1) / 2, NT = 32 * P2;
+  extern __shared__ __align__(16) unsigned char smraw_rows2[];
+  float2* Z = (float2*)smraw_rows2;  // [N][kRowsLd]
+  float2* W = Z + N * kRowsLd;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.x * 64;
+  const int nr = (int)min(64LL, rows - r0);  // real rows of this tile: j < nr (real parts), 32 + j < nr (imaginary)
+  for (int j = threadIdx.x; j < N; j += NT) W[j] = Wg[j];
+  // Z[k] = X[k] + i Y[k] and Z[N - k] = conj X[k] + i conj Y[k] from the two half spectra
+  {
+    constexpr int kU = 4;
+    constexpr int total = 32 * H;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kU * NT) {
+      float2 a[kU], b[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * NT;
+        const int j = e / H;
+        a[u] = make_float2(0.f, 0.f);
+        b[u] = make_float2(0.f, 0.f);
+        if (e < total && j < nr) a[u] = in[(size_t)r0 * H + e];
+        if (e < total && j + 32 < nr) b[u] = in[(size_t)(r0 + 32) * H + e];
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * NT;
+        if (e < total) {
+          const int j = e / H, k = e - j * H;
+          Z[k * kRowsLd + j] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
+          if (k) Z[(N - k) * kRowsLd + j] = make_float2(a[u].x + b[u].y, b[u].x - a[u].y);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  rows2_transform<1, P1, P2>(Z, W, w, lane);
+  // the real rows times the coefficient: Z[n][j] = (x_j[n], x_{32+j}[n]); each thread's coefficients are
+  // requested before any is used
+  {
+    constexpr int per = (32 * N + NT - 1) / NT;
+    const float* c0 = coef + (size_t)r0 * N;
+    float ca[per], cb[per];
+#pragma unroll
+    for (int u = 0; u < per; ++u) {
+      const int e = threadIdx.x + u * NT;
+      const int j = e / N;
+      ca[u] = (e < 32 * N && j < nr) ? c0[e] : 0.f;
+      cb[u] = (e < 32 * N && j + 32 < nr) ? c0[(size_t)32 * N + e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < per; ++u) {
+      const int e = threadIdx.x + u * NT;
+      if (e < 32 * N) {
+        const int j = e / N, n = e - j * N;
+        float2* p = Z + n * kRowsLd + j;
+        const float2 z = *p;
+        *p = make_float2(z.x * scale * ca[u], z.y * scale * cb[u]);
+      }
+    }
+  }
+  __syncthreads();
+  rows2_transform<-1, P1, P2>(Z, W, w, lane);
+  // split: X[k] = (Z[k] + conj Z[N-k]) / 2, Y[k] = (Z[k] - conj Z[N-k]) / (2i)
+  {
+    constexpr int total = 32 * H;
+    for (int e = threadIdx.x; e < total; e += NT) {
+      const int j = e / H, k = e - j * H;
+      const float2 z = Z[k * kRowsLd + j];
+      const float2 zc = Z[(k ? N - k : 0) * kRowsLd + j];
+      if (j < nr) out[(size_t)r0 * H + e] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+      if (j + 32 < nr) out[(size_t)(r0 + 32) * H + e] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+    }
+  }
+}
+
 template <typename R>
 static int row_tile(lrfg_ctx* ctx, int N, size_t* smem) {
   using V = typename CplxOf<R>::T;
@@ -314,10 +440,29 @@ void full_inverse(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_
                                                                                 N, g.H, TF, pl, W));
 }
 
+template <int P1, int P2>
+static void rows2_launch(lrfg_ctx* ctx, const FullGrid& g, float2* half_inout, const float* coef, float scale) {
+  constexpr int N = P1 * P2;
+  const size_t smem = sizeof(float2) * (size_t)N * (kRowsLd + 1);
+  const long long blocks = (g.rows + 63) / 64;
+  LRFG_REQUIRE(blocks < (1LL << 31), "too many rows");
+  const float2* W = twiddle_table<float>(ctx, N);
+  LRFG_CUDA(raise_smem_limit((const void*)rows2_mul_kernel<P1, P2>, smem));
+  LRFG_LAUNCH(ctx, KC_ROWS_FUSED, 5.0 * N * std::log2((double)N) * (double)g.rows,
+              (double)g.rows * (2.0 * g.H * sizeof(float2) + N * sizeof(float)),
+              rows2_mul_kernel<P1, P2><<<(unsigned)blocks, 32 * P2, smem, ctx->stream>>>(half_inout, coef, scale,
+                                                                                        half_inout, g.rows, W));
+}
+
 template <typename R>
 void full_rows_mul(lrfg_ctx* ctx, const FullGrid& g, typename CplxOf<R>::T* half_inout, const R* coef, R scale) {
   using V = typename CplxOf<R>::T;
   const int N = g.N[g.d - 1];
+  if constexpr (sizeof(R) == sizeof(float)) {
+    LRFG_CUDA(ensure_roots(ctx->device));
+    if (N == 243) return rows2_launch<27, 9>(ctx, g, half_inout, coef, scale);
+    if (N == 81) return rows2_launch<9, 9>(ctx, g, half_inout, coef, scale);
+  }
   FftPlan pl = make_plan(N, plan_radix<V>());
   LRFG_CUDA(ensure_roots(ctx->device));
   const V* W = twiddle_table<R>(ctx, N);

@@ -32,6 +32,24 @@ def test_fft_fibres_matches_oracle(ctx, N, sign):
         assert np.abs(got - ref).max() <= 1e-12 * N * np.abs(x).max(), (outer, inner)
 
 
+@pytest.mark.parametrize("N", [3, 9, 27, 45, 81, 135, 243, 729])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft_fibres_f32_matches_oracle(ctx, N, sign):
+    # FP32 passes of the mixed full format (81 and 243 take the two-pass kernel: 32 fibres a block, so
+    # inner sizes below, at and across 32 and batches whose tiles straddle two outer indices).  An FP32
+    # transform errs by a few u_32 log2(N) of the fibre's norm, sqrt(N) max|x| for these inputs.
+    rng = np.random.default_rng(3 * N)
+    for outer, inner in [(1, 1), (3, 7), (1, 32), (2, 33), (5, 122), (1, 300)]:
+        x = (rng.standard_normal((outer, N, inner)) + 1j * rng.standard_normal((outer, N, inner))).astype(np.complex64)
+        ref = _dft_axis1(x.astype(np.complex128), sign)
+        got = ctx.fft_fibres(torch.as_tensor(x, device="cuda"), sign).cpu().numpy()
+        tol = 4 * 2.0 ** -24 * np.log2(N + 1) * np.sqrt(N) * np.abs(x).max()
+        assert np.abs(got - ref).max() <= tol, (outer, inner, np.abs(got - ref).max() / tol)
+        y = torch.as_tensor(x, device="cuda")
+        ctx.fft_fibres(y, sign, out=y)
+        assert torch.equal(y.cpu(), torch.as_tensor(got)), (outer, inner)
+
+
 def test_fft_fibres_in_place_and_empty(ctx):
     x = torch.randn(4, 45, 9, dtype=torch.complex128, device="cuda")
     ref = ctx.fft_fibres(x.clone(), -1)
