@@ -312,8 +312,9 @@ __global__ void __launch_bounds__(32 * P2, 3) rows2_mul_kernel(const float2* in,
   for (int j = threadIdx.x; j < N; j += NT) W[j] = Wg[j];
   // Z[k] = X[k] + i Y[k] and Z[N - k] = conj X[k] + i conj Y[k] from the two half spectra
   {
-    constexpr int kU = 4;
+    // the tile's loads in two rounds of requests (two latencies per block)
     constexpr int total = 32 * H;
+    constexpr int kU = (total + 2 * NT - 1) / (2 * NT);
     for (int e0 = threadIdx.x; e0 < total; e0 += kU * NT) {
       float2 a[kU], b[kU];
 #pragma unroll
