@@ -27,6 +27,7 @@ stay in L2).  nvidia-smi samples clocks during the timed region.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -69,6 +70,8 @@ def parse():
                    help="also stop after this many iterations without a new smallest residual (1: the paper's rule, "
                         "Sec. 4.3; 0: off)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--micro", type=int, default=8,
+                   help="microstructures of the workload's recipe solved together in lockstep (0: skip)")
     p.add_argument("--format", choices=["tt", "tucker"], default="tt",
                    help="low-rank solution format of the timed solve (the coefficient is the same rank-10 TT; a "
                         "Tucker problem compresses it by HOSVD)")
@@ -78,6 +81,12 @@ def parse():
                         "microstructures of mixed N and rank through the serving executor; c5: a Poisson stream "
                         "of requests (d in {2,3}, N 63-729, rank tolerance 1e-6-1e-4) served as they arrive")
     p.add_argument("--count", type=int, default=64, help="c4: requests in the batch")
+    p.add_argument("--group", type=int, default=8,
+                   help="c4: requests of one shape the executor solves together in lockstep (1: one at a time)")
+    p.add_argument("--c4-rank-step", type=int, default=1, help="c4: TT ranks drawn over the multiples of this step")
+    p.add_argument("--c4-prec", choices=["fp64", "mixed"], default="fp64", help="c4: solve precision")
+    p.add_argument("--c4-sketch-over", type=int, default=0,
+                   help="c4: oversampling of the randomised rounding of the products (0: deterministic rounding)")
     p.add_argument("--workers", type=int, default=8, help="c4/c5: executor worker streams")
     p.add_argument("--rate", type=float, default=200.0, help="c5: mean arrival rate (requests/s)")
     p.add_argument("--rank-cap", type=int, default=30, help="c5: rank cap of the tolerance truncation")
@@ -485,6 +494,11 @@ def run_ours(args):
     Pmx6.free()
     Pmx.free()
 
+    # a batch of microstructures of this workload's recipe (seeds SEED + 1 .. SEED + count), one TT solve each
+    # with the timed step's options, solved together in lockstep (lrfg_problems_solve), against their full FP64
+    # solves
+    micro = microstructure_batch(ctx, args, lr_fmt, stream, flush, count=args.micro)
+
     # the configuration of the previous measurements: TT rank 10, deterministic rounding, stop on increase
     P10 = ctx.problem(a_tt, lr_fmt, rank=10, pinv_eps=args.pinv_eps, tol=1e-12, maxit=60, stop_on_increase=True)
     P10.solve(E, want_field=False)
@@ -528,6 +542,7 @@ def run_ours(args):
             "tt_vs_full_fp64": solves_per_s / world / (1e3 / statistics.median(full_ms)),
             "tt_mixed": tt_mixed,
             "homogenised_tensor_6_solves": tensor,
+            "microstructure_batch": micro,
             "tt_rank10_deterministic": {"solves_per_s": 1e3 / statistics.median(ms10), "iters": r10[-1].iters,
                                         "aeff_rel_err": abs(r10[-1].Aeff - full_res.Aeff) / full_res.Aeff},
             "full_class_rooflines": full_roof,
@@ -550,6 +565,56 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+def microstructure_batch(ctx, args, lr_fmt, stream, flush, count=8):
+    """`count` seeded microstructures of the workload's recipe (lognormal SE-GRF, seeds SEED + 1 ..), each
+    compressed to the coefficient rank: their TT solves (the timed step's options) together in lockstep through
+    lrfg_problems_solve, FP64 and LRFG_MIXED, against their full FP64 solves one after the other."""
+    import torch
+    import paper_1902_07455_gb300 as lrfg
+    from synthetic import lognormal_grf
+    if count < 1:
+        return None
+    E = [1.0, 0.0, 0.0]
+    dev = f"cuda:{torch.cuda.current_device()}"
+    coeffs, fulls = [], []
+    for i in range(count):
+        A = torch.as_tensor(lognormal_grf(3, args.N, ell=0.2, var=1.0, seed=SEED + 1 + i), device=dev)
+        a = ctx.tt_compress(A, args.coeff_rank)
+        del A
+        coeffs.append(a)
+    full_ms = 0.0
+    for a in coeffs:
+        a_full = ctx.tt_expand(a)
+        P = ctx.problem(a_full, lrfg.FULL, tol=1e-8, maxit=2000)
+        ms1, r1 = timed_solves(P, E, 1, stream, flush)
+        full_ms += ms1[0]
+        fulls.append(r1[0].Aeff)
+        P.free()
+        del a_full
+    out = {"count": count, "seeds": [SEED + 1 + i for i in range(count)],
+           "full_fp64": {"solves_per_s": count * 1e3 / full_ms, "seconds": full_ms / 1e3}}
+    for name, prec in (("tt_lockstep", lrfg.FP64), ("tt_mixed_lockstep", lrfg.MIXED)):
+        Ps = [ctx.problem(a, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tt_tol, maxit=args.maxit,
+                          stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=prec,
+                          rank_start=args.rank_start, rank_step=args.rank_step) for a in coeffs]
+        lrfg.Problem.solve_together(Ps, [E] * count)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs = lrfg.Problem.solve_together(Ps, [E] * count)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        errs = [abs(r.Aeff - f) / f for r, f in zip(rs, fulls)]
+        out[name] = {"solves_per_s": count * 1e3 / ms, "seconds": ms / 1e3, "iters": [r.iters for r in rs],
+                     "max_rel_err_vs_full": max(errs), "meets_1e-6": max(errs) <= 1e-6,
+                     "vs_full_fp64": (count * 1e3 / ms) / out["full_fp64"]["solves_per_s"]}
+        for P in Ps:
+            P.free()
+    return out
 
 
 def solve_host(ctx, host_cores, args, E):
@@ -728,13 +793,13 @@ def run_c3(args):
     ctx.close()
 
 
-def c4_requests(count, seed=SEED):
+def c4_requests(count, seed=SEED, rank_step=1):
     """Seeded batch: half lognormal SE-GRF (l uniform in [0.1, 0.3], variance (ln(contrast)/4)^2 so that
     exp(+-2 sigma) spans the contrast), half tanh-smoothed inclusions (sphere or cube, radius / half-side
     uniform in [0.15, 0.35]); contrast log-uniform in [5, 100]; N uniform in {45, 81, 135, 243}; TT rank
-    uniform in [5, 30].  Grid coefficients (lognormal, sphere) are TT-compressed to rank 10 on the GPU
-    here, before timing; the cube is its exact rank-2 TT.  Each request: (TT carriages on the host, rank,
-    description)."""
+    uniform in [5, 30] (rank_step > 1: uniform over the multiples of rank_step there).  Grid coefficients
+    (lognormal, sphere) are TT-compressed to rank 10 on the GPU here, before timing; the cube is its exact
+    rank-2 TT.  Each request: (TT carriages on the host, rank, description)."""
     import torch
     import paper_1902_07455_gb300 as lrfg
     from synthetic import lognormal_grf, smoothed_cube, smoothed_sphere
@@ -743,7 +808,10 @@ def c4_requests(count, seed=SEED):
     out = []
     for i in range(count):
         N = int(rng.choice([45, 81, 135, 243]))
-        r = int(rng.integers(5, 31))
+        if rank_step > 1:
+            r = rank_step * int(rng.integers(-(-5 // rank_step), 30 // rank_step + 1))
+        else:
+            r = int(rng.integers(5, 31))
         contrast = float(np.exp(rng.uniform(np.log(5.0), np.log(100.0))))
         if i % 2 == 0:
             ell = float(rng.uniform(0.1, 0.3))
@@ -767,13 +835,13 @@ def c4_requests(count, seed=SEED):
     return out
 
 
-def run_batch(B, reqs, maxit, pinv_eps):
+def run_batch(B, reqs, maxit, pinv_eps, prec=0, sketch_over=0):
     """Submit every request at once to executor B; returns (seconds from first submission to last
     completion, BatchResults)."""
     import paper_1902_07455_gb300 as lrfg
     t0 = time.perf_counter()
-    tickets = [B.submit(c, [1.0, 0.0, 0.0], lrfg.TT, rank=r, pinv_eps=pinv_eps, tol=1e-12, maxit=maxit)
-               for c, r, _ in reqs]
+    tickets = [B.submit(c, [1.0, 0.0, 0.0], lrfg.TT, rank=r, pinv_eps=pinv_eps, tol=1e-12, maxit=maxit, prec=prec,
+                        sketch_over=sketch_over) for c, r, _ in reqs]
     res = [B.wait(t) for t in tickets]
     return time.perf_counter() - t0, res
 
@@ -786,31 +854,39 @@ def run_c4(args):
     from paper_1902_07455_gb300 import build
     build.build()
     t_gen = time.perf_counter()
-    reqs = c4_requests(args.count)
+    reqs = c4_requests(args.count, rank_step=args.c4_rank_step)
     t_gen = time.perf_counter() - t_gen
     import paper_1902_07455_gb300 as lrfg
+    prec = lrfg.MIXED if args.c4_prec == "mixed" else lrfg.FP64
+    kw = dict(prec=prec, sketch_over=args.c4_sketch_over)
     # a warm pass (plans, twiddles and pools of every worker context), then the timed pass
-    with lrfg.Batch(0, workers=args.workers) as B:
-        run_batch(B, reqs, args.maxit, args.pinv_eps)
+    with lrfg.Batch(0, workers=args.workers, group=args.group) as B:
+        run_batch(B, reqs, args.maxit, args.pinv_eps, **kw)
         with ClockSampler(0) as clk:
-            dt, res = run_batch(B, reqs, args.maxit, args.pinv_eps)
-    # one worker: warmed on the largest requests, then the whole batch
+            dt, res = run_batch(B, reqs, args.maxit, args.pinv_eps, **kw)
+    # one worker, one request at a time: warmed on the largest requests, then the whole batch
     big = sorted(reqs, key=lambda q: -q[0][1].shape[1] * q[1] ** 2)[:4]
     with lrfg.Batch(0, workers=1) as B1:
-        run_batch(B1, big, args.maxit, args.pinv_eps)
-        dt1, res1 = run_batch(B1, reqs, args.maxit, args.pinv_eps)
+        run_batch(B1, big, args.maxit, args.pinv_eps, **kw)
+        dt1, res1 = run_batch(B1, reqs, args.maxit, args.pinv_eps, **kw)
     lat = [b.total_s for b in res]
     same = all(a.result.Aeff == b.result.Aeff and a.result.iters == b.result.iters for a, b in zip(res, res1))
+    diff = max(abs(a.result.Aeff - b.result.Aeff) / abs(b.result.Aeff) for a, b in zip(res, res1))
     line = {
         "metric": METRIC, "value": len(reqs) / dt, "unit": "solves/s", "n_gpus": 1, "steps": 1,
         "warmup": 1, "ms_per_step": 1e3 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64" if prec == lrfg.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": f"batch of {len(reqs)} seeded d=3 microstructures (half lognormal SE-GRF, half "
                                f"tanh-smoothed sphere/cube inclusions, contrast 5-100), N in {{45,81,135,243}}, "
-                               f"TT rank 5-30, coefficient TT rank 10 (cube: exact 2), TT MinRes, FP64",
-                   "count": len(reqs), "workers": args.workers, "maxit": args.maxit, "pinv_eps": args.pinv_eps},
+                               f"TT rank 5-30" + (f" in steps of {args.c4_rank_step}" if args.c4_rank_step > 1 else "")
+                               + f", coefficient TT rank 10 (cube: exact 2), TT MinRes, "
+                               + ("FP64" if prec == lrfg.FP64 else "LRFG_MIXED (FP32 transforms and sketch side, "
+                                                                   "FP64 residual)"),
+                   "count": len(reqs), "workers": args.workers, "group": args.group, "maxit": args.maxit,
+                   "pinv_eps": args.pinv_eps, "sketch_over": args.c4_sketch_over, "precision": args.c4_prec},
         "serial_solves_per_s": len(reqs) / dt1, "overlap_speedup": dt1 / dt,
-        "bitwise_equal_to_serial": same,
+        "bitwise_equal_to_serial": same, "max_rel_aeff_diff_vs_serial": diff,
+        "groups": sorted(collections.Counter(b.group for b in res).items()),
         "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
         "run_s_sum": sum(b.run_s for b in res), "iters_mean": float(np.mean([b.result.iters for b in res])),
         "e2e": {"value": len(reqs) / dt, "unit": "solves/s",

@@ -365,6 +365,17 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* problem, const double* E, const lrfg
  * restart from their best iterates at the next rank, which leaves each item's sequence that of its own solve.
  * Otherwise the nb solves run one after the other.  Status as lrfg_problem_solve (LRFG_ENOCONV if any right-hand side reached maxit). */
 lrfg_status lrfg_problem_solve_many(lrfg_problem* problem, int nb, const double* E, lrfg_result* res);
+/* Solve np problems of one shape together (a batch of microstructures): problem i for E_i (row i of E, a host
+ * array of np x d doubles); res[i] receives its result (res[i].seconds is the wall time of the whole call).  The
+ * problems must belong to one context.  When every problem is one lrfg_problem_solve_many runs in lockstep
+ * (isotropic GaNi LRFG_TT, rank_tol = 0), all have the same grid, equal options (after their defaults are applied)
+ * and equal coefficient TT ranks, and np d <= 32, their minimal-residual iterations (Sec. 4.3) run in lockstep: one
+ * launch sequence per operator application (Eq. (Pls_lowrank)), truncation and inner product for all np, item i
+ * with problem i's coefficient and right-hand side and its own step length, best iterate and stopping test (with
+ * rank adaptation, the shared rank as in lrfg_problem_solve_many); each result equals problem i's own solve up to
+ * the rounding order of the batched products.  Otherwise the problems are solved one after the other.  LRFG_EINVAL
+ * for np < 1, a null problem, problems of different contexts or of different d; otherwise status as lrfg_problem_solve_many. */
+lrfg_status lrfg_problems_solve(int np, lrfg_problem* const* problems, const double* E, lrfg_result* res);
 /* The homogenised tensor A_eff (d x d, symmetric) of Eq. (homog): the diagonal A_aa from the solves with
  * E = e_a, each off-diagonal entry by polarisation of the quadratic form q(E) = A_eff E.E (Sec. 2.1),
  * A_ab = (q(e_a + e_b) - q(e_a) - q(e_b)) / 2 — d (d + 1) / 2 solves with the problem's options, run
@@ -391,6 +402,13 @@ lrfg_status lrfg_solve(lrfg_ctx* ctx, const lrfg_coeff* coeff, const double* E, 
  * same shape (d, N, coefficient format and rank, solution format, precision, rank), or an estimate
  * from the sizes before one ran.  Each request is one lrfg_solve on its worker's context, so its
  * result is that of the same solve run alone.
+ *
+ * Batching across requests (lrfg_batch_set_group, off by default): a worker that takes the head request also
+ * takes the queued requests that one lockstep solve can share with it (isotropic GaNi LRFG_TT solves with
+ * rank_tol = 0 of TT coefficients with equal grid and ranks, equal options), in queue order while their
+ * footprints fit, up to the group size, and solves them together by lrfg_problems_solve: one launch sequence per
+ * operator application, truncation and inner product for all of them.  Each result then equals its own solve up
+ * to the rounding order of the batched products.  Requests that arrive while a group runs form the next group.
  * ------------------------------------------------------------------------------------------- */
 
 typedef struct lrfg_batch lrfg_batch;
@@ -399,8 +417,9 @@ typedef struct {
   double queue_s;    /* submission to start (waiting for a worker and for HBM) */
   double run_s;      /* start to completion */
   double total_s;    /* submission to completion: the request's latency */
-  double peak_bytes; /* device pool high-water mark of the solve */
+  double peak_bytes; /* device pool high-water mark of the solve (of the whole group's lockstep solve) */
   int worker;        /* worker that ran it */
+  int group;         /* requests solved together with it in lockstep, itself included (1: alone) */
   char message[200]; /* lrfg_last_error of the failed solve ("" on success) */
 } lrfg_batch_report;
 
@@ -412,6 +431,9 @@ lrfg_status lrfg_batch_create(lrfg_batch** out, int device, int workers, size_t 
  * sizes give LRFG_EINVAL here; everything else lrfg_solve checks is reported by lrfg_batch_poll. */
 lrfg_status lrfg_batch_submit(lrfg_batch* batch, const lrfg_coeff* coeff, const double* E, const lrfg_opts* opts,
                               unsigned long long* ticket);
+/* Requests of one lockstep key taken together, at most max_requests (1..32; 1, the default, takes them one
+ * at a time).  It applies to groups formed after the call.  LRFG_EINVAL outside 1..32. */
+lrfg_status lrfg_batch_set_group(lrfg_batch* batch, int max_requests);
 /* *ready = 1 when the request has completed; then *solve_status (lrfg_solve's status), *res and
  * *report (each may be NULL) are filled and the ticket is retired (a second poll gives LRFG_EINVAL).
  * wait = 1 blocks until it completes.  LRFG_EINVAL for an unknown or retired ticket. */

@@ -598,6 +598,24 @@ class Problem:
         return [Result(r.Aeff, r.iters, r.rel_resid, bool(r.converged), r.applies, list(r.ranks)[: self.d + 1],
                        r.seconds, st) for r in res]
 
+    @staticmethod
+    def solve_together(problems, Es):
+        """Solve problem i for row i of Es (len(problems) x d) through lrfg_problems_solve: in lockstep when the
+        problems share grid, options and coefficient ranks (a batch of microstructures of one shape), else one
+        after the other; returns the list of Results."""
+        problems = list(problems)
+        if not problems:
+            raise ValueError("no problems")
+        ctx, d = problems[0].ctx, problems[0].d
+        Es = np.ascontiguousarray(np.asarray(Es, dtype=np.float64).reshape(len(problems), d))
+        hs = (C.c_void_p * len(problems))(*[p.h for p in problems])
+        res = (L.lrfg_result * len(problems))()
+        st = ctx.lib.lrfg_problems_solve(len(problems), hs, Es.ctypes.data_as(C.POINTER(C.c_double)), res)
+        if st not in (L.LRFG_OK, L.LRFG_ENOCONV):
+            ctx.check(st)
+        return [Result(r.Aeff, r.iters, r.rel_resid, bool(r.converged), r.applies, list(r.ranks)[: d + 1],
+                       r.seconds, st) for r in res]
+
     def aeff(self, E, field: Field) -> float:
         out = C.c_double()
         self.ctx.check(self.ctx.lib.lrfg_problem_aeff(self.h, _dvec(E), field.h, C.byref(out)))
@@ -690,15 +708,17 @@ class BatchResult:
     total_s: float   # latency: submission to completion
     peak_bytes: float
     worker: int
+    group: int = 1   # requests solved together with it in lockstep (itself included)
 
 
 class Batch:
     """The serving executor of the library (``lrfg_batch_*``): ``workers`` threads, each with its own
     non-blocking stream and context, run submitted solves concurrently in FIFO order; a request starts
     when a worker is free and its HBM footprint fits in ``budget`` bytes (0: no cap) beside the requests
-    running.  Coefficients are host arrays, copied at submission."""
+    running.  Coefficients are host arrays, copied at submission.  ``group`` > 1: a worker takes up to that many
+    queued requests of one shape together and solves them in lockstep (lrfg_batch_set_group)."""
 
-    def __init__(self, device: int = 0, workers: int = 4, budget: int = 0):
+    def __init__(self, device: int = 0, workers: int = 4, budget: int = 0, group: int = 1):
         self.lib = L.load()
         h = C.c_void_p()
         st = self.lib.lrfg_batch_create(C.byref(h), int(device), int(workers), int(budget))
@@ -706,11 +726,17 @@ class Batch:
             raise LrfgError(st, "lrfg_batch_create failed")
         self.h = h
         self.workers = int(workers)
+        if int(group) != 1:
+            st = self.lib.lrfg_batch_set_group(self.h, int(group))
+            if st != L.LRFG_OK:
+                self.close()
+                raise LrfgError(st, "lrfg_batch_set_group rejected the group size")
+        self.group = int(group)
 
     def submit(self, coeff, E, fmt: int, rank: int = 10, pinv_eps: float = 0.1, tol: float = 1e-8,
                maxit: int = 200, stop_on_increase: bool = True, prec: int = L.LRFG_FP64, rank_tol: float = 0.0,
                coeff_rank: int = 0, rank_start: int = 0, rank_step: int = 1, B=None,
-               disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0) -> int:
+               disc: int = L.LRFG_GANI, sketch_over: int = 0, sketch_seed: int = 0, sketch_keep: bool = False) -> int:
         c, keep = _host_coeff(coeff)
         _set_b(c, B)
         o = L.lrfg_opts()
@@ -718,7 +744,7 @@ class Batch:
         o.tol, o.maxit, o.stop_on_increase = float(tol), int(maxit), int(bool(stop_on_increase))
         o.rank_tol, o.coeff_rank = float(rank_tol), int(coeff_rank)
         o.rank_start, o.rank_step, o.disc = int(rank_start), int(rank_step), int(disc)
-        o.sketch_over, o.sketch_seed = int(sketch_over), int(sketch_seed)
+        o.sketch_over, o.sketch_seed, o.sketch_keep = int(sketch_over), int(sketch_seed), int(bool(sketch_keep))
         t = C.c_ulonglong()
         st = self.lib.lrfg_batch_submit(self.h, C.byref(c), _dvec(E), C.byref(o), C.byref(t))
         del keep
@@ -741,7 +767,7 @@ class Batch:
             raise LrfgError(sst.value, f"request {ticket}: {tm.message.decode(errors='replace')}")
         r = Result(res.Aeff, res.iters, res.rel_resid, bool(res.converged), res.applies, list(res.ranks), res.seconds,
                    sst.value)
-        return BatchResult(r, tm.queue_s, tm.run_s, tm.total_s, tm.peak_bytes, tm.worker)
+        return BatchResult(r, tm.queue_s, tm.run_s, tm.total_s, tm.peak_bytes, tm.worker, tm.group)
 
     def wait(self, ticket: int) -> BatchResult:
         return self.poll(ticket, wait=True)

@@ -45,7 +45,7 @@ class lrfg_result(C.Structure):
 
 class lrfg_batch_report(C.Structure):
     _fields_ = [("queue_s", C.c_double), ("run_s", C.c_double), ("total_s", C.c_double),
-                ("peak_bytes", C.c_double), ("worker", C.c_int), ("message", C.c_char * 200)]
+                ("peak_bytes", C.c_double), ("worker", C.c_int), ("group", C.c_int), ("message", C.c_char * 200)]
 
 
 _P = C.c_void_p
@@ -97,6 +97,7 @@ SIGNATURES = {
     "lrfg_problem_aeff": (_ST, [_P, C.POINTER(_D), _P, C.POINTER(_D)]),
     "lrfg_problem_solve_many": (_ST, [_P, _I, C.POINTER(_D), C.POINTER(lrfg_result)]),
     "lrfg_problem_aeff_tensor": (_ST, [_P, C.POINTER(_D), C.POINTER(lrfg_result)]),
+    "lrfg_problems_solve": (_ST, [_I, C.POINTER(_P), C.POINTER(_D), C.POINTER(lrfg_result)]),
     "lrfg_solve": (_ST, [_P, C.POINTER(lrfg_coeff), C.POINTER(_D), C.POINTER(lrfg_opts), C.POINTER(lrfg_result),
                          C.POINTER(_P)]),
     "lrfg_field_from_full": (_ST, [_P, _I, C.POINTER(_I), _P, _I, C.POINTER(_P)]),
@@ -111,6 +112,7 @@ SIGNATURES = {
     "lrfg_batch_poll": (_ST, [_P, C.c_ulonglong, _I, C.POINTER(_I), C.POINTER(_ST), C.POINTER(lrfg_result),
                               C.POINTER(lrfg_batch_report)]),
     "lrfg_batch_info": (_ST, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_size_t)]),
+    "lrfg_batch_set_group": (_ST, [_P, _I]),
     "lrfg_batch_destroy": (_ST, [_P]),
 }
 

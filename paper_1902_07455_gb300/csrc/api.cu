@@ -1044,11 +1044,15 @@ bool lockstep_ok(const lrfg_problem* P) {
 }
 
 // The operator of lr_apply on nb items at once (items of identical ranks, stored item after item): the gradient,
-// material, divergence, sum and preconditioner stages each take one launch sequence for all items.
-void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, bool mixed = false) {
+// material, divergence, sum and preconditioner stages each take one launch sequence for all items.  Item b's
+// material product takes the coefficient of problem Ps[b] (Ps null: P's for every item); the problems share P's
+// grid, options, coefficient ranks, exponential sum and sketch.
+void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, bool mixed = false,
+                 lrfg_problem* const* Ps = nullptr) {
   lrfg_ctx* ctx = P->ctx;
   const int d = P->d, nb = v.nb;
   const TTView a = view_of(P->a_tt);
+  auto coeff_core = [&](int b, int j) -> const double* { return Ps ? Ps[b]->a_tt.core[j].get() : a.core[j]; };
   TTView omv;
   const TTView* om = sketch_for(P, r, omv);
   // gradient carriages D_a v_a of every item (items contiguous: one launch per mode)
@@ -1077,8 +1081,10 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, boo
     }
     for (int al = 0; al < d; ++al)
       for (int b = 0; b < nb; ++b)
-        for (int j = 0; j < d; ++j)
+        for (int j = 0; j < d; ++j) {
           z.y[j][al * nb + b] = (j == al ? grad[j].get() : v.core[j]) + (size_t)b * v.elems(j);
+          if (Ps) z.xi[j][al * nb + b] = coeff_core(b, j);
+        }
     tt_round_sketch(ctx, z, *om, r, w, 0.0, mixed, !P->opts.sketch_keep);
   } else {
     TTBatch kr;
@@ -1086,7 +1092,7 @@ void apply_batch(lrfg_problem* P, const TTBatchView& v, TTBatch& out, int r, boo
     for (int al = 0; al < d; ++al)
       for (int b = 0; b < nb; ++b)
         for (int j = 0; j < d; ++j)
-          khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1],
+          khatri_rao(ctx, coeff_core(b, j), a.r[j], a.N[j], a.r[j + 1],
                      (j == al ? grad[j].get() : v.core[j]) + (size_t)b * v.elems(j), v.r[j], v.r[j + 1],
                      kr.core[j].get() + (size_t)(al * nb + b) * kr.elems(j));
     tt_round_batch(ctx, batch_view(kr), r, w, 0.0);
@@ -1130,8 +1136,11 @@ void ttb_copy_item(lrfg_ctx* ctx, const TTBatch& src, TTBatch& dst, int b) {
 // right-hand sides are rebuilt at it and every unfinished item restarts from its best iterate with its residual
 // recomputed.  Each item thus follows the rank-adapting iteration of solve_tt, only waiting for the others before
 // a rise.  At the cap a failure to decrease ends the item, as there.
-void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
+// Ps (null: P for every item): item i solves problem Ps[i] (its own coefficient; grid, coefficient ranks and options
+// those of P), so several microstructures of one shape share every launch.
+void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res, lrfg_problem* const* Ps = nullptr) {
   lrfg_ctx* ctx = P->ctx;
+  auto prob = [&](int i) { return Ps ? Ps[i] : P; };
   const int d = P->d, cap = P->opts.rank;
   const bool adapt = P->opts.rank_start > 0;
   int rk = adapt ? std::min(P->opts.rank_start, cap) : cap;
@@ -1174,7 +1183,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
     std::vector<TT> bs(nb);
     std::vector<const TT*> ptr(nb);
     for (int i = 0; i < nb; ++i) {
-      lr_rhs(P, E + (size_t)i * d, bs[i], rk);
+      lr_rhs(prob(i), E + (size_t)i * d, bs[i], rk);
       ptr[i] = &bs[i];
     }
     pack(ptr, b);
@@ -1199,7 +1208,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
   std::vector<double> nr(nb, 1.0);
   auto residual = [&]() {
     TTBatch cu;
-    apply_batch(P, batch_view(u), cu, rk);
+    apply_batch(P, batch_view(u), cu, rk, false, Ps);
     ++applies;
     TTBatchView t[2] = {batch_view(b), batch_view(cu)};
     const double hs[2] = {1.0, -1.0};
@@ -1279,7 +1288,7 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
     }
     // q = C r; omega = (q, r) / (q, q)
     TTBatch q;
-    apply_batch(P, batch_view(r), q, rk, P->opts.prec == LRFG_MIXED);
+    apply_batch(P, batch_view(r), q, rk, P->opts.prec == LRFG_MIXED, Ps);
     ++applies;
     host_dots(q, q, &q, &r);
     for (int i = 0; i < nb; ++i) omega[i] = (h[i] > 0.0) ? h[nb + i] / h[i] : 0.0;
@@ -1318,10 +1327,10 @@ void solve_tt_many(lrfg_problem* P, const double* E, int nb, lrfg_result* res) {
       int r1[4] = {1, 1, 1, 1};
       tt_alloc(ctx, z, d, P->N, r1);
       for (int j = 0; j < d; ++j) fill(ctx, z.core[j].get(), 0.0, P->N[j]);
-      o.Aeff = lr_aeff(P, E + (size_t)i * d, view_of(z));
+      o.Aeff = lr_aeff(prob(i), E + (size_t)i * d, view_of(z));
       for (int j = 0; j < 4; ++j) o.ranks[j] = 1;
     } else {
-      o.Aeff = lr_aeff(P, E + (size_t)i * d, view_of(best_u[i]));
+      o.Aeff = lr_aeff(prob(i), E + (size_t)i * d, view_of(best_u[i]));
       for (int j = 0; j < 4; ++j) o.ranks[j] = j <= d ? best_u[i].r[j] : 1;
     }
   }
@@ -1941,6 +1950,56 @@ lrfg_status lrfg_problem_solve_many(lrfg_problem* P, int nb, const double* E, lr
       res[i].seconds = sec;
       if (!res[i].converged && !(P->opts.fmt != LRFG_FULL && P->opts.stop_on_increase && res[i].applies > 0 &&
                                  res[i].iters < P->opts.maxit))
+        noconv = true;
+    }
+  });
+  if (st == LRFG_OK && noconv) return LRFG_ENOCONV;
+  return st;
+}
+
+// whether problems P and Q can share one lockstep solve: the same grid, options and coefficient TT ranks
+static bool same_shape(const lrfg_problem* P, const lrfg_problem* Q) {
+  if (P->ctx != Q->ctx || P->d != Q->d) return false;
+  for (int j = 0; j < P->d; ++j)
+    if (P->N[j] != Q->N[j]) return false;
+  for (int j = 0; j <= P->d; ++j)
+    if (P->a_tt.r[j] != Q->a_tt.r[j]) return false;
+  const lrfg_opts &a = P->opts, &b = Q->opts;
+  return a.fmt == b.fmt && a.prec == b.prec && a.rank == b.rank && a.pinv_eps == b.pinv_eps && a.tol == b.tol &&
+         a.maxit == b.maxit && a.stop_on_increase == b.stop_on_increase && a.rank_tol == b.rank_tol &&
+         a.rank_start == b.rank_start && a.rank_step == b.rank_step && a.disc == b.disc &&
+         a.sketch_over == b.sketch_over && a.sketch_seed == b.sketch_seed && a.sketch_keep == b.sketch_keep;
+}
+
+lrfg_status lrfg_problems_solve(int np, lrfg_problem* const* Ps, const double* E, lrfg_result* res) {
+  if (np < 1 || !Ps || !Ps[0]) return LRFG_EINVAL;
+  lrfg_problem* P = Ps[0];
+  bool noconv = false;
+  lrfg_status st = guard(P->ctx, [&] {
+    LRFG_REQUIRE(E && res, "null argument");
+    for (int i = 0; i < np; ++i) {
+      LRFG_REQUIRE(Ps[i] && Ps[i]->ctx == P->ctx, "problems must share one context");
+      LRFG_REQUIRE(Ps[i]->d == P->d, "problems must have the same dimension d");
+    }
+    for (int i = 0; i < np * P->d; ++i) LRFG_REQUIRE(std::isfinite(E[i]), "E must be finite");
+    bool together = np * P->d <= kMaxSketchItems;
+    for (int i = 0; i < np && together; ++i) together = lockstep_ok(Ps[i]) && same_shape(P, Ps[i]);
+    auto t0 = std::chrono::steady_clock::now();
+    if (together) {
+      solve_tt_many(P, E, np, res, Ps);
+      LRFG_CUDA(cudaStreamSynchronize(P->ctx->stream));
+    } else {
+      for (int i = 0; i < np; ++i) {
+        const lrfg_status s1 = lrfg_problem_solve(Ps[i], E + (size_t)i * P->d, res + i, nullptr);
+        if (s1 != LRFG_OK && s1 != LRFG_ENOCONV) fail(s1, "problem %d: %s", i, P->ctx->last_error.c_str());
+      }
+    }
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < np; ++i) {
+      res[i].seconds = sec;
+      const lrfg_opts& o = Ps[i]->opts;
+      if (!res[i].converged &&
+          !(o.fmt != LRFG_FULL && o.stop_on_increase && res[i].applies > 0 && res[i].iters < o.maxit))
         noconv = true;
     }
   });

@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <deque>
 #include <memory>
+#include <string>
 #include <thread>
 #include <tuple>
 
@@ -34,9 +35,25 @@ struct Request {
   double E[3] = {0, 0, 0};
   lrfg_opts opts{};
   ShapeKey key{};
+  std::string group_key;  // requests with equal non-empty keys may be solved together in lockstep
   size_t footprint = 0;
   Clock::time_point submitted;
 };
+
+// The key of the requests that one lockstep solve (lrfg_problems_solve) can take together: isotropic GaNi TT
+// solves at a fixed rank or with rank adaptation, of TT coefficients of equal grid and ranks, with equal options.
+// Empty for every other request.
+std::string lockstep_key(const lrfg_coeff& c, const lrfg_opts& o) {
+  if (c.fmt != LRFG_TT || o.fmt != LRFG_TT || o.disc != LRFG_GANI || o.rank_tol != 0.0) return std::string();
+  for (double b : c.B)
+    if (b != 0.0) return std::string();
+  char k[512];
+  std::snprintf(k, sizeof(k), "%d|%d,%d,%d|%d,%d,%d,%d|%d|%d|%.17g|%.17g|%d|%d|%d|%d|%d|%u|%d", c.d, c.N[0], c.N[1],
+                c.d == 3 ? c.N[2] : 1, c.tt.r[0], c.tt.r[1], c.tt.r[2], c.d == 3 ? c.tt.r[3] : 1, (int)o.prec, o.rank,
+                o.pinv_eps, o.tol, o.maxit, o.stop_on_increase, o.rank_start, o.rank_step, o.sketch_over,
+                o.sketch_seed, o.sketch_keep);
+  return std::string(k);
+}
 
 struct Done {
   bool ready = false;
@@ -93,7 +110,8 @@ struct lrfg_batch {
   std::condition_variable cv_work, cv_done;
   std::deque<std::unique_ptr<Request>> queue;
   std::map<unsigned long long, Done> done;
-  std::map<ShapeKey, size_t> measured;  // pool high-water mark of the last solve of each shape
+  int group_max = 1;                    // requests of one lockstep key a worker takes together (1: one at a time)
+  std::map<ShapeKey, size_t> measured;  // pool high-water mark per request of the last solve of each shape
   std::vector<size_t> reserved;         // bytes each worker's pool holds
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
@@ -108,12 +126,61 @@ size_t total(const std::vector<size_t>& v) {
   return s;
 }
 
+// one request's status from its result, as lrfg_problem_solve gives it
+lrfg_status member_status(const lrfg_result& r, const lrfg_opts& o) {
+  const bool stopped = o.stop_on_increase && r.applies > 0 && r.iters < o.maxit;
+  return (r.converged || stopped) ? LRFG_OK : LRFG_ENOCONV;
+}
+
+// Solve the requests of one group on the worker's context: one request by lrfg_solve; several (of one lockstep
+// key) by lrfg_problems_solve over their problems, in lockstep.  st[i] / res[i] / msg[i] per request.
+void run_group(lrfg_ctx* ctx, std::vector<std::unique_ptr<Request>>& g, std::vector<lrfg_status>& st,
+               std::vector<lrfg_result>& res, std::vector<std::string>& msg) {
+  const size_t n = g.size();
+  st.assign(n, LRFG_OK);
+  res.assign(n, lrfg_result{});
+  msg.assign(n, std::string());
+  if (n == 1) {
+    st[0] = lrfg_solve(ctx, &g[0]->coeff, g[0]->E, &g[0]->opts, &res[0], nullptr);
+    if (st[0] != LRFG_OK) msg[0] = lrfg_last_error(ctx);
+    return;
+  }
+  std::vector<lrfg_problem*> ps;
+  std::vector<size_t> who;
+  std::vector<double> Es;
+  for (size_t i = 0; i < n; ++i) {
+    lrfg_problem* P = nullptr;
+    st[i] = lrfg_problem_create(ctx, &g[i]->coeff, &g[i]->opts, &P);
+    if (st[i] != LRFG_OK) {
+      msg[i] = lrfg_last_error(ctx);
+      continue;
+    }
+    ps.push_back(P);
+    who.push_back(i);
+    for (int j = 0; j < g[i]->coeff.d; ++j) Es.push_back(g[i]->E[j]);
+  }
+  if (!ps.empty()) {
+    std::vector<lrfg_result> rs(ps.size());
+    const lrfg_status s1 = lrfg_problems_solve((int)ps.size(), ps.data(), Es.data(), rs.data());
+    const std::string m1 = s1 == LRFG_OK ? std::string() : std::string(lrfg_last_error(ctx));
+    for (size_t k = 0; k < ps.size(); ++k) {
+      const size_t i = who[k];
+      res[i] = rs[k];
+      st[i] = (s1 == LRFG_OK || s1 == LRFG_ENOCONV) ? member_status(rs[k], g[i]->opts) : s1;
+      if (st[i] == LRFG_ENOCONV) msg[i] = lrfg_strerror(LRFG_ENOCONV);
+      else if (st[i] != LRFG_OK) msg[i] = m1;
+      lrfg_problem_free(ps[k]);
+    }
+  }
+}
+
 void worker_loop(lrfg_batch* B, int w) {
   cudaSetDevice(B->device);
   lrfg_ctx* ctx = B->ctxs[w];
   DevicePool* pool = ctx->pool;
   for (;;) {
-    std::unique_ptr<Request> req;
+    std::vector<std::unique_ptr<Request>> g;
+    size_t footprint = 0;
     {
       std::unique_lock<std::mutex> lock(B->mu);
       // FIFO admission: the head request starts when its footprint fits beside those in flight; a
@@ -128,38 +195,67 @@ void worker_loop(lrfg_batch* B, int w) {
         if (B->stopping) return;
         continue;
       }
-      req = std::move(B->queue.front());
+      auto fp = [&](Request& r) {
+        auto m = B->measured.find(r.key);
+        if (m != B->measured.end()) r.footprint = m->second;
+        return r.footprint;
+      };
+      g.push_back(std::move(B->queue.front()));
       B->queue.pop_front();
-      auto m = B->measured.find(req->key);
-      if (m != B->measured.end()) req->footprint = m->second;
-      B->in_flight_bytes += req->footprint;
+      footprint = fp(*g[0]);
+      // continuous batching across requests: queued requests of the head's lockstep key join it (in queue
+      // order, while their footprints fit), so that one launch sequence serves all of them
+      const std::string key = g[0]->group_key;
+      if (B->group_max > 1 && !key.empty()) {
+        for (auto it = B->queue.begin(); it != B->queue.end() && (int)g.size() < B->group_max;) {
+          if ((*it)->group_key == key) {
+            const size_t f = fp(**it);
+            if (B->budget == 0 || B->in_flight_bytes + footprint + f <= B->budget || B->running == 0) {
+              footprint += f;
+              g.push_back(std::move(*it));
+              it = B->queue.erase(it);
+              continue;
+            }
+          }
+          ++it;
+        }
+      }
+      B->in_flight_bytes += footprint;
       ++B->running;
     }
     const Clock::time_point t0 = Clock::now();
     pool->reset_peak();
     const size_t base = pool->in_use();
-    lrfg_result res{};
-    const lrfg_status st = lrfg_solve(ctx, &req->coeff, req->E, &req->opts, &res, nullptr);
+    std::vector<lrfg_status> st;
+    std::vector<lrfg_result> res;
+    std::vector<std::string> msg;
+    run_group(ctx, g, st, res, msg);
     const size_t peak = pool->peak() - base;
     const Clock::time_point t1 = Clock::now();
     bool trim = false;
     {
       std::lock_guard<std::mutex> lock(B->mu);
-      B->in_flight_bytes -= req->footprint;
+      B->in_flight_bytes -= footprint;
       --B->running;
-      if (st == LRFG_OK || st == LRFG_ENOCONV) B->measured[req->key] = peak;
+      bool ok = true;
+      for (lrfg_status s1 : st) ok = ok && (s1 == LRFG_OK || s1 == LRFG_ENOCONV);
+      // per request: a group's high-water mark shared out over its members
+      if (ok) B->measured[g[0]->key] = (peak + g.size() - 1) / g.size();
       B->reserved[w] = pool->reserved();
       trim = B->budget && total(B->reserved) > B->budget;
-      Done& d = B->done[req->id];
-      d.status = st;
-      d.result = res;
-      d.report.queue_s = std::chrono::duration<double>(t0 - req->submitted).count();
-      d.report.run_s = std::chrono::duration<double>(t1 - t0).count();
-      d.report.total_s = std::chrono::duration<double>(t1 - req->submitted).count();
-      d.report.worker = w;
-      d.report.peak_bytes = (double)peak;
-      if (st != LRFG_OK) std::snprintf(d.report.message, sizeof(d.report.message), "%s", lrfg_last_error(ctx));
-      d.ready = true;
+      for (size_t i = 0; i < g.size(); ++i) {
+        Done& d = B->done[g[i]->id];
+        d.status = st[i];
+        d.result = res[i];
+        d.report.queue_s = std::chrono::duration<double>(t0 - g[i]->submitted).count();
+        d.report.run_s = std::chrono::duration<double>(t1 - t0).count();
+        d.report.total_s = std::chrono::duration<double>(t1 - g[i]->submitted).count();
+        d.report.worker = w;
+        d.report.group = (int)g.size();
+        d.report.peak_bytes = (double)peak;
+        if (st[i] != LRFG_OK) std::snprintf(d.report.message, sizeof(d.report.message), "%s", msg[i].c_str());
+        d.ready = true;
+      }
     }
     if (trim) {
       // the pools together cache more than the budget: return this worker's cached blocks
@@ -265,6 +361,7 @@ lrfg_status lrfg_batch_submit(lrfg_batch* B, const lrfg_coeff* coeff, const doub
   const int* N = coeff->N;
   req->key = ShapeKey(coeff->d, N[0], N[1], coeff->d == 3 ? N[2] : 1, (int)coeff->fmt, coeff_rank(*coeff),
                       (int)opts->fmt, (int)opts->prec, opts->rank, (int)opts->disc);
+  req->group_key = lockstep_key(*coeff, *opts);
   req->footprint = estimate_footprint(*coeff, *opts);
   req->submitted = Clock::now();
   {
@@ -276,6 +373,13 @@ lrfg_status lrfg_batch_submit(lrfg_batch* B, const lrfg_coeff* coeff, const doub
     B->queue.push_back(std::move(req));
   }
   B->cv_work.notify_all();
+  return LRFG_OK;
+}
+
+lrfg_status lrfg_batch_set_group(lrfg_batch* B, int max_requests) {
+  if (!B || max_requests < 1 || max_requests > 32) return LRFG_EINVAL;
+  std::lock_guard<std::mutex> lock(B->mu);
+  B->group_max = max_requests;
   return LRFG_OK;
 }
 

@@ -183,7 +183,8 @@ struct SketchSource {
   int N[3] = {0, 0, 0};
   int s[4] = {1, 1, 1, 1};
   const double* dense[3] = {nullptr, nullptr, nullptr};
-  TTView x{};
+  TTView x{};                                      // KHATRI_RAO: the coefficient factor (ranks, shared carriages)
+  const double* xi[3][kMaxSketchItems] = {};       // KHATRI_RAO: item b's own coefficient carriages (null: x's)
   const double* y[3][kMaxSketchItems] = {};
   int ry[4] = {1, 1, 1, 1};
   int nblocks = 0;

@@ -72,7 +72,7 @@ struct ItemPtrs {
 // U[i',k,c] = sum_k' y[k,k'] W[(i',k'), c], then T[(i,k),c] = sum_i' x[i,i'] U[i',k,c]
 // S = double, or float on the sketch side of the mixed-precision path (x, y read in FP64 and rounded)
 template <typename S>
-__global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict__ x, int a0, int a1,
+__global__ void __launch_bounds__(256) kr_right_kernel(const __grid_constant__ ItemPtrs x, int a0, int a1,
                                                        const __grid_constant__ ItemPtrs y,
                                                        int r0, int r1, int N, const S* __restrict__ W,
                                                        long long sW, int ell, int LC, S* T, long long sT) {
@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict_
   S* Xs = Us + (size_t)a1 * r0 * LC;        // a0 x a1
   S* Ys = Xs + (size_t)a0 * a1;             // r0 x r1
   const double* yb = y.p[b];
+  const double* xb = x.p[b];
   const S* Wb = W + (size_t)b * sW;
   for (int t = threadIdx.x; t < a0 * a1; t += blockDim.x) {
     const int i = t / a1, ip = t - i * a1;
-    Xs[t] = (S)x[((size_t)i * N + n) * a1 + ip];
+    Xs[t] = (S)xb[((size_t)i * N + n) * a1 + ip];
   }
   for (int t = threadIdx.x; t < r0 * r1; t += blockDim.x) {
     const int k = t / r1, kp = t - k * r1;
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(256) kr_right_kernel(const double* __restrict_
 
 // Out[b][l, n, (i',k')] = sum_{i,k} M_b[l, (i,k)] x[i,n,i'] y_b[k,n,k']: one block per (n, l-chunk, item);
 // V[c,i,k'] = sum_k M[c,(i,k)] y[k,k'], then Out[c,(i',k')] = sum_i V[c,i,k'] x[i,i']
-__global__ void __launch_bounds__(256) kr_left_kernel(const double* __restrict__ x, int a0, int a1,
+__global__ void __launch_bounds__(256) kr_left_kernel(const __grid_constant__ ItemPtrs x, int a0, int a1,
                                                       const __grid_constant__ ItemPtrs y,
                                                       int r0, int r1, int N, const double* __restrict__ M,
                                                       long long sM, int ell, int LC, double* Out, long long sO) {
@@ -141,10 +142,11 @@ __global__ void __launch_bounds__(256) kr_left_kernel(const double* __restrict__
   double* Xs = Vs + (size_t)LC * a0 * r1;        // a0 x a1
   double* Ys = Xs + (size_t)a0 * a1;             // r0 x r1
   const double* yb = y.p[b];
+  const double* xb = x.p[b];
   const double* Mb = M + (size_t)b * sM;
   for (int t = threadIdx.x; t < a0 * a1; t += blockDim.x) {
     const int i = t / a1, ip = t - i * a1;
-    Xs[t] = x[((size_t)i * N + n) * a1 + ip];
+    Xs[t] = xb[((size_t)i * N + n) * a1 + ip];
   }
   for (int t = threadIdx.x; t < r0 * r1; t += blockDim.x) {
     const int k = t / r1, kp = t - k * r1;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(256) kr_left_kernel(const double* __restrict__
 
 // Khatri-Rao carriage of every item: out[b][(i,k), n, (i',k')] = x[i,n,i'] y_b[k,n,k'] (first and last carriages of
 // the product, which the rounding needs explicitly; they are small)
-__global__ void kr_items_kernel(const double* __restrict__ x, int a0, int a1, const __grid_constant__ ItemPtrs y, int r0,
+__global__ void kr_items_kernel(const __grid_constant__ ItemPtrs x, int a0, int a1, const __grid_constant__ ItemPtrs y, int r0,
                                 int r1, int N, int nb, double* out) {
   const long long per = (long long)a0 * r0 * N * a1 * r1, total = per * nb;
   const int s1w = a1 * r1;
@@ -194,7 +196,7 @@ __global__ void kr_items_kernel(const double* __restrict__ x, int a0, int a1, co
     const long long rest = q / s1w;
     const int n = (int)(rest % N), row = (int)(rest / N);
     const int i = row / r0, k = row - i * r0, ip = col / r1, kp = col - ip * r1;
-    out[t] = x[((size_t)i * N + n) * a1 + ip] * y.p[b][((size_t)k * N + n) * r1 + kp];
+    out[t] = x.p[b][((size_t)i * N + n) * a1 + ip] * y.p[b][((size_t)k * N + n) * r1 + kp];
   }
 }
 
@@ -206,7 +208,7 @@ static int chunk_for(size_t per_col, size_t fixed, int ell, size_t budget) {
 }
 
 template <typename S>
-static void kr_right(lrfg_ctx* ctx, const double* x, int a0, int a1, const ItemPtrs& y, int r0, int r1, int N, int nb,
+static void kr_right(lrfg_ctx* ctx, const ItemPtrs& x, int xn, int a0, int a1, const ItemPtrs& y, int r0, int r1, int N, int nb,
                      const S* W, int ell, S* T) {
   const size_t budget = 100 * 1024;
   const size_t fixed = sizeof(S) * ((size_t)a0 * a1 + (size_t)r0 * r1);
@@ -218,13 +220,13 @@ static void kr_right(lrfg_ctx* ctx, const double* x, int a0, int a1, const ItemP
   dim3 grid(N, (ell + LC - 1) / LC, nb);
   const double flops = 2.0 * nb * N * (double)ell * ((double)a1 * r0 * r1 + (double)a0 * r0 * a1);
   const double bytes = sizeof(S) * nb * ((double)a0 * r0 * N * ell + (double)a1 * r1 * ell) +
-                       sizeof(double) * ((double)a0 * N * a1 + (double)nb * r0 * N * r1);
+                       sizeof(double) * ((double)xn * a0 * N * a1 + (double)nb * r0 * N * r1);
   LRFG_LAUNCH(ctx, KC_SKETCH, flops, bytes,
               kr_right_kernel<S><<<grid, 256, smem, ctx->stream>>>(x, a0, a1, y, r0, r1, N, W, (long long)a1 * r1 * ell,
                                                                   ell, LC, T, (long long)a0 * r0 * N * ell));
 }
 
-static void kr_left(lrfg_ctx* ctx, const double* x, int a0, int a1, const ItemPtrs& y, int r0, int r1, int N, int nb,
+static void kr_left(lrfg_ctx* ctx, const ItemPtrs& x, int xn, int a0, int a1, const ItemPtrs& y, int r0, int r1, int N, int nb,
                     const double* M, int ell, double* Out) {
   const size_t budget = 100 * 1024;
   const size_t fixed = sizeof(double) * ((size_t)a0 * a1 + (size_t)r0 * r1);
@@ -236,7 +238,7 @@ static void kr_left(lrfg_ctx* ctx, const double* x, int a0, int a1, const ItemPt
   dim3 grid(N, (ell + LC - 1) / LC, nb);
   const double flops = 2.0 * nb * N * (double)ell * ((double)a0 * r1 * r0 + (double)a1 * r1 * a0);
   const double bytes = sizeof(double) * nb * ((double)ell * N * a1 * r1 + (double)r0 * N * r1 + (double)ell * a0 * r0) +
-                       sizeof(double) * (double)a0 * N * a1;
+                       sizeof(double) * (double)xn * a0 * N * a1;
   LRFG_LAUNCH(ctx, KC_SKETCH, flops, bytes,
               kr_left_kernel<<<grid, 256, smem, ctx->stream>>>(x, a0, a1, y, r0, r1, N, M, (long long)ell * a0 * r0,
                                                               ell, LC, Out, (long long)ell * N * a1 * r1));
@@ -403,16 +405,24 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
 // ------------------------------------------------------------------------------------------------
 // sources
 // ------------------------------------------------------------------------------------------------
+// carriage j of every item's coefficient factor: its own (xi) or the shared one (x)
+static ItemPtrs coeff_items(const SketchSource& z, int j) {
+  ItemPtrs p{};
+  for (int b = 0; b < z.nb; ++b) p.p[b] = z.xi[j][b] ? z.xi[j][b] : z.x.core[j];
+  return p;
+}
+
 void SketchSource::materialise(lrfg_ctx* ctx, int j, double* dst) const {
   const long long e = (long long)s[j] * N[j] * s[j + 1];
   if (kind == KHATRI_RAO) {
     ItemPtrs p{};
     for (int b = 0; b < nb; ++b) p.p[b] = y[j][b];
     const long long total = e * nb;
+    const double xn = xi[j][0] ? nb : 1;
     LRFG_LAUNCH(ctx, KC_KHATRI_RAO, (double)total,
-                sizeof(double) * ((double)total + (double)x.r[j] * N[j] * x.r[j + 1] + (double)nb * ry[j] * N[j] * ry[j + 1]),
-                kr_items_kernel<<<grid_of(ctx, total), 256, 0, ctx->stream>>>(x.core[j], x.r[j], x.r[j + 1], p, ry[j],
-                                                                            ry[j + 1], N[j], nb, dst));
+                sizeof(double) * ((double)total + xn * x.r[j] * N[j] * x.r[j + 1] + (double)nb * ry[j] * N[j] * ry[j + 1]),
+                kr_items_kernel<<<grid_of(ctx, total), 256, 0, ctx->stream>>>(coeff_items(*this, j), x.r[j], x.r[j + 1],
+                                                                            p, ry[j], ry[j + 1], N[j], nb, dst));
     return;
   }
   for (int b = 0; b < nb; ++b) {
@@ -421,7 +431,7 @@ void SketchSource::materialise(lrfg_ctx* ctx, int j, double* dst) const {
       LRFG_CUDA(cudaMemcpyAsync(o, dense[j] + (size_t)b * e, sizeof(double) * e, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
     } else if (kind == KHATRI_RAO) {
-      khatri_rao(ctx, x.core[j], x.r[j], N[j], x.r[j + 1], y[j][b], ry[j], ry[j + 1], o);
+      khatri_rao(ctx, xi[j][b] ? xi[j][b] : x.core[j], x.r[j], N[j], x.r[j + 1], y[j][b], ry[j], ry[j + 1], o);
     } else {
       // exponential-sum blocks F_m of carriage j (r_j x N x r_{j+1} each, weights already in carriage 0)
       const int R = nblocks, a = ry[j], c = ry[j + 1];
@@ -445,7 +455,7 @@ void SketchSource::right_middle(lrfg_ctx* ctx, const double* W, int ell, double*
   } else if (kind == KHATRI_RAO) {
     ItemPtrs p{};
     for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
-    kr_right<double>(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
+    kr_right<double>(ctx, coeff_items(*this, 1), xi[1][0] ? nb : 1, x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
   } else {
     // T[(m,k), n, l] = sum_k' F_m[k, n, k'] W[(m,k'), l]: for each item, one product per block
     const int R = nblocks, a = ry[1], c = ry[2];
@@ -461,7 +471,7 @@ void SketchSource::right_middle_f32(lrfg_ctx* ctx, const float* W, int ell, floa
   if (kind == KHATRI_RAO) {
     ItemPtrs p{};
     for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
-    kr_right<float>(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
+    kr_right<float>(ctx, coeff_items(*this, 1), xi[1][0] ? nb : 1, x.r[1], x.r[2], p, ry[1], ry[2], n, nb, W, ell, T);
   } else if (kind == DENSE) {
     const long long e = (long long)s[1] * n * s[2];
     DBuf<float> Z32(ctx->pool, (size_t)e * nb);
@@ -489,7 +499,7 @@ void SketchSource::left_middle(lrfg_ctx* ctx, const double* M, int ell, double* 
   } else if (kind == KHATRI_RAO) {
     ItemPtrs p{};
     for (int b = 0; b < nb; ++b) p.p[b] = y[1][b];
-    kr_left(ctx, x.core[1], x.r[1], x.r[2], p, ry[1], ry[2], n, nb, M, ell, X);
+    kr_left(ctx, coeff_items(*this, 1), xi[1][0] ? nb : 1, x.r[1], x.r[2], p, ry[1], ry[2], n, nb, M, ell, X);
   } else {
     // tmp[m][l, n, k'] = sum_k M[l, (m,k)] F_m[k, n, k'], then interleaved into X[l, n, (m,k')], item by item
     const int R = nblocks, a = ry[1], c = ry[2];

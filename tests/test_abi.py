@@ -69,6 +69,7 @@ def test_batch_entry_points_check_arguments_without_gpu(lib):
     ready = ctypes.c_int()
     assert lib.lrfg_batch_poll(None, ctypes.c_ulonglong(1), 0, ctypes.byref(ready), None, None, None) == 1
     assert lib.lrfg_batch_destroy(None) == 1
+    assert lib.lrfg_batch_set_group(None, 2) == 1
 
 
 def test_batch_binding_without_gpu_raises():
@@ -109,3 +110,17 @@ def test_aeff_tensor_entry_point_rejects_a_null_problem(lib):
     A = (ctypes.c_double * 9)(*([7.0] * 9))
     assert f(None, A, None) == L.LRFG_EINVAL
     assert list(A) == [7.0] * 9
+
+
+def test_problems_solve_rejects_bad_arguments(lib):
+    """lrfg_problems_solve without a GPU: no problems, a null array or a null first problem are invalid arguments
+    (checked before any device work)."""
+    from paper_1902_07455_gb300 import _lib as L
+    f = lib.lrfg_problems_solve
+    f.restype, f.argtypes = L.SIGNATURES["lrfg_problems_solve"]
+    E = (ctypes.c_double * 3)(1.0, 0.0, 0.0)
+    res = (L.lrfg_result * 1)()
+    hs = (ctypes.c_void_p * 1)(None)
+    assert f(0, hs, E, res) == L.LRFG_EINVAL
+    assert f(1, None, E, res) == L.LRFG_EINVAL
+    assert f(1, hs, E, res) == L.LRFG_EINVAL

@@ -166,3 +166,35 @@ def test_destroy_drops_queued_requests_and_releases_waiting_polls():
     assert not th.is_alive()
     assert out["st"] == 0 and out["ready"] == 1
     assert out["sst"] == 1 and "dropped" in out["msg"]
+
+
+def test_batch_groups_requests_of_one_shape_in_lockstep(ctx):
+    """Batching across requests: with a group size > 1 the worker takes the queued requests of one shape
+    (different microstructures, same grid, coefficient ranks and options) together and solves them in lockstep
+    (lrfg_problems_solve).  Each result equals its own solve up to the rounding order of the batched products;
+    requests of other shapes run alone."""
+    d, N = 3, 27
+    coeffs = [lr.tt_svd(lognormal_grf(d, N, ell=0.2, var=0.25, seed=s), rmax=6) for s in (41, 42, 43, 44)]
+    assert len({tuple(c.shape[0] for c in a) for a in coeffs}) == 1
+    kw = dict(rank=12, maxit=40, tol=5e-2, stop_on_increase=False, sketch_over=6)
+    Es = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]]
+    solo = [_solo(ctx, a, E, lrfg.TT, kw) for a, E in zip(coeffs, Es)]
+    _, t2, w2 = smoothed_cube(2, 63, contrast=10.0, full=False)
+    other = (lr.tt_from_separable(t2, w2), [1.0, 0.0], lrfg.TT, dict(rank=6, maxit=30))
+    other_solo = _solo(ctx, *other)
+    blocker = lognormal_grf(3, 81, seed=45)  # keeps the single worker busy while the rest is queued
+    with lrfg.Batch(0, workers=1, group=8) as B:
+        tb = B.submit(blocker, [1.0, 0.0, 0.0], lrfg.FULL, tol=1e-8)
+        tickets = [B.submit(a, E, lrfg.TT, **kw) for a, E in zip(coeffs[:2], Es[:2])]
+        to = B.submit(other[0], other[1], other[2], **other[3])
+        tickets += [B.submit(a, E, lrfg.TT, **kw) for a, E in zip(coeffs[2:], Es[2:])]
+        assert B.wait(tb).group == 1
+        out = [B.wait(t) for t in tickets]
+        o = B.wait(to)
+    assert o.group == 1 and o.result.Aeff == other_solo.Aeff
+    assert all(br.group == 4 for br in out), [br.group for br in out]
+    assert len({br.run_s for br in out}) == 1  # one solve served all four
+    for br, s in zip(out, solo):
+        assert br.result.converged and s.converged
+        assert abs(br.result.Aeff - s.Aeff) <= 1e-9 * s.Aeff, (br.result.Aeff, s.Aeff)
+        assert br.result.iters == s.iters
