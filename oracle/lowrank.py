@@ -37,8 +37,8 @@ the rank), or with ``rank_tol`` to the smallest ranks within that relative toler
 TT bond, tol / sqrt(d) per Tucker mode); the residual is recomputed from its definition each iteration
 and truncated; inner products of Fourier tensors take the real part; the relative error of Eq.
 (rel_error) is reported as an absolute value.  Also here: a constant anisotropic part B of the material
-(Sec. 4.4), the rank-adapting iteration Sec. 4.3 proposes (``minres_rank_adaptive``), and Ga in TT format
-(``LowRankGaTT``, Sec. 2.2.3 with the truncations of Eq. (Pls_lowrank)).
+(Sec. 4.4), the rank-adapting iteration Sec. 4.3 proposes (``minres_rank_adaptive``), and Ga in the low-rank
+formats (``LowRankGa``: TT, Tucker, CP for d = 2; Sec. 2.2.3 with the truncations of Eq. (Pls_lowrank)).
 """
 from __future__ import annotations
 
@@ -697,7 +697,7 @@ def minres_rank_adaptive(op: LowRankGaNi, E, rank_start, rank_step, tol=1e-10, m
 
 
 # ----------------------------------------------------------------------------------------------
-# Ga (exact integration on the double grid, Sec. 2.2.3) in TT format
+# Ga (exact integration on the double grid, Sec. 2.2.3) in the low-rank formats
 # ----------------------------------------------------------------------------------------------
 
 
@@ -707,6 +707,25 @@ def tt_mode_map(x, j, L):
     out = [G.copy() for G in x]
     out[j] = np.einsum("mn,anb->amb", L, x[j])
     return out
+
+
+def tucker_mode_map(x, j, L):
+    """The same linear map on mode j of a Tucker tensor: factor B_j <- L B_j (core unchanged)."""
+    c, F = x
+    F = [f.copy() for f in F]
+    F[j] = L @ F[j]
+    return c.copy(), F
+
+
+def cp_mode_map(x, j, L):
+    """The same on mode j of a CP tensor (d = 2): factor B_j <- L B_j (weights unchanged)."""
+    c, B1, B2 = x
+    if j == 0:
+        return c.copy(), L @ B1, B2.copy()
+    return c.copy(), B1.copy(), L @ B2
+
+
+MODE_MAPS = {"tt": tt_mode_map, "tucker": tucker_mode_map, "cp": cp_mode_map}
 
 
 def ga_matrices(N: int):
@@ -730,15 +749,17 @@ def ga_matrices(N: int):
     return inj, inj.T.copy(), np.real(ext)
 
 
-class LowRankGaTT:
-    """Ga in TT format: C~ v ~= T P~^-1 T grad^* I* F_M T A~ F_M^-1 I grad^ v and
-    b~ = - T P~^-1 grad^* I* F_M A~ E (Eq. (ls_Ga_fourier) with the truncations placed as in Eq.
-    (Pls_lowrank)), A~ the modified coefficient of a pixel-wise constant a given as a TT of pixel values on
-    the grid N; I, I* and the DFTs act mode by mode.  Interface of ``LowRankGaNi`` (for ``minres``)."""
+class LowRankGa:
+    """Ga in a low-rank format (TT, Tucker, or CP for d = 2): C~ v ~= T P~^-1 T grad^* I* F_M T A~ F_M^-1 I grad^ v
+    and b~ = - T P~^-1 grad^* I* F_M A~ E (Eq. (ls_Ga_fourier) with the truncations placed as in Eq.
+    (Pls_lowrank)), A~ the modified coefficient of a pixel-wise constant a given in the same format as its
+    pixel values on the grid N; I, I* and the DFTs act mode by mode (on carriage fibres or factor columns).
+    Interface of ``LowRankGaNi`` (for ``minres``)."""
 
-    def __init__(self, a_tt, shape, rank=10, pinv_eps=0.1, rank_tol=None):
-        self.f = FORMATS["tt"]
-        self.fmt = "tt"
+    def __init__(self, a_tt, shape, rank=10, pinv_eps=0.1, rank_tol=None, fmt="tt"):
+        self.f = FORMATS[fmt]
+        self.fmt = fmt
+        self._map = MODE_MAPS[fmt]
         self.shape = tuple(int(n) for n in shape)
         self.d = len(self.shape)
         self.rank = rank
@@ -746,9 +767,9 @@ class LowRankGaTT:
         self.B = None
         self.K = [_fg.frequencies(n).astype(np.float64) for n in self.shape]
         self.mats = [ga_matrices(n) for n in self.shape]
-        At = [np.asarray(G, dtype=np.float64) for G in a_tt]
+        At = _as_float(fmt, a_tt)
         for j in range(self.d):
-            At = tt_mode_map(At, j, self.mats[j][2])
+            At = self._map(At, j, self.mats[j][2])
         self.At = At                                             # values on the double grid
         xmax = float(sum(((n - 1) // 2) ** 2 for n in self.shape))
         t, w = _expsum.expsum_inverse(xmax, pinv_eps)
@@ -760,12 +781,12 @@ class LowRankGaTT:
 
     def _inject(self, xh):
         for j in range(self.d):
-            xh = tt_mode_map(xh, j, self.mats[j][0])
+            xh = self._map(xh, j, self.mats[j][0])
         return xh
 
     def _project(self, xh):
         for j in range(self.d):
-            xh = tt_mode_map(xh, j, self.mats[j][1])
+            xh = self._map(xh, j, self.mats[j][1])
         return xh
 
     def _grad_double(self, vh, a):
@@ -797,7 +818,7 @@ class LowRankGaTT:
         return f.scale(self.T(f.had(self.Pinv, acc)), -1.0)
 
     def homogenised_coefficient(self, uh, E) -> float:
-        """sum over the double grid of A~ |E + e|^2 (exact integration), by TT contractions:
+        """sum over the double grid of A~ |E + e|^2 (exact integration), by low-rank contractions:
         |E|^2 <A~, 1> + 2 sum_a E_a <A~, e_a> + sum_a <A~ e_a, e_a>."""
         f = self.f
         E = np.asarray(E, dtype=np.float64)
@@ -812,6 +833,20 @@ class LowRankGaTT:
 
     def full_field(self, uh) -> np.ndarray:
         return np.real(_fg.idft(self.f.full(uh), self.d))
+
+
+LowRankGaTT = LowRankGa  # the TT instance (fmt="tt"), under its earlier name
+
+
+def _as_float(fmt, x):
+    """A real FP64 copy of a low-rank tensor of the given format."""
+    if fmt == "tt":
+        return [np.asarray(G, dtype=np.float64) for G in x]
+    if fmt == "tucker":
+        c, F = x
+        return np.asarray(c, dtype=np.float64), [np.asarray(f, dtype=np.float64) for f in F]
+    c, B1, B2 = x
+    return np.asarray(c, dtype=np.float64), np.asarray(B1, dtype=np.float64), np.asarray(B2, dtype=np.float64)
 
 
 def relative_error(A_full: float, A_lowrank: float) -> float:

@@ -155,3 +155,25 @@ def test_untruncated_tt_ga_equals_full_ga(d, N):
     op = lr.LowRankGaTT(lr.tt_from_separable(terms, w), (N,) * d, rank=None, rank_tol=1e-15)
     out = lr.minres(op, E, tol=1e-13, maxit=600, stop_on_increase=False)
     assert abs(out["Aeff"] - full["Aeff"]) <= 1e-10 * full["Aeff"]
+
+
+@pytest.mark.parametrize("fmt,d,N", [("tucker", 3, 9), ("tucker", 2, 13), ("cp", 2, 13)])
+def test_tucker_cp_modified_coefficient_matches_the_full_one(fmt, d, N):
+    """The modified coefficient formed factor by factor (Tucker, CP) against the FFT route of the full one."""
+    a, terms, w = smoothed_cube(d, N, contrast=10.0)
+    a_lr = lr.tucker_from_separable(terms, w) if fmt == "tucker" else lr.cp_from_separable(terms, w)
+    op = lr.LowRankGa(a_lr, (N,) * d, rank=None, fmt=fmt)
+    ref = ga.ga_coefficient(a)
+    assert np.abs(np.real(op.f.full(op.At)) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("fmt,d,N", [("tucker", 2, 13), ("tucker", 3, 9), ("cp", 2, 13)])
+def test_untruncated_tucker_cp_ga_equals_full_ga(fmt, d, N):
+    """Untruncated Tucker / CP Ga MinRes reaches the full-format Ga solution (pinned above) to 1e-10."""
+    a, terms, w = square_inclusion(d, N)
+    E = np.eye(d)[0]
+    full = ga.solve_ga(a, E, tol=1e-13, maxit=3000)
+    a_lr = lr.tucker_from_separable(terms, w) if fmt == "tucker" else lr.cp_from_separable(terms, w)
+    op = lr.LowRankGa(a_lr, (N,) * d, rank=None, rank_tol=1e-15, fmt=fmt)
+    out = lr.minres(op, E, tol=1e-13, maxit=600, stop_on_increase=False)
+    assert abs(out["Aeff"] - full["Aeff"]) <= 1e-10 * full["Aeff"]

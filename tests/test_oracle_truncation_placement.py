@@ -67,27 +67,30 @@ def gani_rhs_full(a_full, E, r, pinv_eps):
     return -T_full(pinv_grid(a_full.shape, pinv_eps) * acc, r)
 
 
-def ga_apply_full(At, vh, r, pinv_eps):
-    """T P~^-1 T grad^* I* F_M T A~ F_M^-1 I grad^ v on full grids (Ga, double grid M = 2N - 1)."""
+def ga_apply_full(At, vh, r, pinv_eps, T=None):
+    """T P~^-1 T grad^* I* F_M T A~ F_M^-1 I grad^ v on full grids (Ga, double grid M = 2N - 1); T: the
+    truncation of a full tensor (default T_full)."""
+    T = T or T_full
     d = vh.ndim
     N, M = vh.shape[0], At.shape[0]
     g = fg.grad_hat(vh)
     acc = np.zeros(vh.shape, dtype=np.complex128)
     for a in range(d):
         e = fg.idft(ge.inject(g[a], M, d), d)                   # gradient component on the double grid
-        w = T_full(At * e, r)                                   # T A~ e_a there
+        w = T(At * e, r)                                        # T A~ e_a there
         acc = acc + fg.div_hat(component(d, a, ge.project(fg.dft(w, d), N, d)))
-    s = T_full(acc, r)
-    return T_full(pinv_grid(vh.shape, pinv_eps) * s, r)
+    s = T(acc, r)
+    return T(pinv_grid(vh.shape, pinv_eps) * s, r)
 
 
-def ga_rhs_full(At, E, N, r, pinv_eps):
+def ga_rhs_full(At, E, N, r, pinv_eps, T=None):
+    T = T or T_full
     d = At.ndim
     ah = ge.project(fg.dft(At.astype(np.complex128), d), N, d)
     acc = np.zeros((N,) * d, dtype=np.complex128)
     for a in range(d):
         acc = acc + fg.div_hat(component(d, a, float(E[a]) * ah))
-    return -T_full(pinv_grid((N,) * d, pinv_eps) * acc, r)
+    return -T(pinv_grid((N,) * d, pinv_eps) * acc, r)
 
 
 def rel(x, y):
@@ -222,3 +225,29 @@ def test_minres_patience_continues_past_one_rise():
     # patience 1 is the paper's rule: stop at the first rise
     one = lr.minres(ScriptedOperator(bump_call=6, factor=3.0), np.zeros(2), tol=1e-14, maxit=8, stop_on_increase=1)
     assert one["iters"] == 2
+
+
+def T_hosvd(X, r):
+    """T of a full tensor in Tucker format: its truncated HOSVD at multilinear rank r (App. A.2.3), expanded."""
+    return lr.tucker_full(*lr.tucker_hosvd(X, rmax=r))
+
+
+@pytest.mark.parametrize("d,N,ra,r", [(2, 9, 2, 2), (3, 7, 2, 2)])
+def test_ga_tucker_apply_and_rhs_by_full_grids(d, N, ra, r):
+    """Ga in Tucker format against the full-grid route with T the truncated HOSVD of the expanded tensor:
+    the Tucker truncation (QR of the factors, HOSVD of the core) of any exact Tucker form of a tensor is the
+    truncated HOSVD of that tensor."""
+    a_tt, vh = _operands(d, N, ra, 71 + d + N)
+    a_pix = np.real(lr.tt_full(a_tt))
+    a_tk = lr.tucker_hosvd(a_pix)  # exact Tucker form of the pixel values
+    v_tk = lr.tucker_hosvd(lr.tt_full(vh))
+    At = ge.ga_coefficient(a_pix)
+    op = lr.LowRankGa(a_tk, (N,) * d, rank=r, pinv_eps=0.1, fmt="tucker")
+    got = lr.tucker_full(*op.apply(v_tk))
+    ref = ga_apply_full(At, lr.tt_full(vh), r, 0.1, T=T_hosvd)
+    assert rel(got, ref) <= 1e-11, rel(got, ref)
+    E = np.array([1.0, 0.5, -0.25][:d])
+    got_b = lr.tucker_full(*op.rhs(E))
+    ref_b = ga_rhs_full(At, E, N, r, 0.1, T=T_hosvd)
+    assert rel(got_b, ref_b) <= 1e-11, rel(got_b, ref_b)
+    assert rel(ga_apply_full(At, lr.tt_full(vh), None, 0.1, T=T_hosvd), ref) > 1e-3  # every T cuts
