@@ -208,6 +208,9 @@ struct lrfg_problem {
   DBuf<double2> wcM;
   // Ga in TT: the modified coefficient on the double grid, and its projection on the grid (right-hand side)
   TT a_ga_tt, a_down_tt;
+  // Ga in Tucker / CP: the same in Tucker form (tkga views them)
+  TK a_ga_tk, a_down_tk;
+  TKGa tkga{};
   // randomised rounding (opts.sketch_over > 0): the sketch TT of ranks rank + sketch_over, by rank
   std::map<int, TT> sketches;
 };
@@ -395,6 +398,9 @@ double quad_form(const double* B, const double* E, int d) {
     for (int j = 0; j < d; ++j) v += E[i] * B[i * 3 + j] * E[j];
   return v;
 }
+
+// Ga descriptor of a Tucker / CP problem (null: GaNi)
+const TKGa* tk_ga(const lrfg_problem* P) { return P->ga && tucker_like(P->opts.fmt) ? &P->tkga : nullptr; }
 
 // ---- TT operator pieces -----------------------------------------------------------------------
 
@@ -826,7 +832,8 @@ void apply_into(lrfg_problem* P, const lrfg_field* in, lrfg_field* out) {
     }
   } else if (tucker_like(P->opts.fmt)) {
     TK res;
-    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res, P->opts.rank_tol, aniso_b(P));
+    tk_apply(P->ctx, tk_view(P->a_tk), tk_view(in->tk), P->pt, P->pw, P->opts.rank, res, P->opts.rank_tol, aniso_b(P),
+             tk_ga(P));
     out->tk = std::move(res);
   } else {
     TT res;
@@ -909,7 +916,7 @@ void solve_tucker(lrfg_problem* P, const double* E, lrfg_result* res, lrfg_field
   TK best;
   const TKSolveResult r = tk_solve(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, P->opts.tol,
                                    P->opts.maxit, P->opts.stop_on_increase, best, P->opts.rank_tol, aniso_b(P),
-                                   P->opts.rank_start, P->opts.rank_step);
+                                   P->opts.rank_start, P->opts.rank_step, tk_ga(P));
   res->iters = r.iters;
   res->rel_resid = r.rel_resid;
   res->converged = r.rel_resid <= P->opts.tol ? 1 : 0;
@@ -1708,8 +1715,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     LRFG_REQUIRE(opts->sketch_keep == 0 || opts->sketch_over > 0, "sketch_keep needs sketch_over > 0");
     if (opts->sketch_over > 0 && (opts->fmt != LRFG_TT || opts->disc != LRFG_GANI))
       fail(LRFG_ENOTSUP, "the randomised rounding (sketch_over > 0) is implemented for LRFG_TT GaNi solutions");
-    if (opts->disc == LRFG_GA && ((opts->fmt != LRFG_FULL && opts->fmt != LRFG_TT) || opts->prec != LRFG_FP64))
-      fail(LRFG_ENOTSUP, "LRFG_GA is implemented for LRFG_FULL and LRFG_TT solutions in LRFG_FP64");
+    if (opts->disc == LRFG_GA && opts->prec != LRFG_FP64) fail(LRFG_ENOTSUP, "LRFG_GA is implemented in LRFG_FP64");
     LRFG_REQUIRE(coeff->fmt == LRFG_FULL || coeff->fmt == LRFG_TT || coeff->fmt == LRFG_TUCKER,
                  "coefficient format must be FULL, TT or TUCKER");
     P = new lrfg_problem();
@@ -1722,7 +1728,7 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
     P->aniso = check_aniso(P->d, coeff->B, P->B);
     P->ga = opts->disc == LRFG_GA;
-    if (P->ga && P->aniso && opts->fmt == LRFG_TT)
+    if (P->ga && P->aniso && opts->fmt != LRFG_FULL)
       fail(LRFG_ENOTSUP, "LRFG_GA with an anisotropic part is implemented for LRFG_FULL solutions");
     const long long n = grid_size(P->d, P->N);
     // coefficient -> device
@@ -1803,18 +1809,26 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
           M[j] = 2 * P->N[j] - 1;
           make_plan(M[j], 27);  // LRFG_ENOTSUP when the double grid has a prime factor above 31
         }
-        TTBatch ag, ad;
-        tt_ga_map(ctx, view_of(P->a_tt), 1, M, GA_EXTEND, ag);
-        tt_ga_map(ctx, item_view(ag, 0), 1, P->N, GA_DOWN, ad);
-        P->a_ga_tt.d = P->a_down_tt.d = P->d;
-        for (int j = 0; j < 3; ++j) {
-          P->a_ga_tt.N[j] = ag.N[j];
-          P->a_down_tt.N[j] = ad.N[j];
-        }
-        for (int j = 0; j < 4; ++j) P->a_ga_tt.r[j] = P->a_down_tt.r[j] = ag.r[j];
-        for (int j = 0; j < P->d; ++j) {
-          P->a_ga_tt.core[j] = std::move(ag.core[j]);
-          P->a_down_tt.core[j] = std::move(ad.core[j]);
+        if (tucker_like(opts->fmt)) {
+          // the factors of a's pixel values mapped to the modified coefficient, and its projection
+          tk_ga_map(ctx, tk_view(P->a_tk), M, GA_EXTEND, P->a_ga_tk);
+          tk_ga_map(ctx, tk_view(P->a_ga_tk), P->N, GA_DOWN, P->a_down_tk);
+          P->tkga.a_ga = tk_view(P->a_ga_tk);
+          P->tkga.a_down = tk_view(P->a_down_tk);
+        } else {
+          TTBatch ag, ad;
+          tt_ga_map(ctx, view_of(P->a_tt), 1, M, GA_EXTEND, ag);
+          tt_ga_map(ctx, item_view(ag, 0), 1, P->N, GA_DOWN, ad);
+          P->a_ga_tt.d = P->a_down_tt.d = P->d;
+          for (int j = 0; j < 3; ++j) {
+            P->a_ga_tt.N[j] = ag.N[j];
+            P->a_down_tt.N[j] = ad.N[j];
+          }
+          for (int j = 0; j < 4; ++j) P->a_ga_tt.r[j] = P->a_down_tt.r[j] = ag.r[j];
+          for (int j = 0; j < P->d; ++j) {
+            P->a_ga_tt.core[j] = std::move(ag.core[j]);
+            P->a_down_tt.core[j] = std::move(ad.core[j]);
+          }
         }
       }
     }
@@ -1884,7 +1898,7 @@ lrfg_status lrfg_problem_rhs(lrfg_problem* P, const double* E, lrfg_field** out)
         full_rhs<double>(P, E, f->half.get(), 1);
       }
     } else if (tucker_like(P->opts.fmt)) {
-      tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk, P->opts.rank_tol);
+      tk_rhs(P->ctx, tk_view(P->a_tk), E, P->pt, P->pw, P->opts.rank, f->tk, P->opts.rank_tol, tk_ga(P));
     } else {
       lr_rhs(P, E, f->tt, P->opts.rank);
     }
@@ -1924,7 +1938,7 @@ lrfg_status lrfg_problem_aeff(lrfg_problem* P, const double* E, const lrfg_field
     LRFG_REQUIRE(E && Aeff, "null argument");
     check_field(P, u);
     *Aeff = (P->opts.fmt == LRFG_FULL)     ? full_aeff(P, E, u->half.get())
-            : tucker_like(P->opts.fmt)     ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk), aniso_b(P))
+            : tucker_like(P->opts.fmt)     ? tk_aeff(P->ctx, tk_view(P->a_tk), E, tk_view(u->tk), aniso_b(P), tk_ga(P))
                                            : lr_aeff(P, E, view_of(u->tt));
   });
 }

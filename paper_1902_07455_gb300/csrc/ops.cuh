@@ -239,6 +239,13 @@ struct TKSolveResult {
   double rel_resid;
   int applies;
 };
+// Ga in Tucker / CP format (Sec. 2.2.3): the modified coefficient on the double grid M = 2N - 1 and its
+// projection back to the grid (the right-hand side's coefficient), both with the factors of a's pixel values
+// mapped mode by mode
+struct TKGa {
+  TKView a_ga;    // on M
+  TKView a_down;  // on N
+};
 TKView tk_view(const TK& x);
 void tk_alloc(lrfg_ctx* ctx, TK& x, int d, const int* N, const int* r);
 void tk_copy(lrfg_ctx* ctx, const TKView& x, TK& out);
@@ -254,15 +261,20 @@ void tk_expand(lrfg_ctx* ctx, const TKView& x, double* values);
 void tk_compress(lrfg_ctx* ctx, int d, const int* N, const double* values, int rmax, double tol, TK& out);
 void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, const std::vector<double>& w, int rmax,
                 TK& out, double tol = 0.0);
+// every factor of x resampled to the grid n_out by the Ga mode map `mode` (GA_UP / GA_DOWN / GA_EXTEND)
+void tk_ga_map(lrfg_ctx* ctx, const TKView& x, const int* n_out, int mode, TK& out);
+// ga: Ga (null: GaNi); B is then null (isotropic)
 void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
-              const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0, const double* B = nullptr);
+              const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0, const double* B = nullptr,
+              const TKGa* ga = nullptr);
 void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
-            const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0);
+            const std::vector<double>& pw, int rank, TK& out, double rtol = 0.0, const TKGa* ga = nullptr);
 // B: the constant anisotropic part (3 x 3 row-major storage) or null
-double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u, const double* B = nullptr);
+double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u, const double* B = nullptr,
+               const TKGa* ga = nullptr);
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
                        TK& best_u, double rtol = 0.0, const double* B = nullptr, int rank_start = 0,
-                       int rank_step = 1);
+                       int rank_step = 1, const TKGa* ga = nullptr);
 
 }  // namespace lrfg

@@ -412,14 +412,37 @@ void tk_precond(lrfg_ctx* ctx, const TKView& x, const std::vector<double>& t, co
 // the truncated operator, right-hand side, A_eff and minimal-residual solve in Tucker format
 // (Eq. (Pls_lowrank), Sec. 3.3) -- the same steps as the TT path
 // ------------------------------------------------------------------------------------------------
+void tk_ga_map(lrfg_ctx* ctx, const TKView& x, const int* n_out, int mode, TK& out) {
+  tk_alloc(ctx, out, x.d, n_out, x.r);
+  LRFG_CUDA(cudaMemcpyAsync(out.core.get(), x.core, sizeof(double) * core_size(x.d, x.r), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  for (int j = 0; j < x.d; ++j) ga_resample(ctx, x.fac[j], out.fac[j].get(), 1, x.N[j], x.r[j], n_out[j], mode);
+}
+
+// Ga (Eq. (ls_Ga_fourier) with the truncations of Eq. (Pls_lowrank)): each gradient component's factors
+// interpolated to the double grid, the product with the modified coefficient and T there, the factors
+// projected back, then the divergence, the sum and the preconditioner as for GaNi
+static void tk_material_ga(lrfg_ctx* ctx, const TKGa& ga, const TKView& e, int rank, TK& out, double rtol) {
+  TK eu, ae, wr;
+  tk_ga_map(ctx, e, ga.a_ga.N, GA_UP, eu);
+  tk_hadamard(ctx, ga.a_ga, tk_view(eu), ae);  // A~ (.) e_alpha on the double grid
+  tk_round(ctx, tk_view(ae), rank, wr, rtol);  // T there
+  tk_ga_map(ctx, tk_view(wr), e.N, GA_DOWN, out);
+}
+
 void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector<double>& pt,
-              const std::vector<double>& pw, int rank, TK& out, double rtol, const double* B) {
+              const std::vector<double>& pw, int rank, TK& out, double rtol, const double* B, const TKGa* ga) {
   const int d = v.d;
   TK w[3], es[3];
   for (int alpha = 0; alpha < d; ++alpha)
     tk_mode_operator(ctx, v, alpha, LRFG_MUL_DERIV, 0.0, 1.0, es[alpha]);         // gradient, mode alpha
   for (int alpha = 0; alpha < d; ++alpha) {
     TK ae, wr;
+    if (ga) {
+      tk_material_ga(ctx, *ga, tk_view(es[alpha]), rank, wr, rtol);
+      tk_mode_operator(ctx, tk_view(wr), alpha, LRFG_MUL_DERIV, 0.0, -1.0, w[alpha]);  // divergence
+      continue;
+    }
     tk_hadamard(ctx, a, tk_view(es[alpha]), ae);                                  // a (.) e_alpha
     if (B) {
       // constant anisotropic part: + sum_beta B[alpha][beta] e_beta (zero entries skipped)
@@ -448,8 +471,10 @@ void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector
   tk_precond(ctx, tk_view(s), pt, pw, rank, out, rtol);
 }
 
-void tk_rhs(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
-            const std::vector<double>& pw, int rank, TK& out, double rtol) {
+void tk_rhs(lrfg_ctx* ctx, const TKView& a_in, const double* E, const std::vector<double>& pt,
+            const std::vector<double>& pw, int rank, TK& out, double rtol, const TKGa* ga) {
+  // Ga: -T P~^-1 grad^* I* F_M A~ E, i.e. the GaNi form with the projection of A~ on the grid
+  const TKView a = ga ? ga->a_down : a_in;
   const int d = a.d;
   TK t[3];
   TKView terms[3];
@@ -479,10 +504,19 @@ static void tk_ones(lrfg_ctx* ctx, int d, const int* N, TK& x) {
   for (int j = 0; j < d; ++j) fill(ctx, x.fac[j].get(), 1.0, N[j]);
 }
 
-double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u, const double* B) {
+double tk_aeff(lrfg_ctx* ctx, const TKView& a_in, const double* E, const TKView& u_in, const double* B,
+               const TKGa* ga) {
+  // Ga: the exact integral, the sum over the double grid of A~ |E + e|^2 (A~ carries the quadrature weights),
+  // with u interpolated there (its gradient on the double grid is the interpolated gradient: zero padding
+  // keeps the frequencies)
+  TK uu;
+  if (ga) tk_ga_map(ctx, u_in, ga->a_ga.N, GA_UP, uu);
+  const TKView a = ga ? ga->a_ga : a_in;
+  const TKView u = ga ? tk_view(uu) : u_in;
   const int d = a.d;
   double size = 1.0;
-  for (int j = 0; j < d; ++j) size *= a.N[j];
+  if (!ga)
+    for (int j = 0; j < d; ++j) size *= a.N[j];
   TK ones;
   tk_ones(ctx, d, a.N, ones);
   double EE = 0.0;
@@ -516,12 +550,12 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a, const double* E, const TKView& u,
 // rebuilt and the iteration restarts from the best iterate with its residual recomputed at the new rank.
 TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const std::vector<double>& pt,
                        const std::vector<double>& pw, int rank, double tol, int maxit, int stop_on_increase,
-                       TK& best_u, double rtol, const double* B, int rank_start, int rank_step) {
+                       TK& best_u, double rtol, const double* B, int rank_start, int rank_step, const TKGa* ga) {
   TKSolveResult res{};
   const bool adapt = rank_start > 0;
   int rc = adapt ? std::min(rank_start, rank) : rank;
   TK b;
-  tk_rhs(ctx, a, E, pt, pw, rc, b, rtol);
+  tk_rhs(ctx, a, E, pt, pw, rc, b, rtol, ga);
   double nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
   TK u, r;
   bool u_zero = true, best_zero = true;
@@ -530,7 +564,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
   tk_copy(ctx, tk_view(b), r);
   auto residual = [&]() {  // r <- T(b - C u) at the current rank
     TK cu, diff, rn;
-    tk_apply(ctx, a, tk_view(u), pt, pw, rc, cu, rtol, B);
+    tk_apply(ctx, a, tk_view(u), pt, pw, rc, cu, rtol, B, ga);
     ++applies;
     TKView xs[2] = {tk_view(b), tk_view(cu)};
     const double sc[2] = {1.0, -1.0};
@@ -556,7 +590,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
       do {
         rc = std::min(rank, rc + std::max(1, rank_step));
         TK nbv;
-        tk_rhs(ctx, a, E, pt, pw, rc, nbv, rtol);
+        tk_rhs(ctx, a, E, pt, pw, rc, nbv, rtol, ga);
         b = std::move(nbv);
         nb = std::sqrt(std::max(tk_dot(ctx, tk_view(b), tk_view(b)), 0.0));
         u_zero = best_zero;
@@ -575,7 +609,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
     }
     if ((nr <= tol && (!adapt || (rc >= rank && cap_steps > 0))) || it >= maxit) break;
     TK q;
-    tk_apply(ctx, a, tk_view(r), pt, pw, rc, q, rtol, B);
+    tk_apply(ctx, a, tk_view(r), pt, pw, rc, q, rtol, B, ga);
     ++applies;
     const double qq = tk_dot(ctx, tk_view(q), tk_view(q));
     if (qq == 0.0) break;
@@ -610,7 +644,7 @@ TKSolveResult tk_solve(lrfg_ctx* ctx, const TKView& a, const double* E, const st
   res.iters = best_it;
   res.rel_resid = nb > 0.0 ? best : 0.0;
   res.applies = applies;
-  res.Aeff = tk_aeff(ctx, a, E, tk_view(best_u), B);
+  res.Aeff = tk_aeff(ctx, a, E, tk_view(best_u), B, ga);
   return res;
 }
 

@@ -67,7 +67,8 @@ def test_ga_not_supported(ctx):
         ctx.problem(a, lrfg.FULL, disc=lrfg.GA)
     assert e.value.status == 6
     a = random_field((13, 13), seed=1)
-    for kw in (dict(fmt=lrfg.TUCKER, rank=3), dict(fmt=lrfg.FULL, prec=lrfg.MIXED)):
+    B = [[0.5, 0.1], [0.1, 0.3]]
+    for kw in (dict(fmt=lrfg.FULL, prec=lrfg.MIXED), dict(fmt=lrfg.TUCKER, rank=3, B=B), dict(fmt=lrfg.TT, rank=3, B=B)):
         fmt = kw.pop("fmt")
         with pytest.raises(lrfg.LrfgError) as e:
             ctx.problem(a, fmt, disc=lrfg.GA, **kw)
@@ -115,3 +116,66 @@ def test_untruncated_tt_ga_equals_full_ga(ctx):
     tt, _ = ctx.problem(lrfg.TTensor.from_numpy(lr.tt_from_separable(terms, w)), lrfg.TT, rank=N, tol=1e-12,
                         maxit=400, stop_on_increase=False, disc=lrfg.GA).solve(E, want_field=False)
     assert abs(tt.Aeff - full.Aeff) <= 1e-9 * full.Aeff
+
+
+# ---- Ga in Tucker and CP format -------------------------------------------------------------------------
+def _random_tucker(shape, ranks, seed):
+    rng = np.random.default_rng(seed)
+    core = rng.standard_normal(tuple(ranks))
+    factors = [rng.standard_normal((n, r)) / np.sqrt(n) for n, r in zip(shape, ranks)]
+    return core, factors
+
+
+def _tucker_coeff(fmt, terms, w):
+    """The coefficient's exact Tucker form, and the oracle's form of the same format."""
+    tk = lr.tucker_from_separable(terms, w)
+    return tk, (tk if fmt == "tucker" else lr.cp_from_separable(terms, w))
+
+
+@pytest.mark.parametrize("fmt,d,N,rank,rx", [("tucker", 2, 13, 4, (3, 3)), ("tucker", 3, 13, 3, (3, 2, 3)),
+                                             ("cp", 2, 25, 5, (4, 4))])
+def test_tucker_cp_ga_apply_and_rhs(ctx, fmt, d, N, rank, rx):
+    shape = (N,) * d
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    tk, a_lr = _tucker_coeff(fmt, terms, w)
+    op = lr.LowRankGa(a_lr, shape, rank=rank, pinv_eps=0.1, fmt=fmt)
+    core, factors = _random_tucker(shape, rx, seed=23)
+    if fmt == "tucker":
+        ref = np.real(lr.tucker_full(*lr.tucker_idft(op.apply(lr.tucker_dft((core, factors))))))
+        refb = np.real(lr.tucker_full(*lr.tucker_idft(op.rhs(np.eye(d)[0]))))
+    else:  # a rank-r CP operand: the Tucker input with a diagonal core
+        core = np.diag(np.diag(core))
+        cp = (np.diag(core).copy(), factors[0], factors[1])
+        ref = np.real(lr.cp_full(lr.cp_idft(op.apply(lr.cp_dft(cp)))))
+        refb = np.real(lr.cp_full(lr.cp_idft(op.rhs(np.eye(d)[0]))))
+    P = ctx.problem(lrfg.TuckerTensor.from_numpy(*tk), lrfg.TUCKER if fmt == "tucker" else lrfg.CP, rank=rank,
+                    pinv_eps=0.1, disc=lrfg.GA)
+    out = P.apply(ctx.field_from_tucker(lrfg.TuckerTensor.from_numpy(core, factors))).full()
+    # the Tucker operator's bound (its P~^-1 product's collinear factors; see test_gpu_tucker)
+    assert rel(out, ref) <= 1e-6
+    assert rel(P.rhs(np.eye(d)[0]).full(), refb) <= 1e-7
+
+
+@pytest.mark.parametrize("fmt,d,N,rank", [("tucker", 2, 25, 6), ("tucker", 3, 13, 4), ("cp", 2, 25, 6)])
+def test_tucker_cp_ga_solve(ctx, fmt, d, N, rank):
+    _, terms, w = smoothed_cube(d, N, contrast=10.0)
+    tk, a_lr = _tucker_coeff(fmt, terms, w)
+    E = np.eye(d)[0]
+    ref = lr.minres(lr.LowRankGa(a_lr, (N,) * d, rank=rank, pinv_eps=0.1, fmt=fmt), E, tol=1e-10, maxit=40)
+    P = ctx.problem(lrfg.TuckerTensor.from_numpy(*tk), lrfg.TUCKER if fmt == "tucker" else lrfg.CP, rank=rank,
+                    tol=1e-10, maxit=40, disc=lrfg.GA)
+    res, u = P.solve(E)
+    assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])
+    assert abs(P.aeff(E, u) - res.Aeff) <= 1e-12 * res.Aeff
+
+
+@pytest.mark.parametrize("fmt", ["tucker", "cp"])
+def test_untruncated_tucker_cp_ga_equals_full_ga(ctx, fmt):
+    d, N = 2, 13
+    a, terms, w = square_inclusion(d, N)
+    E = np.eye(d)[0]
+    full, _ = ctx.problem(a, lrfg.FULL, disc=lrfg.GA, tol=1e-12, maxit=3000).solve(E, want_field=False)
+    tk = lr.tucker_from_separable(terms, w)
+    lo, _ = ctx.problem(lrfg.TuckerTensor.from_numpy(*tk), lrfg.TUCKER if fmt == "tucker" else lrfg.CP, rank=N,
+                        tol=1e-12, maxit=400, stop_on_increase=False, disc=lrfg.GA).solve(E, want_field=False)
+    assert abs(lo.Aeff - full.Aeff) <= 1e-9 * full.Aeff
