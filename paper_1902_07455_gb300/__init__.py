@@ -407,7 +407,7 @@ class Context:
         rank cap of a grid coefficient's TT compression (0: ``rank``).  ``rank_start`` > 0: rank-adapting
         MinRes from that rank up to ``rank`` in steps of ``rank_step`` (TT).  ``B``: constant symmetric
         positive semidefinite d x d anisotropic part, A~ = a I + B.  ``disc``: GANI, or GA (exact integration
-        of the pixel-wise constant material on the double grid; FULL, FP64).  ``sketch_over`` > 0 (TT, GaNi):
+        of the pixel-wise constant material on the double grid; FP64, every format, isotropic for low rank).  ``sketch_over`` > 0 (TT, GaNi):
         the material and P~^-1 products are truncated by the randomised rounding with a sketch of ranks
         rank + sketch_over from SplitMix64 stream ``sketch_seed``; ``sketch_keep``: those truncations keep the
         sketch's rank (no final rounding to ``rank``)."""

@@ -1382,8 +1382,9 @@ lrfg_status lrfg_create(lrfg_ctx** out, int device, void* stream, size_t budget)
     ctx->pool = new DevicePool(budget);
     LRFG_CUDA(cudaMalloc(&ctx->work_dev, sizeof(double) * 2 * KC_COUNT));
     LRFG_CUDA(cudaMemsetAsync(ctx->work_dev, 0, sizeof(double) * 2 * KC_COUNT, ctx->stream));
-    LRFG_CUDA(cudaMalloc(&ctx->splitk_cnt, sizeof(unsigned int) * kSplitKCounters));
-    LRFG_CUDA(cudaMemsetAsync(ctx->splitk_cnt, 0, sizeof(unsigned int) * kSplitKCounters, ctx->stream));
+    const size_t ncnt = (size_t)kSplitKCounters * (1 + kSplitKGroups);
+    LRFG_CUDA(cudaMalloc(&ctx->splitk_cnt, sizeof(unsigned int) * ncnt));
+    LRFG_CUDA(cudaMemsetAsync(ctx->splitk_cnt, 0, sizeof(unsigned int) * ncnt, ctx->stream));
     LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != LRFG_OK) {

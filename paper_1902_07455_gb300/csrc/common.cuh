@@ -201,8 +201,10 @@ class KTimer {
   cudaEvent_t start_ = nullptr;
 };
 
-// capacity of the split-K arrival counters (a split product has fewer than 4 x 2 x 152 output tiles)
+// capacity of the split-K arrival counters (a split product has fewer than 4 x 2 x 152 output tiles), and
+// of the group counters of the two-level reduction (at most kSplitKGroups groups per tile), stored after them
 constexpr int kSplitKCounters = 4096;
+constexpr int kSplitKGroups = 64;
 
 // the device counter pair (flops, bytes) of class kc
 inline double* work_counter(lrfg_ctx* ctx, KClass kc) { return ctx->work_dev ? ctx->work_dev + 2 * (int)kc : nullptr; }

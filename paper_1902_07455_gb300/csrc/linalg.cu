@@ -17,7 +17,10 @@ namespace lrfg {
 // through shared memory in k-steps of 32, and long K is split across blocks until about two blocks per SM are busy (split-K: each
 // split writes its partial block to a workspace; the last split of a tile to arrive, found by an arrival
 // counter, sums the partials in split order, so every product, and with it every solve, is bitwise
-// reproducible whatever else runs on the GPU, and no second launch is needed).  An output costs two
+// reproducible whatever else runs on the GPU, and no second launch is needed).  With many splits the sum is
+// two-level: the splits form groups of about sqrt(splits); the last split of each group to arrive sums its
+// group's partials in order into a group partial, and the last group sums the group partials in order — the
+// reduction then runs on as many blocks as there are groups instead of on one.  An output costs two
 // shared-memory reads per FMA, far below the shared-memory bandwidth at the FP64 rate.
 // ------------------------------------------------------------------------------------------------
 constexpr int GK = 32;  // k-step
@@ -35,8 +38,9 @@ __device__ __forceinline__ void gemm_fma_rows(T* acc, const T (*As)[TILE + 1], c
 // dynM / dynN (optional, per batch item): the product is computed only for rows < dynM[b] * mulM and
 // columns < dynN[b] * mulN (data-dependent active sizes, e.g. numerical ranks); the rest of C is not
 // written.  With splits > 1 the partial sums go to part[((split * batches + item) * M + row) * N + column]
-// (M, N the static sizes).  TILE = 64 (16 outputs per thread) or 32 (4 per thread, for small products:
-// four times the blocks, so that a product of a few tiles still spreads over the SMs).
+// (M, N the static sizes).  TILE = 64 (16 outputs per thread), 32 (4 per thread, for small products:
+// four times the blocks, so that a product of a few tiles still spreads over the SMs) or 16 (one per thread,
+// for products of one or a few 32-tiles with a short K, see gemm_impl).
 // T = double (the FP64 products) or float (the FP32 sketch products of the mixed-precision path).
 template <bool TA, bool TB, int TILE, typename T>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha_d, const T* __restrict__ A,
@@ -44,7 +48,8 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
                                                     long long sB, double beta_d, T* C, int ldc, long long sC,
                                                     int splits, int kchunk, const int* __restrict__ dynM, int mulM,
                                                     const int* __restrict__ dynN, int mulN, double* work,
-                                                    T* __restrict__ part, unsigned int* __restrict__ cnt) {
+                                                    T* __restrict__ part, unsigned int* __restrict__ cnt,
+                                                    int gsize) {
   constexpr int NMAX = TILE * TILE / 256;
   const T alpha = (T)alpha_d, beta = (T)beta_d;
   __shared__ T As[GK][TILE + 1];
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
         case 1: gemm_fma_rows<1, TILE>(acc, As, Bs, pk, kc); break;
         default: break;
       }
-    } else {
+    } else if constexpr (NMAX == 4) {
       switch (nact) {
         case 4: gemm_fma_rows<4, TILE>(acc, As, Bs, pk, kc); break;
         case 3: gemm_fma_rows<3, TILE>(acc, As, Bs, pk, kc); break;
@@ -121,6 +126,8 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
         case 1: gemm_fma_rows<1, TILE>(acc, As, Bs, pk, kc); break;
         default: break;
       }
+    } else {
+      if (nact == 1) gemm_fma_rows<1, TILE>(acc, As, Bs, pk, kc);
     }
     __syncthreads();
   }
@@ -132,14 +139,45 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       if (j >= nact) break;
       P[split * pstride + (size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff)] = acc[j];
     }
-    // the last split of this tile to arrive sums all partials in split order
     __shared__ unsigned int s_last;
+    const size_t tile_id = ((size_t)batch * gridDim.y / splits + bm) * gridDim.x + bn;
+    unsigned int* c = cnt + tile_id;
+    // the partials the tile's last block sums: every split's (one level), or every group's (two levels: the
+    // group partials sit after the splits' in the workspace)
+    int nsum = splits;
+    const T* S = P;
+    if (gsize < splits) {
+      const int ngroups = (splits + gsize - 1) / gsize;
+      const int g = split / gsize, g0 = g * gsize, gn = min(gsize, splits - g0);
+      unsigned int* cg = cnt + kSplitKCounters + tile_id * kSplitKGroups + g;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(cg, 1u);
+        s_last = (prev == (unsigned int)gn - 1u) ? 1u : 0u;
+      }
+      __syncthreads();
+      if (!s_last) return;
+      __threadfence();
+      // the group's last split: its partials in split order into group partial g
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j >= nact) break;
+        const size_t off = (size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff);
+        T v = (T)0;
+        for (int s = g0; s < g0 + gn; ++s) v += __ldcg(P + s * pstride + off);
+        P[(size_t)(splits + g) * pstride + off] = v;
+      }
+      if (threadIdx.x == 0) *cg = 0u;
+      nsum = ngroups;
+      S = P + (size_t)splits * pstride;
+    }
+    // the last (split or group) of this tile to arrive sums the partials in order
     __threadfence();
     __syncthreads();
-    unsigned int* c = cnt + ((size_t)batch * gridDim.y / splits + bm) * gridDim.x + bn;
     if (threadIdx.x == 0) {
       const unsigned int prev = atomicAdd(c, 1u);
-      s_last = (prev == (unsigned int)splits - 1u) ? 1u : 0u;
+      s_last = (prev == (unsigned int)nsum - 1u) ? 1u : 0u;
     }
     __syncthreads();
     if (!s_last) return;
@@ -149,7 +187,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       if (j >= nact) break;
       const size_t off = (size_t)(m0 + (pk[j] >> 16)) * Ns + n0 + (pk[j] & 0xffff);
       T v = (T)0;
-      for (int s = 0; s < splits; ++s) v += __ldcg(P + s * pstride + off);
+      for (int s = 0; s < nsum; ++s) v += __ldcg(S + s * pstride + off);
       T* cp = C + (size_t)(m0 + (pk[j] >> 16)) * ldc + n0 + (pk[j] & 0xffff);
       *cp = (beta_d == 0.0) ? alpha * v : alpha * v + beta * (*cp);
     }
@@ -168,23 +206,24 @@ template <int TILE, typename T>
 static void launch_dgemm(lrfg_ctx* ctx, int transA, int transB, dim3 grid, double flops, double bytes, int M, int N,
                          int K, double alpha, const T* A, int lda, long long sA, const T* B, int ldb,
                          long long sB, double beta, T* C, int ldc, long long sC, int splits, int kchunk,
-                         const int* dynM, int mulM, const int* dynN, int mulN, double* work, T* part) {
+                         const int* dynM, int mulM, const int* dynN, int mulN, double* work, T* part,
+                         int gsize = 1 << 30) {
   if (!transA && !transB)
     LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<false, false, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
-        ctx->splitk_cnt));
+        ctx->splitk_cnt, gsize));
   else if (transA && !transB)
     LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<true, false, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
-        ctx->splitk_cnt));
+        ctx->splitk_cnt, gsize));
   else if (!transA && transB)
     LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<false, true, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
-        ctx->splitk_cnt));
+        ctx->splitk_cnt, gsize));
   else
     LRFG_LAUNCH_KC(ctx, (std::is_same<T, float>::value ? KC_GEMM32 : KC_GEMM), flops, bytes, dgemm_kernel<true, true, TILE, T><<<grid, 256, 0, ctx->stream>>>(
         M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part,
-        ctx->splitk_cnt));
+        ctx->splitk_cnt, gsize));
 }
 
 __global__ void scale_matrix_kernel(double* C, int M, int N, int ldc, long long sC, int batch, double beta) {
@@ -233,10 +272,14 @@ static void gemm_impl(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K
   // spreads those products)
   auto fill = [&](long long blocks) { return (double)blocks / (double)(((blocks + nsm - 1) / nsm) * nsm); };
   const bool dyn = dynM || dynN;
-  const int tile = (!dyn && (std::min(M, N) <= 32 || active_tiles(64) < nsm ||
-                             fill(active_tiles(32)) > fill(active_tiles(64)) + 0.05))
-                       ? 32
-                       : 64;
+  int tile = (!dyn && (std::min(M, N) <= 32 || active_tiles(64) < nsm ||
+                       fill(active_tiles(32)) > fill(active_tiles(64)) + 0.05))
+                 ? 32
+                 : 64;
+  // 16 x 16 tiles when even the largest split of the 32-tiles leaves most SMs idle: one k-step of a 32-tile
+  // block is 32 K FMAs, 8 us of one SM's FP64 pipe, so a product of a few 32-tiles whose K is too short to
+  // split further runs on a few SMs for that long; 16-tiles give four times the blocks at a quarter of the work
+  if (tile == 32 && active_tiles(32) * std::max(1, K / GK) < nsm) tile = 16;
   const long long active = active_tiles(tile);
   // split long K until about two blocks per SM are busy, without passing that (a second, partial round of
   // blocks would cost as much as the first)
@@ -253,19 +296,29 @@ static void gemm_impl(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K
   LRFG_REQUIRE((long long)bmn * splits < 65536, "gemm too many row blocks x splits");
   if (splits > 1)
     LRFG_REQUIRE((long long)bmn * bnn * batch <= kSplitKCounters, "split-K product with too many output tiles");
+  // two-level reduction of the partials from 9 splits on: groups of ceil(sqrt(splits))
+  int gsize = 1 << 30, ngroups = 0;
+  if (splits > 8) {
+    gsize = (int)std::ceil(std::sqrt((double)splits));
+    ngroups = (splits + gsize - 1) / gsize;
+    LRFG_REQUIRE(ngroups <= kSplitKGroups, "split-K product with too many groups (%d)", ngroups);
+  }
   DBuf<T> part;
-  if (splits > 1) part = DBuf<T>(ctx->pool, (size_t)splits * M * N * batch);
+  if (splits > 1) part = DBuf<T>(ctx->pool, (size_t)(splits + ngroups) * M * N * batch);
   // products with data-dependent sizes count their work on the device
   double* work = (dynM || dynN) ? work_counter(ctx, KC_GEMM) : nullptr;
   const double flops = work ? 0.0 : 2.0 * M * N * (double)K * batch;
   const double bytes = work ? 0.0 : sizeof(T) * ((double)M * K + (double)K * N + (double)M * N) * batch;
   dim3 grid(bnn, bmn * splits, batch);
-  if (tile == 32)
+  if (tile == 16)
+    launch_dgemm<16, T>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get(), gsize);
+  else if (tile == 32)
     launch_dgemm<32, T>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
+                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get(), gsize);
   else
     launch_dgemm<64, T>(ctx, transA, transB, grid, flops, bytes, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get());
+                     sC, splits, kchunk, dynM, mulM, dynN, mulN, work, part.get(), gsize);
 }
 
 void gemm_dyn(lrfg_ctx* ctx, int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,

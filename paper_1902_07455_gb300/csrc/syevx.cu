@@ -466,12 +466,15 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
   double* lam = beta + nl;     // kl
   // the vectors, their LU factors and the reflectors in shared memory where they fit (flags 1, 2, 4): the
   // solves, the re-orthogonalisation and the back-transformation are dependent chains of their loads
+  // strides in shared memory are odd numbers of doubles, so that the lanes of a warp walking different vectors
+  // (inverse iteration: one lane per vector) or different rows (the warp sums) hit different banks
+  const int npad = nl | 1;
   double* next = lam + kl;
   double* Y = g.Y;
   double* lu = g.lu;
   double* W = g.W;
-  if (smem_flags & 1) { Y = next; next += (size_t)kl * nl; }
-  if (smem_flags & 2) { lu = next; next += (size_t)kl * 5 * nl; }
+  if (smem_flags & 1) { Y = next; next += (size_t)kl * npad; }
+  if (smem_flags & 2) { lu = next; next += (size_t)kl * 5 * npad; }
   if (smem_flags & 4) W = next;
   const size_t nnl = (size_t)nl * nl;
   const bool viaB = g.hdr[4] != 0.0;
@@ -479,6 +482,9 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
   const int k = min(kl, n);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+  const int yst = (smem_flags & 1) ? npad : n;       // between vectors of Y
+  const int fst = (smem_flags & 2) ? npad : n;       // between the fields of one vector's LU factors
+  const int wld = (smem_flags & 4) ? npad : n;       // leading dimension of the reflectors
   double* wout = wg + (size_t)blockIdx.x * nl;
   double* Vout = Vg + (size_t)blockIdx.x * (size_t)nl * ldv;
   for (int i = tid; i < n; i += nthr) {
@@ -488,14 +494,14 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
   }
   for (int t = tid; t < k; t += nthr) lam[t] = g.lam[t];
   if (smem_flags & 4)
-    for (size_t t = tid; t < (size_t)n * n; t += nthr) W[t] = g.W[t];
+    for (size_t t = tid; t < (size_t)n * n; t += nthr) W[(t / n) * wld + t % n] = g.W[t];
   __syncthreads();
   const double tnorm = fmax(fabs(g.hdr[1]), fabs(g.hdr[2]));
   if (tnorm == 0.0) {
     // the zero matrix: eigenvalues 0, eigenvectors the unit vectors
     for (size_t q = tid; q < (size_t)k * n; q += nthr) {
       const int t = (int)(q / n), i = (int)(q - (q / n) * n);
-      Y[q] = (i == t) ? 1.0 : 0.0;
+      Y[(size_t)t * yst + i] = (i == t) ? 1.0 : 0.0;
     }
   } else {
   // separate exactly equal eigenvalues slightly so that their factorisations differ
@@ -509,23 +515,23 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
   // 3. inverse iteration, three passes with cluster re-orthogonalisation
   const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
   for (int t = tid; t < k; t += nthr) {
-    double* y = Y + (size_t)t * n;
+    double* y = Y + (size_t)t * yst;
     // deterministic start vector with entries in [0.5, 1.5)
     unsigned h = 2166136261u ^ (unsigned)(t * 2654435761u);
     for (int i = 0; i < n; ++i) {
       h = h * 1664525u + 1013904223u;
       y[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
     }
-    double* f = lu + (size_t)t * 5 * n;
-    trid_factor(d, e, n, lam[t], tiny, f, f + n, f + 2 * n, f + 3 * n, (int*)(f + 4 * n));
+    double* f = lu + (size_t)t * 5 * fst;
+    trid_factor(d, e, n, lam[t], tiny, f, f + fst, f + 2 * fst, f + 3 * fst, (int*)(f + 4 * fst));
   }
   __syncthreads();
   const double ortol = 1e-3 * tnorm;
   for (int pass = 0; pass < 3; ++pass) {
     for (int t = tid; t < k; t += nthr) {
-      double* y = Y + (size_t)t * n;
-      const double* f = lu + (size_t)t * 5 * n;
-      trid_solve(n, f, f + n, f + 2 * n, f + 3 * n, (const int*)(f + 4 * n), y);
+      double* y = Y + (size_t)t * yst;
+      const double* f = lu + (size_t)t * 5 * fst;
+      trid_solve(n, f, f + fst, f + 2 * fst, f + 3 * fst, (const int*)(f + 4 * fst), y);
       double s = 0.0;
       for (int i = 0; i < n; ++i) s += y[i] * y[i];
       if (s > 0.0 && isfinite(s)) {
@@ -542,10 +548,10 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
     // block barrier: the pairs are a dependent chain, and barriers between them cost more than the warp's sums)
     if (tid < 32) {
       for (int t = 1; t < k; ++t) {
-        double* yt = Y + (size_t)t * n;
+        double* yt = Y + (size_t)t * yst;
         bool touched = false;
         for (int s2 = t - 1; s2 >= 0 && lam[s2] - lam[t] <= ortol; --s2) {
-          const double* ys = Y + (size_t)s2 * n;
+          const double* ys = Y + (size_t)s2 * yst;
           double dp = 0.0;
           for (int i = tid; i < n; i += 32) dp += ys[i] * yt[i];
           dp = warp_sum(dp);
@@ -567,16 +573,16 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
 
   // 4. back-transformation x = H_0 H_1 ... H_{n-3} y (one warp per vector; the reflectors are read-only)
   for (int t = warp; t < k; t += nw) {
-    double* yv = Y + (size_t)t * n;
+    double* yv = Y + (size_t)t * yst;
     for (int j = n - 3; j >= 0; --j) {
       const double b = beta[j];
       if (b == 0.0) continue;
       const int m = n - j - 1;
       double* y = yv + (j + 1);
       double s = 0.0;
-      for (int i = lane; i < m; i += 32) s += W[(size_t)(j + 1 + i) * n + j] * y[i];
+      for (int i = lane; i < m; i += 32) s += W[(size_t)(j + 1 + i) * wld + j] * y[i];
       s = b * warp_sum(s);
-      for (int i = lane; i < m; i += 32) y[i] -= s * W[(size_t)(j + 1 + i) * n + j];
+      for (int i = lane; i < m; i += 32) y[i] -= s * W[(size_t)(j + 1 + i) * wld + j];
       __syncwarp();
     }
   }
@@ -590,7 +596,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
   if (!viaB) {
     for (size_t q = tid; q < (size_t)k * n; q += nthr) {
       int t = (int)(q / n), i = (int)(q - (q / n) * n);
-      Vout[(size_t)i * ldv + t] = Y[(size_t)t * n + i];
+      Vout[(size_t)i * ldv + t] = Y[(size_t)t * yst + i];
     }
     return;
   }
@@ -603,7 +609,7 @@ __global__ void __launch_bounds__(kSyevxThreads) syevx_vec_kernel(int nl, int kl
     const int t = (int)(q / nA), i = (int)(q - (q / nA) * nA);
     const double sg = lam[t] > 0.0 ? sqrt(lam[t]) : 0.0;
     double acc = 0.0;
-    for (int l = 0; l < n; ++l) acc = fma(B[(size_t)i * nl + l], Y[(size_t)t * n + l], acc);
+    for (int l = 0; l < n; ++l) acc = fma(B[(size_t)i * nl + l], Y[(size_t)t * yst + l], acc);
     U[q] = sg > 0.0 ? acc / sg : 0.0;
   }
   __syncthreads();
@@ -678,7 +684,9 @@ static void syevx_launch(lrfg_ctx* ctx, const double* A, double* w, double* V, i
   // K3: the vectors, then their LU factors, then the reflectors in shared memory while they fit
   size_t smem3 = sizeof(double) * (40 + 3 * (size_t)n + (size_t)k);
   int flags3 = 0;
-  const size_t parts[3] = {sizeof(double) * (size_t)k * n, sizeof(double) * (size_t)k * 5 * n, wbytes};
+  const size_t npad = (size_t)(n | 1);  // K3's odd shared-memory strides
+  const size_t parts[3] = {sizeof(double) * (size_t)k * npad, sizeof(double) * (size_t)k * 5 * npad,
+                           sizeof(double) * (size_t)n * npad};
   for (int q = 0; q < 3; ++q)
     if (smem3 + parts[q] <= lim) {
       smem3 += parts[q];
