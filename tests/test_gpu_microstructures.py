@@ -49,18 +49,19 @@ def test_microstructures_together_equal_separate_solves(ctx, d, N, rank, over, a
         P.free()
 
 
-# a fixed number of iterations on both sides (no stopping test that a rounding-level difference could move)
+# a fixed number of iterations on both sides, few enough that the residual still falls monotonically (at the
+# truncation floor the best iterate moves with the rounding order)
 @pytest.mark.parametrize("d,N,rank,over", [(3, 21, 5, 5), (2, 45, 8, 0)])
 def test_microstructures_together_match_oracle(ctx, d, N, rank, over):
     coeffs = _coeffs(d, N, 5, seeds=[21, 22, 23])
     Es = [np.eye(d)[0], np.eye(d)[1], np.ones(d)]
     sketch = (over, 0) if over else None
-    Ps = [ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-14, maxit=12,
+    Ps = [ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-14, maxit=6,
                       stop_on_increase=False, sketch_over=over) for a in coeffs]
     together = lrfg.Problem.solve_together(Ps, Es)
     for a, m, E in zip(coeffs, together, Es):
         op = lr.LowRankGaNi(a, (N,) * d, fmt="tt", rank=rank, pinv_eps=0.1, sketch=sketch)
-        ref = lr.minres(op, np.asarray(E), tol=1e-14, maxit=12, stop_on_increase=False)
+        ref = lr.minres(op, np.asarray(E), tol=1e-14, maxit=6, stop_on_increase=False)
         assert abs(m.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (E, m.Aeff, ref["Aeff"], m.iters, ref["iters"])
     for P in Ps:
         P.free()
