@@ -754,9 +754,12 @@ class LowRankGa:
     and b~ = - T P~^-1 grad^* I* F_M A~ E (Eq. (ls_Ga_fourier) with the truncations placed as in Eq.
     (Pls_lowrank)), A~ the modified coefficient of a pixel-wise constant a given in the same format as its
     pixel values on the grid N; I, I* and the DFTs act mode by mode (on carriage fibres or factor columns).
-    Interface of ``LowRankGaNi`` (for ``minres``)."""
+    Interface of ``LowRankGaNi`` (for ``minres``).  A constant anisotropic part B (Sec. 4.4) is part of the
+    material A = a I + B whose modified coefficient is taken: A~ = a~ I + B 1~, 1~ the modified coefficient of the
+    constant 1 (the same mode maps applied to the all-ones tensor), so component a of the product on the double
+    grid is a~ e_a + sum_b B[a, b] 1~ e_b before its T."""
 
-    def __init__(self, a_tt, shape, rank=10, pinv_eps=0.1, rank_tol=None, fmt="tt"):
+    def __init__(self, a_tt, shape, rank=10, pinv_eps=0.1, rank_tol=None, fmt="tt", B=None):
         self.f = FORMATS[fmt]
         self.fmt = fmt
         self._map = MODE_MAPS[fmt]
@@ -764,13 +767,16 @@ class LowRankGa:
         self.d = len(self.shape)
         self.rank = rank
         self.rank_tol = rank_tol
-        self.B = None
+        self.B = None if B is None else np.asarray(B, dtype=np.float64)
         self.K = [_fg.frequencies(n).astype(np.float64) for n in self.shape]
         self.mats = [ga_matrices(n) for n in self.shape]
         At = _as_float(fmt, a_tt)
+        Ones = self.f.sep([[np.ones(n) for n in self.shape]])
         for j in range(self.d):
             At = self._map(At, j, self.mats[j][2])
+            Ones = self._map(Ones, j, self.mats[j][2])
         self.At = At                                             # values on the double grid
+        self.Ones = Ones                                         # 1~, the modified coefficient of 1
         xmax = float(sum(((n - 1) // 2) ** 2 for n in self.shape))
         t, w = _expsum.expsum_inverse(xmax, pinv_eps)
         self.pinv_t, self.pinv_w = t, w
@@ -796,8 +802,15 @@ class LowRankGa:
     def apply(self, vh):
         f = self.f
         acc = None
+        eds = [self._grad_double(vh, a) for a in range(self.d)] if self.B is not None else None
         for a in range(self.d):
-            w = self.T(f.had(self.At, self._grad_double(vh, a)))   # T A~ e_a on the double grid
+            ed = eds[a] if eds is not None else self._grad_double(vh, a)
+            m = f.had(self.At, ed)
+            if self.B is not None:
+                for b in range(self.d):
+                    if self.B[a, b] != 0.0:
+                        m = f.add(m, f.scale(f.had(self.Ones, eds[b]), float(self.B[a, b])))
+            w = self.T(m)                                            # T A~ e_a on the double grid
             wh = self._project(f.dft(w))                           # I* F_M
             term = f.mmul(wh, a, -2j * np.pi * self.K[a])
             acc = term if acc is None else f.add(acc, term)
@@ -819,16 +832,28 @@ class LowRankGa:
 
     def homogenised_coefficient(self, uh, E) -> float:
         """sum over the double grid of A~ |E + e|^2 (exact integration), by low-rank contractions:
-        |E|^2 <A~, 1> + 2 sum_a E_a <A~, e_a> + sum_a <A~ e_a, e_a>."""
+        |E|^2 <A~, 1> + 2 sum_a E_a <A~, e_a> + sum_a <A~ e_a, e_a>; with B also
+        E.B E <1~, 1> + 2 sum_ab E_a B[a, b] <1~, e_b> + sum_ab B[a, b] <1~ e_a, e_b>."""
         f = self.f
         E = np.asarray(E, dtype=np.float64)
         ones = f.sep([[np.ones(2 * n - 1) for n in self.shape]])
         val = float(E @ E) * np.real(f.dot(ones, self.At))
+        es = []
         for a in range(self.d):
             e = self._grad_double(uh, a)
+            es.append(e)
             ae = f.had(self.At, e)
             val += 2.0 * float(E[a]) * np.real(f.dot(ones, ae))
             val += np.real(f.dot(e, ae))
+        if self.B is not None:
+            val += float(E @ self.B @ E) * np.real(f.dot(ones, self.Ones))
+            for a in range(self.d):
+                for b in range(self.d):
+                    if self.B[a, b] == 0.0:
+                        continue
+                    oe = f.had(self.Ones, es[a])
+                    val += 2.0 * float(E[b] * self.B[b, a]) * np.real(f.dot(ones, oe))
+                    val += float(self.B[a, b]) * np.real(f.dot(oe, es[b]))
         return float(val)
 
     def full_field(self, uh) -> np.ndarray:

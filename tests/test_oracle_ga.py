@@ -68,8 +68,9 @@ def test_coefficient_matches_quadrature_of_the_dirichlet_kernel():
         assert abs(Ah[i0, i1] - quad_fourier(a, (ks[i0], ks[i1]))) <= 1e-13 * abs(Ah[0, 0])
 
 
-def dense_galerkin(a, E):
-    """Minimise int a |E + grad u|^2 over u in T_N by the dense Galerkin system with quadrature A^(k - l)."""
+def dense_galerkin(a, E, B=None):
+    """Minimise int (E + grad u).(a I + B)(E + grad u) over u in T_N by the dense Galerkin system with quadrature
+    A^(k - l); a constant B adds 4 pi^2 l.B k on the diagonal (k = l) and E.B E to the energy."""
     N = a.shape[0]
     ks = fg.frequencies(N)
     K2 = [(k0, k1) for k0 in ks for k1 in ks if (k0, k1) != (0, 0)]
@@ -86,9 +87,12 @@ def dense_galerkin(a, E):
     for i, l in enumerate(K2):
         for j, k in enumerate(K2):
             K[i, j] = 4 * np.pi ** 2 * (k[0] * l[0] + k[1] * l[1]) * Ahat((k[0] - l[0], k[1] - l[1]))
+            if B is not None and i == j:
+                K[i, j] += 4 * np.pi ** 2 * (np.array(l) @ B @ np.array(k))
         rhs[i] = 2j * np.pi * (E[0] * l[0] + E[1] * l[1]) * Ahat((-l[0], -l[1]))
     u = np.linalg.solve(K, rhs)
-    return float(np.real(Ahat((0, 0)) * (E @ E) - np.vdot(u, K @ u)))
+    eBe = 0.0 if B is None else float(E @ B @ E)
+    return float(np.real(Ahat((0, 0)) * (E @ E) + eBe - np.vdot(u, K @ u)))
 
 
 @pytest.mark.parametrize("N,seed", [(5, 1), (7, 2)])
@@ -177,3 +181,19 @@ def test_untruncated_tucker_cp_ga_equals_full_ga(fmt, d, N):
     op = lr.LowRankGa(a_lr, (N,) * d, rank=None, rank_tol=1e-15, fmt=fmt)
     out = lr.minres(op, E, tol=1e-13, maxit=600, stop_on_increase=False)
     assert abs(out["Aeff"] - full["Aeff"]) <= 1e-10 * full["Aeff"]
+
+
+@pytest.mark.parametrize("fmt,N", [("tt", 5), ("tt", 7), ("tucker", 7), ("cp", 5)])
+def test_untruncated_lowrank_ga_with_anisotropy_matches_dense_galerkin(fmt, N):
+    """Low-rank Ga with a constant anisotropic part B (A~ = a~ I + B 1~), untruncated, against the dense
+    Galerkin solve of the anisotropic material assembled from quadrature (d = 2)."""
+    a, terms, w = square_inclusion(2, N)
+    B = np.array([[0.7, 0.25], [0.25, 0.4]])
+    a_lr = {"tt": lr.tt_from_separable, "tucker": lr.tucker_from_separable, "cp": lr.cp_from_separable}[fmt](terms, w)
+    op = lr.LowRankGa(a_lr, (N, N), rank=None, rank_tol=1e-15, fmt=fmt, B=B)
+    for E in (np.array([1.0, 0.0]), np.array([0.3, -1.2])):
+        ref = dense_galerkin(a, E, B)
+        out = lr.minres(op, E, tol=1e-13, maxit=600, stop_on_increase=False)
+        assert abs(out["Aeff"] - ref) <= 1e-10 * ref, (out["Aeff"], ref)
+    # B changes the answer (the pin is not vacuous)
+    assert abs(dense_galerkin(a, np.array([1.0, 0.0])) - dense_galerkin(a, np.array([1.0, 0.0]), B)) > 0.1

@@ -294,3 +294,27 @@ def _bad_round_sketch(carry=True, final=True, right_sweep_from_left=False):
 def test_randomised_rounding_slips(monkeypatch, variant):
     monkeypatch.setattr(sk_mod, "tt_round_sketch", _bad_round_sketch(**variant))
     _must_fail(tsk.test_exact_when_the_sketch_covers_the_ranks, (7, 9, 11), [4, 5], 6, 3)
+
+
+@pytest.mark.parametrize("variant", ["plain_ones", "no_b_in_aeff"])
+def test_ga_anisotropy_slips(monkeypatch, variant):
+    """Low-rank Ga with B: the anisotropic part multiplied by the grid's plain ones instead of the modified
+    coefficient of 1, or left out of A_eff."""
+    import tests.test_oracle_ga as tg
+    orig_init = lr.LowRankGa.__init__
+    if variant == "plain_ones":
+        def init(self, *args, **kw):
+            orig_init(self, *args, **kw)
+            self.Ones = self.f.sep([[np.ones(2 * n - 1) for n in self.shape]])
+        monkeypatch.setattr(lr.LowRankGa, "__init__", init)
+    else:
+        orig_aeff = lr.LowRankGa.homogenised_coefficient
+
+        def aeff(self, uh, E):
+            B, self.B = self.B, None
+            try:
+                return orig_aeff(self, uh, E)
+            finally:
+                self.B = B
+        monkeypatch.setattr(lr.LowRankGa, "homogenised_coefficient", aeff)
+    _must_fail(tg.test_untruncated_lowrank_ga_with_anisotropy_matches_dense_galerkin, "tt", 5)
