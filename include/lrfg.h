@@ -138,8 +138,9 @@ typedef struct {
                            statement about the cap's solution: below it the residual is truncated at the
                            lower rank); at the cap it stops as the fixed-rank iteration, by stop_on_increase */
   int rank_step;        /* rank increment of the rank-adapting MinRes (0 selects 1) */
-  lrfg_disc disc;       /* LRFG_GANI (default), or LRFG_GA with LRFG_FP64 (every solution format; the low-rank
-                           formats with an isotropic coefficient, B = 0): the grid values of a
+  lrfg_disc disc;       /* LRFG_GANI (default), or LRFG_GA with LRFG_FP64 (every solution format, with or without
+                           an anisotropic part B, which enters as part of the material, A~ = a~ I + B 1~): the
+                           grid values of a
                            are read as a pixel-wise constant material (a_p on the cell of side 1/N centred at
                            x_p), its integrals against the double-grid basis are computed exactly (DoGIP), and
                            A_eff is the exact integral of a |E + grad u|^2.  N_j and the double grid 2N_j - 1

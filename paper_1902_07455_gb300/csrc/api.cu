@@ -206,10 +206,11 @@ struct lrfg_problem {
   FullGrid gM{};
   DBuf<double> a_ga, wrM;
   DBuf<double2> wcM;
-  // Ga in TT: the modified coefficient on the double grid, and its projection on the grid (right-hand side)
-  TT a_ga_tt, a_down_tt;
+  // Ga in TT: the modified coefficient on the double grid, and its projection on the grid (right-hand side);
+  // with an anisotropic part also the modified coefficient of the constant 1
+  TT a_ga_tt, a_down_tt, ones_ga_tt;
   // Ga in Tucker / CP: the same in Tucker form (tkga views them)
-  TK a_ga_tk, a_down_tk;
+  TK a_ga_tk, a_down_tk, ones_ga_tk;
   TKGa tkga{};
   // randomised rounding (opts.sketch_over > 0): the sketch TT of ranks rank + sketch_over, by rank
   std::map<int, TT> sketches;
@@ -474,19 +475,53 @@ void lr_apply_ga(lrfg_problem* P, const TTView& v, TT& out, int r) {
     for (int j = 0; j < d; ++j)
       khatri_rao(ctx, a.core[j], a.r[j], a.N[j], a.r[j + 1], (j == alpha) ? gu[j].get() : vu.core[j].get(), v.r[j],
                  v.r[j + 1], kr.core[j].get() + (size_t)alpha * kr.elems(j));
-  for (auto& g : gu) g.reset();
-  vu = TTBatch();
-  TTBatch w;
-  tt_round_batch(ctx, batch_view(kr), r, w, tol);  // T on the double grid
-  kr = TTBatch();
-  TTBatch wd;  // I* F_M back to the grid, every item
-  tt_ga_map(ctx, item_view(w, 0), d, P->N, GA_DOWN, wd);
-  w = TTBatch();
   TTView terms[3];
+  TTBatch wd;        // I* F_M back to the grid, every item (isotropic)
+  TTBatch wda[3];    // the same, component by component (anisotropic)
+  if (!P->aniso) {
+    for (auto& g : gu) g.reset();
+    vu = TTBatch();
+    TTBatch w;
+    tt_round_batch(ctx, batch_view(kr), r, w, tol);  // T on the double grid
+    kr = TTBatch();
+    tt_ga_map(ctx, item_view(w, 0), d, P->N, GA_DOWN, wd);
+    for (int alpha = 0; alpha < d; ++alpha) terms[alpha] = item_view(wd, alpha);
+  } else {
+    // A~ = a~ I + B 1~ (1~ the modified coefficient of the constant 1): component a on the double grid is
+    // a~ (.) e_a + sum_b B[a][b] 1~ (.) e_b (a TT sum, zero entries of B skipped), then T there
+    const TTView one = view_of(P->ones_ga_tt);
+    TT oe[3];
+    for (int beta = 0; beta < d; ++beta) {
+      TTView e = item_view(vu, 0);
+      e.core[beta] = gu[beta].get();
+      tt_hadamard(ctx, one, e, oe[beta]);  // 1~ (.) e_b, rank of e_b
+    }
+    for (auto& g : gu) g.reset();
+    vu = TTBatch();
+    for (int alpha = 0; alpha < d; ++alpha) {
+      TTView xs[4];
+      double sc[4];
+      int m = 0;
+      xs[m] = item_view(kr, alpha);
+      sc[m++] = 1.0;
+      for (int beta = 0; beta < d; ++beta) {
+        const double bab = P->B[alpha * 3 + beta];
+        if (bab == 0.0) continue;
+        xs[m] = view_of(oe[beta]);
+        sc[m++] = bab;
+      }
+      TT sum, wa;
+      tt_add_many(ctx, xs, sc, m, sum);
+      tt_round(ctx, view_of(sum), r, wa, tol);  // T on the double grid
+      tt_ga_map(ctx, view_of(wa), 1, P->N, GA_DOWN, wda[alpha]);
+      terms[alpha] = item_view(wda[alpha], 0);
+    }
+    kr = TTBatch();
+  }
   for (int alpha = 0; alpha < d; ++alpha) {
-    terms[alpha] = item_view(wd, alpha);
     double* c = const_cast<double*>(terms[alpha].core[alpha]);
-    fibre_operator(ctx, c, c, wd.r[alpha], wd.N[alpha], wd.r[alpha + 1], LRFG_MUL_DERIV, 0.0, -1.0);
+    fibre_operator(ctx, c, c, terms[alpha].r[alpha], terms[alpha].N[alpha], terms[alpha].r[alpha + 1],
+                   LRFG_MUL_DERIV, 0.0, -1.0);
   }
   TT acc;
   tt_add_many(ctx, terms, nullptr, d, acc);
@@ -634,17 +669,39 @@ double lr_aeff_ga(lrfg_problem* P, const double* E, const TTView& u) {
   double val = EE * tt_dot(ctx, a, view_of(ones));
   TTBatch uu;
   tt_ga_map(ctx, u, 1, M, GA_UP, uu);
+  DBuf<double> gu[3];
+  TTView es[3];
   for (int alpha = 0; alpha < d; ++alpha) {
     DBuf<double> g(ctx->pool, (size_t)u.r[alpha] * u.N[alpha] * u.r[alpha + 1]);
     fibre_operator(ctx, u.core[alpha], g.get(), u.r[alpha], u.N[alpha], u.r[alpha + 1], LRFG_MUL_DERIV, 0.0, 1.0);
-    DBuf<double> gu(ctx->pool, (size_t)u.r[alpha] * M[alpha] * u.r[alpha + 1]);
-    ga_resample(ctx, g.get(), gu.get(), u.r[alpha], u.N[alpha], u.r[alpha + 1], M[alpha], GA_UP);
+    gu[alpha] = DBuf<double>(ctx->pool, (size_t)u.r[alpha] * M[alpha] * u.r[alpha + 1]);
+    ga_resample(ctx, g.get(), gu[alpha].get(), u.r[alpha], u.N[alpha], u.r[alpha + 1], M[alpha], GA_UP);
     TTView e = item_view(uu, 0);
-    e.core[alpha] = gu.get();
+    e.core[alpha] = gu[alpha].get();
+    es[alpha] = e;
     TT ae;
     tt_hadamard(ctx, a, e, ae);
     if (E[alpha] != 0.0) val += 2.0 * E[alpha] * tt_dot(ctx, view_of(ae), view_of(ones));
     val += tt_dot(ctx, view_of(ae), e);
+  }
+  if (P->aniso) {
+    // the part of B 1~: E.B E <1~, 1> + 2 sum_ab E_b B[b][a] <1~ (.) e_a, 1> + sum_ab B[a][b] <1~ (.) e_a, e_b>
+    const TTView one = view_of(P->ones_ga_tt);
+    val += quad_form(P->B, E, d) * tt_dot(ctx, one, view_of(ones));
+    for (int al = 0; al < d; ++al) {
+      TT oe;
+      bool made = false;
+      for (int be = 0; be < d; ++be) {
+        const double bab = P->B[al * 3 + be];
+        if (bab == 0.0) continue;
+        if (!made) {
+          tt_hadamard(ctx, one, es[al], oe);
+          made = true;
+        }
+        val += 2.0 * E[be] * P->B[be * 3 + al] * tt_dot(ctx, view_of(oe), view_of(ones));
+        val += bab * tt_dot(ctx, view_of(oe), es[be]);
+      }
+    }
   }
   return val;
 }
@@ -709,7 +766,14 @@ void full_apply_ga(lrfg_problem* P, const double2* v, double2* out, int precond)
     half_acc_div(ctx, g, (const double2*)P->wc.get(), out, alpha, 1.0, alpha == 0,
                  precond && alpha == g.d - 1 && !P->aniso);                       // grad^*
   }
-  if (P->aniso) half_acc_aniso(ctx, g, v, out, P->B, precond);
+  // constant anisotropic part: its exact integral is the grid's, grad^* F B F^-1 grad^ = 4 pi^2 k.B k, on the
+  // scale of the double-grid product above: A~ carries the double grid's quadrature weight 1 / |M| (a constant
+  // material c gives c / |M| times the GaNi operator), so B enters as B / |M|
+  if (P->aniso) {
+    double Bs[9];
+    for (int i = 0; i < 9; ++i) Bs[i] = P->B[i] / (double)gM.n_real;
+    half_acc_aniso(ctx, g, v, out, Bs, precond);
+  }
 }
 
 template <typename R>
@@ -1729,8 +1793,6 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
     for (int j = 0; j < 3; ++j) P->N[j] = j < coeff->d ? coeff->N[j] : 0;
     P->aniso = check_aniso(P->d, coeff->B, P->B);
     P->ga = opts->disc == LRFG_GA;
-    if (P->ga && P->aniso && opts->fmt != LRFG_FULL)
-      fail(LRFG_ENOTSUP, "LRFG_GA with an anisotropic part is implemented for LRFG_FULL solutions");
     const long long n = grid_size(P->d, P->N);
     // coefficient -> device
     if (coeff->fmt == LRFG_FULL) {
@@ -1816,6 +1878,15 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
           tk_ga_map(ctx, tk_view(P->a_ga_tk), P->N, GA_DOWN, P->a_down_tk);
           P->tkga.a_ga = tk_view(P->a_ga_tk);
           P->tkga.a_down = tk_view(P->a_down_tk);
+          if (P->aniso) {
+            TK one;
+            int r1[3] = {1, 1, 1};
+            tk_alloc(ctx, one, P->d, P->N, r1);
+            fill(ctx, one.core.get(), 1.0, 1);
+            for (int j = 0; j < P->d; ++j) fill(ctx, one.fac[j].get(), 1.0, P->N[j]);
+            tk_ga_map(ctx, tk_view(one), M, GA_EXTEND, P->ones_ga_tk);
+            P->tkga.ones_ga = tk_view(P->ones_ga_tk);
+          }
         } else {
           TTBatch ag, ad;
           tt_ga_map(ctx, view_of(P->a_tt), 1, M, GA_EXTEND, ag);
@@ -1829,6 +1900,16 @@ lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lr
           for (int j = 0; j < P->d; ++j) {
             P->a_ga_tt.core[j] = std::move(ag.core[j]);
             P->a_down_tt.core[j] = std::move(ad.core[j]);
+          }
+          if (P->aniso) {
+            TT one;
+            ones_tt(ctx, P->d, P->N, one);
+            TTBatch og;
+            tt_ga_map(ctx, view_of(one), 1, M, GA_EXTEND, og);
+            P->ones_ga_tt.d = P->d;
+            for (int j = 0; j < 3; ++j) P->ones_ga_tt.N[j] = og.N[j];
+            for (int j = 0; j < 4; ++j) P->ones_ga_tt.r[j] = og.r[j];
+            for (int j = 0; j < P->d; ++j) P->ones_ga_tt.core[j] = std::move(og.core[j]);
           }
         }
       }

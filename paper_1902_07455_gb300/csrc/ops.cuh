@@ -243,8 +243,9 @@ struct TKSolveResult {
 // projection back to the grid (the right-hand side's coefficient), both with the factors of a's pixel values
 // mapped mode by mode
 struct TKGa {
-  TKView a_ga;    // on M
-  TKView a_down;  // on N
+  TKView a_ga;     // on M
+  TKView a_down;   // on N
+  TKView ones_ga;  // on M: the modified coefficient of the constant 1 (with an anisotropic part B)
 };
 TKView tk_view(const TK& x);
 void tk_alloc(lrfg_ctx* ctx, TK& x, int d, const int* N, const int* r);

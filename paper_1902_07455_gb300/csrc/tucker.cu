@@ -436,8 +436,35 @@ void tk_apply(lrfg_ctx* ctx, const TKView& a, const TKView& v, const std::vector
   TK w[3], es[3];
   for (int alpha = 0; alpha < d; ++alpha)
     tk_mode_operator(ctx, v, alpha, LRFG_MUL_DERIV, 0.0, 1.0, es[alpha]);         // gradient, mode alpha
+  // Ga with an anisotropic part: A~ = a~ I + B 1~ on the double grid, component a is a~ (.) e_a +
+  // sum_b B[a][b] 1~ (.) e_b before its T (the gradients interpolated there once, 1~ (.) e_b once)
+  TK eu[3], oe[3];
+  if (ga && B)
+    for (int beta = 0; beta < d; ++beta) {
+      tk_ga_map(ctx, tk_view(es[beta]), ga->a_ga.N, GA_UP, eu[beta]);
+      tk_hadamard(ctx, ga->ones_ga, tk_view(eu[beta]), oe[beta]);
+    }
   for (int alpha = 0; alpha < d; ++alpha) {
     TK ae, wr;
+    if (ga && B) {
+      TK prod, sum, wm;
+      tk_hadamard(ctx, ga->a_ga, tk_view(eu[alpha]), prod);
+      TKView xs[4];
+      double sc[4];
+      int m = 0;
+      xs[m] = tk_view(prod);
+      sc[m++] = 1.0;
+      for (int beta = 0; beta < d; ++beta)
+        if (B[alpha * 3 + beta] != 0.0) {
+          xs[m] = tk_view(oe[beta]);
+          sc[m++] = B[alpha * 3 + beta];
+        }
+      tk_add_many(ctx, xs, sc, m, sum);
+      tk_round(ctx, tk_view(sum), rank, wm, rtol);  // T on the double grid
+      tk_ga_map(ctx, tk_view(wm), v.N, GA_DOWN, wr);
+      tk_mode_operator(ctx, tk_view(wr), alpha, LRFG_MUL_DERIV, 0.0, -1.0, w[alpha]);  // divergence
+      continue;
+    }
     if (ga) {
       tk_material_ga(ctx, *ga, tk_view(es[alpha]), rank, wr, rtol);
       tk_mode_operator(ctx, tk_view(wr), alpha, LRFG_MUL_DERIV, 0.0, -1.0, w[alpha]);  // divergence
@@ -530,7 +557,29 @@ double tk_aeff(lrfg_ctx* ctx, const TKView& a_in, const double* E, const TKView&
     if (E[alpha] != 0.0) val += 2.0 * E[alpha] * tk_dot(ctx, tk_view(ae), tk_view(ones)) / size;
     val += tk_dot(ctx, tk_view(ae), tk_view(e[alpha])) / size;
   }
-  if (B) {
+  if (B && ga) {
+    // the part of B 1~ (exact integration): E.B E <1~, 1> + 2 sum_ab E_b B[b][a] <1~ (.) e_a, 1> +
+    // sum_ab B[a][b] <1~ (.) e_a, e_b>
+    const TKView one = ga->ones_ga;
+    double ebe = 0.0;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) ebe += E[i] * B[i * 3 + j] * E[j];
+    val += ebe * tk_dot(ctx, one, tk_view(ones));
+    for (int al = 0; al < d; ++al) {
+      TK oe;
+      bool made = false;
+      for (int be = 0; be < d; ++be) {
+        const double bab = B[al * 3 + be];
+        if (bab == 0.0) continue;
+        if (!made) {
+          tk_hadamard(ctx, one, tk_view(e[al]), oe);
+          made = true;
+        }
+        val += 2.0 * E[be] * B[be * 3 + al] * tk_dot(ctx, tk_view(oe), tk_view(ones));
+        val += bab * tk_dot(ctx, tk_view(oe), tk_view(e[be]));
+      }
+    }
+  } else if (B) {
     // (E + e).B(E + e) averaged: E.B E + sum_ab B_ab <e_a, e_b> / |N| (e has zero mean)
     for (int i = 0; i < d; ++i)
       for (int j = 0; j < d; ++j) {
