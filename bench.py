@@ -70,6 +70,8 @@ def parse():
                    help="also stop after this many iterations without a new smallest residual (1: the paper's rule, "
                         "Sec. 4.3; 0: off)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tensor", action="store_true",
+                   help="leave out the homogenised tensor's six solves (a reported extra, not the timed step)")
     p.add_argument("--micro", type=int, default=8,
                    help="microstructures of the workload's recipe solved together in lockstep (0: skip)")
     p.add_argument("--format", choices=["tt", "tucker"], default="tt",
@@ -250,6 +252,22 @@ def roofline(stats, fp64_peak=None):
     total = sum(v["ms"] for v in stats.values())
     out.update({"kernel_class": dom, "launches": s["launches"], "avg_launch_ms": per_launch_ms,
                 "share": s["ms"] / total if total > 0 else None, "traffic": None})
+    # every class beside it, against the same denominators (a latency-bound class shows a small fraction: its
+    # launches are one block per small matrix, and its time is the length of a sequential algorithm)
+    alu_peak = fp64_peak if fp64_peak else FP64_DERIVED_TFLOPS
+    out["by_class"] = {}
+    for k, v in stats.items():
+        if not v["launches"] or v["ms"] <= 0:
+            continue
+        if k in ALU_CLASSES:
+            a = v["flops"] / (v["ms"] * 1e-3) / 1e12
+            out["by_class"][k] = {"bound": "alu", "achieved": round(a, 5), "unit": "TFLOP/s", "frac": round(a / alu_peak, 5),
+                                  "share": round(v["ms"] / total, 4), "avg_launch_us": round(1e3 * v["ms"] / v["launches"], 1)}
+        else:
+            a = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+            out["by_class"][k] = {"bound": "hbm", "achieved": round(a, 2), "unit": "GB/s",
+                                  "frac": round(a / float(peaks["hbm_gbs"]), 5), "share": round(v["ms"] / total, 4),
+                                  "avg_launch_us": round(1e3 * v["ms"] / v["launches"], 1)}
     return out
 
 
@@ -460,49 +478,7 @@ def run_ours(args):
     Pmx1.free()
     # the homogenised tensor (Eq. (homog)): the d (d + 1) / 2 = 6 solves of the polarisation fields, TT in
     # lockstep (lrfg_problem_solve_many: one launch sequence for all six) against six full FP64 solves
-    Es6 = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 1.0]]
-    P6 = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tensor_tol, maxit=args.maxit,
-                     stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over,
-                     rank_start=args.rank_start, rank_step=args.rank_step)
-    P6.solve_many(Es6)
-    tensor_ms, tensor_tt = [], None
-    for _ in range(2):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tensor_tt = P6.solve_many(Es6)
-        e1.record(stream)
-        e1.synchronize()
-        tensor_ms.append(e0.elapsed_time(e1))
-    full6_ms, full6 = 0.0, []
-    for E6 in Es6:
-        ms1, r1 = timed_solves(Pfull, E6, 1, stream, flush)
-        full6_ms += ms1[0]
-        full6.append(r1[0])
-    tensor = {"tol": args.tensor_tol,
-              "tt_lockstep": {"solves_per_s": 6e3 / min(tensor_ms), "seconds": min(tensor_ms) / 1e3,
-                              "iters": [r.iters for r in tensor_tt]},
-              "full_fp64": {"solves_per_s": 6e3 / full6_ms, "seconds": full6_ms / 1e3},
-              "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(tensor_tt, full6))}
-    tensor["tt_vs_full_fp64"] = tensor["tt_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
-    P6.free()
-    Pmx6 = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tensor_tol, maxit=args.maxit,
-                       stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=lrfg.MIXED,
-                       rank_start=args.rank_start, rank_step=args.rank_step)
-    Pmx6.solve_many(Es6)
-    flush.fill_(1.0)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    mx6 = Pmx6.solve_many(Es6)
-    e1.record(stream)
-    e1.synchronize()
-    tensor["tt_mixed_lockstep"] = {"solves_per_s": 6e3 / e0.elapsed_time(e1),
-                                   "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(mx6, full6))}
-    tensor["tt_mixed_vs_full_fp64"] = tensor["tt_mixed_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
-    tensor["meets_1e-6"] = max(tensor["max_rel_err_vs_full"], tensor["tt_mixed_lockstep"]["max_rel_err_vs_full"]) <= 1e-6
-    Pmx6.free()
+    tensor = None if args.no_tensor else homogenised_tensor(ctx, args, a_tt, lr_fmt, Pfull, stream, flush)
     Pmx.free()
 
     # a batch of microstructures of this workload's recipe (seeds SEED + 1 .. SEED + count), one TT solve each
@@ -580,6 +556,57 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+def homogenised_tensor(ctx, args, a_tt, lr_fmt, Pfull, stream, flush):
+    """The homogenised tensor (Eq. (homog)): the d (d + 1) / 2 = 6 solves of the polarisation fields, TT in lockstep
+    (lrfg_problem_solve_many: one launch sequence for all six), FP64 and LRFG_MIXED, against six full FP64 solves."""
+    import torch
+    import paper_1902_07455_gb300 as lrfg
+    Es6 = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 1.0]]
+    P6 = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tensor_tol, maxit=args.maxit,
+                     stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over,
+                     rank_start=args.rank_start, rank_step=args.rank_step)
+    P6.solve_many(Es6)
+    tensor_ms, tensor_tt = [], None
+    for _ in range(2):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tensor_tt = P6.solve_many(Es6)
+        e1.record(stream)
+        e1.synchronize()
+        tensor_ms.append(e0.elapsed_time(e1))
+    full6_ms, full6 = 0.0, []
+    for E6 in Es6:
+        ms1, r1 = timed_solves(Pfull, E6, 1, stream, flush)
+        full6_ms += ms1[0]
+        full6.append(r1[0])
+    tensor = {"tol": args.tensor_tol,
+              "tt_lockstep": {"solves_per_s": 6e3 / min(tensor_ms), "seconds": min(tensor_ms) / 1e3,
+                              "iters": [r.iters for r in tensor_tt]},
+              "full_fp64": {"solves_per_s": 6e3 / full6_ms, "seconds": full6_ms / 1e3},
+              "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(tensor_tt, full6))}
+    tensor["tt_vs_full_fp64"] = tensor["tt_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
+    P6.free()
+    Pmx6 = ctx.problem(a_tt, lr_fmt, rank=args.rank, pinv_eps=args.pinv_eps, tol=args.tensor_tol, maxit=args.maxit,
+                       stop_on_increase=args.stop_on_increase, sketch_over=args.sketch_over, prec=lrfg.MIXED,
+                       rank_start=args.rank_start, rank_step=args.rank_step)
+    Pmx6.solve_many(Es6)
+    flush.fill_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mx6 = Pmx6.solve_many(Es6)
+    e1.record(stream)
+    e1.synchronize()
+    tensor["tt_mixed_lockstep"] = {"solves_per_s": 6e3 / e0.elapsed_time(e1),
+                                   "max_rel_err_vs_full": max(abs(a.Aeff - b.Aeff) / b.Aeff for a, b in zip(mx6, full6))}
+    tensor["tt_mixed_vs_full_fp64"] = tensor["tt_mixed_lockstep"]["solves_per_s"] / tensor["full_fp64"]["solves_per_s"]
+    tensor["meets_1e-6"] = max(tensor["max_rel_err_vs_full"], tensor["tt_mixed_lockstep"]["max_rel_err_vs_full"]) <= 1e-6
+    Pmx6.free()
+    return tensor
 
 
 def microstructure_batch(ctx, args, lr_fmt, stream, flush, count=8):

@@ -195,6 +195,37 @@ def tt_round(x, rmax=None, tol=None):
     return G
 
 
+def tt_truncate_left_orth(x, rmax=None, tol=None):
+    """Truncation of a TT whose carriages 1..d-1 are left-orthonormal (the second half of the rounding of
+    App. A.3.3 run from the right): for j = d-1 down to 1, the truncated SVD of carriage j unfolded as
+    r_{j-1} x (N_j r_j) = U S V^*, carriage j <- V^* (k rows), carriage j-1 <- carriage j-1 U S.  With the
+    left part orthonormal, that SVD is the SVD of the whole unfolding at bond j.  Fixed rank ``rmax`` and/or
+    relative tolerance ``tol`` (split evenly over the d-1 SVDs, as in tt_round)."""
+    d = len(x)
+    G = [g.copy() for g in x]
+    loc_tol = None if tol is None else tol / np.sqrt(max(d - 1, 1))
+    for j in range(d - 1, 0, -1):
+        a, n, b = G[j].shape
+        U, s, Vt = np.linalg.svd(G[j].reshape(a, n * b), full_matrices=False)
+        k = _keep(s, rmax, loc_tol)
+        G[j] = Vt[:k].reshape(k, n, b)
+        G[j - 1] = np.tensordot(G[j - 1], U[:, :k] * s[:k], axes=([2], [0]))
+    return G
+
+
+def tt_round_rl(x, rmax=None, tol=None):
+    """TT rounding in the other direction (App. A.3.3 mirrored): left-to-right orthogonalisation by QR, then
+    the truncated SVDs from right to left (tt_truncate_left_orth)."""
+    d = len(x)
+    G = [g.copy() for g in x]
+    for j in range(d - 1):
+        a, n, b = G[j].shape
+        Q, R = np.linalg.qr(G[j].reshape(a * n, b))
+        G[j] = Q.reshape(a, n, Q.shape[1])
+        G[j + 1] = np.tensordot(R, G[j + 1], axes=([1], [0]))
+    return tt_truncate_left_orth(G, rmax=rmax, tol=tol)
+
+
 def tt_zeros(shape, dtype=np.complex128):
     return [np.zeros((1, n, 1), dtype=dtype) for n in shape]
 

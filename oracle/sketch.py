@@ -11,10 +11,13 @@ A74-A95) replaces it for those products; this module restates it in plain NumPy:
          W_{d-1} = [1],   W_{j-1} = sum_n y_j[:, n, :] W_j omega_j[:, n, :]^T        (s_{j-1} x l_{j-1});
   2. sweep from the left: with the current left carriage X_j (unfolded (a n) x s_j),
          A = X_j W_j,  Q = orth(A),  X_j <- Q,  X_{j+1} <- (Q^* X_j) X_{j+1};
-  3. the result (ranks l_j, left-orthonormal) is rounded deterministically (App. A.3.3) to the target rank
-     or tolerance.
+  3. the result (ranks l_j, left-orthonormal) is truncated to the target rank or tolerance by the truncated
+     SVDs of App. A.3.3 taken from the right (lowrank.tt_truncate_left_orth): its carriages are already
+     left-orthonormal, so the orthogonalisation half of the deterministic rounding has nothing left to do,
+     and the truncation sweeps back from the right as the sketch method's authors do after their left sweep.
 When y has TT ranks <= l_j the sketch spans its unfoldings exactly and the result equals the deterministic
-rounding; otherwise it is a near-optimal approximation with high probability (op. cit.).
+rounding taken in that direction (lowrank.tt_round_rl: orthogonalise from the left, truncate from the right);
+otherwise it is a near-optimal approximation with high probability (op. cit.).
 
 The sketch carriages have Rademacher entries +-1 from the counter-based generator SplitMix64 (Steele, Lea
 and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): value i of stream `seed` is
@@ -62,7 +65,7 @@ def sketch_tt(shape, ell, seed: int):
 
 def tt_round_sketch(y, omega, rmax=None, tol=None, final=True):
     """Randomised TT rounding of y with the sketch TT omega (randomize-then-orthogonalize, then the
-    deterministic rounding of App. A.3.3 to rank rmax / tolerance tol; final=False: the left-orthonormal
+    truncated SVDs of App. A.3.3 from the right to rank rmax / tolerance tol; final=False: the left-orthonormal
     result of the sketch, of the sketch's ranks, without that last step)."""
     d = len(y)
     if d == 1:
@@ -82,4 +85,4 @@ def tt_round_sketch(y, omega, rmax=None, tol=None, final=True):
         x[j + 1] = np.tensordot(M, x[j + 1], axes=([1], [0]))
     if not final:
         return x
-    return _lr.tt_round(x, rmax=rmax, tol=tol)
+    return _lr.tt_truncate_left_orth(x, rmax=rmax, tol=tol)

@@ -8,7 +8,8 @@
 //   1. right-to-left contraction with a sketch TT Omega of ranks l:  W_{d-1} = Z_{d-1} Omega_{d-1}^T,
 //      W_{j-1} = sum_n Z_j[:, n, :] W_j Omega_j[:, n, :]^T;
 //   2. left to right: A = X_j W_j, Q = orth(A), X_j <- Q, X_{j+1} <- (Q^T X_j) x Z_{j+1};
-//   3. the rank-l result is rounded deterministically (tt_round_batch) to the target rank or tolerance.
+//   3. the rank-l result, left-orthonormal after step 2, is truncated to the target rank or tolerance by the
+//      truncated SVDs of App. A.3.3 taken from the right (truncate_left_orth, below).
 // The products are never formed: the middle carriage of a Khatri-Rao product Z_1 = x_1 (.) y_1 enters steps 1
 // and 2 through two fused kernels that contract x's and y's carriages one after the other (r_A^2 r l + r_A r^2 l
 // multiply-adds per fibre index instead of r_A^2 r^2 l), and the block-diagonal middle carriage of the
@@ -279,6 +280,95 @@ static void cholqr2(lrfg_ctx* ctx, const double* A, int m, int l, int nb, double
 }
 
 // ------------------------------------------------------------------------------------------------
+// Truncation of the left-orthonormal rank-l result, from the right (App. A.3.3's truncated SVDs with the
+// modes read backwards).  Carriages 0..d-2 of y are left-orthonormal, so at bond j (from d-1 down to 1) the
+// SVD of the whole unfolding is that of the current carriage j unfolded as a x (n b).  By Gram-SVD:
+//     S = C_w C_w^T = V diag(w) V^T   (C_w: carriage j with its last index scaled by the previous bond's
+//                                      singular values sqrt(w'); C_w = C at bond d-1),
+//     carriage j  <- V_k^T C          (k x n b; the weights stay in the carriages to the right),
+//     carriage j-1 <- carriage j-1 V_k (still left-orthonormal: V_k has orthonormal columns).
+// The trace of S is the squared norm of the tensor truncated so far, so the tolerance rule of tol_ranks applies
+// bond by bond with tol / sqrt(d-1), as in the rounding from the left.  No pivoted-Cholesky factor and no right
+// Gram sweep: the orthogonalisation half of the deterministic rounding was done by the sketch's left sweep.
+// ------------------------------------------------------------------------------------------------
+// out[item][row][t] = X[item][row][t] * sqrt(max(w[item][t], 0)) for t < k (w has stride ws per item)
+__global__ void scale_cols_sqrt_kernel(const double* __restrict__ X, const double* __restrict__ wg, int rows, int k,
+                                       int ws, double* __restrict__ out) {
+  const size_t item = blockIdx.y;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)rows * k) return;
+  const double w = wg[item * ws + (int)(t % k)];
+  out[item * (size_t)rows * k + t] = X[item * (size_t)rows * k + t] * (w > 0.0 ? sqrt(w) : 0.0);
+}
+
+static void truncate_left_orth(lrfg_ctx* ctx, const TTBatch& y, int rmax, TTBatch& out, double tol) {
+  const int d = y.d, nb = y.nb;
+  int kr[4] = {1, 1, 1, 1};
+  for (int j = d - 1; j >= 1; --j) kr[j] = std::min(rmax, std::min(y.r[j], y.N[j] * kr[j + 1]));
+  const double tol_j = d > 1 ? tol / std::sqrt((double)(d - 1)) : 0.0;
+  if (tol > 0.0) {
+    out.d = d;
+    out.nb = nb;
+    for (int j = 0; j < 3; ++j) out.N[j] = j < d ? y.N[j] : 0;
+    for (int j = 0; j < 4; ++j) out.r[j] = 1;
+  } else {
+    ttb_alloc(ctx, out, d, y.N, kr, nb);
+  }
+  // C: carriage j before its truncation (a x cols per item); Cw: the same with the last index weighted
+  const double* C = y.core[d - 1].get();
+  DBuf<double> Xp, Cw, wprev;
+  const double* Cg = C;
+  int b = 1;  // rank right of bond j after its truncation
+  for (int j = d - 1; j >= 1; --j) {
+    const int a = y.r[j], n = y.N[j], cols = n * b, kcap = kr[j];
+    const long long sc = (long long)a * cols, saa = (long long)a * a;
+    DBuf<double> S(ctx->pool, (size_t)saa * nb), w(ctx->pool, (size_t)a * nb), V(ctx->pool, (size_t)saa * nb);
+    gemm(ctx, 0, 1, a, a, cols, 1.0, Cg, cols, sc, Cg, cols, sc, 0.0, S.get(), a, saa, nb);
+    syevx(ctx, S.get(), w.get(), V.get(), a, kcap, nb);
+    int k = kcap;
+    if (tol > 0.0) {
+      DBuf<int> kd(ctx->pool, (size_t)nb);
+      tol_ranks(ctx, S.get(), nullptr, w.get(), V.get(), a, kcap, tol_j * tol_j, nb, kd.get());
+      std::vector<int> kh(nb);
+      LRFG_CUDA(cudaMemcpyAsync(kh.data(), kd.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+      LRFG_CUDA(cudaStreamSynchronize(ctx->stream));
+      k = 1;
+      for (int v : kh) k = std::max(k, std::min(v, kcap));
+      out.r[j] = k;
+      out.core[j] = DBuf<double>(ctx->pool, out.elems(j) * nb);
+    }
+    // carriage j of the output: V_k^T C (k x cols)
+    gemm(ctx, 1, 0, k, cols, a, 1.0, V.get(), a, saa, C, cols, sc, 0.0, out.core[j].get(), cols,
+         (long long)k * cols, nb);
+    // carriage j-1 times V_k: rows = r_{j-1} N_{j-1}
+    const int rows = y.r[j - 1] * y.N[j - 1];
+    const long long sx = (long long)rows * a, sk = (long long)rows * k;
+    double* dst;
+    DBuf<double> next;
+    if (j - 1 == 0) {
+      if (tol > 0.0) out.core[0] = DBuf<double>(ctx->pool, out.elems(0) * nb);
+      dst = out.core[0].get();
+    } else {
+      next = DBuf<double>(ctx->pool, (size_t)sk * nb);
+      dst = next.get();
+    }
+    gemm(ctx, 0, 0, rows, k, a, 1.0, y.core[j - 1].get(), a, sx, V.get(), a, saa, 0.0, dst, k, sk, nb);
+    if (j - 1 >= 1) {
+      // the next bond's Gram sees carriage j-1 with its last index weighted by this bond's singular values
+      DBuf<double> cw(ctx->pool, (size_t)sk * nb);
+      LRFG_LAUNCH(ctx, KC_TT_MISC, (double)sk * nb, 2.0 * sizeof(double) * sk * nb,
+                  scale_cols_sqrt_kernel<<<dim3((unsigned)((sk + 255) / 256), nb), 256, 0, ctx->stream>>>(
+                      dst, w.get(), rows, k, a, cw.get()));
+      Xp = std::move(next);
+      Cw = std::move(cw);
+      C = Xp.get();
+      Cg = Cw.get();
+      b = k;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // the rounding driver
 // ------------------------------------------------------------------------------------------------
 // A = X W for the left sweep: in FP64, or (fp32) X rounded to FP32 times the FP32 W, the result widened again
@@ -394,12 +484,12 @@ void tt_round_sketch(lrfg_ctx* ctx, const SketchSource& z, const TTView& omega, 
   y.core[jl] = DBuf<double>(ctx->pool, (size_t)sy * nb);
   gemm(ctx, 0, 0, l[jl], N[jl], s[jl], 1.0, M.get(), s[jl], (long long)l[jl] * s[jl], Zl.get(), N[jl], el, 0.0,
        y.core[jl].get(), N[jl], sy, nb);
-  // deterministic rounding of the rank-l result (or, without `final`, the rank-l result itself)
+  // truncation of the left-orthonormal rank-l result from the right (or, without `final`, that result itself)
   if (!final) {
     out = std::move(y);
     return;
   }
-  tt_round_batch(ctx, batch_view(y), rmax, out, tol);
+  truncate_left_orth(ctx, y, rmax, out, tol);
 }
 
 // ------------------------------------------------------------------------------------------------

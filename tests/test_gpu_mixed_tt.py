@@ -41,13 +41,18 @@ def test_mixed_apply_matches_fp64_oracle(ctx, d, N, rank, rx, over):
     P.free()
 
 
-@pytest.mark.parametrize("d,N,rank,over", [(3, 21, 6, 6), (2, 45, 8, 0), (3, 27, 8, 8)])
-def test_mixed_solve_matches_fp64_oracle(ctx, d, N, rank, over):
+# its: iterations over which the oracle's residual still falls at every step.  Past them the d = 3 cases sit at
+# their rank's truncation floor, where the residual rises and falls again (d = 3, N = 21, rank 6: 0.0190 at step
+# 7, 0.077 at 10, 0.0196 at 12) and the best iterate (Sec. 4.3) is a near-tie that FP32 transforms may decide
+# either way.
+@pytest.mark.parametrize("d,N,rank,over,its", [(3, 21, 6, 6, 6), (2, 45, 8, 0, 12), (3, 27, 8, 8, 4)])
+def test_mixed_solve_matches_fp64_oracle(ctx, d, N, rank, over, its):
     a = lr.tt_svd(lognormal_grf(d, N, ell=0.2, var=0.25, seed=7), rmax=8)
     E = np.eye(d)[0]
     op = lr.LowRankGaNi(a, (N,) * d, fmt="tt", rank=rank, pinv_eps=0.1, sketch=(over, 0) if over else None)
-    ref = lr.minres(op, E, tol=1e-14, maxit=12, stop_on_increase=False)
-    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-14, maxit=12,
+    ref = lr.minres(op, E, tol=1e-14, maxit=its, stop_on_increase=False)
+    assert ref["iters"] == its  # still falling at the last step
+    P = ctx.problem(lrfg.TTensor.from_numpy(a), lrfg.TT, rank=rank, pinv_eps=0.1, tol=1e-14, maxit=its,
                     stop_on_increase=False, sketch_over=over, prec=lrfg.MIXED)
     res, _ = P.solve(E, want_field=False)
     assert abs(res.Aeff - ref["Aeff"]) <= 1e-6 * ref["Aeff"], (res.Aeff, ref["Aeff"])

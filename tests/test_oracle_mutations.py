@@ -286,7 +286,7 @@ def _bad_round_sketch(carry=True, final=True, right_sweep_from_left=False):
                 x[j + 1] = np.tensordot(M, x[j + 1], axes=([1], [0]))
             else:
                 x[j + 1] = np.tensordot(np.eye(Q.shape[1], b), x[j + 1], axes=([1], [0]))
-        return lr.tt_round(x, rmax=rmax, tol=tol) if final else x
+        return lr.tt_truncate_left_orth(x, rmax=rmax, tol=tol) if final else x
     return bad
 
 
@@ -318,3 +318,31 @@ def test_ga_anisotropy_slips(monkeypatch, variant):
                 self.B = B
         monkeypatch.setattr(lr.LowRankGa, "homogenised_coefficient", aeff)
     _must_fail(tg.test_untruncated_lowrank_ga_with_anisotropy_matches_dense_galerkin, "tt", 5)
+
+
+def _bad_truncate_left_orth(variant):
+    def bad(x, rmax=None, tol=None):
+        d = len(x)
+        if variant == "from_the_left":
+            return lr.tt_round(x, rmax=rmax, tol=tol)
+        G = [g.copy() for g in x]
+        loc_tol = None if tol is None else (tol if variant == "tol_not_split" else tol / np.sqrt(max(d - 1, 1)))
+        for j in range(d - 1, 0, -1):
+            a, n, b = G[j].shape
+            U, s, Vt = np.linalg.svd(G[j].reshape(a, n * b), full_matrices=False)
+            k = lr._keep(s, rmax, loc_tol)
+            G[j] = Vt[:k].reshape(k, n, b)
+            carry = U[:, :k] if variant == "no_singular_values" else U[:, :k] * s[:k]
+            G[j - 1] = np.tensordot(G[j - 1], carry, axes=([2], [0]))
+        return G
+    return bad
+
+
+@pytest.mark.parametrize("variant", ["from_the_left", "no_singular_values"])
+def test_truncation_from_the_right_slips(monkeypatch, variant):
+    """The truncation that ends the randomised rounding: swept from the left instead, or carrying U without the
+    singular values into the carriage on the left."""
+    monkeypatch.setattr(lr, "tt_truncate_left_orth", _bad_truncate_left_orth(variant))
+    _must_fail(tsk.test_right_to_left_rounding_is_the_mirrored_rounding, (7, 9, 11), [4, 5], 3, None)
+    if variant == "no_singular_values":
+        _must_fail(tsk.test_right_to_left_rounding_at_one_bond_is_eckart_young)

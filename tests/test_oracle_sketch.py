@@ -46,7 +46,7 @@ def test_exact_when_the_sketch_covers_the_ranks(shape, ranks, ell, rmax):
     y = random_tt(shape, ranks, seed=3)
     om = sk.sketch_tt(shape, ell, seed=19)
     got = sk.tt_round_sketch(y, om, rmax=rmax)
-    ref = lr.tt_round(y, rmax=rmax)
+    ref = lr.tt_round_rl(y, rmax=rmax)
     # (a bond where the tensor's rank is below rmax may carry zero singular values on either side)
     assert all(r <= rmax for r in lr.tt_ranks(got))
     assert _rel(got, ref) <= 1e-11
@@ -65,10 +65,10 @@ def test_near_optimal_above_the_sketch_ranks():
         assert lr.tt_ranks(got) == [1, 6, 6, 1]
         e = _rel(got, z)
         assert e <= 1.5 * e_det, (e, e_det)
-        for G in got[:-1]:  # left-orthonormal carriages
+        for G in got[1:]:  # right-orthonormal carriages after the truncation from the right
             a, n, b = G.shape
-            M = G.reshape(a * n, b)
-            assert np.allclose(M.T @ M, np.eye(b), atol=1e-12)
+            M = G.reshape(a, n * b)
+            assert np.allclose(M @ M.T, np.eye(a), atol=1e-12)
 
 
 def test_sketch_with_tolerance_keeps_the_bound():
@@ -115,8 +115,56 @@ def test_kept_sketch_rank_is_the_sketch_projection():
     kept = sk.tt_round_sketch(y, om, rmax=3, final=False)
     assert lr.tt_ranks(kept)[1:-1] == [7, 7] or max(lr.tt_ranks(kept)) <= 7
     assert _rel(kept, y) <= 1e-12
-    assert _rel(lr.tt_round(kept, rmax=3), sk.tt_round_sketch(y, om, rmax=3)) <= 1e-12
+    assert _rel(lr.tt_truncate_left_orth(kept, rmax=3), sk.tt_round_sketch(y, om, rmax=3)) <= 1e-12
     for G in kept[:-1]:
         a, n, b = G.shape
         M = G.reshape(a * n, b)
         assert np.allclose(M.T @ M, np.eye(b), atol=1e-12)
+
+
+# ---- the truncation from the right that ends the randomised rounding -------------------------------------------
+def _mirror(x):
+    """The same tensor with its modes in reverse order: carriage j of the mirror is carriage d-1-j transposed."""
+    return [G.transpose(2, 1, 0).copy() for G in reversed(x)]
+
+
+@pytest.mark.parametrize("shape,ranks,rmax,tol", [((7, 9, 11), [4, 5], 3, None), ((9, 8, 10), [6, 7], 4, None),
+                                                  ((11, 13), [6], 3, None), ((8, 9, 10), [6, 6], 6, 0.2)])
+def test_right_to_left_rounding_is_the_mirrored_rounding(shape, ranks, rmax, tol):
+    # rounding from the left of the mirrored tensor, mirrored back, is rounding from the right: every SVD sees
+    # the same unfolding in the same order (App. A.3.3 with the modes read backwards)
+    y = random_tt(shape, ranks, seed=11)
+    got = lr.tt_round_rl(y, rmax=rmax, tol=tol)
+    ref = _mirror(lr.tt_round(_mirror(y), rmax=rmax, tol=tol))
+    assert lr.tt_ranks(got) == lr.tt_ranks(ref)
+    assert _rel(got, ref) <= 1e-11
+
+
+def test_right_to_left_rounding_at_one_bond_is_eckart_young():
+    # ranks [4, 5] rounded to 4: only the last bond loses rank, and the first SVD from the right sees the exact
+    # unfolding (N0 N1) x N2, so the result is its best rank-4 approximation (Eckart-Young), from the SVD of the
+    # full matrix; the first bond then has rank <= 4 already and is left as it is
+    shape = (7, 9, 11)
+    y = random_tt(shape, [4, 5], seed=12)
+    A = lr.tt_full(y)
+    U, s, Vt = np.linalg.svd(A.reshape(-1, shape[2]), full_matrices=False)
+    best = ((U[:, :4] * s[:4]) @ Vt[:4]).reshape(shape)
+    got = lr.tt_round_rl(y, rmax=4)
+    assert lr.tt_ranks(got) == [1, 4, 4, 1]
+    assert np.linalg.norm(lr.tt_full(got) - best) / np.linalg.norm(best) <= 1e-12
+
+
+def test_truncation_from_the_right_keeps_the_tolerance_bound():
+    shape = (12, 13, 14)
+    z = lr.tt_hadamard(random_tt(shape, [4, 4], seed=21), random_tt(shape, [4, 4], seed=22))
+    for tol in (0.3, 0.1, 0.01):
+        got = lr.tt_round_rl(z, tol=tol)
+        assert _rel(got, z) <= tol * (1 + 1e-12)
+    # and it is quasi-optimal at a fixed rank: within sqrt(d-1) of the best error of each unfolding combined
+    got = lr.tt_round_rl(z, rmax=5)
+    A = lr.tt_full(z)
+    tails = []
+    for j in range(1, 3):
+        s = np.linalg.svd(A.reshape(int(np.prod(shape[:j])), -1), compute_uv=False)
+        tails.append(np.sum(s[5:] ** 2))
+    assert np.linalg.norm(lr.tt_full(got) - A) ** 2 <= sum(tails) * (1 + 1e-9)
