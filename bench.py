@@ -473,7 +473,9 @@ def run_ours(args):
                        rank_start=args.rank_start, rank_step=args.rank_step, sketch_seed=1)
     mx_ms, mx_res = timed_solves([Pmx, Pmx1], E, 2, stream, flush)
     tt_mixed = {"solves_per_s": 2e3 / sum(mx_ms), "p50_ms": pct(mx_ms, 50), "p99_ms": pct(mx_ms, 99),
-                "sketch_seeds": [0, 1], "iters": [r.iters for r in mx_res], "aeff": mx_res[-1].Aeff,
+                "sketch_seeds": [0, 1], "iters": [r.iters for r in mx_res], "applies": [r.applies for r in mx_res],
+                "converged": [bool(r.converged) for r in mx_res], "ms": [round(m, 2) for m in mx_ms],
+                "aeff": mx_res[-1].Aeff,
                 "aeff_rel_err": max(abs(r.Aeff - full_res.Aeff) / full_res.Aeff for r in mx_res)}
     Pmx1.free()
     # the homogenised tensor (Eq. (homog)): the d (d + 1) / 2 = 6 solves of the polarisation fields, TT in
@@ -518,7 +520,8 @@ def run_ours(args):
             "tt_iters": res.iters, "tt_rel_resid": res.rel_resid, "tt_aeff": res.Aeff, "full_aeff": full_res.Aeff,
             "aeff_rel_err": rel_err, "meets_1e-6": rel_err <= 1e-6,
             "per_step": {"sketch_seed": list(range(len(results))), "iters": [r.iters for r in results],
-                         "applies": [r.applies for r in results], "ms": [round(m, 2) for m in step_ms],
+                         "applies": [r.applies for r in results], "converged": [bool(r.converged) for r in results],
+                         "ms": [round(m, 2) for m in step_ms],
                          "aeff_rel_err": [float("%.3g" % e) for e in errs]},
             "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
             "full": {"solves_per_s": 1e3 / statistics.median(full_ms), "p50_ms": pct(full_ms, 50),
