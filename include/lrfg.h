@@ -153,7 +153,7 @@ typedef struct {
                            An extension of the paper's method (Al Daas et al. 2023); LRFG_ENOTSUP elsewhere */
   unsigned int sketch_seed; /* SplitMix64 stream of that sketch */
   int sketch_keep;      /* with sketch_over > 0: 0 = the randomised truncations of the products end with the
-                           deterministic rounding to `rank`; 1 = they return the sketch's rank rank + sketch_over
+                           truncation from the right to `rank`; 1 = they return the sketch's rank rank + sketch_over
                            (the intermediate rank of the product truncations, the other truncations unchanged:
                            the operator's output then has rank rank + sketch_over) */
 } lrfg_opts;
@@ -278,9 +278,11 @@ lrfg_status lrfg_tucker_round_tol(lrfg_ctx* ctx, const lrfg_tucker* x, int rmax,
  *   2. W_{d-1} = x_{d-1} Omega_{d-1}^T, W_{j-1} = sum_n x_j[:, n, :] W_j Omega_j[:, n, :]^T (right to left);
  *   3. left to right: A = X_j W_j, Q = orth(A) (CholeskyQR2, directions below ~1e-6 of the largest singular
  *      value at the bond dropped), X_j <- Q, X_{j+1} <- (Q^T X_j) x_{j+1};
- *   4. the rank-ell result rounded deterministically to ranks <= rmax (tol > 0: the smallest such ranks within
- *      the relative tolerance tol, as lrfg_tt_round_tol).
- * When x's ranks do not exceed ell the result equals lrfg_tt_round's (up to rounding).  d = 2 or 3.  out->r is
+ *   4. the rank-ell result, left-orthonormal after step 3, truncated to ranks <= rmax by the truncated SVDs of
+ *      App. A.3.3 taken from the right (tol > 0: the smallest such ranks within the relative tolerance tol,
+ *      tol / sqrt(d-1) per bond, as lrfg_tt_round_tol).
+ * When x's ranks do not exceed ell the result equals the deterministic rounding taken in that direction (up to
+ * rounding); that is lrfg_tt_round's result for d = 2, or when only one bond loses rank.  d = 2 or 3.  out->r is
  * set; out->cores must each hold min(rmax, ..) N[j] min(rmax, ..) doubles. */
 lrfg_status lrfg_tt_round_sketch(lrfg_ctx* ctx, const lrfg_tt* x, int ell, unsigned long long seed, int rmax,
                                  double tol, lrfg_tt* out);
