@@ -54,3 +54,24 @@ def test_single_process_is_identity():
     import bench
     assert bench.reduce_max(3.5, "cpu") == 3.5
     assert bench.job_throughput(5, 1, 2.0) == 2.5
+
+
+def test_roofline_of_the_dominant_class_and_every_class():
+    """bench.roofline: the dominant class (by time) against its bound's peak, and every class beside it."""
+    import bench
+    stats = {"gemm": {"ms": 200.0, "launches": 4000, "flops": 1.0e11, "bytes": 1.0e9},
+             "eigen": {"ms": 260.0, "launches": 1800, "flops": 1.2e8, "bytes": 1.0e6},
+             "tt_misc": {"ms": 30.0, "launches": 4000, "flops": 2.0e8, "bytes": 3.0e9},
+             "khatri_rao": {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0}}
+    out = bench.roofline(stats, fp64_peak=1.25)
+    assert out["kernel_class"] == "eigen" and out["bound"] == "alu"
+    assert abs(out["achieved"] - 1.2e8 / 0.26 / 1e12) <= 1e-12
+    assert abs(out["frac"] - out["achieved"] / 1.25) <= 1e-12
+    assert abs(out["share"] - 260.0 / 490.0) <= 1e-12
+    by = out["by_class"]
+    assert set(by) == {"gemm", "eigen", "tt_misc"}  # classes without launches are left out
+    assert by["gemm"]["bound"] == "alu" and abs(by["gemm"]["frac"] - 0.4) <= 1e-4
+    peaks, _ = bench.measured_peaks()
+    assert by["tt_misc"]["bound"] == "hbm" and by["tt_misc"]["unit"] == "GB/s"
+    assert abs(by["tt_misc"]["achieved"] - 100.0) <= 0.01
+    assert abs(by["tt_misc"]["frac"] - 100.0 / float(peaks["hbm_gbs"])) <= 1e-4
