@@ -168,3 +168,15 @@ def test_truncation_from_the_right_keeps_the_tolerance_bound():
         s = np.linalg.svd(A.reshape(int(np.prod(shape[:j])), -1), compute_uv=False)
         tails.append(np.sum(s[5:] ** 2))
     assert np.linalg.norm(lr.tt_full(got) - A) ** 2 <= sum(tails) * (1 + 1e-9)
+
+
+def test_right_to_left_rounding_leaves_right_orthonormal_carriages():
+    # after the truncations from the right, carriages 1..d-1 have orthonormal rows (their SVD factors V^*) and the
+    # first carriage carries the norm
+    z = lr.tt_hadamard(random_tt((9, 10, 11), [4, 4], seed=31), random_tt((9, 10, 11), [3, 4], seed=32))
+    got = lr.tt_round_rl(z, rmax=6)
+    for G in got[1:]:
+        a, n, b = G.shape
+        M = G.reshape(a, n * b)
+        assert np.abs(M @ M.T - np.eye(a)).max() <= 1e-13
+    assert abs(np.linalg.norm(got[0]) - np.linalg.norm(lr.tt_full(got))) <= 1e-12 * np.linalg.norm(got[0])
