@@ -75,3 +75,18 @@ def test_roofline_of_the_dominant_class_and_every_class():
     assert by["tt_misc"]["bound"] == "hbm" and by["tt_misc"]["unit"] == "GB/s"
     assert abs(by["tt_misc"]["achieved"] - 100.0) <= 0.01
     assert abs(by["tt_misc"]["frac"] - 100.0 / float(peaks["hbm_gbs"])) <= 1e-4
+
+
+def test_default_workload_has_its_stored_oracle_solve(monkeypatch):
+    """The default bench options match the oracle's stored solve (tests/golden), so the CPU baseline and the
+    reference arm time the same workload instead of reporting it unavailable; the stored counts are consistent."""
+    import sys
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    got = bench.oracle_applies_per_solve(args)
+    assert got is not None
+    applies, g = got
+    assert applies == sum(g["applies_by_rank"].values())
+    assert set(g["applies_by_rank"]) <= {str(r) for r in range(args.rank_start, args.rank + 1, args.rank_step)}
+    assert g["rel_resid"] <= args.tt_tol
