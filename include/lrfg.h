@@ -177,7 +177,10 @@ typedef struct {
  * lrfg_destroy fails with LRFG_EINVAL while problems or fields of the context are still alive. */
 lrfg_status lrfg_create(lrfg_ctx** ctx, int device, void* stream, size_t hbm_budget_bytes);
 lrfg_status lrfg_destroy(lrfg_ctx* ctx);
+/* A static string naming a status (never NULL). */
 const char* lrfg_strerror(lrfg_status st);
+/* The message of the context's last failed call ("" after a success); owned by the context, valid until its
+ * next call. */
 const char* lrfg_last_error(const lrfg_ctx* ctx);
 /* Wait for the context's stream. */
 lrfg_status lrfg_sync(lrfg_ctx* ctx);
@@ -335,6 +338,7 @@ lrfg_status lrfg_tt_expand(lrfg_ctx* ctx, const lrfg_tt* x, double* values);
  * (opts->rank when 0), with the tolerance opts->rank_tol when it is > 0. */
 lrfg_status lrfg_problem_create(lrfg_ctx* ctx, const lrfg_coeff* coeff, const lrfg_opts* opts,
                                 lrfg_problem** problem);
+/* Waits for the context's stream, then releases the problem (LRFG_EINVAL for NULL). */
 lrfg_status lrfg_problem_free(lrfg_problem* problem);
 /* TT ranks of the resident coefficient (r_A), or all 1 for LRFG_FULL. */
 lrfg_status lrfg_problem_coeff_ranks(const lrfg_problem* problem, int ranks[4]);
@@ -468,6 +472,7 @@ lrfg_status lrfg_field_info(const lrfg_field* f, lrfg_format* fmt, int* d, int N
 lrfg_status lrfg_field_export_full(lrfg_ctx* ctx, const lrfg_field* f, double* values, int on_device);
 /* TT carriages of a TT field into caller buffers of the sizes lrfg_field_info implies. */
 lrfg_status lrfg_field_export_tt(lrfg_ctx* ctx, const lrfg_field* f, double* const cores[3], int on_device);
+/* Waits for the context's stream, then releases the field (LRFG_EINVAL for NULL). */
 lrfg_status lrfg_field_free(lrfg_field* f);
 
 #ifdef __cplusplus
