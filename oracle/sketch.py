@@ -14,7 +14,7 @@ A74-A95) replaces it for those products; this module restates it in plain NumPy:
   3. the result (ranks l_j, left-orthonormal) is truncated to the target rank or tolerance by the truncated
      SVDs of App. A.3.3 taken from the right (lowrank.tt_truncate_left_orth): its carriages are already
      left-orthonormal, so the orthogonalisation half of the deterministic rounding has nothing left to do,
-     and the truncation sweeps back from the right as the sketch method's authors do after their left sweep.
+     and one sweep of truncated SVDs from the right completes it.
 When y has TT ranks <= l_j the sketch spans its unfoldings exactly and the result equals the deterministic
 rounding taken in that direction (lowrank.tt_round_rl: orthogonalise from the left, truncate from the right);
 otherwise it is a near-optimal approximation with high probability (op. cit.).
