@@ -346,3 +346,55 @@ def test_truncation_from_the_right_slips(monkeypatch, variant):
     _must_fail(tsk.test_right_to_left_rounding_is_the_mirrored_rounding, (7, 9, 11), [4, 5], 3, None)
     if variant == "no_singular_values":
         _must_fail(tsk.test_right_to_left_rounding_at_one_bond_is_eckart_young)
+
+
+# ---- planted mistakes in the exponential sum and the Tucker / CP truncations ------------------------------------
+import oracle.expsum as es_mod  # noqa: E402
+
+
+def test_expsum_weights_off_by_a_factor(monkeypatch):
+    """The sinc-quadrature weights h e^tau with h taken from the wrong step (a 5% larger h in the weights)."""
+    orig = es_mod.expsum_inverse
+
+    def bad(xmax, eps):
+        t, w = orig(xmax, eps)
+        return t, 1.05 * w
+    monkeypatch.setattr(es_mod, "expsum_inverse", bad)
+    _must_fail(tl.test_expsum_inverse_accuracy, 63, 2, 1e-2)
+
+
+def test_cp_truncation_without_its_weights(monkeypatch):
+    """App. A.1.3 with the weights c left out of the SVD of R1 diag(c) R2^T (reading 10)."""
+    def bad(x, rmax=None, tol=None):
+        c, B1, B2 = x
+        Q1, R1 = np.linalg.qr(B1)
+        Q2, R2 = np.linalg.qr(B2)
+        U, s, Vt = np.linalg.svd(R1 @ R2.T, full_matrices=False)
+        k = lr._keep(s, rmax, tol)
+        return s[:k], Q1 @ U[:, :k], Q2 @ Vt[:k].T
+    monkeypatch.setattr(lr, "cp_round", bad)
+    _must_fail(tl.test_cp_truncation_is_eckart_young)
+
+
+def test_hosvd_with_the_wrong_unfolding(monkeypatch):
+    """HOSVD factors from the tensor reshaped row-major to N_j x (rest) instead of unfolded along mode j."""
+    def bad(A, rmax=None, tol=None):
+        d = A.ndim
+        factors = []
+        loc_tol = None if tol is None else tol / np.sqrt(d)
+        for j in range(d):
+            M = A.reshape(A.shape[j], -1)
+            U, s, _ = np.linalg.svd(M, full_matrices=False)
+            factors.append(U[:, :lr._keep(s, rmax, loc_tol)])
+        core = A
+        for j, B in enumerate(factors):
+            core = np.moveaxis(np.tensordot(B.conj().T, core, axes=([1], [j])), 0, j)
+        return core, factors
+    monkeypatch.setattr(lr, "tucker_hosvd", bad)
+    _must_fail(tl.test_tt_svd_and_hosvd_error_bounds)
+
+
+def test_truncation_from_the_right_with_the_tolerance_not_split(monkeypatch):
+    """The truncation from the right with the whole tolerance at every bond instead of tol / sqrt(d - 1)."""
+    monkeypatch.setattr(lr, "tt_truncate_left_orth", _bad_truncate_left_orth("tol_not_split"))
+    _must_fail(tsk.test_truncation_from_the_right_keeps_the_tolerance_bound)
